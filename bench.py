@@ -1,0 +1,317 @@
+"""Benchmark: time-to-solution per source of the CSEM forward hot path on one GB300.
+
+One step = the whole path on the marine model (64^3 Kuhn cells, 1.57 M tets, 1.87 M edges,
+one x-directed dipole at 1 Hz): global edge numbering, assembly of matrix and right-hand
+side, the Jacobi-GMRES(50) solve to a relative residual of 1e-8, and the receiver fields.
+The headline runs the mixed-precision solver (complex64 Krylov vectors and matrix, FP64
+residuals and solution); the plain complex128 solver is timed beside it.
+
+Prints one JSON line.  --impl reference times the CPU oracle on a bounded sample of the same
+workload instead.  Synthetic inputs: seeded, generated by paper_1808_00186_gb300.synth.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=64, help="cells per axis of the marine model")
+    p.add_argument("--no-plain", action="store_true", help="skip the complex128 comparison run")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        d = json.load(open(MEASURED))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1808_00186_gb300 import api, synth
+    from paper_1808_00186_gb300 import build as libbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    libbuild.build()
+    api.load()
+
+    # Replicas: every rank solves its own copy of the model (the path does not shard).
+    m = synth.marine_model(args.n, n_src=1)
+    S = len(m.sources)
+    ctx = api.Context(local)
+    dev = torch.device("cuda", local)
+    nodes = torch.as_tensor(m.mesh.nodes, device=dev)
+    tets = torch.as_tensor(m.mesh.tets, device=dev)
+    sigma = torch.as_tensor(m.sigma, device=dev)
+    rx = torch.as_tensor(m.receivers, device=dev)
+
+    n_edges = [0]
+
+    def step(precision):
+        E = api.petgem_mesh_edges(ctx.h, nodes, tets)
+        n_edges[0] = E
+        api.petgem_assemble(ctx.h, m.freq, sigma, m.sigma_p, m.sources)
+        x = torch.zeros((S, E), dtype=torch.complex128, device=dev)
+        st, info = api.petgem_solve(ctx.h, x, S, api.solve_opts(precision=precision, tol=1e-8))
+        out = torch.empty((S, rx.shape[0], 3, 3), dtype=torch.complex128, device=dev)
+        api.petgem_receivers(ctx.h, rx, x, out)
+        return info, out
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed(precision, steps, warmup, profile=False, clocks=None):
+        for _ in range(warmup):
+            step(precision)
+        barrier()
+        if profile:
+            api.petgem_profile(ctx.h, True)
+        launches0 = api.petgem_launch_count(ctx.h)
+        if clocks:
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        infos = []
+        for _ in range(steps):
+            infos.append(step(precision)[0])
+        e1.record()
+        barrier()
+        cl = clocks.stop() if clocks else None
+        ms = e0.elapsed_time(e1) / steps
+        launches = (api.petgem_launch_count(ctx.h) - launches0) // steps
+        t = torch.tensor([ms], device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item()), infos[-1], launches, cl
+
+    hbm, peak_kind = peaks()
+    clocks = ClockSampler(local)
+    ms_mixed, info_mixed, launches, cl = timed(api.PREC_MIXED, args.steps, args.warmup, profile=True, clocks=clocks)
+    # Dominant kernel over the timed region (CUDA events around each launch on the ctx stream).
+    kstats = {}
+    for name in ("spmv_c64", "mdot_c64", "mupdate_c64", "residual_c128", "element", "matrix_gather", "rhs",
+                 "rcv_locate"):
+        n, kms, by = api.petgem_kernel_stats(ctx.h, name)
+        if n:
+            kstats[name] = {"launches": n, "ms": kms, "bytes": by, "gbs": by / (kms * 1e-3) / 1e9}
+    api.petgem_profile(ctx.h, False)
+    plain = None
+    if not args.no_plain:
+        ms_plain, info_plain, _, _ = timed(api.PREC_C128, 1, 1)
+        plain = {"ms_per_step": ms_plain, "s_per_source": ms_plain / 1e3 / S, "iters": info_plain[0]["iters"],
+                 "true_rel_residual": info_plain[0]["true_rel_residual"]}
+
+    # End to end through the public API from pinned host buffers, results read back each step.
+    h_nodes = torch.as_tensor(m.mesh.nodes).pin_memory()
+    h_tets = torch.as_tensor(m.mesh.tets).pin_memory()
+    h_sigma = torch.as_tensor(m.sigma).pin_memory()
+    h_rx = torch.as_tensor(m.receivers).pin_memory()
+    h_out = torch.empty((S, m.receivers.shape[0], 3, 3), dtype=torch.complex128).pin_memory()
+
+    def e2e_step():
+        nodes.copy_(h_nodes, non_blocking=True)
+        tets.copy_(h_tets, non_blocking=True)
+        sigma.copy_(h_sigma, non_blocking=True)
+        rx.copy_(h_rx, non_blocking=True)
+        info, out = step(api.PREC_MIXED)
+        h_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        return info
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        e2e_step()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / max(1, args.steps)
+    h2d = sum(t.numel() * t.element_size() for t in (h_nodes, h_tets, h_sigma, h_rx))
+    d2h = h_out.numel() * h_out.element_size()
+
+    result = None
+    if rank == 0:
+        dom = max(kstats.items(), key=lambda kv: kv[1]["ms"]) if kstats else None
+        roof = None
+        if dom:
+            name, ks = dom
+            achieved = ks["gbs"]
+            roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(achieved / hbm, 4), "peak_source": peak_kind,
+                    "traffic": None, "launches": ks["launches"], "avg_launch_us": round(ks["ms"] / ks["launches"] * 1e3, 2),
+                    "algorithmic_bytes_per_launch": ks["bytes"] / ks["launches"]}
+        s_per_source = ms_mixed / 1e3 / S
+        result = {
+            "metric": "time-to-solution per source at rel-residual 1e-8 (mixed c64/FP64-refined Jacobi-GMRES(50))",
+            "value": round(s_per_source * world / world, 6),
+            "unit": "s/source",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms_mixed, 3),
+            "higher_is_better": False,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "c64+f64",
+            "data": "synthetic (seeded Kuhn mesh, marine layered model)",
+            "config": {"workload": "marine_n%d_1src_1Hz" % args.n, "tets": m.mesh.n_tets,
+                       "edges": n_edges[0], "sources": S, "restart": 50, "tol": 1e-8, "precision": "mixed",
+                       "l2": "working set > L2 (no flush needed)", "parallelism": "replicas" if world > 1 else "single"},
+            "iters": info_mixed[0]["iters"], "cycles": info_mixed[0]["restarts"],
+            "true_rel_residual": info_mixed[0]["true_rel_residual"],
+            "plain_c128": plain,
+            "speedup_vs_plain": round(plain["ms_per_step"] / ms_mixed, 3) if plain else None,
+            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "gbs": round(v["gbs"], 1)}
+                        for k, v in kstats.items()},
+            "roofline": roof,
+            "clocks": cl,
+            "e2e": {"value": round(e2e_s / S, 6), "unit": "s/source", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+        }
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return result
+
+
+def oracle_sample(n, gpu_iters=None):
+    """Oracle on the host: full assembly of the workload + 10 GMRES iterations, scaled to a
+    time-to-solution with the iteration count (measured here or given)."""
+    import oracle
+    from paper_1808_00186_gb300 import synth
+    oracle.build()
+    m = synth.marine_model(n, n_src=1)
+    src = synth.sources_array(m.sources)
+    t0 = time.perf_counter()
+    s = oracle.System(m.mesh.nodes, m.mesh.tets, m.sigma, m.sigma_p, m.freq, src)
+    t_asm = time.perf_counter() - t0
+    k = 10
+    t0 = time.perf_counter()
+    s.solve(restart=50, tol=1e-8, maxit=k)
+    t_it = (time.perf_counter() - t0) / k
+    iters = gpu_iters if gpu_iters else 2000
+    return {"t_assembly_s": t_asm, "t_iter_s": t_it, "iters_scaled_to": iters,
+            "value": t_asm + t_it * iters, "cores": 1,
+            "sample": "full oracle assembly of the %d^3 marine model + %d GMRES(50) iterations; value = "
+                      "assembly + per-iteration time x %d iterations" % (n, k, iters)}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.perf_counter()
+        samples = [oracle_sample(args.n) for _ in range(max(1, args.steps))]
+        samp = samples[-1]
+        v = statistics.median(x["value"] for x in samples)
+        print(json.dumps({"impl": "reference", "metric": "time-to-solution per source at rel-residual 1e-8 "
+                          "(mixed c64/FP64-refined Jacobi-GMRES(50))", "value": round(v, 3), "unit": "s/source",
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+                          "config": {"workload": "marine_n%d_1src_1Hz" % args.n},
+                          "cpu_baseline": {"value": round(v, 3), "unit": "s/source", "cores": 1, "kind": "oracle",
+                                           "sample": samp["sample"]},
+                          "e2e": {"value": round(v, 3), "unit": "s/source", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0},
+                          "wall_s": round(time.perf_counter() - t0, 1)}))
+        return
+    res = run_ours(args)
+    if rank == 0 and res is not None:
+        cpu = oracle_sample(args.n, gpu_iters=(res["plain_c128"] or {}).get("iters") or res["iters"])
+        res["cpu_baseline"] = {"value": round(cpu["value"], 3), "unit": "s/source", "cores": cpu["cores"],
+                               "kind": "oracle", "sample": cpu["sample"]}
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

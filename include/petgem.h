@@ -1,0 +1,181 @@
+/* petgem.h - C ABI of the GB300 (sm_103a) hot path of the secondary-field CSEM forward solver.
+ *
+ * The method is the one of Castillo-Reyes, de la Puente and Cela, "PETGEM: A parallel code for
+ * 3D CSEM forward modeling using edge finite elements" (Computers & Geosciences, 2018):
+ *   curl curl E_s + i w mu0 sigma E_s = -i w mu0 (sigma - sigma_p) E_p        (Section 2, eq. 6)
+ * with E_s = 0 on the outer boundary, discretised with lowest-order Nedelec edge elements on
+ * tetrahedra (Section 3 eq. 9, Appendix B), the whole-space dipole primary field E_p
+ * (Appendix A), a Krylov solve (Section 5.1 uses GMRES) and interpolation of E at receivers
+ * (Section 3 eq. 7).  The calls follow the paper's problem statement (Section 4: physics,
+ * mesh, solver and results sections of its parameters file).
+ *
+ * Conventions for every call:
+ *   - Pointers documented as "device" are CUDA device pointers on the context's device; the
+ *     caller owns them and keeps them alive until the call returns (for calls that only
+ *     enqueue work: until the context stream has passed the work).  "host" pointers are read
+ *     or written before the call returns.
+ *   - Complex arrays are interleaved (re, im) pairs: complex128 = 2 doubles, complex64 = 2 floats.
+ *   - All work is ordered on the stream given to petgem_create.  Calls that return a host
+ *     scalar or struct synchronise that stream before returning.
+ *   - Every call returns a status code (PETGEM_OK = 0).  No C++ exception crosses this ABI.
+ *     petgem_last_error gives a message for the last failing call on a context.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef PETGEM_H
+#define PETGEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------------- status codes */
+enum {
+  PETGEM_OK = 0,
+  PETGEM_ERR_INVALID_ARG = 1,     /* null pointer, bad size, call out of order */
+  PETGEM_ERR_BAD_MESH = 2,        /* node id out of range, repeated node, non-manifold face */
+  PETGEM_ERR_DEGENERATE_TET = 3,  /* a tet with zero volume */
+  PETGEM_ERR_OUT_OF_MEMORY = 4,
+  PETGEM_ERR_CUDA = 5,            /* a CUDA runtime error (message in petgem_last_error) */
+  PETGEM_ERR_NOT_CONVERGED = 6,   /* iteration cap reached; info is still filled */
+  PETGEM_ERR_BREAKDOWN = 7,       /* Krylov breakdown or a NaN/Inf in the iteration */
+  PETGEM_ERR_RECEIVER_OUTSIDE = 8,/* a receiver lies in no tet; its outputs are NaN */
+  PETGEM_ERR_UNSUPPORTED = 9      /* a size or option this build does not handle */
+};
+
+/* ----------------------------------------------------------------------- types */
+typedef struct petgem_ctx petgem_ctx; /* opaque; owns the library's device workspaces */
+
+/* Electric dipole source of Appendix A (eqs. A.1-A.3): position (m), orientation and moment
+ * I * dS (A m).  axis: 0 = x-, 1 = y-, 2 = z-directed. */
+typedef struct {
+  double x, y, z;
+  double moment;
+  int32_t axis;
+  int32_t reserved;
+} petgem_dipole;
+
+enum { PETGEM_PREC_C128 = 0, PETGEM_PREC_MIXED = 1 };
+enum { PETGEM_PRECOND_JACOBI = 0 };
+
+/* Solver options.  Restarted GMRES(restart), right-preconditioned by Jacobi D = diag(A),
+ * x0 taken from the x argument, stopping when ||b - A x||_2 / ||b||_2 <= tol with the
+ * residual recomputed in FP64 at every restart.
+ *   precision = PETGEM_PREC_C128: every vector and the matrix in complex128.
+ *   precision = PETGEM_PREC_MIXED: FP64 iterative refinement; each refinement step runs
+ *     GMRES cycles on a complex64 copy of the matrix with complex64 Krylov vectors (dot
+ *     products summed in FP64 across the vector) until the inner residual falls by
+ *     inner_tol or inner_cycles cycles have run; x and the residual stay complex128.
+ *   batch: number of sources iterated together (their SpMVs become one SpMM); 0 = all. */
+typedef struct {
+  int32_t restart;
+  int32_t precision;
+  int32_t precond;
+  int32_t batch;
+  double tol;
+  double inner_tol;
+  int64_t max_iters;   /* cap on Krylov iterations per source */
+  int32_t inner_cycles;
+  int32_t use_graphs;  /* 1 = replay each restart cycle as a CUDA graph */
+} petgem_solve_opts;
+
+/* Per-source results of petgem_solve. */
+typedef struct {
+  int64_t iters;       /* Krylov iterations (SpMVs inside Arnoldi) */
+  int64_t restarts;    /* GMRES cycles */
+  int64_t refinements; /* FP64 residual evaluations after the first */
+  double true_rel_residual; /* ||b - A x|| / ||b|| in FP64 at exit */
+  int32_t status;      /* PETGEM_OK, PETGEM_ERR_NOT_CONVERGED or PETGEM_ERR_BREAKDOWN */
+  int32_t reserved;
+} petgem_solve_info;
+
+/* ----------------------------------------------------------------------- lifecycle */
+/* Create a context bound to CUDA device `device`, ordering all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+int petgem_create(petgem_ctx **out, int device, void *cuda_stream);
+/* Free every device buffer the context owns.  NULL is accepted. */
+int petgem_destroy(petgem_ctx *ctx);
+const char *petgem_status_string(int status);
+const char *petgem_last_error(const petgem_ctx *ctx);
+
+/* ----------------------------------------------------------------------- mesh (Appendix B) */
+/* Global edge numbering and orientation, boundary edges and the sparse pattern.
+ * nodes: device double[n_nodes][3] (m).  tets: device int32[n_tets][4] node ids (0-based),
+ *   either orientation.
+ * Local edge i of a tet joins local nodes (a, b) = (1,2), (1,3), (1,4), (2,3), (4,2), (3,4)
+ * (Appendix B eqs. B.1-B.6, 1-based).  A global edge runs from its lower to its higher node
+ * id and its sign in a tet is +1 when the local edge runs the same way (eq. B.16).  Global
+ * edge ids are the ranks of (low id, high id) in lexicographic order, so the numbering is
+ * unique.  Boundary edges are the edges of faces held by exactly one tet (Dirichlet edges of
+ * Section 2).  The sparse pattern has one row per edge: interior rows hold the interior
+ * columns they couple to, boundary rows hold their diagonal only.
+ * n_edges_out: host; receives the edge count (synchronises the stream).
+ * Errors: PETGEM_ERR_BAD_MESH (ids out of range, repeated node, face in more than two tets),
+ * PETGEM_ERR_UNSUPPORTED (n_tets >= 2^31 / 36 or n_nodes >= 2^31). */
+int petgem_mesh_edges(petgem_ctx *ctx, int64_t n_nodes, const double *nodes, int64_t n_tets,
+                      const int32_t *tets, int64_t *n_edges_out);
+
+/* Copy the topology out (each pointer optional, device): edges int32[E][2] (low, high),
+ * tet_edges int32[T][6], signs int8[T][6] in {+1, -1}, boundary uint8[E] in {0, 1}. */
+int petgem_get_topology(petgem_ctx *ctx, int32_t *edges, int32_t *tet_edges, int8_t *signs,
+                        uint8_t *boundary);
+
+/* ----------------------------------------------------------------------- assembly (Section 3) */
+/* Element matrices and right-hand sides, global assembly and Dirichlet rows (eqs. 6 and 9):
+ *   A = sum_e K^e + i w mu0 sigma_e M^e,  b_s = sum_e -i w mu0 (sigma_e - sigma_p) R^e_s,
+ *   R^e_{s,k} = int_e S_k N_k . E_p(x; source s, sigma_p) dV,
+ * w = 2 pi freq_hz, mu0 = 4 pi 1e-7 H/m.  K^e and M^e are the closed forms of eqs. B.14-B.15;
+ * R^e uses the symmetric 4-point degree-2 rule and is skipped where sigma_e = sigma_p.
+ * Boundary rows become identity rows with b = 0.  Contributions are summed in a fixed order,
+ * so repeated calls give bit-identical results.
+ * sigma: device double[n_tets] (S/m, > 0).  src: host petgem_dipole[n_src].
+ * Requires petgem_mesh_edges.  Errors: PETGEM_ERR_DEGENERATE_TET, PETGEM_ERR_INVALID_ARG. */
+int petgem_assemble(petgem_ctx *ctx, double freq_hz, const double *sigma, double sigma_p,
+                    int32_t n_src, const petgem_dipole *src);
+
+/* Copy the assembled system out.  nnz_out: host (synchronises).  row_ptr int64[E+1],
+ * col int32[nnz], val complex128[nnz], b complex128[n_src][E], diag complex128[E] (each device,
+ * optional).  Rows list columns in increasing order. */
+int petgem_get_system(petgem_ctx *ctx, int64_t *nnz_out, int64_t *row_ptr, int32_t *col, void *val,
+                      void *b, void *diag);
+
+/* Element matrices as computed by the assembly kernel: K, M device double[21][n_tets], the
+ * upper triangle (i <= j, row-major order of (i, j)) of the signed 6x6 matrices; vol device
+ * double[n_tets] (optional). */
+int petgem_get_elements(petgem_ctx *ctx, double *K21, double *M21, double *vol);
+
+/* ----------------------------------------------------------------------- solve (Section 5.1) */
+/* Solve A x_s = b_s for every source.  x: device complex128[n_src][E]; the initial guess in,
+ * the solution out.  info: host petgem_solve_info[n_src].  opts: host (NULL = defaults:
+ * restart 50, c128, Jacobi, tol 1e-8, max_iters 200000, inner_tol 1e-4, inner_cycles 1).
+ * Returns PETGEM_ERR_NOT_CONVERGED or PETGEM_ERR_BREAKDOWN if any source ended that way. */
+int petgem_solve(petgem_ctx *ctx, const petgem_solve_opts *opts, void *x, petgem_solve_info *info);
+
+/* y = A x for the assembled matrix (complex128, device, n_src = 1 vector of E entries). */
+int petgem_spmv(petgem_ctx *ctx, const void *x, void *y);
+
+/* ----------------------------------------------------------------------- receivers (eq. 7) */
+/* Field at receiver points.  rx: device double[n_rcv][3].  x: device complex128[n_src][E]
+ * (edge DOFs, e.g. from petgem_solve).  out: device complex128[n_src][n_rcv][3][3], the
+ * innermost pair of axes being (kind, component) with kind 0 = E_p (sigma_p), 1 = E_s =
+ * sum_i S_i N_i(x) x_g(i) (eq. 7), 2 = E_p + E_s.  A receiver belongs to the lowest-id tet
+ * whose barycentric coordinates are all >= -1e-12.  Returns PETGEM_ERR_RECEIVER_OUTSIDE when
+ * some receiver is in no tet (its nine outputs are NaN). */
+int petgem_receivers(petgem_ctx *ctx, int32_t n_rcv, const double *rx, const void *x, void *out);
+
+/* ----------------------------------------------------------------------- measurement */
+/* Per-kernel device time recorded with CUDA events around launches while enabled.
+ * petgem_profile(ctx, 1) clears and enables, 0 disables.  petgem_kernel_stats returns, for
+ * kernel `name` (e.g. "spmv_c64"), the launch count, total milliseconds and the algorithmic
+ * bytes those launches moved (synchronises). */
+int petgem_profile(petgem_ctx *ctx, int enable);
+int petgem_kernel_stats(petgem_ctx *ctx, const char *name, int64_t *launches, double *total_ms,
+                        double *bytes);
+/* Number of kernel launches the context has issued since creation (host counter). */
+int64_t petgem_launch_count(const petgem_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PETGEM_H */

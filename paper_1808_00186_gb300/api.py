@@ -1,0 +1,292 @@
+"""Thin Python binding of the petgem C ABI (include/petgem.h).
+
+Argument marshalling only: every step of the computation runs in libpetgem.so's CUDA
+kernels.  Device buffers are torch CUDA tensors (torch is used for memory and streams);
+the functions take and return them with the layouts petgem.h documents.
+
+load() raises when the library is missing: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpetgem.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "petgem.h")
+
+OK, ERR_INVALID_ARG, ERR_BAD_MESH, ERR_DEGENERATE_TET, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_NOT_CONVERGED, \
+    ERR_BREAKDOWN, ERR_RECEIVER_OUTSIDE, ERR_UNSUPPORTED = range(10)
+PREC_C128, PREC_MIXED = 0, 1
+
+
+class petgem_dipole(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_double), ("y", ctypes.c_double), ("z", ctypes.c_double),
+                ("moment", ctypes.c_double), ("axis", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class petgem_solve_opts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int32), ("precision", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("batch", ctypes.c_int32), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("max_iters", ctypes.c_int64), ("inner_cycles", ctypes.c_int32), ("use_graphs", ctypes.c_int32)]
+
+
+class petgem_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("restarts", ctypes.c_int64), ("refinements", ctypes.c_int64),
+                ("true_rel_residual", ctypes.c_double), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_P, _I64, _I32, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+_SIGNATURES = {
+    "petgem_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P]),
+    "petgem_destroy": (ctypes.c_int, [_P]),
+    "petgem_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "petgem_last_error": (ctypes.c_char_p, [_P]),
+    "petgem_mesh_edges": (ctypes.c_int, [_P, _I64, _P, _I64, _P, ctypes.POINTER(_I64)]),
+    "petgem_get_topology": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "petgem_assemble": (ctypes.c_int, [_P, _D, _P, _D, _I32, ctypes.POINTER(petgem_dipole)]),
+    "petgem_get_system": (ctypes.c_int, [_P, ctypes.POINTER(_I64), _P, _P, _P, _P, _P]),
+    "petgem_get_elements": (ctypes.c_int, [_P, _P, _P, _P]),
+    "petgem_solve": (ctypes.c_int, [_P, ctypes.POINTER(petgem_solve_opts), _P, ctypes.POINTER(petgem_solve_info)]),
+    "petgem_spmv": (ctypes.c_int, [_P, _P, _P]),
+    "petgem_receivers": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
+    "petgem_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "petgem_kernel_stats": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.POINTER(_I64), ctypes.POINTER(_D),
+                                           ctypes.POINTER(_D)]),
+    "petgem_launch_count": (_I64, [_P]),
+}
+
+_lib = None
+
+
+def header_functions() -> list:
+    """Names of the functions include/petgem.h declares."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|int64_t|const char \*)\s*\*?\s*(petgem_\w+)\s*\(", text, re.M)))
+
+
+def load(path: str = LIB_PATH):
+    """Load libpetgem.so (built by paper_1808_00186_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libpetgem.so is not built (run __graft_entry__.build()); no fallback exists")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class PetgemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d): %s" % (load().petgem_status_string(status).decode(), status, msg))
+        self.status = status
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("expected a contiguous CUDA tensor")
+        return t.data_ptr()
+    raise TypeError("expected a torch CUDA tensor")
+
+
+# ------------------------------------------------------------------ same-name wrappers
+def petgem_create(device: int = 0, stream=None):
+    h = _P()
+    st = load().petgem_create(ctypes.byref(h), device, stream)
+    if st != OK:
+        raise PetgemError(st, "petgem_create failed")
+    return h
+
+
+def petgem_destroy(ctx) -> int:
+    return load().petgem_destroy(ctx)
+
+
+def _check(ctx, st, allowed=(OK,)):
+    if st not in allowed:
+        raise PetgemError(st, load().petgem_last_error(ctx).decode())
+    return st
+
+
+def petgem_mesh_edges(ctx, nodes, tets) -> int:
+    n = _I64(0)
+    _check(ctx, load().petgem_mesh_edges(ctx, nodes.shape[0], _ptr(nodes), tets.shape[0], _ptr(tets), ctypes.byref(n)))
+    return n.value
+
+
+def petgem_get_topology(ctx, edges=None, tet_edges=None, signs=None, boundary=None):
+    _check(ctx, load().petgem_get_topology(ctx, _ptr(edges), _ptr(tet_edges), _ptr(signs), _ptr(boundary)))
+
+
+def dipoles(sources) -> ctypes.Array:
+    arr = (petgem_dipole * len(sources))()
+    for i, s in enumerate(sources):
+        arr[i] = petgem_dipole(s.x, s.y, s.z, s.moment, s.axis, 0)
+    return arr
+
+
+def petgem_assemble(ctx, freq, sigma, sigma_p, sources):
+    arr = dipoles(sources)
+    _check(ctx, load().petgem_assemble(ctx, float(freq), _ptr(sigma), float(sigma_p), len(sources), arr))
+
+
+def petgem_get_system(ctx, row_ptr=None, col=None, val=None, b=None, diag=None) -> int:
+    nnz = _I64(0)
+    _check(ctx, load().petgem_get_system(ctx, ctypes.byref(nnz), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(b),
+                                         _ptr(diag)))
+    return nnz.value
+
+
+def petgem_get_elements(ctx, K21=None, M21=None, vol=None):
+    _check(ctx, load().petgem_get_elements(ctx, _ptr(K21), _ptr(M21), _ptr(vol)))
+
+
+def solve_opts(restart=50, precision=PREC_C128, tol=1e-8, inner_tol=1e-4, max_iters=200000, batch=1,
+               inner_cycles=1, use_graphs=0) -> petgem_solve_opts:
+    return petgem_solve_opts(restart, precision, 0, batch, tol, inner_tol, max_iters, inner_cycles, use_graphs)
+
+
+def petgem_solve(ctx, x, n_src, opts=None, allow_not_converged=False):
+    info = (petgem_solve_info * n_src)()
+    o = opts if opts is not None else solve_opts()
+    allowed = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
+    st = _check(ctx, load().petgem_solve(ctx, ctypes.byref(o), _ptr(x), info), allowed)
+    return st, [dict(iters=i.iters, restarts=i.restarts, refinements=i.refinements,
+                     true_rel_residual=i.true_rel_residual, status=i.status) for i in info]
+
+
+def petgem_spmv(ctx, x, y):
+    _check(ctx, load().petgem_spmv(ctx, _ptr(x), _ptr(y)))
+
+
+def petgem_receivers(ctx, rx, x, out, allow_outside=False) -> int:
+    allowed = (OK, ERR_RECEIVER_OUTSIDE) if allow_outside else (OK,)
+    return _check(ctx, load().petgem_receivers(ctx, rx.shape[0], _ptr(rx), _ptr(x), _ptr(out)), allowed)
+
+
+def petgem_profile(ctx, enable: bool):
+    _check(ctx, load().petgem_profile(ctx, 1 if enable else 0))
+
+
+def petgem_kernel_stats(ctx, name: str):
+    n, ms, by = _I64(0), _D(0.0), _D(0.0)
+    _check(ctx, load().petgem_kernel_stats(ctx, name.encode(), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
+    return n.value, ms.value, by.value
+
+
+def petgem_launch_count(ctx) -> int:
+    return load().petgem_launch_count(ctx)
+
+
+# ------------------------------------------------------------------ convenience
+@dataclass
+class Forward:
+    """Device-resident results of one forward run (see run_forward)."""
+    n_edges: int
+    x: object          # complex128 [n_src, E]
+    rcv: object        # complex128 [n_src, n_rcv, 3, 3]
+    info: list
+    status: int
+
+
+class Context:
+    """Owns a petgem context on the current torch CUDA device and stream."""
+
+    def __init__(self, device=None, stream=None):
+        import torch
+        self.torch = torch
+        dev = torch.cuda.current_device() if device is None else device
+        st = torch.cuda.current_stream(dev) if stream is None else stream
+        self.device = dev
+        self.stream = st
+        self.h = petgem_create(dev, ctypes.c_void_p(st.cuda_stream))
+
+    def close(self):
+        if getattr(self, "h", None):
+            petgem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def tensor(self, a, dtype=None):
+        t = self.torch.as_tensor(np.ascontiguousarray(a), device="cuda:%d" % self.device)
+        return t if dtype is None else t.to(dtype)
+
+    def mesh(self, nodes, tets) -> int:
+        self.nodes = nodes if hasattr(nodes, "data_ptr") else self.tensor(nodes, self.torch.float64)
+        self.tets = tets if hasattr(tets, "data_ptr") else self.tensor(tets, self.torch.int32)
+        self.n_edges = petgem_mesh_edges(self.h, self.nodes, self.tets)
+        return self.n_edges
+
+    def topology(self):
+        T, E = self.tets.shape[0], self.n_edges
+        tt = self.torch
+        out = (tt.empty((E, 2), dtype=tt.int32, device=self.nodes.device),
+               tt.empty((T, 6), dtype=tt.int32, device=self.nodes.device),
+               tt.empty((T, 6), dtype=tt.int8, device=self.nodes.device),
+               tt.empty(E, dtype=tt.uint8, device=self.nodes.device))
+        petgem_get_topology(self.h, *out)
+        return out
+
+    def assemble(self, freq, sigma, sigma_p, sources):
+        self.sigma = sigma if hasattr(sigma, "data_ptr") else self.tensor(sigma, self.torch.float64)
+        self.n_src = len(sources)
+        petgem_assemble(self.h, freq, self.sigma, sigma_p, sources)
+
+    def system(self):
+        tt = self.torch
+        E = self.n_edges
+        nnz = petgem_get_system(self.h)
+        d = self.nodes.device
+        rp = tt.empty(E + 1, dtype=tt.int64, device=d)
+        col = tt.empty(nnz, dtype=tt.int32, device=d)
+        val = tt.empty(nnz, dtype=tt.complex128, device=d)
+        b = tt.empty((self.n_src, E), dtype=tt.complex128, device=d)
+        dg = tt.empty(E, dtype=tt.complex128, device=d)
+        petgem_get_system(self.h, rp, col, val, b, dg)
+        return rp, col, val, b, dg
+
+    def elements(self):
+        tt = self.torch
+        T = self.tets.shape[0]
+        K = tt.empty((21, T), dtype=tt.float64, device=self.nodes.device)
+        M = tt.empty((21, T), dtype=tt.float64, device=self.nodes.device)
+        v = tt.empty(T, dtype=tt.float64, device=self.nodes.device)
+        petgem_get_elements(self.h, K, M, v)
+        return K, M, v
+
+    def solve(self, x=None, **opts):
+        tt = self.torch
+        if x is None:
+            x = tt.zeros((self.n_src, self.n_edges), dtype=tt.complex128, device=self.nodes.device)
+        allow = opts.pop("allow_not_converged", False)
+        st, info = petgem_solve(self.h, x, self.n_src, solve_opts(**opts), allow_not_converged=allow)
+        return x, info, st
+
+    def receivers(self, rx, x, allow_outside=False):
+        tt = self.torch
+        rxt = rx if hasattr(rx, "data_ptr") else self.tensor(rx, tt.float64)
+        out = tt.empty((self.n_src, rxt.shape[0], 3, 3), dtype=tt.complex128, device=self.nodes.device)
+        st = petgem_receivers(self.h, rxt, x, out, allow_outside=allow_outside)
+        return out, st

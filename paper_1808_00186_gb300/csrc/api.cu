@@ -1,0 +1,303 @@
+// C ABI of the petgem library (declared in include/petgem.h).  Argument checking, context
+// lifetime, error reporting and the per-kernel timers; the stages themselves live in
+// topology.cu, assembly.cu, krylov.cu and receivers.cu.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "ctx.cuh"
+
+namespace petgem {
+
+KernelTimer::KernelTimer(petgem_ctx* ctx, const char* nm, double b) : c(ctx), name(nm), bytes(b) {
+  if (!c->profiling) return;
+  for (cudaEvent_t* e : {&e0, &e1}) {
+    if (!c->event_pool.empty()) {
+      *e = c->event_pool.back();
+      c->event_pool.pop_back();
+    } else if (cudaEventCreate(e) != cudaSuccess) {
+      *e = nullptr;
+    }
+  }
+  if (e0 && e1) cudaEventRecord(e0, c->stream);
+}
+
+KernelTimer::~KernelTimer() {
+  if (!c->profiling || !e0 || !e1) return;
+  cudaEventRecord(e1, c->stream);
+  c->pending.push_back(PendingTiming{name, e0, e1, bytes});
+}
+
+Status resolve_timings(petgem_ctx* c) {
+  for (auto& p : c->pending) {
+    PG_CUDA(cudaEventSynchronize(p.stop));
+    float ms = 0.f;
+    PG_CUDA(cudaEventElapsedTime(&ms, p.start, p.stop));
+    KernelStat& k = c->stats[p.name];
+    k.launches++;
+    k.ms += ms;
+    k.bytes += p.bytes;
+    c->event_pool.push_back(p.start);
+    c->event_pool.push_back(p.stop);
+  }
+  c->pending.clear();
+  return Status{};
+}
+
+Status check_flags(petgem_ctx* c, const char* where) {
+  uint32_t f = 0;
+  PG_CUDA(cudaMemcpyAsync(&f, c->flags.ptr, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+  PG_CUDA(cudaStreamSynchronize(c->stream));
+  if (f & (kFlagBadNode | kFlagRepeatedNode | kFlagNonManifold))
+    return Status{PETGEM_ERR_BAD_MESH,
+                  std::string(where) + ": " +
+                      ((f & kFlagBadNode)        ? "node id out of range"
+                       : (f & kFlagRepeatedNode) ? "a tet repeats a node"
+                                                 : "a face is shared by more than two tets")};
+  if (f & kFlagDegenerate) return Status{PETGEM_ERR_DEGENERATE_TET, std::string(where) + ": a tet has zero volume"};
+  return Status{};
+}
+
+}  // namespace petgem
+
+using petgem::Status;
+
+namespace {
+
+int finish(petgem_ctx* c, const Status& s) {
+  if (c) c->last_error = s.ok() ? std::string() : s.msg;
+  return s.code;
+}
+
+Status set_device(petgem_ctx* c) {
+  PG_CUDA(cudaSetDevice(c->device));
+  return Status{};
+}
+
+}  // namespace
+
+extern "C" {
+
+int petgem_create(petgem_ctx** out, int device, void* cuda_stream) {
+  if (!out) return PETGEM_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return PETGEM_ERR_CUDA;
+  }
+  petgem_ctx* c = new (std::nothrow) petgem_ctx();
+  if (!c) return PETGEM_ERR_OUT_OF_MEMORY;
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  Status s = set_device(c);
+  if (s.ok()) s = c->flags.reserve(sizeof(uint32_t));
+  if (!s.ok()) {
+    delete c;
+    return s.code;
+  }
+  *out = c;
+  return PETGEM_OK;
+}
+
+int petgem_destroy(petgem_ctx* c) {
+  if (!c) return PETGEM_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  petgem::destroy_solver(c);
+  for (petgem::DevBuf* b : {&c->nodes, &c->tets, &c->edges, &c->tet_edges, &c->signs, &c->boundary, &c->occ, &c->eptr,
+                            &c->row_ptr, &c->col, &c->gptr, &c->pkey, &c->pij, &c->flags, &c->sigma, &c->K21, &c->M21,
+                            &c->vol, &c->val, &c->diag, &c->b})
+    b->release();
+  for (auto& p : c->pending) {
+    cudaEventDestroy(p.start);
+    cudaEventDestroy(p.stop);
+  }
+  for (auto e : c->event_pool) cudaEventDestroy(e);
+  delete c;
+  return PETGEM_OK;
+}
+
+const char* petgem_status_string(int s) {
+  switch (s) {
+    case PETGEM_OK: return "ok";
+    case PETGEM_ERR_INVALID_ARG: return "invalid argument";
+    case PETGEM_ERR_BAD_MESH: return "bad mesh";
+    case PETGEM_ERR_DEGENERATE_TET: return "degenerate tetrahedron";
+    case PETGEM_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case PETGEM_ERR_CUDA: return "CUDA error";
+    case PETGEM_ERR_NOT_CONVERGED: return "not converged";
+    case PETGEM_ERR_BREAKDOWN: return "Krylov breakdown";
+    case PETGEM_ERR_RECEIVER_OUTSIDE: return "receiver outside the mesh";
+    case PETGEM_ERR_UNSUPPORTED: return "unsupported size or option";
+    default: return "unknown status";
+  }
+}
+
+const char* petgem_last_error(const petgem_ctx* c) { return c ? c->last_error.c_str() : "null context"; }
+
+int petgem_mesh_edges(petgem_ctx* c, int64_t n_nodes, const double* nodes, int64_t n_tets, const int32_t* tets,
+                      int64_t* n_edges_out) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (!nodes || !tets || n_nodes < 4 || n_tets < 1)
+    return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_mesh_edges: need nodes, tets, n_nodes >= 4, n_tets >= 1"});
+  if (n_nodes >= (1ll << 31) || 6 * n_tets >= (1ll << 31))
+    return finish(c, Status{PETGEM_ERR_UNSUPPORTED, "petgem_mesh_edges: n_nodes < 2^31 and 6 n_tets < 2^31 required"});
+  Status s = set_device(c);
+  if (!s.ok()) return finish(c, s);
+  c->assembled = false;
+  c->n_nodes = n_nodes;
+  c->n_tets = n_tets;
+  s = c->nodes.reserve(3 * n_nodes * sizeof(double));
+  if (s.ok()) s = c->tets.reserve(4 * n_tets * sizeof(int32_t));
+  if (s.ok() && cudaMemcpyAsync(c->nodes.ptr, nodes, 3 * n_nodes * sizeof(double), cudaMemcpyDeviceToDevice,
+                                c->stream) != cudaSuccess)
+    s = Status{PETGEM_ERR_CUDA, "copy of nodes failed"};
+  if (s.ok() && cudaMemcpyAsync(c->tets.ptr, tets, 4 * n_tets * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                c->stream) != cudaSuccess)
+    s = Status{PETGEM_ERR_CUDA, "copy of tets failed"};
+  if (s.ok()) s = petgem::build_topology(c);
+  if (!s.ok()) {
+    c->n_edges = 0;
+    cudaGetLastError();
+    return finish(c, s);
+  }
+  if (n_edges_out) *n_edges_out = c->n_edges;
+  return finish(c, s);
+}
+
+int petgem_get_topology(petgem_ctx* c, int32_t* edges, int32_t* tet_edges, int8_t* signs, uint8_t* boundary) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (c->n_edges == 0) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_get_topology: no mesh"});
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaSuccess;
+  if (edges && e == cudaSuccess) e = cudaMemcpyAsync(edges, c->edges.ptr, 2 * c->n_edges * 4, cudaMemcpyDeviceToDevice, s);
+  if (tet_edges && e == cudaSuccess)
+    e = cudaMemcpyAsync(tet_edges, c->tet_edges.ptr, 6 * c->n_tets * 4, cudaMemcpyDeviceToDevice, s);
+  if (signs && e == cudaSuccess) e = cudaMemcpyAsync(signs, c->signs.ptr, 6 * c->n_tets, cudaMemcpyDeviceToDevice, s);
+  if (boundary && e == cudaSuccess)
+    e = cudaMemcpyAsync(boundary, c->boundary.ptr, c->n_edges, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return finish(c, Status{PETGEM_ERR_CUDA, cudaGetErrorString(e)});
+  return finish(c, Status{});
+}
+
+int petgem_assemble(petgem_ctx* c, double freq_hz, const double* sigma, double sigma_p, int32_t n_src,
+                    const petgem_dipole* src) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (c->n_edges == 0) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_assemble: call petgem_mesh_edges first"});
+  if (!sigma || !(freq_hz > 0.0) || !(sigma_p > 0.0) || n_src < 1 || !src)
+    return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_assemble: need sigma, freq > 0, sigma_p > 0, n_src >= 1"});
+  for (int32_t i = 0; i < n_src; ++i)
+    if (src[i].axis < 0 || src[i].axis > 2 || !std::isfinite(src[i].x) || !std::isfinite(src[i].y) ||
+        !std::isfinite(src[i].z) || !std::isfinite(src[i].moment))
+      return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_assemble: bad dipole " + std::to_string(i)});
+  Status s = set_device(c);
+  if (!s.ok()) return finish(c, s);
+  c->freq = freq_hz;
+  c->omega = 2.0 * 3.141592653589793238462643383279502884 * freq_hz;
+  c->sigma_p = sigma_p;
+  c->n_src = n_src;
+  c->src.assign(src, src + n_src);
+  c->assembled = false;
+  s = petgem::build_assembly(c, sigma);
+  if (!s.ok()) cudaGetLastError();
+  return finish(c, s);
+}
+
+int petgem_get_system(petgem_ctx* c, int64_t* nnz_out, int64_t* row_ptr, int32_t* col, void* val, void* b,
+                      void* diag) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (c->n_edges == 0) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_get_system: no mesh"});
+  if ((val || b || diag) && !c->assembled)
+    return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_get_system: not assembled"});
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaSuccess;
+  if (row_ptr) e = cudaMemcpyAsync(row_ptr, c->row_ptr.ptr, (c->n_edges + 1) * 8, cudaMemcpyDeviceToDevice, s);
+  if (col && e == cudaSuccess) e = cudaMemcpyAsync(col, c->col.ptr, c->nnz * 4, cudaMemcpyDeviceToDevice, s);
+  if (val && e == cudaSuccess) e = cudaMemcpyAsync(val, c->val.ptr, c->nnz * 16, cudaMemcpyDeviceToDevice, s);
+  if (b && e == cudaSuccess) e = cudaMemcpyAsync(b, c->b.ptr, (int64_t)c->n_src * c->n_edges * 16, cudaMemcpyDeviceToDevice, s);
+  if (diag && e == cudaSuccess) e = cudaMemcpyAsync(diag, c->diag.ptr, c->n_edges * 16, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return finish(c, Status{PETGEM_ERR_CUDA, cudaGetErrorString(e)});
+  if (nnz_out) *nnz_out = c->nnz;
+  return finish(c, Status{});
+}
+
+int petgem_get_elements(petgem_ctx* c, double* K21, double* M21, double* vol) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (!c->assembled) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_get_elements: not assembled"});
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaSuccess;
+  if (K21) e = cudaMemcpyAsync(K21, c->K21.ptr, 21 * c->n_tets * 8, cudaMemcpyDeviceToDevice, s);
+  if (M21 && e == cudaSuccess) e = cudaMemcpyAsync(M21, c->M21.ptr, 21 * c->n_tets * 8, cudaMemcpyDeviceToDevice, s);
+  if (vol && e == cudaSuccess) e = cudaMemcpyAsync(vol, c->vol.ptr, c->n_tets * 8, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return finish(c, Status{PETGEM_ERR_CUDA, cudaGetErrorString(e)});
+  return finish(c, Status{});
+}
+
+int petgem_solve(petgem_ctx* c, const petgem_solve_opts* opts, void* x, petgem_solve_info* info) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (!c->assembled) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve: call petgem_assemble first"});
+  if (!x || !info) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve: need x and info"});
+  petgem_solve_opts o{};
+  o.restart = 50;
+  o.precision = PETGEM_PREC_C128;
+  o.precond = PETGEM_PRECOND_JACOBI;
+  o.batch = 1;
+  o.tol = 1e-8;
+  o.inner_tol = 1e-4;
+  o.max_iters = 200000;
+  o.inner_cycles = 1;
+  o.use_graphs = 0;
+  if (opts) o = *opts;
+  if (!(o.tol > 0.0) || o.max_iters < 0 || (o.precision != PETGEM_PREC_C128 && o.precision != PETGEM_PREC_MIXED) ||
+      o.precond != PETGEM_PRECOND_JACOBI || !(o.inner_tol >= 0.0 && o.inner_tol < 1.0))
+    return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve: bad options"});
+  Status s = set_device(c);
+  if (s.ok()) s = petgem::run_solve(c, o, static_cast<double2*>(x), info);
+  if (s.code == PETGEM_ERR_CUDA || s.code == PETGEM_ERR_OUT_OF_MEMORY) cudaGetLastError();
+  return finish(c, s);
+}
+
+int petgem_spmv(petgem_ctx* c, const void* x, void* y) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (!c->assembled || !x || !y) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_spmv: not assembled or null"});
+  Status s = set_device(c);
+  if (s.ok()) s = petgem::run_spmv(c, static_cast<const double2*>(x), static_cast<double2*>(y));
+  return finish(c, s);
+}
+
+int petgem_receivers(petgem_ctx* c, int32_t n_rcv, const double* rx, const void* x, void* out) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (!c->assembled) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_receivers: call petgem_assemble first"});
+  if (n_rcv < 1 || !rx || !x || !out) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_receivers: bad arguments"});
+  Status s = set_device(c);
+  bool outside = false;
+  if (s.ok()) s = petgem::run_receivers(c, n_rcv, rx, static_cast<const double2*>(x), static_cast<double2*>(out), &outside);
+  if (s.ok() && outside) s = Status{PETGEM_ERR_RECEIVER_OUTSIDE, "petgem_receivers: a receiver lies in no tet"};
+  return finish(c, s);
+}
+
+int petgem_profile(petgem_ctx* c, int enable) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  Status s = petgem::resolve_timings(c);
+  c->stats.clear();
+  c->profiling = enable != 0;
+  return finish(c, s);
+}
+
+int petgem_kernel_stats(petgem_ctx* c, const char* name, int64_t* launches, double* total_ms, double* bytes) {
+  if (!c || !name) return PETGEM_ERR_INVALID_ARG;
+  Status s = petgem::resolve_timings(c);
+  if (!s.ok()) return finish(c, s);
+  auto it = c->stats.find(name);
+  petgem::KernelStat k = it == c->stats.end() ? petgem::KernelStat{} : it->second;
+  if (launches) *launches = k.launches;
+  if (total_ms) *total_ms = k.ms;
+  if (bytes) *bytes = k.bytes;
+  return finish(c, Status{});
+}
+
+int64_t petgem_launch_count(const petgem_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,239 @@
+// Element matrices, primary-field right-hand sides and the deterministic global assembly.
+//
+// Section 3 eq. 9 with the mass term scaled by mu0 as in eqs. 3 and 6:
+//   (K^e + i w mu0 sigma_e M^e) E_s^e = -i w mu0 (sigma_e - sigma_p) R^e,
+// K^e and M^e from Appendix B eqs. B.14-B.15 (signed by eq. B.16), R^e_k = int S_k N_k . E_p,
+// E_p the whole-space dipole field of Appendix A.  All in FP64.
+#include <math.h>
+
+#include "ctx.cuh"
+#include "physics.cuh"
+
+namespace petgem {
+namespace {
+
+using namespace phys;
+
+// Packed upper-triangle index of (i, j), i <= j, row-major: 0..20.
+__constant__ int kSym[36] = {0, 1, 2,  3,  4,  5,  1, 6,  7,  8,  9,  10, 2,  7,  11, 12, 13, 14,
+                             3, 8, 12, 15, 16, 17, 4, 9, 13, 16, 18, 19, 5, 10, 14, 17, 19, 20};
+
+// One thread per tet: the 21 distinct entries of the symmetric signed K^e and M^e (eqs. B.14-B.15).
+// curl N_i = 2 l_i grad l_a x grad l_b is constant, so K_ij = V (curl N_i S_i) . (curl N_j S_j);
+// M_ij = S_i S_j l_i l_j int (l_a gl_b - l_b gl_a) . (l_c gl_d - l_d gl_c) with
+// int l_p l_q = V (1 + delta_pq) / 20.
+__global__ void k_element(const double* __restrict__ nodes, const int32_t* __restrict__ tets,
+                          const int8_t* __restrict__ signs, int64_t n_tets, double* __restrict__ K21,
+                          double* __restrict__ M21, double* __restrict__ vol, uint32_t* __restrict__ flags) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n_tets) return;
+  TetGeom G;
+  if (!tet_geometry(nodes, tets, t, G)) {
+    atomicOr(flags, kFlagDegenerate);
+    for (int k = 0; k < 21; ++k) {
+      K21[k * n_tets + t] = 0.0;
+      M21[k * n_tets + t] = 0.0;
+    }
+    vol[t] = 0.0;
+    return;
+  }
+  double S[6], cu[6][3];
+  for (int i = 0; i < 6; ++i) {
+    S[i] = (double)signs[6 * t + i];
+    cross(G.g[kA[i]], G.g[kB[i]], cu[i]);
+    double f = 2.0 * G.len[i] * S[i];
+    for (int d = 0; d < 3; ++d) cu[i][d] *= f;
+  }
+  double gg[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b = a; b < 4; ++b) gg[a][b] = gg[b][a] = dot(G.g[a], G.g[b]);
+  const double v20 = G.vol / 20.0;
+  int k = 0;
+  for (int i = 0; i < 6; ++i) {
+    const int a = kA[i], b = kB[i];
+    for (int j = i; j < 6; ++j, ++k) {
+      const int c = kA[j], d = kB[j];
+      double Iac = v20 * (a == c ? 2.0 : 1.0), Iad = v20 * (a == d ? 2.0 : 1.0);
+      double Ibc = v20 * (b == c ? 2.0 : 1.0), Ibd = v20 * (b == d ? 2.0 : 1.0);
+      double m = Iac * gg[b][d] - Iad * gg[b][c] - Ibc * gg[a][d] + Ibd * gg[a][c];
+      K21[k * n_tets + t] = G.vol * dot(cu[i], cu[j]);
+      M21[k * n_tets + t] = S[i] * S[j] * G.len[i] * G.len[j] * m;
+    }
+  }
+  vol[t] = G.vol;
+}
+
+struct DipoleDev {
+  double x, y, z, moment;
+  int axis;
+};
+
+// One thread per (tet, source of this chunk): R^e_k = sum_q (V/4) S_k N_k(x_q) . E_p(x_q) on the
+// symmetric 4-point rule (barycentric alpha, beta, beta, beta and permutations), then scaled by
+// -i w mu0 (sigma_e - sigma_p).  Tets with sigma_e == sigma_p write zeros.  be layout:
+// [slot = 6 t + k][chunk source].
+__global__ void k_rhs(const double* __restrict__ nodes, const int32_t* __restrict__ tets,
+                      const int8_t* __restrict__ signs, const double* __restrict__ sigma, int64_t n_tets,
+                      double sigma_p, double omega, const DipoleDev* __restrict__ src, int n_chunk,
+                      double2* __restrict__ be) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n_tets * n_chunk) return;
+  int64_t t = idx / n_chunk;
+  int sc = (int)(idx - t * n_chunk);
+  double dsig = sigma[t] - sigma_p;
+  if (dsig == 0.0) {
+    for (int k = 0; k < 6; ++k) be[(6 * t + k) * n_chunk + sc] = make_double2(0.0, 0.0);
+    return;
+  }
+  TetGeom G;
+  if (!tet_geometry(nodes, tets, t, G)) {
+    for (int k = 0; k < 6; ++k) be[(6 * t + k) * n_chunk + sc] = make_double2(0.0, 0.0);
+    return;
+  }
+  const double alpha = 0.58541019662496845446, beta = 0.13819660112501051518;  // (5 +- ...) / 20
+  const double kappa = sqrt(omega * kMu0 * sigma_p * 0.5);
+  const DipoleDev D = src[sc];
+  double2 R[6];
+  for (int k = 0; k < 6; ++k) R[k] = make_double2(0.0, 0.0);
+  for (int q = 0; q < 4; ++q) {
+    double lam[4] = {beta, beta, beta, beta};
+    lam[q] = alpha;
+    double x[3];
+    for (int d = 0; d < 3; ++d) x[d] = lam[0] * G.p[0][d] + lam[1] * G.p[1][d] + lam[2] * G.p[2][d] + lam[3] * G.p[3][d];
+    double dv[3] = {x[0] - D.x, x[1] - D.y, x[2] - D.z};
+    double2 E[3];
+    dipole_field(dv, D.axis, D.moment, sigma_p, kappa, E);
+    for (int k = 0; k < 6; ++k) {
+      const int a = kA[k], b = kB[k];
+      double N[3];
+      for (int d = 0; d < 3; ++d) N[d] = G.len[k] * (lam[a] * G.g[b][d] - lam[b] * G.g[a][d]);
+      double2 ne = make_double2(N[0] * E[0].x + N[1] * E[1].x + N[2] * E[2].x,
+                                N[0] * E[0].y + N[1] * E[1].y + N[2] * E[2].y);
+      R[k] = cadd(R[k], ne);
+    }
+  }
+  // -i w mu0 dsig * (V/4) * S_k * R_k
+  const double f = omega * kMu0 * dsig * G.vol * 0.25;
+  for (int k = 0; k < 6; ++k) {
+    double s = (double)signs[6 * t + k] * f;
+    be[(6 * t + k) * n_chunk + sc] = make_double2(s * R[k].y, -s * R[k].x);
+  }
+}
+
+// b[s][e] = sum over the occurrences of edge e (sorted by slot = 6 t + k) of be; 0 on the boundary.
+__global__ void k_rhs_gather(const int64_t* __restrict__ eptr, const int32_t* __restrict__ occ,
+                             const uint8_t* __restrict__ boundary, int64_t n_edges, const double2* __restrict__ be,
+                             int n_chunk, int s0, double2* __restrict__ b) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n_edges * n_chunk) return;
+  int sc = (int)(idx / n_edges);
+  int64_t e = idx - (int64_t)sc * n_edges;
+  double2 acc = make_double2(0.0, 0.0);
+  if (!boundary[e]) {
+    for (int64_t p = eptr[e]; p < eptr[e + 1]; ++p) acc = cadd(acc, be[(int64_t)occ[p] * n_chunk + sc]);
+  }
+  b[(int64_t)(s0 + sc) * n_edges + e] = acc;
+}
+
+// One thread per row: A[q] = sum of the gathered element entries K + i w mu0 sigma_t M in
+// (tet, i, j) order; an empty gather range is a Dirichlet identity entry.  Also the diagonal.
+__global__ void k_matrix_gather(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                const int64_t* __restrict__ gptr, const uint64_t* __restrict__ pkey,
+                                const uint8_t* __restrict__ pij, const double* __restrict__ K21,
+                                const double* __restrict__ M21, const double* __restrict__ sigma,
+                                int64_t n_tets, int64_t n_edges, double wmu0, double2* __restrict__ val,
+                                double2* __restrict__ diag) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= n_edges) return;
+  double2 dg = make_double2(0.0, 0.0);
+  for (int64_t q = row_ptr[r]; q < row_ptr[r + 1]; ++q) {
+    int64_t g0 = gptr[q], g1 = gptr[q + 1];
+    double2 acc;
+    if (g0 == g1) {
+      acc = make_double2(1.0, 0.0);
+    } else {
+      acc = make_double2(0.0, 0.0);
+      for (int64_t p = g0; p < g1; ++p) {
+        int64_t t = (int64_t)(uint32_t)(pkey[p] & 0xffffffffu);
+        int k = kSym[pij[p]];
+        acc.x += K21[k * n_tets + t];
+        acc.y += wmu0 * sigma[t] * M21[k * n_tets + t];
+      }
+    }
+    val[q] = acc;
+    if (col[q] == r) dg = acc;
+  }
+  diag[r] = dg;
+}
+
+}  // namespace
+
+Status build_assembly(petgem_ctx* c, const double* sigma_dev) {
+  cudaStream_t s = c->stream;
+  const int64_t T = c->n_tets, E = c->n_edges, S = c->n_src;
+  uint32_t* flags = c->flags.as<uint32_t>();
+  PG_CUDA(cudaMemsetAsync(flags, 0, sizeof(uint32_t), s));
+  PG_TRY(c->sigma.reserve(T * sizeof(double)));
+  PG_CUDA(cudaMemcpyAsync(c->sigma.ptr, sigma_dev, T * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  PG_TRY(c->K21.reserve(21 * T * sizeof(double)));
+  PG_TRY(c->M21.reserve(21 * T * sizeof(double)));
+  PG_TRY(c->vol.reserve(T * sizeof(double)));
+  {
+    KernelTimer kt(c, "element", (double)T * (4 * 4 + 12 * 8 + 6 + 43 * 8));
+    k_element<<<blocks_for(T, 128), 128, 0, s>>>(c->nodes.as<double>(), c->tets.as<int32_t>(), c->signs.as<int8_t>(),
+                                                  T, c->K21.as<double>(), c->M21.as<double>(), c->vol.as<double>(),
+                                                  flags);
+    c->launches++;
+  }
+  PG_CUDA(cudaGetLastError());
+  PG_TRY(check_flags(c, "petgem_assemble"));
+
+  PG_TRY(c->val.reserve(c->nnz * sizeof(double2)));
+  PG_TRY(c->diag.reserve(E * sizeof(double2)));
+  {
+    KernelTimer kt(c, "matrix_gather", (double)c->nnz * (8 + 16 + 8) + (double)c->n_pairs * (9 + 24));
+    k_matrix_gather<<<blocks_for(E, 128), 128, 0, s>>>(
+        c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->gptr.as<int64_t>(), c->pkey.as<uint64_t>(),
+        c->pij.as<uint8_t>(), c->K21.as<double>(), c->M21.as<double>(), c->sigma.as<double>(), T, E, c->omega * kMu0,
+        c->val.as<double2>(), c->diag.as<double2>());
+    c->launches++;
+  }
+  PG_CUDA(cudaGetLastError());
+
+  // Right-hand sides, in chunks of sources so the per-slot buffer stays near 1 GB.
+  PG_TRY(c->b.reserve(S * E * sizeof(double2)));
+  int64_t per_src = 6 * T * (int64_t)sizeof(double2);
+  int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(S, (int64_t)(1ll << 30) / std::max<int64_t>(per_src, 1)));
+  double2* be = nullptr;
+  PG_CUDA(cudaMallocAsync((void**)&be, per_src * chunk, s));
+  DipoleDev* dsrc = nullptr;
+  PG_CUDA(cudaMallocAsync((void**)&dsrc, sizeof(DipoleDev) * S, s));
+  std::vector<DipoleDev> hsrc(S);
+  for (int64_t i = 0; i < S; ++i)
+    hsrc[i] = DipoleDev{c->src[i].x, c->src[i].y, c->src[i].z, c->src[i].moment, c->src[i].axis};
+  PG_CUDA(cudaMemcpyAsync(dsrc, hsrc.data(), sizeof(DipoleDev) * S, cudaMemcpyHostToDevice, s));
+  for (int s0 = 0; s0 < S; s0 += chunk) {
+    int n_chunk = (int)std::min<int64_t>(chunk, S - s0);
+    {
+      KernelTimer kt(c, "rhs", (double)T * n_chunk * 6 * 16);
+      k_rhs<<<blocks_for(T * n_chunk, 128), 128, 0, s>>>(c->nodes.as<double>(), c->tets.as<int32_t>(),
+                                                          c->signs.as<int8_t>(), c->sigma.as<double>(), T, c->sigma_p,
+                                                          c->omega, dsrc + s0, n_chunk, be);
+      c->launches++;
+    }
+    PG_CUDA(cudaGetLastError());
+    k_rhs_gather<<<blocks_for(E * n_chunk, 256), 256, 0, s>>>(c->eptr.as<int64_t>(), c->occ.as<int32_t>(),
+                                                              c->boundary.as<uint8_t>(), E, be, n_chunk, s0,
+                                                              c->b.as<double2>());
+    c->launches++;
+    PG_CUDA(cudaGetLastError());
+  }
+  PG_CUDA(cudaFreeAsync(be, s));
+  PG_CUDA(cudaFreeAsync(dsrc, s));
+  PG_TRY(check_flags(c, "petgem_assemble"));
+  c->assembled = true;
+  c->assembly_version++;
+  return Status{};
+}
+
+}  // namespace petgem

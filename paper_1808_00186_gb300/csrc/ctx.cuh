@@ -1,0 +1,111 @@
+// Context object behind the opaque petgem_ctx handle, and the device buffer helper.
+#pragma once
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace petgem {
+
+// Device buffer owned by the context (cudaMalloc / cudaFree; grows, never shrinks).
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  Status reserve(size_t n) {
+    if (n <= bytes && ptr) return Status{};
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    if (n == 0) return Status{};
+    cudaError_t e = cudaMalloc(&ptr, n);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return Status{PETGEM_ERR_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(n) + " bytes failed"};
+    }
+    bytes = n;
+    return Status{};
+  }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+  }
+  template <typename T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// Per-kernel timing while profiling is on: CUDA events around each launch on the ctx stream.
+struct KernelStat {
+  int64_t launches = 0;
+  double ms = 0.0;
+  double bytes = 0.0;
+};
+
+struct PendingTiming {
+  std::string name;
+  cudaEvent_t start, stop;
+  double bytes;
+};
+
+struct Solver;  // Krylov workspaces (krylov.cu)
+
+}  // namespace petgem
+
+struct petgem_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string last_error;
+  int64_t launches = 0;
+
+  // ---- mesh
+  int64_t n_nodes = 0, n_tets = 0, n_edges = 0, n_pairs = 0, nnz = 0;
+  petgem::DevBuf nodes, tets;              // copies of the caller's arrays
+  petgem::DevBuf edges, tet_edges, signs, boundary;
+  petgem::DevBuf occ, eptr;                // edge occurrences sorted by (edge, slot); offsets
+  petgem::DevBuf row_ptr, col, gptr, pkey, pij;  // CSR pattern and its gather map
+  petgem::DevBuf flags;                    // uint32 device error word
+
+  // ---- assembly
+  bool assembled = false;
+  int64_t assembly_version = 0;
+  double freq = 0.0, omega = 0.0, sigma_p = 1.0;
+  int32_t n_src = 0;
+  std::vector<petgem_dipole> src;
+  petgem::DevBuf sigma, K21, M21, vol;
+  petgem::DevBuf val, diag, b;             // A (complex128), diag(A), b [n_src][E]
+
+  // ---- solver state (krylov.cu)
+  petgem::Solver* solver = nullptr;
+
+  // ---- profiling
+  bool profiling = false;
+  std::vector<cudaEvent_t> event_pool;
+  std::vector<petgem::PendingTiming> pending;
+  std::map<std::string, petgem::KernelStat> stats;
+};
+
+namespace petgem {
+
+// Timing scope: while profiling, records an event pair around the launches inside it.
+struct KernelTimer {
+  petgem_ctx* c;
+  std::string name;
+  double bytes;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  KernelTimer(petgem_ctx* ctx, const char* nm, double b);
+  ~KernelTimer();
+};
+
+Status resolve_timings(petgem_ctx* c);
+Status check_flags(petgem_ctx* c, const char* where);
+
+// Stages implemented in the .cu files.
+Status build_topology(petgem_ctx* c);
+Status build_assembly(petgem_ctx* c, const double* sigma_dev);
+Status run_receivers(petgem_ctx* c, int32_t n_rcv, const double* rx, const double2* x, double2* out,
+                     bool* outside);
+Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info);
+Status run_spmv(petgem_ctx* c, const double2* x, double2* y);
+void destroy_solver(petgem_ctx* c);
+
+}  // namespace petgem

@@ -1,0 +1,48 @@
+"""The C ABI library builds for sm_103a, loads, and exports every function include/petgem.h
+declares (no compute calls: these run without a GPU)."""
+import ctypes
+import os
+
+import pytest
+
+from paper_1808_00186_gb300 import api
+from paper_1808_00186_gb300 import build as libbuild
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    return libbuild.build()
+
+
+def test_header_declares_the_boundary():
+    names = api.header_functions()
+    for required in ("petgem_create", "petgem_destroy", "petgem_mesh_edges", "petgem_assemble", "petgem_solve",
+                     "petgem_receivers", "petgem_status_string", "petgem_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    L = ctypes.CDLL(lib_path)
+    missing = [n for n in api.header_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(api.header_functions()) == set(api._SIGNATURES)
+
+
+def test_status_strings_without_gpu(lib_path):
+    L = api.load(lib_path)
+    assert L.petgem_status_string(0) == b"ok"
+    assert L.petgem_status_string(api.ERR_NOT_CONVERGED) == b"not converged"
+    assert L.petgem_last_error(None) == b"null context"
+    # A null context is rejected before any CUDA call.
+    assert L.petgem_solve(None, None, None, None) == api.ERR_INVALID_ARG
+    assert L.petgem_destroy(None) == api.OK
+
+
+def test_no_cpu_fallback_when_library_missing(tmp_path):
+    saved = api._lib
+    api._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            api.load(str(tmp_path / "missing.so"))
+    finally:
+        api._lib = saved
