@@ -37,6 +37,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=64, help="cells per axis of the marine model")
     p.add_argument("--no-plain", action="store_true", help="skip the complex128 comparison run")
+    p.add_argument("--profile-step", action="store_true",
+                   help="run one untimed step of the hot path and exit (the command profilers capture)")
+    p.add_argument("--precision", default="mixed", choices=["mixed", "c128"], help="solver of --profile-step")
     return p.parse_args()
 
 
@@ -173,13 +176,21 @@ def run_ours(args):
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item()), infos[-1], launches, cl
 
+    if args.profile_step:
+        info, _ = step(api.PREC_MIXED if args.precision == "mixed" else api.PREC_C128)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_step": True, "n": args.n, "edges": n_edges[0], "info": info,
+                          "launches": api.petgem_launch_count(ctx.h)}))
+        ctx.close()
+        return None
+
     hbm, peak_kind = peaks()
     clocks = ClockSampler(local)
     ms_mixed, info_mixed, launches, cl = timed(api.PREC_MIXED, args.steps, args.warmup, profile=True, clocks=clocks)
     # Dominant kernel over the timed region (CUDA events around each launch on the ctx stream).
     kstats = {}
-    for name in ("spmv_c64", "mdot_c64", "mupdate_c64", "residual_c128", "element", "matrix_gather", "rhs",
-                 "rcv_locate"):
+    for name in ("spmv_c64", "cgs_dot_c64", "cgs_upd_dot_c64", "cgs_upd_c64", "cycle_init_c64",
+                 "xupdate_c64", "residual_c128", "element", "matrix_gather", "rhs", "rcv_locate"):
         n, kms, by = api.petgem_kernel_stats(ctx.h, name)
         if n:
             kstats[name] = {"launches": n, "ms": kms, "bytes": by, "gbs": by / (kms * 1e-3) / 1e9}
@@ -246,6 +257,7 @@ def run_ours(args):
                        "edges": n_edges[0], "sources": S, "restart": 50, "tol": 1e-8, "precision": "mixed",
                        "l2": "working set > L2 (no flush needed)", "parallelism": "replicas" if world > 1 else "single"},
             "iters": info_mixed[0]["iters"], "cycles": info_mixed[0]["restarts"],
+            "reorth_steps": info_mixed[0]["reorth"],
             "true_rel_residual": info_mixed[0]["true_rel_residual"],
             "plain_c128": plain,
             "speedup_vs_plain": round(plain["ms_per_step"] / ms_mixed, 3) if plain else None,

@@ -41,7 +41,8 @@ enum {
   PETGEM_ERR_NOT_CONVERGED = 6,   /* iteration cap reached; info is still filled */
   PETGEM_ERR_BREAKDOWN = 7,       /* Krylov breakdown or a NaN/Inf in the iteration */
   PETGEM_ERR_RECEIVER_OUTSIDE = 8,/* a receiver lies in no tet; its outputs are NaN */
-  PETGEM_ERR_UNSUPPORTED = 9      /* a size or option this build does not handle */
+  PETGEM_ERR_UNSUPPORTED = 9,    /* a size or option this build does not handle */
+  PETGEM_ERR_TIMEOUT = 10         /* a bounded device-side wait gave up; the call was abandoned */
 };
 
 /* ----------------------------------------------------------------------- types */
@@ -86,8 +87,8 @@ typedef struct {
   int64_t restarts;    /* GMRES cycles */
   int64_t refinements; /* FP64 residual evaluations after the first */
   double true_rel_residual; /* ||b - A x|| / ||b|| in FP64 at exit */
-  int32_t status;      /* PETGEM_OK, PETGEM_ERR_NOT_CONVERGED or PETGEM_ERR_BREAKDOWN */
-  int32_t reserved;
+  int32_t status;      /* PETGEM_OK, PETGEM_ERR_NOT_CONVERGED, _BREAKDOWN or _TIMEOUT */
+  int32_t reorth;      /* Arnoldi steps that needed a second Gram-Schmidt pass */
 } petgem_solve_info;
 
 /* ----------------------------------------------------------------------- lifecycle */

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libpetgem.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "petgem.h")
 
 OK, ERR_INVALID_ARG, ERR_BAD_MESH, ERR_DEGENERATE_TET, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_NOT_CONVERGED, \
-    ERR_BREAKDOWN, ERR_RECEIVER_OUTSIDE, ERR_UNSUPPORTED = range(10)
+    ERR_BREAKDOWN, ERR_RECEIVER_OUTSIDE, ERR_UNSUPPORTED, ERR_TIMEOUT = range(11)
 PREC_C128, PREC_MIXED = 0, 1
 
 
@@ -37,7 +37,7 @@ class petgem_solve_opts(ctypes.Structure):
 
 class petgem_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("restarts", ctypes.c_int64), ("refinements", ctypes.c_int64),
-                ("true_rel_residual", ctypes.c_double), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("true_rel_residual", ctypes.c_double), ("status", ctypes.c_int32), ("reorth", ctypes.c_int32)]
 
 
 _P, _I64, _I32, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
@@ -163,7 +163,7 @@ def petgem_solve(ctx, x, n_src, opts=None, allow_not_converged=False):
     allowed = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
     st = _check(ctx, load().petgem_solve(ctx, ctypes.byref(o), _ptr(x), info), allowed)
     return st, [dict(iters=i.iters, restarts=i.restarts, refinements=i.refinements,
-                     true_rel_residual=i.true_rel_residual, status=i.status) for i in info]
+                     true_rel_residual=i.true_rel_residual, status=i.status, reorth=i.reorth) for i in info]
 
 
 def petgem_spmv(ctx, x, y):

@@ -1,6 +1,7 @@
 // C ABI of the petgem library (declared in include/petgem.h).  Argument checking, context
 // lifetime, error reporting and the per-kernel timers; the stages themselves live in
 // topology.cu, assembly.cu, krylov.cu and receivers.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -9,7 +10,8 @@
 
 namespace petgem {
 
-KernelTimer::KernelTimer(petgem_ctx* ctx, const char* nm, double b) : c(ctx), name(nm), bytes(b) {
+KernelTimer::KernelTimer(petgem_ctx* ctx, const char* nm, double b, int it, int ps)
+    : c(ctx), name(nm), bytes(b), iter(it), pass(ps) {
   if (!c->profiling) return;
   for (cudaEvent_t* e : {&e0, &e1}) {
     if (!c->event_pool.empty()) {
@@ -25,7 +27,22 @@ KernelTimer::KernelTimer(petgem_ctx* ctx, const char* nm, double b) : c(ctx), na
 KernelTimer::~KernelTimer() {
   if (!c->profiling || !e0 || !e1) return;
   cudaEventRecord(e1, c->stream);
-  c->pending.push_back(PendingTiming{name, e0, e1, bytes});
+  c->pending.push_back(PendingTiming{name, e0, e1, bytes, iter, pass});
+}
+
+void drop_idle_timings(petgem_ctx* c, size_t from, int k, const uint8_t* refined) {
+  std::vector<PendingTiming> keep(c->pending.begin(), c->pending.begin() + std::min(from, c->pending.size()));
+  for (size_t i = from; i < c->pending.size(); ++i) {
+    const PendingTiming& p = c->pending[i];
+    bool idle = p.iter >= 0 && (p.iter >= k || (p.pass == 1 && !refined[p.iter]));
+    if (idle) {
+      c->event_pool.push_back(p.start);
+      c->event_pool.push_back(p.stop);
+    } else {
+      keep.push_back(p);
+    }
+  }
+  c->pending.swap(keep);
 }
 
 Status resolve_timings(petgem_ctx* c) {
@@ -130,6 +147,7 @@ const char* petgem_status_string(int s) {
     case PETGEM_ERR_BREAKDOWN: return "Krylov breakdown";
     case PETGEM_ERR_RECEIVER_OUTSIDE: return "receiver outside the mesh";
     case PETGEM_ERR_UNSUPPORTED: return "unsupported size or option";
+    case PETGEM_ERR_TIMEOUT: return "device wait timed out";
     default: return "unknown status";
   }
 }

@@ -45,6 +45,8 @@ struct PendingTiming {
   std::string name;
   cudaEvent_t start, stop;
   double bytes;
+  int iter;   // Arnoldi step of the launch (-1: not part of a cycle)
+  int pass;   // 0: runs whenever the cycle is alive, 1: only when that step re-orthogonalised
 };
 
 struct Solver;  // Krylov workspaces (krylov.cu)
@@ -91,10 +93,15 @@ struct KernelTimer {
   petgem_ctx* c;
   std::string name;
   double bytes;
+  int iter, pass;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  KernelTimer(petgem_ctx* ctx, const char* nm, double b);
+  KernelTimer(petgem_ctx* ctx, const char* nm, double b, int it = -1, int ps = 0);
   ~KernelTimer();
 };
+
+// Drop the timings, recorded since pending index `from`, of cycle launches that returned at
+// once: steps >= k, and second-pass launches of steps that did not re-orthogonalise.
+void drop_idle_timings(petgem_ctx* c, size_t from, int k, const uint8_t* refined);
 
 Status resolve_timings(petgem_ctx* c);
 Status check_flags(petgem_ctx* c, const char* where);

@@ -25,16 +25,20 @@
 
 namespace petgem {
 
-constexpr int kMaxM = 64;  // largest restart length
+constexpr int kMaxM = 64;        // capacity of the Hessenberg arrays
+constexpr int kMaxRestart = 62;  // Gram-Schmidt slots j + 2 <= 64
 
 struct GState {
   int m, k, done, refine;
   unsigned counter;
-  int pad0;
+  int n_refine;    // steps of this cycle that took a second Gram-Schmidt pass
+  int timeout;     // a bounded wait in a kernel gave up
+  int pad1;
   double stop_abs;
   double nrm_w;    // ||w||^2 before orthogonalisation (pass 0)
   double rnorm2;   // ||r||^2 of the FP64 residual at the start of the cycle
   double beta0;
+  uint8_t refined[kMaxM];
   double2 H[(kMaxM + 1) * kMaxM];  // column j at H[j * (kMaxM + 1) + i], rotated in place
   double2 g[kMaxM + 1];
   double cs_c[kMaxM];
@@ -43,6 +47,7 @@ struct GState {
   double2 h2[kMaxM + 1];  // projections, pass 1
   double2 c[kMaxM + 1];   // update coefficients inv_beta[k] * h[k] of the running pass
   double inv_beta[kMaxM + 1];
+  float inv_beta32[kMaxM + 1];  // the same scales in FP32, for the complex64 kernels
   double2 y[kMaxM];       // cycle solution, already scaled by inv_beta
 };
 
@@ -54,6 +59,7 @@ struct Solver {
   DevBuf ahat128, ahat64, dinv;  // scaled matrix (c128, c64)
   DevBuf V, u, r, partials, state;
   int64_t n_blocks = 0;
+  int sms = 0;
 };
 
 namespace {
@@ -118,6 +124,8 @@ __device__ inline double warp_sum(double v) {
   return v;
 }
 
+
+
 // Block-level "last block done" handshake: returns true in exactly one block, after every block
 // has published its partials.
 __device__ inline bool last_block(unsigned* counter) {
@@ -157,6 +165,7 @@ __device__ void finish_column(GState* st, int j, const double2* h, double beta2)
   for (int i = 0; i <= j; ++i) Hc[i] = h[i];
   Hc[j + 1] = make_double2(beta, 0.0);
   st->inv_beta[j + 1] = beta > 0.0 ? 1.0 / beta : 0.0;
+  st->inv_beta32[j + 1] = (float)st->inv_beta[j + 1];
   for (int i = 0; i < j; ++i) {
     double2 a = Hc[i], b = Hc[i + 1];
     double c = st->cs_c[i];
@@ -192,6 +201,18 @@ __device__ void finish_column(GState* st, int j, const double2* h, double beta2)
 }
 
 // ------------------------------------------------------------------ kernels
+// Output scaling of the Arnoldi SpMV.  complex64: FP32 only (no FP64 instruction in the kernel:
+// on this GPU a single FP64 multiply per row costs as much as the row's memory traffic).
+template <typename T> __device__ inline T scale_out(typename Acc<T>::type acc, const GState* st, int j);
+template <> __device__ inline float2 scale_out<float2>(float2 acc, const GState* st, int j) {
+  const float s = st->inv_beta32[j];
+  return make_float2(acc.x * s, acc.y * s);
+}
+template <> __device__ inline double2 scale_out<double2>(double2 acc, const GState* st, int j) {
+  const double s = st->inv_beta[j];
+  return make_double2(acc.x * s, acc.y * s);
+}
+
 // y = (Ahat x) * scale, G lanes per row.  x = V_j, y = V_{j+1}, scale = 1/||V_j||.
 template <typename T, int G>
 __global__ void __launch_bounds__(256) k_spmv_arnoldi(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
@@ -211,10 +232,7 @@ __global__ void __launch_bounds__(256) k_spmv_arnoldi(const int64_t* __restrict_
     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
     acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
   }
-  if (row < n && lane == 0) {
-    double s = st->inv_beta[j];
-    y[row] = from_d2<T>(make_double2((double)acc.x * s, (double)acc.y * s));
-  }
+  if (row < n && lane == 0) y[row] = scale_out<T>(acc, st, j);
 }
 
 // r = b - Ahat u in FP64 (complex128 matrix and vectors).
@@ -276,8 +294,11 @@ __global__ void __launch_bounds__(kT) k_cycle_init(const double2* __restrict__ r
     st->g[0] = make_double2(b0, 0.0);
     for (int i = 1; i <= kMaxM; ++i) st->g[i] = make_double2(0.0, 0.0);
     st->inv_beta[0] = b0 > 0.0 ? 1.0 / b0 : 0.0;
+    st->inv_beta32[0] = (float)st->inv_beta[0];
     st->k = 0;
     st->refine = 0;
+    st->n_refine = 0;
+    for (int i = 0; i < kMaxM; ++i) st->refined[i] = 0;
     st->stop_abs = fmax(tol_abs, inner_rel * sqrt(r2));
     // Converged before the first step (FP64 residual already small), nothing to do, or not finite.
     if (!isfinite(r2) || !isfinite(b0))
@@ -288,195 +309,234 @@ __global__ void __launch_bounds__(kT) k_cycle_init(const double2* __restrict__ r
   }
 }
 
-// Projections of w = V_{j+1} on V_0..V_j (scaled to the normalised basis) and ||w||^2.
-template <typename T>
-__global__ void __launch_bounds__(kT) k_mdot(const T* __restrict__ V, int64_t ld, int64_t n, int j,
-                                             GState* __restrict__ st, double2* __restrict__ partials, int pass) {
-  if (st->done || (pass == 1 && !st->refine)) return;
-  __shared__ double2 red[kMaxM + 2][kT / 32];
-  __shared__ double2 fin[kMaxM + 2];
-  const int nk = j + 1, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const T* w = V + (int64_t)(j + 1) * ld;
-  int64_t base = blockIdx.x * (int64_t)kRows + threadIdx.x;
-  T wr[kR];
-#pragma unroll
-  for (int q = 0; q < kR; ++q) {
-    int64_t i = base + (int64_t)q * kT;
-    wr[q] = i < n ? w[i] : zero<T>();
-  }
-  {
-    typename Acc<T>::type a = zero<T>();
-#pragma unroll
-    for (int q = 0; q < kR; ++q) a.x += nrm2(wr[q]);
-    double2 s = warp_sum(make_double2((double)a.x, 0.0));
-    if (lane == 0) red[nk][wid] = s;
-  }
-  int k = 0;
-  for (; k + 1 < nk; k += 2) {  // two vectors per step: 16 independent loads in flight
-    const T* v0 = V + (int64_t)k * ld;
-    const T* v1 = v0 + ld;
-    T a0[kR], a1[kR];
-#pragma unroll
-    for (int q = 0; q < kR; ++q) {
-      int64_t i = base + (int64_t)q * kT;
-      a0[q] = i < n ? v0[i] : zero<T>();
-      a1[q] = i < n ? v1[i] : zero<T>();
-    }
-    typename Acc<T>::type s0 = zero<T>(), s1 = zero<T>();
-#pragma unroll
-    for (int q = 0; q < kR; ++q) {
-      fma_conj(s0, a0[q], wr[q]);
-      fma_conj(s1, a1[q], wr[q]);
-    }
-    double2 d0 = warp_sum(to_d2(s0)), d1 = warp_sum(to_d2(s1));
-    if (lane == 0) {
-      red[k][wid] = d0;
-      red[k + 1][wid] = d1;
-    }
-  }
-  for (; k < nk; ++k) {
-    const T* v0 = V + (int64_t)k * ld;
-    typename Acc<T>::type s0 = zero<T>();
-#pragma unroll
-    for (int q = 0; q < kR; ++q) {
-      int64_t i = base + (int64_t)q * kT;
-      if (i < n) fma_conj(s0, v0[i], wr[q]);
-    }
-    double2 d0 = warp_sum(to_d2(s0));
-    if (lane == 0) red[k][wid] = d0;
-  }
-  __syncthreads();
-  for (int kk = threadIdx.x; kk <= nk; kk += kT) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int ww = 0; ww < kT / 32; ++ww) s = cadd(s, red[kk][ww]);
-    partials[(int64_t)blockIdx.x * kPStride + kk] = s;
-  }
-  if (!last_block(&st->counter)) return;
-  reduce_partials(partials, gridDim.x, nk + 1, fin);
-  for (int kk = threadIdx.x; kk < nk; kk += kT) {
-    double ib = st->inv_beta[kk];
-    double2 h = cscale(fin[kk], ib);  // v_k^H w with v_k = V_k / ||V_k||
-    if (pass == 0)
-      st->h[kk] = h;
-    else
-      st->h2[kk] = h;
-    st->c[kk] = cscale(h, ib);        // w -= V_k * (h_k / ||V_k||)
-  }
-  if (threadIdx.x == 0) {
-    if (pass == 0) st->nrm_w = fin[nk].x;
-    st->counter = 0;
-  }
+// ------------------------------------------------------------------ TMA-staged Gram-Schmidt
+// One persistent kernel, three modes, for classical Gram-Schmidt with one re-orthogonalisation
+// (CGS2) of w = V_{j+1} against V_0..V_j:
+//   mode 0: h1 = V^H w, ||w||^2
+//   mode 1: w <- w - V c1 (c1 = h1 scaled), then h2 = V^H w on the updated w
+//   mode 2: w <- w - V c2, ||w||^2; the last block finishes the Hessenberg column
+// so V is read three times per Arnoldi step.  Each block walks row tiles; for a tile, one thread
+// issues a 1-D bulk copy (cp.async.bulk, completion on an mbarrier) of every vector's 2 KB slice
+// into shared memory, double-buffered so the next tile streams in while this one is used.  Rows
+// per tile: 256 (complex64) or 128 (complex128).  ld is a multiple of 256 elements, so every slice
+// is whole and 16-byte aligned; rows >= n are zero padding.
+constexpr int kSliceBytes = 2048;
+constexpr int kSliceStride = kSliceBytes + 16;  // 16-byte pad shifts banks between slices
+constexpr int kCgsThreads = 256;
+constexpr int kCgsDynSmem = 210 * 1024;  // dynamic shared memory available to the stages
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s: no copy takes that long
+
+__device__ inline unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ inline void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ inline void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ inline unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: false if the phase did not complete within kWaitLimitNs.
+__device__ inline bool mbar_wait(uint64_t* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  return true;
+}
+__device__ inline void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
 }
 
-// w = V_{j+1} <- w - sum_k V_k c_k, ||w||^2; the last block decides on a second pass or
-// finishes the Hessenberg column.
-template <typename T>
-__global__ void __launch_bounds__(kT) k_mupdate(T* __restrict__ V, int64_t ld, int64_t n, int j,
-                                                GState* __restrict__ st, double2* __restrict__ partials, int pass) {
-  if (st->done || (pass == 1 && !st->refine)) return;
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kCgsThreads, 1) k_cgs(T* __restrict__ V, int64_t ld, int64_t n, int j,
+                                                        GState* __restrict__ st, double2* __restrict__ partials,
+                                                        int n_tiles, int n_stages) {
+  constexpr int TR = kSliceBytes / (int)sizeof(T);  // rows per tile
+  if (st->done) return;
+  extern __shared__ __align__(128) unsigned char stage_mem[];
+  __shared__ uint64_t bar[2];
   __shared__ T cs[kMaxM + 1];
-  __shared__ double red[kT / 32];
-  __shared__ double2 fin[1];
-  __shared__ double2 hsum[kMaxM + 1];
-  const int nk = j + 1;
-  for (int k = threadIdx.x; k < nk; k += kT) cs[k] = from_d2<T>(st->c[k]);
+  __shared__ double2 red[kCgsThreads / 32][64];
+  __shared__ double2 fin[kMaxM + 2];
+  __shared__ bool aborted;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int nwarps = kCgsThreads / 32;
+  const int nv = j + 2;  // staged slices: V_0..V_j and w = V_{j+1}
+  const size_t stage_bytes = (size_t)nv * kSliceStride;
+  const int my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    aborted = false;
+  }
+  if (MODE != 0)
+    for (int k = tid; k <= j; k += kCgsThreads) cs[k] = from_d2<T>(st->c[k]);
   __syncthreads();
-  T* w = V + (int64_t)(j + 1) * ld;
-  int64_t base = blockIdx.x * (int64_t)kRows + threadIdx.x;
-  T wr[kR];
-#pragma unroll
-  for (int q = 0; q < kR; ++q) {
-    int64_t i = base + (int64_t)q * kT;
-    wr[q] = i < n ? w[i] : zero<T>();
+  auto issue = [&](int it, int sidx) {
+    const int64_t r0 = (int64_t)(blockIdx.x + (int64_t)it * gridDim.x) * TR;
+    unsigned char* base = stage_mem + sidx * stage_bytes;
+    mbar_expect_tx(&bar[sidx], (unsigned)(nv * kSliceBytes));
+    for (int k = 0; k < nv; ++k) bulk_g2s(base + (size_t)k * kSliceStride, V + (int64_t)k * ld + r0, kSliceBytes, &bar[sidx]);
+  };
+  if (tid == 0) {
+    if (my_tiles > 0) issue(0, 0);
+    if (n_stages == 2 && my_tiles > 1) issue(1, 1);
   }
-  int k = 0;
-  for (; k + 1 < nk; k += 2) {
-    const T* v0 = V + (int64_t)k * ld;
-    const T* v1 = v0 + ld;
-    T a0[kR], a1[kR];
-#pragma unroll
-    for (int q = 0; q < kR; ++q) {
-      int64_t i = base + (int64_t)q * kT;
-      a0[q] = i < n ? v0[i] : zero<T>();
-      a1[q] = i < n ? v1[i] : zero<T>();
+  typename Acc<T>::type a_hi = zero<T>();
+  double2 acc0 = make_double2(0.0, 0.0), acc1 = make_double2(0.0, 0.0);
+  double nrm = 0.0;
+  const int k0 = lane, k1 = lane + 32;
+  const bool has0 = k0 <= j + 1, has1 = k1 <= j + 1;
+  for (int it = 0; it < my_tiles; ++it) {
+    const int sidx = n_stages == 2 ? (it & 1) : 0;
+    const unsigned parity = n_stages == 2 ? ((it >> 1) & 1) : (it & 1);
+    if (!mbar_wait(&bar[sidx], parity)) aborted = true;
+    __syncthreads();
+    if (aborted) break;
+    const unsigned char* base = stage_mem + sidx * stage_bytes;
+    T* ws = (T*)(stage_mem + sidx * stage_bytes + (size_t)(j + 1) * kSliceStride);
+    const int64_t r0 = (int64_t)(blockIdx.x + (int64_t)it * gridDim.x) * TR;
+    if (MODE != 0) {  // row per thread: w -= sum_k V_k c_k
+      if (tid < TR) {
+        T w = ws[tid];
+        for (int k = 0; k <= j; ++k) sub_mul(w, ((const T*)(base + (size_t)k * kSliceStride))[tid], cs[k]);
+        const int64_t r = r0 + tid;
+        if (r < n) {
+          V[(int64_t)(j + 1) * ld + r] = w;
+          if (MODE == 2) a_hi.x += nrm2(w);
+        }
+        ws[tid] = w;
+      }
+      __syncthreads();
     }
-    const T c0 = cs[k], c1 = cs[k + 1];
-#pragma unroll
-    for (int q = 0; q < kR; ++q) {
-      sub_mul(wr[q], a0[q], c0);
-      sub_mul(wr[q], a1[q], c1);
+    if (MODE != 2) {  // lane owns slots k0 and k1 (slot j + 1 is ||w||^2); rows staggered by lane
+      typename Acc<T>::type s0 = zero<T>(), s1 = zero<T>();
+      for (int r = wid; r < TR; r += nwarps) {
+        const int row = (r + lane) & (TR - 1);
+        const T wv = ws[row];
+        if (has0) fma_conj(s0, ((const T*)(base + (size_t)k0 * kSliceStride))[row], wv);
+        if (has1) fma_conj(s1, ((const T*)(base + (size_t)k1 * kSliceStride))[row], wv);
+      }
+      acc0 = cadd(acc0, to_d2(s0));
+      acc1 = cadd(acc1, to_d2(s1));
+    } else if ((it & 7) == 7) {  // flush the FP32 norm every 8 tiles (2048 rows per thread at most)
+      nrm += (double)a_hi.x;
+      a_hi = zero<T>();
+    }
+    __syncthreads();  // every thread is done with this stage
+    if (tid == 0 && it + n_stages < my_tiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(it + n_stages, sidx);
     }
   }
-  for (; k < nk; ++k) {
-    const T* v0 = V + (int64_t)k * ld;
-    const T c0 = cs[k];
-#pragma unroll
-    for (int q = 0; q < kR; ++q) {
-      int64_t i = base + (int64_t)q * kT;
-      if (i < n) sub_mul(wr[q], v0[i], c0);
-    }
-  }
-  double nn = 0.0;
-#pragma unroll
-  for (int q = 0; q < kR; ++q) {
-    int64_t i = base + (int64_t)q * kT;
-    if (i < n) {
-      w[i] = wr[q];
-      nn += (double)nrm2(wr[q]);
-    }
-  }
-  nn = warp_sum(nn);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nn;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int ww = 0; ww < kT / 32; ++ww) s += red[ww];
-    partials[(int64_t)blockIdx.x * kPStride] = make_double2(s, 0.0);
-  }
-  if (!last_block(&st->counter)) return;
-  reduce_partials(partials, gridDim.x, 1, fin);
-  const double n2 = fin[0].x;
-  if (pass == 0 && n2 < 0.5 * st->nrm_w) {  // lost more than 1 - 1/sqrt(2) of the norm: one more pass
-    if (threadIdx.x == 0) {
-      st->refine = 1;
-      st->counter = 0;
+  if (aborted) {
+    // Give the copies still in flight a bounded chance to land before the block's shared memory
+    // is released, report, and leave the rest of the cycle to skip.
+    if (tid == 0) {
+      for (int sidx = 0; sidx < n_stages; ++sidx) mbar_wait(&bar[sidx], 0), mbar_wait(&bar[sidx], 1);
+      st->timeout = 1;
+      atomicExch(&st->done, 2);
     }
     return;
   }
-  for (int kk = threadIdx.x; kk < nk; kk += kT) hsum[kk] = pass == 0 ? st->h[kk] : cadd(st->h[kk], st->h2[kk]);
+  nrm += (double)a_hi.x;
+  if (MODE != 2) {
+    red[wid][k0] = acc0;
+    red[wid][k1] = acc1;
+  } else {
+    double t = warp_sum(nrm);
+    if (lane == 0) red[wid][0] = make_double2(t, 0.0);
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    finish_column(st, j, hsum, n2);
-    st->refine = 0;
-    st->counter = 0;
+  const int nslots = MODE == 2 ? 1 : j + 2;
+  for (int k = tid; k < nslots; k += kCgsThreads) {
+    double2 sum = make_double2(0.0, 0.0);
+    for (int w2 = 0; w2 < nwarps; ++w2) sum = cadd(sum, red[w2][k]);
+    partials[(int64_t)blockIdx.x * kPStride + k] = sum;
+  }
+  if (!last_block(&st->counter)) return;
+  reduce_partials(partials, gridDim.x, nslots, fin);
+  if (MODE == 0) {
+    for (int k = tid; k <= j; k += kCgsThreads) {
+      const double ib = st->inv_beta[k];
+      const double2 h = cscale(fin[k], ib);
+      st->h[k] = h;
+      st->c[k] = cscale(h, ib);
+    }
+    if (tid == 0) {
+      st->nrm_w = fin[j + 1].x;
+      st->counter = 0;
+    }
+  } else if (MODE == 1) {
+    for (int k = tid; k <= j; k += kCgsThreads) {
+      const double ib = st->inv_beta[k];
+      const double2 h = cscale(fin[k], ib);
+      st->h2[k] = h;
+      st->c[k] = cscale(h, ib);
+    }
+    if (tid == 0) st->counter = 0;
+  } else {
+    __shared__ double2 hsum[kMaxM + 1];
+    for (int k = tid; k <= j; k += kCgsThreads) hsum[k] = cadd(st->h[k], st->h2[k]);
+    __syncthreads();
+    if (tid == 0) {
+      finish_column(st, j, hsum, fin[0].x);
+      st->refined[j] = 1;
+      st->n_refine += 1;
+      st->counter = 0;
+    }
   }
 }
 
-// y = H(0:k, 0:k)^{-1} g(0:k), scaled by 1/||V_i|| for the unnormalised basis.
+// y = H(0:k, 0:k)^{-1} g(0:k), scaled by 1/||V_i|| for the unnormalised basis.  One warp:
+// column-oriented back substitution (lane l keeps the running right-hand side of rows l, l+32).
 __global__ void k_backsolve(GState* st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int lane = threadIdx.x;
   const int kk = st->k;
+  double2 rhs0 = lane < kk ? st->g[lane] : make_double2(0.0, 0.0);
+  double2 rhs1 = lane + 32 < kk ? st->g[lane + 32] : make_double2(0.0, 0.0);
   for (int i = kk - 1; i >= 0; --i) {
-    double2 acc = st->g[i];
-    for (int l = i + 1; l < kk; ++l) acc = csub(acc, cmul(st->H[l * (kMaxM + 1) + i], st->y[l]));
-    st->y[i] = cdiv(acc, st->H[i * (kMaxM + 1) + i]);
+    double2 ri = i < 32 ? rhs0 : rhs1;
+    double2 yi = make_double2(__shfl_sync(0xffffffffu, ri.x, i & 31), __shfl_sync(0xffffffffu, ri.y, i & 31));
+    yi = cdiv(yi, st->H[i * (kMaxM + 1) + i]);
+    if (lane == 0) st->y[i] = cscale(yi, st->inv_beta[i]);
+    const double2* Hc = &st->H[i * (kMaxM + 1)];
+    if (lane < i) rhs0 = csub(rhs0, cmul(Hc[lane], yi));
+    if (lane + 32 < i) rhs1 = csub(rhs1, cmul(Hc[lane + 32], yi));
   }
-  for (int i = 0; i < kk; ++i) st->y[i] = cscale(st->y[i], st->inv_beta[i]);
 }
 
-// u += sum_k V_k y_k in FP64.
+// u += sum_k V_k y_k.  complex128: in FP64.  complex64: the correction sum_k V_k y_k is formed in
+// FP32 (it is the inner solve's correction, accurate to complex64 anyway) and added to u in FP64.
 template <typename T>
 __global__ void __launch_bounds__(kT) k_xupdate(const T* __restrict__ V, int64_t ld, int64_t n,
                                                 double2* __restrict__ u, const GState* __restrict__ st) {
-  __shared__ double2 ys[kMaxM];
+  __shared__ T ys[kMaxM];
   const int kk = st->done == 2 ? 0 : st->k;  // a failed cycle leaves u untouched
-  for (int k = threadIdx.x; k < kk; k += kT) ys[k] = st->y[k];
+  for (int k = threadIdx.x; k < kk; k += kT) ys[k] = from_d2<T>(st->y[k]);
   __syncthreads();
   int64_t i = blockIdx.x * (int64_t)kT + threadIdx.x;
   if (i >= n || kk == 0) return;
-  double2 acc = u[i];
-  for (int k = 0; k < kk; ++k) fma_c(acc, to_d2(V[(int64_t)k * ld + i]), ys[k]);
-  u[i] = acc;
+  typename Acc<T>::type acc = zero<T>();
+  for (int k = 0; k < kk; ++k) fma_c(acc, V[(int64_t)k * ld + i], ys[k]);
+  u[i] = cadd(u[i], to_d2(acc));
 }
 
 __global__ void k_scale_in(const double2* __restrict__ x, const double2* __restrict__ d, double2* __restrict__ u,
@@ -551,11 +611,12 @@ __global__ void __launch_bounds__(kT) k_norm2(const double2* __restrict__ b, int
 constexpr int kGroup = 8;  // lanes per row in the CSR kernels (rows hold at most ~19 entries)
 
 // ------------------------------------------------------------------ host side
-struct HostState {
+struct HostState {  // leading fields of GState
   int m, k, done, refine;
   unsigned counter;
-  int pad0;
+  int n_refine, timeout, pad1;
   double stop_abs, nrm_w, rnorm2, beta0;
+  uint8_t refined[kMaxM];
 };
 
 Status read_state(petgem_ctx* c, HostState* hs) {
@@ -581,10 +642,19 @@ Status prepare(petgem_ctx* c, int m) {
     S->version = c->assembly_version;
   }
   S->n = n;
-  S->ld = (n + 63) / 64 * 64;
+  S->ld = (n + 255) / 256 * 256;  // whole 2 KB slices for the staged Gram-Schmidt kernel
   S->m = m;
   S->n_blocks = (n + kRows - 1) / kRows;
-  PG_TRY(S->V.reserve((size_t)(m + 1) * S->ld * sizeof(double2)));
+  const size_t vbytes_all = (size_t)(m + 1) * S->ld * sizeof(double2);
+  const bool fresh = S->V.bytes < vbytes_all;
+  PG_TRY(S->V.reserve(vbytes_all));
+  if (fresh) PG_CUDA(cudaMemsetAsync(S->V.ptr, 0, S->V.bytes, s));  // padding rows stay zero
+  if (S->sms == 0) {
+    PG_CUDA(cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, c->device));
+    for (auto f : {(const void*)k_cgs<float2, 0>, (const void*)k_cgs<float2, 1>, (const void*)k_cgs<float2, 2>,
+                   (const void*)k_cgs<double2, 0>, (const void*)k_cgs<double2, 1>, (const void*)k_cgs<double2, 2>})
+      PG_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kCgsDynSmem));
+  }
   PG_TRY(S->u.reserve(n * sizeof(double2)));
   PG_TRY(S->r.reserve(n * sizeof(double2)));
   PG_TRY(S->partials.reserve((size_t)std::max<int64_t>(S->n_blocks, 1) * kPStride * sizeof(double2)));
@@ -603,39 +673,53 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, double tol_abs, double inn
   double2* part = S->partials.as<double2>();
   const unsigned nb = (unsigned)S->n_blocks;
   const double vbytes = (double)sizeof(T) * n;
-  k_cycle_init<T><<<nb, kT, 0, s>>>(S->r.as<double2>(), V, n, st, part, tol_abs, inner_rel);
-  c->launches++;
-  const char* spmv_name = sizeof(T) == 16 ? "spmv_c128" : "spmv_c64";
-  const char* dot_name = sizeof(T) == 16 ? "mdot_c128" : "mdot_c64";
-  const char* upd_name = sizeof(T) == 16 ? "mupdate_c128" : "mupdate_c64";
+  const bool c128 = sizeof(T) == 16;
+  const size_t pending0 = c->pending.size();
+  {
+    KernelTimer kt(c, c128 ? "cycle_init_c128" : "cycle_init_c64", 16.0 * n + vbytes);
+    k_cycle_init<T><<<nb, kT, 0, s>>>(S->r.as<double2>(), V, n, st, part, tol_abs, inner_rel);
+    c->launches++;
+  }
   const double spmv_bytes = (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 2.0 * vbytes;
   const unsigned spmv_blocks = blocks_for(n * kGroup, 256);
   for (int j = 0; j < m; ++j) {
     T* vj = V + (int64_t)j * ld;
     T* vn = vj + ld;
     {
-      KernelTimer kt(c, spmv_name, spmv_bytes);
+      KernelTimer kt(c, c128 ? "spmv_c128" : "spmv_c64", spmv_bytes, j, 0);
       k_spmv_arnoldi<T, kGroup><<<spmv_blocks, 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), ahat, vj,
                                                             vn, n, st, j);
     }
+    const int nv = j + 2;
+    const int n_stages = 2 * nv * kSliceStride <= kCgsDynSmem ? 2 : 1;
+    const size_t dyn = (size_t)n_stages * nv * kSliceStride;
+    const int tiles = (int)(ld * sizeof(T) / kSliceBytes);
+    const unsigned grid = (unsigned)std::min(tiles, S->sms);
     {
-      KernelTimer kt(c, dot_name, (j + 2) * vbytes);
-      k_mdot<T><<<nb, kT, 0, s>>>(V, ld, n, j, st, part, 0);
+      KernelTimer kt(c, c128 ? "cgs_dot_c128" : "cgs_dot_c64", (j + 2) * vbytes, j, 0);
+      k_cgs<T, 0><<<grid, kCgsThreads, dyn, s>>>(V, ld, n, j, st, part, tiles, n_stages);
     }
     {
-      KernelTimer kt(c, upd_name, (j + 3) * vbytes);
-      k_mupdate<T><<<nb, kT, 0, s>>>(V, ld, n, j, st, part, 0);
+      KernelTimer kt(c, c128 ? "cgs_upd_dot_c128" : "cgs_upd_dot_c64", (j + 3) * vbytes, j, 0);
+      k_cgs<T, 1><<<grid, kCgsThreads, dyn, s>>>(V, ld, n, j, st, part, tiles, n_stages);
     }
-    k_mdot<T><<<nb, kT, 0, s>>>(V, ld, n, j, st, part, 1);
-    k_mupdate<T><<<nb, kT, 0, s>>>(V, ld, n, j, st, part, 1);
-    c->launches += 5;
+    {
+      KernelTimer kt(c, c128 ? "cgs_upd_c128" : "cgs_upd_c64", (j + 3) * vbytes, j, 0);
+      k_cgs<T, 2><<<grid, kCgsThreads, dyn, s>>>(V, ld, n, j, st, part, tiles, n_stages);
+    }
+    c->launches += 4;
   }
   PG_CUDA(cudaGetLastError());
   k_backsolve<<<1, 32, 0, s>>>(st);
-  k_xupdate<T><<<blocks_for(n, kT), kT, 0, s>>>(V, ld, n, S->u.as<double2>(), st);
+  {
+    KernelTimer kt(c, c128 ? "xupdate_c128" : "xupdate_c64", 32.0 * n + (double)m * vbytes);
+    k_xupdate<T><<<blocks_for(n, kT), kT, 0, s>>>(V, ld, n, S->u.as<double2>(), st);
+  }
   c->launches += 2;
   PG_CUDA(cudaGetLastError());
-  return read_state(c, hs);
+  PG_TRY(read_state(c, hs));
+  if (c->profiling) drop_idle_timings(c, pending0, hs->done == 2 ? 0 : hs->k, hs->refined);
+  return Status{};
 }
 
 }  // namespace
@@ -665,7 +749,7 @@ Status run_spmv(petgem_ctx* c, const double2* x, double2* y) {
 
 Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info) {
   const int m = o.restart;
-  if (m < 1 || m > kMaxM) return Status{PETGEM_ERR_UNSUPPORTED, "restart must be in [1, 64]"};
+  if (m < 1 || m > kMaxRestart) return Status{PETGEM_ERR_UNSUPPORTED, "restart must be in [1, 62]"};
   PG_TRY(prepare(c, m));
   Solver* S = c->solver;
   cudaStream_t s = c->stream;
@@ -692,7 +776,7 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
     }
     k_scale_in<<<blocks_for(n, 256), 256, 0, s>>>(xs, c->diag.as<double2>(), S->u.as<double2>(), n);
     c->launches++;
-    int64_t iters = 0, cycles = 0;
+    int64_t iters = 0, cycles = 0, reorth = 0;
     int status = PETGEM_OK;
     double relres = 0.0;
     while (true) {
@@ -722,8 +806,9 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
       }
       iters += hs.k;
       cycles += 1;
+      reorth += hs.n_refine;
       if (hs.done == 2) {  // u was left as it was before this cycle
-        status = PETGEM_ERR_BREAKDOWN;
+        status = hs.timeout ? PETGEM_ERR_TIMEOUT : PETGEM_ERR_BREAKDOWN;
         break;
       }
     }
@@ -735,6 +820,7 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
     inf.refinements = cycles;
     inf.true_rel_residual = relres;
     inf.status = status;
+    inf.reorth = (int32_t)std::min<int64_t>(reorth, INT32_MAX);
     if (status != PETGEM_OK && worst.ok()) worst = Status{status, "source " + std::to_string(src) + " did not converge"};
   }
   PG_CUDA(cudaStreamSynchronize(s));
