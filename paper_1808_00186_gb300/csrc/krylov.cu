@@ -59,6 +59,7 @@ struct Solver {
   DevBuf ahat128, ahat64, dinv;  // scaled matrix (c128, c64)
   DevBuf V, u, r, partials, state;
   int64_t n_blocks = 0;
+  int64_t ld_used = 0;
   int sms = 0;
 };
 
@@ -159,7 +160,7 @@ __device__ void reduce_partials(const double2* partials, int nblocks, int nk, do
 
 // New Hessenberg column j from the projections h (summed over passes) and beta = ||V_{j+1}||:
 // earlier rotations, a new complex Givens rotation, the residual estimate and the stopping test.
-__device__ void finish_column(GState* st, int j, const double2* h, double beta2) {
+__device__ __noinline__ void finish_column(GState* st, int j, const double2* h, double beta2) {
   double beta = sqrt(beta2);
   double2* Hc = &st->H[j * (kMaxM + 1)];
   for (int i = 0; i <= j; ++i) Hc[i] = h[i];
@@ -223,11 +224,20 @@ __global__ void __launch_bounds__(256) k_spmv_arnoldi(const int64_t* __restrict_
   int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t row = gid / G;
   int lane = (int)(gid % G);
-  typename Acc<T>::type acc = zero<T>();
+  typename Acc<T>::type acc = zero<T>(), acc2 = zero<T>();
   if (row < n) {
-    int64_t p1 = rp[row + 1];
-    for (int64_t p = rp[row] + lane; p < p1; p += G) fma_c(acc, val[p], x[col[p]]);
+    const int64_t p1 = rp[row + 1];
+    int64_t p = rp[row] + lane;
+    for (; p + G < p1; p += 2 * G) {  // two entries per lane in flight
+      const int32_t c0 = __ldg(&col[p]), c1 = __ldg(&col[p + G]);
+      const T a0 = __ldg(&val[p]), a1 = __ldg(&val[p + G]);
+      fma_c(acc, a0, __ldg(&x[c0]));
+      fma_c(acc2, a1, __ldg(&x[c1]));
+    }
+    if (p < p1) fma_c(acc, __ldg(&val[p]), __ldg(&x[__ldg(&col[p])]));
   }
+  acc.x += acc2.x;
+  acc.y += acc2.y;
   for (int o = G / 2; o > 0; o >>= 1) {
     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
     acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
@@ -318,12 +328,17 @@ __global__ void __launch_bounds__(kT) k_cycle_init(const double2* __restrict__ r
 // so V is read three times per Arnoldi step.  Each block walks row tiles; for a tile, one thread
 // issues a 1-D bulk copy (cp.async.bulk, completion on an mbarrier) of every vector's 2 KB slice
 // into shared memory, double-buffered so the next tile streams in while this one is used.  Rows
-// per tile: 256 (complex64) or 128 (complex128).  ld is a multiple of 256 elements, so every slice
-// is whole and 16-byte aligned; rows >= n are zero padding.
-constexpr int kSliceBytes = 2048;
+// per tile: 128 (complex64) or 64 (complex128).  ld is a multiple of 256 elements, so every slice
+// is whole and 16-byte aligned; rows >= n are zero padding.  Two blocks per SM hide each other's
+// waits; each block double-buffers its own tiles.
+constexpr int kSliceBytes = 1024;
 constexpr int kSliceStride = kSliceBytes + 16;  // 16-byte pad shifts banks between slices
 constexpr int kCgsThreads = 256;
-constexpr int kCgsDynSmem = 210 * 1024;  // dynamic shared memory available to the stages
+constexpr int kCgsBlocksPerSM = 2;
+// Dynamic shared memory per block: two blocks per SM must fit in the SM's 228 KB together with
+// their ~4 KB of static shared memory and the 1 KB each block reserves.
+constexpr int kCgsDynSmem = 106 * 1024;
+constexpr int kCgsRedBytes = (kCgsThreads / 32) * 64 * 16;  // end-of-kernel reduction, aliased on the stages
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s: no copy takes that long
 
 __device__ inline unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -364,7 +379,7 @@ __device__ inline void bulk_g2s(void* dst, const void* src, unsigned bytes, uint
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kCgsThreads, 1) k_cgs(T* __restrict__ V, int64_t ld, int64_t n, int j,
+__global__ void __launch_bounds__(kCgsThreads, kCgsBlocksPerSM) k_cgs(T* __restrict__ V, int64_t ld, int64_t n, int j,
                                                         GState* __restrict__ st, double2* __restrict__ partials,
                                                         int n_tiles, int n_stages) {
   constexpr int TR = kSliceBytes / (int)sizeof(T);  // rows per tile
@@ -372,11 +387,12 @@ __global__ void __launch_bounds__(kCgsThreads, 1) k_cgs(T* __restrict__ V, int64
   extern __shared__ __align__(128) unsigned char stage_mem[];
   __shared__ uint64_t bar[2];
   __shared__ T cs[kMaxM + 1];
-  __shared__ double2 red[kCgsThreads / 32][64];
   __shared__ double2 fin[kMaxM + 2];
+  __shared__ __align__(16) unsigned char wraw[kSliceBytes];  // updated w of the tile (never a copy target)
   __shared__ bool aborted;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr int nwarps = kCgsThreads / 32;
+  T* wbuf = (T*)wraw;
   const int nv = j + 2;  // staged slices: V_0..V_j and w = V_{j+1}
   const size_t stage_bytes = (size_t)nv * kSliceStride;
   const int my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -400,6 +416,7 @@ __global__ void __launch_bounds__(kCgsThreads, 1) k_cgs(T* __restrict__ V, int64
     if (n_stages == 2 && my_tiles > 1) issue(1, 1);
   }
   typename Acc<T>::type a_hi = zero<T>();
+  typename Acc<T>::type f0 = zero<T>(), f1 = zero<T>();  // FP32 (complex64) running sums of the slots
   double2 acc0 = make_double2(0.0, 0.0), acc1 = make_double2(0.0, 0.0);
   double nrm = 0.0;
   const int k0 = lane, k1 = lane + 32;
@@ -410,33 +427,59 @@ __global__ void __launch_bounds__(kCgsThreads, 1) k_cgs(T* __restrict__ V, int64
     if (!mbar_wait(&bar[sidx], parity)) aborted = true;
     __syncthreads();
     if (aborted) break;
+    // Staged slices are only ever written by the bulk copies; the updated w goes to wbuf.
     const unsigned char* base = stage_mem + sidx * stage_bytes;
-    T* ws = (T*)(stage_mem + sidx * stage_bytes + (size_t)(j + 1) * kSliceStride);
+    const T* ws = (const T*)(base + (size_t)(j + 1) * kSliceStride);
     const int64_t r0 = (int64_t)(blockIdx.x + (int64_t)it * gridDim.x) * TR;
     if (MODE != 0) {  // row per thread: w -= sum_k V_k c_k
       if (tid < TR) {
-        T w = ws[tid];
-        for (int k = 0; k <= j; ++k) sub_mul(w, ((const T*)(base + (size_t)k * kSliceStride))[tid], cs[k]);
+        T w = ws[tid], w2 = zero<T>();
+        int k = 0;
+        for (; k + 1 <= j; k += 2) {  // two independent chains
+          sub_mul(w, ((const T*)(base + (size_t)k * kSliceStride))[tid], cs[k]);
+          sub_mul(w2, ((const T*)(base + (size_t)(k + 1) * kSliceStride))[tid], cs[k + 1]);
+        }
+        if (k <= j) sub_mul(w, ((const T*)(base + (size_t)k * kSliceStride))[tid], cs[k]);
+        w.x += w2.x;
+        w.y += w2.y;
         const int64_t r = r0 + tid;
         if (r < n) {
           V[(int64_t)(j + 1) * ld + r] = w;
           if (MODE == 2) a_hi.x += nrm2(w);
         }
-        ws[tid] = w;
+        if (MODE == 1) wbuf[tid] = w;
       }
       __syncthreads();
     }
     if (MODE != 2) {  // lane owns slots k0 and k1 (slot j + 1 is ||w||^2); rows staggered by lane
-      typename Acc<T>::type s0 = zero<T>(), s1 = zero<T>();
-      for (int r = wid; r < TR; r += nwarps) {
-        const int row = (r + lane) & (TR - 1);
-        const T wv = ws[row];
-        if (has0) fma_conj(s0, ((const T*)(base + (size_t)k0 * kSliceStride))[row], wv);
-        if (has1) fma_conj(s1, ((const T*)(base + (size_t)k1 * kSliceStride))[row], wv);
+      const T* wsrc = MODE == 0 ? ws : wbuf;
+      const T* v0 = (const T*)(base + (size_t)k0 * kSliceStride);
+      const T* v1 = (const T*)(base + (size_t)k1 * kSliceStride);
+      typename Acc<T>::type t0 = zero<T>(), t1 = zero<T>();  // second row of each pair
+#pragma unroll 2
+      for (int r = wid; r < TR; r += 2 * nwarps) {
+        const int ra = (r + lane) & (TR - 1), rb = (r + nwarps + lane) & (TR - 1);
+        const T wa = wsrc[ra], wb = wsrc[rb];
+        if (has0) {
+          fma_conj(f0, v0[ra], wa);
+          fma_conj(t0, v0[rb], wb);
+        }
+        if (has1) {
+          fma_conj(f1, v1[ra], wa);
+          fma_conj(t1, v1[rb], wb);
+        }
       }
-      acc0 = cadd(acc0, to_d2(s0));
-      acc1 = cadd(acc1, to_d2(s1));
-    } else if ((it & 7) == 7) {  // flush the FP32 norm every 8 tiles (2048 rows per thread at most)
+      f0.x += t0.x;
+      f0.y += t0.y;
+      f1.x += t1.x;
+      f1.y += t1.y;
+      if ((it & 3) == 3) {  // FP32 sums over 4 tiles (64 rows per lane), then FP64
+        acc0 = cadd(acc0, to_d2(f0));
+        acc1 = cadd(acc1, to_d2(f1));
+        f0 = zero<T>();
+        f1 = zero<T>();
+      }
+    } else if ((it & 7) == 7) {  // flush the FP32 norm every 8 tiles (8 rows per thread)
       nrm += (double)a_hi.x;
       a_hi = zero<T>();
     }
@@ -457,6 +500,10 @@ __global__ void __launch_bounds__(kCgsThreads, 1) k_cgs(T* __restrict__ V, int64
     return;
   }
   nrm += (double)a_hi.x;
+  acc0 = cadd(acc0, to_d2(f0));
+  acc1 = cadd(acc1, to_d2(f1));
+  // Every issued copy has been waited for, so the stage memory is free for the block reduction.
+  double2(*red)[64] = reinterpret_cast<double2(*)[64]>(stage_mem);
   if (MODE != 2) {
     red[wid][k0] = acc0;
     red[wid][k1] = acc1;
@@ -608,7 +655,7 @@ __global__ void __launch_bounds__(kT) k_norm2(const double2* __restrict__ b, int
   }
 }
 
-constexpr int kGroup = 8;  // lanes per row in the CSR kernels (rows hold at most ~19 entries)
+constexpr int kGroup = 4;  // lanes per row in the CSR kernels (rows hold at most ~19 entries)
 
 // ------------------------------------------------------------------ host side
 struct HostState {  // leading fields of GState
@@ -626,7 +673,7 @@ Status read_state(petgem_ctx* c, HostState* hs) {
   return Status{};
 }
 
-Status prepare(petgem_ctx* c, int m) {
+Status prepare(petgem_ctx* c, int m, int prec) {
   if (!c->solver) c->solver = new Solver();
   Solver* S = c->solver;
   cudaStream_t s = c->stream;
@@ -646,18 +693,26 @@ Status prepare(petgem_ctx* c, int m) {
   S->m = m;
   S->n_blocks = (n + kRows - 1) / kRows;
   const size_t vbytes_all = (size_t)(m + 1) * S->ld * sizeof(double2);
-  const bool fresh = S->V.bytes < vbytes_all;
+  // The staged Gram-Schmidt kernel reads whole 2 KB slices, so the rows n..ld-1 of every basis
+  // vector must be zero.  Kernels never write them, but complex64 and complex128 vectors place
+  // their padding at different byte offsets: clear the buffer when it grows or the layout changes.
+  const bool fresh = S->V.bytes < vbytes_all || S->prec != prec || S->ld_used != S->ld;
   PG_TRY(S->V.reserve(vbytes_all));
-  if (fresh) PG_CUDA(cudaMemsetAsync(S->V.ptr, 0, S->V.bytes, s));  // padding rows stay zero
+  if (fresh) PG_CUDA(cudaMemsetAsync(S->V.ptr, 0, S->V.bytes, s));
+  S->prec = prec;
+  S->ld_used = S->ld;
   if (S->sms == 0) {
     PG_CUDA(cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, c->device));
     for (auto f : {(const void*)k_cgs<float2, 0>, (const void*)k_cgs<float2, 1>, (const void*)k_cgs<float2, 2>,
                    (const void*)k_cgs<double2, 0>, (const void*)k_cgs<double2, 1>, (const void*)k_cgs<double2, 2>})
       PG_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kCgsDynSmem));
   }
+  PG_TRY(S->partials.reserve((size_t)std::max<int64_t>(std::max<int64_t>(S->n_blocks, kCgsBlocksPerSM * S->sms), 1) *
+                             kPStride * sizeof(double2)));
   PG_TRY(S->u.reserve(n * sizeof(double2)));
   PG_TRY(S->r.reserve(n * sizeof(double2)));
-  PG_TRY(S->partials.reserve((size_t)std::max<int64_t>(S->n_blocks, 1) * kPStride * sizeof(double2)));
+  // Partials: one row per block of the widest reduction grid (vector kernels: n_blocks; the
+  // persistent Gram-Schmidt kernel: one block per SM).
   PG_TRY(S->state.reserve(sizeof(GState)));
   PG_CUDA(cudaMemsetAsync(S->state.ptr, 0, sizeof(GState), s));
   return Status{};
@@ -692,9 +747,9 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, double tol_abs, double inn
     }
     const int nv = j + 2;
     const int n_stages = 2 * nv * kSliceStride <= kCgsDynSmem ? 2 : 1;
-    const size_t dyn = (size_t)n_stages * nv * kSliceStride;
+    const size_t dyn = std::max<size_t>((size_t)n_stages * nv * kSliceStride, kCgsRedBytes);
     const int tiles = (int)(ld * sizeof(T) / kSliceBytes);
-    const unsigned grid = (unsigned)std::min(tiles, S->sms);
+    const unsigned grid = (unsigned)std::min(tiles, kCgsBlocksPerSM * S->sms);
     {
       KernelTimer kt(c, c128 ? "cgs_dot_c128" : "cgs_dot_c64", (j + 2) * vbytes, j, 0);
       k_cgs<T, 0><<<grid, kCgsThreads, dyn, s>>>(V, ld, n, j, st, part, tiles, n_stages);
@@ -750,7 +805,7 @@ Status run_spmv(petgem_ctx* c, const double2* x, double2* y) {
 Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info) {
   const int m = o.restart;
   if (m < 1 || m > kMaxRestart) return Status{PETGEM_ERR_UNSUPPORTED, "restart must be in [1, 62]"};
-  PG_TRY(prepare(c, m));
+  PG_TRY(prepare(c, m, o.precision));
   Solver* S = c->solver;
   cudaStream_t s = c->stream;
   const int64_t n = c->n_edges;

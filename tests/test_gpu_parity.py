@@ -77,11 +77,26 @@ def model_case(name):
         return synth.cube_block_model(16)
     if name == "cube_block_n5":
         return synth.cube_block_model(5)
+    if name == "cube_block_n24":
+        return synth.cube_block_model(24)
     if name == "marine_n12":
         return synth.marine_model(12, n_src=3)
     if name == "bathymetry_n10":
         return synth.bathymetry_model(10, 4)
     raise KeyError(name)
+
+
+_ORACLE = {}
+
+
+def oracle_solution(name):
+    """Oracle system and its 1e-8 solution for a named model, computed once per test session."""
+    if name not in _ORACLE:
+        m = model_case(name)
+        ref = oracle.System(m.mesh.nodes, m.mesh.tets, m.sigma, m.sigma_p, m.freq, synth.sources_array(m.sources))
+        xr, info_r, st_r = ref.solve(tol=1e-8)
+        _ORACLE[name] = (m, ref, xr, st_r)
+    return _ORACLE[name]
 
 
 def gpu_forward(m, solve=True, **opts):
@@ -149,12 +164,11 @@ def test_spmv_matches_oracle():
 
 
 @pytest.mark.parametrize("precision", [api.PREC_C128, api.PREC_MIXED])
-@pytest.mark.parametrize("name", ["cube_block_n16", "marine_n12"])
+@pytest.mark.parametrize("name", ["cube_block_n16", "marine_n12", "cube_block_n24"])
 def test_solve_and_receivers(name, precision):
-    m = model_case(name)
-    src = synth.sources_array(m.sources)
-    ref = oracle.System(m.mesh.nodes, m.mesh.tets, m.sigma, m.sigma_p, m.freq, src)
-    xr, info_r, st_r = ref.solve(tol=1e-8)
+    # cube_block_n24 has 102,024 edges: each persistent Gram-Schmidt block walks 3 (complex64) or
+    # 6 (complex128) row tiles, so the double-buffered stages are reused.
+    m, ref, xr, st_r = oracle_solution(name)
     assert st_r == oracle.OK
     g = gpu_forward(m, precision=precision, tol=1e-8)
     _, _, _, b = ref.system()
@@ -171,6 +185,18 @@ def test_solve_and_receivers(name, precision):
     # Receivers alone, from the same DOFs: interpolation parity at FP64 level.
     rr_same, _ = ref.receivers(g["x"], m.receivers)
     assert rel(g["rcv"], rr_same) <= 1e-12
+
+
+def test_precision_switch_in_one_context():
+    # complex64 and complex128 Krylov vectors share one workspace with different layouts.
+    m, ref, xr, _ = oracle_solution("cube_block_n24")
+    with api.Context(0) as ctx:
+        ctx.mesh(m.mesh.nodes, m.mesh.tets)
+        ctx.assemble(m.freq, m.sigma, m.sigma_p, m.sources)
+        for prec in (api.PREC_C128, api.PREC_MIXED, api.PREC_C128, api.PREC_MIXED):
+            x, info, st = ctx.solve(precision=prec)
+            assert st == api.OK and info[0]["true_rel_residual"] <= 1e-8
+            assert rel(x.cpu().numpy()[0], xr[0]) <= 1e-6
 
 
 def test_solve_tight_tolerance_agrees_closely():
