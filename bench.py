@@ -189,7 +189,7 @@ def run_ours(args):
     ms_mixed, info_mixed, launches, cl = timed(api.PREC_MIXED, args.steps, args.warmup, profile=True, clocks=clocks)
     # Dominant kernel over the timed region (CUDA events around each launch on the ctx stream).
     kstats = {}
-    for name in ("spmv_c64", "cgs_dot_c64", "cgs_upd_dot_c64", "cgs_upd_c64", "cycle_init_c64",
+    for name in ("spmv_c64", "mdot_c64", "cgs_upd_c64", "cycle_init_c64",
                  "xupdate_c64", "residual_c128", "element", "matrix_gather", "rhs", "rcv_locate"):
         n, kms, by = api.petgem_kernel_stats(ctx.h, name)
         if n:
@@ -254,7 +254,7 @@ def run_ours(args):
             "dtype": "c64+f64",
             "data": "synthetic (seeded Kuhn mesh, marine layered model)",
             "config": {"workload": "marine_n%d_1src_1Hz" % args.n, "tets": m.mesh.n_tets,
-                       "edges": n_edges[0], "sources": S, "restart": 50, "tol": 1e-8, "precision": "mixed",
+                       "edges": n_edges[0], "sources": S, "restart": 50, "tol": 1e-8, "precision": "mixed", "orth": "cgs",
                        "l2": "working set > L2 (no flush needed)", "parallelism": "replicas" if world > 1 else "single"},
             "iters": info_mixed[0]["iters"], "cycles": info_mixed[0]["restarts"],
             "reorth_steps": info_mixed[0]["reorth"],

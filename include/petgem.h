@@ -65,9 +65,9 @@ enum { PETGEM_PRECOND_JACOBI = 0 };
  * residual recomputed in FP64 at every restart.
  *   precision = PETGEM_PREC_C128: every vector and the matrix in complex128.
  *   precision = PETGEM_PREC_MIXED: FP64 iterative refinement; each refinement step runs
- *     GMRES cycles on a complex64 copy of the matrix with complex64 Krylov vectors (dot
+ *     a GMRES cycle on a complex64 copy of the matrix with complex64 Krylov vectors (dot
  *     products summed in FP64 across the vector) until the inner residual falls by
- *     inner_tol or inner_cycles cycles have run; x and the residual stay complex128.
+ *     inner_tol or restart steps have run; x and the residual stay complex128.
  *   batch: number of sources iterated together (their SpMVs become one SpMM); 0 = all. */
 typedef struct {
   int32_t restart;
@@ -77,9 +77,15 @@ typedef struct {
   double tol;
   double inner_tol;
   int64_t max_iters;   /* cap on Krylov iterations per source */
-  int32_t inner_cycles;
+  int32_t orth;        /* Arnoldi orthogonalisation: PETGEM_ORTH_CGS (default), _CGS2, _CGS_IFNEEDED */
   int32_t use_graphs;  /* 1 = replay each restart cycle as a CUDA graph */
 } petgem_solve_opts;
+
+/* Orthogonalisation of each new Krylov vector w against the basis V:
+ *   CGS: classical Gram-Schmidt once (two passes over V per step; the default of PETSc's GMRES);
+ *   CGS2: classical Gram-Schmidt twice (three passes);
+ *   CGS_IFNEEDED: a second pass only when ||w|| fell below 1/sqrt(2) of its value. */
+enum { PETGEM_ORTH_CGS2 = 0, PETGEM_ORTH_CGS = 1, PETGEM_ORTH_CGS_IFNEEDED = 2 };
 
 /* Per-source results of petgem_solve. */
 typedef struct {
@@ -149,7 +155,7 @@ int petgem_get_elements(petgem_ctx *ctx, double *K21, double *M21, double *vol);
 /* ----------------------------------------------------------------------- solve (Section 5.1) */
 /* Solve A x_s = b_s for every source.  x: device complex128[n_src][E]; the initial guess in,
  * the solution out.  info: host petgem_solve_info[n_src].  opts: host (NULL = defaults:
- * restart 50, c128, Jacobi, tol 1e-8, max_iters 200000, inner_tol 1e-4, inner_cycles 1).
+ * restart 50, c128, Jacobi, tol 1e-8, max_iters 200000, inner_tol 1e-4, orth CGS).
  * Returns PETGEM_ERR_NOT_CONVERGED or PETGEM_ERR_BREAKDOWN if any source ended that way. */
 int petgem_solve(petgem_ctx *ctx, const petgem_solve_opts *opts, void *x, petgem_solve_info *info);
 

@@ -22,6 +22,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "petgem.h")
 OK, ERR_INVALID_ARG, ERR_BAD_MESH, ERR_DEGENERATE_TET, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_NOT_CONVERGED, \
     ERR_BREAKDOWN, ERR_RECEIVER_OUTSIDE, ERR_UNSUPPORTED, ERR_TIMEOUT = range(11)
 PREC_C128, PREC_MIXED = 0, 1
+ORTH_CGS2, ORTH_CGS, ORTH_CGS_IFNEEDED = 0, 1, 2
 
 
 class petgem_dipole(ctypes.Structure):
@@ -32,7 +33,7 @@ class petgem_dipole(ctypes.Structure):
 class petgem_solve_opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("precision", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("max_iters", ctypes.c_int64), ("inner_cycles", ctypes.c_int32), ("use_graphs", ctypes.c_int32)]
+                ("max_iters", ctypes.c_int64), ("orth", ctypes.c_int32), ("use_graphs", ctypes.c_int32)]
 
 
 class petgem_solve_info(ctypes.Structure):
@@ -153,8 +154,8 @@ def petgem_get_elements(ctx, K21=None, M21=None, vol=None):
 
 
 def solve_opts(restart=50, precision=PREC_C128, tol=1e-8, inner_tol=1e-4, max_iters=200000, batch=1,
-               inner_cycles=1, use_graphs=0) -> petgem_solve_opts:
-    return petgem_solve_opts(restart, precision, 0, batch, tol, inner_tol, max_iters, inner_cycles, use_graphs)
+               orth=ORTH_CGS, use_graphs=0) -> petgem_solve_opts:
+    return petgem_solve_opts(restart, precision, 0, batch, tol, inner_tol, max_iters, orth, use_graphs)
 
 
 def petgem_solve(ctx, x, n_src, opts=None, allow_not_converged=False):

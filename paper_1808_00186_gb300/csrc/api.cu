@@ -265,11 +265,12 @@ int petgem_solve(petgem_ctx* c, const petgem_solve_opts* opts, void* x, petgem_s
   o.tol = 1e-8;
   o.inner_tol = 1e-4;
   o.max_iters = 200000;
-  o.inner_cycles = 1;
+  o.orth = PETGEM_ORTH_CGS;
   o.use_graphs = 0;
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_iters < 0 || (o.precision != PETGEM_PREC_C128 && o.precision != PETGEM_PREC_MIXED) ||
-      o.precond != PETGEM_PRECOND_JACOBI || !(o.inner_tol >= 0.0 && o.inner_tol < 1.0))
+      o.precond != PETGEM_PRECOND_JACOBI || !(o.inner_tol >= 0.0 && o.inner_tol < 1.0) || o.orth < 0 ||
+      o.orth > PETGEM_ORTH_CGS_IFNEEDED)
     return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve: bad options"});
   Status s = set_device(c);
   if (s.ok()) s = petgem::run_solve(c, o, static_cast<double2*>(x), info);

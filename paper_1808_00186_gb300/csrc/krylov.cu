@@ -331,15 +331,116 @@ __global__ void __launch_bounds__(kT) k_cycle_init(const double2* __restrict__ r
 // per tile: 128 (complex64) or 64 (complex128).  ld is a multiple of 256 elements, so every slice
 // is whole and 16-byte aligned; rows >= n are zero padding.  Two blocks per SM hide each other's
 // waits; each block double-buffers its own tiles.
-constexpr int kSliceBytes = 1024;
-constexpr int kSliceStride = kSliceBytes + 16;  // 16-byte pad shifts banks between slices
+constexpr int kMaxSlice = 2048;   // largest per-vector slice of a row tile (bytes)
+constexpr int kSlicePad = 16;     // pad between slices: shifts shared-memory banks, keeps 16-byte alignment
+constexpr int kMaxStages = 4;
 constexpr int kCgsThreads = 256;
 constexpr int kCgsBlocksPerSM = 2;
 // Dynamic shared memory per block: two blocks per SM must fit in the SM's 228 KB together with
-// their ~4 KB of static shared memory and the 1 KB each block reserves.
-constexpr int kCgsDynSmem = 106 * 1024;
+// their ~5 KB of static shared memory and the 1 KB each block reserves.
+constexpr int kCgsDynSmem = 105 * 1024;
 constexpr int kCgsRedBytes = (kCgsThreads / 32) * 64 * 16;  // end-of-kernel reduction, aliased on the stages
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s: no copy takes that long
+
+// Slice size and stage count for nv staged vectors: 1 KB slices, double-buffered (the fastest
+// measured shape on this GPU; deeper staging with smaller slices lost more to per-tile overhead).
+struct CgsShape {
+  int slice, stages;
+};
+inline CgsShape cgs_shape(int nv) {
+  const int st = kCgsDynSmem / (nv * (1024 + kSlicePad));
+  return CgsShape{1024, st >= 2 ? 2 : 1};
+}
+
+// ------------------------------------------------------------------ projections (dot pass)
+// h = V^H w and ||w||^2 for w = V_{j+1}: each thread keeps kR rows of w in registers and streams
+// the basis two vectors at a time (2 kR independent loads in flight), high occupancy.  complex64:
+// FP32 products over the thread's rows and an FP32 tree over the warp (256 rows); the warp totals
+// are turned into FP64 only at the end, and everything across warps and blocks is FP64.
+template <typename T>
+__global__ void __launch_bounds__(kT) k_mdot(const T* __restrict__ V, int64_t ld, int64_t n, int j,
+                                             GState* __restrict__ st, double2* __restrict__ partials) {
+  if (st->done) return;
+  using A = typename Acc<T>::type;
+  __shared__ A red[kMaxM + 2][kT / 32];
+  __shared__ double2 fin[kMaxM + 2];
+  const int nk = j + 1, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const T* w = V + (int64_t)(j + 1) * ld;
+  const int64_t base = blockIdx.x * (int64_t)kRows + threadIdx.x;
+  T wr[kR];
+#pragma unroll
+  for (int q = 0; q < kR; ++q) {
+    const int64_t i = base + (int64_t)q * kT;
+    wr[q] = i < n ? w[i] : zero<T>();
+  }
+  auto warp_tree = [&](A a) {
+    for (int o = 16; o > 0; o >>= 1) {
+      a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+      a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+    }
+    return a;
+  };
+  {
+    A a = zero<T>();
+#pragma unroll
+    for (int q = 0; q < kR; ++q) a.x += nrm2(wr[q]);
+    a = warp_tree(a);
+    if (lane == 0) red[nk][wid] = a;
+  }
+  int k = 0;
+  for (; k + 1 < nk; k += 2) {
+    const T* v0 = V + (int64_t)k * ld;
+    const T* v1 = v0 + ld;
+    T a0[kR], a1[kR];
+#pragma unroll
+    for (int q = 0; q < kR; ++q) {
+      const int64_t i = base + (int64_t)q * kT;
+      a0[q] = i < n ? v0[i] : zero<T>();
+      a1[q] = i < n ? v1[i] : zero<T>();
+    }
+    A s0 = zero<T>(), s1 = zero<T>();
+#pragma unroll
+    for (int q = 0; q < kR; ++q) {
+      fma_conj(s0, a0[q], wr[q]);
+      fma_conj(s1, a1[q], wr[q]);
+    }
+    s0 = warp_tree(s0);
+    s1 = warp_tree(s1);
+    if (lane == 0) {
+      red[k][wid] = s0;
+      red[k + 1][wid] = s1;
+    }
+  }
+  for (; k < nk; ++k) {
+    const T* v0 = V + (int64_t)k * ld;
+    A s0 = zero<T>();
+#pragma unroll
+    for (int q = 0; q < kR; ++q) {
+      const int64_t i = base + (int64_t)q * kT;
+      if (i < n) fma_conj(s0, v0[i], wr[q]);
+    }
+    s0 = warp_tree(s0);
+    if (lane == 0) red[k][wid] = s0;
+  }
+  __syncthreads();
+  for (int kk = threadIdx.x; kk <= nk; kk += kT) {
+    double2 sum = make_double2(0.0, 0.0);
+    for (int ww = 0; ww < kT / 32; ++ww) sum = cadd(sum, to_d2(red[kk][ww]));
+    partials[(int64_t)blockIdx.x * kPStride + kk] = sum;
+  }
+  if (!last_block(&st->counter)) return;
+  reduce_partials(partials, gridDim.x, nk + 1, fin);
+  for (int kk = threadIdx.x; kk < nk; kk += kT) {
+    const double ib = st->inv_beta[kk];
+    const double2 h = cscale(fin[kk], ib);  // v_k^H w with v_k = V_k / ||V_k||
+    st->h[kk] = h;
+    st->c[kk] = cscale(h, ib);              // w -= V_k * (h_k / ||V_k||)
+  }
+  if (threadIdx.x == 0) {
+    st->nrm_w = fin[nk].x;
+    st->counter = 0;
+  }
+}
 
 __device__ inline unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ inline void mbar_init(uint64_t* bar, unsigned count) {
@@ -381,40 +482,44 @@ __device__ inline void bulk_g2s(void* dst, const void* src, unsigned bytes, uint
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kCgsThreads, kCgsBlocksPerSM) k_cgs(T* __restrict__ V, int64_t ld, int64_t n, int j,
                                                         GState* __restrict__ st, double2* __restrict__ partials,
-                                                        int n_tiles, int n_stages) {
-  constexpr int TR = kSliceBytes / (int)sizeof(T);  // rows per tile
-  if (st->done) return;
+                                                        int n_tiles, int slice, int n_stages, int pass,
+                                                        int need_refine, double eta2) {
+  if (st->done || (need_refine && !st->refine)) return;
   extern __shared__ __align__(128) unsigned char stage_mem[];
-  __shared__ uint64_t bar[2];
+  __shared__ uint64_t bar[kMaxStages];
   __shared__ T cs[kMaxM + 1];
   __shared__ double2 fin[kMaxM + 2];
-  __shared__ __align__(16) unsigned char wraw[kSliceBytes];  // updated w of the tile (never a copy target)
+  __shared__ __align__(16) unsigned char wraw[kMaxSlice];  // updated w of the tile (never a copy target)
   __shared__ bool aborted;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr int nwarps = kCgsThreads / 32;
   T* wbuf = (T*)wraw;
-  const int nv = j + 2;  // staged slices: V_0..V_j and w = V_{j+1}
-  const size_t stage_bytes = (size_t)nv * kSliceStride;
+  const int TR = slice / (int)sizeof(T);  // rows per tile: 32..256, a power of two
+  const int stride = slice + kSlicePad;
+  const int nv = j + 2;                   // staged slices: V_0..V_j and w = V_{j+1}
+  const size_t stage_bytes = (size_t)nv * stride;
   const int my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int i = 0; i < n_stages; ++i) mbar_init(&bar[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     aborted = false;
   }
   if (MODE != 0)
     for (int k = tid; k <= j; k += kCgsThreads) cs[k] = from_d2<T>(st->c[k]);
   __syncthreads();
-  auto issue = [&](int it, int sidx) {
+  auto issue = [&](int it) {
+    const int sidx = it % n_stages;
     const int64_t r0 = (int64_t)(blockIdx.x + (int64_t)it * gridDim.x) * TR;
     unsigned char* base = stage_mem + sidx * stage_bytes;
-    mbar_expect_tx(&bar[sidx], (unsigned)(nv * kSliceBytes));
-    for (int k = 0; k < nv; ++k) bulk_g2s(base + (size_t)k * kSliceStride, V + (int64_t)k * ld + r0, kSliceBytes, &bar[sidx]);
+    mbar_expect_tx(&bar[sidx], (unsigned)(nv * slice));
+    for (int k = 0; k < nv; ++k) bulk_g2s(base + (size_t)k * stride, V + (int64_t)k * ld + r0, slice, &bar[sidx]);
   };
-  if (tid == 0) {
-    if (my_tiles > 0) issue(0, 0);
-    if (n_stages == 2 && my_tiles > 1) issue(1, 1);
-  }
+  if (tid == 0)
+    for (int it = 0; it < n_stages && it < my_tiles; ++it) issue(it);
+  // Update mode: one thread per row (threads beyond TR rows idle: fewer instructions measured faster
+  // than sharing a row between threads).
+  const int split = 1;
+  const int urow = tid, usub = 0;
   typename Acc<T>::type a_hi = zero<T>();
   typename Acc<T>::type f0 = zero<T>(), f1 = zero<T>();  // FP32 (complex64) running sums of the slots
   double2 acc0 = make_double2(0.0, 0.0), acc1 = make_double2(0.0, 0.0);
@@ -422,43 +527,49 @@ __global__ void __launch_bounds__(kCgsThreads, kCgsBlocksPerSM) k_cgs(T* __restr
   const int k0 = lane, k1 = lane + 32;
   const bool has0 = k0 <= j + 1, has1 = k1 <= j + 1;
   for (int it = 0; it < my_tiles; ++it) {
-    const int sidx = n_stages == 2 ? (it & 1) : 0;
-    const unsigned parity = n_stages == 2 ? ((it >> 1) & 1) : (it & 1);
+    const int sidx = it % n_stages;
+    const unsigned parity = (unsigned)((it / n_stages) & 1);
     if (!mbar_wait(&bar[sidx], parity)) aborted = true;
     __syncthreads();
     if (aborted) break;
     // Staged slices are only ever written by the bulk copies; the updated w goes to wbuf.
     const unsigned char* base = stage_mem + sidx * stage_bytes;
-    const T* ws = (const T*)(base + (size_t)(j + 1) * kSliceStride);
+    const T* ws = (const T*)(base + (size_t)(j + 1) * stride);
     const int64_t r0 = (int64_t)(blockIdx.x + (int64_t)it * gridDim.x) * TR;
-    if (MODE != 0) {  // row per thread: w -= sum_k V_k c_k
-      if (tid < TR) {
-        T w = ws[tid], w2 = zero<T>();
-        int k = 0;
-        for (; k + 1 <= j; k += 2) {  // two independent chains
-          sub_mul(w, ((const T*)(base + (size_t)k * kSliceStride))[tid], cs[k]);
-          sub_mul(w2, ((const T*)(base + (size_t)(k + 1) * kSliceStride))[tid], cs[k + 1]);
+    if (MODE != 0) {  // w -= sum_k V_k c_k, rows over threads (split threads per row for short tiles)
+      if (urow < TR) {
+        T w = usub == 0 ? ws[urow] : zero<T>(), w2 = zero<T>();
+        int k = usub;
+        for (; k + split <= j; k += 2 * split) {  // two independent chains
+          sub_mul(w, ((const T*)(base + (size_t)k * stride))[urow], cs[k]);
+          sub_mul(w2, ((const T*)(base + (size_t)(k + split) * stride))[urow], cs[k + split]);
         }
-        if (k <= j) sub_mul(w, ((const T*)(base + (size_t)k * kSliceStride))[tid], cs[k]);
+        if (k <= j) sub_mul(w, ((const T*)(base + (size_t)k * stride))[urow], cs[k]);
         w.x += w2.x;
         w.y += w2.y;
-        const int64_t r = r0 + tid;
-        if (r < n) {
-          V[(int64_t)(j + 1) * ld + r] = w;
-          if (MODE == 2) a_hi.x += nrm2(w);
+        for (int o = 1; o < split; o <<= 1) {  // the split threads are adjacent lanes
+          w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
+          w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
         }
-        if (MODE == 1) wbuf[tid] = w;
+        const int64_t r = r0 + urow;
+        if (usub == 0) {
+          if (r < n) {
+            V[(int64_t)(j + 1) * ld + r] = w;
+            if (MODE == 2) a_hi.x += nrm2(w);
+          }
+          if (MODE == 1) wbuf[urow] = w;
+        }
       }
       __syncthreads();
     }
     if (MODE != 2) {  // lane owns slots k0 and k1 (slot j + 1 is ||w||^2); rows staggered by lane
       const T* wsrc = MODE == 0 ? ws : wbuf;
-      const T* v0 = (const T*)(base + (size_t)k0 * kSliceStride);
-      const T* v1 = (const T*)(base + (size_t)k1 * kSliceStride);
+      const T* v0 = (const T*)(base + (size_t)k0 * stride);
+      const T* v1 = (const T*)(base + (size_t)k1 * stride);
+      const int mask = TR - 1;
       typename Acc<T>::type t0 = zero<T>(), t1 = zero<T>();  // second row of each pair
-#pragma unroll 2
       for (int r = wid; r < TR; r += 2 * nwarps) {
-        const int ra = (r + lane) & (TR - 1), rb = (r + nwarps + lane) & (TR - 1);
+        const int ra = (r + lane) & mask, rb = (r + nwarps + lane) & mask;
         const T wa = wsrc[ra], wb = wsrc[rb];
         if (has0) {
           fma_conj(f0, v0[ra], wa);
@@ -473,20 +584,20 @@ __global__ void __launch_bounds__(kCgsThreads, kCgsBlocksPerSM) k_cgs(T* __restr
       f0.y += t0.y;
       f1.x += t1.x;
       f1.y += t1.y;
-      if ((it & 3) == 3) {  // FP32 sums over 4 tiles (64 rows per lane), then FP64
+      if ((it & 3) == 3) {  // FP32 sums over at most 4 tiles (<= 128 rows per lane), then FP64
         acc0 = cadd(acc0, to_d2(f0));
         acc1 = cadd(acc1, to_d2(f1));
         f0 = zero<T>();
         f1 = zero<T>();
       }
-    } else if ((it & 7) == 7) {  // flush the FP32 norm every 8 tiles (8 rows per thread)
+    } else if ((it & 7) == 7) {  // flush the FP32 norm every 8 tiles (<= 8 rows per thread)
       nrm += (double)a_hi.x;
       a_hi = zero<T>();
     }
     __syncthreads();  // every thread is done with this stage
     if (tid == 0 && it + n_stages < my_tiles) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(it + n_stages, sidx);
+      issue(it + n_stages);
     }
   }
   if (aborted) {
@@ -524,11 +635,14 @@ __global__ void __launch_bounds__(kCgsThreads, kCgsBlocksPerSM) k_cgs(T* __restr
     for (int k = tid; k <= j; k += kCgsThreads) {
       const double ib = st->inv_beta[k];
       const double2 h = cscale(fin[k], ib);
-      st->h[k] = h;
+      if (pass == 0)
+        st->h[k] = h;
+      else
+        st->h2[k] = h;
       st->c[k] = cscale(h, ib);
     }
     if (tid == 0) {
-      st->nrm_w = fin[j + 1].x;
+      if (pass == 0) st->nrm_w = fin[j + 1].x;
       st->counter = 0;
     }
   } else if (MODE == 1) {
@@ -540,13 +654,24 @@ __global__ void __launch_bounds__(kCgsThreads, kCgsBlocksPerSM) k_cgs(T* __restr
     }
     if (tid == 0) st->counter = 0;
   } else {
+    // pass 0 with eta2 > 0: keep this single pass only if ||w|| kept more than eta of its norm.
+    if (pass == 0 && eta2 > 0.0 && fin[0].x < eta2 * st->nrm_w) {
+      if (tid == 0) {
+        st->refine = 1;
+        st->counter = 0;
+      }
+      return;
+    }
     __shared__ double2 hsum[kMaxM + 1];
-    for (int k = tid; k <= j; k += kCgsThreads) hsum[k] = cadd(st->h[k], st->h2[k]);
+    for (int k = tid; k <= j; k += kCgsThreads) hsum[k] = pass == 1 ? cadd(st->h[k], st->h2[k]) : st->h[k];
     __syncthreads();
     if (tid == 0) {
       finish_column(st, j, hsum, fin[0].x);
-      st->refined[j] = 1;
-      st->n_refine += 1;
+      if (pass == 1) {
+        st->refined[j] = 1;
+        st->n_refine += 1;
+      }
+      st->refine = 0;
       st->counter = 0;
     }
   }
@@ -719,7 +844,7 @@ Status prepare(petgem_ctx* c, int m, int prec) {
 }
 
 template <typename T>
-Status run_cycle(petgem_ctx* c, const T* ahat, int m, double tol_abs, double inner_rel, HostState* hs) {
+Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, double inner_rel, HostState* hs) {
   Solver* S = c->solver;
   cudaStream_t s = c->stream;
   const int64_t n = S->n, ld = S->ld;
@@ -746,23 +871,41 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, double tol_abs, double inn
                                                             vn, n, st, j);
     }
     const int nv = j + 2;
-    const int n_stages = 2 * nv * kSliceStride <= kCgsDynSmem ? 2 : 1;
-    const size_t dyn = std::max<size_t>((size_t)n_stages * nv * kSliceStride, kCgsRedBytes);
-    const int tiles = (int)(ld * sizeof(T) / kSliceBytes);
+    const CgsShape shp = cgs_shape(nv);
+    const size_t dyn = std::max<size_t>((size_t)shp.stages * nv * (shp.slice + kSlicePad), kCgsRedBytes);
+    const int tiles = (int)(ld * sizeof(T) / shp.slice);
     const unsigned grid = (unsigned)std::min(tiles, kCgsBlocksPerSM * S->sms);
-    {
-      KernelTimer kt(c, c128 ? "cgs_dot_c128" : "cgs_dot_c64", (j + 2) * vbytes, j, 0);
-      k_cgs<T, 0><<<grid, kCgsThreads, dyn, s>>>(V, ld, n, j, st, part, tiles, n_stages);
+    const int64_t wb = (int64_t)vbytes;
+    auto cgs = [&](int mode, int pass, int need_refine, double eta2, const char* name, double bytes, int tag) {
+      KernelTimer kt(c, name, bytes, j, tag);
+      if (mode == 0)
+        k_cgs<T, 0><<<grid, kCgsThreads, dyn, s>>>(V, ld, n, j, st, part, tiles, shp.slice, shp.stages, pass, need_refine, eta2);
+      else if (mode == 1)
+        k_cgs<T, 1><<<grid, kCgsThreads, dyn, s>>>(V, ld, n, j, st, part, tiles, shp.slice, shp.stages, pass, need_refine, eta2);
+      else
+        k_cgs<T, 2><<<grid, kCgsThreads, dyn, s>>>(V, ld, n, j, st, part, tiles, shp.slice, shp.stages, pass, need_refine, eta2);
+      c->launches++;
+    };
+    const double dot_b = (double)(j + 2) * wb, upd_b = (double)(j + 3) * wb;
+    auto mdot = [&]() {
+      KernelTimer kt(c, c128 ? "mdot_c128" : "mdot_c64", dot_b, j, 0);
+      k_mdot<T><<<nb, kT, 0, s>>>(V, ld, n, j, st, part);
+      c->launches++;
+    };
+    if (orth == 0) {  // CGS2: dots, update + dots, update + norm
+      mdot();
+      cgs(1, 0, 0, 0.0, c128 ? "cgs_upd_dot_c128" : "cgs_upd_dot_c64", upd_b, 0);
+      cgs(2, 1, 0, 0.0, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0);
+    } else if (orth == 1) {  // CGS: dots, update + norm
+      mdot();
+      cgs(2, 0, 0, 0.0, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0);
+    } else {  // CGS, second pass when the norm fell below 1/sqrt(2) of its value
+      mdot();
+      cgs(2, 0, 0, 0.5, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0);
+      cgs(0, 1, 1, 0.0, c128 ? "cgs_dot2_c128" : "cgs_dot2_c64", dot_b, 1);
+      cgs(2, 1, 1, 0.0, c128 ? "cgs_upd2_c128" : "cgs_upd2_c64", upd_b, 1);
     }
-    {
-      KernelTimer kt(c, c128 ? "cgs_upd_dot_c128" : "cgs_upd_dot_c64", (j + 3) * vbytes, j, 0);
-      k_cgs<T, 1><<<grid, kCgsThreads, dyn, s>>>(V, ld, n, j, st, part, tiles, n_stages);
-    }
-    {
-      KernelTimer kt(c, c128 ? "cgs_upd_c128" : "cgs_upd_c64", (j + 3) * vbytes, j, 0);
-      k_cgs<T, 2><<<grid, kCgsThreads, dyn, s>>>(V, ld, n, j, st, part, tiles, n_stages);
-    }
-    c->launches += 4;
+    c->launches += 1;
   }
   PG_CUDA(cudaGetLastError());
   k_backsolve<<<1, 32, 0, s>>>(st);
@@ -846,9 +989,9 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
       const double tol_abs = o.tol * bnorm;
       // A cycle whose starting residual already meets tol runs no iteration (k = 0).
       if (o.precision == PETGEM_PREC_MIXED)
-        PG_TRY(run_cycle<float2>(c, S->ahat64.as<float2>(), mj, tol_abs, o.inner_tol, &hs));
+        PG_TRY(run_cycle<float2>(c, S->ahat64.as<float2>(), mj, o.orth, tol_abs, o.inner_tol, &hs));
       else
-        PG_TRY(run_cycle<double2>(c, S->ahat128.as<double2>(), mj, tol_abs, 0.0, &hs));
+        PG_TRY(run_cycle<double2>(c, S->ahat128.as<double2>(), mj, o.orth, tol_abs, 0.0, &hs));
       relres = sqrt(hs.rnorm2) / bnorm;  // FP64 residual of the current u
       if (!isfinite(relres)) {
         status = PETGEM_ERR_BREAKDOWN;

@@ -187,6 +187,20 @@ def test_solve_and_receivers(name, precision):
     assert rel(g["rcv"], rr_same) <= 1e-12
 
 
+@pytest.mark.parametrize("orth", [api.ORTH_CGS2, api.ORTH_CGS_IFNEEDED])
+@pytest.mark.parametrize("precision", [api.PREC_C128, api.PREC_MIXED])
+def test_orthogonalisation_variants(orth, precision):
+    m, ref, xr, _ = oracle_solution("cube_block_n24")
+    g = gpu_forward(m, precision=precision, tol=1e-8, orth=orth)
+    _, _, _, b = ref.system()
+    inf = g["info"][0]
+    assert inf["status"] == api.OK and inf["true_rel_residual"] <= 1e-8
+    assert np.linalg.norm(b[0] - ref.spmv(g["x"][0])) / np.linalg.norm(b[0]) <= 1.0001e-8
+    assert rel(g["x"][0], xr[0]) <= 1e-6
+    if orth == api.ORTH_CGS2:
+        assert inf["reorth"] == inf["iters"]
+
+
 def test_precision_switch_in_one_context():
     # complex64 and complex128 Krylov vectors share one workspace with different layouts.
     m, ref, xr, _ = oracle_solution("cube_block_n24")
@@ -195,7 +209,7 @@ def test_precision_switch_in_one_context():
         ctx.assemble(m.freq, m.sigma, m.sigma_p, m.sources)
         for prec in (api.PREC_C128, api.PREC_MIXED, api.PREC_C128, api.PREC_MIXED):
             x, info, st = ctx.solve(precision=prec)
-            assert st == api.OK and info[0]["true_rel_residual"] <= 1e-8
+            assert st == api.OK and info[0]["true_rel_residual"] <= 1e-8 and info[0]["reorth"] == 0
             assert rel(x.cpu().numpy()[0], xr[0]) <= 1e-6
 
 
