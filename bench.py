@@ -37,6 +37,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=64, help="cells per axis of the marine model")
     p.add_argument("--no-plain", action="store_true", help="skip the complex128 comparison run")
+    p.add_argument("--block-sources", type=int, default=32, help="sources of the multi-source block solve (0 = skip)")
     p.add_argument("--profile-step", action="store_true",
                    help="run one untimed step of the hot path and exit (the command profilers capture)")
     p.add_argument("--precision", default="mixed", choices=["mixed", "c128"], help="solver of --profile-step")
@@ -201,6 +202,39 @@ def run_ours(args):
         plain = {"ms_per_step": ms_plain, "s_per_source": ms_plain / 1e3 / S, "iters": info_plain[0]["iters"],
                  "true_rel_residual": info_plain[0]["true_rel_residual"]}
 
+    # Multi-source block solve (all sources of one frequency in one SpMM-based solve): the marine
+    # mesh with args.block_sources dipoles along x in [-4, 4] km; timed once after a warm-up.
+    block = None
+    if args.block_sources > 1:
+        mb = synth.marine_model(args.n, n_src=args.block_sources)
+        Sb = len(mb.sources)
+
+        def block_step():
+            Eb = api.petgem_mesh_edges(ctx.h, nodes, tets)
+            api.petgem_assemble(ctx.h, mb.freq, sigma, mb.sigma_p, mb.sources)
+            xb = torch.zeros((Sb, Eb), dtype=torch.complex128, device=dev)
+            st, info = api.petgem_solve(ctx.h, xb, Sb, api.solve_opts(precision=api.PREC_MIXED, tol=1e-8, batch=0))
+            return info
+
+        block_step()
+        barrier()
+        api.petgem_profile(ctx.h, True)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record()
+        binfo = block_step()
+        b1.record()
+        barrier()
+        bks = {}
+        for name in ("bspmm_c64", "bmdot_c64", "bmupdate_c64", "bresidual_c128"):
+            n_, kms, by = api.petgem_kernel_stats(ctx.h, name)
+            if n_:
+                bks[name] = {"launches": n_, "ms": round(kms, 3), "gbs": round(by / (kms * 1e-3) / 1e9, 1)}
+        api.petgem_profile(ctx.h, False)
+        bms = b0.elapsed_time(b1)
+        block = {"sources": Sb, "ms_per_step": round(bms, 3), "s_per_source": round(bms / 1e3 / Sb, 6),
+                 "iters_max": max(i["iters"] for i in binfo),
+                 "worst_true_rel_residual": max(i["true_rel_residual"] for i in binfo), "kernels": bks}
+
     # End to end through the public API from pinned host buffers, results read back each step.
     h_nodes = torch.as_tensor(m.mesh.nodes).pin_memory()
     h_tets = torch.as_tensor(m.mesh.tets).pin_memory()
@@ -260,6 +294,7 @@ def run_ours(args):
             "reorth_steps": info_mixed[0]["reorth"],
             "true_rel_residual": info_mixed[0]["true_rel_residual"],
             "plain_c128": plain,
+            "block_multi_source": block,
             "speedup_vs_plain": round(plain["ms_per_step"] / ms_mixed, 3) if plain else None,
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "gbs": round(v["gbs"], 1)}
                         for k, v in kstats.items()},

@@ -112,6 +112,7 @@ Status build_assembly(petgem_ctx* c, const double* sigma_dev);
 Status run_receivers(petgem_ctx* c, int32_t n_rcv, const double* rx, const double2* x, double2* out,
                      bool* outside);
 Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info);
+Status run_solve_block(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info);
 Status run_spmv(petgem_ctx* c, const double2* x, double2* y);
 void destroy_solver(petgem_ctx* c);
 

@@ -21,185 +21,11 @@
 
 #include <algorithm>
 
-#include "ctx.cuh"
+#include "krylov.cuh"
 
 namespace petgem {
 
-constexpr int kMaxM = 64;        // capacity of the Hessenberg arrays
-constexpr int kMaxRestart = 62;  // Gram-Schmidt slots j + 2 <= 64
-
-struct GState {
-  int m, k, done, refine;
-  unsigned counter;
-  int n_refine;    // steps of this cycle that took a second Gram-Schmidt pass
-  int timeout;     // a bounded wait in a kernel gave up
-  int pad1;
-  double stop_abs;
-  double nrm_w;    // ||w||^2 before orthogonalisation (pass 0)
-  double rnorm2;   // ||r||^2 of the FP64 residual at the start of the cycle
-  double beta0;
-  uint8_t refined[kMaxM];
-  double2 H[(kMaxM + 1) * kMaxM];  // column j at H[j * (kMaxM + 1) + i], rotated in place
-  double2 g[kMaxM + 1];
-  double cs_c[kMaxM];
-  double2 cs_s[kMaxM];
-  double2 h[kMaxM + 1];   // projections of the current column, pass 0
-  double2 h2[kMaxM + 1];  // projections, pass 1
-  double2 c[kMaxM + 1];   // update coefficients inv_beta[k] * h[k] of the running pass
-  double inv_beta[kMaxM + 1];
-  float inv_beta32[kMaxM + 1];  // the same scales in FP32, for the complex64 kernels
-  double2 y[kMaxM];       // cycle solution, already scaled by inv_beta
-};
-
-struct Solver {
-  int64_t n = 0, ld = 0;
-  int m = 0;
-  int prec = -1;
-  int64_t version = -1;  // assembly version the scaled matrices belong to
-  DevBuf ahat128, ahat64, dinv;  // scaled matrix (c128, c64)
-  DevBuf V, u, r, partials, state;
-  int64_t n_blocks = 0;
-  int64_t ld_used = 0;
-  int sms = 0;
-};
-
 namespace {
-
-constexpr int kT = 256;   // threads per block of the vector kernels
-constexpr int kR = 8;     // rows per thread of the vector kernels
-constexpr int kRows = kT * kR;
-constexpr int kPStride = kMaxM + 2;
-
-// ------------------------------------------------------------------ precision traits
-__device__ inline double2 to_d2(double2 a) { return a; }
-__device__ inline double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
-template <typename T> __device__ inline T from_d2(double2 a);
-template <> __device__ inline double2 from_d2<double2>(double2 a) { return a; }
-template <> __device__ inline float2 from_d2<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
-template <typename T> __device__ inline T zero();
-template <> __device__ inline double2 zero<double2>() { return make_double2(0.0, 0.0); }
-template <> __device__ inline float2 zero<float2>() { return make_float2(0.f, 0.f); }
-
-// Accumulator of a thread's products: FP64 for complex128 data, FP32 for complex64 data
-// (only over the thread's kR rows; everything across threads is summed in FP64).
-template <typename T> struct Acc;
-template <> struct Acc<double2> { using type = double2; };
-template <> struct Acc<float2> { using type = float2; };
-
-__device__ inline void fma_conj(double2& acc, double2 a, double2 b) {  // acc += conj(a) b
-  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-  acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
-}
-__device__ inline void fma_conj(float2& acc, float2 a, float2 b) {
-  acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
-  acc.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y));
-}
-__device__ inline void fma_c(double2& acc, double2 a, double2 b) {  // acc += a b
-  acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
-  acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
-}
-__device__ inline void fma_c(float2& acc, float2 a, float2 b) {
-  acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
-  acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
-}
-__device__ inline void sub_mul(double2& w, double2 v, double2 c) {  // w -= v c
-  w.x = fma(-v.x, c.x, fma(v.y, c.y, w.x));
-  w.y = fma(-v.x, c.y, fma(-v.y, c.x, w.y));
-}
-__device__ inline void sub_mul(float2& w, float2 v, float2 c) {
-  w.x = fmaf(-v.x, c.x, fmaf(v.y, c.y, w.x));
-  w.y = fmaf(-v.x, c.y, fmaf(-v.y, c.x, w.y));
-}
-__device__ inline double nrm2(double2 a) { return a.x * a.x + a.y * a.y; }
-__device__ inline float nrm2(float2 a) { return a.x * a.x + a.y * a.y; }
-
-__device__ inline double2 warp_sum(double2 v) {
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-  }
-  return v;
-}
-__device__ inline double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-
-
-// Block-level "last block done" handshake: returns true in exactly one block, after every block
-// has published its partials.
-__device__ inline bool last_block(unsigned* counter) {
-  __shared__ bool last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned t = atomicAdd(counter, 1u);
-    last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (last) __threadfence();
-  return last;
-}
-
-// Sum partials[b * kPStride + k] over blocks b for k in [0, nk) in a fixed order; result in out[k].
-__device__ void reduce_partials(const double2* partials, int nblocks, int nk, double2* out) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = w; k < nk; k += kT / 32) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int b = lane; b < nblocks; b += 32) {
-      double2 p = __ldcg(&partials[(int64_t)b * kPStride + k]);
-      s.x += p.x;
-      s.y += p.y;
-    }
-    s = warp_sum(s);
-    if (lane == 0) out[k] = s;
-  }
-  __syncthreads();
-}
-
-// New Hessenberg column j from the projections h (summed over passes) and beta = ||V_{j+1}||:
-// earlier rotations, a new complex Givens rotation, the residual estimate and the stopping test.
-__device__ __noinline__ void finish_column(GState* st, int j, const double2* h, double beta2) {
-  double beta = sqrt(beta2);
-  double2* Hc = &st->H[j * (kMaxM + 1)];
-  for (int i = 0; i <= j; ++i) Hc[i] = h[i];
-  Hc[j + 1] = make_double2(beta, 0.0);
-  st->inv_beta[j + 1] = beta > 0.0 ? 1.0 / beta : 0.0;
-  st->inv_beta32[j + 1] = (float)st->inv_beta[j + 1];
-  for (int i = 0; i < j; ++i) {
-    double2 a = Hc[i], b = Hc[i + 1];
-    double c = st->cs_c[i];
-    double2 s = st->cs_s[i];
-    Hc[i] = cadd(cscale(a, c), cmul(s, b));
-    Hc[i + 1] = csub(cscale(b, c), cconjmul(s, a));  // -conj(s) a + c b
-  }
-  double2 a = Hc[j];
-  double aa = sqrt(cabs2(a));
-  double rho = sqrt(aa * aa + beta * beta);
-  double c;
-  double2 s;
-  if (aa == 0.0) {
-    c = 0.0;
-    s = make_double2(1.0, 0.0);
-  } else {
-    c = aa / rho;
-    s = cscale(a, beta / (aa * rho));
-  }
-  st->cs_c[j] = c;
-  st->cs_s[j] = s;
-  Hc[j] = cadd(cscale(a, c), cscale(s, beta));
-  Hc[j + 1] = make_double2(0.0, 0.0);
-  double2 gj = st->g[j];
-  st->g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));  // -conj(s) g_j
-  st->g[j] = cscale(gj, c);
-  st->k = j + 1;
-  double res = sqrt(cabs2(st->g[j + 1]));
-  if (!isfinite(res) || !isfinite(beta) || !(rho > 0.0))
-    st->done = 2;
-  else if (res <= st->stop_abs || beta == 0.0)
-    st->done = 1;
-}
 
 // ------------------------------------------------------------------ kernels
 // Output scaling of the Arnoldi SpMV.  complex64: FP32 only (no FP64 instruction in the kernel:
@@ -679,21 +505,7 @@ __global__ void __launch_bounds__(kCgsThreads, kCgsBlocksPerSM) k_cgs(T* __restr
 
 // y = H(0:k, 0:k)^{-1} g(0:k), scaled by 1/||V_i|| for the unnormalised basis.  One warp:
 // column-oriented back substitution (lane l keeps the running right-hand side of rows l, l+32).
-__global__ void k_backsolve(GState* st) {
-  const int lane = threadIdx.x;
-  const int kk = st->k;
-  double2 rhs0 = lane < kk ? st->g[lane] : make_double2(0.0, 0.0);
-  double2 rhs1 = lane + 32 < kk ? st->g[lane + 32] : make_double2(0.0, 0.0);
-  for (int i = kk - 1; i >= 0; --i) {
-    double2 ri = i < 32 ? rhs0 : rhs1;
-    double2 yi = make_double2(__shfl_sync(0xffffffffu, ri.x, i & 31), __shfl_sync(0xffffffffu, ri.y, i & 31));
-    yi = cdiv(yi, st->H[i * (kMaxM + 1) + i]);
-    if (lane == 0) st->y[i] = cscale(yi, st->inv_beta[i]);
-    const double2* Hc = &st->H[i * (kMaxM + 1)];
-    if (lane < i) rhs0 = csub(rhs0, cmul(Hc[lane], yi));
-    if (lane + 32 < i) rhs1 = csub(rhs1, cmul(Hc[lane + 32], yi));
-  }
-}
+__global__ void k_backsolve(GState* st) { backsolve_warp(st, threadIdx.x); }
 
 // u += sum_k V_k y_k.  complex128: in FP64.  complex64: the correction sum_k V_k y_k is formed in
 // FP32 (it is the inner solve's correction, accurate to complex64 anyway) and added to u in FP64.
@@ -780,16 +592,8 @@ __global__ void __launch_bounds__(kT) k_norm2(const double2* __restrict__ b, int
   }
 }
 
-constexpr int kGroup = 4;  // lanes per row in the CSR kernels (rows hold at most ~19 entries)
 
 // ------------------------------------------------------------------ host side
-struct HostState {  // leading fields of GState
-  int m, k, done, refine;
-  unsigned counter;
-  int n_refine, timeout, pad1;
-  double stop_abs, nrm_w, rnorm2, beta0;
-  uint8_t refined[kMaxM];
-};
 
 Status read_state(petgem_ctx* c, HostState* hs) {
   Solver* S = c->solver;
@@ -798,7 +602,9 @@ Status read_state(petgem_ctx* c, HostState* hs) {
   return Status{};
 }
 
-Status prepare(petgem_ctx* c, int m, int prec) {
+// Scaled matrices (once per assembly) and device facts; then, for the single-source driver, its
+// workspaces.  The multi-source driver (block.cu) sizes its own.
+Status prepare(petgem_ctx* c, int m, int prec, bool single) {
   if (!c->solver) c->solver = new Solver();
   Solver* S = c->solver;
   cudaStream_t s = c->stream;
@@ -813,31 +619,32 @@ Status prepare(petgem_ctx* c, int m, int prec) {
     PG_CUDA(cudaGetLastError());
     S->version = c->assembly_version;
   }
-  S->n = n;
-  S->ld = (n + 255) / 256 * 256;  // whole 2 KB slices for the staged Gram-Schmidt kernel
-  S->m = m;
-  S->n_blocks = (n + kRows - 1) / kRows;
-  const size_t vbytes_all = (size_t)(m + 1) * S->ld * sizeof(double2);
-  // The staged Gram-Schmidt kernel reads whole 2 KB slices, so the rows n..ld-1 of every basis
-  // vector must be zero.  Kernels never write them, but complex64 and complex128 vectors place
-  // their padding at different byte offsets: clear the buffer when it grows or the layout changes.
-  const bool fresh = S->V.bytes < vbytes_all || S->prec != prec || S->ld_used != S->ld;
-  PG_TRY(S->V.reserve(vbytes_all));
-  if (fresh) PG_CUDA(cudaMemsetAsync(S->V.ptr, 0, S->V.bytes, s));
-  S->prec = prec;
-  S->ld_used = S->ld;
   if (S->sms == 0) {
     PG_CUDA(cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, c->device));
     for (auto f : {(const void*)k_cgs<float2, 0>, (const void*)k_cgs<float2, 1>, (const void*)k_cgs<float2, 2>,
                    (const void*)k_cgs<double2, 0>, (const void*)k_cgs<double2, 1>, (const void*)k_cgs<double2, 2>})
       PG_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kCgsDynSmem));
   }
+  S->n = n;
+  S->ld = (n + 255) / 256 * 256;  // whole slices for the staged Gram-Schmidt kernel
+  S->m = m;
+  S->n_blocks = (n + kRows - 1) / kRows;
+  if (!single) return Status{};
+  const size_t vbytes_all = (size_t)(m + 1) * S->ld * (prec == PETGEM_PREC_MIXED ? sizeof(float2) : sizeof(double2));
+  // The staged Gram-Schmidt kernel reads whole slices, so the rows n..ld-1 of every basis vector
+  // must be zero.  Kernels never write them, but complex64 and complex128 vectors place their
+  // padding at different byte offsets: clear the buffer when it grows or the layout changes.
+  const bool fresh = S->V.bytes < vbytes_all || S->prec != prec || S->ld_used != S->ld;
+  PG_TRY(S->V.reserve(vbytes_all));
+  if (fresh) PG_CUDA(cudaMemsetAsync(S->V.ptr, 0, S->V.bytes, s));
+  S->prec = prec;
+  S->ld_used = S->ld;
+  // Partials: one row per block of the widest reduction grid (vector kernels: n_blocks; the
+  // persistent Gram-Schmidt kernel: two blocks per SM).
   PG_TRY(S->partials.reserve((size_t)std::max<int64_t>(std::max<int64_t>(S->n_blocks, kCgsBlocksPerSM * S->sms), 1) *
                              kPStride * sizeof(double2)));
   PG_TRY(S->u.reserve(n * sizeof(double2)));
   PG_TRY(S->r.reserve(n * sizeof(double2)));
-  // Partials: one row per block of the widest reduction grid (vector kernels: n_blocks; the
-  // persistent Gram-Schmidt kernel: one block per SM).
   PG_TRY(S->state.reserve(sizeof(GState)));
   PG_CUDA(cudaMemsetAsync(S->state.ptr, 0, sizeof(GState), s));
   return Status{};
@@ -948,7 +755,9 @@ Status run_spmv(petgem_ctx* c, const double2* x, double2* y) {
 Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info) {
   const int m = o.restart;
   if (m < 1 || m > kMaxRestart) return Status{PETGEM_ERR_UNSUPPORTED, "restart must be in [1, 62]"};
-  PG_TRY(prepare(c, m, o.precision));
+  const bool block = o.batch != 1 && c->n_src > 1;
+  PG_TRY(prepare(c, m, o.precision, !block));
+  if (block) return run_solve_block(c, o, x, info);
   Solver* S = c->solver;
   cudaStream_t s = c->stream;
   const int64_t n = c->n_edges;
