@@ -58,7 +58,7 @@ typedef struct {
 } petgem_dipole;
 
 enum { PETGEM_PREC_C128 = 0, PETGEM_PREC_MIXED = 1 };
-enum { PETGEM_PRECOND_JACOBI = 0 };
+enum { PETGEM_PRECOND_JACOBI = 0, PETGEM_PRECOND_LEARNED = 1 };
 
 /* Solver options.  Restarted GMRES(restart), right-preconditioned by Jacobi D = diag(A),
  * x0 taken from the x argument, stopping when ||b - A x||_2 / ||b||_2 <= tol with the
@@ -68,7 +68,12 @@ enum { PETGEM_PRECOND_JACOBI = 0 };
  *     a GMRES cycle on a complex64 copy of the matrix with complex64 Krylov vectors (dot
  *     products summed in FP64 across the vector) until the inner residual falls by
  *     inner_tol or restart steps have run; x and the residual stay complex128.
- *   batch: number of sources iterated together (their SpMVs become one SpMM); 0 = all. */
+ *   batch: number of sources iterated together (their SpMVs become one SpMM); 0 = all (groups
+ *     of up to 32).  batch = 1 solves the sources one after the other.
+ *   precond = PETGEM_PRECOND_LEARNED (single-source solves): flexible GMRES whose
+ *     preconditioner is z = v + s N(v / s) in the Jacobi-scaled variables, N the network of
+ *     petgem_learned_create, s the RMS of v; when a cycle cuts the FP64 residual by less than
+ *     1 %, the solve falls back to Jacobi (info.fell_back). */
 typedef struct {
   int32_t restart;
   int32_t precision;
@@ -95,6 +100,8 @@ typedef struct {
   double true_rel_residual; /* ||b - A x|| / ||b|| in FP64 at exit */
   int32_t status;      /* PETGEM_OK, PETGEM_ERR_NOT_CONVERGED, _BREAKDOWN or _TIMEOUT */
   int32_t reorth;      /* Arnoldi steps that needed a second Gram-Schmidt pass */
+  int32_t fell_back;   /* learned preconditioner: 1 if the solve switched back to Jacobi */
+  int32_t reserved;
 } petgem_solve_info;
 
 /* ----------------------------------------------------------------------- lifecycle */
@@ -170,6 +177,42 @@ int petgem_spmv(petgem_ctx *ctx, const void *x, void *y);
  * whose barycentric coordinates are all >= -1e-12.  Returns PETGEM_ERR_RECEIVER_OUTSIDE when
  * some receiver is in no tet (its nine outputs are NaN). */
 int petgem_receivers(petgem_ctx *ctx, int32_t n_rcv, const double *rx, const void *x, void *out);
+
+/* ----------------------------------------------------------------------- learned preconditioner */
+/* Not in the paper (it solves with GMRES, SQMR and MUMPS, Sections 5.1-5.3).  A 3-D
+ * convolutional network on the node grid of a Kuhn-split lattice of nx x ny x nz cells whose
+ * node ids are i + (nx+1) (j + (ny+1) k): every edge is a step (+x, +y, +z, +xy, +xz, +yz or
+ * +xyz) from its low node, so edge vectors map one-to-one onto 7 grid channels (x Re, Im).  Four
+ * levels (the node grid and three 2x poolings), seven 3x3x3 convolutions (16/32 channels, BF16
+ * operands on the tensor cores, FP32 accumulation and FP32 master weights), ReLU, skip additions.
+ * Input: the residual (16 channels with two conductivity features); output: the correction added
+ * to the Jacobi step.
+ * petgem_learned_create: after petgem_mesh_edges on such a lattice; keeps the parameters when
+ *   called again for another mesh (the network is fully convolutional).  PETGEM_ERR_UNSUPPORTED
+ *   if some edge is not a lattice step.
+ * petgem_learned_params: host float[n] in (set) / out (get, and grad = the gradient accumulated by
+ *   the last train step, scaled by 1 / n_samples); NULL to skip; *n_params receives the count.
+ * petgem_learned_train_step: one Adam step (lr) on the mean squared error of n_samples pairs
+ *   (residual, correction) of the assembled system (source 0): x_iters device complex128
+ *   [n_samples][E] are iterates, x_star device complex128[E] the converged solution; the target
+ *   of iterate x is D (x* - x) - r with r = b - A x, both scaled by 1 / RMS(r).  *loss: host.
+ * petgem_learned_apply: z = r + s N(r / s) for one device complex128 vector r of E entries. */
+int petgem_learned_create(petgem_ctx *ctx, int32_t nx, int32_t ny, int32_t nz);
+int petgem_learned_params(petgem_ctx *ctx, const float *set, float *get, float *grad, int64_t *n_params);
+int petgem_learned_train_step(petgem_ctx *ctx, int32_t n_samples, const void *x_iters, const void *x_star,
+                              float lr, double *loss);
+int petgem_learned_apply(petgem_ctx *ctx, const void *r, void *z);
+
+/* The network's tensor-core kernels as plain functions (test and diagnostic entry points):
+ * grids are gx x gy x gz voxels (v = x + gx (y + gy z)), activations BF16 [V][C], weights BF16
+ * [27][cout][cin] with tap t = (dx+1) + 3 (dy+1) + 9 (dz+1), zero "same" padding; cin, cout in
+ * {16, 32}.  petgem_nn_conv3d: y[v][co] = bias[co] + sum_t,ci W[t][co][ci] x[v + d_t][ci], ReLU
+ * when relu != 0, y BF16 (y_fp32 = 0) or FP32 [V][cout].  petgem_nn_conv3d_wgrad: dw[t][co][ci] =
+ * sum_v dy[v][co] x[v + d_t][ci] (FP32).  All pointers device; work ordered on `stream`. */
+int petgem_nn_conv3d(void *stream, int32_t gx, int32_t gy, int32_t gz, int32_t cin, int32_t cout, const void *x,
+                     const void *w, const float *bias, int32_t relu, void *y, int32_t y_fp32);
+int petgem_nn_conv3d_wgrad(void *stream, int32_t gx, int32_t gy, int32_t gz, int32_t cin, int32_t cout, const void *x,
+                           const void *dy, float *dw);
 
 /* ----------------------------------------------------------------------- measurement */
 /* Per-kernel device time recorded with CUDA events around launches while enabled.

@@ -1,0 +1,203 @@
+"""FP64 CPU oracle of the learned preconditioner's network and of its grid maps.
+
+TEST INFRASTRUCTURE (like the rest of oracle/): used only by tests/ and the benchmark's CPU
+legs.  The paper has no learned part; what this file fixes is the design the CUDA library
+implements, written plainly so that its kernels can be checked element by element, and pinned
+by finite differences (tests/test_oracle_learned.py).
+
+Conventions shared with the CUDA kernels (by definition, not by code):
+  * grid tensors are numpy arrays [Z, Y, X, C], so the flat voxel index is v = x + X (y + Y z)
+    (the node numbering of the Kuhn lattice) with the channels innermost;
+  * a 3x3x3 convolution with zero "same" padding has weights W[t][co][ci], tap
+    t = (dx + 1) + 3 (dy + 1) + 9 (dz + 1), and bias b[co]:
+        y[v][co] = b[co] + sum_t sum_ci W[t][co][ci] x[v + (dx, dy, dz)][ci];
+  * pooling averages the (up to 8) fine voxels 2 c + {0, 1} of a coarse voxel c that exist
+    (coarse size ceil(G / 2)); upsampling copies a coarse voxel to its fine children.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+OFFS = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]  # tap order t
+
+
+def shift(x: np.ndarray, d) -> np.ndarray:
+    """x[v + d] for d = (dx, dy, dz), zeros outside the grid; x is [Z, Y, X, C]."""
+    out = np.zeros_like(x)
+    sl_dst, sl_src = [], []
+    for a, n in zip((d[2], d[1], d[0]), x.shape[:3]):
+        if a >= 0:
+            sl_dst.append(slice(0, n - a))
+            sl_src.append(slice(a, n))
+        else:
+            sl_dst.append(slice(-a, n))
+            sl_src.append(slice(0, n + a))
+    out[tuple(sl_dst)] = x[tuple(sl_src)]
+    return out
+
+
+def conv3d(x: np.ndarray, W: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """x [Z,Y,X,Cin], W [27, Cout, Cin], b [Cout] -> [Z,Y,X,Cout]."""
+    y = np.zeros(x.shape[:3] + (W.shape[1],)) + b
+    for t, d in enumerate(OFFS):
+        y += shift(x, d) @ W[t].T
+    return y
+
+
+def conv3d_backward(x: np.ndarray, W: np.ndarray, dy: np.ndarray):
+    """Gradients of sum(dy * conv3d(x, W, b)) w.r.t. x, W and b."""
+    dx = np.zeros_like(x, dtype=np.float64)
+    dW = np.zeros_like(W, dtype=np.float64)
+    for t, d in enumerate(OFFS):
+        xs = shift(x, d)
+        dW[t] = np.einsum("zyxo,zyxi->oi", dy, xs)
+        dx += shift(dy @ W[t], tuple(-a for a in d))
+    db = dy.sum(axis=(0, 1, 2))
+    return dx, dW, db
+
+
+def pool(x: np.ndarray) -> np.ndarray:
+    X, Y, Z, C = x.shape  # (axis sizes; the averaging is the same along every axis)
+    cX, cY, cZ = (X + 1) // 2, (Y + 1) // 2, (Z + 1) // 2
+    s = np.zeros((cX, cY, cZ, C))
+    n = np.zeros((cX, cY, cZ, 1))
+    for ox in (0, 1):
+        for oy in (0, 1):
+            for oz in (0, 1):
+                part = x[ox::2, oy::2, oz::2]
+                s[:part.shape[0], :part.shape[1], :part.shape[2]] += part
+                n[:part.shape[0], :part.shape[1], :part.shape[2]] += 1
+    return s / n
+
+
+def pool_backward(dy: np.ndarray, fine_shape) -> np.ndarray:
+    X, Y, Z, C = fine_shape
+    cX, cY, cZ = dy.shape[:3]
+    n = np.zeros((cX, cY, cZ, 1))
+    for ox in (0, 1):
+        for oy in (0, 1):
+            for oz in (0, 1):
+                n[:len(range(ox, X, 2)), :len(range(oy, Y, 2)), :len(range(oz, Z, 2))] += 1
+    g = dy / n
+    dx = np.zeros(fine_shape)
+    for ox in (0, 1):
+        for oy in (0, 1):
+            for oz in (0, 1):
+                tgt = dx[ox::2, oy::2, oz::2]
+                tgt += g[:tgt.shape[0], :tgt.shape[1], :tgt.shape[2]]
+    return dx
+
+
+def upsample(x: np.ndarray, fine_shape) -> np.ndarray:
+    X, Y, Z = fine_shape[:3]
+    out = np.repeat(np.repeat(np.repeat(x, 2, 0), 2, 1), 2, 2)
+    return out[:X, :Y, :Z]
+
+
+def upsample_backward(dy: np.ndarray, coarse_shape) -> np.ndarray:
+    dx = np.zeros(coarse_shape)
+    X, Y, Z = dy.shape[:3]
+    for ox in (0, 1):
+        for oy in (0, 1):
+            for oz in (0, 1):
+                part = dy[ox::2, oy::2, oz::2]
+                dx[:part.shape[0], :part.shape[1], :part.shape[2]] += part
+    return dx
+
+
+# ---------------------------------------------------------------- the network
+# name: (in channels, out channels, relu).  Level 0 is the (N+1)^3 node grid, levels 1..3 are
+# successive poolings.  Decoder levels add the upsampled coarse features to the encoder's.
+LAYERS = [("c1", 16, 16, True), ("c2", 16, 32, True), ("c3", 32, 32, True), ("c4", 32, 32, True),
+          ("c5", 32, 32, True), ("c6", 32, 16, True), ("c7", 16, 16, False)]
+N_IN, N_OUT = 16, 14
+
+
+def init_params(seed: int = 0, scale: float = 1.0) -> dict:
+    rng = np.random.default_rng(seed)
+    p = {}
+    for name, ci, co, _ in LAYERS:
+        std = scale * np.sqrt(2.0 / (27 * ci))
+        p[name + ".W"] = rng.normal(size=(27, co, ci)) * std
+        p[name + ".b"] = rng.normal(size=co) * 0.01
+    p["c7.W"][:, N_OUT:, :] = 0.0   # output channels 14, 15 are padding
+    p["c7.b"][N_OUT:] = 0.0
+    return p
+
+
+def forward(p: dict, x: np.ndarray):
+    """x [Z,Y,X,16] -> (y [Z,Y,X,16], cache).  Channels 14, 15 of y are zero."""
+    relu = lambda a: np.maximum(a, 0.0)
+    a1 = relu(conv3d(x, p["c1.W"], p["c1.b"]))
+    p1 = pool(a1)
+    a2 = relu(conv3d(p1, p["c2.W"], p["c2.b"]))
+    p2 = pool(a2)
+    a3 = relu(conv3d(p2, p["c3.W"], p["c3.b"]))
+    p3 = pool(a3)
+    a4 = relu(conv3d(p3, p["c4.W"], p["c4.b"]))
+    s5 = upsample(a4, a3.shape) + a3
+    a5 = relu(conv3d(s5, p["c5.W"], p["c5.b"]))
+    s6 = upsample(a5, a2.shape) + a2
+    a6 = relu(conv3d(s6, p["c6.W"], p["c6.b"]))
+    s7 = upsample(a6, a1.shape) + a1
+    y = conv3d(s7, p["c7.W"], p["c7.b"])
+    cache = dict(x=x, a1=a1, p1=p1, a2=a2, p2=p2, a3=a3, p3=p3, a4=a4, s5=s5, a5=a5, s6=s6, a6=a6, s7=s7)
+    return y, cache
+
+
+def backward(p: dict, cache: dict, dy: np.ndarray) -> dict:
+    """Gradients of sum(dy * forward(p, x)) with respect to every parameter."""
+    c = cache
+    g = {}
+    ds7, g["c7.W"], g["c7.b"] = conv3d_backward(c["s7"], p["c7.W"], dy)
+    da1 = ds7.copy()
+    da6 = upsample_backward(ds7, c["a6"].shape)
+    dz6 = da6 * (c["a6"] > 0)
+    ds6, g["c6.W"], g["c6.b"] = conv3d_backward(c["s6"], p["c6.W"], dz6)
+    da2 = ds6.copy()
+    da5 = upsample_backward(ds6, c["a5"].shape)
+    dz5 = da5 * (c["a5"] > 0)
+    ds5, g["c5.W"], g["c5.b"] = conv3d_backward(c["s5"], p["c5.W"], dz5)
+    da3 = ds5.copy()
+    da4 = upsample_backward(ds5, c["a4"].shape)
+    dz4 = da4 * (c["a4"] > 0)
+    dp3, g["c4.W"], g["c4.b"] = conv3d_backward(c["p3"], p["c4.W"], dz4)
+    da3 += pool_backward(dp3, c["a3"].shape)
+    dz3 = da3 * (c["a3"] > 0)
+    dp2, g["c3.W"], g["c3.b"] = conv3d_backward(c["p2"], p["c3.W"], dz3)
+    da2 += pool_backward(dp2, c["a2"].shape)
+    dz2 = da2 * (c["a2"] > 0)
+    dp1, g["c2.W"], g["c2.b"] = conv3d_backward(c["p1"], p["c2.W"], dz2)
+    da1 += pool_backward(dp1, c["a1"].shape)
+    dz1 = da1 * (c["a1"] > 0)
+    _, g["c1.W"], g["c1.b"] = conv3d_backward(c["x"], p["c1.W"], dz1)
+    return g
+
+
+def loss(p: dict, x: np.ndarray, target: np.ndarray):
+    """Mean squared error over the 14 output channels: 0.5 * mean((y - t)^2); returns (L, dL/dy)."""
+    y, cache = forward(p, x)
+    diff = np.zeros_like(y)
+    diff[..., :N_OUT] = y[..., :N_OUT] - target[..., :N_OUT]
+    cnt = np.prod(y.shape[:3]) * N_OUT
+    return 0.5 * float((diff ** 2).sum()) / cnt, diff / cnt, cache
+
+
+# ---------------------------------------------------------------- edge <-> grid
+# Edge classes of a Kuhn-split lattice, by the step from the edge's low node to its high node.
+CLASSES = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1), (1, 1, 1)]
+
+
+def edge_grid_index(edges: np.ndarray, n: int) -> np.ndarray:
+    """Grid slot (voxel * 7 + class) of every edge (low, high) of a Kuhn lattice with n cells a side
+    and node id i + (n+1) (j + (n+1) k); -1 if the edge is not a lattice step."""
+    s = n + 1
+    lo, hi = edges[:, 0].astype(np.int64), edges[:, 1].astype(np.int64)
+    li, lj, lk = lo % s, (lo // s) % s, lo // (s * s)
+    hi_i, hi_j, hi_k = hi % s, (hi // s) % s, hi // (s * s)
+    d = np.stack([hi_i - li, hi_j - lj, hi_k - lk], axis=1)
+    out = np.full(edges.shape[0], -1, np.int64)
+    for c, step in enumerate(CLASSES):
+        m = np.all(d == np.array(step), axis=1)
+        out[m] = lo[m] * 7 + c
+    return out

@@ -23,6 +23,7 @@ OK, ERR_INVALID_ARG, ERR_BAD_MESH, ERR_DEGENERATE_TET, ERR_OUT_OF_MEMORY, ERR_CU
     ERR_BREAKDOWN, ERR_RECEIVER_OUTSIDE, ERR_UNSUPPORTED, ERR_TIMEOUT = range(11)
 PREC_C128, PREC_MIXED = 0, 1
 ORTH_CGS2, ORTH_CGS, ORTH_CGS_IFNEEDED = 0, 1, 2
+PRECOND_JACOBI, PRECOND_LEARNED = 0, 1
 
 
 class petgem_dipole(ctypes.Structure):
@@ -38,7 +39,8 @@ class petgem_solve_opts(ctypes.Structure):
 
 class petgem_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("restarts", ctypes.c_int64), ("refinements", ctypes.c_int64),
-                ("true_rel_residual", ctypes.c_double), ("status", ctypes.c_int32), ("reorth", ctypes.c_int32)]
+                ("true_rel_residual", ctypes.c_double), ("status", ctypes.c_int32), ("reorth", ctypes.c_int32),
+                ("fell_back", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _P, _I64, _I32, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
@@ -59,6 +61,12 @@ _SIGNATURES = {
     "petgem_kernel_stats": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.POINTER(_I64), ctypes.POINTER(_D),
                                            ctypes.POINTER(_D)]),
     "petgem_launch_count": (_I64, [_P]),
+    "petgem_learned_create": (ctypes.c_int, [_P, _I32, _I32, _I32]),
+    "petgem_learned_params": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(_I64)]),
+    "petgem_learned_train_step": (ctypes.c_int, [_P, _I32, _P, _P, ctypes.c_float, ctypes.POINTER(_D)]),
+    "petgem_learned_apply": (ctypes.c_int, [_P, _P, _P]),
+    "petgem_nn_conv3d": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _P, _P, _I32, _P, _I32]),
+    "petgem_nn_conv3d_wgrad": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _P, _P]),
 }
 
 _lib = None
@@ -154,8 +162,8 @@ def petgem_get_elements(ctx, K21=None, M21=None, vol=None):
 
 
 def solve_opts(restart=50, precision=PREC_C128, tol=1e-8, inner_tol=1e-4, max_iters=200000, batch=1,
-               orth=ORTH_CGS, use_graphs=0) -> petgem_solve_opts:
-    return petgem_solve_opts(restart, precision, 0, batch, tol, inner_tol, max_iters, orth, use_graphs)
+               orth=ORTH_CGS, use_graphs=0, precond=PRECOND_JACOBI) -> petgem_solve_opts:
+    return petgem_solve_opts(restart, precision, precond, batch, tol, inner_tol, max_iters, orth, use_graphs)
 
 
 def petgem_solve(ctx, x, n_src, opts=None, allow_not_converged=False):
@@ -164,7 +172,8 @@ def petgem_solve(ctx, x, n_src, opts=None, allow_not_converged=False):
     allowed = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
     st = _check(ctx, load().petgem_solve(ctx, ctypes.byref(o), _ptr(x), info), allowed)
     return st, [dict(iters=i.iters, restarts=i.restarts, refinements=i.refinements,
-                     true_rel_residual=i.true_rel_residual, status=i.status, reorth=i.reorth) for i in info]
+                     true_rel_residual=i.true_rel_residual, status=i.status, reorth=i.reorth,
+                     fell_back=i.fell_back) for i in info]
 
 
 def petgem_spmv(ctx, x, y):
@@ -184,6 +193,58 @@ def petgem_kernel_stats(ctx, name: str):
     n, ms, by = _I64(0), _D(0.0), _D(0.0)
     _check(ctx, load().petgem_kernel_stats(ctx, name.encode(), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
     return n.value, ms.value, by.value
+
+
+def petgem_learned_create(ctx, nx, ny, nz):
+    _check(ctx, load().petgem_learned_create(ctx, nx, ny, nz))
+
+
+def petgem_learned_params(ctx, set_params=None, get=False, grad=False):
+    """Set (host float32 array) and/or get the network parameters (and the last mean gradient).
+    Returns the parameter count, or the requested arrays."""
+    n = _I64(0)
+    _check(ctx, load().petgem_learned_params(ctx, None, None, None, ctypes.byref(n)))
+    src = None
+    if set_params is not None:
+        src = np.ascontiguousarray(set_params, dtype=np.float32)
+        if src.size != n.value:
+            raise ValueError("expected %d parameters" % n.value)
+    out = np.zeros(n.value, np.float32) if get else None
+    gout = np.zeros(n.value, np.float32) if grad else None
+    _check(ctx, load().petgem_learned_params(ctx, None if src is None else src.ctypes.data,
+                                             None if out is None else out.ctypes.data,
+                                             None if gout is None else gout.ctypes.data, ctypes.byref(n)))
+    if get and grad:
+        return out, gout
+    if get:
+        return out
+    if grad:
+        return gout
+    return n.value
+
+
+def petgem_learned_train_step(ctx, x_iters, x_star, lr) -> float:
+    loss = _D(0.0)
+    _check(ctx, load().petgem_learned_train_step(ctx, x_iters.shape[0], _ptr(x_iters), _ptr(x_star),
+                                                  ctypes.c_float(lr), ctypes.byref(loss)))
+    return loss.value
+
+
+def petgem_learned_apply(ctx, r, z):
+    _check(ctx, load().petgem_learned_apply(ctx, _ptr(r), _ptr(z)))
+
+
+def petgem_nn_conv3d(stream, grid, cin, cout, x, w, bias, relu, y, y_fp32):
+    st = load().petgem_nn_conv3d(stream, grid[0], grid[1], grid[2], cin, cout, _ptr(x), _ptr(w), _ptr(bias),
+                                 1 if relu else 0, _ptr(y), 1 if y_fp32 else 0)
+    if st != OK:
+        raise PetgemError(st, "petgem_nn_conv3d")
+
+
+def petgem_nn_conv3d_wgrad(stream, grid, cin, cout, x, dy, dw):
+    st = load().petgem_nn_conv3d_wgrad(stream, grid[0], grid[1], grid[2], cin, cout, _ptr(x), _ptr(dy), _ptr(dw))
+    if st != OK:
+        raise PetgemError(st, "petgem_nn_conv3d_wgrad")
 
 
 def petgem_launch_count(ctx) -> int:

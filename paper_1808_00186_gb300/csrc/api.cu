@@ -7,6 +7,7 @@
 #include <new>
 
 #include "ctx.cuh"
+#include "learned.cuh"
 
 namespace petgem {
 
@@ -91,6 +92,12 @@ Status set_device(petgem_ctx* c) {
   return Status{};
 }
 
+#define PG_CUDA_S(st, call)                                                            \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) st = Status{PETGEM_ERR_CUDA, cudaGetErrorString(e_)};       \
+  } while (0)
+
 }  // namespace
 
 extern "C" {
@@ -122,6 +129,9 @@ int petgem_destroy(petgem_ctx* c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   petgem::destroy_solver(c);
+  delete c->net;
+  c->net = nullptr;
+  c->slots.release();
   for (petgem::DevBuf* b : {&c->nodes, &c->tets, &c->edges, &c->tet_edges, &c->signs, &c->boundary, &c->occ, &c->eptr,
                             &c->row_ptr, &c->col, &c->gptr, &c->pkey, &c->pij, &c->flags, &c->sigma, &c->K21, &c->M21,
                             &c->vol, &c->val, &c->diag, &c->b})
@@ -164,6 +174,7 @@ int petgem_mesh_edges(petgem_ctx* c, int64_t n_nodes, const double* nodes, int64
   Status s = set_device(c);
   if (!s.ok()) return finish(c, s);
   c->assembled = false;
+  c->slots_ready = false;  // the learned preconditioner's edge map belongs to the previous mesh
   c->n_nodes = n_nodes;
   c->n_tets = n_tets;
   s = c->nodes.reserve(3 * n_nodes * sizeof(double));
@@ -269,9 +280,12 @@ int petgem_solve(petgem_ctx* c, const petgem_solve_opts* opts, void* x, petgem_s
   o.use_graphs = 0;
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_iters < 0 || (o.precision != PETGEM_PREC_C128 && o.precision != PETGEM_PREC_MIXED) ||
-      o.precond != PETGEM_PRECOND_JACOBI || !(o.inner_tol >= 0.0 && o.inner_tol < 1.0) || o.orth < 0 ||
+      (o.precond != PETGEM_PRECOND_JACOBI && o.precond != PETGEM_PRECOND_LEARNED) ||
+      !(o.inner_tol >= 0.0 && o.inner_tol < 1.0) || o.orth < 0 ||
       o.orth > PETGEM_ORTH_CGS_IFNEEDED)
     return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve: bad options"});
+  if (o.precond == PETGEM_PRECOND_LEARNED && (!c->net || !c->slots_ready))
+    return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve: learned preconditioner needs petgem_learned_create"});
   Status s = set_device(c);
   if (s.ok()) s = petgem::run_solve(c, o, static_cast<double2*>(x), info);
   if (s.code == PETGEM_ERR_CUDA || s.code == PETGEM_ERR_OUT_OF_MEMORY) cudaGetLastError();
@@ -295,6 +309,168 @@ int petgem_receivers(petgem_ctx* c, int32_t n_rcv, const double* rx, const void*
   if (s.ok()) s = petgem::run_receivers(c, n_rcv, rx, static_cast<const double2*>(x), static_cast<double2*>(out), &outside);
   if (s.ok() && outside) s = Status{PETGEM_ERR_RECEIVER_OUTSIDE, "petgem_receivers: a receiver lies in no tet"};
   return finish(c, s);
+}
+
+int petgem_learned_create(petgem_ctx* c, int32_t nx, int32_t ny, int32_t nz) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (c->n_edges == 0 || nx < 1 || ny < 1 || nz < 1 ||
+      (int64_t)(nx + 1) * (ny + 1) * (nz + 1) != c->n_nodes || (int64_t)6 * nx * ny * nz != c->n_tets)
+    return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_learned_create: mesh must be an (nx+1)(ny+1)(nz+1)-node lattice"});
+  Status s = set_device(c);
+  if (!s.ok()) return finish(c, s);
+  if (!c->net) c->net = new petgem::nn::Net();
+  if (!c->net->ready || c->net->nx != nx || c->net->ny != ny || c->net->nz != nz) {
+    // new grid size: reallocate the activations, keep the parameters
+    std::vector<float> keep;
+    if (c->net->ready) {
+      keep.resize(c->net->n_params);
+      cudaMemcpy(keep.data(), c->net->params.ptr, keep.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    }
+    s = c->net->init(c, nx, ny, nz);
+    if (s.ok() && !keep.empty())
+      if (cudaMemcpyAsync(c->net->params.ptr, keep.data(), keep.size() * sizeof(float), cudaMemcpyHostToDevice,
+                          c->stream) != cudaSuccess)
+        s = Status{PETGEM_ERR_CUDA, "petgem_learned_create: parameter copy failed"};
+    if (s.ok()) s = c->net->pack_weights(c->stream);
+    if (s.ok() && keep.empty()) cudaStreamSynchronize(c->stream);
+  }
+  if (s.ok()) s = c->slots.reserve(c->n_edges * sizeof(int32_t));
+  if (s.ok()) {
+    PG_CUDA_S(s, cudaMemsetAsync(c->net->err.ptr, 0, sizeof(int), c->stream));
+    if (s.ok())
+      s = petgem::nn::edge_slots(c->stream, c->edges.as<int32_t>(), c->n_edges, nx + 1, ny + 1, nz + 1,
+                                 c->slots.as<int32_t>(), c->net->err.as<int>());
+    int bad = 0;
+    if (s.ok() && (cudaMemcpyAsync(&bad, c->net->err.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+                   cudaStreamSynchronize(c->stream) != cudaSuccess))
+      s = Status{PETGEM_ERR_CUDA, "petgem_learned_create: CUDA error"};
+    if (s.ok() && bad) s = Status{PETGEM_ERR_UNSUPPORTED, "petgem_learned_create: an edge is not a lattice step"};
+    cudaMemsetAsync(c->net->err.ptr, 0, sizeof(int), c->stream);
+  }
+  if (s.ok()) {  // lattice spacing from the first cell's corner nodes
+    double p0[3], px[3], py[3], pz[3];
+    const double* nd = c->nodes.as<double>();
+    cudaMemcpy(p0, nd, 24, cudaMemcpyDeviceToHost);
+    cudaMemcpy(px, nd + 3 * 1, 24, cudaMemcpyDeviceToHost);
+    cudaMemcpy(py, nd + 3 * (int64_t)(nx + 1), 24, cudaMemcpyDeviceToHost);
+    cudaMemcpy(pz, nd + 3 * (int64_t)(nx + 1) * (ny + 1), 24, cudaMemcpyDeviceToHost);
+    const double hx = fabs(px[0] - p0[0]), hy = fabs(py[1] - p0[1]), hz = fabs(pz[2] - p0[2]);
+    c->lattice_h = cbrt(hx * hy * hz);
+  }
+  c->slots_ready = s.ok();
+  return finish(c, s);
+}
+
+int petgem_learned_params(petgem_ctx* c, const float* set, float* get, float* grad, int64_t* n_params) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (!c->net || !c->net->ready) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_learned_params: no network"});
+  petgem::nn::Net* N = c->net;
+  Status s = set_device(c);
+  if (n_params) *n_params = N->n_params;
+  if (s.ok() && set) {
+    if (cudaMemcpy(N->params.ptr, set, N->n_params * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      s = Status{PETGEM_ERR_CUDA, "petgem_learned_params: copy failed"};
+    if (s.ok()) s = N->pack_weights(c->stream);
+    N->adam_t = 0;
+    cudaMemsetAsync(N->adam_m.ptr, 0, N->n_params * sizeof(float), c->stream);
+    cudaMemsetAsync(N->adam_v.ptr, 0, N->n_params * sizeof(float), c->stream);
+  }
+  if (s.ok() && get) {
+    if (cudaMemcpyAsync(get, N->params.ptr, N->n_params * sizeof(float), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      s = Status{PETGEM_ERR_CUDA, "petgem_learned_params: copy failed"};
+  }
+  if (s.ok() && grad) {
+    if (cudaMemcpyAsync(grad, N->grads.ptr, N->n_params * sizeof(float), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      s = Status{PETGEM_ERR_CUDA, "petgem_learned_params: copy failed"};
+  }
+  return finish(c, s);
+}
+
+int petgem_learned_train_step(petgem_ctx* c, int32_t n_samples, const void* x_iters, const void* x_star, float lr,
+                              double* loss) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (!c->net || !c->slots_ready || !c->assembled || n_samples < 1 || !x_iters || !x_star || !(lr > 0.f))
+    return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_learned_train_step: bad arguments or state"});
+  petgem::nn::Net* N = c->net;
+  cudaStream_t st = c->stream;
+  const int64_t E = c->n_edges;
+  Status s = set_device(c);
+  if (s.ok()) s = N->rtmp.reserve(E * sizeof(double2));
+  if (s.ok()) s = N->dutmp.reserve(E * sizeof(double2));
+  if (s.ok()) s = N->features(st, c->sigma.as<double>(), c->sigma_p, c->omega, c->lattice_h);
+  if (s.ok() && cudaMemsetAsync(N->loss_acc.ptr, 0, sizeof(double), st) != cudaSuccess)
+    s = Status{PETGEM_ERR_CUDA, "memset"};
+  for (int32_t i = 0; i < n_samples && s.ok(); ++i) {
+    const double2* xi = static_cast<const double2*>(x_iters) + (int64_t)i * E;
+    s = petgem::nn::residual_and_error(c, xi, static_cast<const double2*>(x_star), N->rtmp.as<double2>(),
+                                       N->dutmp.as<double2>());
+    if (s.ok())
+      s = N->sample_grad(st, N->rtmp.as<double2>(), N->dutmp.as<double2>(), c->slots.as<int32_t>(), E, i > 0);
+    c->launches += 60;
+  }
+  if (s.ok()) s = N->adam_step(st, lr, 1.f / (float)n_samples);
+  if (s.ok()) s = petgem::nn::check_err(st, N->err.as<int>(), "petgem_learned_train_step");
+  double l = 0.0;
+  if (s.ok() && (cudaMemcpyAsync(&l, N->loss_acc.ptr, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                 cudaStreamSynchronize(st) != cudaSuccess))
+    s = Status{PETGEM_ERR_CUDA, "petgem_learned_train_step: CUDA error"};
+  if (loss) *loss = l / n_samples;
+  return finish(c, s);
+}
+
+int petgem_learned_apply(petgem_ctx* c, const void* r, void* z) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (!c->net || !c->slots_ready || !c->assembled || !r || !z)
+    return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_learned_apply: bad arguments or state"});
+  petgem::nn::Net* N = c->net;
+  Status s = set_device(c);
+  if (s.ok()) s = N->features(c->stream, c->sigma.as<double>(), c->sigma_p, c->omega, c->lattice_h);
+  if (s.ok())
+    s = N->apply<double2>(c->stream, static_cast<const double2*>(r), c->slots.as<int32_t>(), c->n_edges,
+                          static_cast<double2*>(z));
+  c->launches += 20;
+  if (s.ok()) s = petgem::nn::check_err(c->stream, N->err.as<int>(), "petgem_learned_apply");
+  return finish(c, s);
+}
+
+int petgem_nn_conv3d(void* stream, int32_t gx, int32_t gy, int32_t gz, int32_t cin, int32_t cout, const void* x,
+                     const void* w, const float* bias, int32_t relu, void* y, int32_t y_fp32) {
+  if (gx < 1 || gy < 1 || gz < 1 || !x || !w || !bias || !y) return PETGEM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* err = nullptr;
+  if (cudaMallocAsync((void**)&err, sizeof(int), s) != cudaSuccess) return PETGEM_ERR_OUT_OF_MEMORY;
+  cudaMemsetAsync(err, 0, sizeof(int), s);
+  Status st = petgem::nn::conv3d(s, gx, gy, gz, cin, cout, static_cast<const __nv_bfloat16*>(x),
+                                 static_cast<const __nv_bfloat16*>(w), bias, relu != 0,
+                                 y_fp32 ? nullptr : static_cast<__nv_bfloat16*>(y),
+                                 y_fp32 ? static_cast<float*>(y) : nullptr, err);
+  if (st.ok()) st = petgem::nn::check_err(s, err, "petgem_nn_conv3d");
+  cudaFreeAsync(err, s);
+  return st.code;
+}
+
+int petgem_nn_conv3d_wgrad(void* stream, int32_t gx, int32_t gy, int32_t gz, int32_t cin, int32_t cout, const void* x,
+                           const void* dy, float* dw) {
+  if (gx < 1 || gy < 1 || gz < 1 || !x || !dy || !dw) return PETGEM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t V = (int64_t)gx * gy * gz;
+  const int splits = petgem::nn::wgrad_splits(V);
+  int* err = nullptr;
+  float* part = nullptr;
+  if (cudaMallocAsync((void**)&err, sizeof(int), s) != cudaSuccess) return PETGEM_ERR_OUT_OF_MEMORY;
+  if (cudaMallocAsync((void**)&part, (size_t)splits * 27 * 32 * 32 * sizeof(float), s) != cudaSuccess) {
+    cudaFreeAsync(err, s);
+    return PETGEM_ERR_OUT_OF_MEMORY;
+  }
+  cudaMemsetAsync(err, 0, sizeof(int), s);
+  Status st = petgem::nn::conv3d_wgrad(s, gx, gy, gz, cin, cout, static_cast<const __nv_bfloat16*>(x),
+                                       static_cast<const __nv_bfloat16*>(dy), part, splits, dw, false, err);
+  if (st.ok()) st = petgem::nn::check_err(s, err, "petgem_nn_conv3d_wgrad");
+  cudaFreeAsync(part, s);
+  cudaFreeAsync(err, s);
+  return st.code;
 }
 
 int petgem_profile(petgem_ctx* c, int enable) {

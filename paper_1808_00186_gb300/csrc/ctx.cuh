@@ -50,6 +50,9 @@ struct PendingTiming {
 };
 
 struct Solver;  // Krylov workspaces (krylov.cu)
+namespace nn {
+struct Net;  // learned preconditioner (learned.cu)
+}
 
 }  // namespace petgem
 
@@ -78,6 +81,12 @@ struct petgem_ctx {
 
   // ---- solver state (krylov.cu)
   petgem::Solver* solver = nullptr;
+
+  // ---- learned preconditioner (learned.cu): network, edge -> grid slots of the current mesh
+  petgem::nn::Net* net = nullptr;
+  petgem::DevBuf slots;
+  bool slots_ready = false;
+  double lattice_h = 0.0;
 
   // ---- profiling
   bool profiling = false;

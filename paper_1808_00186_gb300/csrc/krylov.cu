@@ -22,6 +22,7 @@
 #include <algorithm>
 
 #include "krylov.cuh"
+#include "learned.cuh"
 
 namespace petgem {
 
@@ -651,7 +652,8 @@ Status prepare(petgem_ctx* c, int m, int prec, bool single) {
 }
 
 template <typename T>
-Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, double inner_rel, HostState* hs) {
+Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, double inner_rel, bool learned,
+                 HostState* hs) {
   Solver* S = c->solver;
   cudaStream_t s = c->stream;
   const int64_t n = S->n, ld = S->ld;
@@ -669,12 +671,22 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
   }
   const double spmv_bytes = (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 2.0 * vbytes;
   const unsigned spmv_blocks = blocks_for(n * kGroup, 256);
+  // Flexible GMRES with the learned preconditioner: z_j = N-corrected v_j, stored in Z, and the
+  // solution update uses Z instead of V.
+  T* Z = learned ? S->Z.as<T>() : nullptr;
   for (int j = 0; j < m; ++j) {
     T* vj = V + (int64_t)j * ld;
     T* vn = vj + ld;
+    const T* xin = vj;
+    if (learned) {
+      KernelTimer kt(c, "learned_apply", 0.0, j, 0);
+      PG_TRY(c->net->apply<T>(s, vj, c->slots.as<int32_t>(), n, Z + (int64_t)j * ld));
+      xin = Z + (int64_t)j * ld;
+      c->launches += 20;
+    }
     {
       KernelTimer kt(c, c128 ? "spmv_c128" : "spmv_c64", spmv_bytes, j, 0);
-      k_spmv_arnoldi<T, kGroup><<<spmv_blocks, 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), ahat, vj,
+      k_spmv_arnoldi<T, kGroup><<<spmv_blocks, 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), ahat, xin,
                                                             vn, n, st, j);
     }
     const int nv = j + 2;
@@ -718,7 +730,7 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
   k_backsolve<<<1, 32, 0, s>>>(st);
   {
     KernelTimer kt(c, c128 ? "xupdate_c128" : "xupdate_c64", 32.0 * n + (double)m * vbytes);
-    k_xupdate<T><<<blocks_for(n, kT), kT, 0, s>>>(V, ld, n, S->u.as<double2>(), st);
+    k_xupdate<T><<<blocks_for(n, kT), kT, 0, s>>>(learned ? Z : V, ld, n, S->u.as<double2>(), st);
   }
   c->launches += 2;
   PG_CUDA(cudaGetLastError());
@@ -755,7 +767,7 @@ Status run_spmv(petgem_ctx* c, const double2* x, double2* y) {
 Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info) {
   const int m = o.restart;
   if (m < 1 || m > kMaxRestart) return Status{PETGEM_ERR_UNSUPPORTED, "restart must be in [1, 62]"};
-  const bool block = o.batch != 1 && c->n_src > 1;
+  const bool block = o.batch != 1 && c->n_src > 1 && o.precond != PETGEM_PRECOND_LEARNED;
   PG_TRY(prepare(c, m, o.precision, !block));
   if (block) return run_solve_block(c, o, x, info);
   Solver* S = c->solver;
@@ -785,7 +797,13 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
     c->launches++;
     int64_t iters = 0, cycles = 0, reorth = 0;
     int status = PETGEM_OK;
-    double relres = 0.0;
+    double relres = 0.0, prev_relres = 0.0;
+    bool learned = o.precond == PETGEM_PRECOND_LEARNED;
+    int fell_back = 0;
+    if (learned) {
+      PG_TRY(S->Z.reserve((size_t)m * S->ld * (o.precision == PETGEM_PREC_MIXED ? sizeof(float2) : sizeof(double2))));
+      PG_TRY(c->net->features(s, c->sigma.as<double>(), c->sigma_p, c->omega, c->lattice_h));
+    }
     while (true) {
       {
         KernelTimer kt(c, "residual_c128", (double)c->nnz * 20 + 8.0 * (n + 1) + 48.0 * n);
@@ -798,9 +816,9 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
       const double tol_abs = o.tol * bnorm;
       // A cycle whose starting residual already meets tol runs no iteration (k = 0).
       if (o.precision == PETGEM_PREC_MIXED)
-        PG_TRY(run_cycle<float2>(c, S->ahat64.as<float2>(), mj, o.orth, tol_abs, o.inner_tol, &hs));
+        PG_TRY(run_cycle<float2>(c, S->ahat64.as<float2>(), mj, o.orth, tol_abs, o.inner_tol, learned, &hs));
       else
-        PG_TRY(run_cycle<double2>(c, S->ahat128.as<double2>(), mj, o.orth, tol_abs, 0.0, &hs));
+        PG_TRY(run_cycle<double2>(c, S->ahat128.as<double2>(), mj, o.orth, tol_abs, 0.0, learned, &hs));
       relres = sqrt(hs.rnorm2) / bnorm;  // FP64 residual of the current u
       if (!isfinite(relres)) {
         status = PETGEM_ERR_BREAKDOWN;
@@ -814,6 +832,12 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
       iters += hs.k;
       cycles += 1;
       reorth += hs.n_refine;
+      // Fallback: a learned cycle that cut the FP64 residual by less than 1 % hands over to Jacobi.
+      if (learned && cycles > 1 && relres > 0.99 * prev_relres) {
+        learned = false;
+        fell_back = 1;
+      }
+      prev_relres = relres;
       if (hs.done == 2) {  // u was left as it was before this cycle
         status = hs.timeout ? PETGEM_ERR_TIMEOUT : PETGEM_ERR_BREAKDOWN;
         break;
@@ -828,6 +852,8 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
     inf.true_rel_residual = relres;
     inf.status = status;
     inf.reorth = (int32_t)std::min<int64_t>(reorth, INT32_MAX);
+    inf.fell_back = fell_back;
+    if (o.precond == PETGEM_PRECOND_LEARNED) PG_TRY(nn::check_err(s, c->net->err.as<int>(), "petgem_solve (learned)"));
     if (status != PETGEM_OK && worst.ok()) worst = Status{status, "source " + std::to_string(src) + " did not converge"};
   }
   PG_CUDA(cudaStreamSynchronize(s));

@@ -1,0 +1,587 @@
+// Learned preconditioner: a small 4-level 3-D convolutional network on the structured grid of a
+// Kuhn-split lattice (one grid node per mesh node, seven edge classes per node), trained on the
+// GPU with the library's own tensor-core kernels, applied as z = r + s N(r / s) inside FGMRES in
+// the Jacobi-scaled variables (so N = 0 is exactly Jacobi).  Not part of the paper: the paper
+// solves with GMRES / SQMR / MUMPS (Sections 5.1-5.3); the plain solver stays the fallback.
+//
+// Network (levels G0 = lattice nodes, G1..G3 = successive 2x poolings, BF16 activations, FP32
+// accumulation and master weights):
+//   a1 = relu(c1 16->16 on G0)        p1 = pool a1     a2 = relu(c2 16->32 on G1)
+//   p2 = pool a2                      a3 = relu(c3 32->32 on G2)
+//   p3 = pool a3                      a4 = relu(c4 32->32 on G3)
+//   a5 = relu(c5 32->32 on up(a4) + a3)       a6 = relu(c6 32->16 on up(a5) + a2)
+//   y  = c7 16->16 on up(a6) + a1     (channels 14, 15 of y unused)
+// Input channels: 7 edge classes x (Re, Im) of the residual scaled by its RMS, log10(sigma / sigma_p)
+// and log10(w mu0 sigma h^2) of the cell at the node.  Output: the correction on the same slots.
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "ctx.cuh"
+#include "learned_kernels.cuh"
+#include "learned.cuh"
+
+namespace petgem {
+namespace nn {
+namespace {
+
+constexpr int kIn = 16, kOut = 14;
+
+__global__ void k_f32_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16(a[i]);
+}
+// Wd[t][ci][co] = W[26 - t][co][ci]: the input gradient of a convolution is the convolution of
+// the output gradient with the flipped, transposed kernel.
+__global__ void k_flip_weights(const float* __restrict__ W, int cin, int cout, __nv_bfloat16* __restrict__ Wd) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 27 * cin * cout) return;
+  const int co = idx % cout, ci = (idx / cout) % cin, t = idx / (cout * cin);
+  Wd[idx] = __float2bfloat16(W[((26 - t) * cout + co) * cin + ci]);
+}
+
+__device__ inline void grid_coords(int64_t v, int gx, int gy, int& x, int& y, int& z) {
+  x = (int)(v % gx);
+  y = (int)((v / gx) % gy);
+  z = (int)(v / ((int64_t)gx * gy));
+}
+
+// Average of the existing children 2c + {0,1}^3 of every coarse voxel.
+__global__ void k_pool(const __nv_bfloat16* __restrict__ in, int gx, int gy, int gz, int C,
+                       __nv_bfloat16* __restrict__ out) {
+  const int cx = (gx + 1) / 2, cy = (gy + 1) / 2, cz = (gz + 1) / 2;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)cx * cy * cz * C) return;
+  const int c = (int)(idx % C);
+  int x, y, z;
+  grid_coords(idx / C, cx, cy, x, y, z);
+  float s = 0.f;
+  int n = 0;
+  for (int o = 0; o < 8; ++o) {
+    const int fx = 2 * x + (o & 1), fy = 2 * y + ((o >> 1) & 1), fz = 2 * z + (o >> 2);
+    if (fx < gx && fy < gy && fz < gz) {
+      s += __bfloat162float(in[((int64_t)fx + gx * ((int64_t)fy + (int64_t)gy * fz)) * C + c]);
+      ++n;
+    }
+  }
+  out[idx] = __float2bfloat16(s / n);
+}
+// din[f] += dout[parent(f)] / (children of the parent)
+__global__ void k_pool_bwd_add(const __nv_bfloat16* __restrict__ dout, int gx, int gy, int gz, int C,
+                               __nv_bfloat16* __restrict__ din) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)gx * gy * gz * C) return;
+  const int c = (int)(idx % C);
+  int x, y, z;
+  grid_coords(idx / C, gx, gy, x, y, z);
+  const int cx = (gx + 1) / 2, cy = (gy + 1) / 2;
+  const int px = x / 2, py = y / 2, pz = z / 2;
+  const int nx = (2 * px + 1 < gx) ? 2 : 1, ny = (2 * py + 1 < gy) ? 2 : 1, nz = (2 * pz + 1 < gz) ? 2 : 1;
+  const float g = __bfloat162float(dout[((int64_t)px + cx * ((int64_t)py + (int64_t)cy * pz)) * C + c]) / (nx * ny * nz);
+  din[idx] = __float2bfloat16(__bfloat162float(din[idx]) + g);
+}
+// out[f] = coarse[parent(f)] + skip[f]
+__global__ void k_up_add(const __nv_bfloat16* __restrict__ coarse, const __nv_bfloat16* __restrict__ skip, int gx,
+                         int gy, int gz, int C, __nv_bfloat16* __restrict__ out) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)gx * gy * gz * C) return;
+  const int c = (int)(idx % C);
+  int x, y, z;
+  grid_coords(idx / C, gx, gy, x, y, z);
+  const int cx = (gx + 1) / 2, cy = (gy + 1) / 2;
+  const float a = __bfloat162float(coarse[((int64_t)(x / 2) + cx * ((int64_t)(y / 2) + (int64_t)cy * (z / 2))) * C + c]);
+  out[idx] = __float2bfloat16(a + __bfloat162float(skip[idx]));
+}
+// dcoarse[c] = sum of dfine over c's children
+__global__ void k_up_bwd(const __nv_bfloat16* __restrict__ dfine, int gx, int gy, int gz, int C,
+                         __nv_bfloat16* __restrict__ dcoarse) {
+  const int cx = (gx + 1) / 2, cy = (gy + 1) / 2, cz = (gz + 1) / 2;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)cx * cy * cz * C) return;
+  const int c = (int)(idx % C);
+  int x, y, z;
+  grid_coords(idx / C, cx, cy, x, y, z);
+  float s = 0.f;
+  for (int o = 0; o < 8; ++o) {
+    const int fx = 2 * x + (o & 1), fy = 2 * y + ((o >> 1) & 1), fz = 2 * z + (o >> 2);
+    if (fx < gx && fy < gy && fz < gz) s += __bfloat162float(dfine[((int64_t)fx + gx * ((int64_t)fy + (int64_t)gy * fz)) * C + c]);
+  }
+  dcoarse[idx] = __float2bfloat16(s);
+}
+// dy *= (y > 0)
+__global__ void k_relu_bwd(__nv_bfloat16* __restrict__ dy, const __nv_bfloat16* __restrict__ y, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n && !(__bfloat162float(y[i]) > 0.f)) dy[i] = __float2bfloat16(0.f);
+}
+// db[co] (+)= sum_v dy[v][co]: one block per channel, fixed order.
+__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dy, int64_t V, int C, float* __restrict__ db, int acc) {
+  __shared__ float red[256];
+  const int c = blockIdx.x;
+  float s = 0.f;
+  for (int64_t v = threadIdx.x; v < V; v += 256) s += __bfloat162float(dy[v * C + c]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) db[c] = acc ? db[c] + red[0] : red[0];
+}
+
+// ------------------------------------------------------------ edges <-> grid
+// slot of every edge: low node * 7 + class; -1 when the edge is not a lattice step.
+__global__ void k_edge_slots(const int32_t* __restrict__ edges, int64_t E, int gx, int gy, int gz,
+                             int32_t* __restrict__ slot, int* __restrict__ bad) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int64_t lo = edges[2 * e], hi = edges[2 * e + 1];
+  int x0, y0, z0, x1, y1, z1;
+  grid_coords(lo, gx, gy, x0, y0, z0);
+  grid_coords(hi, gx, gy, x1, y1, z1);
+  const int dx = x1 - x0, dy = y1 - y0, dz = z1 - z0;
+  int cls = -1;
+  if (dx == 1 && dy == 0 && dz == 0) cls = 0;
+  else if (dx == 0 && dy == 1 && dz == 0) cls = 1;
+  else if (dx == 0 && dy == 0 && dz == 1) cls = 2;
+  else if (dx == 1 && dy == 1 && dz == 0) cls = 3;
+  else if (dx == 1 && dy == 0 && dz == 1) cls = 4;
+  else if (dx == 0 && dy == 1 && dz == 1) cls = 5;
+  else if (dx == 1 && dy == 1 && dz == 1) cls = 6;
+  if (cls < 0 || hi >= (int64_t)gx * gy * gz) {
+    atomicOr(bad, 1);
+    slot[e] = -1;
+  } else {
+    slot[e] = (int32_t)(lo * 7 + cls);
+  }
+}
+// Model features at every node: log10(sigma / sigma_p) and log10(w mu0 sigma h^2) of the cell
+// whose lowest corner is the node (the last node layer repeats its neighbour's cell).
+__global__ void k_node_features(const double* __restrict__ sigma, int nx, int ny, int nz, double sigma_p,
+                                double wmu0h2, float* __restrict__ feat) {
+  const int gx = nx + 1, gy = ny + 1, gz = nz + 1;
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= (int64_t)gx * gy * gz) return;
+  int x, y, z;
+  grid_coords(v, gx, gy, x, y, z);
+  const int cxi = min(x, nx - 1), cyi = min(y, ny - 1), czi = min(z, nz - 1);
+  const int64_t cell = cxi + (int64_t)nx * (cyi + (int64_t)ny * czi);
+  double s = 0.0;  // the cell's six tets share one sigma in the synthetic models; average them
+  for (int p = 0; p < 6; ++p) s += sigma[6 * cell + p];
+  s /= 6.0;
+  feat[2 * v] = (float)log10(s / sigma_p);
+  feat[2 * v + 1] = (float)log10(wmu0h2 * s);
+}
+// Network input: residual (complex) on the edge slots scaled by 1/s, plus the two features.
+template <typename T>
+__global__ void k_to_grid(const T* __restrict__ r, const int32_t* __restrict__ slot, int64_t E,
+                          const float* __restrict__ inv_s, float* __restrict__ g32) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int32_t sl = slot[e];
+  if (sl < 0) return;
+  const int64_t v = sl / 7;
+  const int c = sl - (int)(v * 7);
+  const float f = *inv_s;
+  g32[v * kIn + c] = (float)r[e].x * f;
+  g32[v * kIn + 7 + c] = (float)r[e].y * f;
+}
+__global__ void k_pack_input(const float* __restrict__ g32, const float* __restrict__ feat, int64_t V,
+                             __nv_bfloat16* __restrict__ x) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= V * kIn) return;
+  const int c = (int)(i % kIn);
+  const int64_t v = i / kIn;
+  x[i] = __float2bfloat16(c < 14 ? g32[i] : feat[2 * v + (c - 14)]);
+}
+// z_e = r_e + s * y[slot] (complex: Re from class c, Im from class 7 + c)
+template <typename T>
+__global__ void k_from_grid(const T* __restrict__ r, const float* __restrict__ y, const int32_t* __restrict__ slot,
+                            int64_t E, const float* __restrict__ s_ptr, T* __restrict__ z) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int32_t sl = slot[e];
+  T out = r[e];
+  if (sl >= 0) {
+    const int64_t v = sl / 7;
+    const int c = sl - (int)(v * 7);
+    const float s = *s_ptr;
+    out.x += s * y[v * 16 + c];
+    out.y += s * y[v * 16 + 7 + c];
+  }
+  z[e] = out;
+}
+// RMS of a complex vector -> (1/s, s) with s = RMS (1 when the vector is zero).
+template <typename T>
+__global__ void k_rms(const T* __restrict__ r, int64_t E, float* __restrict__ out) {
+  __shared__ double red[256];
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < E; i += 256) a += (double)r[i].x * r[i].x + (double)r[i].y * r[i].y;
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double s = sqrt(red[0] / (double)E);
+    if (!(s > 0.0)) s = 1.0;
+    out[0] = (float)(1.0 / s);
+    out[1] = (float)s;
+  }
+}
+// Training target on the grid: (u* - u_k) / s - r / s, i.e. what N must add to the Jacobi step.
+__global__ void k_target_grid(const double2* __restrict__ du, const double2* __restrict__ r,
+                              const int32_t* __restrict__ slot, int64_t E, const float* __restrict__ inv_s,
+                              float* __restrict__ t32) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int32_t sl = slot[e];
+  if (sl < 0) return;
+  const int64_t v = sl / 7;
+  const int c = sl - (int)(v * 7);
+  const float f = *inv_s;
+  t32[v * 16 + c] = (float)(du[e].x - r[e].x) * f;
+  t32[v * 16 + 7 + c] = (float)(du[e].y - r[e].y) * f;
+}
+// loss += 0.5 sum (y - t)^2 / count over the 14 output channels; dy = (y - t) / count (BF16).
+__global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, int64_t V, double inv_count,
+                      __nv_bfloat16* __restrict__ dy, double* __restrict__ loss_part) {
+  __shared__ double red[256];
+  double a = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V * 16; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % 16);
+    float d = c < kOut ? y[i] - t[i] : 0.f;
+    a += 0.5 * (double)d * d;
+    dy[i] = __float2bfloat16((float)(d * inv_count));
+  }
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0] * inv_count;
+}
+__global__ void k_sum(const double* __restrict__ a, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += a[i];
+    *out += s;
+  }
+}
+// Adam (Kingma & Ba 2015) on FP32 master weights.
+__global__ void k_adam(float* __restrict__ w, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int64_t n, float lr, float b1, float b2, float eps, float c1, float c2, float gscale) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i] * gscale;
+  g[i] = gi;  // keep the mean gradient readable
+  m[i] = b1 * m[i] + (1.f - b1) * gi;
+  v[i] = b2 * v[i] + (1.f - b2) * gi * gi;
+  w[i] -= lr * (m[i] / c1) / (sqrtf(v[i] / c2) + eps);
+}
+
+// r = b - A x (one thread per row, FP64) and du = D (x* - x).
+__global__ void k_res_err(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                          const double2* __restrict__ val, const double2* __restrict__ b, const double2* __restrict__ d,
+                          const double2* __restrict__ x, const double2* __restrict__ xs, int64_t n,
+                          double2* __restrict__ r, double2* __restrict__ du) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double2 acc = b[i];
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) acc = csub(acc, cmul(val[p], x[col[p]]));
+  r[i] = acc;
+  du[i] = cmul(d[i], csub(xs[i], x[i]));
+}
+
+unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ------------------------------------------------------------ host side
+Status conv3d(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, const __nv_bfloat16* x,
+              const __nv_bfloat16* w, const float* bias, bool relu, __nv_bfloat16* ybf, float* yf, int* err) {
+  const int64_t V = (int64_t)gx * gy * gz;
+  const unsigned grid = nb(V, kConvRows);
+#define PG_CONV(CI, CO)                                                                                        \
+  if (cin == CI && cout == CO) {                                                                               \
+    static bool attr = false;                                                                                  \
+    if (!attr) {                                                                                               \
+      PG_CUDA(cudaFuncSetAttribute(k_conv3d<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                                   conv_smem(CI, CO)));                                                        \
+      attr = true;                                                                                             \
+    }                                                                                                          \
+    k_conv3d<CI, CO><<<grid, 128, conv_smem(CI, CO), s>>>(x, w, bias, gx, gy, gz, relu ? 1 : 0, ybf, yf, err); \
+    PG_CUDA(cudaGetLastError());                                                                               \
+    return Status{};                                                                                           \
+  }
+  PG_CONV(16, 16)
+  PG_CONV(16, 32)
+  PG_CONV(32, 16)
+  PG_CONV(32, 32)
+#undef PG_CONV
+  return Status{PETGEM_ERR_UNSUPPORTED, "conv3d: channel counts must be 16 or 32"};
+}
+
+Status conv3d_wgrad(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, const __nv_bfloat16* x,
+                    const __nv_bfloat16* dy, float* part, int splits, float* dw, bool accumulate, int* err) {
+  const dim3 grid((27 * cin + kConvRows - 1) / kConvRows, splits);
+#define PG_WG(CI, CO)                                                                                  \
+  if (cin == CI && cout == CO) {                                                                       \
+    k_conv3d_wgrad<CI, CO><<<grid, 128, 0, s>>>(x, dy, gx, gy, gz, part, err);                         \
+    PG_CUDA(cudaGetLastError());                                                                       \
+    k_wgrad_reduce<<<nb(27 * cin * cout), 256, 0, s>>>(part, splits, cin, cout, dw, accumulate ? 1 : 0); \
+    PG_CUDA(cudaGetLastError());                                                                       \
+    return Status{};                                                                                   \
+  }
+  PG_WG(16, 16)
+  PG_WG(16, 32)
+  PG_WG(32, 16)
+  PG_WG(32, 32)
+#undef PG_WG
+  return Status{PETGEM_ERR_UNSUPPORTED, "conv3d_wgrad: channel counts must be 16 or 32"};
+}
+
+int wgrad_splits(int64_t V) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, (V + 4095) / 4096)); }
+
+Status Net::init(petgem_ctx* c, int nx_, int ny_, int nz_) {
+  nx = nx_;
+  ny = ny_;
+  nz = nz_;
+  g[0][0] = nx + 1;
+  g[0][1] = ny + 1;
+  g[0][2] = nz + 1;
+  for (int l = 1; l < 4; ++l)
+    for (int a = 0; a < 3; ++a) g[l][a] = (g[l - 1][a] + 1) / 2;
+  for (int l = 0; l < 4; ++l) V[l] = (int64_t)g[l][0] * g[l][1] * g[l][2];
+  const int spec[7][4] = {{16, 16, 1, 0}, {16, 32, 1, 1}, {32, 32, 1, 2}, {32, 32, 1, 3},
+                          {32, 32, 1, 2}, {32, 16, 1, 1}, {16, 16, 0, 0}};  // cin, cout, relu, level
+  n_params = 0;
+  for (int i = 0; i < 7; ++i) {
+    L[i].cin = spec[i][0];
+    L[i].cout = spec[i][1];
+    L[i].relu = spec[i][2];
+    L[i].level = spec[i][3];
+    L[i].w_off = n_params;
+    n_params += 27 * L[i].cin * L[i].cout;
+    L[i].b_off = n_params;
+    n_params += L[i].cout;
+  }
+  PG_TRY(params.reserve(n_params * sizeof(float)));
+  PG_TRY(grads.reserve(n_params * sizeof(float)));
+  PG_TRY(adam_m.reserve(n_params * sizeof(float)));
+  PG_TRY(adam_v.reserve(n_params * sizeof(float)));
+  PG_TRY(wb.reserve(n_params * sizeof(__nv_bfloat16)));
+  PG_TRY(wd.reserve(n_params * sizeof(__nv_bfloat16)));
+  cudaStream_t s = c->stream;
+  PG_CUDA(cudaMemsetAsync(params.ptr, 0, n_params * sizeof(float), s));
+  PG_CUDA(cudaMemsetAsync(adam_m.ptr, 0, n_params * sizeof(float), s));
+  PG_CUDA(cudaMemsetAsync(adam_v.ptr, 0, n_params * sizeof(float), s));
+  adam_t = 0;
+  // activations (BF16) by level
+  auto act = [&](DevBuf& b, int lvl, int ch) { return b.reserve((size_t)V[lvl] * ch * sizeof(__nv_bfloat16) + 64); };
+  PG_TRY(act(x0, 0, 16));
+  PG_TRY(act(a1, 0, 16));
+  PG_TRY(act(p1, 1, 16));
+  PG_TRY(act(a2, 1, 32));
+  PG_TRY(act(p2, 2, 32));
+  PG_TRY(act(a3, 2, 32));
+  PG_TRY(act(p3, 3, 32));
+  PG_TRY(act(a4, 3, 32));
+  PG_TRY(act(s5, 2, 32));
+  PG_TRY(act(a5, 2, 32));
+  PG_TRY(act(s6, 1, 32));
+  PG_TRY(act(a6, 1, 16));
+  PG_TRY(act(s7, 0, 16));
+  PG_TRY(act(dy, 0, 16));
+  PG_TRY(act(ds7, 0, 16));
+  PG_TRY(act(da6, 1, 16));
+  PG_TRY(act(ds6, 1, 32));
+  PG_TRY(act(da5, 2, 32));
+  PG_TRY(act(ds5, 2, 32));
+  PG_TRY(act(da4, 3, 32));
+  PG_TRY(act(dp3, 3, 32));
+  PG_TRY(act(dp2, 2, 32));
+  PG_TRY(act(dp1, 1, 16));
+  PG_TRY(y.reserve((size_t)V[0] * 16 * sizeof(float)));
+  PG_TRY(g32.reserve((size_t)V[0] * 16 * sizeof(float)));
+  PG_TRY(t32.reserve((size_t)V[0] * 16 * sizeof(float)));
+  PG_TRY(feat.reserve((size_t)V[0] * 2 * sizeof(float)));
+  PG_TRY(scal.reserve(16 * sizeof(float)));
+  PG_TRY(loss_part.reserve(1024 * sizeof(double)));
+  PG_TRY(loss_acc.reserve(sizeof(double)));
+  PG_TRY(err.reserve(sizeof(int)));
+  PG_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
+  PG_TRY(zbias.reserve(32 * sizeof(float)));
+  PG_CUDA(cudaMemsetAsync(zbias.ptr, 0, 32 * sizeof(float), s));
+  const int splits = wgrad_splits(V[0]);
+  PG_TRY(wpart.reserve((size_t)splits * 27 * 32 * 32 * sizeof(float)));
+  PG_CUDA(cudaMemsetAsync(feat.ptr, 0, (size_t)V[0] * 2 * sizeof(float), s));
+  ready = true;
+  return Status{};
+}
+
+Status Net::pack_weights(cudaStream_t s) {
+  k_f32_to_bf16<<<nb(n_params), 256, 0, s>>>(params.as<float>(), wb.as<__nv_bfloat16>(), n_params);
+  for (int i = 0; i < 7; ++i)
+    k_flip_weights<<<nb(27 * L[i].cin * L[i].cout), 256, 0, s>>>(
+        params.as<float>() + L[i].w_off, L[i].cin, L[i].cout, wd.as<__nv_bfloat16>() + L[i].w_off);
+  PG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+Status Net::conv(cudaStream_t s, int i, const __nv_bfloat16* in, __nv_bfloat16* out, float* outf) {
+  const int* gg = g[L[i].level];
+  return conv3d(s, gg[0], gg[1], gg[2], L[i].cin, L[i].cout, in, wb.as<__nv_bfloat16>() + L[i].w_off,
+                params.as<float>() + L[i].b_off, L[i].relu != 0, out, outf, err.as<int>());
+}
+
+// Input grid x0 (BF16 [V0][16]) -> y (FP32 [V0][16]).
+Status Net::forward(cudaStream_t s) {
+  using B = __nv_bfloat16;
+  PG_TRY(conv(s, 0, x0.as<B>(), a1.as<B>(), nullptr));
+  k_pool<<<nb(V[1] * 16), 256, 0, s>>>(a1.as<B>(), g[0][0], g[0][1], g[0][2], 16, p1.as<B>());
+  PG_TRY(conv(s, 1, p1.as<B>(), a2.as<B>(), nullptr));
+  k_pool<<<nb(V[2] * 32), 256, 0, s>>>(a2.as<B>(), g[1][0], g[1][1], g[1][2], 32, p2.as<B>());
+  PG_TRY(conv(s, 2, p2.as<B>(), a3.as<B>(), nullptr));
+  k_pool<<<nb(V[3] * 32), 256, 0, s>>>(a3.as<B>(), g[2][0], g[2][1], g[2][2], 32, p3.as<B>());
+  PG_TRY(conv(s, 3, p3.as<B>(), a4.as<B>(), nullptr));
+  k_up_add<<<nb(V[2] * 32), 256, 0, s>>>(a4.as<B>(), a3.as<B>(), g[2][0], g[2][1], g[2][2], 32, s5.as<B>());
+  PG_TRY(conv(s, 4, s5.as<B>(), a5.as<B>(), nullptr));
+  k_up_add<<<nb(V[1] * 32), 256, 0, s>>>(a5.as<B>(), a2.as<B>(), g[1][0], g[1][1], g[1][2], 32, s6.as<B>());
+  PG_TRY(conv(s, 5, s6.as<B>(), a6.as<B>(), nullptr));
+  k_up_add<<<nb(V[0] * 16), 256, 0, s>>>(a6.as<B>(), a1.as<B>(), g[0][0], g[0][1], g[0][2], 16, s7.as<B>());
+  PG_TRY(conv(s, 6, s7.as<B>(), nullptr, y.as<float>()));
+  PG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+Status Net::dgrad(cudaStream_t s, int i, const __nv_bfloat16* dout, __nv_bfloat16* din) {
+  const int* gg = g[L[i].level];  // the input gradient has no bias term: zbias is all zeros
+  return conv3d(s, gg[0], gg[1], gg[2], L[i].cout, L[i].cin, dout, wd.as<__nv_bfloat16>() + L[i].w_off,
+                zbias.as<float>(), false, din, nullptr, err.as<int>());
+}
+
+Status Net::wgrad(cudaStream_t s, int i, const __nv_bfloat16* in, const __nv_bfloat16* dout, bool acc) {
+  const int* gg = g[L[i].level];
+  const int64_t Vl = (int64_t)gg[0] * gg[1] * gg[2];
+  PG_TRY(conv3d_wgrad(s, gg[0], gg[1], gg[2], L[i].cin, L[i].cout, in, dout, wpart.as<float>(), wgrad_splits(Vl),
+                      grads.as<float>() + L[i].w_off, acc, err.as<int>()));
+  k_bias_grad<<<L[i].cout, 256, 0, s>>>(dout, Vl, L[i].cout, grads.as<float>() + L[i].b_off, acc ? 1 : 0);
+  PG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+// dy (BF16 [V0][16]) -> parameter gradients (accumulated when acc).
+Status Net::backward(cudaStream_t s, bool acc) {
+  using B = __nv_bfloat16;
+  PG_TRY(wgrad(s, 6, s7.as<B>(), dy.as<B>(), acc));
+  PG_TRY(dgrad(s, 6, dy.as<B>(), ds7.as<B>()));                        // = da1 (skip) part
+  k_up_bwd<<<nb(V[1] * 16), 256, 0, s>>>(ds7.as<B>(), g[0][0], g[0][1], g[0][2], 16, da6.as<B>());
+  k_relu_bwd<<<nb(V[1] * 16), 256, 0, s>>>(da6.as<B>(), a6.as<B>(), V[1] * 16);
+  PG_TRY(wgrad(s, 5, s6.as<B>(), da6.as<B>(), acc));
+  PG_TRY(dgrad(s, 5, da6.as<B>(), ds6.as<B>()));                       // = da2 part
+  k_up_bwd<<<nb(V[2] * 32), 256, 0, s>>>(ds6.as<B>(), g[1][0], g[1][1], g[1][2], 32, da5.as<B>());
+  k_relu_bwd<<<nb(V[2] * 32), 256, 0, s>>>(da5.as<B>(), a5.as<B>(), V[2] * 32);
+  PG_TRY(wgrad(s, 4, s5.as<B>(), da5.as<B>(), acc));
+  PG_TRY(dgrad(s, 4, da5.as<B>(), ds5.as<B>()));                       // = da3 part
+  k_up_bwd<<<nb(V[3] * 32), 256, 0, s>>>(ds5.as<B>(), g[2][0], g[2][1], g[2][2], 32, da4.as<B>());
+  k_relu_bwd<<<nb(V[3] * 32), 256, 0, s>>>(da4.as<B>(), a4.as<B>(), V[3] * 32);
+  PG_TRY(wgrad(s, 3, p3.as<B>(), da4.as<B>(), acc));
+  PG_TRY(dgrad(s, 3, da4.as<B>(), dp3.as<B>()));
+  k_pool_bwd_add<<<nb(V[2] * 32), 256, 0, s>>>(dp3.as<B>(), g[2][0], g[2][1], g[2][2], 32, ds5.as<B>());  // da3
+  k_relu_bwd<<<nb(V[2] * 32), 256, 0, s>>>(ds5.as<B>(), a3.as<B>(), V[2] * 32);
+  PG_TRY(wgrad(s, 2, p2.as<B>(), ds5.as<B>(), acc));
+  PG_TRY(dgrad(s, 2, ds5.as<B>(), dp2.as<B>()));
+  k_pool_bwd_add<<<nb(V[1] * 32), 256, 0, s>>>(dp2.as<B>(), g[1][0], g[1][1], g[1][2], 32, ds6.as<B>());  // da2
+  k_relu_bwd<<<nb(V[1] * 32), 256, 0, s>>>(ds6.as<B>(), a2.as<B>(), V[1] * 32);
+  PG_TRY(wgrad(s, 1, p1.as<B>(), ds6.as<B>(), acc));
+  PG_TRY(dgrad(s, 1, ds6.as<B>(), dp1.as<B>()));
+  k_pool_bwd_add<<<nb(V[0] * 16), 256, 0, s>>>(dp1.as<B>(), g[0][0], g[0][1], g[0][2], 16, ds7.as<B>());  // da1
+  k_relu_bwd<<<nb(V[0] * 16), 256, 0, s>>>(ds7.as<B>(), a1.as<B>(), V[0] * 16);
+  PG_TRY(wgrad(s, 0, x0.as<B>(), ds7.as<B>(), acc));
+  PG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+// Build the input grid from an edge vector r (Jacobi-scaled residual); *inv_s, s in scal[0..1].
+template <typename T>
+Status Net::load_input(cudaStream_t s, const T* r, const int32_t* slot, int64_t E) {
+  k_rms<T><<<1, 256, 0, s>>>(r, E, scal.as<float>());
+  PG_CUDA(cudaMemsetAsync(g32.ptr, 0, (size_t)V[0] * 16 * sizeof(float), s));
+  k_to_grid<T><<<nb(E), 256, 0, s>>>(r, slot, E, scal.as<float>(), g32.as<float>());
+  k_pack_input<<<nb(V[0] * kIn), 256, 0, s>>>(g32.as<float>(), feat.as<float>(), V[0], x0.as<__nv_bfloat16>());
+  PG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+template <typename T>
+Status Net::apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T* z) {
+  PG_TRY(load_input(s, r, slot, E));
+  PG_TRY(forward(s));
+  k_from_grid<T><<<nb(E), 256, 0, s>>>(r, y.as<float>(), slot, E, scal.as<float>() + 1, z);
+  PG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+template Status Net::apply<float2>(cudaStream_t, const float2*, const int32_t*, int64_t, float2*);
+template Status Net::apply<double2>(cudaStream_t, const double2*, const int32_t*, int64_t, double2*);
+
+// One sample: r = Jacobi-scaled residual, du = D (x* - x_k) (both complex128 edge vectors).
+Status Net::sample_grad(cudaStream_t s, const double2* r, const double2* du, const int32_t* slot, int64_t E, bool acc) {
+  PG_TRY(load_input(s, r, slot, E));
+  PG_CUDA(cudaMemsetAsync(t32.ptr, 0, (size_t)V[0] * 16 * sizeof(float), s));
+  k_target_grid<<<nb(E), 256, 0, s>>>(du, r, slot, E, scal.as<float>(), t32.as<float>());
+  PG_TRY(forward(s));
+  const int blocks = (int)std::min<int64_t>(1024, nb(V[0] * 16));
+  // mean over the slots that carry edges: 14 channels of every node
+  k_mse<<<blocks, 256, 0, s>>>(y.as<float>(), t32.as<float>(), V[0], 1.0 / ((double)V[0] * kOut),
+                               dy.as<__nv_bfloat16>(), loss_part.as<double>());
+  k_sum<<<1, 32, 0, s>>>(loss_part.as<double>(), blocks, loss_acc.as<double>());
+  PG_TRY(backward(s, acc));
+  return Status{};
+}
+
+Status Net::adam_step(cudaStream_t s, float lr, float gscale) {
+  ++adam_t;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)adam_t), c2 = 1.f - powf(b2, (float)adam_t);
+  k_adam<<<nb(n_params), 256, 0, s>>>(params.as<float>(), grads.as<float>(), adam_m.as<float>(), adam_v.as<float>(),
+                                      n_params, lr, b1, b2, 1e-8f, c1, c2, gscale);
+  PG_CUDA(cudaGetLastError());
+  return pack_weights(s);
+}
+
+Status Net::features(cudaStream_t s, const double* sigma, double sigma_p, double omega, double h) {
+  const double mu0 = 4.0e-7 * 3.141592653589793238462643383279502884;
+  k_node_features<<<nb(V[0]), 256, 0, s>>>(sigma, nx, ny, nz, sigma_p, omega * mu0 * h * h, feat.as<float>());
+  PG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+Status edge_slots(cudaStream_t s, const int32_t* edges, int64_t E, int gx, int gy, int gz, int32_t* slot, int* bad) {
+  k_edge_slots<<<nb(E), 256, 0, s>>>(edges, E, gx, gy, gz, slot, bad);
+  PG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+Status residual_and_error(petgem_ctx* c, const double2* x, const double2* xstar, double2* r, double2* du) {
+  k_res_err<<<nb(c->n_edges), 256, 0, c->stream>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(),
+                                                   c->val.as<double2>(), c->b.as<double2>(), c->diag.as<double2>(), x,
+                                                   xstar, c->n_edges, r, du);
+  PG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+Status check_err(cudaStream_t s, const int* err, const char* where) {
+  int h = 0;
+  PG_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PG_CUDA(cudaStreamSynchronize(s));
+  if (h) return Status{PETGEM_ERR_TIMEOUT, std::string(where) + ": a tensor-core wait timed out"};
+  return Status{};
+}
+
+}  // namespace nn
+}  // namespace petgem
