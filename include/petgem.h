@@ -70,10 +70,11 @@ enum { PETGEM_PRECOND_JACOBI = 0, PETGEM_PRECOND_LEARNED = 1 };
  *     inner_tol or restart steps have run; x and the residual stay complex128.
  *   batch: number of sources iterated together (their SpMVs become one SpMM); 0 = all (groups
  *     of up to 32).  batch = 1 solves the sources one after the other.
- *   precond = PETGEM_PRECOND_LEARNED (single-source solves): flexible GMRES whose
- *     preconditioner is z = v + s N(v / s) in the Jacobi-scaled variables, N the network of
- *     petgem_learned_create, s the RMS of v; when a cycle cuts the FP64 residual by less than
- *     1 %, the solve falls back to Jacobi (info.fell_back). */
+ *   precond = PETGEM_PRECOND_LEARNED (single-source solves): flexible GMRES whose odd steps use
+ *     z = s N(v / s) (N the network of petgem_learned_create, s the RMS of v, Jacobi-scaled
+ *     variables) and whose even steps use Jacobi, with two-pass Gram-Schmidt.  The first cycle
+ *     runs with Jacobi and measures its FP64 residual reduction; a learned cycle that does not
+ *     beat it is undone and the solve continues with Jacobi alone (info.fell_back). */
 typedef struct {
   int32_t restart;
   int32_t precision;
@@ -185,22 +186,22 @@ int petgem_receivers(petgem_ctx *ctx, int32_t n_rcv, const double *rx, const voi
  * +xyz) from its low node, so edge vectors map one-to-one onto 7 grid channels (x Re, Im).  Four
  * levels (the node grid and three 2x poolings), seven 3x3x3 convolutions (16/32 channels, BF16
  * operands on the tensor cores, FP32 accumulation and FP32 master weights), ReLU, skip additions.
- * Input: the residual (16 channels with two conductivity features); output: the correction added
- * to the Jacobi step.
+ * Input: the residual (16 channels with two conductivity features); output: a correction
+ * direction, trained so that one step along it removes as much of the residual as possible.
  * petgem_learned_create: after petgem_mesh_edges on such a lattice; keeps the parameters when
  *   called again for another mesh (the network is fully convolutional).  PETGEM_ERR_UNSUPPORTED
  *   if some edge is not a lattice step.
  * petgem_learned_params: host float[n] in (set) / out (get, and grad = the gradient accumulated by
  *   the last train step, scaled by 1 / n_samples); NULL to skip; *n_params receives the count.
- * petgem_learned_train_step: one Adam step (lr) on the mean squared error of n_samples pairs
- *   (residual, correction) of the assembled system (source 0): x_iters device complex128
- *   [n_samples][E] are iterates, x_star device complex128[E] the converged solution; the target
- *   of iterate x is D (x* - x) - r with r = b - A x, both scaled by 1 / RMS(r).  *loss: host.
- * petgem_learned_apply: z = r + s N(r / s) for one device complex128 vector r of E entries. */
+ * petgem_learned_train_step: one Adam step (lr) on the mean over n_samples solver iterates
+ *   x_iters (device complex128 [n_samples][E], e.g. the iterate at the start of every GMRES cycle)
+ *   of the residual angle L = 1 - |<r, Ahat z>|^2 / (|r|^2 |Ahat z|^2), r = b - A x of the
+ *   assembled system (source 0), z the network's direction for r, Ahat = A D^{-1}: zero when
+ *   one step along z removes the whole residual.  *loss (host) receives the mean L.
+ * petgem_learned_apply: z = s N(r / s), s = RMS(r), for one device complex128 vector r of E entries. */
 int petgem_learned_create(petgem_ctx *ctx, int32_t nx, int32_t ny, int32_t nz);
 int petgem_learned_params(petgem_ctx *ctx, const float *set, float *get, float *grad, int64_t *n_params);
-int petgem_learned_train_step(petgem_ctx *ctx, int32_t n_samples, const void *x_iters, const void *x_star,
-                              float lr, double *loss);
+int petgem_learned_train_step(petgem_ctx *ctx, int32_t n_samples, const void *x_iters, float lr, double *loss);
 int petgem_learned_apply(petgem_ctx *ctx, const void *r, void *z);
 
 /* The network's tensor-core kernels as plain functions (test and diagnostic entry points):

@@ -201,3 +201,37 @@ def edge_grid_index(edges: np.ndarray, n: int) -> np.ndarray:
         m = np.all(d == np.array(step), axis=1)
         out[m] = lo[m] * 7 + c
     return out
+
+
+# ---------------------------------------------------------------- residual-angle training loss
+def edges_to_grid(v_edges: np.ndarray, slot: np.ndarray, n_nodes: int, scale: float = 1.0) -> np.ndarray:
+    """[n_nodes, 16] grid with Re / Im of an edge vector on channels c / 7 + c of its slot."""
+    g = np.zeros((n_nodes, 16))
+    v, c = slot // 7, slot % 7
+    g[v, c] = v_edges.real * scale
+    g[v, 7 + c] = v_edges.imag * scale
+    return g
+
+
+def grid_to_edges(g: np.ndarray, slot: np.ndarray) -> np.ndarray:
+    v, c = slot // 7, slot % 7
+    return g[v, c] + 1j * g[v, 7 + c]
+
+
+def angle_loss(y_grid: np.ndarray, r: np.ndarray, slot: np.ndarray, spmv, diag: np.ndarray):
+    """L = 1 - |<r, Ahat z>|^2 / (|r|^2 |Ahat z|^2) for z = the network output on the edges and
+    Ahat = A D^{-1} (A complex symmetric, so Ahat^H g = conj(D)^{-1} conj(A) g).  Returns
+    (L, dL/dy on the grid): the gradient of the real loss with respect to Re y and Im y."""
+    z = grid_to_edges(y_grid, slot)
+    w = spmv(z / diag)
+    a = np.vdot(r, w)
+    b = np.vdot(w, w).real
+    c = np.vdot(r, r).real
+    L = 1.0 - abs(a) ** 2 / (b * c)
+    gw = -2.0 * (a * r / (c * b) - abs(a) ** 2 * w / (c * b * b))      # dL/dRe w + i dL/dIm w
+    gz = np.conj(spmv(np.conj(gw))) / np.conj(diag)                    # Ahat^H gw = conj(D)^-1 conj(A) gw
+    gy = np.zeros_like(y_grid)
+    v, cc = slot // 7, slot % 7
+    gy[v, cc] = gz.real
+    gy[v, 7 + cc] = gz.imag
+    return L, gy

@@ -63,7 +63,7 @@ _SIGNATURES = {
     "petgem_launch_count": (_I64, [_P]),
     "petgem_learned_create": (ctypes.c_int, [_P, _I32, _I32, _I32]),
     "petgem_learned_params": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(_I64)]),
-    "petgem_learned_train_step": (ctypes.c_int, [_P, _I32, _P, _P, ctypes.c_float, ctypes.POINTER(_D)]),
+    "petgem_learned_train_step": (ctypes.c_int, [_P, _I32, _P, ctypes.c_float, ctypes.POINTER(_D)]),
     "petgem_learned_apply": (ctypes.c_int, [_P, _P, _P]),
     "petgem_nn_conv3d": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _P, _P, _I32, _P, _I32]),
     "petgem_nn_conv3d_wgrad": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _P, _P]),
@@ -223,10 +223,10 @@ def petgem_learned_params(ctx, set_params=None, get=False, grad=False):
     return n.value
 
 
-def petgem_learned_train_step(ctx, x_iters, x_star, lr) -> float:
+def petgem_learned_train_step(ctx, x_iters, lr) -> float:
     loss = _D(0.0)
-    _check(ctx, load().petgem_learned_train_step(ctx, x_iters.shape[0], _ptr(x_iters), _ptr(x_star),
-                                                  ctypes.c_float(lr), ctypes.byref(loss)))
+    _check(ctx, load().petgem_learned_train_step(ctx, x_iters.shape[0], _ptr(x_iters), ctypes.c_float(lr),
+                                                  ctypes.byref(loss)))
     return loss.value
 
 

@@ -388,27 +388,25 @@ int petgem_learned_params(petgem_ctx* c, const float* set, float* get, float* gr
   return finish(c, s);
 }
 
-int petgem_learned_train_step(petgem_ctx* c, int32_t n_samples, const void* x_iters, const void* x_star, float lr,
-                              double* loss) {
+int petgem_learned_train_step(petgem_ctx* c, int32_t n_samples, const void* x_iters, float lr, double* loss) {
   if (!c) return PETGEM_ERR_INVALID_ARG;
-  if (!c->net || !c->slots_ready || !c->assembled || n_samples < 1 || !x_iters || !x_star || !(lr > 0.f))
+  if (!c->net || !c->slots_ready || !c->assembled || n_samples < 1 || !x_iters || !(lr > 0.f))
     return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_learned_train_step: bad arguments or state"});
   petgem::nn::Net* N = c->net;
   cudaStream_t st = c->stream;
   const int64_t E = c->n_edges;
   Status s = set_device(c);
-  if (s.ok()) s = N->rtmp.reserve(E * sizeof(double2));
-  if (s.ok()) s = N->dutmp.reserve(E * sizeof(double2));
+  for (petgem::DevBuf* b : {&N->rtmp, &N->dutmp, &N->wtmp, &N->gtmp})
+    if (s.ok()) s = b->reserve(E * sizeof(double2));
+  if (s.ok()) s = N->dvec.reserve(8 * sizeof(double));
   if (s.ok()) s = N->features(st, c->sigma.as<double>(), c->sigma_p, c->omega, c->lattice_h);
   if (s.ok() && cudaMemsetAsync(N->loss_acc.ptr, 0, sizeof(double), st) != cudaSuccess)
     s = Status{PETGEM_ERR_CUDA, "memset"};
   for (int32_t i = 0; i < n_samples && s.ok(); ++i) {
     const double2* xi = static_cast<const double2*>(x_iters) + (int64_t)i * E;
-    s = petgem::nn::residual_and_error(c, xi, static_cast<const double2*>(x_star), N->rtmp.as<double2>(),
-                                       N->dutmp.as<double2>());
-    if (s.ok())
-      s = N->sample_grad(st, N->rtmp.as<double2>(), N->dutmp.as<double2>(), c->slots.as<int32_t>(), E, i > 0);
-    c->launches += 60;
+    s = petgem::nn::residual_and_error(c, xi, xi, N->rtmp.as<double2>(), N->dutmp.as<double2>());
+    if (s.ok()) s = N->sample_grad(st, c, N->rtmp.as<double2>(), c->slots.as<int32_t>(), E, i > 0);
+    c->launches += 70;
   }
   if (s.ok()) s = N->adam_step(st, lr, 1.f / (float)n_samples);
   if (s.ok()) s = petgem::nn::check_err(st, N->err.as<int>(), "petgem_learned_train_step");

@@ -678,11 +678,16 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
     T* vj = V + (int64_t)j * ld;
     T* vn = vj + ld;
     const T* xin = vj;
-    if (learned) {
-      KernelTimer kt(c, "learned_apply", 0.0, j, 0);
-      PG_TRY(c->net->apply<T>(s, vj, c->slots.as<int32_t>(), n, Z + (int64_t)j * ld));
-      xin = Z + (int64_t)j * ld;
-      c->launches += 20;
+    if (learned) {  // odd steps: the network's direction; even steps: Jacobi (z = v)
+      T* zj = Z + (int64_t)j * ld;
+      if (j & 1) {
+        KernelTimer kt(c, "learned_apply", 0.0, j, 0);
+        PG_TRY(c->net->apply<T>(s, vj, c->slots.as<int32_t>(), n, zj));
+        c->launches += 20;
+      } else {
+        PG_CUDA(cudaMemcpyAsync(zj, vj, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      }
+      xin = zj;
     }
     {
       KernelTimer kt(c, c128 ? "spmv_c128" : "spmv_c64", spmv_bytes, j, 0);
@@ -798,28 +803,55 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
     int64_t iters = 0, cycles = 0, reorth = 0;
     int status = PETGEM_OK;
     double relres = 0.0, prev_relres = 0.0;
-    bool learned = o.precond == PETGEM_PRECOND_LEARNED;
+    // Learned preconditioner: the first cycle runs with Jacobi and measures its residual reduction
+    // per cycle; learned cycles follow while each reduces the FP64 residual more than that.
+    bool want_learned = o.precond == PETGEM_PRECOND_LEARNED;
+    bool learned = false;
+    double jacobi_rate = -1.0;
     int fell_back = 0;
-    if (learned) {
+    if (want_learned) {
       PG_TRY(S->Z.reserve((size_t)m * S->ld * (o.precision == PETGEM_PREC_MIXED ? sizeof(float2) : sizeof(double2))));
+      PG_TRY(S->usave.reserve(n * sizeof(double2)));
       PG_TRY(c->net->features(s, c->sigma.as<double>(), c->sigma_p, c->omega, c->lattice_h));
     }
-    while (true) {
-      {
-        KernelTimer kt(c, "residual_c128", (double)c->nnz * 20 + 8.0 * (n + 1) + 48.0 * n);
-        k_residual<kGroup><<<rb, 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(),
-                                              S->ahat128.as<double2>(), S->u.as<double2>(), b, S->r.as<double2>(), n);
-        c->launches++;
-      }
+    bool prev_learned = false;
+    auto residual = [&]() -> Status {
+      KernelTimer kt(c, "residual_c128", (double)c->nnz * 20 + 8.0 * (n + 1) + 48.0 * n);
+      k_residual<kGroup><<<rb, 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), S->ahat128.as<double2>(),
+                                            S->u.as<double2>(), b, S->r.as<double2>(), n);
+      c->launches++;
       PG_CUDA(cudaGetLastError());
+      return Status{};
+    };
+    while (true) {
+      PG_TRY(residual());
+      if (want_learned && cycles > 0) {
+        k_norm2<<<nb, kT, 0, s>>>(S->r.as<double2>(), n, st, part);
+        c->launches++;
+        PG_TRY(read_state(c, &hs));
+        const double rate = sqrt(hs.rnorm2) / bnorm / prev_relres;
+        if (prev_learned && !(rate < jacobi_rate)) {
+          // the learned cycle just run did no better than a Jacobi cycle: undo it, stay with Jacobi
+          PG_CUDA(cudaMemcpyAsync(S->u.ptr, S->usave.ptr, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+          PG_TRY(residual());
+          want_learned = false;
+          fell_back = 1;
+        } else if (!prev_learned && jacobi_rate < 0.0) {
+          jacobi_rate = rate;
+        }
+      }
+      learned = want_learned && jacobi_rate >= 0.0;
+      if (learned) PG_CUDA(cudaMemcpyAsync(S->usave.ptr, S->u.ptr, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
       const int mj = (int)std::min<int64_t>(m, std::max<int64_t>(o.max_iters - iters, 0));
       const double tol_abs = o.tol * bnorm;
+      // Learned cycles always re-orthogonalise: the network's directions can be nearly dependent.
+      const int orth = learned ? PETGEM_ORTH_CGS2 : o.orth;
       // A cycle whose starting residual already meets tol runs no iteration (k = 0).
       if (o.precision == PETGEM_PREC_MIXED)
-        PG_TRY(run_cycle<float2>(c, S->ahat64.as<float2>(), mj, o.orth, tol_abs, o.inner_tol, learned, &hs));
+        PG_TRY(run_cycle<float2>(c, S->ahat64.as<float2>(), mj, orth, tol_abs, o.inner_tol, learned, &hs));
       else
-        PG_TRY(run_cycle<double2>(c, S->ahat128.as<double2>(), mj, o.orth, tol_abs, 0.0, learned, &hs));
-      relres = sqrt(hs.rnorm2) / bnorm;  // FP64 residual of the current u
+        PG_TRY(run_cycle<double2>(c, S->ahat128.as<double2>(), mj, orth, tol_abs, 0.0, learned, &hs));
+      relres = sqrt(hs.rnorm2) / bnorm;  // FP64 residual of u before this cycle's update
       if (!isfinite(relres)) {
         status = PETGEM_ERR_BREAKDOWN;
         break;
@@ -832,11 +864,7 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
       iters += hs.k;
       cycles += 1;
       reorth += hs.n_refine;
-      // Fallback: a learned cycle that cut the FP64 residual by less than 1 % hands over to Jacobi.
-      if (learned && cycles > 1 && relres > 0.99 * prev_relres) {
-        learned = false;
-        fell_back = 1;
-      }
+      prev_learned = learned;
       prev_relres = relres;
       if (hs.done == 2) {  // u was left as it was before this cycle
         status = hs.timeout ? PETGEM_ERR_TIMEOUT : PETGEM_ERR_BREAKDOWN;

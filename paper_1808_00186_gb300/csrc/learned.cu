@@ -1,8 +1,10 @@
 // Learned preconditioner: a small 4-level 3-D convolutional network on the structured grid of a
 // Kuhn-split lattice (one grid node per mesh node, seven edge classes per node), trained on the
-// GPU with the library's own tensor-core kernels, applied as z = r + s N(r / s) inside FGMRES in
-// the Jacobi-scaled variables (so N = 0 is exactly Jacobi).  Not part of the paper: the paper
-// solves with GMRES / SQMR / MUMPS (Sections 5.1-5.3); the plain solver stays the fallback.
+// GPU with the library's own tensor-core kernels to predict the direction of the exact correction
+// Ahat^{-1} r from the residual r (Jacobi-scaled variables).  Inside flexible GMRES its output
+// z = s N(r / s) is used on every other Arnoldi step, the Jacobi step z = r on the others, so the
+// Krylov space holds both kinds of directions.  Not part of the paper: the paper solves with
+// GMRES / SQMR / MUMPS (Sections 5.1-5.3); the plain solver stays the fallback.
 //
 // Network (levels G0 = lattice nodes, G1..G3 = successive 2x poolings, BF16 activations, FP32
 // accumulation and master weights):
@@ -27,7 +29,7 @@ namespace petgem {
 namespace nn {
 namespace {
 
-constexpr int kIn = 16, kOut = 14;
+constexpr int kIn = 16;
 
 __global__ void k_f32_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -195,20 +197,22 @@ __global__ void k_pack_input(const float* __restrict__ g32, const float* __restr
   const int64_t v = i / kIn;
   x[i] = __float2bfloat16(c < 14 ? g32[i] : feat[2 * v + (c - 14)]);
 }
-// z_e = r_e + s * y[slot] (complex: Re from class c, Im from class 7 + c)
+// z_e = s * y[slot] (complex: Re from class c, Im from class 7 + c)
 template <typename T>
-__global__ void k_from_grid(const T* __restrict__ r, const float* __restrict__ y, const int32_t* __restrict__ slot,
-                            int64_t E, const float* __restrict__ s_ptr, T* __restrict__ z) {
+__global__ void k_from_grid(const float* __restrict__ y, const int32_t* __restrict__ slot, int64_t E,
+                            const float* __restrict__ s_ptr, T* __restrict__ z) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= E) return;
   const int32_t sl = slot[e];
-  T out = r[e];
+  T out;
+  out.x = 0;
+  out.y = 0;
   if (sl >= 0) {
     const int64_t v = sl / 7;
     const int c = sl - (int)(v * 7);
     const float s = *s_ptr;
-    out.x += s * y[v * 16 + c];
-    out.y += s * y[v * 16 + 7 + c];
+    out.x = s * y[v * 16 + c];
+    out.y = s * y[v * 16 + 7 + c];
   }
   z[e] = out;
 }
@@ -229,46 +233,6 @@ __global__ void k_rms(const T* __restrict__ r, int64_t E, float* __restrict__ ou
     if (!(s > 0.0)) s = 1.0;
     out[0] = (float)(1.0 / s);
     out[1] = (float)s;
-  }
-}
-// Training target on the grid: (u* - u_k) / s - r / s, i.e. what N must add to the Jacobi step.
-__global__ void k_target_grid(const double2* __restrict__ du, const double2* __restrict__ r,
-                              const int32_t* __restrict__ slot, int64_t E, const float* __restrict__ inv_s,
-                              float* __restrict__ t32) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= E) return;
-  const int32_t sl = slot[e];
-  if (sl < 0) return;
-  const int64_t v = sl / 7;
-  const int c = sl - (int)(v * 7);
-  const float f = *inv_s;
-  t32[v * 16 + c] = (float)(du[e].x - r[e].x) * f;
-  t32[v * 16 + 7 + c] = (float)(du[e].y - r[e].y) * f;
-}
-// loss += 0.5 sum (y - t)^2 / count over the 14 output channels; dy = (y - t) / count (BF16).
-__global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, int64_t V, double inv_count,
-                      __nv_bfloat16* __restrict__ dy, double* __restrict__ loss_part) {
-  __shared__ double red[256];
-  double a = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V * 16; i += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % 16);
-    float d = c < kOut ? y[i] - t[i] : 0.f;
-    a += 0.5 * (double)d * d;
-    dy[i] = __float2bfloat16((float)(d * inv_count));
-  }
-  red[threadIdx.x] = a;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0] * inv_count;
-}
-__global__ void k_sum(const double* __restrict__ a, int n, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += a[i];
-    *out += s;
   }
 }
 // Adam (Kingma & Ba 2015) on FP32 master weights.
@@ -295,6 +259,87 @@ __global__ void k_res_err(const int64_t* __restrict__ rp, const int32_t* __restr
   r[i] = acc;
   du[i] = cmul(d[i], csub(xs[i], x[i]));
 }
+
+// w = Ahat z = A D^{-1} z (complex128, one thread per row).
+__global__ void k_ahat_apply(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                             const double2* __restrict__ val, const double2* __restrict__ d,
+                             const double2* __restrict__ z, int64_t n, double2* __restrict__ w) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+    const int32_t j = col[p];
+    acc = cadd(acc, cmul(val[p], cdiv(z[j], d[j])));
+  }
+  w[i] = acc;
+}
+// g = Ahat^H y = conj(D)^{-1} conj(A) y (A complex symmetric).
+__global__ void k_ahat_adjoint(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                               const double2* __restrict__ val, const double2* __restrict__ d,
+                               const double2* __restrict__ y, int64_t n, double2* __restrict__ g) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) acc = cadd(acc, cconjmul(val[p], y[col[p]]));
+  g[i] = cdiv(acc, make_double2(d[i].x, -d[i].y));
+}
+// dv = (<r, w>, |w|^2, |r|^2) in FP64 (one block), and loss += 1 - |<r,w>|^2 / (|w|^2 |r|^2).
+__global__ void k_angle_dots(const double2* __restrict__ r, const double2* __restrict__ w, int64_t n,
+                             double* __restrict__ dv, double* __restrict__ loss) {
+  __shared__ double red[4][1024];
+  double ax = 0.0, ay = 0.0, b = 0.0, c = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double2 ri = r[i], wi = w[i];
+    ax += ri.x * wi.x + ri.y * wi.y;
+    ay += ri.x * wi.y - ri.y * wi.x;
+    b += wi.x * wi.x + wi.y * wi.y;
+    c += ri.x * ri.x + ri.y * ri.y;
+  }
+  red[0][threadIdx.x] = ax;
+  red[1][threadIdx.x] = ay;
+  red[2][threadIdx.x] = b;
+  red[3][threadIdx.x] = c;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 4; ++q) dv[q] = red[q][0];
+    const double bc = red[2][0] * red[3][0];
+    *loss += bc > 0.0 ? 1.0 - (red[0][0] * red[0][0] + red[1][0] * red[1][0]) / bc : 1.0;
+  }
+}
+// dL/dw (real and imaginary parts as one complex number): -2 (a r / (c b) - |a|^2 w / (c b^2)).
+__global__ void k_angle_gw(const double2* __restrict__ r, const double2* __restrict__ w, int64_t n,
+                           const double* __restrict__ dv, double2* __restrict__ gw) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 a = make_double2(dv[0], dv[1]);
+  const double b = dv[2], c = dv[3];
+  if (!(b > 0.0 && c > 0.0)) {
+    gw[i] = make_double2(0.0, 0.0);
+    return;
+  }
+  const double a2 = a.x * a.x + a.y * a.y;
+  const double2 t1 = cscale(cmul(a, r[i]), 1.0 / (c * b));
+  const double2 t2 = cscale(w[i], a2 / (c * b * b));
+  gw[i] = cscale(csub(t1, t2), -2.0);
+}
+// dy on the grid (BF16): Re / Im of the edge gradient on the edge's slot, zero elsewhere.
+__global__ void k_grad_to_grid(const double2* __restrict__ gz, const int32_t* __restrict__ slot, int64_t E,
+                               __nv_bfloat16* __restrict__ dy) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int32_t sl = slot[e];
+  if (sl < 0) return;
+  const int64_t v = sl / 7;
+  const int c = sl - (int)(v * 7);
+  dy[v * 16 + c] = __float2bfloat16((float)gz[e].x);
+  dy[v * 16 + 7 + c] = __float2bfloat16((float)gz[e].y);
+}
+__global__ void k_set_one(float* p) { *p = 1.0f; }
 
 unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
@@ -407,10 +452,8 @@ Status Net::init(petgem_ctx* c, int nx_, int ny_, int nz_) {
   PG_TRY(act(dp1, 1, 16));
   PG_TRY(y.reserve((size_t)V[0] * 16 * sizeof(float)));
   PG_TRY(g32.reserve((size_t)V[0] * 16 * sizeof(float)));
-  PG_TRY(t32.reserve((size_t)V[0] * 16 * sizeof(float)));
   PG_TRY(feat.reserve((size_t)V[0] * 2 * sizeof(float)));
   PG_TRY(scal.reserve(16 * sizeof(float)));
-  PG_TRY(loss_part.reserve(1024 * sizeof(double)));
   PG_TRY(loss_acc.reserve(sizeof(double)));
   PG_TRY(err.reserve(sizeof(int)));
   PG_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
@@ -521,7 +564,7 @@ template <typename T>
 Status Net::apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T* z) {
   PG_TRY(load_input(s, r, slot, E));
   PG_TRY(forward(s));
-  k_from_grid<T><<<nb(E), 256, 0, s>>>(r, y.as<float>(), slot, E, scal.as<float>() + 1, z);
+  k_from_grid<T><<<nb(E), 256, 0, s>>>(y.as<float>(), slot, E, scal.as<float>() + 1, z);
   PG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -529,17 +572,26 @@ Status Net::apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T*
 template Status Net::apply<float2>(cudaStream_t, const float2*, const int32_t*, int64_t, float2*);
 template Status Net::apply<double2>(cudaStream_t, const double2*, const int32_t*, int64_t, double2*);
 
-// One sample: r = Jacobi-scaled residual, du = D (x* - x_k) (both complex128 edge vectors).
-Status Net::sample_grad(cudaStream_t s, const double2* r, const double2* du, const int32_t* slot, int64_t E, bool acc) {
+// One training sample, r = the residual of a solver iterate (complex128 edge vector).  Loss: the
+// residual angle L = 1 - |<r, Ahat z>|^2 / (|r|^2 |Ahat z|^2) of the network's direction z
+// (scale-free, as flexible GMRES is), back-propagated through Ahat^H to the grid.
+Status Net::sample_grad(cudaStream_t s, petgem_ctx* c, const double2* r, const int32_t* slot, int64_t E, bool acc) {
   PG_TRY(load_input(s, r, slot, E));
-  PG_CUDA(cudaMemsetAsync(t32.ptr, 0, (size_t)V[0] * 16 * sizeof(float), s));
-  k_target_grid<<<nb(E), 256, 0, s>>>(du, r, slot, E, scal.as<float>(), t32.as<float>());
   PG_TRY(forward(s));
-  const int blocks = (int)std::min<int64_t>(1024, nb(V[0] * 16));
-  // mean over the slots that carry edges: 14 channels of every node
-  k_mse<<<blocks, 256, 0, s>>>(y.as<float>(), t32.as<float>(), V[0], 1.0 / ((double)V[0] * kOut),
-                               dy.as<__nv_bfloat16>(), loss_part.as<double>());
-  k_sum<<<1, 32, 0, s>>>(loss_part.as<double>(), blocks, loss_acc.as<double>());
+  double2* z = dutmp.as<double2>();
+  double2* w = wtmp.as<double2>();
+  double2* gw = gtmp.as<double2>();
+  k_set_one<<<1, 1, 0, s>>>(scal.as<float>() + 4);
+  k_from_grid<double2><<<nb(E), 256, 0, s>>>(y.as<float>(), slot, E, scal.as<float>() + 4, z);
+  k_ahat_apply<<<nb(E), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(),
+                                     c->diag.as<double2>(), z, E, w);
+  k_angle_dots<<<1, 1024, 0, s>>>(r, w, E, dvec.as<double>(), loss_acc.as<double>());
+  k_angle_gw<<<nb(E), 256, 0, s>>>(r, w, E, dvec.as<double>(), gw);
+  k_ahat_adjoint<<<nb(E), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(),
+                                       c->diag.as<double2>(), gw, E, z);
+  PG_CUDA(cudaMemsetAsync(dy.ptr, 0, (size_t)V[0] * 16 * sizeof(__nv_bfloat16), s));
+  k_grad_to_grid<<<nb(E), 256, 0, s>>>(z, slot, E, dy.as<__nv_bfloat16>());
+  PG_CUDA(cudaGetLastError());
   PG_TRY(backward(s, acc));
   return Status{};
 }

@@ -23,7 +23,7 @@ struct Net {
   DevBuf params, grads, adam_m, adam_v, wb, wd, zbias;
   DevBuf x0, a1, p1, a2, p2, a3, p3, a4, s5, a5, s6, a6, s7, y;
   DevBuf dy, ds7, da6, ds6, da5, ds5, da4, dp3, dp2, dp1;
-  DevBuf g32, t32, feat, scal, loss_part, loss_acc, err, wpart, rtmp, dutmp;
+  DevBuf g32, feat, scal, loss_acc, err, wpart, rtmp, dutmp, wtmp, gtmp, dvec;
 
   Status init(petgem_ctx* c, int nx, int ny, int nz);
   Status pack_weights(cudaStream_t s);
@@ -34,7 +34,7 @@ struct Net {
   Status backward(cudaStream_t s, bool acc);
   template <typename T> Status load_input(cudaStream_t s, const T* r, const int32_t* slot, int64_t E);
   template <typename T> Status apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T* z);
-  Status sample_grad(cudaStream_t s, const double2* r, const double2* du, const int32_t* slot, int64_t E, bool acc);
+  Status sample_grad(cudaStream_t s, petgem_ctx* c, const double2* r, const int32_t* slot, int64_t E, bool acc);
   Status adam_step(cudaStream_t s, float lr, float gscale);
   Status features(cudaStream_t s, const double* sigma, double sigma_p, double omega, double h);
 };

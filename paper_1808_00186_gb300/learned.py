@@ -5,8 +5,8 @@ seven convolutions c1..c7 in order, W[27][cout][cin] then b[cout], with (cin, co
 (16,16), (16,32), (32,32), (32,32), (32,32), (32,16), (16,16).  Output channels 14, 15 of c7 are
 padding and stay zero.
 
-Training pairs come from the plain solver: the iterate x_k at the start of every GMRES cycle and the
-converged solution x*; the library turns each into (residual, target correction) on the grid.
+Training samples come from the plain solver: the iterate x_k at the start of every GMRES cycle; the
+library turns each into its residual and trains the network's direction on the residual angle.
 """
 from __future__ import annotations
 
@@ -33,15 +33,16 @@ def layout():
 
 
 def init_params(seed: int = 0) -> np.ndarray:
-    """He-normal weights, zero biases; the output layer starts at zero, so the untrained network
-    adds nothing and the preconditioner is exactly Jacobi."""
+    """He-normal weights, zero biases; the output layer starts small."""
     rng = np.random.default_rng(seed)
     lay, n = layout()
     p = np.zeros(n, np.float32)
     for name, w, b, ci, co in lay:
+        scale = 0.1 if name == "c7" else 1.0
+        wv = rng.normal(size=(27, co, ci)) * np.sqrt(2.0 / (27 * ci)) * scale
         if name == "c7":
-            continue
-        p[w:w + 27 * co * ci] = rng.normal(size=27 * co * ci) * np.sqrt(2.0 / (27 * ci))
+            wv[:, N_OUT:, :] = 0.0
+        p[w:w + 27 * co * ci] = wv.reshape(-1)
     return p
 
 
@@ -124,7 +125,7 @@ def train(n: int = 32, models: int = 200, epochs: int = 2, lr: float = 1e-3, see
             if first:
                 api.petgem_learned_params(ctx.h, set_params=p)
                 first = False
-            losses.append(api.petgem_learned_train_step(ctx.h, its.contiguous(), xstar.contiguous(), lr))
+            losses.append(api.petgem_learned_train_step(ctx.h, its.contiguous(), lr))
         history.append(float(np.mean(losses)))
         if log:
             log("epoch %d loss %.4e" % (ep, history[-1]))

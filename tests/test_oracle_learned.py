@@ -88,3 +88,35 @@ def test_edge_grid_map_is_injective(n):
     # every lattice direction appears, and axis edges number 3 n (n+1)^2
     cls = g % 7
     assert np.sum(cls < 3) == 3 * n * (n + 1) ** 2
+
+
+def test_angle_loss_gradient_by_finite_differences():
+    from paper_1808_00186_gb300 import synth as S
+    m = S.cube_block_model(3)
+    sysm = oracle.System(m.mesh.nodes, m.mesh.tets, m.sigma, m.sigma_p, m.freq, S.sources_array(m.sources))
+    edges, _, _, _ = sysm.topology()
+    rp, col, val, b = sysm.system()
+    diag = np.array([val[rp[i]:rp[i + 1]][col[rp[i]:rp[i + 1]] == i][0] for i in range(sysm.n_edges)])
+    slot = L.edge_grid_index(edges, 3)
+    rng = np.random.default_rng(0)
+    y = rng.normal(size=(4 ** 3, 16))
+    r = rng.normal(size=sysm.n_edges) + 1j * rng.normal(size=sysm.n_edges)
+    loss, gy = L.angle_loss(y, r, slot, sysm.spmv, diag)
+    assert 0.0 <= loss <= 1.0
+    for idx in rng.choice(y.size, 12, replace=False):
+        i, c = np.unravel_index(idx, y.shape)
+        old = y[i, c]
+        y[i, c] = old + 1e-6
+        lp, _ = L.angle_loss(y, r, slot, sysm.spmv, diag)
+        y[i, c] = old - 1e-6
+        lm, _ = L.angle_loss(y, r, slot, sysm.spmv, diag)
+        y[i, c] = old
+        assert abs((lp - lm) / 2e-6 - gy[i, c]) <= 1e-6 * max(1.0, abs(gy[i, c])), (i, c)
+    # the exact correction direction z = D A^{-1} r has zero loss
+    A = np.zeros((sysm.n_edges, sysm.n_edges), complex)
+    for i in range(sysm.n_edges):
+        A[i, col[rp[i]:rp[i + 1]]] = val[rp[i]:rp[i + 1]]
+    z = diag * np.linalg.solve(A, r)
+    yz = L.edges_to_grid(z, slot, 4 ** 3)
+    l0, _ = L.angle_loss(yz, r, slot, sysm.spmv, diag)
+    assert l0 < 1e-10
