@@ -215,6 +215,25 @@ int petgem_nn_conv3d(void *stream, int32_t gx, int32_t gy, int32_t gz, int32_t c
 int petgem_nn_conv3d_wgrad(void *stream, int32_t gx, int32_t gy, int32_t gz, int32_t cin, int32_t cout, const void *x,
                            const void *dy, float *dw);
 
+/* Allocation-free form of petgem_nn_conv3d_wgrad.  The paper has no counterpart: it is an
+ * integration entry point.  Same arguments, layouts and result (dw FP32 [27][cout][cin], device,
+ * overwritten; x, dy device, read only; work ordered on `stream`, which must belong to the
+ * current device; returns after the stream has passed the work).  For callers that cannot
+ * allocate device memory during the call (a framework whose caching allocator holds the free
+ * memory, or a step run with allocation forbidden because an allocation can wait on a lock and
+ * a release can synchronise the device): it calls no cudaMalloc, cudaMallocAsync, cudaFree or
+ * other allocating routine, and works in a fixed scratch array of the library's device code
+ * (3.4 MB per device) that holds grids of at most PETGEM_NOALLOC_MAX_VOXELS voxels.
+ *   - gx gy gz > PETGEM_NOALLOC_MAX_VOXELS, or cin / cout not in {16, 32}: PETGEM_ERR_UNSUPPORTED,
+ *     nothing launched and dw untouched.  Null pointer or a dimension < 1: PETGEM_ERR_INVALID_ARG.
+ *   - The first call on a device looks the scratch's address up (cudaGetSymbolAddress, with that
+ *     device current; PETGEM_ERR_CUDA if it fails); make that first call before any stream capture.
+ *   - All calls on a device share the scratch: calls that overlap in time (two streams, two host
+ *     threads) race on it and give wrong results.  Serialise them. */
+#define PETGEM_NOALLOC_MAX_VOXELS 131072
+int petgem_nn_conv3d_wgrad_noalloc(void *stream, int32_t gx, int32_t gy, int32_t gz, int32_t cin, int32_t cout,
+                                   const void *x, const void *dy, float *dw);
+
 /* ----------------------------------------------------------------------- measurement */
 /* Per-kernel device time recorded with CUDA events around launches while enabled.
  * petgem_profile(ctx, 1) clears and enables, 0 disables.  petgem_kernel_stats returns, for

@@ -67,6 +67,7 @@ _SIGNATURES = {
     "petgem_learned_apply": (ctypes.c_int, [_P, _P, _P]),
     "petgem_nn_conv3d": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _P, _P, _I32, _P, _I32]),
     "petgem_nn_conv3d_wgrad": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _P, _P]),
+    "petgem_nn_conv3d_wgrad_noalloc": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _P, _P]),
 }
 
 _lib = None
@@ -245,6 +246,19 @@ def petgem_nn_conv3d_wgrad(stream, grid, cin, cout, x, dy, dw):
     st = load().petgem_nn_conv3d_wgrad(stream, grid[0], grid[1], grid[2], cin, cout, _ptr(x), _ptr(dy), _ptr(dw))
     if st != OK:
         raise PetgemError(st, "petgem_nn_conv3d_wgrad")
+
+
+# Largest grid (voxels) petgem_nn_conv3d_wgrad_noalloc accepts: the size of its fixed scratch.
+NOALLOC_MAX_VOXELS = 131072
+
+
+def petgem_nn_conv3d_wgrad_noalloc(stream, grid, cin, cout, x, dy, dw):
+    """petgem_nn_conv3d_wgrad without any device allocation (fixed library scratch; calls on one
+    device must not overlap in time)."""
+    st = load().petgem_nn_conv3d_wgrad_noalloc(stream, grid[0], grid[1], grid[2], cin, cout, _ptr(x), _ptr(dy),
+                                               _ptr(dw))
+    if st != OK:
+        raise PetgemError(st, "petgem_nn_conv3d_wgrad_noalloc")
 
 
 def petgem_launch_count(ctx) -> int:

@@ -46,3 +46,14 @@ def test_no_cpu_fallback_when_library_missing(tmp_path):
             api.load(str(tmp_path / "missing.so"))
     finally:
         api._lib = saved
+
+
+def test_noalloc_limit_matches_header_and_is_checked_on_the_host(lib_path):
+    import re
+    text = open(api.HEADER).read()
+    assert int(re.search(r"#define PETGEM_NOALLOC_MAX_VOXELS (\d+)", text).group(1)) == api.NOALLOC_MAX_VOXELS
+    L = api.load(lib_path)
+    fake = ctypes.c_void_p(256)  # never dereferenced: the sizes are rejected before any CUDA call
+    assert L.petgem_nn_conv3d_wgrad_noalloc(None, 64, 64, 33, 16, 16, fake, fake, fake) == api.ERR_UNSUPPORTED
+    assert L.petgem_nn_conv3d_wgrad_noalloc(None, 8, 8, 8, 24, 16, fake, fake, fake) == api.ERR_UNSUPPORTED
+    assert L.petgem_nn_conv3d_wgrad_noalloc(None, 0, 8, 8, 16, 16, fake, fake, fake) == api.ERR_INVALID_ARG
