@@ -12,16 +12,17 @@
 #include <vector>
 
 #include "krylov.cuh"
+#include "gs.cuh"
 
 namespace petgem {
 namespace {
 
 constexpr int kBMaxP = 32;
-constexpr int kBRowsPerTile = 128;  // rows per tile of the projection kernel
 
 struct BGroup {
   unsigned counter;
   int all_done;
+  unsigned long long gbar;  // arrivals at the projection kernel's grid barrier (only grows)
 };
 
 // -------------------------------------------------------------------- layout changes
@@ -191,138 +192,6 @@ __global__ void __launch_bounds__(256) k_bcycle_init(const double2* __restrict__
   }
 }
 
-// -------------------------------------------------------------------- projections
-// h[k][s] = V_k,s^H w_s for k <= j and ||w_s||^2 (slot j + 1), w = V_{j+1}.  Thread (g, s) owns
-// source s and the slots k = g, g + G, ... (G = 256 / P), so no reduction across threads is needed
-// inside a block: each thread streams its slots' rows (the P sources of a row are contiguous, so a
-// warp reads whole rows) and keeps FP32 sums over a 128-row tile, then FP64 across tiles.
-template <typename T, int P>
-__global__ void __launch_bounds__(256) k_bmdot(const T* __restrict__ V, int64_t ldb, int64_t n, int j,
-                                               GState* __restrict__ sts, BGroup* __restrict__ grp,
-                                               double2* __restrict__ partials) {
-  if (grp->all_done) return;
-  constexpr int G = 256 / P;                  // slot groups
-  constexpr int kSlots = (kMaxM + 2 + G - 1) / G;
-  const int tid = threadIdx.x, s = tid % P, g = tid / P;
-  const int nk = j + 2;                       // slots 0..j and j + 1
-  const int ns = g < nk ? (nk - 1 - g) / G + 1 : 0;  // this thread's slot count
-  const T* W = V + (int64_t)(j + 1) * ldb;
-  double2 acc[kSlots];
-#pragma unroll
-  for (int q = 0; q < kSlots; ++q) acc[q] = make_double2(0.0, 0.0);
-  const int64_t tiles = (n + kBRowsPerTile - 1) / kBRowsPerTile;
-  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int64_t r0 = t * kBRowsPerTile, r1 = min(n, r0 + kBRowsPerTile);
-#pragma unroll
-    for (int q = 0; q < kSlots; ++q) {
-      if (q >= ns) break;
-      const T* Vk = V + (int64_t)(g + q * G) * ldb;
-      typename Acc<T>::type a = zero<T>(), b = zero<T>();
-      int64_t r = r0;
-      for (; r + 8 <= r1; r += 8) {  // 16 independent loads in flight per thread
-        T v[8], w[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          v[u] = Vk[(r + u) * P + s];
-          w[u] = W[(r + u) * P + s];
-        }
-#pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-          fma_conj(a, v[u], w[u]);
-          fma_conj(b, v[u + 1], w[u + 1]);
-        }
-      }
-      for (; r < r1; ++r) fma_conj(a, Vk[r * P + s], W[r * P + s]);
-      acc[q] = cadd(acc[q], to_d2(a));
-      acc[q] = cadd(acc[q], to_d2(b));
-    }
-  }
-  const int stride = (kMaxM + 2) * P;
-#pragma unroll
-  for (int q = 0; q < kSlots; ++q)
-    if (q < ns) partials[(int64_t)blockIdx.x * stride + (g + q * G) * P + s] = acc[q];
-  if (!last_block(&grp->counter)) return;
-  for (int idx = tid; idx < nk * P; idx += 256) {
-    double2 sum = make_double2(0.0, 0.0), sum2 = make_double2(0.0, 0.0);
-    unsigned b = 0;
-    for (; b + 1 < gridDim.x; b += 2) {  // two loads in flight
-      sum = cadd(sum, __ldcg(&partials[(int64_t)b * stride + idx]));
-      sum2 = cadd(sum2, __ldcg(&partials[(int64_t)(b + 1) * stride + idx]));
-    }
-    if (b < gridDim.x) sum = cadd(sum, __ldcg(&partials[(int64_t)b * stride + idx]));
-    sum = cadd(sum, sum2);
-    const int k = idx / P, ss = idx - k * P;
-    GState* st = &sts[ss];
-    if (k <= j) {
-      const double ib = st->inv_beta[k];
-      const double2 h = cscale(sum, ib);
-      st->h[k] = h;
-      st->c[k] = cscale(h, ib);
-    } else {
-      st->nrm_w = sum.x;
-    }
-  }
-  __syncthreads();
-  if (tid == 0) grp->counter = 0;
-}
-
-// -------------------------------------------------------------------- update + column
-// w_s -= sum_k V_k,s c_k,s; ||w_s||^2; the last block finishes every live source's Hessenberg
-// column (Givens rotations and stopping test) and the group flag.
-template <typename T, int P>
-__global__ void __launch_bounds__(256) k_bmupdate(T* __restrict__ V, int64_t ldb, int64_t n, int j,
-                                                  GState* __restrict__ sts, BGroup* __restrict__ grp,
-                                                  double2* __restrict__ partials) {
-  if (grp->all_done) return;
-  __shared__ T cs[(kMaxM + 1) * P];
-  __shared__ double red[256];
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < (j + 1) * P; idx += 256) {
-    const int k = idx / P, ss = idx - k * P;
-    cs[idx] = from_d2<T>(sts[ss].c[k]);
-  }
-  __syncthreads();
-  T* W = V + (int64_t)(j + 1) * ldb;
-  double nrm = 0.0;
-  const int64_t total = n * P;
-  for (int64_t e = blockIdx.x * (int64_t)256 + tid; e < total; e += (int64_t)gridDim.x * 256) {
-    const int s = (int)(e % P);  // == tid % P: the grid stride is a multiple of P
-    T w = W[e], w2 = zero<T>();
-    int k = 0;
-    for (; k + 1 <= j; k += 2) {
-      sub_mul(w, V[(int64_t)k * ldb + e], cs[k * P + s]);
-      sub_mul(w2, V[(int64_t)(k + 1) * ldb + e], cs[(k + 1) * P + s]);
-    }
-    if (k <= j) sub_mul(w, V[(int64_t)k * ldb + e], cs[k * P + s]);
-    w.x += w2.x;
-    w.y += w2.y;
-    W[e] = w;
-    nrm += (double)nrm2(w);
-  }
-  red[tid] = nrm;
-  __syncthreads();
-  if (tid < P) {
-    double sum = 0.0;
-    for (int m = tid; m < 256; m += P) sum += red[m];
-    partials[(int64_t)blockIdx.x * P + tid] = make_double2(sum, 0.0);
-  }
-  if (!last_block(&grp->counter)) return;
-  __shared__ double2 red2[256];
-  __shared__ double2 fin[kBMaxP];
-  source_sums<P>(partials, gridDim.x, red2, fin);
-  if (tid < P) {
-    GState* st = &sts[tid];
-    if (st->done == 0) finish_column(st, j, st->h, fin[tid].x);
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int alive = 0;
-    for (int s = 0; s < P; ++s) alive += sts[s].done == 0;
-    grp->all_done = alive == 0;
-    grp->counter = 0;
-  }
-}
-
 // One warp per source: y = H^{-1} g for that source's cycle.
 __global__ void k_bbacksolve(GState* sts) { backsolve_warp(&sts[threadIdx.x >> 5], threadIdx.x & 31); }
 
@@ -384,11 +253,10 @@ Status run_group(petgem_ctx* c, const petgem_solve_opts& o, const double2* b, do
   PG_TRY(S->bstates.reserve(P * sizeof(GState)));
   PG_TRY(S->bgroup.reserve(sizeof(BGroup)));
   PG_TRY(S->btol.reserve(2 * P * sizeof(double)));
-  const int grid_dot = std::max(1, std::min<int>((int)((n + kBRowsPerTile - 1) / kBRowsPerTile), 4 * S->sms));
+  PG_TRY((gs_setup<T, P>()));
   const unsigned grid_init = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_for(n * P, 256), 8 * S->sms));
-  const unsigned grid_upd = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_for(n * P, 256), 8 * S->sms));
-  const size_t part_rows = std::max<size_t>({(size_t)grid_dot * (kMaxM + 2) * P, (size_t)grid_init * P,
-                                             (size_t)grid_upd * P});
+  const size_t part_rows = std::max<size_t>({(size_t)kDotBlocksPerSM * S->sms * kPStride * P, (size_t)grid_init * P,
+                                             (size_t)pupd_grid(n, P, S->sms) * P});
   PG_TRY(S->partials.reserve(part_rows * sizeof(double2)));
   PG_CUDA(cudaMemsetAsync(S->bstates.ptr, 0, P * sizeof(GState), s));
   PG_CUDA(cudaMemsetAsync(S->bgroup.ptr, 0, sizeof(BGroup), s));
@@ -440,11 +308,12 @@ Status run_group(petgem_ctx* c, const petgem_solve_opts& o, const double2* b, do
       }
       {
         KernelTimer kt(c, sizeof(T) == 8 ? "bmdot_c64" : "bmdot_c128", (double)(j + 2) * n * P * sizeof(T));
-        k_bmdot<T, P><<<grid_dot, 256, 0, s>>>(V, ldb, n, j, sts, grp, part);
+        PG_TRY((launch_pdot<T, P>(s, S->sms, V, ldb, n, j, sts, &grp->all_done, &grp->gbar, part, 0, 0)));
       }
       {
         KernelTimer kt(c, sizeof(T) == 8 ? "bmupdate_c64" : "bmupdate_c128", (double)(j + 3) * n * P * sizeof(T));
-        k_bmupdate<T, P><<<grid_upd, 256, 0, s>>>(V, ldb, n, j, sts, grp, part);
+        PG_TRY((launch_pupd<T, P>(s, S->sms, V, ldb, n, j, sts, &grp->all_done, &grp->counter, part, 0, 0, 0.0,
+                                  1)));
       }
       c->launches += 3;
     }

@@ -8,21 +8,22 @@
 //   c128: Krylov vectors and Ahat in complex128, all arithmetic FP64.
 //   mixed: Krylov vectors and Ahat in complex64; every cycle restarts from the residual
 //     b - Ahat u computed in FP64 with u in complex128 (iterative refinement: each GMRES cycle
-//     solves for a correction, added to u in FP64).  Dot products take FP32 products over 8
-//     rows per thread and sum everything across threads in FP64.
+//     solves for a correction, added to u in FP64).  Dot products take FP32 products over a
+//     thread's 8 elements and its warp (256 elements) and sum everything beyond in FP64.
 //
-// Arnoldi with classical Gram-Schmidt and a conditional second pass: after w <- w - V (V^H w),
-// the pass is repeated when ||w|| fell below eta * ||w_before|| (eta = 1/sqrt(2)).
-// Each Krylov vector V_k is stored unnormalised with its scale 1/||V_k|| on the device, so no
-// separate normalisation pass is needed.  The Hessenberg column, its Givens rotations and the
-// stopping test run in the last block of each reduction kernel: a cycle of m iterations needs
-// no host synchronisation, and kernels after the stop return at once.
+// Arnoldi with classical Gram-Schmidt (gs.cuh): one projection pass and one update pass (CGS, the
+// default), two of each (CGS2), or a second pair only when ||w|| fell below eta * ||w_before||
+// (eta = 1/sqrt(2)).  Each Krylov vector V_k is stored unnormalised with its scale 1/||V_k|| on
+// the device, so no separate normalisation pass is needed.  The Hessenberg column, its Givens
+// rotations and the stopping test run in the last block of the update kernel: a cycle of m
+// iterations needs no host synchronisation, and kernels after the stop return at once.
 #include <math.h>
 
 #include <algorithm>
 
 #include "krylov.cuh"
 #include "learned.cuh"
+#include "gs.cuh"
 
 namespace petgem {
 
@@ -146,364 +147,6 @@ __global__ void __launch_bounds__(kT) k_cycle_init(const double2* __restrict__ r
   }
 }
 
-// ------------------------------------------------------------------ TMA-staged Gram-Schmidt
-// One persistent kernel, three modes, for classical Gram-Schmidt with one re-orthogonalisation
-// (CGS2) of w = V_{j+1} against V_0..V_j:
-//   mode 0: h1 = V^H w, ||w||^2
-//   mode 1: w <- w - V c1 (c1 = h1 scaled), then h2 = V^H w on the updated w
-//   mode 2: w <- w - V c2, ||w||^2; the last block finishes the Hessenberg column
-// so V is read three times per Arnoldi step.  Each block walks row tiles; for a tile, one thread
-// issues a 1-D bulk copy (cp.async.bulk, completion on an mbarrier) of every vector's 2 KB slice
-// into shared memory, double-buffered so the next tile streams in while this one is used.  Rows
-// per tile: 128 (complex64) or 64 (complex128).  ld is a multiple of 256 elements, so every slice
-// is whole and 16-byte aligned; rows >= n are zero padding.  Two blocks per SM hide each other's
-// waits; each block double-buffers its own tiles.
-constexpr int kMaxSlice = 2048;   // largest per-vector slice of a row tile (bytes)
-constexpr int kSlicePad = 16;     // pad between slices: shifts shared-memory banks, keeps 16-byte alignment
-constexpr int kMaxStages = 4;
-constexpr int kCgsThreads = 256;
-constexpr int kCgsBlocksPerSM = 2;
-// Dynamic shared memory per block: two blocks per SM must fit in the SM's 228 KB together with
-// their ~5 KB of static shared memory and the 1 KB each block reserves.
-constexpr int kCgsDynSmem = 105 * 1024;
-constexpr int kCgsRedBytes = (kCgsThreads / 32) * 64 * 16;  // end-of-kernel reduction, aliased on the stages
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s: no copy takes that long
-
-// Slice size and stage count for nv staged vectors: 1 KB slices, double-buffered (the fastest
-// measured shape on this GPU; deeper staging with smaller slices lost more to per-tile overhead).
-struct CgsShape {
-  int slice, stages;
-};
-inline CgsShape cgs_shape(int nv) {
-  const int st = kCgsDynSmem / (nv * (1024 + kSlicePad));
-  return CgsShape{1024, st >= 2 ? 2 : 1};
-}
-
-// ------------------------------------------------------------------ projections (dot pass)
-// h = V^H w and ||w||^2 for w = V_{j+1}: each thread keeps kR rows of w in registers and streams
-// the basis two vectors at a time (2 kR independent loads in flight), high occupancy.  complex64:
-// FP32 products over the thread's rows and an FP32 tree over the warp (256 rows); the warp totals
-// are turned into FP64 only at the end, and everything across warps and blocks is FP64.
-template <typename T>
-__global__ void __launch_bounds__(kT) k_mdot(const T* __restrict__ V, int64_t ld, int64_t n, int j,
-                                             GState* __restrict__ st, double2* __restrict__ partials) {
-  if (st->done) return;
-  using A = typename Acc<T>::type;
-  __shared__ A red[kMaxM + 2][kT / 32];
-  __shared__ double2 fin[kMaxM + 2];
-  const int nk = j + 1, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const T* w = V + (int64_t)(j + 1) * ld;
-  const int64_t base = blockIdx.x * (int64_t)kRows + threadIdx.x;
-  T wr[kR];
-#pragma unroll
-  for (int q = 0; q < kR; ++q) {
-    const int64_t i = base + (int64_t)q * kT;
-    wr[q] = i < n ? w[i] : zero<T>();
-  }
-  auto warp_tree = [&](A a) {
-    for (int o = 16; o > 0; o >>= 1) {
-      a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
-      a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
-    }
-    return a;
-  };
-  {
-    A a = zero<T>();
-#pragma unroll
-    for (int q = 0; q < kR; ++q) a.x += nrm2(wr[q]);
-    a = warp_tree(a);
-    if (lane == 0) red[nk][wid] = a;
-  }
-  int k = 0;
-  for (; k + 1 < nk; k += 2) {
-    const T* v0 = V + (int64_t)k * ld;
-    const T* v1 = v0 + ld;
-    T a0[kR], a1[kR];
-#pragma unroll
-    for (int q = 0; q < kR; ++q) {
-      const int64_t i = base + (int64_t)q * kT;
-      a0[q] = i < n ? v0[i] : zero<T>();
-      a1[q] = i < n ? v1[i] : zero<T>();
-    }
-    A s0 = zero<T>(), s1 = zero<T>();
-#pragma unroll
-    for (int q = 0; q < kR; ++q) {
-      fma_conj(s0, a0[q], wr[q]);
-      fma_conj(s1, a1[q], wr[q]);
-    }
-    s0 = warp_tree(s0);
-    s1 = warp_tree(s1);
-    if (lane == 0) {
-      red[k][wid] = s0;
-      red[k + 1][wid] = s1;
-    }
-  }
-  for (; k < nk; ++k) {
-    const T* v0 = V + (int64_t)k * ld;
-    A s0 = zero<T>();
-#pragma unroll
-    for (int q = 0; q < kR; ++q) {
-      const int64_t i = base + (int64_t)q * kT;
-      if (i < n) fma_conj(s0, v0[i], wr[q]);
-    }
-    s0 = warp_tree(s0);
-    if (lane == 0) red[k][wid] = s0;
-  }
-  __syncthreads();
-  for (int kk = threadIdx.x; kk <= nk; kk += kT) {
-    double2 sum = make_double2(0.0, 0.0);
-    for (int ww = 0; ww < kT / 32; ++ww) sum = cadd(sum, to_d2(red[kk][ww]));
-    partials[(int64_t)blockIdx.x * kPStride + kk] = sum;
-  }
-  if (!last_block(&st->counter)) return;
-  reduce_partials(partials, gridDim.x, nk + 1, fin);
-  for (int kk = threadIdx.x; kk < nk; kk += kT) {
-    const double ib = st->inv_beta[kk];
-    const double2 h = cscale(fin[kk], ib);  // v_k^H w with v_k = V_k / ||V_k||
-    st->h[kk] = h;
-    st->c[kk] = cscale(h, ib);              // w -= V_k * (h_k / ||V_k||)
-  }
-  if (threadIdx.x == 0) {
-    st->nrm_w = fin[nk].x;
-    st->counter = 0;
-  }
-}
-
-__device__ inline unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ inline void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ inline void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ inline bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ inline unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Bounded wait: false if the phase did not complete within kWaitLimitNs.
-__device__ inline bool mbar_wait(uint64_t* bar, unsigned parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > kWaitLimitNs) return false;
-  return true;
-}
-__device__ inline void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(dst)),
-               "l"(src), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
-}
-
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kCgsThreads, kCgsBlocksPerSM) k_cgs(T* __restrict__ V, int64_t ld, int64_t n, int j,
-                                                        GState* __restrict__ st, double2* __restrict__ partials,
-                                                        int n_tiles, int slice, int n_stages, int pass,
-                                                        int need_refine, double eta2) {
-  if (st->done || (need_refine && !st->refine)) return;
-  extern __shared__ __align__(128) unsigned char stage_mem[];
-  __shared__ uint64_t bar[kMaxStages];
-  __shared__ T cs[kMaxM + 1];
-  __shared__ double2 fin[kMaxM + 2];
-  __shared__ __align__(16) unsigned char wraw[kMaxSlice];  // updated w of the tile (never a copy target)
-  __shared__ bool aborted;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr int nwarps = kCgsThreads / 32;
-  T* wbuf = (T*)wraw;
-  const int TR = slice / (int)sizeof(T);  // rows per tile: 32..256, a power of two
-  const int stride = slice + kSlicePad;
-  const int nv = j + 2;                   // staged slices: V_0..V_j and w = V_{j+1}
-  const size_t stage_bytes = (size_t)nv * stride;
-  const int my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  if (tid == 0) {
-    for (int i = 0; i < n_stages; ++i) mbar_init(&bar[i], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    aborted = false;
-  }
-  if (MODE != 0)
-    for (int k = tid; k <= j; k += kCgsThreads) cs[k] = from_d2<T>(st->c[k]);
-  __syncthreads();
-  auto issue = [&](int it) {
-    const int sidx = it % n_stages;
-    const int64_t r0 = (int64_t)(blockIdx.x + (int64_t)it * gridDim.x) * TR;
-    unsigned char* base = stage_mem + sidx * stage_bytes;
-    mbar_expect_tx(&bar[sidx], (unsigned)(nv * slice));
-    for (int k = 0; k < nv; ++k) bulk_g2s(base + (size_t)k * stride, V + (int64_t)k * ld + r0, slice, &bar[sidx]);
-  };
-  if (tid == 0)
-    for (int it = 0; it < n_stages && it < my_tiles; ++it) issue(it);
-  // Update mode: one thread per row (threads beyond TR rows idle: fewer instructions measured faster
-  // than sharing a row between threads).
-  const int split = 1;
-  const int urow = tid, usub = 0;
-  typename Acc<T>::type a_hi = zero<T>();
-  typename Acc<T>::type f0 = zero<T>(), f1 = zero<T>();  // FP32 (complex64) running sums of the slots
-  double2 acc0 = make_double2(0.0, 0.0), acc1 = make_double2(0.0, 0.0);
-  double nrm = 0.0;
-  const int k0 = lane, k1 = lane + 32;
-  const bool has0 = k0 <= j + 1, has1 = k1 <= j + 1;
-  for (int it = 0; it < my_tiles; ++it) {
-    const int sidx = it % n_stages;
-    const unsigned parity = (unsigned)((it / n_stages) & 1);
-    if (!mbar_wait(&bar[sidx], parity)) aborted = true;
-    __syncthreads();
-    if (aborted) break;
-    // Staged slices are only ever written by the bulk copies; the updated w goes to wbuf.
-    const unsigned char* base = stage_mem + sidx * stage_bytes;
-    const T* ws = (const T*)(base + (size_t)(j + 1) * stride);
-    const int64_t r0 = (int64_t)(blockIdx.x + (int64_t)it * gridDim.x) * TR;
-    if (MODE != 0) {  // w -= sum_k V_k c_k, rows over threads (split threads per row for short tiles)
-      if (urow < TR) {
-        T w = usub == 0 ? ws[urow] : zero<T>(), w2 = zero<T>();
-        int k = usub;
-        for (; k + split <= j; k += 2 * split) {  // two independent chains
-          sub_mul(w, ((const T*)(base + (size_t)k * stride))[urow], cs[k]);
-          sub_mul(w2, ((const T*)(base + (size_t)(k + split) * stride))[urow], cs[k + split]);
-        }
-        if (k <= j) sub_mul(w, ((const T*)(base + (size_t)k * stride))[urow], cs[k]);
-        w.x += w2.x;
-        w.y += w2.y;
-        for (int o = 1; o < split; o <<= 1) {  // the split threads are adjacent lanes
-          w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
-          w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
-        }
-        const int64_t r = r0 + urow;
-        if (usub == 0) {
-          if (r < n) {
-            V[(int64_t)(j + 1) * ld + r] = w;
-            if (MODE == 2) a_hi.x += nrm2(w);
-          }
-          if (MODE == 1) wbuf[urow] = w;
-        }
-      }
-      __syncthreads();
-    }
-    if (MODE != 2) {  // lane owns slots k0 and k1 (slot j + 1 is ||w||^2); rows staggered by lane
-      const T* wsrc = MODE == 0 ? ws : wbuf;
-      const T* v0 = (const T*)(base + (size_t)k0 * stride);
-      const T* v1 = (const T*)(base + (size_t)k1 * stride);
-      const int mask = TR - 1;
-      typename Acc<T>::type t0 = zero<T>(), t1 = zero<T>();  // second row of each pair
-      for (int r = wid; r < TR; r += 2 * nwarps) {
-        const int ra = (r + lane) & mask, rb = (r + nwarps + lane) & mask;
-        const T wa = wsrc[ra], wb = wsrc[rb];
-        if (has0) {
-          fma_conj(f0, v0[ra], wa);
-          fma_conj(t0, v0[rb], wb);
-        }
-        if (has1) {
-          fma_conj(f1, v1[ra], wa);
-          fma_conj(t1, v1[rb], wb);
-        }
-      }
-      f0.x += t0.x;
-      f0.y += t0.y;
-      f1.x += t1.x;
-      f1.y += t1.y;
-      if ((it & 3) == 3) {  // FP32 sums over at most 4 tiles (<= 128 rows per lane), then FP64
-        acc0 = cadd(acc0, to_d2(f0));
-        acc1 = cadd(acc1, to_d2(f1));
-        f0 = zero<T>();
-        f1 = zero<T>();
-      }
-    } else if ((it & 7) == 7) {  // flush the FP32 norm every 8 tiles (<= 8 rows per thread)
-      nrm += (double)a_hi.x;
-      a_hi = zero<T>();
-    }
-    __syncthreads();  // every thread is done with this stage
-    if (tid == 0 && it + n_stages < my_tiles) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(it + n_stages);
-    }
-  }
-  if (aborted) {
-    // Give the copies still in flight a bounded chance to land before the block's shared memory
-    // is released, report, and leave the rest of the cycle to skip.
-    if (tid == 0) {
-      for (int sidx = 0; sidx < n_stages; ++sidx) mbar_wait(&bar[sidx], 0), mbar_wait(&bar[sidx], 1);
-      st->timeout = 1;
-      atomicExch(&st->done, 2);
-    }
-    return;
-  }
-  nrm += (double)a_hi.x;
-  acc0 = cadd(acc0, to_d2(f0));
-  acc1 = cadd(acc1, to_d2(f1));
-  // Every issued copy has been waited for, so the stage memory is free for the block reduction.
-  double2(*red)[64] = reinterpret_cast<double2(*)[64]>(stage_mem);
-  if (MODE != 2) {
-    red[wid][k0] = acc0;
-    red[wid][k1] = acc1;
-  } else {
-    double t = warp_sum(nrm);
-    if (lane == 0) red[wid][0] = make_double2(t, 0.0);
-  }
-  __syncthreads();
-  const int nslots = MODE == 2 ? 1 : j + 2;
-  for (int k = tid; k < nslots; k += kCgsThreads) {
-    double2 sum = make_double2(0.0, 0.0);
-    for (int w2 = 0; w2 < nwarps; ++w2) sum = cadd(sum, red[w2][k]);
-    partials[(int64_t)blockIdx.x * kPStride + k] = sum;
-  }
-  if (!last_block(&st->counter)) return;
-  reduce_partials(partials, gridDim.x, nslots, fin);
-  if (MODE == 0) {
-    for (int k = tid; k <= j; k += kCgsThreads) {
-      const double ib = st->inv_beta[k];
-      const double2 h = cscale(fin[k], ib);
-      if (pass == 0)
-        st->h[k] = h;
-      else
-        st->h2[k] = h;
-      st->c[k] = cscale(h, ib);
-    }
-    if (tid == 0) {
-      if (pass == 0) st->nrm_w = fin[j + 1].x;
-      st->counter = 0;
-    }
-  } else if (MODE == 1) {
-    for (int k = tid; k <= j; k += kCgsThreads) {
-      const double ib = st->inv_beta[k];
-      const double2 h = cscale(fin[k], ib);
-      st->h2[k] = h;
-      st->c[k] = cscale(h, ib);
-    }
-    if (tid == 0) st->counter = 0;
-  } else {
-    // pass 0 with eta2 > 0: keep this single pass only if ||w|| kept more than eta of its norm.
-    if (pass == 0 && eta2 > 0.0 && fin[0].x < eta2 * st->nrm_w) {
-      if (tid == 0) {
-        st->refine = 1;
-        st->counter = 0;
-      }
-      return;
-    }
-    __shared__ double2 hsum[kMaxM + 1];
-    for (int k = tid; k <= j; k += kCgsThreads) hsum[k] = pass == 1 ? cadd(st->h[k], st->h2[k]) : st->h[k];
-    __syncthreads();
-    if (tid == 0) {
-      finish_column(st, j, hsum, fin[0].x);
-      if (pass == 1) {
-        st->refined[j] = 1;
-        st->n_refine += 1;
-      }
-      st->refine = 0;
-      st->counter = 0;
-    }
-  }
-}
-
 // y = H(0:k, 0:k)^{-1} g(0:k), scaled by 1/||V_i|| for the unnormalised basis.  One warp:
 // column-oriented back substitution (lane l keeps the running right-hand side of rows l, l+32).
 __global__ void k_backsolve(GState* st) { backsolve_warp(st, threadIdx.x); }
@@ -620,14 +263,11 @@ Status prepare(petgem_ctx* c, int m, int prec, bool single) {
     PG_CUDA(cudaGetLastError());
     S->version = c->assembly_version;
   }
-  if (S->sms == 0) {
-    PG_CUDA(cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, c->device));
-    for (auto f : {(const void*)k_cgs<float2, 0>, (const void*)k_cgs<float2, 1>, (const void*)k_cgs<float2, 2>,
-                   (const void*)k_cgs<double2, 0>, (const void*)k_cgs<double2, 1>, (const void*)k_cgs<double2, 2>})
-      PG_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kCgsDynSmem));
-  }
+  if (S->sms == 0) PG_CUDA(cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, c->device));
+  PG_TRY((gs_setup<float2, 1>()));
+  PG_TRY((gs_setup<double2, 1>()));
   S->n = n;
-  S->ld = (n + 255) / 256 * 256;  // whole slices for the staged Gram-Schmidt kernel
+  S->ld = (n + 255) / 256 * 256;
   S->m = m;
   S->n_blocks = (n + kRows - 1) / kRows;
   if (!single) return Status{};
@@ -640,10 +280,11 @@ Status prepare(petgem_ctx* c, int m, int prec, bool single) {
   if (fresh) PG_CUDA(cudaMemsetAsync(S->V.ptr, 0, S->V.bytes, s));
   S->prec = prec;
   S->ld_used = S->ld;
-  // Partials: one row per block of the widest reduction grid (vector kernels: n_blocks; the
-  // persistent Gram-Schmidt kernel: two blocks per SM).
-  PG_TRY(S->partials.reserve((size_t)std::max<int64_t>(std::max<int64_t>(S->n_blocks, kCgsBlocksPerSM * S->sms), 1) *
-                             kPStride * sizeof(double2)));
+  // Partials: one row of kPStride per block of the widest reduction grid (vector kernels:
+  // n_blocks; the projection kernel: kDotBlocksPerSM per SM), and one value per update block.
+  PG_TRY(S->partials.reserve(((size_t)std::max<int64_t>(S->n_blocks, (int64_t)kDotBlocksPerSM * S->sms) * kPStride +
+                              (size_t)kUpdBlocksPerSM * S->sms) *
+                             sizeof(double2)));
   PG_TRY(S->u.reserve(n * sizeof(double2)));
   PG_TRY(S->r.reserve(n * sizeof(double2)));
   PG_TRY(S->state.reserve(sizeof(GState)));
@@ -694,40 +335,32 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
       k_spmv_arnoldi<T, kGroup><<<spmv_blocks, 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), ahat, xin,
                                                             vn, n, st, j);
     }
-    const int nv = j + 2;
-    const CgsShape shp = cgs_shape(nv);
-    const size_t dyn = std::max<size_t>((size_t)shp.stages * nv * (shp.slice + kSlicePad), kCgsRedBytes);
-    const int tiles = (int)(ld * sizeof(T) / shp.slice);
-    const unsigned grid = (unsigned)std::min(tiles, kCgsBlocksPerSM * S->sms);
-    const int64_t wb = (int64_t)vbytes;
-    auto cgs = [&](int mode, int pass, int need_refine, double eta2, const char* name, double bytes, int tag) {
+    const double dot_b = (double)(j + 2) * vbytes, upd_b = (double)(j + 3) * vbytes;
+    auto sdot = [&](int pass, int need_refine, const char* name, double bytes, int tag) -> Status {
       KernelTimer kt(c, name, bytes, j, tag);
-      if (mode == 0)
-        k_cgs<T, 0><<<grid, kCgsThreads, dyn, s>>>(V, ld, n, j, st, part, tiles, shp.slice, shp.stages, pass, need_refine, eta2);
-      else if (mode == 1)
-        k_cgs<T, 1><<<grid, kCgsThreads, dyn, s>>>(V, ld, n, j, st, part, tiles, shp.slice, shp.stages, pass, need_refine, eta2);
-      else
-        k_cgs<T, 2><<<grid, kCgsThreads, dyn, s>>>(V, ld, n, j, st, part, tiles, shp.slice, shp.stages, pass, need_refine, eta2);
       c->launches++;
+      return launch_pdot<T, 1>(s, S->sms, V, ld, n, j, st, &st->done, &st->gbar, part, pass, need_refine);
     };
-    const double dot_b = (double)(j + 2) * wb, upd_b = (double)(j + 3) * wb;
-    auto mdot = [&]() {
-      KernelTimer kt(c, c128 ? "mdot_c128" : "mdot_c64", dot_b, j, 0);
-      k_mdot<T><<<nb, kT, 0, s>>>(V, ld, n, j, st, part);
+    auto supd = [&](int pass, int need_refine, double eta2, int finish, const char* name, double bytes,
+                    int tag) -> Status {
+      KernelTimer kt(c, name, bytes, j, tag);
       c->launches++;
+      return launch_pupd<T, 1>(s, S->sms, V, ld, n, j, st, &st->done, &st->counter, part, pass, need_refine, eta2,
+                               finish);
     };
-    if (orth == 0) {  // CGS2: dots, update + dots, update + norm
-      mdot();
-      cgs(1, 0, 0, 0.0, c128 ? "cgs_upd_dot_c128" : "cgs_upd_dot_c64", upd_b, 0);
-      cgs(2, 1, 0, 0.0, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0);
+    if (orth == 0) {  // CGS2: dots, update, dots of the updated w, update + norm
+      PG_TRY(sdot(0, 0, c128 ? "mdot_c128" : "mdot_c64", dot_b, 0));
+      PG_TRY(supd(0, 0, 0.0, 0, c128 ? "cgs_upd1_c128" : "cgs_upd1_c64", upd_b, 0));
+      PG_TRY(sdot(1, 0, c128 ? "cgs_dot2_c128" : "cgs_dot2_c64", dot_b, 0));
+      PG_TRY(supd(1, 0, 0.0, 1, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0));
     } else if (orth == 1) {  // CGS: dots, update + norm
-      mdot();
-      cgs(2, 0, 0, 0.0, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0);
+      PG_TRY(sdot(0, 0, c128 ? "mdot_c128" : "mdot_c64", dot_b, 0));
+      PG_TRY(supd(0, 0, 0.0, 1, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0));
     } else {  // CGS, second pass when the norm fell below 1/sqrt(2) of its value
-      mdot();
-      cgs(2, 0, 0, 0.5, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0);
-      cgs(0, 1, 1, 0.0, c128 ? "cgs_dot2_c128" : "cgs_dot2_c64", dot_b, 1);
-      cgs(2, 1, 1, 0.0, c128 ? "cgs_upd2_c128" : "cgs_upd2_c64", upd_b, 1);
+      PG_TRY(sdot(0, 0, c128 ? "mdot_c128" : "mdot_c64", dot_b, 0));
+      PG_TRY(supd(0, 0, 0.5, 1, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0));
+      PG_TRY(sdot(1, 1, c128 ? "cgs_dot2_c128" : "cgs_dot2_c64", dot_b, 1));
+      PG_TRY(supd(1, 1, 0.0, 1, c128 ? "cgs_upd2_c128" : "cgs_upd2_c64", upd_b, 1));
     }
     c->launches += 1;
   }

@@ -32,6 +32,7 @@ struct GState {
   double inv_beta[kMaxM + 1];
   float inv_beta32[kMaxM + 1];  // the same scales in FP32, for the complex64 kernels
   double2 y[kMaxM];       // cycle solution, already scaled by inv_beta
+  unsigned long long gbar;  // arrivals at the projection kernel's grid barrier (only grows)
 };
 
 struct Solver {
@@ -147,25 +148,42 @@ __device__ void reduce_partials(const double2* partials, int nblocks, int nk, do
   __syncthreads();
 }
 
-// New Hessenberg column j from the projections h (summed over passes) and beta = ||V_{j+1}||:
-// earlier rotations, a new complex Givens rotation, the residual estimate and the stopping test.
-__device__ __noinline__ void finish_column(GState* st, int j, const double2* h, double beta2) {
-  double beta = sqrt(beta2);
-  double2* Hc = &st->H[j * (kMaxM + 1)];
-  for (int i = 0; i <= j; ++i) Hc[i] = h[i];
-  Hc[j + 1] = make_double2(beta, 0.0);
-  st->inv_beta[j + 1] = beta > 0.0 ? 1.0 / beta : 0.0;
-  st->inv_beta32[j + 1] = (float)st->inv_beta[j + 1];
+__device__ inline double shfl_d(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ inline double2 shfl_d2(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// New Hessenberg column j from the projections h[0..j] (summed over passes; global or shared
+// memory) and beta = ||V_{j+1}||: the earlier rotations in order, a new complex Givens rotation,
+// the residual estimate and the stopping test.  Called by all 32 lanes of one warp: lane l loads
+// rotation l and l + 32 and entries l and l + 32 of the column at once, so the sequential chain of
+// rotations runs on registers and shuffles instead of a chain of memory round trips.
+__device__ __forceinline__ void finish_column_warp(GState* st, int j, const double2* h, double beta2) {
+  const int l = threadIdx.x & 31;
+  const double beta = sqrt(beta2);
+  const double2 z = make_double2(0.0, 0.0);
+  const double c_lo = l < j ? st->cs_c[l] : 0.0, c_hi = l + 32 < j ? st->cs_c[l + 32] : 0.0;
+  const double2 s_lo = l < j ? st->cs_s[l] : z, s_hi = l + 32 < j ? st->cs_s[l + 32] : z;
+  const double2 h_lo = l <= j ? h[l] : z, h_hi = l + 32 <= j ? h[l + 32] : z;
+  double2 out_lo = h_lo, out_hi = h_hi;  // rotated entries of the column
+  double2 carry = shfl_d2(h_lo, 0);      // entry i after rotations 0..i-1
   for (int i = 0; i < j; ++i) {
-    double2 a = Hc[i], b = Hc[i + 1];
-    double c = st->cs_c[i];
-    double2 s = st->cs_s[i];
-    Hc[i] = cadd(cscale(a, c), cmul(s, b));
-    Hc[i + 1] = csub(cscale(b, c), cconjmul(s, a));  // -conj(s) a + c b
+    const bool hi = i >= 32, hi1 = i + 1 >= 32;
+    const double c = shfl_d(hi ? c_hi : c_lo, i & 31);
+    const double2 s = shfl_d2(hi ? s_hi : s_lo, i & 31);
+    const double2 b = shfl_d2(hi1 ? h_hi : h_lo, (i + 1) & 31);
+    const double2 top = cadd(cscale(carry, c), cmul(s, b));
+    carry = csub(cscale(b, c), cconjmul(s, carry));  // -conj(s) a + c b
+    if (l == (i & 31)) {
+      if (hi)
+        out_hi = top;
+      else
+        out_lo = top;
+    }
   }
-  double2 a = Hc[j];
-  double aa = sqrt(cabs2(a));
-  double rho = sqrt(aa * aa + beta * beta);
+  // new rotation on (carry, beta)
+  const double aa = sqrt(cabs2(carry));
+  const double rho = sqrt(aa * aa + beta * beta);
   double c;
   double2 s;
   if (aa == 0.0) {
@@ -173,23 +191,37 @@ __device__ __noinline__ void finish_column(GState* st, int j, const double2* h, 
     s = make_double2(1.0, 0.0);
   } else {
     c = aa / rho;
-    s = cscale(a, beta / (aa * rho));
+    s = cscale(carry, beta / (aa * rho));
   }
-  st->cs_c[j] = c;
-  st->cs_s[j] = s;
-  Hc[j] = cadd(cscale(a, c), cscale(s, beta));
-  Hc[j + 1] = make_double2(0.0, 0.0);
-  double2 gj = st->g[j];
-  st->g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));  // -conj(s) g_j
-  st->g[j] = cscale(gj, c);
-  st->k = j + 1;
-  double res = sqrt(cabs2(st->g[j + 1]));
-  if (!isfinite(res) || !isfinite(beta) || !(rho > 0.0))
-    st->done = 2;
-  else if (res <= st->stop_abs || beta == 0.0)
-    st->done = 1;
+  const double2 hj = cadd(cscale(carry, c), cscale(s, beta));
+  if (l == (j & 31)) {
+    if (j >= 32)
+      out_hi = hj;
+    else
+      out_lo = hj;
+  }
+  double2* Hc = &st->H[j * (kMaxM + 1)];
+  if (l <= j) Hc[l] = out_lo;
+  if (l + 32 <= j) Hc[l + 32] = out_hi;
+  if (l == 0) {
+    Hc[j + 1] = z;
+    st->inv_beta[j + 1] = beta > 0.0 ? 1.0 / beta : 0.0;
+    st->inv_beta32[j + 1] = (float)st->inv_beta[j + 1];
+    st->cs_c[j] = c;
+    st->cs_s[j] = s;
+    const double2 gj = st->g[j];
+    const double2 g1 = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));  // -conj(s) g_j
+    st->g[j + 1] = g1;
+    st->g[j] = cscale(gj, c);
+    st->k = j + 1;
+    const double res = sqrt(cabs2(g1));
+    if (!isfinite(res) || !isfinite(beta) || !(rho > 0.0))
+      st->done = 2;
+    else if (res <= st->stop_abs || beta == 0.0)
+      st->done = 1;
+  }
+  __syncwarp();
 }
-
 
 // y = H(0:k, 0:k)^{-1} g(0:k), scaled by 1/||V_i|| for the unnormalised basis.  One warp:
 // column-oriented back substitution (lane l keeps the running right-hand side of rows l, l+32).
