@@ -43,34 +43,89 @@ template <> __device__ inline double2 scale_out<double2>(double2 acc, const GSta
 }
 
 // y = (Ahat x) * scale, G lanes per row.  x = V_j, y = V_{j+1}, scale = 1/||V_j||.
+// Latency, not bandwidth, bounds a plain row-per-group CSR product here (a row costs three
+// dependent round trips: row pointers, then columns and values, then the gathers of x), so the
+// kernel is software-pipelined: a persistent grid of lane groups walks rows g, g + groups, ...,
+// and while it gathers x for row i it already loads the columns and values of row i + 1 and the
+// row pointers of row i + 2.  A lane takes up to U of its row's entries in one batch (rows of
+// these meshes hold at most 19 entries: G = 4, U = 5); longer rows finish in a loop.
+constexpr int kSpmvU = 5;
+template <typename T> struct SpmvOcc { static constexpr int value = 4; };  // resident 256-thread blocks per SM
+template <> struct SpmvOcc<double2> { static constexpr int value = 3; };
+
 template <typename T, int G>
-__global__ void __launch_bounds__(256) k_spmv_arnoldi(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                                      const T* __restrict__ val, const T* __restrict__ x,
-                                                      T* __restrict__ y, int64_t n, const GState* __restrict__ st,
-                                                      int j) {
+__device__ inline void spmv_fetch(const int32_t* __restrict__ col, const T* __restrict__ val, int64_t p0, int64_t p1,
+                                  int32_t* c, T* a) {
+#pragma unroll
+  for (int u = 0; u < kSpmvU; ++u) {
+    const int64_t q = p0 + (int64_t)u * G;
+    c[u] = q < p1 ? __ldg(&col[q]) : 0;
+    a[u] = q < p1 ? __ldg(&val[q]) : zero<T>();
+  }
+}
+
+template <typename T, int G>
+__global__ void __launch_bounds__(256, SpmvOcc<T>::value)
+    k_spmv_arnoldi(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const T* __restrict__ val,
+                   const T* __restrict__ x, T* __restrict__ y, int64_t n, const GState* __restrict__ st, int j) {
   if (st->done) return;
-  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t row = gid / G;
-  int lane = (int)(gid % G);
-  typename Acc<T>::type acc = zero<T>(), acc2 = zero<T>();
+  constexpr int U = kSpmvU;
+  const int64_t groups = (int64_t)gridDim.x * (256 / G);
+  const int lane = threadIdx.x % G;
+  int64_t row = blockIdx.x * (int64_t)(256 / G) + threadIdx.x / G;
+  // pipeline state: row (pointers, columns, values), row + groups (pointers)
+  int64_t p0 = 0, p1 = 0;
   if (row < n) {
-    const int64_t p1 = rp[row + 1];
-    int64_t p = rp[row] + lane;
-    for (; p + G < p1; p += 2 * G) {  // two entries per lane in flight
-      const int32_t c0 = __ldg(&col[p]), c1 = __ldg(&col[p + G]);
-      const T a0 = __ldg(&val[p]), a1 = __ldg(&val[p + G]);
-      fma_c(acc, a0, __ldg(&x[c0]));
-      fma_c(acc2, a1, __ldg(&x[c1]));
+    p0 = rp[row] + lane;
+    p1 = rp[row + 1];
+  }
+  int32_t c[U];
+  T a[U];
+  spmv_fetch<T, G>(col, val, p0, p1, c, a);
+  int64_t nrow = row + groups, np0 = 0, np1 = 0;
+  if (nrow < n) {
+    np0 = rp[nrow] + lane;
+    np1 = rp[nrow + 1];
+  }
+  while (__any_sync(0xffffffffu, row < n)) {
+    T xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = p0 + (int64_t)u * G < p1 ? __ldg(&x[c[u]]) : zero<T>();
+    int32_t c2[U];
+    T a2[U];
+    spmv_fetch<T, G>(col, val, np0, np1, c2, a2);
+    const int64_t nnrow = nrow + groups;
+    int64_t nnp0 = 0, nnp1 = 0;
+    if (nnrow < n) {
+      nnp0 = rp[nnrow] + lane;
+      nnp1 = rp[nnrow + 1];
     }
-    if (p < p1) fma_c(acc, __ldg(&val[p]), __ldg(&x[__ldg(&col[p])]));
+    typename Acc<T>::type acc = zero<T>(), acc2 = zero<T>();
+#pragma unroll
+    for (int u = 0; u < U; u += 2) {
+      fma_c(acc, a[u], xv[u]);
+      if (u + 1 < U) fma_c(acc2, a[u + 1], xv[u + 1]);
+    }
+    for (int64_t q = p0 + (int64_t)U * G; q < p1; q += G) fma_c(acc, __ldg(&val[q]), __ldg(&x[__ldg(&col[q])]));
+    acc.x += acc2.x;
+    acc.y += acc2.y;
+    for (int o = G / 2; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (row < n && lane == 0) y[row] = scale_out<T>(acc, st, j);
+    row = nrow;
+    p0 = np0;
+    p1 = np1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c[u] = c2[u];
+      a[u] = a2[u];
+    }
+    nrow = nnrow;
+    np0 = nnp0;
+    np1 = nnp1;
   }
-  acc.x += acc2.x;
-  acc.y += acc2.y;
-  for (int o = G / 2; o > 0; o >>= 1) {
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-  }
-  if (row < n && lane == 0) y[row] = scale_out<T>(acc, st, j);
 }
 
 // r = b - Ahat u in FP64 (complex128 matrix and vectors).
@@ -311,7 +366,8 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
     c->launches++;
   }
   const double spmv_bytes = (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 2.0 * vbytes;
-  const unsigned spmv_blocks = blocks_for(n * kGroup, 256);
+  const unsigned spmv_blocks =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_for(n * kGroup, 256), (int64_t)SpmvOcc<T>::value * S->sms));
   // Flexible GMRES with the learned preconditioner: z_j = N-corrected v_j, stored in Z, and the
   // solution update uses Z instead of V.
   T* Z = learned ? S->Z.as<T>() : nullptr;
