@@ -98,7 +98,11 @@ __global__ void __launch_bounds__(256) k_bresidual(const int64_t* __restrict__ r
 
 // Y = (Ahat X) diag(1 / ||X_s||), zero for stopped sources.  P lanes per row, lane = source: the
 // row's entries are read by the whole lane group (one broadcast transaction) four at a time, all
-// index and value loads of a batch ahead of its gathers of X.
+// index and value loads of a batch ahead of its gathers of X.  Blocks are short (256 / P rows
+// each) and start in row order, so the rows in flight at any time form one narrow band and the
+// rows of X they gather stay in L2.  Every nonzero moves P values of X through L1 (256 B for 32
+// complex64 sources): the product is bound by the L1 data path, not by HBM (persistent sweeps,
+// SM-contiguous bands and whole-row gather batches all measured slower than this form).
 template <typename T, int P>
 __global__ void __launch_bounds__(256) k_bspmm(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                const T* __restrict__ val, const T* __restrict__ X, T* __restrict__ Y,
@@ -286,6 +290,7 @@ Status run_group(petgem_ctx* c, const petgem_solve_opts& o, const double2* b, do
   for (int i = 0; i < P; ++i)
     if (i >= S_g || bn2[i] == 0.0) finished[i] = 1;
   std::vector<HostState> hs(P);
+  const unsigned spmm_grid = blocks_for(n * P, 256);
   const double spmm_bytes = (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 2.0 * n * P * sizeof(T);
   int64_t max_done = 0;
   while (true) {
@@ -303,8 +308,8 @@ Status run_group(petgem_ctx* c, const petgem_solve_opts& o, const double2* b, do
       T* vj = V + (int64_t)j * ldb;
       {
         KernelTimer kt(c, sizeof(T) == 8 ? "bspmm_c64" : "bspmm_c128", spmm_bytes);
-        k_bspmm<T, P><<<blocks_for(n * P, 256), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), ahat, vj,
-                                                             vj + ldb, n, sts, grp, j);
+        k_bspmm<T, P><<<spmm_grid, 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), ahat, vj, vj + ldb, n,
+                                                 sts, grp, j);
       }
       {
         KernelTimer kt(c, sizeof(T) == 8 ? "bmdot_c64" : "bmdot_c128", (double)(j + 2) * n * P * sizeof(T));
