@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--profile-step", action="store_true",
                    help="run one untimed step of the hot path and exit (the command profilers capture)")
     p.add_argument("--precision", default="mixed", choices=["mixed", "c128"], help="solver of --profile-step")
+    p.add_argument("--profile-block", type=int, default=0, metavar="ITERS",
+                   help="run only the 32-source block solve, capped at ITERS iterations (for ncu)")
     return p.parse_args()
 
 
@@ -176,6 +178,20 @@ def run_ours(args):
         if world > 1:
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item()), infos[-1], launches, cl
+
+    if args.profile_block:
+        mb = synth.marine_model(args.n, n_src=32)
+        Eb = api.petgem_mesh_edges(ctx.h, nodes, tets)
+        api.petgem_assemble(ctx.h, mb.freq, sigma, mb.sigma_p, mb.sources)
+        xb = torch.zeros((len(mb.sources), Eb), dtype=torch.complex128, device=dev)
+        _, binfo = api.petgem_solve(ctx.h, xb, len(mb.sources),
+                                    api.solve_opts(precision=api.PREC_MIXED, tol=1e-8, batch=0,
+                                                   max_iters=args.profile_block), allow_not_converged=True)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_block": True, "n": args.n, "edges": Eb, "iters": max(i["iters"] for i in binfo),
+                          "launches": api.petgem_launch_count(ctx.h)}))
+        ctx.close()
+        return None
 
     if args.profile_step:
         info, _ = step(api.PREC_MIXED if args.precision == "mixed" else api.PREC_C128)

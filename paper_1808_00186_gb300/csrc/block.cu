@@ -108,6 +108,8 @@ __global__ void __launch_bounds__(256) k_bspmm(const int64_t* __restrict__ rp, c
                                                const T* __restrict__ val, const T* __restrict__ X, T* __restrict__ Y,
                                                int64_t n, const GState* __restrict__ sts,
                                                const BGroup* __restrict__ grp, int j) {
+  pdl_trigger();
+  pdl_wait();
   if (grp->all_done) return;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t row = gid / P;
@@ -308,8 +310,9 @@ Status run_group(petgem_ctx* c, const petgem_solve_opts& o, const double2* b, do
       T* vj = V + (int64_t)j * ldb;
       {
         KernelTimer kt(c, sizeof(T) == 8 ? "bspmm_c64" : "bspmm_c128", spmm_bytes);
-        k_bspmm<T, P><<<spmm_grid, 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), ahat, vj, vj + ldb, n,
-                                                 sts, grp, j);
+        PG_CUDA(pdl_launch(k_bspmm<T, P>, dim3(spmm_grid), dim3(256), 0, s, false,
+                           (const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), ahat,
+                           (const T*)vj, vj + ldb, n, (const GState*)sts, (const BGroup*)grp, j));
       }
       {
         KernelTimer kt(c, sizeof(T) == 8 ? "bmdot_c64" : "bmdot_c128", (double)(j + 2) * n * P * sizeof(T));

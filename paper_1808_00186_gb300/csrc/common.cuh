@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 
 #include "petgem.h"
 
@@ -61,6 +62,36 @@ struct Status {
       return petgem::Status{PETGEM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
     }                                                                                     \
   } while (0)
+
+// Programmatic dependent launch.  A kernel started with pdl_launch may be scheduled while the
+// kernel before it in the stream is still finishing (its launch is processed early); it must call
+// pdl_wait() before it reads anything that kernel wrote, and may call pdl_trigger() to let the
+// kernel after it be scheduled once every one of its own blocks has started.  Both are no-ops for
+// a kernel started with a plain launch.
+__device__ inline void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ inline void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool cooperative,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  int na = 1;
+  if (cooperative) {
+    attr[1].id = cudaLaunchAttributeCooperative;
+    attr[1].val.cooperative = 1;
+    na = 2;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 #define PG_TRY(expr)                   \
   do {                                 \

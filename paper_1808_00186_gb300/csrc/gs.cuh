@@ -98,6 +98,8 @@ template <typename T, int P>
 __global__ void __launch_bounds__(kDotThreads, kDotBlocksPerSM)
     k_pdot(const T* __restrict__ V, int64_t ldv, int64_t n, int j, GState* __restrict__ sts, int* stop,
            unsigned long long* gbar, double2* __restrict__ partials, int pass, int need_refine) {
+  pdl_trigger();
+  pdl_wait();
   if (*(volatile int*)stop) return;
   if (P == 1 && need_refine && !sts[0].refine) return;
   using A = typename Acc<T>::type;
@@ -261,6 +263,8 @@ template <typename T, int P>
 __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSM)
     k_pupd(T* __restrict__ V, int64_t ldv, int64_t n, int j, GState* __restrict__ sts, int* stop, unsigned* counter,
            double2* __restrict__ partials, int pass, int need_refine, double eta2, int finish) {
+  pdl_trigger();
+  pdl_wait();
   if (*(volatile int*)stop) return;
   if (P == 1 && need_refine && !sts[0].refine) return;
   constexpr int NW = kUpdThreads / 32;
@@ -388,9 +392,8 @@ Status gs_setup() {
 template <typename T, int P>
 Status launch_pdot(cudaStream_t s, int sms, const T* V, int64_t ldv, int64_t n, int j, GState* sts, int* stop,
                    unsigned long long* gbar, double2* part, int pass, int need_refine) {
-  void* args[] = {&V, &ldv, &n, &j, &sts, &stop, &gbar, &part, &pass, &need_refine};
-  PG_CUDA(cudaLaunchCooperativeKernel((const void*)k_pdot<T, P>, dim3(kDotBlocksPerSM * sms), dim3(kDotThreads),
-                                      args, 0, s));
+  PG_CUDA(pdl_launch(k_pdot<T, P>, dim3(kDotBlocksPerSM * sms), dim3(kDotThreads), 0, s, true, V, ldv, n, j, sts,
+                     stop, gbar, part, pass, need_refine));
   return Status{};
 }
 
@@ -401,9 +404,8 @@ inline int pupd_grid(int64_t n, int P, int sms) {
 template <typename T, int P>
 Status launch_pupd(cudaStream_t s, int sms, T* V, int64_t ldv, int64_t n, int j, GState* sts, int* stop,
                    unsigned* counter, double2* part, int pass, int need_refine, double eta2, int finish) {
-  k_pupd<T, P><<<pupd_grid(n, P, sms), kUpdThreads, 0, s>>>(V, ldv, n, j, sts, stop, counter, part, pass,
-                                                            need_refine, eta2, finish);
-  PG_CUDA(cudaGetLastError());
+  PG_CUDA(pdl_launch(k_pupd<T, P>, dim3(pupd_grid(n, P, sms)), dim3(kUpdThreads), 0, s, false, V, ldv, n, j, sts,
+                     stop, counter, part, pass, need_refine, eta2, finish));
   return Status{};
 }
 

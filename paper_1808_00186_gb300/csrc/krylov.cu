@@ -68,6 +68,8 @@ template <typename T, int G>
 __global__ void __launch_bounds__(256, SpmvOcc<T>::value)
     k_spmv_arnoldi(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const T* __restrict__ val,
                    const T* __restrict__ x, T* __restrict__ y, int64_t n, const GState* __restrict__ st, int j) {
+  pdl_trigger();
+  pdl_wait();
   if (st->done) return;
   constexpr int U = kSpmvU;
   const int64_t groups = (int64_t)gridDim.x * (256 / G);
@@ -388,8 +390,9 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
     }
     {
       KernelTimer kt(c, c128 ? "spmv_c128" : "spmv_c64", spmv_bytes, j, 0);
-      k_spmv_arnoldi<T, kGroup><<<spmv_blocks, 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), ahat, xin,
-                                                            vn, n, st, j);
+      PG_CUDA(pdl_launch(k_spmv_arnoldi<T, kGroup>, dim3(spmv_blocks), dim3(256), 0, s, false,
+                         (const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), ahat, xin, vn,
+                         n, (const GState*)st, j));
     }
     const double dot_b = (double)(j + 2) * vbytes, upd_b = (double)(j + 3) * vbytes;
     auto sdot = [&](int pass, int need_refine, const char* name, double bytes, int tag) -> Status {
