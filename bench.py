@@ -41,9 +41,18 @@ def parse():
     p.add_argument("--profile-step", action="store_true",
                    help="run one untimed step of the hot path and exit (the command profilers capture)")
     p.add_argument("--precision", default="mixed", choices=["mixed", "c128"], help="solver of --profile-step")
+    p.add_argument("--no-learned", action="store_true", help="skip the learned-network measurement")
     p.add_argument("--profile-block", type=int, default=0, metavar="ITERS",
                    help="run only the 32-source block solve, capped at ITERS iterations (for ncu)")
     return p.parse_args()
+
+
+def tensor_peak():
+    """Dense BF16 tensor peak (burst): measured, else the fallback figure."""
+    try:
+        return float(json.load(open(MEASURED))["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
 
 
 def dist_env():
@@ -257,6 +266,40 @@ def run_ours(args):
                  "iters_max": max(i["iters"] for i in binfo),
                  "worst_true_rel_residual": max(i["true_rel_residual"] for i in binfo), "kernels": bks}
 
+    # Learned preconditioner (tcgen05 convolutions): the network on this mesh's parent grid
+    # ((n+1)^3 nodes), apply time and the convolutions' throughput against the BF16 tensor peak.
+    learned = None
+    if not args.no_learned:
+        from paper_1808_00186_gb300 import learned as PL
+        E = api.petgem_mesh_edges(ctx.h, nodes, tets)
+        api.petgem_assemble(ctx.h, m.freq, sigma, m.sigma_p, m.sources)
+        api.petgem_learned_create(ctx.h, args.n, args.n, args.n)
+        api.petgem_learned_params(ctx.h, set_params=PL.init_params(0))
+        gen = torch.Generator(device=dev).manual_seed(7)
+        r = torch.randn(E, dtype=torch.complex128, device=dev, generator=gen)
+        z = torch.empty_like(r)
+        for _ in range(3):
+            api.petgem_learned_apply(ctx.h, r, z)
+        barrier()
+        reps = 5
+        api.petgem_profile(ctx.h, True)
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record()
+        for _ in range(reps):
+            api.petgem_learned_apply(ctx.h, r, z)
+        l1.record()
+        barrier()
+        nc, cms, flops = api.petgem_kernel_stats(ctx.h, "conv3d_fwd")
+        api.petgem_profile(ctx.h, False)
+        bf16 = tensor_peak()
+        tf = flops / (cms * 1e-3) / 1e12 if cms > 0 else 0.0
+        learned = {"grid": [args.n + 1] * 3, "apply_ms": round(l0.elapsed_time(l1) / reps, 3),
+                   "conv3d_fwd": {"launches": nc, "ms": round(cms, 3), "gflop": round(flops / 1e9, 2),
+                                  "tflops": round(tf, 1)},
+                   "roofline": {"kernel": "conv3d_fwd", "bound": "tensor", "achieved": round(tf, 1),
+                                "peak": bf16[0], "unit": "TFLOP/s", "frac": round(tf / bf16[0], 4),
+                                "peak_source": bf16[1], "traffic": None}}
+
     # End to end through the public API from pinned host buffers, results read back each step.
     h_nodes = torch.as_tensor(m.mesh.nodes).pin_memory()
     h_tets = torch.as_tensor(m.mesh.tets).pin_memory()
@@ -318,6 +361,7 @@ def run_ours(args):
             "true_rel_residual": info_mixed[0]["true_rel_residual"],
             "plain_c128": plain,
             "block_multi_source": block,
+            "learned_network": learned,
             "speedup_vs_plain": round(plain["ms_per_step"] / ms_mixed, 3) if plain else None,
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "gbs": round(v["gbs"], 1)}
                         for k, v in kstats.items()},

@@ -238,7 +238,8 @@ int petgem_nn_conv3d_wgrad_noalloc(void *stream, int32_t gx, int32_t gy, int32_t
 /* Per-kernel device time recorded with CUDA events around launches while enabled.
  * petgem_profile(ctx, 1) clears and enables, 0 disables.  petgem_kernel_stats returns, for
  * kernel `name` (e.g. "spmv_c64"), the launch count, total milliseconds and the algorithmic
- * bytes those launches moved (synchronises). */
+ * bytes those launches moved (synchronises).  For the network's tensor-core convolutions
+ * ("conv3d_fwd") the third value counts floating-point operations (2 per multiply-add). */
 int petgem_profile(petgem_ctx *ctx, int enable);
 int petgem_kernel_stats(petgem_ctx *ctx, const char *name, int64_t *launches, double *total_ms,
                         double *bytes);

@@ -392,6 +392,7 @@ Status conv3d_wgrad(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, c
 int wgrad_splits(int64_t V) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, (V + 4095) / 4096)); }
 
 Status Net::init(petgem_ctx* c, int nx_, int ny_, int nz_) {
+  ctx = c;
   nx = nx_;
   ny = ny_;
   nz = nz_;
@@ -477,6 +478,8 @@ Status Net::pack_weights(cudaStream_t s) {
 
 Status Net::conv(cudaStream_t s, int i, const __nv_bfloat16* in, __nv_bfloat16* out, float* outf) {
   const int* gg = g[L[i].level];
+  // timed (when profiling) with its floating-point operations in place of bytes
+  KernelTimer kt(ctx, "conv3d_fwd", 2.0 * 27.0 * L[i].cin * L[i].cout * (double)gg[0] * gg[1] * gg[2]);
   return conv3d(s, gg[0], gg[1], gg[2], L[i].cin, L[i].cout, in, wb.as<__nv_bfloat16>() + L[i].w_off,
                 params.as<float>() + L[i].b_off, L[i].relu != 0, out, outf, err.as<int>());
 }

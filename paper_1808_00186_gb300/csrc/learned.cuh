@@ -13,6 +13,7 @@ struct Layer {
 };
 
 struct Net {
+  petgem_ctx* ctx = nullptr;
   bool ready = false;
   int nx = 0, ny = 0, nz = 0;
   int g[4][3];      // grid dimensions of levels 0..3
