@@ -85,7 +85,22 @@ typedef struct {
   int64_t max_iters;   /* cap on Krylov iterations per source */
   int32_t orth;        /* Arnoldi orthogonalisation: PETGEM_ORTH_CGS (default), _CGS2, _CGS_IFNEEDED */
   int32_t use_graphs;  /* 1 = replay each restart cycle as a CUDA graph */
+  int32_t method;      /* PETGEM_METHOD_GMRES (default) or PETGEM_METHOD_COCG */
+  int32_t reserved;
 } petgem_solve_opts;
+
+/* Krylov method.
+ *   GMRES: restarted GMRES(restart) as above.
+ *   COCG: conjugate orthogonal conjugate gradient for the complex-symmetric matrix (A^T = A),
+ *     the short-recurrence family the paper's Section 5.3 solves with (symmetric QMR): CG with
+ *     the bilinear form u^T v, Jacobi as the symmetric scaling D^{-1/2} A D^{-1/2}, no basis
+ *     stored.  precision MIXED: complex64 inner solves that each reduce the scaled residual by
+ *     inner_tol, restarted from the FP64 residual b - A x; C128: FP64 throughout.  `restart` is
+ *     the number of iterations between host checks of the device-side stopping flag; `batch`
+ *     and `orth` are ignored; precond must be Jacobi (PETGEM_ERR_UNSUPPORTED otherwise).
+ *     info.restarts counts the inner solves.  A breakdown of the bilinear form (p^T A p = 0) ends
+ *     an inner solve early; one at the very first step returns PETGEM_ERR_BREAKDOWN. */
+enum { PETGEM_METHOD_GMRES = 0, PETGEM_METHOD_COCG = 1 };
 
 /* Orthogonalisation of each new Krylov vector w against the basis V:
  *   CGS: classical Gram-Schmidt once (two passes over V per step; the default of PETSc's GMRES);

@@ -24,6 +24,7 @@ OK, ERR_INVALID_ARG, ERR_BAD_MESH, ERR_DEGENERATE_TET, ERR_OUT_OF_MEMORY, ERR_CU
 PREC_C128, PREC_MIXED = 0, 1
 ORTH_CGS2, ORTH_CGS, ORTH_CGS_IFNEEDED = 0, 1, 2
 PRECOND_JACOBI, PRECOND_LEARNED = 0, 1
+METHOD_GMRES, METHOD_COCG = 0, 1
 
 
 class petgem_dipole(ctypes.Structure):
@@ -34,7 +35,8 @@ class petgem_dipole(ctypes.Structure):
 class petgem_solve_opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("precision", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
-                ("max_iters", ctypes.c_int64), ("orth", ctypes.c_int32), ("use_graphs", ctypes.c_int32)]
+                ("max_iters", ctypes.c_int64), ("orth", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
+                ("method", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class petgem_solve_info(ctypes.Structure):
@@ -163,8 +165,8 @@ def petgem_get_elements(ctx, K21=None, M21=None, vol=None):
 
 
 def solve_opts(restart=50, precision=PREC_C128, tol=1e-8, inner_tol=1e-4, max_iters=200000, batch=1,
-               orth=ORTH_CGS, use_graphs=0, precond=PRECOND_JACOBI) -> petgem_solve_opts:
-    return petgem_solve_opts(restart, precision, precond, batch, tol, inner_tol, max_iters, orth, use_graphs)
+               orth=ORTH_CGS, use_graphs=0, precond=PRECOND_JACOBI, method=METHOD_GMRES) -> petgem_solve_opts:
+    return petgem_solve_opts(restart, precision, precond, batch, tol, inner_tol, max_iters, orth, use_graphs, method, 0)
 
 
 def petgem_solve(ctx, x, n_src, opts=None, allow_not_converged=False):

@@ -129,6 +129,7 @@ int petgem_destroy(petgem_ctx* c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   petgem::destroy_solver(c);
+  petgem::destroy_cocg(c);
   delete c->net;
   c->net = nullptr;
   c->slots.release();
@@ -278,7 +279,12 @@ int petgem_solve(petgem_ctx* c, const petgem_solve_opts* opts, void* x, petgem_s
   o.max_iters = 200000;
   o.orth = PETGEM_ORTH_CGS;
   o.use_graphs = 0;
+  o.method = PETGEM_METHOD_GMRES;
   if (opts) o = *opts;
+  if (o.method != PETGEM_METHOD_GMRES && o.method != PETGEM_METHOD_COCG)
+    return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve: unknown method"});
+  if (o.method == PETGEM_METHOD_COCG && o.precond != PETGEM_PRECOND_JACOBI)
+    return finish(c, Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve: COCG takes the Jacobi preconditioner only"});
   if (!(o.tol > 0.0) || o.max_iters < 0 || (o.precision != PETGEM_PREC_C128 && o.precision != PETGEM_PREC_MIXED) ||
       (o.precond != PETGEM_PRECOND_JACOBI && o.precond != PETGEM_PRECOND_LEARNED) ||
       !(o.inner_tol >= 0.0 && o.inner_tol < 1.0) || o.orth < 0 ||

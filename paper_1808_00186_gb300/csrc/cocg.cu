@@ -1,0 +1,570 @@
+// Conjugate orthogonal conjugate gradient (COCG) for the complex-symmetric system of eq. 9: a
+// short-recurrence alternative to GMRES (the paper's mesh-adaptation study, Section 5.3, solves the
+// same system with a method of this family, symmetric QMR).  COCG is CG with the bilinear form
+// u^T v instead of the Hermitian product; A^T = A makes the residuals orthogonal in that form, so
+// no basis is stored and an iteration moves about half the bytes of a GMRES(50) step.
+//
+// Jacobi enters as a symmetric scaling, Atil = S A S with S = D^{-1/2} (principal complex square
+// root of the diagonal), which keeps the operator complex symmetric (a one-sided scaling A D^{-1}
+// would not be, and COCG diverges on it).  An inner solve iterates on Atil y = S r and returns
+// x += S y.
+//
+// Per iteration: the SpMV q = Atil p with the bilinear dot p^T q fused into it (its last block
+// forms alpha = rho / p^T q), the update kernel (y += alpha p, r -= alpha q, r^T r and ||r||^2; its
+// last block forms beta and the stopping test) and the direction update p = r + beta p.  The
+// scalars live on the device, so a chunk of iterations runs without host synchronisation, and the
+// kernels after a stop return at once.  Mixed precision: Atil and the vectors in complex64 (FP32
+// products within a thread and its warp, FP64 beyond); each inner solve runs until its residual fell
+// by inner_tol and restarts from the FP64 true residual b - A x (iterative refinement).  c128:
+// everything in FP64, one inner solve to the final tolerance.
+#include <math.h>
+
+#include <algorithm>
+
+#include "krylov.cuh"
+
+namespace petgem {
+namespace {
+
+struct CState {
+  int done;  // 0 running, 1 inner threshold reached, 2 breakdown of the bilinear form
+  int k;     // iterations of this inner solve
+  unsigned counter;
+  int pad;
+  double2 rho;  // r^T r
+  double2 alpha, beta;
+  float2 alpha32, beta32;
+  double nr0, nr, stop2;  // ||r||^2 at the start and now; stop when nr <= stop2
+  double rn2;             // FP64 ||v||^2 of the last k_cg_norm
+};
+
+constexpr int kCgG = 4;  // lanes per row of the CSR products (rows hold at most ~19 entries)
+constexpr int kCgU = 5;  // entries per lane in one batch
+template <typename T> struct CgOcc { static constexpr int value = 4; };
+template <> struct CgOcc<double2> { static constexpr int value = 3; };
+
+__device__ inline void bil_fma(float2& acc, float2 a, float2 b) { fma_c(acc, a, b); }  // acc += a b
+__device__ inline void bil_fma(double2& acc, double2 a, double2 b) { fma_c(acc, a, b); }
+
+// Warp-parallel FP64 sum of partials[b * kPStride + slot] over b < nb (eight loads in flight per
+// lane at a time, then a tree): every lane returns the total.
+__device__ inline double2 warp_sum_partials(const double2* partials, int nb, int slot) {
+  const int lane = threadIdx.x & 31;
+  double2 a = make_double2(0.0, 0.0);
+  for (int b0 = 0; b0 < nb; b0 += 256) {
+    double2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int b = b0 + lane + 32 * m;
+      v[m] = b < nb ? __ldcg(&partials[(int64_t)b * kPStride + slot]) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) a = cadd(a, v[m]);
+  }
+  return warp_sum(a);
+}
+
+// Block sums of two complex accumulators (FP64 per warp and block) into partials[b][0..1].
+template <int NT>
+__device__ inline void block_partials2(double2 a0, double2 a1, double2* partials) {
+  __shared__ double2 red[NT / 32][2];
+  a0 = warp_sum(a0);
+  a1 = warp_sum(a1);
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = a0;
+    red[threadIdx.x >> 5][1] = a1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int w = 0; w < NT / 32; ++w) s = cadd(s, red[w][threadIdx.x]);
+    partials[(int64_t)blockIdx.x * kPStride + threadIdx.x] = s;
+  }
+}
+
+// Scaled operator Atil = S A S, S = diag(sq): row by row (one thread per row).
+__global__ void k_cg_scale(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                           const double2* __restrict__ val, const double2* __restrict__ sq, int64_t n,
+                           double2* __restrict__ a128, float2* __restrict__ a64) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 si = sq[i];
+  for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+    const double2 v = cmul(cmul(si, val[p]), sq[col[p]]);
+    a128[p] = v;
+    a64[p] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+// sq = D^{-1/2}: principal complex square root of the diagonal, inverted.
+__global__ void k_cg_sqrt_diag(const double2* __restrict__ d, int64_t n, double2* __restrict__ sq) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 z = d[i];
+  const double m = sqrt(cabs2(z));
+  // sqrt(z) = (sqrt((m + x) / 2), sign(y) sqrt((m - x) / 2)), the root with non-negative real part
+  const double re = sqrt(fmax(0.5 * (m + z.x), 0.0));
+  double im = sqrt(fmax(0.5 * (m - z.x), 0.0));
+  if (z.y < 0.0) im = -im;
+  sq[i] = cdiv(make_double2(1.0, 0.0), make_double2(re, im));
+}
+
+// r64 = b - A x (FP64, the assembled matrix), G lanes per row.
+template <int G>
+__global__ void __launch_bounds__(256) k_cg_residual(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                     const double2* __restrict__ val, const double2* __restrict__ x,
+                                                     const double2* __restrict__ b, double2* __restrict__ r,
+                                                     int64_t n) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t row = gid / G;
+  const int lane = (int)(gid % G);
+  double2 acc = make_double2(0.0, 0.0);
+  if (row < n)
+    for (int64_t p = rp[row] + lane; p < rp[row + 1]; p += G) fma_c(acc, val[p], x[col[p]]);
+  for (int o = G / 2; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (row < n && lane == 0) r[row] = csub(b[row], acc);
+}
+
+// ||v||^2 in FP64 into st->rn2.
+__global__ void __launch_bounds__(kT) k_cg_norm(const double2* __restrict__ v, int64_t n, CState* __restrict__ st,
+                                                double2* __restrict__ partials) {
+  double s = 0.0;
+  const int64_t base = blockIdx.x * (int64_t)kRows + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < kR; ++q) {
+    const int64_t i = base + (int64_t)q * kT;
+    if (i < n) s += nrm2(v[i]);
+  }
+  block_partials2<kT>(make_double2(s, 0.0), make_double2(0.0, 0.0), partials);
+  if (!last_block(&st->counter)) return;
+  if (threadIdx.x < 32) {
+    const double2 t = warp_sum_partials(partials, gridDim.x, 0);
+    if (threadIdx.x == 0) {
+      st->rn2 = t.x;
+      st->counter = 0;
+    }
+  }
+}
+
+// Inner-solve start: r = p = scale S r64 (rounded to T), y = 0, rho = r^T r, ||r||^2, threshold.
+// scale = 1 / ||r64|| keeps the complex64 vectors of O(1) size: after a few refinements the
+// residual's entries are ~1e-20 and their squares would underflow in FP32.
+template <typename T>
+__global__ void __launch_bounds__(kT) k_cg_start(const double2* __restrict__ r64, const double2* __restrict__ sq,
+                                                 T* __restrict__ r, T* __restrict__ p, T* __restrict__ y, int64_t n,
+                                                 CState* __restrict__ st, double2* __restrict__ partials,
+                                                 double inner, double scale) {
+  using A = typename Acc<T>::type;
+  A rho = zero<T>(), nr = zero<T>();
+  const int64_t base = blockIdx.x * (int64_t)kRows + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < kR; ++q) {
+    const int64_t i = base + (int64_t)q * kT;
+    if (i < n) {
+      const T t = from_d2<T>(cscale(cmul(sq[i], r64[i]), scale));
+      r[i] = t;
+      p[i] = t;
+      y[i] = zero<T>();
+      bil_fma(rho, t, t);
+      nr.x += nrm2(t);
+    }
+  }
+  block_partials2<kT>(to_d2(rho), to_d2(nr), partials);
+  if (!last_block(&st->counter)) return;
+  if (threadIdx.x < 32) {
+    const double2 a = warp_sum_partials(partials, gridDim.x, 0);
+    const double2 b = warp_sum_partials(partials, gridDim.x, 1);
+    if (threadIdx.x == 0) {
+      st->rho = a;
+      st->nr0 = b.x;
+      st->nr = b.x;
+      st->stop2 = inner * inner * b.x;
+      st->k = 0;
+      st->done = (b.x > 0.0 && isfinite(b.x)) ? 0 : (b.x == 0.0 ? 1 : 2);
+      st->counter = 0;
+    }
+  }
+}
+
+template <typename T, int G>
+__device__ inline void cg_fetch(const int32_t* __restrict__ col, const T* __restrict__ val, int64_t p0, int64_t p1,
+                                int32_t* c, T* a) {
+#pragma unroll
+  for (int u = 0; u < kCgU; ++u) {
+    const int64_t q = p0 + (int64_t)u * G;
+    c[u] = q < p1 ? __ldg(&col[q]) : 0;
+    a[u] = q < p1 ? __ldg(&val[q]) : zero<T>();
+  }
+}
+
+// q = Atil p and the bilinear p^T q; the last block forms alpha = rho / p^T q.  Persistent and
+// software-pipelined like the Arnoldi SpMV: the gathers of row i overlap the column/value loads of
+// row i + 1 and the row pointers of row i + 2.
+template <typename T, int G>
+__global__ void __launch_bounds__(256, CgOcc<T>::value)
+    k_cg_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const T* __restrict__ val,
+              const T* __restrict__ p, T* __restrict__ q, int64_t n, CState* __restrict__ st,
+              double2* __restrict__ partials) {
+  pdl_trigger();
+  pdl_wait();
+  if (st->done) return;
+  constexpr int U = kCgU;
+  using A = typename Acc<T>::type;
+  const int64_t groups = (int64_t)gridDim.x * (256 / G);
+  const int lane = threadIdx.x % G;
+  int64_t row = blockIdx.x * (int64_t)(256 / G) + threadIdx.x / G;
+  int64_t p0 = 0, p1 = 0;
+  if (row < n) {
+    p0 = rp[row] + lane;
+    p1 = rp[row + 1];
+  }
+  int32_t c[U];
+  T a[U];
+  cg_fetch<T, G>(col, val, p0, p1, c, a);
+  int64_t nrow = row + groups, np0 = 0, np1 = 0;
+  if (nrow < n) {
+    np0 = rp[nrow] + lane;
+    np1 = rp[nrow + 1];
+  }
+  A dot = zero<T>();
+  while (__any_sync(0xffffffffu, row < n)) {
+    T xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = p0 + (int64_t)u * G < p1 ? __ldg(&p[c[u]]) : zero<T>();
+    const T prow = (row < n && lane == 0) ? __ldg(&p[row]) : zero<T>();
+    int32_t c2[U];
+    T a2[U];
+    cg_fetch<T, G>(col, val, np0, np1, c2, a2);
+    const int64_t nnrow = nrow + groups;
+    int64_t nnp0 = 0, nnp1 = 0;
+    if (nnrow < n) {
+      nnp0 = rp[nnrow] + lane;
+      nnp1 = rp[nnrow + 1];
+    }
+    A acc = zero<T>(), acc2 = zero<T>();
+#pragma unroll
+    for (int u = 0; u < U; u += 2) {
+      fma_c(acc, a[u], xv[u]);
+      if (u + 1 < U) fma_c(acc2, a[u + 1], xv[u + 1]);
+    }
+    for (int64_t qq = p0 + (int64_t)U * G; qq < p1; qq += G) fma_c(acc, __ldg(&val[qq]), __ldg(&p[__ldg(&col[qq])]));
+    acc.x += acc2.x;
+    acc.y += acc2.y;
+    for (int o = G / 2; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (row < n && lane == 0) {
+      const T qv = from_d2<T>(to_d2(acc));
+      q[row] = qv;
+      bil_fma(dot, prow, qv);
+    }
+    row = nrow;
+    p0 = np0;
+    p1 = np1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c[u] = c2[u];
+      a[u] = a2[u];
+    }
+    nrow = nnrow;
+    np0 = nnp0;
+    np1 = nnp1;
+  }
+  block_partials2<256>(to_d2(dot), make_double2(0.0, 0.0), partials);
+  if (!last_block(&st->counter)) return;
+  if (threadIdx.x < 32) {
+    const double2 pq = warp_sum_partials(partials, gridDim.x, 0);
+    if (threadIdx.x == 0) {
+      if (!(cabs2(pq) > 0.0) || !isfinite(pq.x) || !isfinite(pq.y)) {
+        st->done = 2;
+      } else {
+        const double2 al = cdiv(st->rho, pq);
+        st->alpha = al;
+        st->alpha32 = make_float2((float)al.x, (float)al.y);
+      }
+      st->counter = 0;
+    }
+  }
+}
+
+template <typename T> __device__ inline T cg_alpha(const CState* st);
+template <> __device__ inline float2 cg_alpha<float2>(const CState* st) { return st->alpha32; }
+template <> __device__ inline double2 cg_alpha<double2>(const CState* st) { return st->alpha; }
+template <typename T> __device__ inline T cg_beta(const CState* st);
+template <> __device__ inline float2 cg_beta<float2>(const CState* st) { return st->beta32; }
+template <> __device__ inline double2 cg_beta<double2>(const CState* st) { return st->beta; }
+
+// y += alpha p, r -= alpha q, rho' = r^T r, ||r||^2; the last block forms beta = rho' / rho and
+// the stopping test.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_update(const T* __restrict__ p, const T* __restrict__ q,
+                                                   T* __restrict__ r, T* __restrict__ y, int64_t n,
+                                                   CState* __restrict__ st, double2* __restrict__ partials) {
+  pdl_trigger();
+  pdl_wait();
+  if (st->done) return;
+  using A = typename Acc<T>::type;
+  const T al = cg_alpha<T>(st);
+  A rho = zero<T>(), nr = zero<T>();
+  double2 rho64 = make_double2(0.0, 0.0), nr64 = rho64;
+  int cnt = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T pv = p[i], qv = q[i];
+    T yv = y[i], rv = r[i];
+    fma_c(yv, al, pv);
+    sub_mul(rv, qv, al);
+    y[i] = yv;
+    r[i] = rv;
+    bil_fma(rho, rv, rv);
+    nr.x += nrm2(rv);
+    if (++cnt == 32) {  // FP32 over at most 32 elements, then FP64
+      rho64 = cadd(rho64, to_d2(rho));
+      nr64 = cadd(nr64, to_d2(nr));
+      rho = zero<T>();
+      nr = zero<T>();
+      cnt = 0;
+    }
+  }
+  rho64 = cadd(rho64, to_d2(rho));
+  nr64 = cadd(nr64, to_d2(nr));
+  block_partials2<256>(rho64, nr64, partials);
+  if (!last_block(&st->counter)) return;
+  if (threadIdx.x < 32) {
+    const double2 rh = warp_sum_partials(partials, gridDim.x, 0);
+    const double2 nn = warp_sum_partials(partials, gridDim.x, 1);
+    if (threadIdx.x == 0) {
+      st->k += 1;
+      st->nr = nn.x;
+      if (!isfinite(nn.x)) {
+        st->done = 2;
+      } else if (nn.x <= st->stop2) {
+        st->done = 1;
+      } else if (!(cabs2(st->rho) > 0.0)) {
+        st->done = 2;
+      } else {
+        const double2 be = cdiv(rh, st->rho);
+        st->beta = be;
+        st->beta32 = make_float2((float)be.x, (float)be.y);
+        st->rho = rh;
+      }
+      st->counter = 0;
+    }
+  }
+}
+
+// p = r + beta p.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_dir(const T* __restrict__ r, T* __restrict__ p, int64_t n,
+                                                const CState* __restrict__ st) {
+  pdl_trigger();
+  pdl_wait();
+  if (st->done) return;
+  const T be = cg_beta<T>(st);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T pv = r[i];
+    fma_c(pv, be, p[i]);
+    p[i] = pv;
+  }
+}
+
+// x += unscale S y (FP64).
+template <typename T>
+__global__ void k_cg_finish(const T* __restrict__ y, const double2* __restrict__ sq, double2* __restrict__ x,
+                            int64_t n, double unscale) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i] = cadd(x[i], cscale(cmul(sq[i], to_d2(y[i])), unscale));
+}
+
+struct CgBuffers {
+  DevBuf sq, a128, a64, r64, r, p, q, y, state, partials;
+  int64_t version = -1;
+};
+
+CgBuffers* cg_bufs(petgem_ctx* c) {
+  if (!c->cocg) c->cocg = new CgBuffers();
+  return static_cast<CgBuffers*>(c->cocg);
+}
+
+Status read_cstate(petgem_ctx* c, CgBuffers* B, CState* h) {
+  PG_CUDA(cudaMemcpyAsync(h, B->state.ptr, sizeof(CState), cudaMemcpyDeviceToHost, c->stream));
+  PG_CUDA(cudaStreamSynchronize(c->stream));
+  return Status{};
+}
+
+template <typename T>
+Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, const double2* b, double2* x,
+                   petgem_solve_info& inf, int sms) {
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n_edges;
+  CState* st = B->state.as<CState>();
+  double2* part = B->partials.as<double2>();
+  const bool c128 = sizeof(T) == 16;
+  const T* at = c128 ? (const T*)B->a128.ptr : (const T*)B->a64.ptr;
+  T *r = B->r.as<T>(), *p = B->p.as<T>(), *q = B->q.as<T>(), *y = B->y.as<T>();
+  const unsigned nb = blocks_for(n, kRows);
+  const unsigned spmv_grid =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_for(n * kCgG, 256), (int64_t)CgOcc<T>::value * sms));
+  const unsigned vec_grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_for(n, 256), 8LL * sms));
+  const double vb = (double)sizeof(T) * n;
+  const double spmv_bytes = (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 3.0 * vb;
+  CState hs;
+  auto norm = [&](const double2* v, double* out) -> Status {
+    k_cg_norm<<<nb, kT, 0, s>>>(v, n, st, part);
+    c->launches++;
+    PG_CUDA(cudaGetLastError());
+    PG_TRY(read_cstate(c, B, &hs));
+    *out = hs.rn2;
+    return Status{};
+  };
+  double bn2 = 0.0;
+  PG_TRY(norm(b, &bn2));
+  const double bnorm = sqrt(bn2);
+  if (bnorm == 0.0) {
+    PG_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+    inf.status = PETGEM_OK;
+    return Status{};
+  }
+  // c128: inner solves to the final tolerance (relative to the scaled residual at their start);
+  // mixed: inner solves that each reduce the scaled residual by inner_tol.
+  const double inner = c128 ? o.tol : std::max(o.inner_tol, o.tol);
+  const int chunk = std::max(1, o.restart);
+  int64_t iters = 0, solves = 0;
+  double relres = 0.0;
+  int status = PETGEM_OK, stalls = 0;
+  double prev = INFINITY;
+  while (true) {
+    {
+      KernelTimer kt(c, "cg_residual_c128", (double)c->nnz * 20 + 8.0 * (n + 1) + 48.0 * n);
+      k_cg_residual<kCgG><<<blocks_for(n * kCgG, 256), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(),
+                                                                    c->val.as<double2>(), x, b, B->r64.as<double2>(),
+                                                                    n);
+      c->launches++;
+    }
+    double rn2 = 0.0;
+    PG_TRY(norm(B->r64.as<double2>(), &rn2));
+    relres = sqrt(rn2) / bnorm;
+    if (!isfinite(relres)) {
+      status = PETGEM_ERR_BREAKDOWN;
+      break;
+    }
+    if (relres <= o.tol) break;
+    if (iters >= o.max_iters) {
+      status = PETGEM_ERR_NOT_CONVERGED;
+      break;
+    }
+    // restarts that no longer halve the FP64 residual: stagnation at the rounding floor
+    stalls = relres > 0.5 * prev ? stalls + 1 : 0;
+    if (stalls >= 3) {
+      status = PETGEM_ERR_NOT_CONVERGED;
+      break;
+    }
+    prev = relres;
+    const double rnorm = sqrt(rn2);
+    k_cg_start<T><<<nb, kT, 0, s>>>(B->r64.as<double2>(), B->sq.as<double2>(), r, p, y, n, st, part, inner,
+                                    1.0 / rnorm);
+    c->launches++;
+    PG_CUDA(cudaGetLastError());
+    int64_t done_iters = 0;
+    while (true) {
+      const int64_t steps = std::min<int64_t>(chunk, o.max_iters - iters - done_iters);
+      if (steps <= 0) break;
+      for (int64_t i = 0; i < steps; ++i) {
+        {
+          KernelTimer kt(c, c128 ? "cg_spmv_c128" : "cg_spmv_c64", spmv_bytes);
+          PG_CUDA(pdl_launch(k_cg_spmv<T, kCgG>, dim3(spmv_grid), dim3(256), 0, s, false,
+                             (const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), at,
+                             (const T*)p, q, n, st, part));
+        }
+        {
+          KernelTimer kt(c, c128 ? "cg_update_c128" : "cg_update_c64", 6.0 * vb);
+          PG_CUDA(pdl_launch(k_cg_update<T>, dim3(vec_grid), dim3(256), 0, s, false, (const T*)p, (const T*)q, r, y, n,
+                             st, part));
+        }
+        {
+          KernelTimer kt(c, c128 ? "cg_dir_c128" : "cg_dir_c64", 3.0 * vb);
+          PG_CUDA(pdl_launch(k_cg_dir<T>, dim3(vec_grid), dim3(256), 0, s, false, (const T*)r, p, n,
+                             (const CState*)st));
+        }
+        c->launches += 3;
+      }
+      PG_TRY(read_cstate(c, B, &hs));
+      done_iters = hs.k;
+      if (hs.done) break;
+    }
+    PG_TRY(read_cstate(c, B, &hs));
+    k_cg_finish<T><<<blocks_for(n, 256), 256, 0, s>>>(y, B->sq.as<double2>(), x, n, rnorm);
+    c->launches++;
+    PG_CUDA(cudaGetLastError());
+    iters += hs.k;
+    solves += 1;
+    if (hs.done == 2 && hs.k == 0) {  // the bilinear form broke down at once: no progress possible
+      status = PETGEM_ERR_BREAKDOWN;
+      break;
+    }
+  }
+  inf.iters = iters;
+  inf.restarts = solves;
+  inf.refinements = solves;
+  inf.true_rel_residual = relres;
+  inf.status = status;
+  return Status{};
+}
+
+}  // namespace
+
+Status run_solve_cocg(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info) {
+  CgBuffers* B = cg_bufs(c);
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n_edges;
+  int sms = 0;
+  PG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+  const bool c128 = o.precision != PETGEM_PREC_MIXED;
+  if (B->version != c->assembly_version) {
+    PG_TRY(B->sq.reserve(n * sizeof(double2)));
+    PG_TRY(B->a128.reserve(c->nnz * sizeof(double2)));
+    PG_TRY(B->a64.reserve(c->nnz * sizeof(float2)));
+    k_cg_sqrt_diag<<<blocks_for(n, 256), 256, 0, s>>>(c->diag.as<double2>(), n, B->sq.as<double2>());
+    k_cg_scale<<<blocks_for(n, 256), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(),
+                                                  B->sq.as<double2>(), n, B->a128.as<double2>(), B->a64.as<float2>());
+    c->launches += 2;
+    PG_CUDA(cudaGetLastError());
+    B->version = c->assembly_version;
+  }
+  const size_t tb = c128 ? sizeof(double2) : sizeof(float2);
+  PG_TRY(B->r64.reserve(n * sizeof(double2)));
+  for (DevBuf* d : {&B->r, &B->p, &B->q, &B->y}) PG_TRY(d->reserve(n * tb));
+  PG_TRY(B->state.reserve(sizeof(CState)));
+  PG_TRY(B->partials.reserve((size_t)std::max<int64_t>(blocks_for(n, kRows), 8LL * sms) * kPStride * sizeof(double2)));
+  PG_CUDA(cudaMemsetAsync(B->state.ptr, 0, sizeof(CState), s));
+  Status worst;
+  for (int32_t src = 0; src < c->n_src; ++src) {
+    petgem_solve_info& inf = info[src];
+    inf = petgem_solve_info{};
+    const double2* b = c->b.as<double2>() + (int64_t)src * n;
+    double2* xs = x + (int64_t)src * n;
+    if (c128)
+      PG_TRY(cocg_source<double2>(c, o, B, b, xs, inf, sms));
+    else
+      PG_TRY(cocg_source<float2>(c, o, B, b, xs, inf, sms));
+    if (inf.status != PETGEM_OK && worst.ok())
+      worst = Status{inf.status, "source " + std::to_string(src) + " did not converge (COCG)"};
+  }
+  PG_CUDA(cudaStreamSynchronize(s));
+  return worst;
+}
+
+void destroy_cocg(petgem_ctx* c) {
+  if (!c->cocg) return;
+  CgBuffers* B = static_cast<CgBuffers*>(c->cocg);
+  for (DevBuf* d : {&B->sq, &B->a128, &B->a64, &B->r64, &B->r, &B->p, &B->q, &B->y, &B->state, &B->partials})
+    d->release();
+  delete B;
+  c->cocg = nullptr;
+}
+
+}  // namespace petgem

@@ -84,6 +84,7 @@ struct petgem_ctx {
 
   // ---- learned preconditioner (learned.cu): network, edge -> grid slots of the current mesh
   petgem::nn::Net* net = nullptr;
+  void* cocg = nullptr;  // COCG solver workspaces (cocg.cu)
   petgem::DevBuf slots;
   bool slots_ready = false;
   double lattice_h = 0.0;
@@ -122,7 +123,9 @@ Status run_receivers(petgem_ctx* c, int32_t n_rcv, const double* rx, const doubl
                      bool* outside);
 Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info);
 Status run_solve_block(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info);
+Status run_solve_cocg(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info);
 Status run_spmv(petgem_ctx* c, const double2* x, double2* y);
 void destroy_solver(petgem_ctx* c);
+void destroy_cocg(petgem_ctx* c);
 
 }  // namespace petgem
