@@ -42,6 +42,7 @@ def parse():
                    help="run one untimed step of the hot path and exit (the command profilers capture)")
     p.add_argument("--precision", default="mixed", choices=["mixed", "c128"], help="solver of --profile-step")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-network measurement")
+    p.add_argument("--no-cocg", action="store_true", help="skip the COCG measurement")
     p.add_argument("--profile-block", type=int, default=0, metavar="ITERS",
                    help="run only the 32-source block solve, capped at ITERS iterations (for ncu)")
     return p.parse_args()
@@ -148,12 +149,12 @@ def run_ours(args):
 
     n_edges = [0]
 
-    def step(precision):
+    def step(precision, method=api.METHOD_GMRES):
         E = api.petgem_mesh_edges(ctx.h, nodes, tets)
         n_edges[0] = E
         api.petgem_assemble(ctx.h, m.freq, sigma, m.sigma_p, m.sources)
         x = torch.zeros((S, E), dtype=torch.complex128, device=dev)
-        st, info = api.petgem_solve(ctx.h, x, S, api.solve_opts(precision=precision, tol=1e-8))
+        st, info = api.petgem_solve(ctx.h, x, S, api.solve_opts(precision=precision, tol=1e-8, method=method))
         out = torch.empty((S, rx.shape[0], 3, 3), dtype=torch.complex128, device=dev)
         api.petgem_receivers(ctx.h, rx, x, out)
         return info, out
@@ -164,9 +165,9 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def timed(precision, steps, warmup, profile=False, clocks=None):
+    def timed(precision, steps, warmup, profile=False, clocks=None, method=api.METHOD_GMRES):
         for _ in range(warmup):
-            step(precision)
+            step(precision, method)
         barrier()
         if profile:
             api.petgem_profile(ctx.h, True)
@@ -177,7 +178,7 @@ def run_ours(args):
         e0.record()
         infos = []
         for _ in range(steps):
-            infos.append(step(precision)[0])
+            infos.append(step(precision, method)[0])
         e1.record()
         barrier()
         cl = clocks.stop() if clocks else None
@@ -230,6 +231,22 @@ def run_ours(args):
         ms_plain, info_plain, _, _ = timed(api.PREC_C128, 1, 1)
         plain = {"ms_per_step": ms_plain, "s_per_source": ms_plain / 1e3 / S, "iters": info_plain[0]["iters"],
                  "true_rel_residual": info_plain[0]["true_rel_residual"]}
+
+    # COCG (short-recurrence complex-symmetric solver), same workload and tolerance: mixed
+    # precision timed like the headline, then one step with per-kernel events.
+    cocg = None
+    if not args.no_cocg:
+        ms_cg, info_cg, _, _ = timed(api.PREC_MIXED, args.steps, 1, method=api.METHOD_COCG)
+        timed(api.PREC_MIXED, 1, 0, profile=True, method=api.METHOD_COCG)
+        cks = {}
+        for name in ("cg_spmv_c64", "cg_update_c64", "cg_residual_c128"):
+            n_, kms, by = api.petgem_kernel_stats(ctx.h, name)
+            if n_:
+                cks[name] = {"launches": n_, "ms": round(kms, 3), "gbs": round(by / (kms * 1e-3) / 1e9, 1)}
+        api.petgem_profile(ctx.h, False)
+        cocg = {"precision": "mixed", "ms_per_step": round(ms_cg, 3), "s_per_source": round(ms_cg / 1e3 / S, 6),
+                "iters": info_cg[0]["iters"], "inner_solves": info_cg[0]["restarts"],
+                "true_rel_residual": info_cg[0]["true_rel_residual"], "kernels": cks}
 
     # Multi-source block solve (all sources of one frequency in one SpMM-based solve): the marine
     # mesh with args.block_sources dipoles along x in [-4, 4] km; timed once after a warm-up.
@@ -360,6 +377,7 @@ def run_ours(args):
             "reorth_steps": info_mixed[0]["reorth"],
             "true_rel_residual": info_mixed[0]["true_rel_residual"],
             "plain_c128": plain,
+            "cocg": cocg,
             "block_multi_source": block,
             "learned_network": learned,
             "speedup_vs_plain": round(plain["ms_per_step"] / ms_mixed, 3) if plain else None,

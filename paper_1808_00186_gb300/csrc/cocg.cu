@@ -301,7 +301,7 @@ template <> __device__ inline double2 cg_beta<double2>(const CState* st) { retur
 // y += alpha p, r -= alpha q, rho' = r^T r, ||r||^2; the last block forms beta = rho' / rho and
 // the stopping test.
 template <typename T>
-__global__ void __launch_bounds__(256) k_cg_update(const T* __restrict__ p, const T* __restrict__ q,
+__global__ void __launch_bounds__(512, 2) k_cg_update(const T* __restrict__ p, const T* __restrict__ q,
                                                    T* __restrict__ r, T* __restrict__ y, int64_t n,
                                                    CState* __restrict__ st, double2* __restrict__ partials) {
   pdl_trigger();
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(256) k_cg_update(const T* __restrict__ p, cons
   }
   rho64 = cadd(rho64, to_d2(rho));
   nr64 = cadd(nr64, to_d2(nr));
-  block_partials2<256>(rho64, nr64, partials);
+  block_partials2<512>(rho64, nr64, partials);
   if (!last_block(&st->counter)) return;
   if (threadIdx.x < 32) {
     const double2 rh = warp_sum_partials(partials, gridDim.x, 0);
@@ -410,6 +410,8 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
   const unsigned spmv_grid =
       (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_for(n * kCgG, 256), (int64_t)CgOcc<T>::value * sms));
   const unsigned vec_grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_for(n, 256), 8LL * sms));
+  // the update reduces two sums over its blocks: a persistent grid keeps the last block's work small
+  const unsigned upd_grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_for(n, 512), 2LL * sms));
   const double vb = (double)sizeof(T) * n;
   const double spmv_bytes = (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 3.0 * vb;
   CState hs;
@@ -429,9 +431,6 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
     inf.status = PETGEM_OK;
     return Status{};
   }
-  // c128: inner solves to the final tolerance (relative to the scaled residual at their start);
-  // mixed: inner solves that each reduce the scaled residual by inner_tol.
-  const double inner = c128 ? o.tol : std::max(o.inner_tol, o.tol);
   const int chunk = std::max(1, o.restart);
   int64_t iters = 0, solves = 0;
   double relres = 0.0;
@@ -464,7 +463,12 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
       break;
     }
     prev = relres;
+    // Inner target: reduce the scaled residual by inner_tol (mixed) but not much below what the
+    // final tolerance still needs (0.3 tol ||b|| / ||r||, a margin for the scaling by S); c128
+    // aims at that need directly.
     const double rnorm = sqrt(rn2);
+    const double need = 0.3 * o.tol * bnorm / rnorm;
+    const double inner = c128 ? need : std::min(std::max(o.inner_tol, need), 0.5);
     k_cg_start<T><<<nb, kT, 0, s>>>(B->r64.as<double2>(), B->sq.as<double2>(), r, p, y, n, st, part, inner,
                                     1.0 / rnorm);
     c->launches++;
@@ -482,7 +486,7 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
         }
         {
           KernelTimer kt(c, c128 ? "cg_update_c128" : "cg_update_c64", 6.0 * vb);
-          PG_CUDA(pdl_launch(k_cg_update<T>, dim3(vec_grid), dim3(256), 0, s, false, (const T*)p, (const T*)q, r, y, n,
+          PG_CUDA(pdl_launch(k_cg_update<T>, dim3(upd_grid), dim3(512), 0, s, false, (const T*)p, (const T*)q, r, y, n,
                              st, part));
         }
         {
