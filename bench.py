@@ -41,6 +41,7 @@ def parse():
     p.add_argument("--profile-step", action="store_true",
                    help="run one untimed step of the hot path and exit (the command profilers capture)")
     p.add_argument("--precision", default="mixed", choices=["mixed", "c128"], help="solver of --profile-step")
+    p.add_argument("--solver", default="gmres", choices=["gmres", "cocg"], help="Krylov method of --profile-step")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-network measurement")
     p.add_argument("--no-cocg", action="store_true", help="skip the COCG measurement")
     p.add_argument("--profile-block", type=int, default=0, metavar="ITERS",
@@ -204,7 +205,8 @@ def run_ours(args):
         return None
 
     if args.profile_step:
-        info, _ = step(api.PREC_MIXED if args.precision == "mixed" else api.PREC_C128)
+        info, _ = step(api.PREC_MIXED if args.precision == "mixed" else api.PREC_C128,
+                       api.METHOD_COCG if args.solver == "cocg" else api.METHOD_GMRES)
         torch.cuda.synchronize()
         print(json.dumps({"profile_step": True, "n": args.n, "edges": n_edges[0], "info": info,
                           "launches": api.petgem_launch_count(ctx.h)}))
@@ -239,7 +241,7 @@ def run_ours(args):
         ms_cg, info_cg, _, _ = timed(api.PREC_MIXED, args.steps, 1, method=api.METHOD_COCG)
         timed(api.PREC_MIXED, 1, 0, profile=True, method=api.METHOD_COCG)
         cks = {}
-        for name in ("cg_spmv_c64", "cg_update_c64", "cg_residual_c128"):
+        for name in ("cg_spmv_c64", "cg_update_c64", "cg_dir_c64", "cg_residual_c128"):
             n_, kms, by = api.petgem_kernel_stats(ctx.h, name)
             if n_:
                 cks[name] = {"launches": n_, "ms": round(kms, 3), "gbs": round(by / (kms * 1e-3) / 1e9, 1)}
@@ -255,33 +257,40 @@ def run_ours(args):
         mb = synth.marine_model(args.n, n_src=args.block_sources)
         Sb = len(mb.sources)
 
-        def block_step():
+        def block_step(method):
             Eb = api.petgem_mesh_edges(ctx.h, nodes, tets)
             api.petgem_assemble(ctx.h, mb.freq, sigma, mb.sigma_p, mb.sources)
             xb = torch.zeros((Sb, Eb), dtype=torch.complex128, device=dev)
-            st, info = api.petgem_solve(ctx.h, xb, Sb, api.solve_opts(precision=api.PREC_MIXED, tol=1e-8, batch=0))
+            st, info = api.petgem_solve(ctx.h, xb, Sb, api.solve_opts(precision=api.PREC_MIXED, tol=1e-8, batch=0,
+                                                                      method=method))
             return info
 
-        block_step()
-        barrier()
-        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        b0.record()
-        binfo = block_step()
-        b1.record()
-        barrier()
-        api.petgem_profile(ctx.h, True)  # per-kernel times: one more solve with events on
-        block_step()
-        barrier()
-        bks = {}
-        for name in ("bspmm_c64", "bmdot_c64", "bmupdate_c64", "bresidual_c128"):
-            n_, kms, by = api.petgem_kernel_stats(ctx.h, name)
-            if n_:
-                bks[name] = {"launches": n_, "ms": round(kms, 3), "gbs": round(by / (kms * 1e-3) / 1e9, 1)}
-        api.petgem_profile(ctx.h, False)
-        bms = b0.elapsed_time(b1)
-        block = {"sources": Sb, "ms_per_step": round(bms, 3), "s_per_source": round(bms / 1e3 / Sb, 6),
-                 "iters_max": max(i["iters"] for i in binfo),
-                 "worst_true_rel_residual": max(i["true_rel_residual"] for i in binfo), "kernels": bks}
+        def block_run(method, names):
+            block_step(method)
+            barrier()
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b0.record()
+            binfo = block_step(method)
+            b1.record()
+            barrier()
+            api.petgem_profile(ctx.h, True)  # per-kernel times: one more solve with events on
+            block_step(method)
+            barrier()
+            bks = {}
+            for name in names:
+                n_, kms, by = api.petgem_kernel_stats(ctx.h, name)
+                if n_:
+                    bks[name] = {"launches": n_, "ms": round(kms, 3), "gbs": round(by / (kms * 1e-3) / 1e9, 1)}
+            api.petgem_profile(ctx.h, False)
+            bms = b0.elapsed_time(b1)
+            return {"sources": Sb, "ms_per_step": round(bms, 3), "s_per_source": round(bms / 1e3 / Sb, 6),
+                    "iters_max": max(i["iters"] for i in binfo),
+                    "worst_true_rel_residual": max(i["true_rel_residual"] for i in binfo), "kernels": bks}
+
+        block = block_run(api.METHOD_GMRES, ("bspmm_c64", "bmdot_c64", "bmupdate_c64", "bresidual_c128"))
+        if not args.no_cocg:
+            block["cocg"] = block_run(api.METHOD_COCG, ("bcg_spmm_c64", "bcg_pq_c64", "bcg_update_c64", "bcg_dir_c64",
+                                                        "bcg_residual_c128"))
 
     # Learned preconditioner (tcgen05 convolutions): the network on this mesh's parent grid
     # ((n+1)^3 nodes), apply time and the convolutions' throughput against the BF16 tensor peak.

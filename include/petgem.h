@@ -97,7 +97,9 @@ typedef struct {
  *     stored.  precision MIXED: complex64 inner solves that each reduce the scaled residual by
  *     inner_tol, restarted from the FP64 residual b - A x; C128: FP64 throughout.  `restart` is
  *     the number of iterations between host checks of the device-side stopping flag; `batch`
- *     and `orth` are ignored; precond must be Jacobi (PETGEM_ERR_UNSUPPORTED otherwise).
+ *     groups sources as for GMRES (their SpMVs become one SpMM; each source keeps its own scalars,
+ *     normalisation and stopping test); `orth` is ignored; precond must be Jacobi
+ *     (PETGEM_ERR_UNSUPPORTED otherwise).
  *     info.restarts counts the inner solves.  A breakdown of the bilinear form (p^T A p = 0) ends
  *     an inner solve early; one at the very first step returns PETGEM_ERR_BREAKDOWN. */
 enum { PETGEM_METHOD_GMRES = 0, PETGEM_METHOD_COCG = 1 };

@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "krylov.cuh"
 
@@ -64,15 +65,27 @@ __device__ inline double2 warp_sum_partials(const double2* partials, int nb, int
   return warp_sum(a);
 }
 
-// Block sums of two complex accumulators (FP64 per warp and block) into partials[b][0..1].
-template <int NT>
-__device__ inline void block_partials2(double2 a0, double2 a1, double2* partials) {
+// Warp tree in the accumulator's own precision (FP32 for complex64 data: an FP64 add costs ~60
+// cycles per warp instruction on this GPU).
+__device__ inline float2 warp_tree(float2 v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+__device__ inline double2 warp_tree(double2 v) { return warp_sum(v); }
+
+// Block sums of two complex accumulators into partials[b][0..1]: the warp tree in the
+// accumulator's precision, FP64 across the warps.
+template <int NT, typename A>
+__device__ inline void block_partials2(A a0, A a1, double2* partials) {
   __shared__ double2 red[NT / 32][2];
-  a0 = warp_sum(a0);
-  a1 = warp_sum(a1);
+  a0 = warp_tree(a0);
+  a1 = warp_tree(a1);
   if ((threadIdx.x & 31) == 0) {
-    red[threadIdx.x >> 5][0] = a0;
-    red[threadIdx.x >> 5][1] = a1;
+    red[threadIdx.x >> 5][0] = to_d2(a0);
+    red[threadIdx.x >> 5][1] = to_d2(a1);
   }
   __syncthreads();
   if (threadIdx.x < 2) {
@@ -172,7 +185,7 @@ __global__ void __launch_bounds__(kT) k_cg_start(const double2* __restrict__ r64
       nr.x += nrm2(t);
     }
   }
-  block_partials2<kT>(to_d2(rho), to_d2(nr), partials);
+  block_partials2<kT>(rho, nr, partials);
   if (!last_block(&st->counter)) return;
   if (threadIdx.x < 32) {
     const double2 a = warp_sum_partials(partials, gridDim.x, 0);
@@ -274,7 +287,7 @@ __global__ void __launch_bounds__(256, CgOcc<T>::value)
     np0 = nnp0;
     np1 = nnp1;
   }
-  block_partials2<256>(to_d2(dot), make_double2(0.0, 0.0), partials);
+  block_partials2<256>(dot, zero<T>(), partials);
   if (!last_block(&st->counter)) return;
   if (threadIdx.x < 32) {
     const double2 pq = warp_sum_partials(partials, gridDim.x, 0);
@@ -329,9 +342,11 @@ __global__ void __launch_bounds__(512, 2) k_cg_update(const T* __restrict__ p, c
       cnt = 0;
     }
   }
-  rho64 = cadd(rho64, to_d2(rho));
-  nr64 = cadd(nr64, to_d2(nr));
-  block_partials2<512>(rho64, nr64, partials);
+  // per-thread totals in the accumulator's precision (FP64 flushes only past 32 elements)
+  rho.x += (decltype(rho.x))rho64.x;
+  rho.y += (decltype(rho.x))rho64.y;
+  nr.x += (decltype(nr.x))nr64.x;
+  block_partials2<512>(rho, nr, partials);
   if (!last_block(&st->counter)) return;
   if (threadIdx.x < 32) {
     const double2 rh = warp_sum_partials(partials, gridDim.x, 0);
@@ -382,6 +397,9 @@ __global__ void k_cg_finish(const T* __restrict__ y, const double2* __restrict__
 
 struct CgBuffers {
   DevBuf sq, a128, a64, r64, r, p, q, y, state, partials;
+  // multi-source solve: interleaved right-hand sides, iterate and residual (c128), vectors (T),
+  // per-source states, group flags and per-source scales / inner targets
+  DevBuf Bt, X, R, rb, pb, qb, yb, bstates, bgrp, bscal;
   int64_t version = -1;
 };
 
@@ -519,6 +537,515 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
   return Status{};
 }
 
+// ------------------------------------------------------------------ multi-source COCG
+// P sources of one frequency iterate in lockstep (element (row i, source s) at i * P + s), each
+// with its own scalars, normalisation and stopping test; the matrix is read once per step for all
+// of them (the SpMM).  A source that met its inner target, or is already converged, stops updating
+// while the others go on.
+struct BGrp {
+  unsigned counter;
+  int all_done;
+};
+
+template <int P>
+__global__ void k_bcg_in(const double2* __restrict__ b, const double2* __restrict__ x, int64_t n, int S_g,
+                         double2* __restrict__ Bt, double2* __restrict__ X) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * P) return;
+  const int64_t i = e / P;
+  const int s = (int)(e - i * P);
+  Bt[e] = s < S_g ? b[(int64_t)s * n + i] : make_double2(0.0, 0.0);
+  X[e] = s < S_g ? x[(int64_t)s * n + i] : make_double2(0.0, 0.0);
+}
+
+template <int P>
+__global__ void k_bcg_out(const double2* __restrict__ X, int64_t n, int S_g, double2* __restrict__ x) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * P) return;
+  const int64_t i = e / P;
+  const int s = (int)(e - i * P);
+  if (s < S_g) x[(int64_t)s * n + i] = X[e];
+}
+
+// R = Bt - A X in FP64, P lanes per row (lane = source).
+template <int P>
+__global__ void __launch_bounds__(256) k_bcg_residual(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                      const double2* __restrict__ val, const double2* __restrict__ X,
+                                                      const double2* __restrict__ Bt, double2* __restrict__ R,
+                                                      int64_t n) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t row = gid / P;
+  const int s = (int)(gid % P);
+  if (row >= n) return;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t p = rp[row]; p < rp[row + 1]; ++p) fma_c(acc, __ldg(&val[p]), X[(int64_t)__ldg(&col[p]) * P + s]);
+  R[row * P + s] = csub(Bt[row * P + s], acc);
+}
+
+// Per-source sums of partials[b * P + s] (double2) over b < nb, one warp per source; every lane of
+// warp w returns the total of source w.
+template <int P>
+__device__ inline double2 source_total(const double2* partials, int nb, int s) {
+  const int lane = threadIdx.x & 31;
+  double2 a = make_double2(0.0, 0.0);
+  for (int b0 = 0; b0 < nb; b0 += 256) {
+    double2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int b = b0 + lane + 32 * m;
+      v[m] = b < nb ? __ldcg(&partials[((int64_t)b * 2) * P + s]) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) a = cadd(a, v[m]);
+  }
+  return warp_sum(a);
+}
+template <int P>
+__device__ inline double2 source_total2(const double2* partials, int nb, int s) {
+  const int lane = threadIdx.x & 31;
+  double2 a = make_double2(0.0, 0.0);
+  for (int b0 = 0; b0 < nb; b0 += 256) {
+    double2 v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int b = b0 + lane + 32 * m;
+      v[m] = b < nb ? __ldcg(&partials[((int64_t)b * 2 + 1) * P + s]) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) a = cadd(a, v[m]);
+  }
+  return warp_sum(a);
+}
+
+// Block sums of two per-source accumulators into partials[(b * 2 + slot) * P + s]: the thread's
+// source is tid mod P (grid strides are multiples of P); tree over the lanes of one source in the
+// accumulator's precision, FP64 across warps.
+template <int NT, int P, typename A>
+__device__ inline void source_partials2(A a0, A a1, double2* partials) {
+  __shared__ double2 red[NT / 32][2][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o >= P; o >>= 1) {
+    a0.x += __shfl_xor_sync(0xffffffffu, a0.x, o);
+    a0.y += __shfl_xor_sync(0xffffffffu, a0.y, o);
+    a1.x += __shfl_xor_sync(0xffffffffu, a1.x, o);
+    a1.y += __shfl_xor_sync(0xffffffffu, a1.y, o);
+  }
+  if (lane < P) {
+    red[warp][0][lane] = to_d2(a0);
+    red[warp][1][lane] = to_d2(a1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * P) {
+    const int slot = threadIdx.x / P, s = threadIdx.x % P;
+    double2 t = make_double2(0.0, 0.0);
+    for (int w = 0; w < NT / 32; ++w) t = cadd(t, red[w][slot][s]);
+    partials[((int64_t)blockIdx.x * 2 + slot) * P + s] = t;
+  }
+}
+
+constexpr int kBcgThreads = 512;  // persistent vector kernels: two blocks per SM
+
+// Per-source ||v_s||^2 (FP64 data) into sts[s].rn2.
+template <int P>
+__global__ void __launch_bounds__(kBcgThreads) k_bcg_norms(const double2* __restrict__ V, int64_t n,
+                                                           CState* __restrict__ sts, BGrp* __restrict__ g,
+                                                           double2* __restrict__ partials) {
+  double a = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)kBcgThreads + threadIdx.x; e < n * P; e += (int64_t)gridDim.x * kBcgThreads)
+    a += nrm2(V[e]);
+  source_partials2<kBcgThreads, P>(make_double2(a, 0.0), make_double2(0.0, 0.0), partials);
+  if (!last_block(&g->counter)) return;
+  const int warp = threadIdx.x >> 5;
+  for (int s = warp; s < P; s += kBcgThreads / 32) {
+    const double2 t = source_total<P>(partials, gridDim.x, s);
+    if ((threadIdx.x & 31) == 0) sts[s].rn2 = t.x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) g->counter = 0;
+}
+
+// Inner-solve start per source: r = p = scale_s S R (rounded to T), y = 0; rho_s, ||r_s||^2, the
+// threshold inner_s^2 ||r_s||^2; scale_s = 0 marks a source that takes no part (done at once).
+template <typename T, int P>
+__global__ void __launch_bounds__(kBcgThreads) k_bcg_start(const double2* __restrict__ R,
+                                                           const double2* __restrict__ sq,
+                                                           const double* __restrict__ scal, T* __restrict__ r,
+                                                           T* __restrict__ p, T* __restrict__ y, int64_t n,
+                                                           CState* __restrict__ sts, BGrp* __restrict__ g,
+                                                           double2* __restrict__ partials) {
+  using A = typename Acc<T>::type;
+  const int s = threadIdx.x % P;
+  const double sc = scal[s];
+  A rho = zero<T>(), nr = zero<T>();
+  for (int64_t e = blockIdx.x * (int64_t)kBcgThreads + threadIdx.x; e < n * P;
+       e += (int64_t)gridDim.x * kBcgThreads) {
+    const T t = from_d2<T>(cscale(cmul(sq[e / P], R[e]), sc));
+    r[e] = t;
+    p[e] = t;
+    y[e] = zero<T>();
+    bil_fma(rho, t, t);
+    nr.x += nrm2(t);
+  }
+  source_partials2<kBcgThreads, P>(rho, nr, partials);
+  if (!last_block(&g->counter)) return;
+  const int warp = threadIdx.x >> 5;
+  for (int q = warp; q < P; q += kBcgThreads / 32) {
+    const double2 a = source_total<P>(partials, gridDim.x, q);
+    const double2 b = source_total2<P>(partials, gridDim.x, q);
+    if ((threadIdx.x & 31) == 0) {
+      CState* st = &sts[q];
+      const double inner = scal[P + q];
+      st->rho = a;
+      st->nr0 = b.x;
+      st->nr = b.x;
+      st->stop2 = inner * inner * b.x;
+      st->k = 0;
+      st->done = (scal[q] != 0.0 && b.x > 0.0 && isfinite(b.x)) ? 0 : ((scal[q] == 0.0 || b.x == 0.0) ? 1 : 2);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int alive = 0;
+    for (int q = 0; q < P; ++q) alive += sts[q].done == 0;
+    g->all_done = alive == 0;
+    g->counter = 0;
+  }
+}
+
+// Q = Atil Pm for all P sources: the row's entries read by its lane group four at a time (the
+// wavefront form of the block GMRES SpMM).
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_bcg_spmm(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                  const T* __restrict__ val, const T* __restrict__ Pm,
+                                                  T* __restrict__ Q, int64_t n, const BGrp* __restrict__ g) {
+  pdl_trigger();
+  pdl_wait();
+  if (g->all_done) return;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t row = gid / P;
+  const int s = (int)(gid % P);
+  if (row >= n) return;
+  typename Acc<T>::type acc = zero<T>(), acc2 = zero<T>();
+  const int64_t p1 = rp[row + 1];
+  int64_t pp = rp[row];
+  for (; pp + 4 <= p1; pp += 4) {
+    int64_t cc[4];
+    T aa[4], xx[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      cc[u] = __ldg(&col[pp + u]);
+      aa[u] = __ldg(&val[pp + u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xx[u] = Pm[cc[u] * P + s];
+    fma_c(acc, aa[0], xx[0]);
+    fma_c(acc2, aa[1], xx[1]);
+    fma_c(acc, aa[2], xx[2]);
+    fma_c(acc2, aa[3], xx[3]);
+  }
+  for (; pp < p1; ++pp) fma_c(acc, __ldg(&val[pp]), Pm[(int64_t)__ldg(&col[pp]) * P + s]);
+  acc.x += acc2.x;
+  acc.y += acc2.y;
+  Q[row * P + s] = from_d2<T>(to_d2(acc));
+}
+
+// Per-source p_s^T q_s; the last block forms alpha_s for every live source.
+template <typename T, int P>
+__global__ void __launch_bounds__(kBcgThreads) k_bcg_pq(const T* __restrict__ Pm, const T* __restrict__ Q, int64_t n,
+                                                        CState* __restrict__ sts, BGrp* __restrict__ g,
+                                                        double2* __restrict__ partials) {
+  pdl_trigger();
+  pdl_wait();
+  if (g->all_done) return;
+  using A = typename Acc<T>::type;
+  A d = zero<T>();
+  for (int64_t e = blockIdx.x * (int64_t)kBcgThreads + threadIdx.x; e < n * P; e += (int64_t)gridDim.x * kBcgThreads)
+    bil_fma(d, Pm[e], Q[e]);
+  source_partials2<kBcgThreads, P>(d, zero<T>(), partials);
+  if (!last_block(&g->counter)) return;
+  const int warp = threadIdx.x >> 5;
+  for (int q = warp; q < P; q += kBcgThreads / 32) {
+    const double2 pq = source_total<P>(partials, gridDim.x, q);
+    if ((threadIdx.x & 31) == 0) {
+      CState* st = &sts[q];
+      if (st->done == 0) {
+        if (!(cabs2(pq) > 0.0) || !isfinite(pq.x) || !isfinite(pq.y)) {
+          st->done = 2;
+        } else {
+          const double2 al = cdiv(st->rho, pq);
+          st->alpha = al;
+          st->alpha32 = make_float2((float)al.x, (float)al.y);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) g->counter = 0;
+}
+
+// y_s += alpha_s p_s, r_s -= alpha_s q_s for live sources; rho'_s, ||r_s||^2; the last block forms
+// beta_s and the stopping tests.
+template <typename T, int P>
+__global__ void __launch_bounds__(kBcgThreads) k_bcg_update(const T* __restrict__ Pm, const T* __restrict__ Q,
+                                                            T* __restrict__ r, T* __restrict__ y, int64_t n,
+                                                            CState* __restrict__ sts, BGrp* __restrict__ g,
+                                                            double2* __restrict__ partials) {
+  pdl_trigger();
+  pdl_wait();
+  if (g->all_done) return;
+  using A = typename Acc<T>::type;
+  const int s = threadIdx.x % P;
+  const bool live = sts[s].done == 0;
+  const T al = cg_alpha<T>(&sts[s]);
+  A rho = zero<T>(), nr = zero<T>();
+  if (live)
+    for (int64_t e = blockIdx.x * (int64_t)kBcgThreads + threadIdx.x; e < n * P;
+         e += (int64_t)gridDim.x * kBcgThreads) {
+      const T pv = Pm[e], qv = Q[e];
+      T yv = y[e], rv = r[e];
+      fma_c(yv, al, pv);
+      sub_mul(rv, qv, al);
+      y[e] = yv;
+      r[e] = rv;
+      bil_fma(rho, rv, rv);
+      nr.x += nrm2(rv);
+    }
+  source_partials2<kBcgThreads, P>(rho, nr, partials);
+  if (!last_block(&g->counter)) return;
+  const int warp = threadIdx.x >> 5;
+  for (int q = warp; q < P; q += kBcgThreads / 32) {
+    const double2 rh = source_total<P>(partials, gridDim.x, q);
+    const double2 nn = source_total2<P>(partials, gridDim.x, q);
+    if ((threadIdx.x & 31) == 0) {
+      CState* st = &sts[q];
+      if (st->done == 0) {
+        st->k += 1;
+        st->nr = nn.x;
+        if (!isfinite(nn.x)) {
+          st->done = 2;
+        } else if (nn.x <= st->stop2) {
+          st->done = 1;
+        } else if (!(cabs2(st->rho) > 0.0)) {
+          st->done = 2;
+        } else {
+          const double2 be = cdiv(rh, st->rho);
+          st->beta = be;
+          st->beta32 = make_float2((float)be.x, (float)be.y);
+          st->rho = rh;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int alive = 0;
+    for (int q = 0; q < P; ++q) alive += sts[q].done == 0;
+    g->all_done = alive == 0;
+    g->counter = 0;
+  }
+}
+
+// p_s = r_s + beta_s p_s for live sources.
+template <typename T, int P>
+__global__ void __launch_bounds__(kBcgThreads) k_bcg_dir(const T* __restrict__ r, T* __restrict__ Pm, int64_t n,
+                                                         const CState* __restrict__ sts,
+                                                         const BGrp* __restrict__ g) {
+  pdl_trigger();
+  pdl_wait();
+  if (g->all_done) return;
+  const int s = threadIdx.x % P;
+  if (sts[s].done != 0) return;
+  const T be = cg_beta<T>(&sts[s]);
+  for (int64_t e = blockIdx.x * (int64_t)kBcgThreads + threadIdx.x; e < n * P;
+       e += (int64_t)gridDim.x * kBcgThreads) {
+    T pv = r[e];
+    fma_c(pv, be, Pm[e]);
+    Pm[e] = pv;
+  }
+}
+
+// X_s += ||r_s|| S y_s for the sources that took part (scale != 0).
+template <typename T, int P>
+__global__ void k_bcg_finish(const T* __restrict__ y, const double2* __restrict__ sq, const double* __restrict__ scal,
+                             double2* __restrict__ X, int64_t n) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * P) return;
+  const int s = (int)(e % P);
+  const double sc = scal[s];
+  if (sc == 0.0) return;
+  X[e] = cadd(X[e], cscale(cmul(sq[e / P], to_d2(y[e])), 1.0 / sc));
+}
+
+template <typename T, int P>
+Status cocg_group(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, const double2* b, double2* x, int S_g,
+                  petgem_solve_info* info, int sms) {
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n_edges, nP = n * P;
+  const bool c128 = sizeof(T) == 16;
+  PG_TRY(B->Bt.reserve(nP * sizeof(double2)));
+  PG_TRY(B->X.reserve(nP * sizeof(double2)));
+  PG_TRY(B->R.reserve(nP * sizeof(double2)));
+  for (DevBuf* d : {&B->rb, &B->pb, &B->qb, &B->yb}) PG_TRY(d->reserve(nP * sizeof(T)));
+  PG_TRY(B->bstates.reserve(P * sizeof(CState)));
+  PG_TRY(B->bgrp.reserve(sizeof(BGrp)));
+  PG_TRY(B->bscal.reserve(2 * P * sizeof(double)));
+  const unsigned vgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_for(nP, kBcgThreads), 2LL * sms));
+  PG_TRY(B->partials.reserve((size_t)vgrid * 2 * P * sizeof(double2) +
+                             (size_t)std::max<int64_t>(blocks_for(n, kRows), 8LL * sms) * kPStride * sizeof(double2)));
+  CState* sts = B->bstates.as<CState>();
+  BGrp* grp = B->bgrp.as<BGrp>();
+  double2* part = B->partials.as<double2>();
+  double* scal = B->bscal.as<double>();
+  const T* at = c128 ? (const T*)B->a128.ptr : (const T*)B->a64.ptr;
+  T *r = B->rb.as<T>(), *pm = B->pb.as<T>(), *q = B->qb.as<T>(), *y = B->yb.as<T>();
+  double2 *Bt = B->Bt.as<double2>(), *X = B->X.as<double2>(), *R = B->R.as<double2>();
+  PG_CUDA(cudaMemsetAsync(sts, 0, P * sizeof(CState), s));
+  PG_CUDA(cudaMemsetAsync(grp, 0, sizeof(BGrp), s));
+  k_bcg_in<P><<<blocks_for(nP, 256), 256, 0, s>>>(b, x, n, S_g, Bt, X);
+  c->launches++;
+  std::vector<CState> hs(P);
+  auto norms = [&](const double2* V) -> Status {
+    k_bcg_norms<P><<<vgrid, kBcgThreads, 0, s>>>(V, n, sts, grp, part);
+    c->launches++;
+    PG_CUDA(cudaGetLastError());
+    PG_CUDA(cudaMemcpyAsync(hs.data(), sts, P * sizeof(CState), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    return Status{};
+  };
+  PG_TRY(norms(Bt));
+  std::vector<double> bn(P), relres(P, 0.0), prev(P, INFINITY), hscal(2 * P, 0.0);
+  std::vector<int64_t> iters(P, 0), solves(P, 0);
+  std::vector<int> status(P, PETGEM_OK), finished(P, 0), stalls(P, 0);
+  for (int i = 0; i < P; ++i) {
+    bn[i] = sqrt(hs[i].rn2);
+    if (i >= S_g || bn[i] == 0.0) finished[i] = 1;
+  }
+  const int chunk = std::max(1, o.restart);
+  const unsigned spmm_grid = blocks_for(nP, 256);
+  const double vb = (double)nP * sizeof(T);
+  const double spmm_bytes = (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 2.0 * vb;
+  int64_t max_done = 0;
+  while (true) {
+    {
+      KernelTimer kt(c, "bcg_residual_c128", (double)c->nnz * 20 + 48.0 * nP);
+      k_bcg_residual<P><<<blocks_for(nP, 256), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(),
+                                                           c->val.as<double2>(), X, Bt, R, n);
+      c->launches++;
+    }
+    PG_TRY(norms(R));
+    bool all = true;
+    for (int i = 0; i < P; ++i) {
+      if (finished[i]) {
+        hscal[i] = 0.0;
+        continue;
+      }
+      const double rn = sqrt(hs[i].rn2);
+      relres[i] = rn / bn[i];
+      if (!isfinite(relres[i])) {
+        status[i] = PETGEM_ERR_BREAKDOWN;
+        finished[i] = 1;
+      } else if (relres[i] <= o.tol) {
+        finished[i] = 1;
+      } else if (iters[i] >= o.max_iters) {
+        status[i] = PETGEM_ERR_NOT_CONVERGED;
+        finished[i] = 1;
+      } else {
+        stalls[i] = relres[i] > 0.5 * prev[i] ? stalls[i] + 1 : 0;
+        if (stalls[i] >= 3) {
+          status[i] = PETGEM_ERR_NOT_CONVERGED;
+          finished[i] = 1;
+        }
+      }
+      prev[i] = relres[i];
+      if (finished[i]) {
+        hscal[i] = 0.0;
+        continue;
+      }
+      all = false;
+      const double need = 0.3 * o.tol * bn[i] / rn;
+      hscal[i] = 1.0 / rn;
+      hscal[P + i] = c128 ? need : std::min(std::max(o.inner_tol, need), 0.5);
+    }
+    if (all) break;
+    PG_CUDA(cudaMemcpyAsync(scal, hscal.data(), 2 * P * sizeof(double), cudaMemcpyHostToDevice, s));
+    k_bcg_start<T, P><<<vgrid, kBcgThreads, 0, s>>>(R, B->sq.as<double2>(), scal, r, pm, y, n, sts, grp, part);
+    c->launches++;
+    PG_CUDA(cudaGetLastError());
+    int64_t done_iters = 0;
+    BGrp hg{};
+    while (true) {
+      const int64_t steps = std::min<int64_t>(chunk, o.max_iters - max_done - done_iters);
+      if (steps <= 0) break;
+      for (int64_t k = 0; k < steps; ++k) {
+        {
+          KernelTimer kt(c, c128 ? "bcg_spmm_c128" : "bcg_spmm_c64", spmm_bytes);
+          PG_CUDA(pdl_launch(k_bcg_spmm<T, P>, dim3(spmm_grid), dim3(256), 0, s, false,
+                             (const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), at,
+                             (const T*)pm, q, n, (const BGrp*)grp));
+        }
+        {
+          KernelTimer kt(c, c128 ? "bcg_pq_c128" : "bcg_pq_c64", 2.0 * vb);
+          PG_CUDA(pdl_launch(k_bcg_pq<T, P>, dim3(vgrid), dim3(kBcgThreads), 0, s, false, (const T*)pm, (const T*)q, n,
+                             sts, grp, part));
+        }
+        {
+          KernelTimer kt(c, c128 ? "bcg_update_c128" : "bcg_update_c64", 6.0 * vb);
+          PG_CUDA(pdl_launch(k_bcg_update<T, P>, dim3(vgrid), dim3(kBcgThreads), 0, s, false, (const T*)pm,
+                             (const T*)q, r, y, n, sts, grp, part));
+        }
+        {
+          KernelTimer kt(c, c128 ? "bcg_dir_c128" : "bcg_dir_c64", 3.0 * vb);
+          PG_CUDA(pdl_launch(k_bcg_dir<T, P>, dim3(vgrid), dim3(kBcgThreads), 0, s, false, (const T*)r, pm, n,
+                             (const CState*)sts, (const BGrp*)grp));
+        }
+        c->launches += 4;
+      }
+      done_iters += steps;
+      PG_CUDA(cudaMemcpyAsync(&hg, grp, sizeof(BGrp), cudaMemcpyDeviceToHost, s));
+      PG_CUDA(cudaStreamSynchronize(s));
+      if (hg.all_done) break;
+    }
+    PG_CUDA(cudaMemcpyAsync(hs.data(), sts, P * sizeof(CState), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    k_bcg_finish<T, P><<<blocks_for(nP, 256), 256, 0, s>>>(y, B->sq.as<double2>(), scal, X, n);
+    c->launches++;
+    PG_CUDA(cudaGetLastError());
+    for (int i = 0; i < P; ++i) {
+      if (finished[i]) continue;
+      iters[i] += hs[i].k;
+      solves[i] += 1;
+      max_done = std::max(max_done, iters[i]);
+      if (hs[i].done == 2 && hs[i].k == 0) {  // the bilinear form broke down at once
+        status[i] = PETGEM_ERR_BREAKDOWN;
+        finished[i] = 1;
+      }
+    }
+  }
+  k_bcg_out<P><<<blocks_for(nP, 256), 256, 0, s>>>(X, n, S_g, x);
+  c->launches++;
+  PG_CUDA(cudaGetLastError());
+  for (int i = 0; i < S_g; ++i) {
+    info[i] = petgem_solve_info{};
+    info[i].iters = iters[i];
+    info[i].restarts = solves[i];
+    info[i].refinements = solves[i];
+    info[i].true_rel_residual = relres[i];
+    info[i].status = status[i];
+  }
+  return Status{};
+}
+
+template <typename T>
+Status cocg_group_p(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, const double2* b, double2* x, int S_g,
+                    petgem_solve_info* info, int sms) {
+  if (S_g <= 2) return cocg_group<T, 2>(c, o, B, b, x, S_g, info, sms);
+  if (S_g <= 4) return cocg_group<T, 4>(c, o, B, b, x, S_g, info, sms);
+  if (S_g <= 8) return cocg_group<T, 8>(c, o, B, b, x, S_g, info, sms);
+  if (S_g <= 16) return cocg_group<T, 16>(c, o, B, b, x, S_g, info, sms);
+  return cocg_group<T, 32>(c, o, B, b, x, S_g, info, sms);
+}
+
 }  // namespace
 
 Status run_solve_cocg(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info) {
@@ -546,6 +1073,22 @@ Status run_solve_cocg(petgem_ctx* c, const petgem_solve_opts& o, double2* x, pet
   PG_TRY(B->partials.reserve((size_t)std::max<int64_t>(blocks_for(n, kRows), 8LL * sms) * kPStride * sizeof(double2)));
   PG_CUDA(cudaMemsetAsync(B->state.ptr, 0, sizeof(CState), s));
   Status worst;
+  if (o.batch != 1 && c->n_src > 1) {  // sources of one frequency together, up to 32 per group
+    const int group = o.batch <= 0 ? 32 : std::min(o.batch, 32);
+    for (int s0 = 0; s0 < c->n_src; s0 += group) {
+      const int S_g = std::min(group, c->n_src - s0);
+      const double2* b = c->b.as<double2>() + (int64_t)s0 * n;
+      if (c128)
+        PG_TRY(cocg_group_p<double2>(c, o, B, b, x + (int64_t)s0 * n, S_g, info + s0, sms));
+      else
+        PG_TRY(cocg_group_p<float2>(c, o, B, b, x + (int64_t)s0 * n, S_g, info + s0, sms));
+    }
+    PG_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < c->n_src; ++i)
+      if (info[i].status != PETGEM_OK && worst.ok())
+        worst = Status{info[i].status, "source " + std::to_string(i) + " did not converge (COCG)"};
+    return worst;
+  }
   for (int32_t src = 0; src < c->n_src; ++src) {
     petgem_solve_info& inf = info[src];
     inf = petgem_solve_info{};
@@ -565,7 +1108,8 @@ Status run_solve_cocg(petgem_ctx* c, const petgem_solve_opts& o, double2* x, pet
 void destroy_cocg(petgem_ctx* c) {
   if (!c->cocg) return;
   CgBuffers* B = static_cast<CgBuffers*>(c->cocg);
-  for (DevBuf* d : {&B->sq, &B->a128, &B->a64, &B->r64, &B->r, &B->p, &B->q, &B->y, &B->state, &B->partials})
+  for (DevBuf* d : {&B->sq, &B->a128, &B->a64, &B->r64, &B->r, &B->p, &B->q, &B->y, &B->state, &B->partials, &B->Bt,
+                    &B->X, &B->R, &B->rb, &B->pb, &B->qb, &B->yb, &B->bstates, &B->bgrp, &B->bscal})
     d->release();
   delete B;
   c->cocg = nullptr;

@@ -64,6 +64,12 @@ __device__ inline double2 lane_tree(double2 a) {
   return a;
 }
 template <int P>
+__device__ inline float lane_tree(float a) {
+#pragma unroll
+  for (int o = 16; o >= P; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  return a;
+}
+template <int P>
 __device__ inline double lane_tree(double a) {
 #pragma unroll
   for (int o = 16; o >= P; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -312,9 +318,10 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSM)
     }
   }
   if (!finish) return;
-  nrm += (double)part.x;
-  nrm = lane_tree<P>(nrm);
-  if (lane < P) red[warp][lane] = nrm;
+  // the thread's total and the warp tree in the accumulator's precision, FP64 across warps
+  using AS = decltype(part.x);
+  const AS tot = lane_tree<P>((AS)(nrm + (double)part.x));
+  if (lane < P) red[warp][lane] = (double)tot;
   __syncthreads();
   if (tid < P) {
     double a = 0.0;
