@@ -41,12 +41,18 @@ def parse():
     p.add_argument("--profile-step", action="store_true",
                    help="run one untimed step of the hot path and exit (the command profilers capture)")
     p.add_argument("--precision", default="mixed", choices=["mixed", "c128"], help="solver of --profile-step")
-    p.add_argument("--solver", default="gmres", choices=["gmres", "cocg"], help="Krylov method of --profile-step")
+    p.add_argument("--solver", default="gmres", choices=["gmres", "cocg"], help="Krylov method of --profile-step / --profile-block")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-network measurement")
     p.add_argument("--no-cocg", action="store_true", help="skip the COCG measurement")
     p.add_argument("--profile-block", type=int, default=0, metavar="ITERS",
                    help="run only the 32-source block solve, capped at ITERS iterations (for ncu)")
     return p.parse_args()
+
+
+# DRAM traffic per launch / algorithmic bytes per launch, from one ncu capture of each kernel at
+# 48^3 (profiles/krylov_kernels_marine_n48_full.md, Arnoldi step j = 20): these kernels stream
+# their vectors once, so the traffic of a bench launch is this ratio times its algorithmic bytes.
+TRAFFIC_RATIO = {"spmv_c64": 0.9988, "mdot_c64": 1.0322, "cgs_upd_c64": 0.9890}
 
 
 def tensor_peak():
@@ -197,7 +203,9 @@ def run_ours(args):
         xb = torch.zeros((len(mb.sources), Eb), dtype=torch.complex128, device=dev)
         _, binfo = api.petgem_solve(ctx.h, xb, len(mb.sources),
                                     api.solve_opts(precision=api.PREC_MIXED, tol=1e-8, batch=0,
-                                                   max_iters=args.profile_block), allow_not_converged=True)
+                                                   max_iters=args.profile_block,
+                                                   method=api.METHOD_COCG if args.solver == "cocg" else api.METHOD_GMRES),
+                                    allow_not_converged=True)
         torch.cuda.synchronize()
         print(json.dumps({"profile_block": True, "n": args.n, "edges": Eb, "iters": max(i["iters"] for i in binfo),
                           "launches": api.petgem_launch_count(ctx.h)}))
@@ -362,7 +370,10 @@ def run_ours(args):
             achieved = ks["gbs"]
             roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(achieved / hbm, 4), "peak_source": peak_kind,
-                    "traffic": None, "launches": ks["launches"], "avg_launch_us": round(ks["ms"] / ks["launches"] * 1e3, 2),
+                    "traffic": (round(TRAFFIC_RATIO[name] * ks["bytes"] / ks["launches"]) if name in TRAFFIC_RATIO
+                                else None),
+                    "traffic_unit": "bytes per launch (ncu DRAM read+write, scaled from 48^3)",
+                    "launches": ks["launches"], "avg_launch_us": round(ks["ms"] / ks["launches"] * 1e3, 2),
                     "algorithmic_bytes_per_launch": ks["bytes"] / ks["launches"]}
         s_per_source = ms_mixed / 1e3 / S
         result = {
