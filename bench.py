@@ -249,7 +249,7 @@ def run_ours(args):
         ms_cg, info_cg, _, _ = timed(api.PREC_MIXED, args.steps, 1, method=api.METHOD_COCG)
         timed(api.PREC_MIXED, 1, 0, profile=True, method=api.METHOD_COCG)
         cks = {}
-        for name in ("cg_spmv_c64", "cg_update_c64", "cg_dir_c64", "cg_residual_c128"):
+        for name in ("cg_inner_c64", "cg_residual_c128"):
             n_, kms, by = api.petgem_kernel_stats(ctx.h, name)
             if n_:
                 cks[name] = {"launches": n_, "ms": round(kms, 3), "gbs": round(by / (kms * 1e-3) / 1e9, 1)}

@@ -31,6 +31,10 @@ KernelTimer::~KernelTimer() {
   c->pending.push_back(PendingTiming{name, e0, e1, bytes, iter, pass});
 }
 
+void set_last_timing_bytes(petgem_ctx* c, double bytes) {
+  if (c->profiling && !c->pending.empty()) c->pending.back().bytes = bytes;
+}
+
 void drop_idle_timings(petgem_ctx* c, size_t from, int k, const uint8_t* refined) {
   std::vector<PendingTiming> keep(c->pending.begin(), c->pending.begin() + std::min(from, c->pending.size()));
   for (size_t i = from; i < c->pending.size(); ++i) {

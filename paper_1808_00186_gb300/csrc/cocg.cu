@@ -9,11 +9,11 @@
 // would not be, and COCG diverges on it).  An inner solve iterates on Atil y = S r and returns
 // x += S y.
 //
-// Per iteration: the SpMV q = Atil p with the bilinear dot p^T q fused into it (its last block
-// forms alpha = rho / p^T q), the update kernel (y += alpha p, r -= alpha q, r^T r and ||r||^2; its
-// last block forms beta and the stopping test) and the direction update p = r + beta p.  The
-// scalars live on the device, so a chunk of iterations runs without host synchronisation, and the
-// kernels after a stop return at once.  Mixed precision: Atil and the vectors in complex64 (FP32
+// The iterations run in one persistent cooperative kernel (k_cg_inner): per iteration the SpMV
+// q = Atil p with the bilinear p^T q fused into it, the residual update (r -= alpha q, r^T r and
+// ||r||^2) and the pass y += alpha p, p = r + beta p, separated by barriers over the grid instead
+// of kernel boundaries.  The scalars never leave the device; the host looks at the state once per
+// chunk of iterations.  Mixed precision: Atil and the vectors in complex64 (FP32
 // products within a thread and its warp, FP64 beyond); each inner solve runs until its residual fell
 // by inner_tol and restarts from the FP64 true residual b - A x (iterative refinement).  c128:
 // everything in FP64, one inner solve to the final tolerance.
@@ -32,6 +32,11 @@ struct CState {
   int k;     // iterations of this inner solve
   unsigned counter;
   int pad;
+  unsigned long long gbar;  // arrivals at the persistent kernel's barriers (only grows)
+  unsigned long long grel;  // the last release of a reducing barrier (the arrival count it closed)
+  double2 sc;               // the scalar a reducing barrier published (alpha or beta)
+  int sc_dn;                // and its stopping decision
+  int pad2;
   double2 rho;  // r^T r
   double2 alpha, beta;
   float2 alpha32, beta32;
@@ -41,6 +46,7 @@ struct CState {
 
 constexpr int kCgG = 4;  // lanes per row of the CSR products (rows hold at most ~19 entries)
 constexpr int kCgU = 5;  // entries per lane in one batch
+constexpr unsigned long long kCgWaitNs = 2000000000ull;  // bound of a barrier wait (2 s)
 template <typename T> struct CgOcc { static constexpr int value = 4; };
 template <> struct CgOcc<double2> { static constexpr int value = 3; };
 
@@ -197,6 +203,8 @@ __global__ void __launch_bounds__(kT) k_cg_start(const double2* __restrict__ r64
       st->stop2 = inner * inner * b.x;
       st->k = 0;
       st->done = (b.x > 0.0 && isfinite(b.x)) ? 0 : (b.x == 0.0 ? 1 : 2);
+      st->gbar = 0;
+      st->grel = 0;
       st->counter = 0;
     }
   }
@@ -213,49 +221,232 @@ __device__ inline void cg_fetch(const int32_t* __restrict__ col, const T* __rest
   }
 }
 
-// q = Atil p and the bilinear p^T q; the last block forms alpha = rho / p^T q.  Persistent and
-// software-pipelined like the Arnoldi SpMV: the gathers of row i overlap the column/value loads of
-// row i + 1 and the row pointers of row i + 2.
+// One system of a persistent COCG launch: its CSR operator (row pointers, columns, values of
+// Atil), its four vectors, its state and block partials, and the range of blocks that serve it.
+template <typename T>
+struct CgSys {
+  const int64_t* rp;
+  const int32_t* col;
+  const T* val;
+  T *p, *q, *r, *y;
+  int64_t n;
+  CState* st;
+  double2* part;  // [nb][kCgSlots]: slot 0 r^T r, 1 ||r||^2, 2 p^T q
+  int b0, nb;
+};
+constexpr int kCgSlots = 4;
+
+__device__ inline unsigned long long cg_now() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Barrier over the nb blocks of one system.  gbar counts arrivals and only grows; every block
+// arrives once per barrier, so each barrier's arrivals are the next nb tickets.  Thread 0 arrives
+// with a release add and waits with acquire loads; the block barriers on either side carry the
+// ordering to the other threads, so every block's writes before the barrier are visible to every
+// block's reads after it.  The wait is bounded (kCgWaitNs): false in every thread of the block when
+// it gave up.
+__device__ inline bool cg_barrier(unsigned long long* gbar, unsigned nb, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t;
+    asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(t) : "l"(gbar) : "memory");
+    const unsigned long long target = (t / nb + 1) * nb;
+    int ok = 1;
+    const unsigned long long w0 = cg_now();
+    while (true) {
+      unsigned long long v;
+      asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(gbar) : "memory");
+      if (v >= target) break;
+      if (cg_now() - w0 > kCgWaitNs) {
+        ok = 0;
+        break;
+      }
+    }
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// Fixed-order FP64 sums of part[b * kCgSlots + s0] and part[b * kCgSlots + s1] over b < nb by the
+// whole block: each thread a few partials (all loads in flight at once), a warp tree, then one over
+// the warps; out[0], out[1] (shared) receive the totals.
+template <int NT>
+__device__ inline void cg_sum_blocks2(const double2* part, int nb, int s0, int s1, double2* out) {
+  __shared__ double2 red[NT / 32][2];
+  double2 a = make_double2(0.0, 0.0), b = a;
+  for (int k = threadIdx.x; k < nb; k += NT) {
+    a = cadd(a, __ldcg(&part[(int64_t)k * kCgSlots + s0]));
+    b = cadd(b, __ldcg(&part[(int64_t)k * kCgSlots + s1]));
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[warp][0] = a;
+    red[warp][1] = b;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double2 u = lane < NT / 32 ? red[lane][0] : make_double2(0.0, 0.0);
+    double2 v = lane < NT / 32 ? red[lane][1] : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int o = NT / 64; o > 0; o >>= 1) {
+      u.x += __shfl_xor_sync(0xffffffffu, u.x, o);
+      u.y += __shfl_xor_sync(0xffffffffu, u.y, o);
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    if (lane == 0) {
+      out[0] = u;
+      out[1] = v;
+    }
+  }
+}
+
+// Reducing barrier over the nb blocks of one system: the last block to arrive (it sees every
+// other block's partials) sums the block partials once, with all its threads, forms the step's
+// scalar and decision in the state, and releases the others, which read the published scalar
+// (sc, sc_dn).  One block reads the partials instead of every block (which would make every block
+// fetch the same lines from L2 and spend the SM's scarce FP64 issue slots on the same sums).
+//   stage 0 (after the SpMV): alpha = rho / p^T q, or a breakdown of the bilinear form.
+//   stage 1 (after the update): r^T r and ||r||^2; the stopping test, beta = rho' / rho, k, nr.
+// The wait is bounded (kCgWaitNs); the result is false in every thread when it gave up.  On
+// return *s_sc and *s_dn hold the scalar and decision in every block.
+template <int NT, int STAGE>
+__device__ inline bool cg_reduce_barrier(CState* st, const double2* part, unsigned nb, int* s_ok, int* s_last,
+                                         double2* s_sc, int* s_dn) {
+  __syncthreads();
+  unsigned long long target = 0;  // this barrier's closing arrival count (thread 0)
+  if (threadIdx.x == 0) {
+    unsigned long long t;
+    asm volatile("atom.add.acq_rel.gpu.u64 %0, [%1], 1;" : "=l"(t) : "l"(&st->gbar) : "memory");
+    target = (t / nb + 1) * nb;
+    *s_last = t + 1 == target;
+    int ok = 1;
+    if (t + 1 != target) {
+      const unsigned long long w0 = cg_now();
+      while (true) {
+        unsigned long long v;
+        asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(&st->grel) : "memory");
+        if (v >= target) break;
+        if (cg_now() - w0 > kCgWaitNs) {
+          ok = 0;
+          break;
+        }
+      }
+    }
+    *s_ok = ok;
+  }
+  __syncthreads();
+  if (!*s_ok) return false;
+  if (*s_last) {
+    __shared__ double2 tot[2];
+    cg_sum_blocks2<NT>(part, nb, STAGE == 0 ? 2 : 0, STAGE == 0 ? 3 : 1, tot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int d = 0;
+      double2 sc = make_double2(0.0, 0.0);
+      if (STAGE == 0) {
+        const double2 pq = tot[0];
+        if (!(cabs2(pq) > 0.0) || !isfinite(pq.x) || !isfinite(pq.y)) {
+          d = 2;
+        } else {
+          sc = cdiv(st->rho, pq);
+          st->alpha = sc;
+        }
+      } else {
+        const double nrm = tot[1].x;
+        st->k += 1;
+        st->nr = nrm;
+        if (!isfinite(nrm))
+          d = 2;
+        else if (nrm <= st->stop2)
+          d = 1;
+        else if (!(cabs2(st->rho) > 0.0))
+          d = 2;
+        if (!d) {
+          sc = cdiv(tot[0], st->rho);
+          st->beta = sc;
+          st->rho = tot[0];
+        }
+      }
+      if (d) st->done = d;
+      st->sc = sc;
+      st->sc_dn = d;
+      *s_sc = sc;
+      *s_dn = d;
+      asm volatile("st.release.gpu.u64 [%0], %1;" ::"l"(&st->grel), "l"(target) : "memory");
+    }
+  } else if (threadIdx.x == 0) {
+    *s_sc = __ldcg(&st->sc);
+    *s_dn = __ldcg(&st->sc_dn);
+  }
+  __syncthreads();
+  return true;
+}
+
+// Block sums of two accumulators into out[0], out[1] (warp tree in the accumulator's precision,
+// FP64 across warps).
+template <int NT, typename A>
+__device__ inline void cg_block_sums(A a0, A a1, double2* out) {
+  __shared__ double2 red[NT / 32][2];
+  a0 = warp_tree(a0);
+  a1 = warp_tree(a1);
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = to_d2(a0);
+    red[threadIdx.x >> 5][1] = to_d2(a1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int w = 0; w < NT / 32; ++w) s = cadd(s, red[w][threadIdx.x]);
+    out[threadIdx.x] = s;
+  }
+}
+
+// q = Atil p over the rows row0, row0 + groups, ... (G lanes per row), software-pipelined: the
+// gathers of row i overlap the column/value loads of row i + 1 and the row pointers of row i + 2.
+// Returns this thread's share of the bilinear p^T q.  p is written by other blocks of the same
+// launch between calls, so its gathers are plain (coherent after the barrier) loads, not
+// read-only-cache loads; the matrix is read-only.
 template <typename T, int G>
-__global__ void __launch_bounds__(256, CgOcc<T>::value)
-    k_cg_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const T* __restrict__ val,
-              const T* __restrict__ p, T* __restrict__ q, int64_t n, CState* __restrict__ st,
-              double2* __restrict__ partials) {
-  pdl_trigger();
-  pdl_wait();
-  if (st->done) return;
+__device__ inline typename Acc<T>::type cg_spmv_rows(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                     const T* __restrict__ val, const T* p, T* q, int64_t n,
+                                                     int64_t row, int64_t groups) {
   constexpr int U = kCgU;
   using A = typename Acc<T>::type;
-  const int64_t groups = (int64_t)gridDim.x * (256 / G);
   const int lane = threadIdx.x % G;
-  int64_t row = blockIdx.x * (int64_t)(256 / G) + threadIdx.x / G;
   int64_t p0 = 0, p1 = 0;
   if (row < n) {
-    p0 = rp[row] + lane;
-    p1 = rp[row + 1];
+    p0 = __ldg(&rp[row]) + lane;
+    p1 = __ldg(&rp[row + 1]);
   }
   int32_t c[U];
   T a[U];
   cg_fetch<T, G>(col, val, p0, p1, c, a);
   int64_t nrow = row + groups, np0 = 0, np1 = 0;
   if (nrow < n) {
-    np0 = rp[nrow] + lane;
-    np1 = rp[nrow + 1];
+    np0 = __ldg(&rp[nrow]) + lane;
+    np1 = __ldg(&rp[nrow + 1]);
   }
   A dot = zero<T>();
   while (__any_sync(0xffffffffu, row < n)) {
     T xv[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = p0 + (int64_t)u * G < p1 ? __ldg(&p[c[u]]) : zero<T>();
-    const T prow = (row < n && lane == 0) ? __ldg(&p[row]) : zero<T>();
+    for (int u = 0; u < U; ++u) xv[u] = p0 + (int64_t)u * G < p1 ? p[c[u]] : zero<T>();
+    const T prow = (row < n && lane == 0) ? p[row] : zero<T>();
     int32_t c2[U];
     T a2[U];
     cg_fetch<T, G>(col, val, np0, np1, c2, a2);
     const int64_t nnrow = nrow + groups;
     int64_t nnp0 = 0, nnp1 = 0;
     if (nnrow < n) {
-      nnp0 = rp[nnrow] + lane;
-      nnp1 = rp[nnrow + 1];
+      nnp0 = __ldg(&rp[nnrow]) + lane;
+      nnp1 = __ldg(&rp[nnrow + 1]);
     }
     A acc = zero<T>(), acc2 = zero<T>();
 #pragma unroll
@@ -263,7 +454,7 @@ __global__ void __launch_bounds__(256, CgOcc<T>::value)
       fma_c(acc, a[u], xv[u]);
       if (u + 1 < U) fma_c(acc2, a[u + 1], xv[u + 1]);
     }
-    for (int64_t qq = p0 + (int64_t)U * G; qq < p1; qq += G) fma_c(acc, __ldg(&val[qq]), __ldg(&p[__ldg(&col[qq])]));
+    for (int64_t qq = p0 + (int64_t)U * G; qq < p1; qq += G) fma_c(acc, __ldg(&val[qq]), p[__ldg(&col[qq])]);
     acc.x += acc2.x;
     acc.y += acc2.y;
     for (int o = G / 2; o > 0; o >>= 1) {
@@ -287,21 +478,158 @@ __global__ void __launch_bounds__(256, CgOcc<T>::value)
     np0 = nnp0;
     np1 = nnp1;
   }
-  block_partials2<256>(dot, zero<T>(), partials);
-  if (!last_block(&st->counter)) return;
-  if (threadIdx.x < 32) {
-    const double2 pq = warp_sum_partials(partials, gridDim.x, 0);
-    if (threadIdx.x == 0) {
-      if (!(cabs2(pq) > 0.0) || !isfinite(pq.x) || !isfinite(pq.y)) {
-        st->done = 2;
-      } else {
-        const double2 al = cdiv(st->rho, pq);
-        st->alpha = al;
-        st->alpha32 = make_float2((float)al.x, (float)al.y);
+  return dot;
+}
+
+// The iterations of an inner COCG solve, persistent: one launch runs up to max_steps iterations
+// of every system in sys[0, nsys), each on its own blocks [b0, b0 + nb), and stops a system when
+// its residual met the inner threshold or its bilinear form broke down.  Per iteration and system
+// three phases, each closed by a barrier over the system's blocks:
+//   SpMV    q = Atil p and the block sums of p^T q;  (reducing barrier: alpha)
+//   update  r -= alpha q, block sums of r^T r and ||r||^2;  (reducing barrier: beta, the stopping
+//           test)
+//   then    y += alpha p and the direction p = r + beta p (one pass over p).
+// The scalars are formed once per barrier, by the block that arrives last, and the state always
+// holds the current rho, k and ||r||^2.  The grid must be resident at once (cooperative launch).
+// A barrier that gives up sets done = 3.
+template <typename T, int G>
+__global__ void __launch_bounds__(256, CgOcc<T>::value)
+    k_cg_inner(const CgSys<T>* __restrict__ sys, int nsys, int max_steps) {
+  __shared__ int s_sys, s_ok, s_dn, s_last;
+  __shared__ double2 s_sc;
+  pdl_wait();
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    int k = 0;
+    while (k + 1 < nsys && (int)blockIdx.x >= sys[k + 1].b0) ++k;
+    s_sys = k;
+  }
+  __syncthreads();
+  const CgSys<T>* S = &sys[s_sys];
+  const int lb = (int)blockIdx.x - S->b0, nb = S->nb;
+  if (lb < 0 || lb >= nb) return;  // blocks past the last system's range (none when the host sizes the grid)
+  CState* st = S->st;
+  // read before the first barrier: the barriers' last blocks rewrite the state after it
+  if (st->done) return;
+  const int64_t n = S->n;
+  const int64_t* rp = S->rp;
+  const int32_t* col = S->col;
+  const T* val = S->val;
+  T *p = S->p, *q = S->q, *r = S->r, *y = S->y;
+  double2* part = S->part;
+  using A = typename Acc<T>::type;
+  const int64_t groups = (int64_t)nb * (256 / G);
+  const int64_t row0 = (int64_t)lb * (256 / G) + tid / G;
+  const int64_t stride = (int64_t)nb * 256, first = (int64_t)lb * 256 + tid;
+  bool fail = false;
+  for (int step = 0; step < max_steps; ++step) {
+    const A dot = cg_spmv_rows<T, G>(rp, col, val, p, q, n, row0, groups);
+    cg_block_sums<256>(dot, zero<T>(), part + (int64_t)lb * kCgSlots + 2);
+    if (!cg_reduce_barrier<256, 0>(st, part, nb, &s_ok, &s_last, &s_sc, &s_dn)) {
+      fail = true;
+      break;
+    }
+    if (s_dn) break;
+    const T al = from_d2<T>(s_sc);
+    A rh = zero<T>(), nr = zero<T>();
+    double2 rh64 = make_double2(0.0, 0.0), nr64 = rh64;
+    int cnt = 0;
+    // r -= alpha q (y += alpha p waits for the direction pass, which reads p anyway); four
+    // elements per thread in flight, then the ragged tail one by one
+    int64_t i = first;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+      T qv[4], rv[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        qv[v] = __ldcg(&q[i + v * stride]);
+        rv[v] = r[i + v * stride];
       }
-      st->counter = 0;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        sub_mul(rv[v], qv[v], al);
+        r[i + v * stride] = rv[v];
+        bil_fma(rh, rv[v], rv[v]);
+        nr.x += nrm2(rv[v]);
+      }
+      cnt += 4;
+      if (cnt >= 32) {  // the accumulator's precision over at most 32 elements, then FP64
+        rh64 = cadd(rh64, to_d2(rh));
+        nr64 = cadd(nr64, to_d2(nr));
+        rh = zero<T>();
+        nr = zero<T>();
+        cnt = 0;
+      }
+    }
+    for (; i < n; i += stride) {
+      T rv = r[i];
+      sub_mul(rv, __ldcg(&q[i]), al);
+      r[i] = rv;
+      bil_fma(rh, rv, rv);
+      nr.x += nrm2(rv);
+    }
+    rh.x += (decltype(rh.x))rh64.x;
+    rh.y += (decltype(rh.x))rh64.y;
+    nr.x += (decltype(nr.x))nr64.x;
+    cg_block_sums<256>(rh, nr, part + (int64_t)lb * kCgSlots);
+    if (!cg_reduce_barrier<256, 1>(st, part, nb, &s_ok, &s_last, &s_sc, &s_dn)) {
+      fail = true;
+      break;
+    }
+    if (s_dn) {  // stopped: the iterate still takes this step's alpha p
+      for (int64_t j = first; j < n; j += stride) {
+        T yv = y[j];
+        fma_c(yv, al, p[j]);
+        y[j] = yv;
+      }
+      break;
+    }
+    // y += alpha p and p = r + beta p
+    const T be = from_d2<T>(s_sc);
+    int64_t j = first;
+    for (; j + 3 * stride < n; j += 4 * stride) {
+      T a[4], b[4], c[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        a[v] = r[j + v * stride];
+        b[v] = p[j + v * stride];
+        c[v] = y[j + v * stride];
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        fma_c(c[v], al, b[v]);
+        y[j + v * stride] = c[v];
+        fma_c(a[v], be, b[v]);
+        p[j + v * stride] = a[v];
+      }
+    }
+    for (; j < n; j += stride) {
+      const T pv = p[j];
+      T yv = y[j], rv = r[j];
+      fma_c(yv, al, pv);
+      y[j] = yv;
+      fma_c(rv, be, pv);
+      p[j] = rv;
+    }
+    if (!cg_barrier(&st->gbar, nb, &s_ok)) {
+      fail = true;
+      break;
     }
   }
+  if (fail && tid == 0) atomicExch(&st->done, 3);
+}
+
+constexpr int kCgChunk = 1024;  // iterations per persistent launch (the host checks the state between)
+
+// Whether the persistent kernel's grid (CgOcc blocks per SM) can be resident at once.
+template <typename T>
+Status cg_setup() {
+  static bool done = false;
+  if (done) return Status{};
+  int nb = 0;
+  PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_inner<T, kCgG>, 256, 0));
+  if (nb < CgOcc<T>::value) return Status{PETGEM_ERR_UNSUPPORTED, "COCG kernel: too few resident blocks per SM"};
+  done = true;
+  return Status{};
 }
 
 template <typename T> __device__ inline T cg_alpha(const CState* st);
@@ -310,81 +638,6 @@ template <> __device__ inline double2 cg_alpha<double2>(const CState* st) { retu
 template <typename T> __device__ inline T cg_beta(const CState* st);
 template <> __device__ inline float2 cg_beta<float2>(const CState* st) { return st->beta32; }
 template <> __device__ inline double2 cg_beta<double2>(const CState* st) { return st->beta; }
-
-// y += alpha p, r -= alpha q, rho' = r^T r, ||r||^2; the last block forms beta = rho' / rho and
-// the stopping test.
-template <typename T>
-__global__ void __launch_bounds__(512, 2) k_cg_update(const T* __restrict__ p, const T* __restrict__ q,
-                                                   T* __restrict__ r, T* __restrict__ y, int64_t n,
-                                                   CState* __restrict__ st, double2* __restrict__ partials) {
-  pdl_trigger();
-  pdl_wait();
-  if (st->done) return;
-  using A = typename Acc<T>::type;
-  const T al = cg_alpha<T>(st);
-  A rho = zero<T>(), nr = zero<T>();
-  double2 rho64 = make_double2(0.0, 0.0), nr64 = rho64;
-  int cnt = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const T pv = p[i], qv = q[i];
-    T yv = y[i], rv = r[i];
-    fma_c(yv, al, pv);
-    sub_mul(rv, qv, al);
-    y[i] = yv;
-    r[i] = rv;
-    bil_fma(rho, rv, rv);
-    nr.x += nrm2(rv);
-    if (++cnt == 32) {  // FP32 over at most 32 elements, then FP64
-      rho64 = cadd(rho64, to_d2(rho));
-      nr64 = cadd(nr64, to_d2(nr));
-      rho = zero<T>();
-      nr = zero<T>();
-      cnt = 0;
-    }
-  }
-  // per-thread totals in the accumulator's precision (FP64 flushes only past 32 elements)
-  rho.x += (decltype(rho.x))rho64.x;
-  rho.y += (decltype(rho.x))rho64.y;
-  nr.x += (decltype(nr.x))nr64.x;
-  block_partials2<512>(rho, nr, partials);
-  if (!last_block(&st->counter)) return;
-  if (threadIdx.x < 32) {
-    const double2 rh = warp_sum_partials(partials, gridDim.x, 0);
-    const double2 nn = warp_sum_partials(partials, gridDim.x, 1);
-    if (threadIdx.x == 0) {
-      st->k += 1;
-      st->nr = nn.x;
-      if (!isfinite(nn.x)) {
-        st->done = 2;
-      } else if (nn.x <= st->stop2) {
-        st->done = 1;
-      } else if (!(cabs2(st->rho) > 0.0)) {
-        st->done = 2;
-      } else {
-        const double2 be = cdiv(rh, st->rho);
-        st->beta = be;
-        st->beta32 = make_float2((float)be.x, (float)be.y);
-        st->rho = rh;
-      }
-      st->counter = 0;
-    }
-  }
-}
-
-// p = r + beta p.
-template <typename T>
-__global__ void __launch_bounds__(256) k_cg_dir(const T* __restrict__ r, T* __restrict__ p, int64_t n,
-                                                const CState* __restrict__ st) {
-  pdl_trigger();
-  pdl_wait();
-  if (st->done) return;
-  const T be = cg_beta<T>(st);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    T pv = r[i];
-    fma_c(pv, be, p[i]);
-    p[i] = pv;
-  }
-}
 
 // x += unscale S y (FP64).
 template <typename T>
@@ -396,7 +649,7 @@ __global__ void k_cg_finish(const T* __restrict__ y, const double2* __restrict__
 }
 
 struct CgBuffers {
-  DevBuf sq, a128, a64, r64, r, p, q, y, state, partials;
+  DevBuf sq, a128, a64, r64, r, p, q, y, state, partials, sys;
   // multi-source solve: interleaved right-hand sides, iterate and residual (c128), vectors (T),
   // per-source states, group flags and per-source scales / inner targets
   DevBuf Bt, X, R, rb, pb, qb, yb, bstates, bgrp, bscal;
@@ -425,13 +678,19 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
   const T* at = c128 ? (const T*)B->a128.ptr : (const T*)B->a64.ptr;
   T *r = B->r.as<T>(), *p = B->p.as<T>(), *q = B->q.as<T>(), *y = B->y.as<T>();
   const unsigned nb = blocks_for(n, kRows);
-  const unsigned spmv_grid =
-      (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_for(n * kCgG, 256), (int64_t)CgOcc<T>::value * sms));
-  const unsigned vec_grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_for(n, 256), 8LL * sms));
-  // the update reduces two sums over its blocks: a persistent grid keeps the last block's work small
-  const unsigned upd_grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_for(n, 512), 2LL * sms));
+  // the persistent kernel's grid: CgOcc blocks per SM (all resident), fewer for a small system
+  const int grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>(blocks_for(n * kCgG, 256), (int64_t)CgOcc<T>::value * sms));
+  PG_TRY(cg_setup<T>());
   const double vb = (double)sizeof(T) * n;
-  const double spmv_bytes = (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 3.0 * vb;
+  // per iteration: SpMV nnz (values + columns) + row pointers + p gathered once, p of the row and
+  // q written; update q, r read and r written; direction r, p, y read and p, y written
+  const double iter_bytes = (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 3.0 * vb + 3.0 * vb + 5.0 * vb;
+  CgSys<T> hsys{(const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), at, p, q, r, y, n,
+                st, part, 0, grid};
+  PG_TRY(B->sys.reserve(sizeof(CgSys<T>)));
+  PG_CUDA(cudaMemcpyAsync(B->sys.ptr, &hsys, sizeof(hsys), cudaMemcpyHostToDevice, s));
+  const CgSys<T>* dsys = B->sys.as<CgSys<T>>();
   CState hs;
   auto norm = [&](const double2* v, double* out) -> Status {
     k_cg_norm<<<nb, kT, 0, s>>>(v, n, st, part);
@@ -449,7 +708,6 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
     inf.status = PETGEM_OK;
     return Status{};
   }
-  const int chunk = std::max(1, o.restart);
   int64_t iters = 0, solves = 0;
   double relres = 0.0;
   int status = PETGEM_OK, stalls = 0;
@@ -491,39 +749,30 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
                                     1.0 / rnorm);
     c->launches++;
     PG_CUDA(cudaGetLastError());
-    int64_t done_iters = 0;
+    hs.k = 0;
+    // the iterations of this inner solve: persistent launches of up to kCgChunk iterations each
     while (true) {
-      const int64_t steps = std::min<int64_t>(chunk, o.max_iters - iters - done_iters);
+      const int steps = (int)std::min<int64_t>(kCgChunk, o.max_iters - iters - hs.k);
       if (steps <= 0) break;
-      for (int64_t i = 0; i < steps; ++i) {
-        {
-          KernelTimer kt(c, c128 ? "cg_spmv_c128" : "cg_spmv_c64", spmv_bytes);
-          PG_CUDA(pdl_launch(k_cg_spmv<T, kCgG>, dim3(spmv_grid), dim3(256), 0, s, false,
-                             (const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), at,
-                             (const T*)p, q, n, st, part));
-        }
-        {
-          KernelTimer kt(c, c128 ? "cg_update_c128" : "cg_update_c64", 6.0 * vb);
-          PG_CUDA(pdl_launch(k_cg_update<T>, dim3(upd_grid), dim3(512), 0, s, false, (const T*)p, (const T*)q, r, y, n,
-                             st, part));
-        }
-        {
-          KernelTimer kt(c, c128 ? "cg_dir_c128" : "cg_dir_c64", 3.0 * vb);
-          PG_CUDA(pdl_launch(k_cg_dir<T>, dim3(vec_grid), dim3(256), 0, s, false, (const T*)r, p, n,
-                             (const CState*)st));
-        }
-        c->launches += 3;
+      {
+        KernelTimer kt(c, c128 ? "cg_inner_c128" : "cg_inner_c64", 0.0);
+        PG_CUDA(pdl_launch(k_cg_inner<T, kCgG>, dim3(grid), dim3(256), 0, s, true, dsys, 1, steps));
       }
+      c->launches++;
+      const int k0 = hs.k;
       PG_TRY(read_cstate(c, B, &hs));
-      done_iters = hs.k;
+      set_last_timing_bytes(c, (hs.k - k0) * iter_bytes);
       if (hs.done) break;
     }
-    PG_TRY(read_cstate(c, B, &hs));
     k_cg_finish<T><<<blocks_for(n, 256), 256, 0, s>>>(y, B->sq.as<double2>(), x, n, rnorm);
     c->launches++;
     PG_CUDA(cudaGetLastError());
     iters += hs.k;
     solves += 1;
+    if (hs.done == 3) {  // a barrier of the persistent kernel gave up
+      status = PETGEM_ERR_TIMEOUT;
+      break;
+    }
     if (hs.done == 2 && hs.k == 0) {  // the bilinear form broke down at once: no progress possible
       status = PETGEM_ERR_BREAKDOWN;
       break;
@@ -1108,7 +1357,7 @@ Status run_solve_cocg(petgem_ctx* c, const petgem_solve_opts& o, double2* x, pet
 void destroy_cocg(petgem_ctx* c) {
   if (!c->cocg) return;
   CgBuffers* B = static_cast<CgBuffers*>(c->cocg);
-  for (DevBuf* d : {&B->sq, &B->a128, &B->a64, &B->r64, &B->r, &B->p, &B->q, &B->y, &B->state, &B->partials, &B->Bt,
+  for (DevBuf* d : {&B->sq, &B->a128, &B->a64, &B->r64, &B->r, &B->p, &B->q, &B->y, &B->state, &B->partials, &B->sys, &B->Bt,
                     &B->X, &B->R, &B->rb, &B->pb, &B->qb, &B->yb, &B->bstates, &B->bgrp, &B->bscal})
     d->release();
   delete B;

@@ -113,6 +113,9 @@ struct KernelTimer {
 // once: steps >= k, and second-pass launches of steps that did not re-orthogonalise.
 void drop_idle_timings(petgem_ctx* c, size_t from, int k, const uint8_t* refined);
 
+// Set the byte count of the most recent timing (for a launch whose work is known only after it).
+void set_last_timing_bytes(petgem_ctx* c, double bytes);
+
 Status resolve_timings(petgem_ctx* c);
 Status check_flags(petgem_ctx* c, const char* where);
 
