@@ -156,12 +156,13 @@ def run_ours(args):
 
     n_edges = [0]
 
-    def step(precision, method=api.METHOD_GMRES):
+    def step(precision, method=api.METHOD_GMRES, graphs=1):
         E = api.petgem_mesh_edges(ctx.h, nodes, tets)
         n_edges[0] = E
         api.petgem_assemble(ctx.h, m.freq, sigma, m.sigma_p, m.sources)
         x = torch.zeros((S, E), dtype=torch.complex128, device=dev)
-        st, info = api.petgem_solve(ctx.h, x, S, api.solve_opts(precision=precision, tol=1e-8, method=method))
+        st, info = api.petgem_solve(ctx.h, x, S, api.solve_opts(precision=precision, tol=1e-8, method=method,
+                                                                use_graphs=graphs))
         out = torch.empty((S, rx.shape[0], 3, 3), dtype=torch.complex128, device=dev)
         api.petgem_receivers(ctx.h, rx, x, out)
         return info, out
@@ -172,9 +173,9 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def timed(precision, steps, warmup, profile=False, clocks=None, method=api.METHOD_GMRES):
+    def timed(precision, steps, warmup, profile=False, clocks=None, method=api.METHOD_GMRES, graphs=1):
         for _ in range(warmup):
-            step(precision, method)
+            step(precision, method, graphs)
         barrier()
         if profile:
             api.petgem_profile(ctx.h, True)
@@ -185,7 +186,7 @@ def run_ours(args):
         e0.record()
         infos = []
         for _ in range(steps):
-            infos.append(step(precision, method)[0])
+            infos.append(step(precision, method, graphs)[0])
         e1.record()
         barrier()
         cl = clocks.stop() if clocks else None
@@ -224,10 +225,13 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     clocks = ClockSampler(local)
     # The step time is taken without per-kernel events (an event pair around each of the ~6000
-    # launches of a solve costs several percent); the per-kernel times come from one more step of
-    # the same workload with the events on, right after.
+    # launches of a solve costs several percent) and with each GMRES cycle replayed as a CUDA graph;
+    # the per-kernel times come from one more step of the same workload with the events on (direct
+    # launches), right after.
     ms_mixed, info_mixed, launches, cl = timed(api.PREC_MIXED, args.steps, args.warmup, clocks=clocks)
     ms_events, _, _, _ = timed(api.PREC_MIXED, 1, 0, profile=True)
+    # The same solve with every kernel launched directly (no CUDA-graph replay of the cycles).
+    ms_direct, _, _, _ = timed(api.PREC_MIXED, args.steps, 1, graphs=0)
     # Dominant kernel over that step (CUDA events around each launch on the ctx stream).
     kstats = {}
     for name in ("spmv_c64", "mdot_c64", "cgs_upd_c64", "cycle_init_c64",
@@ -385,6 +389,7 @@ def run_ours(args):
             "warmup": args.warmup,
             "ms_per_step": round(ms_mixed, 3),
             "ms_per_step_with_kernel_events": round(ms_events, 3),
+            "ms_per_step_without_graphs": round(ms_direct, 3),
             "higher_is_better": False,
             "scaling": "weak",
             "vs_baseline": None,

@@ -84,7 +84,10 @@ typedef struct {
   double inner_tol;
   int64_t max_iters;   /* cap on Krylov iterations per source */
   int32_t orth;        /* Arnoldi orthogonalisation: PETGEM_ORTH_CGS (default), _CGS2, _CGS_IFNEEDED */
-  int32_t use_graphs;  /* 1 = replay each restart cycle as a CUDA graph */
+  int32_t use_graphs;  /* 1 = replay each GMRES restart cycle as a CUDA graph, captured once per
+                          solve configuration (Jacobi preconditioner; ignored with the learned
+                          one, while kernel profiling is on, and by COCG, whose iterations run in
+                          one persistent kernel); results are identical to direct launches */
   int32_t method;      /* PETGEM_METHOD_GMRES (default) or PETGEM_METHOD_COCG */
   int32_t reserved;
 } petgem_solve_opts;

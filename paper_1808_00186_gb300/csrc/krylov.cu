@@ -349,9 +349,17 @@ Status prepare(petgem_ctx* c, int m, int prec, bool single) {
   return Status{};
 }
 
+// FNV-1a over the values that fix a captured cycle's launches.
+inline uint64_t cycle_key(std::initializer_list<uint64_t> v) {
+  uint64_t h = 1469598103934665603ull;
+  for (uint64_t x : v)
+    for (int b = 0; b < 8; ++b) h = (h ^ ((x >> (8 * b)) & 0xffu)) * 1099511628211ull;
+  return h;
+}
+
 template <typename T>
 Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, double inner_rel, bool learned,
-                 HostState* hs) {
+                 bool graph, HostState* hs) {
   Solver* S = c->solver;
   cudaStream_t s = c->stream;
   const int64_t n = S->n, ld = S->ld;
@@ -373,64 +381,109 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
   // Flexible GMRES with the learned preconditioner: z_j = N-corrected v_j, stored in Z, and the
   // solution update uses Z instead of V.
   T* Z = learned ? S->Z.as<T>() : nullptr;
-  for (int j = 0; j < m; ++j) {
-    T* vj = V + (int64_t)j * ld;
-    T* vn = vj + ld;
-    const T* xin = vj;
-    if (learned) {  // odd steps: the network's direction; even steps: Jacobi (z = v)
-      T* zj = Z + (int64_t)j * ld;
-      if (j & 1) {
-        KernelTimer kt(c, "learned_apply", 0.0, j, 0);
-        PG_TRY(c->net->apply<T>(s, vj, c->slots.as<int32_t>(), n, zj));
-        c->launches += 20;
-      } else {
-        PG_CUDA(cudaMemcpyAsync(zj, vj, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  // the launches of one cycle after its initialisation: the m Arnoldi steps (each returns at once
+  // after the cycle stopped), the back substitution and the solution update
+  auto cycle_body = [&]() -> Status {
+    for (int j = 0; j < m; ++j) {
+      T* vj = V + (int64_t)j * ld;
+      T* vn = vj + ld;
+      const T* xin = vj;
+      if (learned) {  // odd steps: the network's direction; even steps: Jacobi (z = v)
+        T* zj = Z + (int64_t)j * ld;
+        if (j & 1) {
+          KernelTimer kt(c, "learned_apply", 0.0, j, 0);
+          PG_TRY(c->net->apply<T>(s, vj, c->slots.as<int32_t>(), n, zj));
+          c->launches += 20;
+        } else {
+          PG_CUDA(cudaMemcpyAsync(zj, vj, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        }
+        xin = zj;
       }
-      xin = zj;
+      {
+        KernelTimer kt(c, c128 ? "spmv_c128" : "spmv_c64", spmv_bytes, j, 0);
+        PG_CUDA(pdl_launch(k_spmv_arnoldi<T, kGroup>, dim3(spmv_blocks), dim3(256), 0, s, false,
+                           (const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), ahat, xin, vn,
+                           n, (const GState*)st, j));
+      }
+      const double dot_b = (double)(j + 2) * vbytes, upd_b = (double)(j + 3) * vbytes;
+      auto sdot = [&](int pass, int need_refine, const char* name, double bytes, int tag) -> Status {
+        KernelTimer kt(c, name, bytes, j, tag);
+        c->launches++;
+        return launch_pdot<T, 1>(s, S->sms, V, ld, n, j, st, &st->done, &st->gbar, part, pass, need_refine);
+      };
+      auto supd = [&](int pass, int need_refine, double eta2, int finish, const char* name, double bytes,
+                      int tag) -> Status {
+        KernelTimer kt(c, name, bytes, j, tag);
+        c->launches++;
+        return launch_pupd<T, 1>(s, S->sms, V, ld, n, j, st, &st->done, &st->counter, part, pass, need_refine, eta2,
+                                 finish);
+      };
+      if (orth == 0) {  // CGS2: dots, update, dots of the updated w, update + norm
+        PG_TRY(sdot(0, 0, c128 ? "mdot_c128" : "mdot_c64", dot_b, 0));
+        PG_TRY(supd(0, 0, 0.0, 0, c128 ? "cgs_upd1_c128" : "cgs_upd1_c64", upd_b, 0));
+        PG_TRY(sdot(1, 0, c128 ? "cgs_dot2_c128" : "cgs_dot2_c64", dot_b, 0));
+        PG_TRY(supd(1, 0, 0.0, 1, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0));
+      } else if (orth == 1) {  // CGS: dots, update + norm
+        PG_TRY(sdot(0, 0, c128 ? "mdot_c128" : "mdot_c64", dot_b, 0));
+        PG_TRY(supd(0, 0, 0.0, 1, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0));
+      } else {  // CGS, second pass when the norm fell below 1/sqrt(2) of its value
+        PG_TRY(sdot(0, 0, c128 ? "mdot_c128" : "mdot_c64", dot_b, 0));
+        PG_TRY(supd(0, 0, 0.5, 1, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0));
+        PG_TRY(sdot(1, 1, c128 ? "cgs_dot2_c128" : "cgs_dot2_c64", dot_b, 1));
+        PG_TRY(supd(1, 1, 0.0, 1, c128 ? "cgs_upd2_c128" : "cgs_upd2_c64", upd_b, 1));
+      }
+      c->launches += 1;
     }
+    PG_CUDA(cudaGetLastError());
+    k_backsolve<<<1, 32, 0, s>>>(st);
     {
-      KernelTimer kt(c, c128 ? "spmv_c128" : "spmv_c64", spmv_bytes, j, 0);
-      PG_CUDA(pdl_launch(k_spmv_arnoldi<T, kGroup>, dim3(spmv_blocks), dim3(256), 0, s, false,
-                         (const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), ahat, xin, vn,
-                         n, (const GState*)st, j));
+      KernelTimer kt(c, c128 ? "xupdate_c128" : "xupdate_c64", 32.0 * n + (double)m * vbytes);
+      k_xupdate<T><<<blocks_for(n, kT), kT, 0, s>>>(learned ? Z : V, ld, n, S->u.as<double2>(), st);
     }
-    const double dot_b = (double)(j + 2) * vbytes, upd_b = (double)(j + 3) * vbytes;
-    auto sdot = [&](int pass, int need_refine, const char* name, double bytes, int tag) -> Status {
-      KernelTimer kt(c, name, bytes, j, tag);
-      c->launches++;
-      return launch_pdot<T, 1>(s, S->sms, V, ld, n, j, st, &st->done, &st->gbar, part, pass, need_refine);
-    };
-    auto supd = [&](int pass, int need_refine, double eta2, int finish, const char* name, double bytes,
-                    int tag) -> Status {
-      KernelTimer kt(c, name, bytes, j, tag);
-      c->launches++;
-      return launch_pupd<T, 1>(s, S->sms, V, ld, n, j, st, &st->done, &st->counter, part, pass, need_refine, eta2,
-                               finish);
-    };
-    if (orth == 0) {  // CGS2: dots, update, dots of the updated w, update + norm
-      PG_TRY(sdot(0, 0, c128 ? "mdot_c128" : "mdot_c64", dot_b, 0));
-      PG_TRY(supd(0, 0, 0.0, 0, c128 ? "cgs_upd1_c128" : "cgs_upd1_c64", upd_b, 0));
-      PG_TRY(sdot(1, 0, c128 ? "cgs_dot2_c128" : "cgs_dot2_c64", dot_b, 0));
-      PG_TRY(supd(1, 0, 0.0, 1, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0));
-    } else if (orth == 1) {  // CGS: dots, update + norm
-      PG_TRY(sdot(0, 0, c128 ? "mdot_c128" : "mdot_c64", dot_b, 0));
-      PG_TRY(supd(0, 0, 0.0, 1, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0));
-    } else {  // CGS, second pass when the norm fell below 1/sqrt(2) of its value
-      PG_TRY(sdot(0, 0, c128 ? "mdot_c128" : "mdot_c64", dot_b, 0));
-      PG_TRY(supd(0, 0, 0.5, 1, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0));
-      PG_TRY(sdot(1, 1, c128 ? "cgs_dot2_c128" : "cgs_dot2_c64", dot_b, 1));
-      PG_TRY(supd(1, 1, 0.0, 1, c128 ? "cgs_upd2_c128" : "cgs_upd2_c64", upd_b, 1));
+    c->launches += 2;
+    PG_CUDA(cudaGetLastError());
+    return Status{};
+  };
+  if (!graph || learned || c->profiling) {
+    PG_TRY(cycle_body());
+  } else {
+    // CUDA graph: captured once for these buffers, sizes and options, replayed every cycle (the
+    // kernels read the cycle's scalars from the device state, so one capture serves every cycle)
+    const uint64_t key = cycle_key({(uint64_t)(uintptr_t)ahat, (uint64_t)(uintptr_t)V, (uint64_t)(uintptr_t)st,
+                                    (uint64_t)(uintptr_t)part, (uint64_t)(uintptr_t)c->row_ptr.ptr,
+                                    (uint64_t)(uintptr_t)c->col.ptr, (uint64_t)(uintptr_t)S->u.ptr, (uint64_t)n,
+                                    (uint64_t)ld, (uint64_t)m, (uint64_t)orth, (uint64_t)sizeof(T),
+                                    (uint64_t)spmv_blocks, (uint64_t)S->sms});
+    if (!S->graph || S->graph_key != key) {
+      if (S->graph) cudaGraphExecDestroy(S->graph);
+      S->graph = nullptr;
+      // captured on a private stream (the context's may be the legacy default stream, which
+      // cannot be captured); the graph is then launched on the context's stream
+      if (!S->cap_stream) PG_CUDA(cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking));
+      const int64_t l0 = c->launches;
+      s = S->cap_stream;
+      PG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      const Status r = cycle_body();
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(s, &g);
+      s = c->stream;
+      if (!r.ok()) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      if (e != cudaSuccess) return Status{PETGEM_ERR_CUDA, std::string("cycle capture: ") + cudaGetErrorString(e)};
+      cudaGraphExec_t ex = nullptr;
+      const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (ei != cudaSuccess) return Status{PETGEM_ERR_CUDA, std::string("cycle graph: ") + cudaGetErrorString(ei)};
+      S->graph = ex;
+      S->graph_key = key;
+      S->graph_launches = c->launches - l0;
+      c->launches = l0;
     }
-    c->launches += 1;
+    PG_CUDA(cudaGraphLaunch(S->graph, s));
+    c->launches += S->graph_launches;
   }
-  PG_CUDA(cudaGetLastError());
-  k_backsolve<<<1, 32, 0, s>>>(st);
-  {
-    KernelTimer kt(c, c128 ? "xupdate_c128" : "xupdate_c64", 32.0 * n + (double)m * vbytes);
-    k_xupdate<T><<<blocks_for(n, kT), kT, 0, s>>>(learned ? Z : V, ld, n, S->u.as<double2>(), st);
-  }
-  c->launches += 2;
-  PG_CUDA(cudaGetLastError());
   PG_TRY(read_state(c, hs));
   if (c->profiling) drop_idle_timings(c, pending0, hs->done == 2 ? 0 : hs->k, hs->refined);
   return Status{};
@@ -441,14 +494,11 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
 void destroy_solver(petgem_ctx* c) {
   if (!c->solver) return;
   Solver* S = c->solver;
-  S->ahat128.release();
-  S->ahat64.release();
-  S->dinv.release();
-  S->V.release();
-  S->u.release();
-  S->r.release();
-  S->partials.release();
-  S->state.release();
+  for (DevBuf* d : {&S->ahat128, &S->ahat64, &S->dinv, &S->V, &S->u, &S->r, &S->partials, &S->state, &S->Z, &S->usave,
+                    &S->Vb, &S->Ub, &S->Rb, &S->Bb, &S->bstates, &S->bgroup, &S->btol})
+    d->release();
+  if (S->graph) cudaGraphExecDestroy(S->graph);
+  if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
   delete S;
   c->solver = nullptr;
 }
@@ -541,9 +591,9 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
       const int orth = learned ? PETGEM_ORTH_CGS2 : o.orth;
       // A cycle whose starting residual already meets tol runs no iteration (k = 0).
       if (o.precision == PETGEM_PREC_MIXED)
-        PG_TRY(run_cycle<float2>(c, S->ahat64.as<float2>(), mj, orth, tol_abs, o.inner_tol, learned, &hs));
+        PG_TRY(run_cycle<float2>(c, S->ahat64.as<float2>(), mj, orth, tol_abs, o.inner_tol, learned, o.use_graphs != 0, &hs));
       else
-        PG_TRY(run_cycle<double2>(c, S->ahat128.as<double2>(), mj, orth, tol_abs, 0.0, learned, &hs));
+        PG_TRY(run_cycle<double2>(c, S->ahat128.as<double2>(), mj, orth, tol_abs, 0.0, learned, o.use_graphs != 0, &hs));
       relres = sqrt(hs.rnorm2) / bnorm;  // FP64 residual of u before this cycle's update
       if (!isfinite(relres)) {
         status = PETGEM_ERR_BREAKDOWN;

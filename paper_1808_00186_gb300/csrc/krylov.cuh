@@ -50,6 +50,12 @@ struct Solver {
   int64_t n_blocks = 0;
   int64_t ld_used = 0;
   int sms = 0;
+  // one Arnoldi cycle captured as a CUDA graph (use_graphs): the launches after the cycle's
+  // initialisation, for the buffers, sizes and options the key hashes
+  cudaGraphExec_t graph = nullptr;
+  uint64_t graph_key = 0;
+  int64_t graph_launches = 0;
+  cudaStream_t cap_stream = nullptr;  // private stream the capture runs on
 };
 
 namespace {
