@@ -44,6 +44,7 @@ def parse():
     p.add_argument("--solver", default="gmres", choices=["gmres", "cocg"], help="Krylov method of --profile-step / --profile-block")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-network measurement")
     p.add_argument("--no-cocg", action="store_true", help="skip the COCG measurement")
+    p.add_argument("--no-batch", action="store_true", help="skip the batch of uneven meshes")
     p.add_argument("--profile-block", type=int, default=0, metavar="ITERS",
                    help="run only the 32-source block solve, capped at ITERS iterations (for ncu)")
     return p.parse_args()
@@ -230,8 +231,6 @@ def run_ours(args):
     # launches), right after.
     ms_mixed, info_mixed, launches, cl = timed(api.PREC_MIXED, args.steps, args.warmup, clocks=clocks)
     ms_events, _, _, _ = timed(api.PREC_MIXED, 1, 0, profile=True)
-    # The same solve with every kernel launched directly (no CUDA-graph replay of the cycles).
-    ms_direct, _, _, _ = timed(api.PREC_MIXED, args.steps, 1, graphs=0)
     # Dominant kernel over that step (CUDA events around each launch on the ctx stream).
     kstats = {}
     for name in ("spmv_c64", "mdot_c64", "cgs_upd_c64", "cycle_init_c64",
@@ -240,6 +239,8 @@ def run_ours(args):
         if n:
             kstats[name] = {"launches": n, "ms": kms, "bytes": by, "gbs": by / (kms * 1e-3) / 1e9}
     api.petgem_profile(ctx.h, False)
+    # The same solve with every kernel launched directly (no CUDA-graph replay of the cycles).
+    ms_direct, _, _, _ = timed(api.PREC_MIXED, args.steps, 1, graphs=0)
     plain = None
     if not args.no_plain:
         ms_plain, info_plain, _, _ = timed(api.PREC_C128, 1, 1)
@@ -306,6 +307,55 @@ def run_ours(args):
 
     # Learned preconditioner (tcgen05 convolutions): the network on this mesh's parent grid
     # ((n+1)^3 nodes), apply time and the convolutions' throughput against the BF16 tensor peak.
+    # Batch of uneven meshes: eight marine models from 16^3 to 48^3 cells (one source each) solved
+    # together by petgem_solve_batch (COCG, mixed precision, one persistent launch per refinement
+    # round, the rounds replayed as CUDA graphs, SpMV lanes per row autotuned), against the same
+    # eight solved one after the other with petgem_solve (COCG, mixed).
+    uneven = None
+    if not args.no_batch:
+        sizes = (16, 20, 24, 28, 32, 36, 40, 48)
+        bctx = []
+        for nn in sizes:
+            mm = synth.marine_model(nn, n_src=1)
+            cc = api.Context(local)
+            cc.mesh(mm.mesh.nodes, mm.mesh.tets)
+            cc.assemble(mm.freq, mm.sigma, mm.sigma_p, mm.sources)
+            bctx.append(cc)
+        xs = [torch.zeros((1, cc.n_edges), dtype=torch.complex128, device=dev) for cc in bctx]
+
+        def batch_once():
+            for xx in xs:
+                xx.zero_()
+            return api.solve_batch(bctx, xs, precision=api.PREC_MIXED, tol=1e-8, use_graphs=1)[1]
+
+        def seq_once():
+            infos = []
+            for cc, xx in zip(bctx, xs):
+                xx.zero_()
+                infos.append(cc.solve(xx, precision=api.PREC_MIXED, tol=1e-8, method=api.METHOD_COCG)[1][0])
+            return infos
+
+        def best_of(fn, reps=3):
+            fn()
+            best, out = float("inf"), None
+            for _ in range(reps):
+                barrier()
+                t0 = time.perf_counter()
+                out = fn()
+                barrier()
+                best = min(best, time.perf_counter() - t0)
+            return best, out
+
+        t_b, ib = best_of(batch_once)
+        t_s, isq = best_of(seq_once)
+        uneven = {"meshes": ["%d^3" % nn for nn in sizes], "edges": [cc.n_edges for cc in bctx],
+                  "batch_ms": round(t_b * 1e3, 3), "sequential_ms": round(t_s * 1e3, 3),
+                  "speedup": round(t_s / t_b, 3), "spmv_lanes": ib[0]["spmv_lanes"],
+                  "iters_batch": [i["iters"] for i in ib], "iters_sequential": [i["iters"] for i in isq],
+                  "worst_true_rel_residual": max(i["true_rel_residual"] for i in ib)}
+        for cc in bctx:
+            cc.close()
+
     learned = None
     if not args.no_learned:
         from paper_1808_00186_gb300 import learned as PL
@@ -404,6 +454,7 @@ def run_ours(args):
             "plain_c128": plain,
             "cocg": cocg,
             "block_multi_source": block,
+            "uneven_batch": uneven,
             "learned_network": learned,
             "speedup_vs_plain": round(plain["ms_per_step"] / ms_mixed, 3) if plain else None,
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "gbs": round(v["gbs"], 1)}

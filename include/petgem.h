@@ -89,7 +89,8 @@ typedef struct {
                           one, while kernel profiling is on, and by COCG, whose iterations run in
                           one persistent kernel); results are identical to direct launches */
   int32_t method;      /* PETGEM_METHOD_GMRES (default) or PETGEM_METHOD_COCG */
-  int32_t reserved;
+  int32_t spmv_lanes;  /* petgem_solve_batch: lanes per matrix row of the SpMV (2, 4 or 8);
+                          0 = chosen by the autotuner; ignored by petgem_solve */
 } petgem_solve_opts;
 
 /* Krylov method.
@@ -122,7 +123,7 @@ typedef struct {
   int32_t status;      /* PETGEM_OK, PETGEM_ERR_NOT_CONVERGED, _BREAKDOWN or _TIMEOUT */
   int32_t reorth;      /* Arnoldi steps that needed a second Gram-Schmidt pass */
   int32_t fell_back;   /* learned preconditioner: 1 if the solve switched back to Jacobi */
-  int32_t reserved;
+  int32_t spmv_lanes;  /* petgem_solve_batch: lanes per row the SpMV ran with; 0 otherwise */
 } petgem_solve_info;
 
 /* ----------------------------------------------------------------------- lifecycle */
@@ -186,6 +187,30 @@ int petgem_get_elements(petgem_ctx *ctx, double *K21, double *M21, double *vol);
  * restart 50, c128, Jacobi, tol 1e-8, max_iters 200000, inner_tol 1e-4, orth CGS).
  * Returns PETGEM_ERR_NOT_CONVERGED or PETGEM_ERR_BREAKDOWN if any source ended that way. */
 int petgem_solve(petgem_ctx *ctx, const petgem_solve_opts *opts, void *x, petgem_solve_info *info);
+
+/* Solve the systems of several contexts together: one mesh per context (sizes may differ), every
+ * (context, source) pair one system A_k x = b_ks, with COCG (opts->method must be
+ * PETGEM_METHOD_COCG, precond Jacobi; precision MIXED or C128 as for petgem_solve).
+ * The inner iterations of all systems run in one persistent cooperative launch per refinement
+ * round (the blocks of the GPU divided among the systems by a scheduler in proportion to each
+ * system's matrix entries times its expected iterations, re-divided every round from the
+ * iterations each system took); the FP64 refinement steps of all systems (solution update, true
+ * residual, its norm, the stopping decision, the next start) run as one launch sequence per
+ * round, replayed as a CUDA graph when opts->use_graphs = 1.  opts->spmv_lanes = 0 lets an
+ * autotuner pick the SpMV's lanes per row (2, 4 or 8) by timing the first iterations with each.
+ * The contexts must share a device and each must have called petgem_assemble.  The work runs on
+ * ctxs[0]'s stream, after the work already queued on every context's stream and before any work
+ * queued on them afterwards.
+ *   ctxs: host array of n_ctx contexts (n_ctx = 0: nothing to do).
+ *   x: host array of n_ctx device pointers, x[k] complex128[n_src_k][E_k] (x0 in, solution out).
+ *   info: host array of sum_k n_src_k entries, context by context, source by source.
+ *   The workspace belongs to ctxs[0] (freed by its petgem_destroy).
+ * Errors: PETGEM_ERR_INVALID_ARG (null arguments, a context not assembled, contexts on different
+ * devices), PETGEM_ERR_UNSUPPORTED (method GMRES, the learned preconditioner, more than 64
+ * systems, spmv_lanes not in {0, 2, 4, 8}), PETGEM_ERR_NOT_CONVERGED / _BREAKDOWN / _TIMEOUT when a
+ * system ended so (info is still filled); the error text is ctxs[0]'s. */
+int petgem_solve_batch(petgem_ctx *const *ctxs, int32_t n_ctx, const petgem_solve_opts *opts, void *const *x,
+                       petgem_solve_info *info);
 
 /* y = A x for the assembled matrix (complex128, device, n_src = 1 vector of E entries). */
 int petgem_spmv(petgem_ctx *ctx, const void *x, void *y);

@@ -36,13 +36,13 @@ class petgem_solve_opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("precision", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("max_iters", ctypes.c_int64), ("orth", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
-                ("method", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("method", ctypes.c_int32), ("spmv_lanes", ctypes.c_int32)]
 
 
 class petgem_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("restarts", ctypes.c_int64), ("refinements", ctypes.c_int64),
                 ("true_rel_residual", ctypes.c_double), ("status", ctypes.c_int32), ("reorth", ctypes.c_int32),
-                ("fell_back", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("fell_back", ctypes.c_int32), ("spmv_lanes", ctypes.c_int32)]
 
 
 _P, _I64, _I32, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
@@ -57,6 +57,8 @@ _SIGNATURES = {
     "petgem_get_system": (ctypes.c_int, [_P, ctypes.POINTER(_I64), _P, _P, _P, _P, _P]),
     "petgem_get_elements": (ctypes.c_int, [_P, _P, _P, _P]),
     "petgem_solve": (ctypes.c_int, [_P, ctypes.POINTER(petgem_solve_opts), _P, ctypes.POINTER(petgem_solve_info)]),
+    "petgem_solve_batch": (ctypes.c_int, [ctypes.POINTER(_P), _I32, ctypes.POINTER(petgem_solve_opts),
+                                          ctypes.POINTER(_P), ctypes.POINTER(petgem_solve_info)]),
     "petgem_spmv": (ctypes.c_int, [_P, _P, _P]),
     "petgem_receivers": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     "petgem_profile": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -165,8 +167,10 @@ def petgem_get_elements(ctx, K21=None, M21=None, vol=None):
 
 
 def solve_opts(restart=50, precision=PREC_C128, tol=1e-8, inner_tol=1e-4, max_iters=200000, batch=1,
-               orth=ORTH_CGS, use_graphs=0, precond=PRECOND_JACOBI, method=METHOD_GMRES) -> petgem_solve_opts:
-    return petgem_solve_opts(restart, precision, precond, batch, tol, inner_tol, max_iters, orth, use_graphs, method, 0)
+               orth=ORTH_CGS, use_graphs=0, precond=PRECOND_JACOBI, method=METHOD_GMRES,
+               spmv_lanes=0) -> petgem_solve_opts:
+    return petgem_solve_opts(restart, precision, precond, batch, tol, inner_tol, max_iters, orth, use_graphs, method,
+                             spmv_lanes)
 
 
 def petgem_solve(ctx, x, n_src, opts=None, allow_not_converged=False):
@@ -174,9 +178,27 @@ def petgem_solve(ctx, x, n_src, opts=None, allow_not_converged=False):
     o = opts if opts is not None else solve_opts()
     allowed = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
     st = _check(ctx, load().petgem_solve(ctx, ctypes.byref(o), _ptr(x), info), allowed)
-    return st, [dict(iters=i.iters, restarts=i.restarts, refinements=i.refinements,
-                     true_rel_residual=i.true_rel_residual, status=i.status, reorth=i.reorth,
-                     fell_back=i.fell_back) for i in info]
+    return st, _info_dicts(info)
+
+
+def _info_dicts(info):
+    return [dict(iters=i.iters, restarts=i.restarts, refinements=i.refinements,
+                 true_rel_residual=i.true_rel_residual, status=i.status, reorth=i.reorth,
+                 fell_back=i.fell_back, spmv_lanes=i.spmv_lanes) for i in info]
+
+
+def petgem_solve_batch(ctxs, xs, n_srcs, opts=None, allow_not_converged=False):
+    """Solve the systems of several contexts together (COCG); xs[k] is context k's solution tensor."""
+    n = len(ctxs)
+    arr = (_P * max(n, 1))(*[c for c in ctxs])
+    xarr = (_P * max(n, 1))(*[_ptr(x) for x in xs])
+    info = (petgem_solve_info * max(sum(n_srcs), 1))()
+    o = opts if opts is not None else solve_opts(method=METHOD_COCG)
+    allowed = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
+    st = load().petgem_solve_batch(arr, n, ctypes.byref(o), xarr, info)
+    if st not in allowed:
+        raise PetgemError(st, load().petgem_last_error(ctxs[0]).decode() if n else "")
+    return st, _info_dicts(info)[:sum(n_srcs)]
 
 
 def petgem_spmv(ctx, x, y):
@@ -276,6 +298,18 @@ class Forward:
     rcv: object        # complex128 [n_src, n_rcv, 3, 3]
     info: list
     status: int
+
+
+def solve_batch(contexts, xs=None, **opts):
+    """petgem_solve_batch over Context objects (COCG); returns (xs, info, status)."""
+    import torch
+    if xs is None:
+        xs = [torch.zeros((c.n_src, c.n_edges), dtype=torch.complex128, device=c.nodes.device) for c in contexts]
+    allow = opts.pop("allow_not_converged", False)
+    opts.setdefault("method", METHOD_COCG)
+    st, info = petgem_solve_batch([c.h for c in contexts], xs, [c.n_src for c in contexts], solve_opts(**opts),
+                                  allow_not_converged=allow)
+    return xs, info, st
 
 
 class Context:

@@ -302,6 +302,38 @@ int petgem_solve(petgem_ctx* c, const petgem_solve_opts* opts, void* x, petgem_s
   return finish(c, s);
 }
 
+int petgem_solve_batch(petgem_ctx* const* ctxs, int32_t n_ctx, const petgem_solve_opts* opts, void* const* x,
+                       petgem_solve_info* info) {
+  if (n_ctx == 0) return PETGEM_OK;
+  if (!ctxs || n_ctx < 0 || !ctxs[0]) return PETGEM_ERR_INVALID_ARG;
+  petgem_ctx* c0 = ctxs[0];
+  if (!opts || !x || !info) return finish(c0, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve_batch: need opts, x and info"});
+  for (int k = 0; k < n_ctx; ++k) {
+    if (!ctxs[k] || !x[k]) return finish(c0, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve_batch: null context or x"});
+    if (!ctxs[k]->assembled)
+      return finish(c0, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve_batch: a context is not assembled"});
+    if (ctxs[k]->device != c0->device)
+      return finish(c0, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve_batch: contexts on different devices"});
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return finish(c0, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve_batch: a context twice"});
+  }
+  const petgem_solve_opts& o = *opts;
+  if (o.method != PETGEM_METHOD_COCG)
+    return finish(c0, Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve_batch: the batch solver is COCG"});
+  if (o.precond != PETGEM_PRECOND_JACOBI)
+    return finish(c0, Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve_batch: Jacobi preconditioner only"});
+  if (o.spmv_lanes != 0 && o.spmv_lanes != 2 && o.spmv_lanes != 4 && o.spmv_lanes != 8)
+    return finish(c0, Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve_batch: spmv_lanes must be 0, 2, 4 or 8"});
+  if (!(o.tol > 0.0) || o.max_iters < 0 || (o.precision != PETGEM_PREC_C128 && o.precision != PETGEM_PREC_MIXED) ||
+      !(o.inner_tol >= 0.0 && o.inner_tol < 1.0))
+    return finish(c0, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve_batch: bad options"});
+  Status s = set_device(c0);
+  if (s.ok())
+    s = petgem::run_solve_batch(ctxs, n_ctx, o, reinterpret_cast<double2* const*>(x), info);
+  if (s.code == PETGEM_ERR_CUDA || s.code == PETGEM_ERR_OUT_OF_MEMORY) cudaGetLastError();
+  return finish(c0, s);
+}
+
 int petgem_spmv(petgem_ctx* c, const void* x, void* y) {
   if (!c) return PETGEM_ERR_INVALID_ARG;
   if (!c->assembled || !x || !y) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_spmv: not assembled or null"});

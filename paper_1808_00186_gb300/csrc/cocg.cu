@@ -232,6 +232,7 @@ struct CgSys {
   int64_t n;
   CState* st;
   double2* part;  // [nb][kCgSlots]: slot 0 r^T r, 1 ||r||^2, 2 p^T q
+  int64_t kmax;   // the inner solve stops when its iteration count reaches kmax
   int b0, nb;
 };
 constexpr int kCgSlots = 4;
@@ -511,6 +512,7 @@ __global__ void __launch_bounds__(256, CgOcc<T>::value)
   CState* st = S->st;
   // read before the first barrier: the barriers' last blocks rewrite the state after it
   if (st->done) return;
+  const int64_t steps = std::min<int64_t>(max_steps, S->kmax - st->k);
   const int64_t n = S->n;
   const int64_t* rp = S->rp;
   const int32_t* col = S->col;
@@ -522,7 +524,7 @@ __global__ void __launch_bounds__(256, CgOcc<T>::value)
   const int64_t row0 = (int64_t)lb * (256 / G) + tid / G;
   const int64_t stride = (int64_t)nb * 256, first = (int64_t)lb * 256 + tid;
   bool fail = false;
-  for (int step = 0; step < max_steps; ++step) {
+  for (int64_t step = 0; step < steps; ++step) {
     const A dot = cg_spmv_rows<T, G>(rp, col, val, p, q, n, row0, groups);
     cg_block_sums<256>(dot, zero<T>(), part + (int64_t)lb * kCgSlots + 2);
     if (!cg_reduce_barrier<256, 0>(st, part, nb, &s_ok, &s_last, &s_sc, &s_dn)) {
@@ -621,12 +623,12 @@ __global__ void __launch_bounds__(256, CgOcc<T>::value)
 constexpr int kCgChunk = 1024;  // iterations per persistent launch (the host checks the state between)
 
 // Whether the persistent kernel's grid (CgOcc blocks per SM) can be resident at once.
-template <typename T>
+template <typename T, int G>
 Status cg_setup() {
   static bool done = false;
   if (done) return Status{};
   int nb = 0;
-  PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_inner<T, kCgG>, 256, 0));
+  PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_inner<T, G>, 256, 0));
   if (nb < CgOcc<T>::value) return Status{PETGEM_ERR_UNSUPPORTED, "COCG kernel: too few resident blocks per SM"};
   done = true;
   return Status{};
@@ -648,8 +650,11 @@ __global__ void k_cg_finish(const T* __restrict__ y, const double2* __restrict__
   x[i] = cadd(x[i], cscale(cmul(sq[i], to_d2(y[i])), unscale));
 }
 
+struct BatchBuffers;
+
 struct CgBuffers {
   DevBuf sq, a128, a64, r64, r, p, q, y, state, partials, sys;
+  BatchBuffers* batch = nullptr;  // workspace of petgem_solve_batch (when this context leads one)
   // multi-source solve: interleaved right-hand sides, iterate and residual (c128), vectors (T),
   // per-source states, group flags and per-source scales / inner targets
   DevBuf Bt, X, R, rb, pb, qb, yb, bstates, bgrp, bscal;
@@ -681,15 +686,14 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
   // the persistent kernel's grid: CgOcc blocks per SM (all resident), fewer for a small system
   const int grid = (int)std::max<int64_t>(
       1, std::min<int64_t>(blocks_for(n * kCgG, 256), (int64_t)CgOcc<T>::value * sms));
-  PG_TRY(cg_setup<T>());
+  PG_TRY((cg_setup<T, kCgG>()));
   const double vb = (double)sizeof(T) * n;
   // per iteration: SpMV nnz (values + columns) + row pointers + p gathered once, p of the row and
   // q written; update q, r read and r written; direction r, p, y read and p, y written
   const double iter_bytes = (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 3.0 * vb + 3.0 * vb + 5.0 * vb;
   CgSys<T> hsys{(const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), at, p, q, r, y, n,
-                st, part, 0, grid};
+                st, part, 0, 0, grid};
   PG_TRY(B->sys.reserve(sizeof(CgSys<T>)));
-  PG_CUDA(cudaMemcpyAsync(B->sys.ptr, &hsys, sizeof(hsys), cudaMemcpyHostToDevice, s));
   const CgSys<T>* dsys = B->sys.as<CgSys<T>>();
   CState hs;
   auto norm = [&](const double2* v, double* out) -> Status {
@@ -750,6 +754,8 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
     c->launches++;
     PG_CUDA(cudaGetLastError());
     hs.k = 0;
+    hsys.kmax = o.max_iters - iters;  // this inner solve's iteration budget
+    PG_CUDA(cudaMemcpyAsync(B->sys.ptr, &hsys, sizeof(hsys), cudaMemcpyHostToDevice, s));
     // the iterations of this inner solve: persistent launches of up to kCgChunk iterations each
     while (true) {
       const int steps = (int)std::min<int64_t>(kCgChunk, o.max_iters - iters - hs.k);
@@ -1295,6 +1301,536 @@ Status cocg_group_p(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, con
   return cocg_group<T, 32>(c, o, B, b, x, S_g, info, sms);
 }
 
+// The scaled operator Atil = S A S (complex128 and complex64) and S = D^{-1/2} of the context's
+// current assembly, built once per assembly on the context's stream.
+Status cg_prepare(petgem_ctx* c) {
+  CgBuffers* B = cg_bufs(c);
+  if (B->version == c->assembly_version) return Status{};
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n_edges;
+  PG_TRY(B->sq.reserve(n * sizeof(double2)));
+  PG_TRY(B->a128.reserve(c->nnz * sizeof(double2)));
+  PG_TRY(B->a64.reserve(c->nnz * sizeof(float2)));
+  k_cg_sqrt_diag<<<blocks_for(n, 256), 256, 0, s>>>(c->diag.as<double2>(), n, B->sq.as<double2>());
+  k_cg_scale<<<blocks_for(n, 256), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(),
+                                                B->sq.as<double2>(), n, B->a128.as<double2>(), B->a64.as<float2>());
+  c->launches += 2;
+  PG_CUDA(cudaGetLastError());
+  B->version = c->assembly_version;
+  return Status{};
+}
+
+// ------------------------------------------------------------------ batch of meshes
+// The systems of several contexts (meshes of different sizes, each with its sources) solved
+// together.  Their inner iterations share one persistent launch (k_cg_inner over a table of
+// systems, each on its own blocks); their FP64 refinement steps run as five launches per round
+// for all systems at once (finish, residual, norm, decide, start: each kernel's blocks are divided
+// among the systems), which a CUDA graph replays when asked.
+
+// Refinement-side view of one system.
+struct CgCtl {
+  double bnorm, relres, prev, scale, inner;  // scale = 1 / ||r|| of the current inner solve
+  int64_t iters, solves;
+  int stalls, status, active, ran;
+};
+template <typename T>
+struct CgRef {
+  const int64_t* rp;
+  const int32_t* col;
+  const double2* val;  // the assembled FP64 matrix (true residual)
+  const double2* sq;   // S = D^{-1/2}
+  const double2* b;
+  double2* x;
+  double2* r64;
+  T *r, *p, *y;
+  CState* st;
+  double2* part;
+  CgCtl* ctl;
+  int64_t n;
+  int v0, vnb;  // blocks of the vector kernels (256 elements each)
+  int r0, rnb;  // blocks of the residual kernel (256 / kCgG rows each)
+};
+constexpr int kBatchMax = 64;        // systems per batch
+constexpr int kBatchTuneSteps = 4;   // iterations per timed launch of the autotuner
+
+// The system whose block range [v0, v0 + vnb) (resid: [r0, r0 + rnb)) holds this block.
+template <typename T, bool RESID>
+__device__ inline int batch_sys(const CgRef<T>* R, int ns) {
+  __shared__ int s_k;
+  if (threadIdx.x == 0) {
+    int k = 0;
+    while (k + 1 < ns && (int)blockIdx.x >= (RESID ? R[k + 1].r0 : R[k + 1].v0)) ++k;
+    s_k = k;
+  }
+  __syncthreads();
+  return s_k;
+}
+
+// "Last block of this system" handshake over nb blocks with the system's own counter.
+__device__ inline bool last_of(unsigned* counter, unsigned nb) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == nb - 1;
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// x += ||r|| S y for the systems whose inner solve ran in the last round.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgb_finish(const CgRef<T>* __restrict__ R, int ns) {
+  const int k = batch_sys<T, false>(R, ns);
+  const CgRef<T>& S = R[k];
+  if (!S.ctl->ran) return;
+  const double unscale = 1.0 / S.ctl->scale;
+  for (int64_t i = (int64_t)(blockIdx.x - S.v0) * 256 + threadIdx.x; i < S.n; i += (int64_t)S.vnb * 256)
+    S.x[i] = cadd(S.x[i], cscale(cmul(S.sq[i], to_d2(S.y[i])), unscale));
+}
+
+// r64 = b - A x (FP64) for the active systems, kCgG lanes per row.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgb_residual(const CgRef<T>* __restrict__ R, int ns) {
+  const int k = batch_sys<T, true>(R, ns);
+  const CgRef<T>& S = R[k];
+  if (!S.ctl->active) return;
+  const int lane = threadIdx.x % kCgG;
+  for (int64_t row = (int64_t)(blockIdx.x - S.r0) * (256 / kCgG) + threadIdx.x / kCgG;
+       __any_sync(0xffffffffu, row < S.n); row += (int64_t)S.rnb * (256 / kCgG)) {
+    double2 acc = make_double2(0.0, 0.0);
+    if (row < S.n)
+      for (int64_t q = S.rp[row] + lane; q < S.rp[row + 1]; q += kCgG) fma_c(acc, S.val[q], S.x[S.col[q]]);
+    for (int o = kCgG / 2; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (row < S.n && lane == 0) S.r64[row] = csub(S.b[row], acc);
+  }
+}
+
+// ||v||^2 (v = r64, or b when of_b) into st->rn2 for the active systems (every system when of_b).
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgb_norm(const CgRef<T>* __restrict__ R, int ns, int of_b) {
+  const int k = batch_sys<T, false>(R, ns);
+  const CgRef<T>& S = R[k];
+  if (!of_b && !S.ctl->active) return;
+  const double2* v = of_b ? S.b : S.r64;
+  const int lb = blockIdx.x - S.v0;
+  double a = 0.0;
+  for (int64_t i = (int64_t)lb * 256 + threadIdx.x; i < S.n; i += (int64_t)S.vnb * 256) a += nrm2(v[i]);
+  cg_block_sums<256>(make_double2(a, 0.0), make_double2(0.0, 0.0), S.part + (int64_t)lb * kCgSlots);
+  if (!last_of(&S.st->counter, S.vnb)) return;
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < S.vnb; b += 32) t += __ldcg(&S.part[(int64_t)b * kCgSlots]).x;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) {
+      S.st->rn2 = t;
+      S.st->counter = 0;
+      if (of_b) {  // the batch's start: ||b||, and which systems have anything to solve
+        CgCtl* c = S.ctl;
+        c->bnorm = sqrt(t);
+        c->relres = 0.0;
+        c->prev = INFINITY;
+        c->iters = c->solves = 0;
+        c->stalls = 0;
+        c->status = PETGEM_OK;
+        c->active = c->bnorm > 0.0;
+        c->ran = 0;
+      }
+    }
+  }
+}
+
+// One thread per system: book the inner solve that just ran, then the stopping decision on the
+// FP64 residual and the next inner solve's target and scale (the host-side rules of the
+// single-system solver, on the device so that the round needs no host round trip).
+__global__ void k_cgb_decide(CgCtl* __restrict__ ctl, const CState* __restrict__ st, int ns, double tol,
+                             double inner_tol, int64_t max_iters, int c128) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ns) return;
+  CgCtl& c = ctl[k];
+  if (c.ran) {
+    c.iters += st[k].k;
+    c.solves += 1;
+    if (st[k].done == 3) {
+      c.status = PETGEM_ERR_TIMEOUT;
+      c.active = 0;
+    } else if (st[k].done == 2 && st[k].k == 0) {
+      c.status = PETGEM_ERR_BREAKDOWN;
+      c.active = 0;
+    }
+    c.ran = 0;
+  }
+  if (!c.active) return;
+  const double rnorm = sqrt(st[k].rn2);
+  c.relres = rnorm / c.bnorm;
+  if (!isfinite(c.relres)) {
+    c.status = PETGEM_ERR_BREAKDOWN;
+    c.active = 0;
+  } else if (c.relres <= tol) {
+    c.active = 0;
+  } else if (c.iters >= max_iters) {
+    c.status = PETGEM_ERR_NOT_CONVERGED;
+    c.active = 0;
+  } else {
+    c.stalls = c.relres > 0.5 * c.prev ? c.stalls + 1 : 0;  // no longer halving: rounding floor
+    if (c.stalls >= 3) {
+      c.status = PETGEM_ERR_NOT_CONVERGED;
+      c.active = 0;
+    }
+  }
+  c.prev = c.relres;
+  if (!c.active) return;
+  const double need = 0.3 * tol * c.bnorm / rnorm;
+  c.inner = c128 ? need : fmin(fmax(inner_tol, need), 0.5);
+  c.scale = 1.0 / rnorm;
+}
+
+// Inner-solve start of every active system (as k_cg_start); an inactive system is marked done so
+// that the persistent kernel's blocks skip it.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgb_start(const CgRef<T>* __restrict__ R, int ns) {
+  const int k = batch_sys<T, false>(R, ns);
+  const CgRef<T>& S = R[k];
+  const int lb = blockIdx.x - S.v0;
+  if (!S.ctl->active) {
+    if (lb == 0 && threadIdx.x == 0) S.st->done = 1;
+    return;
+  }
+  using A = typename Acc<T>::type;
+  const double scale = S.ctl->scale;
+  A rho = zero<T>(), nr = zero<T>();
+  for (int64_t i = (int64_t)lb * 256 + threadIdx.x; i < S.n; i += (int64_t)S.vnb * 256) {
+    const T t = from_d2<T>(cscale(cmul(S.sq[i], S.r64[i]), scale));
+    S.r[i] = t;
+    S.p[i] = t;
+    S.y[i] = zero<T>();
+    bil_fma(rho, t, t);
+    nr.x += nrm2(t);
+  }
+  cg_block_sums<256>(rho, nr, S.part + (int64_t)lb * kCgSlots);
+  if (!last_of(&S.st->counter, S.vnb)) return;
+  __shared__ double2 tot[2];
+  cg_sum_blocks2<256>(S.part, S.vnb, 0, 1, tot);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    CState* st = S.st;
+    const double2 a = tot[0], b = tot[1];
+    const double inner = S.ctl->inner;
+    st->rho = a;
+    st->nr0 = b.x;
+    st->nr = b.x;
+    st->stop2 = inner * inner * b.x;
+    st->k = 0;
+    st->done = (b.x > 0.0 && isfinite(b.x)) ? 0 : (b.x == 0.0 ? 1 : 2);
+    st->gbar = 0;
+    st->grel = 0;
+    st->counter = 0;
+    S.ctl->ran = 1;
+  }
+}
+
+// Blocks of the persistent kernel for the active systems: in proportion to each system's matrix
+// entries times its expected iterations (the last inner solve's, or E^(1/3) before any ran), at
+// least one and at most what its rows fill.
+inline void batch_partition(const std::vector<int>& act, const std::vector<double>& work,
+                            const std::vector<int64_t>& cap, int total, std::vector<int>& nb) {
+  double sum = 0.0;
+  for (int k : act) sum += work[k];
+  int used = 0;
+  for (int k : act) {
+    nb[k] = (int)std::max<int64_t>(1, std::min<int64_t>(cap[k], (int64_t)(total * work[k] / sum)));
+    used += nb[k];
+  }
+  // hand out what rounding left, to the systems with the most work per block
+  while (used < total) {
+    int best = -1;
+    double bw = 0.0;
+    for (int k : act)
+      if (nb[k] < cap[k] && work[k] / nb[k] > bw) {
+        bw = work[k] / nb[k];
+        best = k;
+      }
+    if (best < 0) break;
+    nb[best] += 1;
+    used += 1;
+  }
+  while (used > total) {  // more systems than blocks' worth of minimums cannot happen (kBatchMax)
+    int best = -1;
+    double bw = INFINITY;
+    for (int k : act)
+      if (nb[k] > 1 && work[k] / nb[k] < bw) {
+        bw = work[k] / nb[k];
+        best = k;
+      }
+    if (best < 0) break;
+    nb[best] -= 1;
+    used -= 1;
+  }
+}
+
+struct BatchBuffers {
+  DevBuf vec, st, part, ctl, sys, ref;
+  cudaStream_t cap = nullptr;
+};
+
+template <int G, typename T>
+Status batch_inner_launch(cudaStream_t s, const CgSys<T>* dsys, int na, int grid, int steps) {
+  PG_TRY((cg_setup<T, G>()));
+  PG_CUDA(pdl_launch(k_cg_inner<T, G>, dim3(grid), dim3(256), 0, s, true, dsys, na, steps));
+  return Status{};
+}
+
+template <typename T>
+Status batch_inner(int G, cudaStream_t s, const CgSys<T>* dsys, int na, int grid, int steps) {
+  if (G == 2) return batch_inner_launch<2, T>(s, dsys, na, grid, steps);
+  if (G == 8) return batch_inner_launch<8, T>(s, dsys, na, grid, steps);
+  return batch_inner_launch<4, T>(s, dsys, na, grid, steps);
+}
+
+template <typename T>
+Status solve_batch(petgem_ctx* const* ctxs, int n_ctx, const petgem_solve_opts& o, double2* const* x,
+                   petgem_solve_info* info) {
+  petgem_ctx* c0 = ctxs[0];
+  cudaStream_t s = c0->stream;
+  const bool c128 = sizeof(T) == 16;
+  int sms = 0;
+  PG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->device));
+  CgBuffers* B0 = cg_bufs(c0);
+  if (!B0->batch) B0->batch = new BatchBuffers();
+  BatchBuffers* W = B0->batch;
+  // the systems
+  struct Sys {
+    petgem_ctx* c;
+    int src;
+    int64_t n, nnz;
+  };
+  std::vector<Sys> sys;
+  for (int k = 0; k < n_ctx; ++k)
+    for (int j = 0; j < ctxs[k]->n_src; ++j) sys.push_back(Sys{ctxs[k], j, ctxs[k]->n_edges, ctxs[k]->nnz});
+  const int ns = (int)sys.size();
+  if (ns == 0) return Status{};
+  if (ns > kBatchMax) return Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve_batch: more than 64 systems"};
+  // workspace: per system r, p, q, y (T) and r64 (FP64), each on a 256-byte boundary
+  const int pgrid = CgOcc<T>::value * sms;
+  std::vector<size_t> off(ns);
+  size_t bytes = 0;
+  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+  for (int k = 0; k < ns; ++k) {
+    off[k] = bytes;
+    bytes += 4 * al(sys[k].n * sizeof(T)) + al(sys[k].n * sizeof(double2));
+  }
+  std::vector<int> vnb(ns), rnb(ns);
+  size_t part_rows = 0;
+  for (int k = 0; k < ns; ++k) {
+    vnb[k] = (int)std::max<int64_t>(1, std::min<int64_t>(blocks_for(sys[k].n, 256), 2LL * sms));
+    rnb[k] = (int)std::max<int64_t>(1, std::min<int64_t>(blocks_for(sys[k].n * kCgG, 256), 4LL * sms));
+    part_rows += std::max(vnb[k], pgrid);
+  }
+  PG_TRY(W->vec.reserve(bytes));
+  PG_TRY(W->st.reserve(ns * sizeof(CState)));
+  PG_TRY(W->part.reserve(part_rows * kCgSlots * sizeof(double2)));
+  PG_TRY(W->ctl.reserve(ns * sizeof(CgCtl)));
+  PG_TRY(W->sys.reserve(ns * sizeof(CgSys<T>)));
+  PG_TRY(W->ref.reserve(ns * sizeof(CgRef<T>)));
+  CState* dst = W->st.as<CState>();
+  CgCtl* dctl = W->ctl.as<CgCtl>();
+  PG_CUDA(cudaMemsetAsync(dst, 0, ns * sizeof(CState), s));
+  // tables
+  std::vector<CgRef<T>> ref(ns);
+  std::vector<CgSys<T>> tab(ns);
+  int v0 = 0, r0 = 0;
+  size_t prow = 0;
+  unsigned char* base = W->vec.as<unsigned char>();
+  for (int k = 0; k < ns; ++k) {
+    petgem_ctx* c = sys[k].c;
+    CgBuffers* Bc = cg_bufs(c);
+    const int64_t n = sys[k].n;
+    unsigned char* v = base + off[k];
+    T* r = (T*)v;
+    T* p = (T*)(v + al(n * sizeof(T)));
+    T* q = (T*)(v + 2 * al(n * sizeof(T)));
+    T* y = (T*)(v + 3 * al(n * sizeof(T)));
+    double2* r64 = (double2*)(v + 4 * al(n * sizeof(T)));
+    double2* part = W->part.as<double2>() + prow * kCgSlots;
+    prow += std::max(vnb[k], pgrid);
+    ref[k] = CgRef<T>{c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(), Bc->sq.as<double2>(),
+                      c->b.as<double2>() + (int64_t)sys[k].src * n, nullptr,
+                      r64, r, p, y, dst + k, part, dctl + k, n, v0, vnb[k], r0, rnb[k]};
+    v0 += vnb[k];
+    r0 += rnb[k];
+    const T* at = c128 ? (const T*)Bc->a128.ptr : (const T*)Bc->a64.ptr;
+    tab[k] = CgSys<T>{c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), at, p, q, r, y, n, dst + k, part, 0, 0, 0};
+  }
+  // solution pointers: context k's sources in order
+  {
+    int k = 0;
+    for (int ci = 0; ci < n_ctx; ++ci)
+      for (int j = 0; j < ctxs[ci]->n_src; ++j, ++k) ref[k].x = x[ci] + (int64_t)j * ctxs[ci]->n_edges;
+  }
+  PG_CUDA(cudaMemcpyAsync(W->ref.ptr, ref.data(), ns * sizeof(CgRef<T>), cudaMemcpyHostToDevice, s));
+  const CgRef<T>* dref = W->ref.as<CgRef<T>>();
+  const int vgrid = v0, rgrid = r0;
+  // ||b|| of every system and the control block
+  k_cgb_norm<T><<<vgrid, 256, 0, s>>>(dref, ns, 1);
+  c0->launches++;
+  PG_CUDA(cudaGetLastError());
+  std::vector<CgCtl> hctl(ns);
+  PG_CUDA(cudaMemcpyAsync(hctl.data(), dctl, ns * sizeof(CgCtl), cudaMemcpyDeviceToHost, s));
+  PG_CUDA(cudaStreamSynchronize(s));
+  for (int k = 0; k < ns; ++k)
+    if (!hctl[k].active) PG_CUDA(cudaMemsetAsync(ref[k].x, 0, sys[k].n * sizeof(double2), s));
+  // the refinement round: direct launches, or their graph
+  auto round = [&](cudaStream_t rs) -> Status {
+    k_cgb_finish<T><<<vgrid, 256, 0, rs>>>(dref, ns);
+    k_cgb_residual<T><<<rgrid, 256, 0, rs>>>(dref, ns);
+    k_cgb_norm<T><<<vgrid, 256, 0, rs>>>(dref, ns, 0);
+    k_cgb_decide<<<1, kBatchMax, 0, rs>>>(dctl, dst, ns, o.tol, o.inner_tol, o.max_iters, c128 ? 1 : 0);
+    k_cgb_start<T><<<vgrid, 256, 0, rs>>>(dref, ns);
+    PG_CUDA(cudaGetLastError());
+    return Status{};
+  };
+  cudaGraphExec_t gexec = nullptr;
+  if (o.use_graphs) {
+    if (!W->cap) PG_CUDA(cudaStreamCreateWithFlags(&W->cap, cudaStreamNonBlocking));
+    PG_CUDA(cudaStreamBeginCapture(W->cap, cudaStreamCaptureModeThreadLocal));
+    const Status r = round(W->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(W->cap, &g);
+    if (!r.ok()) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (e != cudaSuccess) return Status{PETGEM_ERR_CUDA, std::string("batch round capture: ") + cudaGetErrorString(e)};
+    const cudaError_t ei = cudaGraphInstantiate(&gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return Status{PETGEM_ERR_CUDA, std::string("batch round graph: ") + cudaGetErrorString(ei)};
+  }
+  struct GraphGuard {
+    cudaGraphExec_t g;
+    ~GraphGuard() {
+      if (g) cudaGraphExecDestroy(g);
+    }
+  } guard{gexec};
+  // rounds
+  int G = o.spmv_lanes ? o.spmv_lanes : kCgG;
+  bool tuned = o.spmv_lanes != 0;
+  std::vector<double> work(ns);
+  std::vector<int64_t> cap(ns), lastk(ns, 0);
+  std::vector<CState> hst(ns);
+  std::vector<int> nb(ns, 0);
+  Status st_all;
+  while (true) {
+    if (gexec)
+      PG_CUDA(cudaGraphLaunch(gexec, s));
+    else
+      PG_TRY(round(s));
+    c0->launches += 5;
+    PG_CUDA(cudaMemcpyAsync(hctl.data(), dctl, ns * sizeof(CgCtl), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> act;
+    for (int k = 0; k < ns; ++k)
+      if (hctl[k].active) act.push_back(k);
+    if (act.empty()) break;
+    // scheduler: the blocks of the persistent grid divided among the active systems
+    auto plan = [&]() -> Status {
+      for (int k : act) {
+        const double expect = lastk[k] > 0 ? (double)lastk[k] : std::cbrt((double)sys[k].n);
+        work[k] = (double)sys[k].nnz * expect;
+        // the same cap for every lane count: the partition, and so the barrier counters' block
+        // counts, must not change between the launches of one inner solve
+        cap[k] = std::max<int64_t>(1, blocks_for(sys[k].n * 8, 256));
+      }
+      batch_partition(act, work, cap, pgrid, nb);
+      std::vector<CgSys<T>> at;
+      int b = 0;
+      for (int k : act) {
+        CgSys<T> e = tab[k];
+        e.b0 = b;
+        e.nb = nb[k];
+        e.kmax = o.max_iters - hctl[k].iters;
+        b += nb[k];
+        at.push_back(e);
+      }
+      PG_CUDA(cudaMemcpyAsync(W->sys.ptr, at.data(), at.size() * sizeof(CgSys<T>), cudaMemcpyHostToDevice, s));
+      return Status{};
+    };
+    auto grid_of = [&]() {
+      int g = 0;
+      for (int k : act) g += nb[k];
+      return g;
+    };
+    const CgSys<T>* dsys = W->sys.as<CgSys<T>>();
+    auto all_done = [&]() -> Status {
+      PG_CUDA(cudaMemcpyAsync(hst.data(), dst, ns * sizeof(CState), cudaMemcpyDeviceToHost, s));
+      PG_CUDA(cudaStreamSynchronize(s));
+      return Status{};
+    };
+    auto running = [&]() {
+      for (int k : act)
+        if (hst[k].done == 0 && hst[k].k < o.max_iters - hctl[k].iters) return true;
+      return false;
+    };
+    PG_TRY(plan());
+    if (!tuned) {
+      // autotuner: a few iterations with each lane count (two passes over the candidates, the
+      // faster of each pair kept), timed with events on the stream; the iterations count towards
+      // the solve
+      PG_TRY((cg_setup<T, 2>()));
+      PG_TRY((cg_setup<T, 4>()));
+      PG_TRY((cg_setup<T, 8>()));
+      struct Events {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Events() {
+          for (cudaEvent_t x : e)
+            if (x) cudaEventDestroy(x);
+        }
+      } ev;
+      PG_CUDA(cudaEventCreate(&ev.e[0]));
+      PG_CUDA(cudaEventCreate(&ev.e[1]));
+      float best[3] = {INFINITY, INFINITY, INFINITY};
+      const int cand[3] = {2, 4, 8};
+      for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < 3; ++i) {
+          PG_CUDA(cudaEventRecord(ev.e[0], s));
+          PG_TRY(batch_inner<T>(cand[i], s, dsys, (int)act.size(), grid_of(), kBatchTuneSteps));
+          PG_CUDA(cudaEventRecord(ev.e[1], s));
+          c0->launches++;
+          PG_CUDA(cudaEventSynchronize(ev.e[1]));
+          float ms = 0.f;
+          PG_CUDA(cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]));
+          best[i] = std::min(best[i], ms);
+        }
+      G = cand[std::min_element(best, best + 3) - best];
+      tuned = true;
+    }
+    PG_TRY(all_done());
+    while (running()) {
+      PG_TRY(batch_inner<T>(G, s, dsys, (int)act.size(), grid_of(), kCgChunk));
+      c0->launches++;
+      PG_TRY(all_done());
+    }
+    for (int k : act) lastk[k] = std::max<int64_t>(1, hst[k].k);
+  }
+  int k = 0;
+  for (int ci = 0; ci < n_ctx; ++ci)
+    for (int j = 0; j < ctxs[ci]->n_src; ++j, ++k) {
+      petgem_solve_info& inf = info[k];
+      inf = petgem_solve_info{};
+      inf.iters = hctl[k].iters;
+      inf.restarts = hctl[k].solves;
+      inf.refinements = hctl[k].solves;
+      inf.true_rel_residual = hctl[k].relres;
+      inf.status = hctl[k].status;
+      inf.spmv_lanes = G;
+      if (inf.status != PETGEM_OK && st_all.ok())
+        st_all = Status{inf.status, "context " + std::to_string(ci) + " source " + std::to_string(j) +
+                                        " did not converge (COCG batch)"};
+    }
+  return st_all;
+}
+
 }  // namespace
 
 Status run_solve_cocg(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info) {
@@ -1304,17 +1840,7 @@ Status run_solve_cocg(petgem_ctx* c, const petgem_solve_opts& o, double2* x, pet
   int sms = 0;
   PG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
   const bool c128 = o.precision != PETGEM_PREC_MIXED;
-  if (B->version != c->assembly_version) {
-    PG_TRY(B->sq.reserve(n * sizeof(double2)));
-    PG_TRY(B->a128.reserve(c->nnz * sizeof(double2)));
-    PG_TRY(B->a64.reserve(c->nnz * sizeof(float2)));
-    k_cg_sqrt_diag<<<blocks_for(n, 256), 256, 0, s>>>(c->diag.as<double2>(), n, B->sq.as<double2>());
-    k_cg_scale<<<blocks_for(n, 256), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(),
-                                                  B->sq.as<double2>(), n, B->a128.as<double2>(), B->a64.as<float2>());
-    c->launches += 2;
-    PG_CUDA(cudaGetLastError());
-    B->version = c->assembly_version;
-  }
+  PG_TRY(cg_prepare(c));
   const size_t tb = c128 ? sizeof(double2) : sizeof(float2);
   PG_TRY(B->r64.reserve(n * sizeof(double2)));
   for (DevBuf* d : {&B->r, &B->p, &B->q, &B->y}) PG_TRY(d->reserve(n * tb));
@@ -1354,9 +1880,45 @@ Status run_solve_cocg(petgem_ctx* c, const petgem_solve_opts& o, double2* x, pet
   return worst;
 }
 
+Status run_solve_batch(petgem_ctx* const* ctxs, int n_ctx, const petgem_solve_opts& o, double2* const* x,
+                       petgem_solve_info* info) {
+  petgem_ctx* c0 = ctxs[0];
+  for (int k = 0; k < n_ctx; ++k) PG_TRY(cg_prepare(ctxs[k]));
+  // order: every context's queued work before the batch (on ctxs[0]'s stream), the batch before
+  // anything queued on them afterwards
+  std::vector<cudaEvent_t> ev;
+  auto join = [&](cudaStream_t from, cudaStream_t to) -> Status {
+    if (from == to) return Status{};
+    cudaEvent_t e;
+    PG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ev.push_back(e);
+    PG_CUDA(cudaEventRecord(e, from));
+    PG_CUDA(cudaStreamWaitEvent(to, e, 0));
+    return Status{};
+  };
+  Status r;
+  for (int k = 1; k < n_ctx && r.ok(); ++k) r = join(ctxs[k]->stream, c0->stream);
+  if (r.ok())
+    r = o.precision == PETGEM_PREC_MIXED ? solve_batch<float2>(ctxs, n_ctx, o, x, info)
+                                         : solve_batch<double2>(ctxs, n_ctx, o, x, info);
+  for (int k = 1; k < n_ctx; ++k) {
+    const Status j = join(c0->stream, ctxs[k]->stream);
+    if (r.ok() && !j.ok()) r = j;
+  }
+  cudaStreamSynchronize(c0->stream);
+  for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  return r;
+}
+
 void destroy_cocg(petgem_ctx* c) {
   if (!c->cocg) return;
   CgBuffers* B = static_cast<CgBuffers*>(c->cocg);
+  if (B->batch) {
+    for (DevBuf* d : {&B->batch->vec, &B->batch->st, &B->batch->part, &B->batch->ctl, &B->batch->sys, &B->batch->ref})
+      d->release();
+    if (B->batch->cap) cudaStreamDestroy(B->batch->cap);
+    delete B->batch;
+  }
   for (DevBuf* d : {&B->sq, &B->a128, &B->a64, &B->r64, &B->r, &B->p, &B->q, &B->y, &B->state, &B->partials, &B->sys, &B->Bt,
                     &B->X, &B->R, &B->rb, &B->pb, &B->qb, &B->yb, &B->bstates, &B->bgrp, &B->bscal})
     d->release();

@@ -127,6 +127,8 @@ Status run_receivers(petgem_ctx* c, int32_t n_rcv, const double* rx, const doubl
 Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info);
 Status run_solve_block(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info);
 Status run_solve_cocg(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info);
+Status run_solve_batch(petgem_ctx* const* ctxs, int n_ctx, const petgem_solve_opts& o, double2* const* x,
+                       petgem_solve_info* info);
 Status run_spmv(petgem_ctx* c, const double2* x, double2* y);
 void destroy_solver(petgem_ctx* c);
 void destroy_cocg(petgem_ctx* c);
