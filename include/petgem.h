@@ -170,6 +170,16 @@ int petgem_get_topology(petgem_ctx *ctx, int32_t *edges, int32_t *tet_edges, int
 int petgem_assemble(petgem_ctx *ctx, double freq_hz, const double *sigma, double sigma_p,
                     int32_t n_src, const petgem_dipole *src);
 
+/* Another frequency (and set of sources) on the same mesh, conductivities and background sigma_p
+ * as the last petgem_assemble: eq. 9 is linear in w, A(w) = K + i w mu0 M_sigma with the real
+ * global matrices K = sum_e K^e and M_sigma = sum_e sigma_e M^e, which petgem_assemble keeps; this
+ * call forms A and diag(A) from them (one pass over the matrix entries instead of the element
+ * matrices and their gather) and computes the right-hand sides for the new frequency and
+ * sources.  petgem_assemble itself forms A the same way, so the two give bit-identical systems.
+ * src: host petgem_dipole[n_src].  Errors: PETGEM_ERR_INVALID_ARG (no petgem_assemble before,
+ * freq_hz <= 0, n_src < 1, a bad dipole). */
+int petgem_assemble_frequency(petgem_ctx *ctx, double freq_hz, int32_t n_src, const petgem_dipole *src);
+
 /* Copy the assembled system out.  nnz_out: host (synchronises).  row_ptr int64[E+1],
  * col int32[nnz], val complex128[nnz], b complex128[n_src][E], diag complex128[E] (each device,
  * optional).  Rows list columns in increasing order. */

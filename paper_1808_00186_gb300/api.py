@@ -54,6 +54,7 @@ _SIGNATURES = {
     "petgem_mesh_edges": (ctypes.c_int, [_P, _I64, _P, _I64, _P, ctypes.POINTER(_I64)]),
     "petgem_get_topology": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "petgem_assemble": (ctypes.c_int, [_P, _D, _P, _D, _I32, ctypes.POINTER(petgem_dipole)]),
+    "petgem_assemble_frequency": (ctypes.c_int, [_P, _D, _I32, ctypes.POINTER(petgem_dipole)]),
     "petgem_get_system": (ctypes.c_int, [_P, ctypes.POINTER(_I64), _P, _P, _P, _P, _P]),
     "petgem_get_elements": (ctypes.c_int, [_P, _P, _P, _P]),
     "petgem_solve": (ctypes.c_int, [_P, ctypes.POINTER(petgem_solve_opts), _P, ctypes.POINTER(petgem_solve_info)]),
@@ -153,6 +154,11 @@ def dipoles(sources) -> ctypes.Array:
 def petgem_assemble(ctx, freq, sigma, sigma_p, sources):
     arr = dipoles(sources)
     _check(ctx, load().petgem_assemble(ctx, float(freq), _ptr(sigma), float(sigma_p), len(sources), arr))
+
+
+def petgem_assemble_frequency(ctx, freq, sources):
+    arr = dipoles(sources)
+    _check(ctx, load().petgem_assemble_frequency(ctx, float(freq), len(sources), arr))
 
 
 def petgem_get_system(ctx, row_ptr=None, col=None, val=None, b=None, diag=None) -> int:
@@ -365,6 +371,10 @@ class Context:
         self.sigma = sigma if hasattr(sigma, "data_ptr") else self.tensor(sigma, self.torch.float64)
         self.n_src = len(sources)
         petgem_assemble(self.h, freq, self.sigma, sigma_p, sources)
+
+    def assemble_frequency(self, freq, sources):
+        self.n_src = len(sources)
+        petgem_assemble_frequency(self.h, freq, sources)
 
     def system(self):
         tt = self.torch

@@ -139,7 +139,7 @@ int petgem_destroy(petgem_ctx* c) {
   c->slots.release();
   for (petgem::DevBuf* b : {&c->nodes, &c->tets, &c->edges, &c->tet_edges, &c->signs, &c->boundary, &c->occ, &c->eptr,
                             &c->row_ptr, &c->col, &c->gptr, &c->pkey, &c->pij, &c->flags, &c->sigma, &c->K21, &c->M21,
-                            &c->vol, &c->val, &c->diag, &c->b})
+                            &c->vol, &c->val, &c->diag, &c->b, &c->kval, &c->mval})
     b->release();
   for (auto& p : c->pending) {
     cudaEventDestroy(p.start);
@@ -234,6 +234,28 @@ int petgem_assemble(petgem_ctx* c, double freq_hz, const double* sigma, double s
   c->src.assign(src, src + n_src);
   c->assembled = false;
   s = petgem::build_assembly(c, sigma);
+  if (!s.ok()) cudaGetLastError();
+  return finish(c, s);
+}
+
+int petgem_assemble_frequency(petgem_ctx* c, double freq_hz, int32_t n_src, const petgem_dipole* src) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (!c->assembled)
+    return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_assemble_frequency: call petgem_assemble first"});
+  if (!(freq_hz > 0.0) || n_src < 1 || !src)
+    return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_assemble_frequency: need freq > 0 and n_src >= 1"});
+  for (int32_t i = 0; i < n_src; ++i)
+    if (src[i].axis < 0 || src[i].axis > 2 || !std::isfinite(src[i].x) || !std::isfinite(src[i].y) ||
+        !std::isfinite(src[i].z) || !std::isfinite(src[i].moment))
+      return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_assemble_frequency: bad dipole " + std::to_string(i)});
+  Status s = set_device(c);
+  if (!s.ok()) return finish(c, s);
+  c->freq = freq_hz;
+  c->omega = 2.0 * 3.141592653589793238462643383279502884 * freq_hz;
+  c->n_src = n_src;
+  c->src.assign(src, src + n_src);
+  c->assembled = false;
+  s = petgem::build_frequency(c);
   if (!s.ok()) cudaGetLastError();
   return finish(c, s);
 }

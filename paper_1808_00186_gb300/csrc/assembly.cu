@@ -135,33 +135,54 @@ __global__ void k_rhs_gather(const int64_t* __restrict__ eptr, const int32_t* __
   b[(int64_t)(s0 + sc) * n_edges + e] = acc;
 }
 
-// One thread per row: A[q] = sum of the gathered element entries K + i w mu0 sigma_t M in
-// (tet, i, j) order; an empty gather range is a Dirichlet identity entry.  Also the diagonal.
+// One thread per row: the global K[q] and M_sigma[q] = sums of the gathered element entries K^e
+// and sigma_t M^e in (tet, i, j) order (an empty gather range is a Dirichlet identity entry:
+// K = 1, M_sigma = 0), kept for later frequencies, and A[q] = K + i w mu0 M_sigma (eq. 9).  Also
+// the diagonal.
 __global__ void k_matrix_gather(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                 const int64_t* __restrict__ gptr, const uint64_t* __restrict__ pkey,
                                 const uint8_t* __restrict__ pij, const double* __restrict__ K21,
                                 const double* __restrict__ M21, const double* __restrict__ sigma,
-                                int64_t n_tets, int64_t n_edges, double wmu0, double2* __restrict__ val,
-                                double2* __restrict__ diag) {
+                                int64_t n_tets, int64_t n_edges, double wmu0, double* __restrict__ kval,
+                                double* __restrict__ mval, double2* __restrict__ val, double2* __restrict__ diag) {
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= n_edges) return;
   double2 dg = make_double2(0.0, 0.0);
   for (int64_t q = row_ptr[r]; q < row_ptr[r + 1]; ++q) {
     int64_t g0 = gptr[q], g1 = gptr[q + 1];
-    double2 acc;
+    double ks = 0.0, ms = 0.0;
     if (g0 == g1) {
-      acc = make_double2(1.0, 0.0);
+      ks = 1.0;
     } else {
-      acc = make_double2(0.0, 0.0);
       for (int64_t p = g0; p < g1; ++p) {
         int64_t t = (int64_t)(uint32_t)(pkey[p] & 0xffffffffu);
         int k = kSym[pij[p]];
-        acc.x += K21[k * n_tets + t];
-        acc.y += wmu0 * sigma[t] * M21[k * n_tets + t];
+        ks += K21[k * n_tets + t];
+        ms += sigma[t] * M21[k * n_tets + t];
       }
     }
-    val[q] = acc;
-    if (col[q] == r) dg = acc;
+    kval[q] = ks;
+    mval[q] = ms;
+    const double2 a = make_double2(ks, wmu0 * ms);
+    val[q] = a;
+    if (col[q] == r) dg = a;
+  }
+  diag[r] = dg;
+}
+
+// Another frequency on the same mesh and conductivities: A[q] = K[q] + i w mu0 M_sigma[q] from
+// the kept real matrices (eq. 9 is linear in w), one thread per row; also the diagonal.
+__global__ void k_matrix_frequency(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                   const double* __restrict__ kval, const double* __restrict__ mval,
+                                   int64_t n_edges, double wmu0, double2* __restrict__ val,
+                                   double2* __restrict__ diag) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= n_edges) return;
+  double2 dg = make_double2(0.0, 0.0);
+  for (int64_t q = row_ptr[r]; q < row_ptr[r + 1]; ++q) {
+    const double2 a = make_double2(kval[q], wmu0 * mval[q]);
+    val[q] = a;
+    if (col[q] == r) dg = a;
   }
   diag[r] = dg;
 }
@@ -190,15 +211,46 @@ Status build_assembly(petgem_ctx* c, const double* sigma_dev) {
 
   PG_TRY(c->val.reserve(c->nnz * sizeof(double2)));
   PG_TRY(c->diag.reserve(E * sizeof(double2)));
+  PG_TRY(c->kval.reserve(c->nnz * sizeof(double)));
+  PG_TRY(c->mval.reserve(c->nnz * sizeof(double)));
   {
-    KernelTimer kt(c, "matrix_gather", (double)c->nnz * (8 + 16 + 8) + (double)c->n_pairs * (9 + 24));
+    KernelTimer kt(c, "matrix_gather", (double)c->nnz * (8 + 16 + 16 + 8) + (double)c->n_pairs * (9 + 24));
     k_matrix_gather<<<blocks_for(E, 128), 128, 0, s>>>(
         c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->gptr.as<int64_t>(), c->pkey.as<uint64_t>(),
         c->pij.as<uint8_t>(), c->K21.as<double>(), c->M21.as<double>(), c->sigma.as<double>(), T, E, c->omega * kMu0,
-        c->val.as<double2>(), c->diag.as<double2>());
+        c->kval.as<double>(), c->mval.as<double>(), c->val.as<double2>(), c->diag.as<double2>());
     c->launches++;
   }
   PG_CUDA(cudaGetLastError());
+  PG_TRY(build_rhs(c));
+  c->assembled = true;
+  c->assembly_version++;
+  return Status{};
+}
+
+Status build_frequency(petgem_ctx* c) {
+  cudaStream_t s = c->stream;
+  const int64_t E = c->n_edges;
+  uint32_t* flags = c->flags.as<uint32_t>();
+  PG_CUDA(cudaMemsetAsync(flags, 0, sizeof(uint32_t), s));
+  {
+    KernelTimer kt(c, "matrix_frequency", (double)c->nnz * (8 + 8 + 4 + 16) + 8.0 * (E + 1) + 16.0 * E);
+    k_matrix_frequency<<<blocks_for(E, 128), 128, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(),
+                                                           c->kval.as<double>(), c->mval.as<double>(), E,
+                                                           c->omega * kMu0, c->val.as<double2>(), c->diag.as<double2>());
+    c->launches++;
+  }
+  PG_CUDA(cudaGetLastError());
+  PG_TRY(build_rhs(c));
+  c->assembled = true;
+  c->assembly_version++;
+  return Status{};
+}
+
+// Right-hand sides of the context's sources at its frequency (eq. 6, App. A).
+Status build_rhs(petgem_ctx* c) {
+  cudaStream_t s = c->stream;
+  const int64_t T = c->n_tets, E = c->n_edges, S = c->n_src;
 
   // Right-hand sides, in chunks of sources so the per-slot buffer stays near 1 GB.
   PG_TRY(c->b.reserve(S * E * sizeof(double2)));
@@ -231,8 +283,6 @@ Status build_assembly(petgem_ctx* c, const double* sigma_dev) {
   PG_CUDA(cudaFreeAsync(be, s));
   PG_CUDA(cudaFreeAsync(dsrc, s));
   PG_TRY(check_flags(c, "petgem_assemble"));
-  c->assembled = true;
-  c->assembly_version++;
   return Status{};
 }
 

@@ -78,6 +78,7 @@ struct petgem_ctx {
   std::vector<petgem_dipole> src;
   petgem::DevBuf sigma, K21, M21, vol;
   petgem::DevBuf val, diag, b;             // A (complex128), diag(A), b [n_src][E]
+  petgem::DevBuf kval, mval;               // real K and M_sigma on the pattern (A = K + i w mu0 M_sigma)
 
   // ---- solver state (krylov.cu)
   petgem::Solver* solver = nullptr;
@@ -122,6 +123,8 @@ Status check_flags(petgem_ctx* c, const char* where);
 // Stages implemented in the .cu files.
 Status build_topology(petgem_ctx* c);
 Status build_assembly(petgem_ctx* c, const double* sigma_dev);
+Status build_frequency(petgem_ctx* c);
+Status build_rhs(petgem_ctx* c);
 Status run_receivers(petgem_ctx* c, int32_t n_rcv, const double* rx, const double2* x, double2* out,
                      bool* outside);
 Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info);
