@@ -262,6 +262,11 @@ def run_ours(args):
         cocg = {"precision": "mixed", "ms_per_step": round(ms_cg, 3), "s_per_source": round(ms_cg / 1e3 / S, 6),
                 "iters": info_cg[0]["iters"], "inner_solves": info_cg[0]["restarts"],
                 "true_rel_residual": info_cg[0]["true_rel_residual"], "kernels": cks}
+        # SQMR (the paper's Section 5.3 solver): COCG's recurrences with the QMR-smoothed iterate
+        ms_q, info_q, _, _ = timed(api.PREC_MIXED, args.steps, 1, method=api.METHOD_SQMR)
+        cocg["sqmr"] = {"precision": "mixed", "ms_per_step": round(ms_q, 3), "s_per_source": round(ms_q / 1e3 / S, 6),
+                        "iters": info_q[0]["iters"], "inner_solves": info_q[0]["restarts"],
+                        "true_rel_residual": info_q[0]["true_rel_residual"]}
 
     # Multi-source block solve (all sources of one frequency in one SpMM-based solve): the marine
     # mesh with args.block_sources dipoles along x in [-4, 4] km; timed once after a warm-up.

@@ -106,7 +106,12 @@ typedef struct {
  *     (PETGEM_ERR_UNSUPPORTED otherwise).
  *     info.restarts counts the inner solves.  A breakdown of the bilinear form (p^T A p = 0) ends
  *     an inner solve early; one at the very first step returns PETGEM_ERR_BREAKDOWN. */
-enum { PETGEM_METHOD_GMRES = 0, PETGEM_METHOD_COCG = 1 };
+/*   SQMR: symmetric QMR, the solver of the paper's Section 5.3: the Lanczos recurrences of COCG
+ *     (same residuals, directions and scalars) with the quasi-minimal-residual iterate, which
+ *     smooths COCG's residual history; each inner solve stops when the quasi-residual norm tau
+ *     fell by inner_tol.  Jacobi as for COCG (the symmetric split D^{1/2} D^{1/2}); sources are
+ *     solved one after the other (`batch` is ignored); otherwise as COCG. */
+enum { PETGEM_METHOD_GMRES = 0, PETGEM_METHOD_COCG = 1, PETGEM_METHOD_SQMR = 2 };
 
 /* Orthogonalisation of each new Krylov vector w against the basis V:
  *   CGS: classical Gram-Schmidt once (two passes over V per step; the default of PETSc's GMRES);

@@ -24,7 +24,7 @@ OK, ERR_INVALID_ARG, ERR_BAD_MESH, ERR_DEGENERATE_TET, ERR_OUT_OF_MEMORY, ERR_CU
 PREC_C128, PREC_MIXED = 0, 1
 ORTH_CGS2, ORTH_CGS, ORTH_CGS_IFNEEDED = 0, 1, 2
 PRECOND_JACOBI, PRECOND_LEARNED = 0, 1
-METHOD_GMRES, METHOD_COCG = 0, 1
+METHOD_GMRES, METHOD_COCG, METHOD_SQMR = 0, 1, 2
 
 
 class petgem_dipole(ctypes.Structure):

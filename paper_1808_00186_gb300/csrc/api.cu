@@ -307,10 +307,10 @@ int petgem_solve(petgem_ctx* c, const petgem_solve_opts* opts, void* x, petgem_s
   o.use_graphs = 0;
   o.method = PETGEM_METHOD_GMRES;
   if (opts) o = *opts;
-  if (o.method != PETGEM_METHOD_GMRES && o.method != PETGEM_METHOD_COCG)
+  if (o.method != PETGEM_METHOD_GMRES && o.method != PETGEM_METHOD_COCG && o.method != PETGEM_METHOD_SQMR)
     return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve: unknown method"});
-  if (o.method == PETGEM_METHOD_COCG && o.precond != PETGEM_PRECOND_JACOBI)
-    return finish(c, Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve: COCG takes the Jacobi preconditioner only"});
+  if (o.method != PETGEM_METHOD_GMRES && o.precond != PETGEM_PRECOND_JACOBI)
+    return finish(c, Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve: COCG and SQMR take the Jacobi preconditioner only"});
   if (!(o.tol > 0.0) || o.max_iters < 0 || (o.precision != PETGEM_PREC_C128 && o.precision != PETGEM_PREC_MIXED) ||
       (o.precond != PETGEM_PRECOND_JACOBI && o.precond != PETGEM_PRECOND_LEARNED) ||
       !(o.inner_tol >= 0.0 && o.inner_tol < 1.0) || o.orth < 0 ||

@@ -37,6 +37,9 @@ struct CState {
   double2 sc;               // the scalar a reducing barrier published (alpha or beta)
   int sc_dn;                // and its stopping decision
   int pad2;
+  double2 sc2;              // SQMR: c^2 alpha, the weight of p in the smoothing direction d
+  double sc3;               // SQMR: c^2 theta_prev^2, the weight of the previous d
+  double tau, theta;        // SQMR: quasi-residual norm and theta of the last step
   double2 rho;  // r^T r
   double2 alpha, beta;
   float2 alpha32, beta32;
@@ -171,11 +174,12 @@ __global__ void __launch_bounds__(kT) k_cg_norm(const double2* __restrict__ v, i
 // Inner-solve start: r = p = scale S r64 (rounded to T), y = 0, rho = r^T r, ||r||^2, threshold.
 // scale = 1 / ||r64|| keeps the complex64 vectors of O(1) size: after a few refinements the
 // residual's entries are ~1e-20 and their squares would underflow in FP32.
+// SQMR (dvec != null): also d = 0, tau = ||r||, theta = 0.
 template <typename T>
 __global__ void __launch_bounds__(kT) k_cg_start(const double2* __restrict__ r64, const double2* __restrict__ sq,
-                                                 T* __restrict__ r, T* __restrict__ p, T* __restrict__ y, int64_t n,
-                                                 CState* __restrict__ st, double2* __restrict__ partials,
-                                                 double inner, double scale) {
+                                                 T* __restrict__ r, T* __restrict__ p, T* __restrict__ y,
+                                                 T* __restrict__ dvec, int64_t n, CState* __restrict__ st,
+                                                 double2* __restrict__ partials, double inner, double scale) {
   using A = typename Acc<T>::type;
   A rho = zero<T>(), nr = zero<T>();
   const int64_t base = blockIdx.x * (int64_t)kRows + threadIdx.x;
@@ -187,6 +191,7 @@ __global__ void __launch_bounds__(kT) k_cg_start(const double2* __restrict__ r64
       r[i] = t;
       p[i] = t;
       y[i] = zero<T>();
+      if (dvec) dvec[i] = zero<T>();
       bil_fma(rho, t, t);
       nr.x += nrm2(t);
     }
@@ -205,6 +210,8 @@ __global__ void __launch_bounds__(kT) k_cg_start(const double2* __restrict__ r64
       st->done = (b.x > 0.0 && isfinite(b.x)) ? 0 : (b.x == 0.0 ? 1 : 2);
       st->gbar = 0;
       st->grel = 0;
+      st->tau = sqrt(b.x);
+      st->theta = 0.0;
       st->counter = 0;
     }
   }
@@ -229,6 +236,7 @@ struct CgSys {
   const int32_t* col;
   const T* val;
   T *p, *q, *r, *y;
+  T* d;           // SQMR: the smoothing direction (unused by COCG)
   int64_t n;
   CState* st;
   double2* part;  // [nb][kCgSlots]: slot 0 r^T r, 1 ||r||^2, 2 p^T q
@@ -317,9 +325,9 @@ __device__ inline void cg_sum_blocks2(const double2* part, int nb, int s0, int s
 //   stage 1 (after the update): r^T r and ||r||^2; the stopping test, beta = rho' / rho, k, nr.
 // The wait is bounded (kCgWaitNs); the result is false in every thread when it gave up.  On
 // return *s_sc and *s_dn hold the scalar and decision in every block.
-template <int NT, int STAGE>
+template <int NT, int STAGE, bool QMR>
 __device__ inline bool cg_reduce_barrier(CState* st, const double2* part, unsigned nb, int* s_ok, int* s_last,
-                                         double2* s_sc, int* s_dn) {
+                                         double2* s_sc, int* s_dn, double2* s_sc2, double* s_sc3) {
   __syncthreads();
   unsigned long long target = 0;  // this barrier's closing arrival count (thread 0)
   if (threadIdx.x == 0) {
@@ -363,9 +371,26 @@ __device__ inline bool cg_reduce_barrier(CState* st, const double2* part, unsign
         const double nrm = tot[1].x;
         st->k += 1;
         st->nr = nrm;
+        // SQMR: quasi-minimal-residual smoothing of the step (theta, c, tau) and the weights of
+        // d = c^2 theta_prev^2 d + c^2 alpha p; the stopping test is on the quasi-residual tau
+        double test = nrm;
+        if (QMR) {  // no smoothing step when the norm is not finite
+          st->sc2 = make_double2(0.0, 0.0);
+          st->sc3 = 0.0;
+        }
+        if (QMR && isfinite(nrm)) {
+          const double th = sqrt(nrm) / st->tau;
+          const double c2 = 1.0 / (1.0 + th * th);
+          const double tau = st->tau * th * sqrt(c2);
+          st->sc2 = cscale(st->alpha, c2);
+          st->sc3 = c2 * st->theta * st->theta;
+          st->theta = th;
+          st->tau = tau;
+          test = tau * tau;
+        }
         if (!isfinite(nrm))
           d = 2;
-        else if (nrm <= st->stop2)
+        else if (test <= st->stop2)
           d = 1;
         else if (!(cabs2(st->rho) > 0.0))
           d = 2;
@@ -380,11 +405,19 @@ __device__ inline bool cg_reduce_barrier(CState* st, const double2* part, unsign
       st->sc_dn = d;
       *s_sc = sc;
       *s_dn = d;
+      if (QMR && STAGE == 1) {
+        *s_sc2 = st->sc2;
+        *s_sc3 = st->sc3;
+      }
       asm volatile("st.release.gpu.u64 [%0], %1;" ::"l"(&st->grel), "l"(target) : "memory");
     }
   } else if (threadIdx.x == 0) {
     *s_sc = __ldcg(&st->sc);
     *s_dn = __ldcg(&st->sc_dn);
+    if (QMR && STAGE == 1) {
+      *s_sc2 = __ldcg(&st->sc2);
+      *s_sc3 = __ldcg(&st->sc3);
+    }
   }
   __syncthreads();
   return true;
@@ -493,11 +526,12 @@ __device__ inline typename Acc<T>::type cg_spmv_rows(const int64_t* __restrict__
 // The scalars are formed once per barrier, by the block that arrives last, and the state always
 // holds the current rho, k and ||r||^2.  The grid must be resident at once (cooperative launch).
 // A barrier that gives up sets done = 3.
-template <typename T, int G>
+template <typename T, int G, bool QMR>
 __global__ void __launch_bounds__(256, CgOcc<T>::value)
     k_cg_inner(const CgSys<T>* __restrict__ sys, int nsys, int max_steps) {
   __shared__ int s_sys, s_ok, s_dn, s_last;
-  __shared__ double2 s_sc;
+  __shared__ double2 s_sc, s_sc2;
+  __shared__ double s_sc3;
   pdl_wait();
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -518,6 +552,7 @@ __global__ void __launch_bounds__(256, CgOcc<T>::value)
   const int32_t* col = S->col;
   const T* val = S->val;
   T *p = S->p, *q = S->q, *r = S->r, *y = S->y;
+  T* dq = S->d;
   double2* part = S->part;
   using A = typename Acc<T>::type;
   const int64_t groups = (int64_t)nb * (256 / G);
@@ -527,7 +562,7 @@ __global__ void __launch_bounds__(256, CgOcc<T>::value)
   for (int64_t step = 0; step < steps; ++step) {
     const A dot = cg_spmv_rows<T, G>(rp, col, val, p, q, n, row0, groups);
     cg_block_sums<256>(dot, zero<T>(), part + (int64_t)lb * kCgSlots + 2);
-    if (!cg_reduce_barrier<256, 0>(st, part, nb, &s_ok, &s_last, &s_sc, &s_dn)) {
+    if (!cg_reduce_barrier<256, 0, QMR>(st, part, nb, &s_ok, &s_last, &s_sc, &s_dn, &s_sc2, &s_sc3)) {
       fail = true;
       break;
     }
@@ -573,44 +608,102 @@ __global__ void __launch_bounds__(256, CgOcc<T>::value)
     rh.y += (decltype(rh.x))rh64.y;
     nr.x += (decltype(nr.x))nr64.x;
     cg_block_sums<256>(rh, nr, part + (int64_t)lb * kCgSlots);
-    if (!cg_reduce_barrier<256, 1>(st, part, nb, &s_ok, &s_last, &s_sc, &s_dn)) {
+    if (!cg_reduce_barrier<256, 1, QMR>(st, part, nb, &s_ok, &s_last, &s_sc, &s_dn, &s_sc2, &s_sc3)) {
       fail = true;
       break;
     }
-    if (s_dn) {  // stopped: the iterate still takes this step's alpha p
-      for (int64_t j = first; j < n; j += stride) {
-        T yv = y[j];
-        fma_c(yv, al, p[j]);
+    if (QMR) {
+      // SQMR: d = c^2 theta_prev^2 d + c^2 alpha p, y += d (the smoothed iterate), p = r + beta p
+      const T wp = from_d2<T>(s_sc2);
+      const decltype(wp.x) wd = (decltype(wp.x))s_sc3;
+      if (s_dn) {  // stopped: the iterate still takes this step's smoothing
+        for (int64_t j = first; j < n; j += stride) {
+          T dv = dq[j];
+          dv.x *= wd;
+          dv.y *= wd;
+          fma_c(dv, wp, p[j]);
+          dq[j] = dv;
+          T yv = y[j];
+          yv.x += dv.x;
+          yv.y += dv.y;
+          y[j] = yv;
+        }
+        break;
+      }
+      const T be = from_d2<T>(s_sc);
+      int64_t j = first;
+      for (; j + stride < n; j += 2 * stride) {
+        T a[2], b[2], c[2], e[2];
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          a[v] = r[j + v * stride];
+          b[v] = p[j + v * stride];
+          c[v] = y[j + v * stride];
+          e[v] = dq[j + v * stride];
+        }
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          e[v].x *= wd;
+          e[v].y *= wd;
+          fma_c(e[v], wp, b[v]);
+          dq[j + v * stride] = e[v];
+          c[v].x += e[v].x;
+          c[v].y += e[v].y;
+          y[j + v * stride] = c[v];
+          fma_c(a[v], be, b[v]);
+          p[j + v * stride] = a[v];
+        }
+      }
+      for (; j < n; j += stride) {
+        const T pv = p[j];
+        T dv = dq[j];
+        dv.x *= wd;
+        dv.y *= wd;
+        fma_c(dv, wp, pv);
+        dq[j] = dv;
+        T yv = y[j], rv = r[j];
+        yv.x += dv.x;
+        yv.y += dv.y;
         y[j] = yv;
+        fma_c(rv, be, pv);
+        p[j] = rv;
       }
-      break;
-    }
-    // y += alpha p and p = r + beta p
-    const T be = from_d2<T>(s_sc);
-    int64_t j = first;
-    for (; j + 3 * stride < n; j += 4 * stride) {
-      T a[4], b[4], c[4];
+    } else {
+      if (s_dn) {  // stopped: the iterate still takes this step's alpha p
+        for (int64_t j = first; j < n; j += stride) {
+          T yv = y[j];
+          fma_c(yv, al, p[j]);
+          y[j] = yv;
+        }
+        break;
+      }
+      // y += alpha p and p = r + beta p
+      const T be = from_d2<T>(s_sc);
+      int64_t j = first;
+      for (; j + 3 * stride < n; j += 4 * stride) {
+        T a[4], b[4], c[4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        a[v] = r[j + v * stride];
-        b[v] = p[j + v * stride];
-        c[v] = y[j + v * stride];
-      }
+        for (int v = 0; v < 4; ++v) {
+          a[v] = r[j + v * stride];
+          b[v] = p[j + v * stride];
+          c[v] = y[j + v * stride];
+        }
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        fma_c(c[v], al, b[v]);
-        y[j + v * stride] = c[v];
-        fma_c(a[v], be, b[v]);
-        p[j + v * stride] = a[v];
+        for (int v = 0; v < 4; ++v) {
+          fma_c(c[v], al, b[v]);
+          y[j + v * stride] = c[v];
+          fma_c(a[v], be, b[v]);
+          p[j + v * stride] = a[v];
+        }
       }
-    }
-    for (; j < n; j += stride) {
-      const T pv = p[j];
-      T yv = y[j], rv = r[j];
-      fma_c(yv, al, pv);
-      y[j] = yv;
-      fma_c(rv, be, pv);
-      p[j] = rv;
+      for (; j < n; j += stride) {
+        const T pv = p[j];
+        T yv = y[j], rv = r[j];
+        fma_c(yv, al, pv);
+        y[j] = yv;
+        fma_c(rv, be, pv);
+        p[j] = rv;
+      }
     }
     if (!cg_barrier(&st->gbar, nb, &s_ok)) {
       fail = true;
@@ -623,12 +716,12 @@ __global__ void __launch_bounds__(256, CgOcc<T>::value)
 constexpr int kCgChunk = 1024;  // iterations per persistent launch (the host checks the state between)
 
 // Whether the persistent kernel's grid (CgOcc blocks per SM) can be resident at once.
-template <typename T, int G>
+template <typename T, int G, bool QMR = false>
 Status cg_setup() {
   static bool done = false;
   if (done) return Status{};
   int nb = 0;
-  PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_inner<T, G>, 256, 0));
+  PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_inner<T, G, QMR>, 256, 0));
   if (nb < CgOcc<T>::value) return Status{PETGEM_ERR_UNSUPPORTED, "COCG kernel: too few resident blocks per SM"};
   done = true;
   return Status{};
@@ -653,7 +746,7 @@ __global__ void k_cg_finish(const T* __restrict__ y, const double2* __restrict__
 struct BatchBuffers;
 
 struct CgBuffers {
-  DevBuf sq, a128, a64, r64, r, p, q, y, state, partials, sys;
+  DevBuf sq, a128, a64, r64, r, p, q, y, d, state, partials, sys;
   BatchBuffers* batch = nullptr;  // workspace of petgem_solve_batch (when this context leads one)
   // multi-source solve: interleaved right-hand sides, iterate and residual (c128), vectors (T),
   // per-source states, group flags and per-source scales / inner targets
@@ -672,7 +765,7 @@ Status read_cstate(petgem_ctx* c, CgBuffers* B, CState* h) {
   return Status{};
 }
 
-template <typename T>
+template <typename T, bool QMR>
 Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, const double2* b, double2* x,
                    petgem_solve_info& inf, int sms) {
   cudaStream_t s = c->stream;
@@ -682,17 +775,20 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
   const bool c128 = sizeof(T) == 16;
   const T* at = c128 ? (const T*)B->a128.ptr : (const T*)B->a64.ptr;
   T *r = B->r.as<T>(), *p = B->p.as<T>(), *q = B->q.as<T>(), *y = B->y.as<T>();
+  T* dq = QMR ? B->d.as<T>() : nullptr;
   const unsigned nb = blocks_for(n, kRows);
   // the persistent kernel's grid: CgOcc blocks per SM (all resident), fewer for a small system
   const int grid = (int)std::max<int64_t>(
       1, std::min<int64_t>(blocks_for(n * kCgG, 256), (int64_t)CgOcc<T>::value * sms));
-  PG_TRY((cg_setup<T, kCgG>()));
+  PG_TRY((cg_setup<T, kCgG, QMR>()));
   const double vb = (double)sizeof(T) * n;
   // per iteration: SpMV nnz (values + columns) + row pointers + p gathered once, p of the row and
-  // q written; update q, r read and r written; direction r, p, y read and p, y written
-  const double iter_bytes = (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 3.0 * vb + 3.0 * vb + 5.0 * vb;
-  CgSys<T> hsys{(const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), at, p, q, r, y, n,
-                st, part, 0, 0, grid};
+  // q written; update q, r read and r written; direction r, p, y read and p, y written (SQMR: and
+  // d read and written)
+  const double iter_bytes =
+      (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 3.0 * vb + 3.0 * vb + (QMR ? 7.0 : 5.0) * vb;
+  CgSys<T> hsys{(const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), at, p, q, r, y, dq,
+                n, st, part, 0, 0, grid};
   PG_TRY(B->sys.reserve(sizeof(CgSys<T>)));
   const CgSys<T>* dsys = B->sys.as<CgSys<T>>();
   CState hs;
@@ -749,7 +845,7 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
     const double rnorm = sqrt(rn2);
     const double need = 0.3 * o.tol * bnorm / rnorm;
     const double inner = c128 ? need : std::min(std::max(o.inner_tol, need), 0.5);
-    k_cg_start<T><<<nb, kT, 0, s>>>(B->r64.as<double2>(), B->sq.as<double2>(), r, p, y, n, st, part, inner,
+    k_cg_start<T><<<nb, kT, 0, s>>>(B->r64.as<double2>(), B->sq.as<double2>(), r, p, y, dq, n, st, part, inner,
                                     1.0 / rnorm);
     c->launches++;
     PG_CUDA(cudaGetLastError());
@@ -761,8 +857,9 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
       const int steps = (int)std::min<int64_t>(kCgChunk, o.max_iters - iters - hs.k);
       if (steps <= 0) break;
       {
-        KernelTimer kt(c, c128 ? "cg_inner_c128" : "cg_inner_c64", 0.0);
-        PG_CUDA(pdl_launch(k_cg_inner<T, kCgG>, dim3(grid), dim3(256), 0, s, true, dsys, 1, steps));
+        KernelTimer kt(c, QMR ? (c128 ? "qmr_inner_c128" : "qmr_inner_c64") : (c128 ? "cg_inner_c128" : "cg_inner_c64"),
+                       0.0);
+        PG_CUDA(pdl_launch(k_cg_inner<T, kCgG, QMR>, dim3(grid), dim3(256), 0, s, true, dsys, 1, steps));
       }
       c->launches++;
       const int k0 = hs.k;
@@ -1578,7 +1675,7 @@ struct BatchBuffers {
 template <int G, typename T>
 Status batch_inner_launch(cudaStream_t s, const CgSys<T>* dsys, int na, int grid, int steps) {
   PG_TRY((cg_setup<T, G>()));
-  PG_CUDA(pdl_launch(k_cg_inner<T, G>, dim3(grid), dim3(256), 0, s, true, dsys, na, steps));
+  PG_CUDA(pdl_launch(k_cg_inner<T, G, false>, dim3(grid), dim3(256), 0, s, true, dsys, na, steps));
   return Status{};
 }
 
@@ -1661,7 +1758,7 @@ Status solve_batch(petgem_ctx* const* ctxs, int n_ctx, const petgem_solve_opts& 
     v0 += vnb[k];
     r0 += rnb[k];
     const T* at = c128 ? (const T*)Bc->a128.ptr : (const T*)Bc->a64.ptr;
-    tab[k] = CgSys<T>{c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), at, p, q, r, y, n, dst + k, part, 0, 0, 0};
+    tab[k] = CgSys<T>{c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), at, p, q, r, y, nullptr, n, dst + k, part, 0, 0, 0};
   }
   // solution pointers: context k's sources in order
   {
@@ -1843,12 +1940,14 @@ Status run_solve_cocg(petgem_ctx* c, const petgem_solve_opts& o, double2* x, pet
   PG_TRY(cg_prepare(c));
   const size_t tb = c128 ? sizeof(double2) : sizeof(float2);
   PG_TRY(B->r64.reserve(n * sizeof(double2)));
+  const bool qmr = o.method == PETGEM_METHOD_SQMR;
   for (DevBuf* d : {&B->r, &B->p, &B->q, &B->y}) PG_TRY(d->reserve(n * tb));
+  if (qmr) PG_TRY(B->d.reserve(n * tb));
   PG_TRY(B->state.reserve(sizeof(CState)));
   PG_TRY(B->partials.reserve((size_t)std::max<int64_t>(blocks_for(n, kRows), 8LL * sms) * kPStride * sizeof(double2)));
   PG_CUDA(cudaMemsetAsync(B->state.ptr, 0, sizeof(CState), s));
   Status worst;
-  if (o.batch != 1 && c->n_src > 1) {  // sources of one frequency together, up to 32 per group
+  if (!qmr && o.batch != 1 && c->n_src > 1) {  // sources of one frequency together, up to 32 per group
     const int group = o.batch <= 0 ? 32 : std::min(o.batch, 32);
     for (int s0 = 0; s0 < c->n_src; s0 += group) {
       const int S_g = std::min(group, c->n_src - s0);
@@ -1869,12 +1968,15 @@ Status run_solve_cocg(petgem_ctx* c, const petgem_solve_opts& o, double2* x, pet
     inf = petgem_solve_info{};
     const double2* b = c->b.as<double2>() + (int64_t)src * n;
     double2* xs = x + (int64_t)src * n;
+    Status r;
     if (c128)
-      PG_TRY(cocg_source<double2>(c, o, B, b, xs, inf, sms));
+      r = qmr ? cocg_source<double2, true>(c, o, B, b, xs, inf, sms) : cocg_source<double2, false>(c, o, B, b, xs, inf, sms);
     else
-      PG_TRY(cocg_source<float2>(c, o, B, b, xs, inf, sms));
+      r = qmr ? cocg_source<float2, true>(c, o, B, b, xs, inf, sms) : cocg_source<float2, false>(c, o, B, b, xs, inf, sms);
+    PG_TRY(r);
     if (inf.status != PETGEM_OK && worst.ok())
-      worst = Status{inf.status, "source " + std::to_string(src) + " did not converge (COCG)"};
+      worst = Status{inf.status, "source " + std::to_string(src) + (qmr ? " did not converge (SQMR)"
+                                                                         : " did not converge (COCG)")};
   }
   PG_CUDA(cudaStreamSynchronize(s));
   return worst;
@@ -1919,7 +2021,7 @@ void destroy_cocg(petgem_ctx* c) {
     if (B->batch->cap) cudaStreamDestroy(B->batch->cap);
     delete B->batch;
   }
-  for (DevBuf* d : {&B->sq, &B->a128, &B->a64, &B->r64, &B->r, &B->p, &B->q, &B->y, &B->state, &B->partials, &B->sys, &B->Bt,
+  for (DevBuf* d : {&B->sq, &B->a128, &B->a64, &B->r64, &B->r, &B->p, &B->q, &B->y, &B->d, &B->state, &B->partials, &B->sys, &B->Bt,
                     &B->X, &B->R, &B->rb, &B->pb, &B->qb, &B->yb, &B->bstates, &B->bgrp, &B->bscal})
     d->release();
   delete B;

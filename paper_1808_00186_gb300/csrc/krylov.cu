@@ -514,7 +514,7 @@ Status run_spmv(petgem_ctx* c, const double2* x, double2* y) {
 Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info) {
   const int m = o.restart;
   if (m < 1 || m > kMaxRestart) return Status{PETGEM_ERR_UNSUPPORTED, "restart must be in [1, 62]"};
-  if (o.method == PETGEM_METHOD_COCG) return run_solve_cocg(c, o, x, info);
+  if (o.method == PETGEM_METHOD_COCG || o.method == PETGEM_METHOD_SQMR) return run_solve_cocg(c, o, x, info);
   const bool block = o.batch != 1 && c->n_src > 1 && o.precond != PETGEM_PRECOND_LEARNED;
   PG_TRY(prepare(c, m, o.precision, !block));
   if (block) return run_solve_block(c, o, x, info);
