@@ -714,6 +714,7 @@ __global__ void __launch_bounds__(256, CgOcc<T>::value)
 }
 
 constexpr int kCgChunk = 1024;  // iterations per persistent launch (the host checks the state between)
+constexpr int64_t kCgInnerMax = 4096;  // iterations of one complex64 inner solve at most
 
 // Whether the persistent kernel's grid (CgOcc blocks per SM) can be resident at once.
 template <typename T, int G, bool QMR = false>
@@ -850,11 +851,14 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
     c->launches++;
     PG_CUDA(cudaGetLastError());
     hs.k = 0;
-    hsys.kmax = o.max_iters - iters;  // this inner solve's iteration budget
+    // this inner solve's iteration budget: what is left, and in complex64 at most kCgInnerMax (the
+    // recursively updated residual drifts from the true one in FP32 over long solves; a fresh FP64
+    // residual bounds the drift)
+    hsys.kmax = std::min<int64_t>(o.max_iters - iters, c128 ? INT64_MAX : kCgInnerMax);
     PG_CUDA(cudaMemcpyAsync(B->sys.ptr, &hsys, sizeof(hsys), cudaMemcpyHostToDevice, s));
     // the iterations of this inner solve: persistent launches of up to kCgChunk iterations each
     while (true) {
-      const int steps = (int)std::min<int64_t>(kCgChunk, o.max_iters - iters - hs.k);
+      const int steps = (int)std::min<int64_t>(kCgChunk, hsys.kmax - hs.k);
       if (steps <= 0) break;
       {
         KernelTimer kt(c, QMR ? (c128 ? "qmr_inner_c128" : "qmr_inner_c64") : (c128 ? "cg_inner_c128" : "cg_inner_c64"),
@@ -1846,7 +1850,7 @@ Status solve_batch(petgem_ctx* const* ctxs, int n_ctx, const petgem_solve_opts& 
         CgSys<T> e = tab[k];
         e.b0 = b;
         e.nb = nb[k];
-        e.kmax = o.max_iters - hctl[k].iters;
+        e.kmax = std::min<int64_t>(o.max_iters - hctl[k].iters, c128 ? INT64_MAX : kCgInnerMax);
         b += nb[k];
         at.push_back(e);
       }
@@ -1866,7 +1870,8 @@ Status solve_batch(petgem_ctx* const* ctxs, int n_ctx, const petgem_solve_opts& 
     };
     auto running = [&]() {
       for (int k : act)
-        if (hst[k].done == 0 && hst[k].k < o.max_iters - hctl[k].iters) return true;
+        if (hst[k].done == 0 && hst[k].k < std::min<int64_t>(o.max_iters - hctl[k].iters, c128 ? INT64_MAX : kCgInnerMax))
+          return true;
       return false;
     };
     PG_TRY(plan());

@@ -82,8 +82,18 @@ def kuhn_mesh(n, lo, hi, jitter: float = 0.0, seed: int = 12345, warp=None) -> M
     """
     if isinstance(n, int):
         n = (n, n, n)
-    nx, ny, nz = n
     xs = [np.linspace(lo[a], hi[a], n[a] + 1) for a in range(3)]
+    return kuhn_mesh_axes(xs, jitter=jitter, seed=seed, warp=warp)
+
+
+def kuhn_mesh_axes(xs, jitter: float = 0.0, seed: int = 12345, warp=None) -> Mesh:
+    """The Kuhn split of the tensor-product grid with node coordinates xs[0], xs[1], xs[2]
+    (strictly increasing; spacings may vary), numbered as in kuhn_mesh.  jitter is relative to
+    the mean spacing of each axis."""
+    n = tuple(len(x) - 1 for x in xs)
+    nx, ny, nz = n
+    lo = tuple(float(x[0]) for x in xs)
+    hi = tuple(float(x[-1]) for x in xs)
     kk, jj, ii = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
     ii, jj, kk = ii.ravel(), jj.ravel(), kk.ravel()
     nodes = np.stack([xs[0][ii], xs[1][jj], xs[2][kk]], axis=1).astype(np.float64)
@@ -226,6 +236,117 @@ def bathymetry_model(n: int = 96, n_src: int = 32, freq: float = 0.5) -> Model:
     rxx = np.linspace(-4000.0, 4000.0, 101)
     rx = np.stack([rxx, np.zeros(101), seafloor(rxx) + 1.0], axis=1)
     return Model("bathymetry_n%d" % n, mesh, sigma, 3.3, freq, srcs, rx)
+
+
+MU0 = 4.0e-7 * math.pi
+
+
+def skin_depth(freq: float, sigma: float) -> float:
+    """Skin depth sqrt(2 / (mu0 w sigma)) in m (Section 5.3): the depth at which a plane wave in a
+    whole space of conductivity sigma has decayed to 1/e."""
+    return math.sqrt(2.0 / (MU0 * 2.0 * math.pi * freq * sigma))
+
+
+def graded_axis(center: float, core_lo: float, core_hi: float, d_s: float, d_delta: float,
+                t_lo: float, t_hi: float, s_c: float = 1.04, s_b: float = 1.1) -> np.ndarray:
+    """Node coordinates of one axis by the spacing rules of Section 5.3.
+
+    Core [core_lo, core_hi], walked from `center` outward on both sides: the i-th step (i = 1,
+    2, ...) is min(s_c^i d_s, d_delta), the power-law stretching of the core.  Boundary layers of
+    thickness t_lo below core_lo and t_hi above core_hi: each step is s_b times the one before (the
+    boundary stretching), starting from the last core step.  A walk ends exactly on its bound: a
+    final step shorter than half the step before it is merged into that step.
+    """
+    def walk(start, end, first_steps):
+        sign = 1.0 if end > start else -1.0
+        length = abs(end - start)
+        pos, out, i = 0.0, [], 0
+        while pos < length:
+            step = first_steps(i)
+            i += 1
+            if pos + step >= length or length - (pos + step) < 0.5 * step:
+                out.append(length)
+                break
+            pos += step
+            out.append(pos)
+        return [start + sign * v for v in out]
+
+    def layer(start, last_step, thickness, sign):
+        if thickness <= 0.0:
+            return []
+        pos, step, out = 0.0, last_step, []
+        while pos < thickness:
+            step *= s_b
+            if pos + step >= thickness or thickness - (pos + step) < 0.5 * step:
+                out.append(thickness)
+                break
+            pos += step
+            out.append(pos)
+        return [start + sign * v for v in out]
+
+    core_step = lambda i: min(s_c ** (i + 1) * d_s, d_delta)
+    hi_side = walk(center, core_hi, core_step) if core_hi > center else []
+    lo_side = walk(center, core_lo, core_step) if core_lo < center else []
+    pts = lo_side[::-1] + [center] + hi_side
+    last_lo = pts[1] - pts[0] if len(pts) > 1 else d_s
+    last_hi = pts[-1] - pts[-2] if len(pts) > 1 else d_s
+    pts = layer(core_lo, last_lo, t_lo, -1.0)[::-1] + pts + layer(core_hi, last_hi, t_hi, 1.0)
+    return np.array(pts, dtype=np.float64)
+
+
+def snap_interfaces(axis: np.ndarray, interfaces) -> np.ndarray:
+    """Move the interior node nearest to each interface coordinate onto it, so that material
+    interfaces are node planes (conforming), as long as both neighbouring spacings stay above
+    half their original size."""
+    a = axis.copy()
+    for v in interfaces:
+        if not (a[0] < v < a[-1]):
+            continue
+        i = int(np.argmin(np.abs(a - v)))
+        if i == 0 or i == len(a) - 1:
+            continue
+        left, right = a[i] - a[i - 1], a[i + 1] - a[i]
+        if v - a[i - 1] >= 0.5 * left and a[i + 1] - v >= 0.5 * right:
+            a[i] = v
+    return a
+
+
+def graded_marine_model(freq: float = 1.0, L_s: float = 250.0, r_delta: float = 3.0, r_s: float = 13.0,
+                        r_xy: float = 8.0, r_z: float = 4.0, r_b: float = 4.0, sigma_min_depth: float = 3.3,
+                        sigma_ave: float = 1.0, n_src: int = 1) -> Model:
+    """The marine model of marine_model on a frequency-adapted graded Kuhn mesh (Section 5.3).
+
+    Spacings: d_delta = delta_min / r_delta with delta_min the skin depth in seawater; near the
+    source d_s = min(L_s / r_s, d_delta) (L_s the dipole length).  Extent: the core spans
+    x_s +- r_xy delta_ave, y_s +- r_xy delta_ave and, vertically, from r_z delta_ave below the
+    source up to the sea surface (the air-water interface closes the domain at the top); boundary
+    layers of r_b delta_ave on every other side.  delta_ave is the skin depth at sigma_ave (the
+    sediment).  The core is centred on the (first) source.  Conductivities, sources and receivers
+    as in marine_model (seawater 3.3 S/m above z = 0 up to the surface at z = 1000 m, sediment
+    1 S/m, the 0.01 S/m reservoir slab 1 km down)."""
+    d_min = skin_depth(freq, sigma_min_depth)
+    d_ave = skin_depth(freq, sigma_ave)
+    d_delta = d_min / r_delta
+    d_s = min(L_s / r_s, d_delta)
+    xs_src = [0.0] if n_src == 1 else list(np.linspace(-4000.0, 4000.0, n_src))
+    src = (xs_src[0], 0.0, 50.0)
+    z_surface = 1000.0
+    tb = r_b * d_ave
+    ax = graded_axis(src[0], src[0] - r_xy * d_ave, src[0] + r_xy * d_ave, d_s, d_delta, tb, tb)
+    ay = graded_axis(src[1], src[1] - r_xy * d_ave, src[1] + r_xy * d_ave, d_s, d_delta, tb, tb)
+    az = graded_axis(src[2], src[2] - r_z * d_ave, z_surface, d_s, d_delta, tb, 0.0)
+    # the seafloor and the reservoir's faces as node planes
+    ax = snap_interfaces(ax, (-1000.0, 1000.0))
+    ay = snap_interfaces(ay, (-1000.0, 1000.0))
+    az = snap_interfaces(az, (0.0, -1000.0, -1100.0))
+    mesh = kuhn_mesh_axes([ax, ay, az])
+    cen = mesh.centroids()
+    sigma = np.where(cen[:, 2] > 0.0, 3.3, 1.0)
+    _boxes(cen, sigma, [((-1000, 1000, -1000, 1000, -1100, -1000), 0.01)])
+    rx = np.stack([np.linspace(-4000.0, 4000.0, 101), np.zeros(101), np.zeros(101)], axis=1)
+    return Model("graded_marine_%gHz" % freq, mesh, sigma, 3.3, freq,
+                 [Dipole(x, 0.0, 50.0, 0, 1.0) for x in xs_src], rx,
+                 extra={"d_delta": d_delta, "d_s": d_s, "delta_ave": d_ave, "delta_min": d_min})
 
 
 def kuhn_counts(n: int) -> dict:
