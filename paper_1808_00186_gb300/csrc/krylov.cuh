@@ -161,32 +161,51 @@ __device__ inline double2 shfl_d2(double2 v, int src) {
 
 // New Hessenberg column j from the projections h[0..j] (summed over passes; global or shared
 // memory) and beta = ||V_{j+1}||: the earlier rotations in order, a new complex Givens rotation,
-// the residual estimate and the stopping test.  Called by all 32 lanes of one warp: lane l loads
-// rotation l and l + 32 and entries l and l + 32 of the column at once, so the sequential chain of
-// rotations runs on registers and shuffles instead of a chain of memory round trips.
+// the residual estimate and the stopping test.  Called by all 32 lanes of one warp.
+//
+// Rotation i maps the pair (carry_i, h_{i+1}) to (top_i, carry_{i+1}) with
+//   top_i = c_i carry_i + s_i h_{i+1},   carry_{i+1} = c_i h_{i+1} - conj(s_i) carry_i,
+// starting from carry_0 = h_0.  The carries follow a first-order linear recurrence, i.e. the
+// composition of the affine maps A_i(x) = -conj(s_i) x + c_i h_{i+1}; composition is associative,
+// so lane l composes its two maps (i = 2l, 2l + 1) and a warp scan over the lanes forms every
+// prefix in log2(32) steps instead of a chain of j dependent steps (each ~60-cycle FP64
+// operations on this part).  The tops then follow elementwise.
 __device__ __forceinline__ void finish_column_warp(GState* st, int j, const double2* h, double beta2) {
   const int l = threadIdx.x & 31;
   const double beta = sqrt(beta2);
-  const double2 z = make_double2(0.0, 0.0);
-  const double c_lo = l < j ? st->cs_c[l] : 0.0, c_hi = l + 32 < j ? st->cs_c[l + 32] : 0.0;
-  const double2 s_lo = l < j ? st->cs_s[l] : z, s_hi = l + 32 < j ? st->cs_s[l + 32] : z;
-  const double2 h_lo = l <= j ? h[l] : z, h_hi = l + 32 <= j ? h[l + 32] : z;
-  double2 out_lo = h_lo, out_hi = h_hi;  // rotated entries of the column
-  double2 carry = shfl_d2(h_lo, 0);      // entry i after rotations 0..i-1
-  for (int i = 0; i < j; ++i) {
-    const bool hi = i >= 32, hi1 = i + 1 >= 32;
-    const double c = shfl_d(hi ? c_hi : c_lo, i & 31);
-    const double2 s = shfl_d2(hi ? s_hi : s_lo, i & 31);
-    const double2 b = shfl_d2(hi1 ? h_hi : h_lo, (i + 1) & 31);
-    const double2 top = cadd(cscale(carry, c), cmul(s, b));
-    carry = csub(cscale(b, c), cconjmul(s, carry));  // -conj(s) a + c b
-    if (l == (i & 31)) {
-      if (hi)
-        out_hi = top;
-      else
-        out_lo = top;
+  const double2 z = make_double2(0.0, 0.0), one = make_double2(1.0, 0.0);
+  const int e0 = 2 * l, e1 = 2 * l + 1;
+  const double c0 = e0 < j ? st->cs_c[e0] : 1.0, c1 = e1 < j ? st->cs_c[e1] : 1.0;
+  const double2 s0 = e0 < j ? st->cs_s[e0] : z, s1 = e1 < j ? st->cs_s[e1] : z;
+  const double2 h0 = e0 <= j ? h[e0] : z, h1 = e1 <= j ? h[e1] : z, h2 = e1 + 1 <= j ? h[e1 + 1] : z;
+  // A_e(x) = a_e x + b_e (identity past the last rotation)
+  const double2 a0 = e0 < j ? make_double2(-s0.x, s0.y) : one, b0 = e0 < j ? cscale(h1, c0) : z;
+  const double2 a1 = e1 < j ? make_double2(-s1.x, s1.y) : one, b1 = e1 < j ? cscale(h2, c1) : z;
+  // this lane's pair A_1 o A_0, then the inclusive scan over lanes (earlier maps apply first)
+  double2 A = cmul(a1, a0), B = cadd(cmul(a1, b0), b1);
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const double2 Ap = make_double2(__shfl_up_sync(0xffffffffu, A.x, d), __shfl_up_sync(0xffffffffu, A.y, d));
+    const double2 Bp = make_double2(__shfl_up_sync(0xffffffffu, B.x, d), __shfl_up_sync(0xffffffffu, B.y, d));
+    if (l >= d) {
+      B = cadd(cmul(A, Bp), B);
+      A = cmul(A, Ap);
     }
   }
+  // exclusive prefix (the maps of the lanes before) applied to carry_0 = h_0
+  double2 Ae = make_double2(__shfl_up_sync(0xffffffffu, A.x, 1), __shfl_up_sync(0xffffffffu, A.y, 1));
+  double2 Be = make_double2(__shfl_up_sync(0xffffffffu, B.x, 1), __shfl_up_sync(0xffffffffu, B.y, 1));
+  if (l == 0) {
+    Ae = one;
+    Be = z;
+  }
+  const double2 hz = shfl_d2(h0, 0);
+  const double2 k0 = cadd(cmul(Ae, hz), Be);  // carry_{2l}
+  const double2 k1 = cadd(cmul(a0, k0), b0);  // carry_{2l+1}
+  double2 out_lo = e0 < j ? cadd(cscale(k0, c0), cmul(s0, h1)) : h0;  // rotated entries 2l, 2l+1
+  double2 out_hi = e1 < j ? cadd(cscale(k1, c1), cmul(s1, h2)) : h1;
+  const double2 kj = (j & 1) ? k1 : k0;
+  const double2 carry = shfl_d2(kj, (j >> 1) & 31);  // carry_j: entry j after rotations 0..j-1
   // new rotation on (carry, beta)
   const double aa = sqrt(cabs2(carry));
   const double rho = sqrt(aa * aa + beta * beta);
@@ -200,15 +219,11 @@ __device__ __forceinline__ void finish_column_warp(GState* st, int j, const doub
     s = cscale(carry, beta / (aa * rho));
   }
   const double2 hj = cadd(cscale(carry, c), cscale(s, beta));
-  if (l == (j & 31)) {
-    if (j >= 32)
-      out_hi = hj;
-    else
-      out_lo = hj;
-  }
+  if (e0 == j) out_lo = hj;
+  if (e1 == j) out_hi = hj;
   double2* Hc = &st->H[j * (kMaxM + 1)];
-  if (l <= j) Hc[l] = out_lo;
-  if (l + 32 <= j) Hc[l + 32] = out_hi;
+  if (e0 <= j) Hc[e0] = out_lo;
+  if (e1 <= j) Hc[e1] = out_hi;
   if (l == 0) {
     Hc[j + 1] = z;
     st->inv_beta[j + 1] = beta > 0.0 ? 1.0 / beta : 0.0;
