@@ -199,7 +199,8 @@ __global__ void __launch_bounds__(256) k_bcycle_init(const double2* __restrict__
 }
 
 // One warp per source: y = H^{-1} g for that source's cycle.
-__global__ void k_bbacksolve(GState* sts) { backsolve_warp(&sts[threadIdx.x >> 5], threadIdx.x & 31); }
+// One block of 32 threads per source (each source's back substitution is one warp's work).
+__global__ void __launch_bounds__(32) k_bbacksolve(GState* sts) { backsolve_warp(&sts[blockIdx.x], threadIdx.x); }
 
 // U += sum_k V_k y_k per source (complex64 basis: correction in FP32, added in FP64).
 template <typename T, int P>
@@ -326,7 +327,7 @@ Status run_group(petgem_ctx* c, const petgem_solve_opts& o, const double2* b, do
       c->launches += 3;
     }
     PG_CUDA(cudaGetLastError());
-    k_bbacksolve<<<1, 32 * P, 0, s>>>(sts);
+    k_bbacksolve<<<P, 32, 0, s>>>(sts);
     k_bxupdate<T, P><<<blocks_for(n * P, 256), 256, 0, s>>>(V, ldb, n, S->Ub.as<double2>(), sts, std::max(mj, 1));
     c->launches += 2;
     PG_CUDA(cudaGetLastError());

@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kT) k_cycle_init(const double2* __restrict__ r
 
 // y = H(0:k, 0:k)^{-1} g(0:k), scaled by 1/||V_i|| for the unnormalised basis.  One warp:
 // column-oriented back substitution (lane l keeps the running right-hand side of rows l, l+32).
-__global__ void k_backsolve(GState* st) { backsolve_warp(st, threadIdx.x); }
+__global__ void __launch_bounds__(32) k_backsolve(GState* st) { backsolve_warp(st, threadIdx.x); }
 
 // u += sum_k V_k y_k.  complex128: in FP64.  complex64: the correction sum_k V_k y_k is formed in
 // FP32 (it is the inner solve's correction, accurate to complex64 anyway) and added to u in FP64.

@@ -248,16 +248,25 @@ __device__ __forceinline__ void finish_column_warp(GState* st, int j, const doub
 // column-oriented back substitution (lane l keeps the running right-hand side of rows l, l+32).
 __device__ inline void backsolve_warp(GState* st, int lane) {
   const int kk = st->k;
-  double2 rhs0 = lane < kk ? st->g[lane] : make_double2(0.0, 0.0);
-  double2 rhs1 = lane + 32 < kk ? st->g[lane + 32] : make_double2(0.0, 0.0);
+  const double2 z = make_double2(0.0, 0.0), one = make_double2(1.0, 0.0);
+  double2 rhs0 = lane < kk ? st->g[lane] : z;
+  double2 rhs1 = lane + 32 < kk ? st->g[lane + 32] : z;
+  // the diagonal's reciprocals, every lane two at once (a complex division is a long FP64 chain)
+  const double2 inv0 = lane < kk ? cdiv(one, st->H[lane * (kMaxM + 1) + lane]) : z;
+  const double2 inv1 = lane + 32 < kk ? cdiv(one, st->H[(lane + 32) * (kMaxM + 1) + lane + 32]) : z;
+  // column i's entries above the diagonal, loaded one column ahead of their use
+  auto col = [&](int i, int r) { return (i >= 0 && r < i) ? st->H[i * (kMaxM + 1) + r] : z; };
+  double2 c0 = col(kk - 1, lane), c1 = col(kk - 1, lane + 32);
   for (int i = kk - 1; i >= 0; --i) {
-    double2 ri = i < 32 ? rhs0 : rhs1;
-    double2 yi = make_double2(__shfl_sync(0xffffffffu, ri.x, i & 31), __shfl_sync(0xffffffffu, ri.y, i & 31));
-    yi = cdiv(yi, st->H[i * (kMaxM + 1) + i]);
+    const double2 n0 = col(i - 1, lane), n1 = col(i - 1, lane + 32);
+    const double2 ri = i < 32 ? rhs0 : rhs1;
+    const double2 inv = i < 32 ? inv0 : inv1;
+    const double2 yi = cmul(shfl_d2(ri, i & 31), shfl_d2(inv, i & 31));
     if (lane == 0) st->y[i] = cscale(yi, st->inv_beta[i]);
-    const double2* Hc = &st->H[i * (kMaxM + 1)];
-    if (lane < i) rhs0 = csub(rhs0, cmul(Hc[lane], yi));
-    if (lane + 32 < i) rhs1 = csub(rhs1, cmul(Hc[lane + 32], yi));
+    if (lane < i) rhs0 = csub(rhs0, cmul(c0, yi));
+    if (lane + 32 < i) rhs1 = csub(rhs1, cmul(c1, yi));
+    c0 = n0;
+    c1 = n1;
   }
 }
 
