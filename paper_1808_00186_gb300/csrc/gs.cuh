@@ -207,20 +207,25 @@ __global__ void __launch_bounds__(kDotThreads, kDotBlocksPerSM)
   }
   // grid barrier: every block arrives once per launch, so the counter is a multiple of the grid
   // size when the launch starts and this launch's arrivals are the next gridDim.x tickets.
+  // Arrival is a release add and the wait acquire loads; the block barriers on either side carry
+  // the ordering to the block's other threads.
   __syncthreads();
   if (tid == 0) {
-    __threadfence();
     const unsigned long long G = gridDim.x;
-    const unsigned long long ticket = atomicAdd(gbar, 1ull);
+    unsigned long long ticket;
+    asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(ticket) : "l"(gbar) : "memory");
     const unsigned long long target = (ticket / G + 1) * G;
     bool okb = true;
     const unsigned long long w0 = gs_time();
-    while (*(volatile unsigned long long*)gbar < target)
+    while (true) {
+      unsigned long long v;
+      asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(gbar) : "memory");
+      if (v >= target) break;
       if (gs_time() - w0 > kGsWaitNs) {
         okb = false;
         break;
       }
-    __threadfence();
+    }
     if (!okb) gs_fail<P>(sts, stop);
     bar_ok = okb;
   }
