@@ -139,7 +139,8 @@ int petgem_destroy(petgem_ctx* c) {
   c->slots.release();
   for (petgem::DevBuf* b : {&c->nodes, &c->tets, &c->edges, &c->tet_edges, &c->signs, &c->boundary, &c->occ, &c->eptr,
                             &c->row_ptr, &c->col, &c->gptr, &c->pkey, &c->pij, &c->flags, &c->sigma, &c->K21, &c->M21,
-                            &c->vol, &c->val, &c->diag, &c->b, &c->kval, &c->mval})
+                            &c->vol, &c->val, &c->diag, &c->b, &c->kval, &c->mval, &c->sell_perm, &c->sell_inv,
+                            &c->sell_sp, &c->sell_col, &c->sell_src})
     b->release();
   for (auto& p : c->pending) {
     cudaEventDestroy(p.start);
@@ -191,6 +192,7 @@ int petgem_mesh_edges(petgem_ctx* c, int64_t n_nodes, const double* nodes, int64
                                 c->stream) != cudaSuccess)
     s = Status{PETGEM_ERR_CUDA, "copy of tets failed"};
   if (s.ok()) s = petgem::build_topology(c);
+  c->mesh_version++;
   if (!s.ok()) {
     c->n_edges = 0;
     cudaGetLastError();

@@ -174,12 +174,14 @@ __global__ void __launch_bounds__(kT) k_cg_norm(const double2* __restrict__ v, i
 // Inner-solve start: r = p = scale S r64 (rounded to T), y = 0, rho = r^T r, ||r||^2, threshold.
 // scale = 1 / ||r64|| keeps the complex64 vectors of O(1) size: after a few refinements the
 // residual's entries are ~1e-20 and their squares would underflow in FP32.
-// SQMR (dvec != null): also d = 0, tau = ||r||, theta = 0.
+// SQMR (dvec != null): also d = 0, tau = ||r||, theta = 0.  perm != null: the iteration vectors
+// are in the SELL layout's renumbering (entry i is edge perm[i]).
 template <typename T>
 __global__ void __launch_bounds__(kT) k_cg_start(const double2* __restrict__ r64, const double2* __restrict__ sq,
-                                                 T* __restrict__ r, T* __restrict__ p, T* __restrict__ y,
-                                                 T* __restrict__ dvec, int64_t n, CState* __restrict__ st,
-                                                 double2* __restrict__ partials, double inner, double scale) {
+                                                 const int32_t* __restrict__ perm, T* __restrict__ r,
+                                                 T* __restrict__ p, T* __restrict__ y, T* __restrict__ dvec, int64_t n,
+                                                 CState* __restrict__ st, double2* __restrict__ partials, double inner,
+                                                 double scale) {
   using A = typename Acc<T>::type;
   A rho = zero<T>(), nr = zero<T>();
   const int64_t base = blockIdx.x * (int64_t)kRows + threadIdx.x;
@@ -187,7 +189,8 @@ __global__ void __launch_bounds__(kT) k_cg_start(const double2* __restrict__ r64
   for (int q = 0; q < kR; ++q) {
     const int64_t i = base + (int64_t)q * kT;
     if (i < n) {
-      const T t = from_d2<T>(cscale(cmul(sq[i], r64[i]), scale));
+      const int64_t o = perm ? perm[i] : i;  // renumbered vectors (SELL layout) gather the original entry
+      const T t = from_d2<T>(cscale(cmul(sq[o], r64[o]), scale));
       r[i] = t;
       p[i] = t;
       y[i] = zero<T>();
@@ -237,6 +240,10 @@ struct CgSys {
   const T* val;
   T *p, *q, *r, *y;
   T* d;           // SQMR: the smoothing direction (unused by COCG)
+  const int64_t* sp;    // SELL-32 layout of the operator (rows and vectors renumbered; null: CSR)
+  const int32_t* scol;
+  const T* sval;
+  int64_t ns;           // slices
   int64_t n;
   CState* st;
   double2* part;  // [nb][kCgSlots]: slot 0 r^T r, 1 ||r||^2, 2 p^T q
@@ -515,6 +522,83 @@ __device__ inline typename Acc<T>::type cg_spmv_rows(const int64_t* __restrict__
   return dot;
 }
 
+// q = Atil p over the SELL-32 slices w0, w0 + nwarps, ... of the renumbered operator (one warp per
+// slice, lane = row), five entries of a slice at a time with the next five's columns and values in
+// flight during this chunk's gathers; returns this thread's share of the bilinear p^T q.  As in
+// cg_spmv_rows, p's gathers are plain loads (other blocks wrote p since the last barrier).
+// (Contiguous slice ranges of equal stored entries per warp measured far slower than this
+// interleaving: one block took 2.6x the others.)
+template <typename T>
+__device__ inline typename Acc<T>::type cg_sell_rows(const int64_t* __restrict__ sp, const int32_t* __restrict__ scol,
+                                                     const T* __restrict__ sval, const T* p, T* q, int64_t n,
+                                                     int64_t ns, int64_t w0, int64_t nwarps) {
+  constexpr int U = 5;
+  using A = typename Acc<T>::type;
+  const int lane = threadIdx.x & 31;
+  A dot = zero<T>();
+  int64_t s = w0, b = 0, w = 0, t = 0;
+  if (s < ns) {
+    b = __ldg(&sp[s]);
+    w = (__ldg(&sp[s + 1]) - b) >> 5;
+  }
+  int32_t c[U];
+  T a[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const bool ok = u < w;
+    c[u] = ok ? __ldg(&scol[b + u * 32 + lane]) : 0;
+    a[u] = ok ? __ldg(&sval[b + u * 32 + lane]) : zero<T>();
+  }
+  A acc = zero<T>(), acc2 = zero<T>();
+  while (s < ns) {
+    T xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = t + u < w ? p[c[u]] : zero<T>();
+    int64_t s2 = s, b2 = b, w2 = w, t2 = t + U;
+    if (t2 >= w) {  // the next chunk is the next slice's first
+      s2 = s + nwarps;
+      t2 = 0;
+      w2 = 0;
+      if (s2 < ns) {
+        b2 = __ldg(&sp[s2]);
+        w2 = (__ldg(&sp[s2 + 1]) - b2) >> 5;
+      }
+    }
+    int32_t c2[U];
+    T a2[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool ok = t2 + u < w2;
+      c2[u] = ok ? __ldg(&scol[b2 + (t2 + u) * 32 + lane]) : 0;
+      a2[u] = ok ? __ldg(&sval[b2 + (t2 + u) * 32 + lane]) : zero<T>();
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) fma_c((u & 1) ? acc2 : acc, a[u], xv[u]);
+    if (t2 == 0) {  // this slice is complete
+      const int64_t r = s * 32 + lane;
+      if (r < n) {
+        acc.x += acc2.x;
+        acc.y += acc2.y;
+        const T qv = from_d2<T>(to_d2(acc));
+        q[r] = qv;
+        bil_fma(dot, p[r], qv);
+      }
+      acc = zero<T>();
+      acc2 = zero<T>();
+    }
+    s = s2;
+    b = b2;
+    w = w2;
+    t = t2;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c[u] = c2[u];
+      a[u] = a2[u];
+    }
+  }
+  return dot;
+}
+
 // The iterations of an inner COCG solve, persistent: one launch runs up to max_steps iterations
 // of every system in sys[0, nsys), each on its own blocks [b0, b0 + nb), and stops a system when
 // its residual met the inner threshold or its bilinear form broke down.  Per iteration and system
@@ -526,7 +610,7 @@ __device__ inline typename Acc<T>::type cg_spmv_rows(const int64_t* __restrict__
 // The scalars are formed once per barrier, by the block that arrives last, and the state always
 // holds the current rho, k and ||r||^2.  The grid must be resident at once (cooperative launch).
 // A barrier that gives up sets done = 3.
-template <typename T, int G, bool QMR>
+template <typename T, int G, bool QMR, bool SELL = false>
 __global__ void __launch_bounds__(256, CgOcc<T>::value)
     k_cg_inner(const CgSys<T>* __restrict__ sys, int nsys, int max_steps) {
   __shared__ int s_sys, s_ok, s_dn, s_last;
@@ -560,7 +644,11 @@ __global__ void __launch_bounds__(256, CgOcc<T>::value)
   const int64_t stride = (int64_t)nb * 256, first = (int64_t)lb * 256 + tid;
   bool fail = false;
   for (int64_t step = 0; step < steps; ++step) {
-    const A dot = cg_spmv_rows<T, G>(rp, col, val, p, q, n, row0, groups);
+    A dot;
+    if constexpr (SELL)
+      dot = cg_sell_rows<T>(S->sp, S->scol, S->sval, p, q, n, S->ns, (int64_t)lb * 8 + (tid >> 5), (int64_t)nb * 8);
+    else
+      dot = cg_spmv_rows<T, G>(rp, col, val, p, q, n, row0, groups);
     cg_block_sums<256>(dot, zero<T>(), part + (int64_t)lb * kCgSlots + 2);
     if (!cg_reduce_barrier<256, 0, QMR>(st, part, nb, &s_ok, &s_last, &s_sc, &s_dn, &s_sc2, &s_sc3)) {
       fail = true;
@@ -717,12 +805,12 @@ constexpr int kCgChunk = 1024;  // iterations per persistent launch (the host ch
 constexpr int64_t kCgInnerMax = 4096;  // iterations of one complex64 inner solve at most
 
 // Whether the persistent kernel's grid (CgOcc blocks per SM) can be resident at once.
-template <typename T, int G, bool QMR = false>
+template <typename T, int G, bool QMR = false, bool SELL = false>
 Status cg_setup() {
   static bool done = false;
   if (done) return Status{};
   int nb = 0;
-  PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_inner<T, G, QMR>, 256, 0));
+  PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_inner<T, G, QMR, SELL>, 256, 0));
   if (nb < CgOcc<T>::value) return Status{PETGEM_ERR_UNSUPPORTED, "COCG kernel: too few resident blocks per SM"};
   done = true;
   return Status{};
@@ -737,17 +825,19 @@ template <> __device__ inline double2 cg_beta<double2>(const CState* st) { retur
 
 // x += unscale S y (FP64).
 template <typename T>
-__global__ void k_cg_finish(const T* __restrict__ y, const double2* __restrict__ sq, double2* __restrict__ x,
-                            int64_t n, double unscale) {
+__global__ void k_cg_finish(const T* __restrict__ y, const double2* __restrict__ sq, const int32_t* __restrict__ perm,
+                            double2* __restrict__ x, int64_t n, double unscale) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  x[i] = cadd(x[i], cscale(cmul(sq[i], to_d2(y[i])), unscale));
+  const int64_t o = perm ? perm[i] : i;
+  x[o] = cadd(x[o], cscale(cmul(sq[o], to_d2(y[i])), unscale));
 }
 
 struct BatchBuffers;
 
 struct CgBuffers {
   DevBuf sq, a128, a64, r64, r, p, q, y, d, state, partials, sys;
+  DevBuf s64, s128;  // the operator's values in the SELL-32 layout (when the mesh has one)
   BatchBuffers* batch = nullptr;  // workspace of petgem_solve_batch (when this context leads one)
   // multi-source solve: interleaved right-hand sides, iterate and residual (c128), vectors (T),
   // per-source states, group flags and per-source scales / inner targets
@@ -781,15 +871,37 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
   // the persistent kernel's grid: CgOcc blocks per SM (all resident), fewer for a small system
   const int grid = (int)std::max<int64_t>(
       1, std::min<int64_t>(blocks_for(n * kCgG, 256), (int64_t)CgOcc<T>::value * sms));
-  PG_TRY((cg_setup<T, kCgG, QMR>()));
+  const bool sell = c->sell_ok;
+  if (sell)
+    PG_TRY((cg_setup<T, kCgG, QMR, true>()));
+  else
+    PG_TRY((cg_setup<T, kCgG, QMR, false>()));
+  const int32_t* perm = sell ? c->sell_perm.as<int32_t>() : nullptr;
   const double vb = (double)sizeof(T) * n;
   // per iteration: SpMV nnz (values + columns) + row pointers + p gathered once, p of the row and
   // q written; update q, r read and r written; direction r, p, y read and p, y written (SQMR: and
   // d read and written)
   const double iter_bytes =
       (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 3.0 * vb + 3.0 * vb + (QMR ? 7.0 : 5.0) * vb;
-  CgSys<T> hsys{(const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), at, p, q, r, y, dq,
-                n, st, part, 0, 0, grid};
+  const T* sv = sell ? (c128 ? (const T*)B->s128.ptr : (const T*)B->s64.ptr) : nullptr;
+  CgSys<T> hsys{(const int64_t*)c->row_ptr.as<int64_t>(),
+                (const int32_t*)c->col.as<int32_t>(),
+                at,
+                p,
+                q,
+                r,
+                y,
+                dq,
+                sell ? (const int64_t*)c->sell_sp.as<int64_t>() : nullptr,
+                sell ? (const int32_t*)c->sell_col.as<int32_t>() : nullptr,
+                sv,
+                sell ? c->sell_ns : 0,
+                n,
+                st,
+                part,
+                0,
+                0,
+                grid};
   PG_TRY(B->sys.reserve(sizeof(CgSys<T>)));
   const CgSys<T>* dsys = B->sys.as<CgSys<T>>();
   CState hs;
@@ -846,7 +958,7 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
     const double rnorm = sqrt(rn2);
     const double need = 0.3 * o.tol * bnorm / rnorm;
     const double inner = c128 ? need : std::min(std::max(o.inner_tol, need), 0.5);
-    k_cg_start<T><<<nb, kT, 0, s>>>(B->r64.as<double2>(), B->sq.as<double2>(), r, p, y, dq, n, st, part, inner,
+    k_cg_start<T><<<nb, kT, 0, s>>>(B->r64.as<double2>(), B->sq.as<double2>(), perm, r, p, y, dq, n, st, part, inner,
                                     1.0 / rnorm);
     c->launches++;
     PG_CUDA(cudaGetLastError());
@@ -863,7 +975,10 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
       {
         KernelTimer kt(c, QMR ? (c128 ? "qmr_inner_c128" : "qmr_inner_c64") : (c128 ? "cg_inner_c128" : "cg_inner_c64"),
                        0.0);
-        PG_CUDA(pdl_launch(k_cg_inner<T, kCgG, QMR>, dim3(grid), dim3(256), 0, s, true, dsys, 1, steps));
+        if (sell)
+          PG_CUDA(pdl_launch(k_cg_inner<T, kCgG, QMR, true>, dim3(grid), dim3(256), 0, s, true, dsys, 1, steps));
+        else
+          PG_CUDA(pdl_launch(k_cg_inner<T, kCgG, QMR, false>, dim3(grid), dim3(256), 0, s, true, dsys, 1, steps));
       }
       c->launches++;
       const int k0 = hs.k;
@@ -871,7 +986,7 @@ Status cocg_source(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, cons
       set_last_timing_bytes(c, (hs.k - k0) * iter_bytes);
       if (hs.done) break;
     }
-    k_cg_finish<T><<<blocks_for(n, 256), 256, 0, s>>>(y, B->sq.as<double2>(), x, n, rnorm);
+    k_cg_finish<T><<<blocks_for(n, 256), 256, 0, s>>>(y, B->sq.as<double2>(), perm, x, n, rnorm);
     c->launches++;
     PG_CUDA(cudaGetLastError());
     iters += hs.k;
@@ -1417,6 +1532,14 @@ Status cg_prepare(petgem_ctx* c) {
                                                 B->sq.as<double2>(), n, B->a128.as<double2>(), B->a64.as<float2>());
   c->launches += 2;
   PG_CUDA(cudaGetLastError());
+  // the same operator in the SELL-32 layout
+  PG_TRY(sell_prepare(c));
+  if (c->sell_ok) {
+    PG_TRY(B->s64.reserve(c->sell_nnz * sizeof(float2)));
+    PG_TRY(B->s128.reserve(c->sell_nnz * sizeof(double2)));
+    PG_TRY(sell_values<float2>(c, B->a64.as<float2>(), B->s64.as<float2>()));
+    PG_TRY(sell_values<double2>(c, B->a128.as<double2>(), B->s128.as<double2>()));
+  }
   B->version = c->assembly_version;
   return Status{};
 }
@@ -1762,7 +1885,8 @@ Status solve_batch(petgem_ctx* const* ctxs, int n_ctx, const petgem_solve_opts& 
     v0 += vnb[k];
     r0 += rnb[k];
     const T* at = c128 ? (const T*)Bc->a128.ptr : (const T*)Bc->a64.ptr;
-    tab[k] = CgSys<T>{c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), at, p, q, r, y, nullptr, n, dst + k, part, 0, 0, 0};
+    tab[k] = CgSys<T>{c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), at, p, q, r, y, nullptr, nullptr, nullptr, nullptr,
+                      0, n, dst + k, part, 0, 0, 0};
   }
   // solution pointers: context k's sources in order
   {
@@ -2026,7 +2150,7 @@ void destroy_cocg(petgem_ctx* c) {
     if (B->batch->cap) cudaStreamDestroy(B->batch->cap);
     delete B->batch;
   }
-  for (DevBuf* d : {&B->sq, &B->a128, &B->a64, &B->r64, &B->r, &B->p, &B->q, &B->y, &B->d, &B->state, &B->partials, &B->sys, &B->Bt,
+  for (DevBuf* d : {&B->sq, &B->a128, &B->a64, &B->r64, &B->r, &B->p, &B->q, &B->y, &B->d, &B->state, &B->partials, &B->sys, &B->s64, &B->s128, &B->Bt,
                     &B->X, &B->R, &B->rb, &B->pb, &B->qb, &B->yb, &B->bstates, &B->bgrp, &B->bscal})
     d->release();
   delete B;

@@ -69,6 +69,14 @@ struct petgem_ctx {
   petgem::DevBuf occ, eptr;                // edge occurrences sorted by (edge, slot); offsets
   petgem::DevBuf row_ptr, col, gptr, pkey, pij;  // CSR pattern and its gather map
   petgem::DevBuf flags;                    // uint32 device error word
+  int64_t mesh_version = 0;                // bumped by every petgem_mesh_edges
+
+  // ---- SELL-32 layout of the pattern, rows in edge-kind order (sell.cu)
+  int64_t sell_version = -1;               // mesh version the layout belongs to
+  bool sell_ok = false;                    // false: the solvers use CSR
+  int64_t sell_ns = 0, sell_nnz = 0;       // slices, stored entries (with padding)
+  petgem::DevBuf sell_perm, sell_inv;      // renumbered row r holds edge perm[r]; inv = perm^-1
+  petgem::DevBuf sell_sp, sell_col, sell_src;  // slice offsets, columns, CSR entry per slot (-1 pad)
 
   // ---- assembly
   bool assembled = false;
@@ -123,6 +131,8 @@ Status check_flags(petgem_ctx* c, const char* where);
 // Stages implemented in the .cu files.
 Status build_topology(petgem_ctx* c);
 Status build_assembly(petgem_ctx* c, const double* sigma_dev);
+Status sell_prepare(petgem_ctx* c);
+template <typename T> Status sell_values(petgem_ctx* c, const T* csr_val, T* out);
 Status build_frequency(petgem_ctx* c);
 Status build_rhs(petgem_ctx* c);
 Status run_receivers(petgem_ctx* c, int32_t n_rcv, const double* rx, const double2* x, double2* out,
