@@ -152,10 +152,86 @@ __global__ void __launch_bounds__(256) k_residual(const int64_t* __restrict__ rp
 
 // Cycle start: V_0 = r (rounded to T), ||r||^2 in FP64, ||V_0||^2, then (last block) the
 // Arnoldi state: g = (||V_0||, 0, ...), 1/||V_0||, stop threshold.
+// y = (Ahat x) * scale over the SELL-32 layout (rows and vectors renumbered, sell.cu): one warp per
+// slice, lane = row, slices interleaved over the grid; five entries of a slice at a time with the
+// next five's columns and values in flight during this chunk's gathers.  Grouping the rows by edge
+// kind makes a slice's 32 rows consecutive lattice edges of one kind, so the column, value and
+// gather loads of each entry are coalesced, which lifts the product from the L1 limit of the CSR
+// form to close to the HBM rate.
 template <typename T>
-__global__ void __launch_bounds__(kT) k_cycle_init(const double2* __restrict__ r, T* __restrict__ V0, int64_t n,
-                                                   GState* __restrict__ st, double2* __restrict__ partials,
-                                                   double tol_abs, double inner_rel) {
+__global__ void __launch_bounds__(256, SpmvOcc<T>::value)
+    k_spmv_sell(const int64_t* __restrict__ sp, const int32_t* __restrict__ scol, const T* __restrict__ sval,
+                const T* __restrict__ x, T* __restrict__ y, int64_t n, int64_t ns, const GState* __restrict__ st, int j) {
+  pdl_trigger();
+  pdl_wait();
+  if (st->done) return;
+  constexpr int U = 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, b = 0, w = 0, t = 0;
+  if (s < ns) {
+    b = __ldg(&sp[s]);
+    w = (__ldg(&sp[s + 1]) - b) >> 5;
+  }
+  int32_t c[U];
+  T a[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const bool ok = u < w;
+    c[u] = ok ? __ldg(&scol[b + u * 32 + lane]) : 0;
+    a[u] = ok ? __ldg(&sval[b + u * 32 + lane]) : zero<T>();
+  }
+  typename Acc<T>::type acc = zero<T>(), acc2 = zero<T>();
+  while (s < ns) {
+    T xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = t + u < w ? __ldg(&x[c[u]]) : zero<T>();
+    int64_t s2 = s, b2 = b, w2 = w, t2 = t + U;
+    if (t2 >= w) {  // the next chunk is the next slice's first
+      s2 = s + nwarps;
+      t2 = 0;
+      w2 = 0;
+      if (s2 < ns) {
+        b2 = __ldg(&sp[s2]);
+        w2 = (__ldg(&sp[s2 + 1]) - b2) >> 5;
+      }
+    }
+    int32_t c2[U];
+    T a2[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool ok = t2 + u < w2;
+      c2[u] = ok ? __ldg(&scol[b2 + (t2 + u) * 32 + lane]) : 0;
+      a2[u] = ok ? __ldg(&sval[b2 + (t2 + u) * 32 + lane]) : zero<T>();
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) fma_c((u & 1) ? acc2 : acc, a[u], xv[u]);
+    if (t2 == 0) {  // this slice is complete
+      const int64_t r = s * 32 + lane;
+      if (r < n) {
+        acc.x += acc2.x;
+        acc.y += acc2.y;
+        y[r] = scale_out<T>(acc, st, j);
+      }
+      acc = zero<T>();
+      acc2 = zero<T>();
+    }
+    s = s2;
+    b = b2;
+    w = w2;
+    t = t2;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c[u] = c2[u];
+      a[u] = a2[u];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kT) k_cycle_init(const double2* __restrict__ r, const int32_t* __restrict__ perm,
+                                                   T* __restrict__ V0, int64_t n, GState* __restrict__ st,
+                                                   double2* __restrict__ partials, double tol_abs, double inner_rel) {
   __shared__ double2 red[kT / 32];
   __shared__ double2 fin[2];
   double rr = 0.0, vv = 0.0;
@@ -164,7 +240,7 @@ __global__ void __launch_bounds__(kT) k_cycle_init(const double2* __restrict__ r
   for (int q = 0; q < kR; ++q) {
     int64_t i = base + (int64_t)q * kT;
     if (i < n) {
-      double2 v = r[i];
+      double2 v = r[perm ? perm[i] : i];  // the basis is in the SELL renumbering when perm is set
       T t = from_d2<T>(v);
       V0[i] = t;
       rr += nrm2(v);
@@ -211,8 +287,8 @@ __global__ void __launch_bounds__(32) k_backsolve(GState* st) { backsolve_warp(s
 // u += sum_k V_k y_k.  complex128: in FP64.  complex64: the correction sum_k V_k y_k is formed in
 // FP32 (it is the inner solve's correction, accurate to complex64 anyway) and added to u in FP64.
 template <typename T>
-__global__ void __launch_bounds__(kT) k_xupdate(const T* __restrict__ V, int64_t ld, int64_t n,
-                                                double2* __restrict__ u, const GState* __restrict__ st) {
+__global__ void __launch_bounds__(kT) k_xupdate(const T* __restrict__ V, const int32_t* __restrict__ perm, int64_t ld,
+                                                int64_t n, double2* __restrict__ u, const GState* __restrict__ st) {
   __shared__ T ys[kMaxM];
   const int kk = st->done == 2 ? 0 : st->k;  // a failed cycle leaves u untouched
   for (int k = threadIdx.x; k < kk; k += kT) ys[k] = from_d2<T>(st->y[k]);
@@ -221,7 +297,8 @@ __global__ void __launch_bounds__(kT) k_xupdate(const T* __restrict__ V, int64_t
   if (i >= n || kk == 0) return;
   typename Acc<T>::type acc = zero<T>();
   for (int k = 0; k < kk; ++k) fma_c(acc, V[(int64_t)k * ld + i], ys[k]);
-  u[i] = cadd(u[i], to_d2(acc));
+  const int64_t o = perm ? perm[i] : i;
+  u[o] = cadd(u[o], to_d2(acc));
 }
 
 __global__ void k_scale_in(const double2* __restrict__ x, const double2* __restrict__ d, double2* __restrict__ u,
@@ -318,6 +395,14 @@ Status prepare(petgem_ctx* c, int m, int prec, bool single) {
                                                           S->ahat64.as<float2>());
     c->launches++;
     PG_CUDA(cudaGetLastError());
+    // the same matrix in the SELL-32 layout (single-source Jacobi cycles use it)
+    PG_TRY(sell_prepare(c));
+    if (c->sell_ok) {
+      PG_TRY(S->sell64.reserve(c->sell_nnz * sizeof(float2)));
+      PG_TRY(S->sell128.reserve(c->sell_nnz * sizeof(double2)));
+      PG_TRY(sell_values<float2>(c, S->ahat64.as<float2>(), S->sell64.as<float2>()));
+      PG_TRY(sell_values<double2>(c, S->ahat128.as<double2>(), S->sell128.as<double2>()));
+    }
     S->version = c->assembly_version;
   }
   if (S->sms == 0) PG_CUDA(cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, c->device));
@@ -370,14 +455,20 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
   const double vbytes = (double)sizeof(T) * n;
   const bool c128 = sizeof(T) == 16;
   const size_t pending0 = c->pending.size();
+  // SELL-32 products (renumbered basis) for Jacobi cycles when the mesh has the layout
+  const bool sell = c->sell_ok && !learned;
+  const int32_t* perm = sell ? c->sell_perm.as<int32_t>() : nullptr;
   {
     KernelTimer kt(c, c128 ? "cycle_init_c128" : "cycle_init_c64", 16.0 * n + vbytes);
-    k_cycle_init<T><<<nb, kT, 0, s>>>(S->r.as<double2>(), V, n, st, part, tol_abs, inner_rel);
+    k_cycle_init<T><<<nb, kT, 0, s>>>(S->r.as<double2>(), perm, V, n, st, part, tol_abs, inner_rel);
     c->launches++;
   }
-  const double spmv_bytes = (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 2.0 * vbytes;
+  const double spmv_bytes = sell ? (double)c->sell_nnz * (sizeof(T) + 4) + 8.0 * (c->sell_ns + 1) + 2.0 * vbytes
+                                 : (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 2.0 * vbytes;
   const unsigned spmv_blocks =
       (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_for(n * kGroup, 256), (int64_t)SpmvOcc<T>::value * S->sms));
+  const unsigned sell_blocks = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>(blocks_for(c->sell_ns * 32, 256), (int64_t)SpmvOcc<T>::value * S->sms));
   // Flexible GMRES with the learned preconditioner: z_j = N-corrected v_j, stored in Z, and the
   // solution update uses Z instead of V.
   T* Z = learned ? S->Z.as<T>() : nullptr;
@@ -401,9 +492,15 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
       }
       {
         KernelTimer kt(c, c128 ? "spmv_c128" : "spmv_c64", spmv_bytes, j, 0);
-        PG_CUDA(pdl_launch(k_spmv_arnoldi<T, kGroup>, dim3(spmv_blocks), dim3(256), 0, s, false,
-                           (const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), ahat, xin, vn,
-                           n, (const GState*)st, j));
+        if (sell)
+          PG_CUDA(pdl_launch(k_spmv_sell<T>, dim3(sell_blocks), dim3(256), 0, s, false,
+                             (const int64_t*)c->sell_sp.as<int64_t>(), (const int32_t*)c->sell_col.as<int32_t>(),
+                             (const T*)(c128 ? S->sell128.ptr : S->sell64.ptr), xin, vn, n, c->sell_ns,
+                             (const GState*)st, j));
+        else
+          PG_CUDA(pdl_launch(k_spmv_arnoldi<T, kGroup>, dim3(spmv_blocks), dim3(256), 0, s, false,
+                             (const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), ahat, xin,
+                             vn, n, (const GState*)st, j));
       }
       const double dot_b = (double)(j + 2) * vbytes, upd_b = (double)(j + 3) * vbytes;
       auto sdot = [&](int pass, int need_refine, const char* name, double bytes, int tag) -> Status {
@@ -438,7 +535,7 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
     k_backsolve<<<1, 32, 0, s>>>(st);
     {
       KernelTimer kt(c, c128 ? "xupdate_c128" : "xupdate_c64", 32.0 * n + (double)m * vbytes);
-      k_xupdate<T><<<blocks_for(n, kT), kT, 0, s>>>(learned ? Z : V, ld, n, S->u.as<double2>(), st);
+      k_xupdate<T><<<blocks_for(n, kT), kT, 0, s>>>(learned ? Z : V, perm, ld, n, S->u.as<double2>(), st);
     }
     c->launches += 2;
     PG_CUDA(cudaGetLastError());
@@ -453,7 +550,9 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
                                     (uint64_t)(uintptr_t)part, (uint64_t)(uintptr_t)c->row_ptr.ptr,
                                     (uint64_t)(uintptr_t)c->col.ptr, (uint64_t)(uintptr_t)S->u.ptr, (uint64_t)n,
                                     (uint64_t)ld, (uint64_t)m, (uint64_t)orth, (uint64_t)sizeof(T),
-                                    (uint64_t)spmv_blocks, (uint64_t)S->sms});
+                                    (uint64_t)spmv_blocks, (uint64_t)S->sms, (uint64_t)sell,
+                                    (uint64_t)(uintptr_t)(sell ? (c128 ? S->sell128.ptr : S->sell64.ptr) : nullptr),
+                                    (uint64_t)(uintptr_t)c->sell_perm.ptr});
     if (!S->graph || S->graph_key != key) {
       if (S->graph) cudaGraphExecDestroy(S->graph);
       S->graph = nullptr;
@@ -494,7 +593,7 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
 void destroy_solver(petgem_ctx* c) {
   if (!c->solver) return;
   Solver* S = c->solver;
-  for (DevBuf* d : {&S->ahat128, &S->ahat64, &S->dinv, &S->V, &S->u, &S->r, &S->partials, &S->state, &S->Z, &S->usave,
+  for (DevBuf* d : {&S->ahat128, &S->ahat64, &S->sell128, &S->sell64, &S->dinv, &S->V, &S->u, &S->r, &S->partials, &S->state, &S->Z, &S->usave,
                     &S->Vb, &S->Ub, &S->Rb, &S->Bb, &S->bstates, &S->bgroup, &S->btol})
     d->release();
   if (S->graph) cudaGraphExecDestroy(S->graph);

@@ -41,6 +41,7 @@ struct Solver {
   int prec = -1;
   int64_t version = -1;  // assembly version the scaled matrices belong to
   DevBuf ahat128, ahat64, dinv;  // scaled matrix (c128, c64)
+  DevBuf sell128, sell64;        // the scaled matrix in the SELL-32 layout (sell.cu)
   DevBuf V, u, r, partials, state, Z, usave;
   // multi-source solve (block.cu): interleaved basis / iterate / residual / right-hand sides,
   // one Arnoldi state per source, a group flag and the per-source stopping thresholds
