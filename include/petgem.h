@@ -89,8 +89,10 @@ typedef struct {
                           one, while kernel profiling is on, and by COCG, whose iterations run in
                           one persistent kernel); results are identical to direct launches */
   int32_t method;      /* PETGEM_METHOD_GMRES (default) or PETGEM_METHOD_COCG */
-  int32_t spmv_lanes;  /* petgem_solve_batch: lanes per matrix row of the SpMV (2, 4 or 8);
-                          0 = chosen by the autotuner; ignored by petgem_solve */
+  int32_t spmv_lanes;  /* petgem_solve_batch: layout of the sparse product: 2, 4 or 8 = CSR with that
+                          many lanes per row, 1 = SELL-32 with rows grouped by edge kind (CSR with
+                          4 lanes when a mesh lacks that layout); 0 = chosen by the autotuner;
+                          ignored by petgem_solve (which uses SELL-32 when the mesh has it) */
 } petgem_solve_opts;
 
 /* Krylov method.
@@ -128,7 +130,8 @@ typedef struct {
   int32_t status;      /* PETGEM_OK, PETGEM_ERR_NOT_CONVERGED, _BREAKDOWN or _TIMEOUT */
   int32_t reorth;      /* Arnoldi steps that needed a second Gram-Schmidt pass */
   int32_t fell_back;   /* learned preconditioner: 1 if the solve switched back to Jacobi */
-  int32_t spmv_lanes;  /* petgem_solve_batch: lanes per row the SpMV ran with; 0 otherwise */
+  int32_t spmv_lanes;  /* petgem_solve_batch: the product's layout it ran with (as in the options:
+                          1 = SELL-32, 2 / 4 / 8 = CSR lanes per row); 0 otherwise */
 } petgem_solve_info;
 
 /* ----------------------------------------------------------------------- lifecycle */
@@ -212,7 +215,8 @@ int petgem_solve(petgem_ctx *ctx, const petgem_solve_opts *opts, void *x, petgem
  * iterations each system took); the FP64 refinement steps of all systems (solution update, true
  * residual, its norm, the stopping decision, the next start) run as one launch sequence per
  * round, replayed as a CUDA graph when opts->use_graphs = 1.  opts->spmv_lanes = 0 lets an
- * autotuner pick the SpMV's lanes per row (2, 4 or 8) by timing the first iterations with each.
+ * autotuner pick the sparse product's layout (CSR with 2, 4 or 8 lanes per row, or SELL-32 when
+ * every mesh has it) by timing a few iterations with each before the first inner solve.
  * The contexts must share a device and each must have called petgem_assemble.  The work runs on
  * ctxs[0]'s stream, after the work already queued on every context's stream and before any work
  * queued on them afterwards.

@@ -346,8 +346,8 @@ int petgem_solve_batch(petgem_ctx* const* ctxs, int32_t n_ctx, const petgem_solv
     return finish(c0, Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve_batch: the batch solver is COCG"});
   if (o.precond != PETGEM_PRECOND_JACOBI)
     return finish(c0, Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve_batch: Jacobi preconditioner only"});
-  if (o.spmv_lanes != 0 && o.spmv_lanes != 2 && o.spmv_lanes != 4 && o.spmv_lanes != 8)
-    return finish(c0, Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve_batch: spmv_lanes must be 0, 2, 4 or 8"});
+  if (o.spmv_lanes != 0 && o.spmv_lanes != 1 && o.spmv_lanes != 2 && o.spmv_lanes != 4 && o.spmv_lanes != 8)
+    return finish(c0, Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve_batch: spmv_lanes must be 0, 1, 2, 4 or 8"});
   if (!(o.tol > 0.0) || o.max_iters < 0 || (o.precision != PETGEM_PREC_C128 && o.precision != PETGEM_PREC_MIXED) ||
       !(o.inner_tol >= 0.0 && o.inner_tol < 1.0))
     return finish(c0, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve_batch: bad options"});

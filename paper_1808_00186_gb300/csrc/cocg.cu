@@ -1567,6 +1567,7 @@ struct CgRef {
   double2* x;
   double2* r64;
   T *r, *p, *y;
+  const int32_t* perm;  // the inner solve's vectors in the SELL renumbering (null: original order)
   CState* st;
   double2* part;
   CgCtl* ctl;
@@ -1575,7 +1576,7 @@ struct CgRef {
   int r0, rnb;  // blocks of the residual kernel (256 / kCgG rows each)
 };
 constexpr int kBatchMax = 64;        // systems per batch
-constexpr int kBatchTuneSteps = 4;   // iterations per timed launch of the autotuner
+constexpr int kBatchTuneSteps = 2;   // iterations per timed launch of the autotuner
 
 // The system whose block range [v0, v0 + vnb) (resid: [r0, r0 + rnb)) holds this block.
 template <typename T, bool RESID>
@@ -1608,8 +1609,10 @@ __global__ void __launch_bounds__(256) k_cgb_finish(const CgRef<T>* __restrict__
   const CgRef<T>& S = R[k];
   if (!S.ctl->ran) return;
   const double unscale = 1.0 / S.ctl->scale;
-  for (int64_t i = (int64_t)(blockIdx.x - S.v0) * 256 + threadIdx.x; i < S.n; i += (int64_t)S.vnb * 256)
-    S.x[i] = cadd(S.x[i], cscale(cmul(S.sq[i], to_d2(S.y[i])), unscale));
+  for (int64_t i = (int64_t)(blockIdx.x - S.v0) * 256 + threadIdx.x; i < S.n; i += (int64_t)S.vnb * 256) {
+    const int64_t o = S.perm ? S.perm[i] : i;
+    S.x[o] = cadd(S.x[o], cscale(cmul(S.sq[o], to_d2(S.y[i])), unscale));
+  }
 }
 
 // r64 = b - A x (FP64) for the active systems, kCgG lanes per row.
@@ -1726,7 +1729,8 @@ __global__ void __launch_bounds__(256) k_cgb_start(const CgRef<T>* __restrict__ 
   const double scale = S.ctl->scale;
   A rho = zero<T>(), nr = zero<T>();
   for (int64_t i = (int64_t)lb * 256 + threadIdx.x; i < S.n; i += (int64_t)S.vnb * 256) {
-    const T t = from_d2<T>(cscale(cmul(S.sq[i], S.r64[i]), scale));
+    const int64_t o = S.perm ? S.perm[i] : i;
+    const T t = from_d2<T>(cscale(cmul(S.sq[o], S.r64[o]), scale));
     S.r[i] = t;
     S.p[i] = t;
     S.y[i] = zero<T>();
@@ -1808,6 +1812,11 @@ Status batch_inner_launch(cudaStream_t s, const CgSys<T>* dsys, int na, int grid
 
 template <typename T>
 Status batch_inner(int G, cudaStream_t s, const CgSys<T>* dsys, int na, int grid, int steps) {
+  if (G == 1) {  // the SELL-32 products
+    PG_TRY((cg_setup<T, kCgG, false, true>()));
+    PG_CUDA(pdl_launch(k_cg_inner<T, kCgG, false, true>, dim3(grid), dim3(256), 0, s, true, dsys, na, steps));
+    return Status{};
+  }
   if (G == 2) return batch_inner_launch<2, T>(s, dsys, na, grid, steps);
   if (G == 8) return batch_inner_launch<8, T>(s, dsys, na, grid, steps);
   return batch_inner_launch<4, T>(s, dsys, na, grid, steps);
@@ -1881,13 +1890,41 @@ Status solve_batch(petgem_ctx* const* ctxs, int n_ctx, const petgem_solve_opts& 
     prow += std::max(vnb[k], pgrid);
     ref[k] = CgRef<T>{c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(), Bc->sq.as<double2>(),
                       c->b.as<double2>() + (int64_t)sys[k].src * n, nullptr,
-                      r64, r, p, y, dst + k, part, dctl + k, n, v0, vnb[k], r0, rnb[k]};
+                      r64, r, p, y, nullptr, dst + k, part, dctl + k, n, v0, vnb[k], r0, rnb[k]};
     v0 += vnb[k];
     r0 += rnb[k];
     const T* at = c128 ? (const T*)Bc->a128.ptr : (const T*)Bc->a64.ptr;
-    tab[k] = CgSys<T>{c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), at, p, q, r, y, nullptr, nullptr, nullptr, nullptr,
-                      0, n, dst + k, part, 0, 0, 0};
+    const bool sl = c->sell_ok;
+    tab[k] = CgSys<T>{c->row_ptr.as<int64_t>(),
+                      c->col.as<int32_t>(),
+                      at,
+                      p,
+                      q,
+                      r,
+                      y,
+                      nullptr,
+                      sl ? c->sell_sp.as<int64_t>() : nullptr,
+                      sl ? c->sell_col.as<int32_t>() : nullptr,
+                      sl ? (c128 ? (const T*)Bc->s128.ptr : (const T*)Bc->s64.ptr) : nullptr,
+                      sl ? c->sell_ns : 0,
+                      n,
+                      dst + k,
+                      part,
+                      0,
+                      0,
+                      0};
   }
+  bool all_sell = true;  // every mesh has the SELL-32 layout: the layout is one of the candidates
+  for (int k = 0; k < ns; ++k) all_sell = all_sell && sys[k].c->sell_ok;
+  // the inner solves' vector order: the SELL renumbering (layout 1) or the original (CSR)
+  auto set_layout = [&](bool sell) -> Status {
+    for (int k = 0; k < ns; ++k) {
+      petgem_ctx* ck = sys[k].c;
+      ref[k].perm = sell ? ck->sell_perm.as<int32_t>() : nullptr;
+    }
+    PG_CUDA(cudaMemcpyAsync(W->ref.ptr, ref.data(), ns * sizeof(CgRef<T>), cudaMemcpyHostToDevice, s));
+    return Status{};
+  };
   // solution pointers: context k's sources in order
   {
     int k = 0;
@@ -1939,8 +1976,11 @@ Status solve_batch(petgem_ctx* const* ctxs, int n_ctx, const petgem_solve_opts& 
     }
   } guard{gexec};
   // rounds
+  // layout: 1 = SELL-32 (one lane per row), 2 / 4 / 8 = CSR with that many lanes per row
   int G = o.spmv_lanes ? o.spmv_lanes : kCgG;
+  if (G == 1 && !all_sell) G = kCgG;
   bool tuned = o.spmv_lanes != 0;
+  if (G == 1) PG_TRY(set_layout(true));
   std::vector<double> work(ns);
   std::vector<int64_t> cap(ns), lastk(ns, 0);
   std::vector<CState> hst(ns);
@@ -2000,12 +2040,14 @@ Status solve_batch(petgem_ctx* const* ctxs, int n_ctx, const petgem_solve_opts& 
     };
     PG_TRY(plan());
     if (!tuned) {
-      // autotuner: a few iterations with each lane count (two passes over the candidates, the
-      // faster of each pair kept), timed with events on the stream; the iterations count towards
-      // the solve
+      // autotuner: a few iterations with each layout of the product (CSR with 2, 4 or 8 lanes per
+      // row, and SELL-32 when every mesh has it), two passes over the candidates with the faster of
+      // each pair kept, timed with events on the stream; each probe restarts the inner solve, and
+      // the solve proper restarts once more with the winner
       PG_TRY((cg_setup<T, 2>()));
       PG_TRY((cg_setup<T, 4>()));
       PG_TRY((cg_setup<T, 8>()));
+      PG_TRY((cg_setup<T, kCgG, false, true>()));
       struct Events {
         cudaEvent_t e[2] = {nullptr, nullptr};
         ~Events() {
@@ -2015,10 +2057,19 @@ Status solve_batch(petgem_ctx* const* ctxs, int n_ctx, const petgem_solve_opts& 
       } ev;
       PG_CUDA(cudaEventCreate(&ev.e[0]));
       PG_CUDA(cudaEventCreate(&ev.e[1]));
-      float best[3] = {INFINITY, INFINITY, INFINITY};
-      const int cand[3] = {2, 4, 8};
+      float best[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+      const int cand[4] = {2, 4, 8, 1};
+      const int nc = all_sell ? 4 : 3;
+      bool sell_now = false;
       for (int pass = 0; pass < 2; ++pass)
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < nc; ++i) {
+          // every candidate starts the inner solve afresh in its own vector order
+          if ((cand[i] == 1) != sell_now) {
+            sell_now = cand[i] == 1;
+            PG_TRY(set_layout(sell_now));
+          }
+          k_cgb_start<T><<<vgrid, 256, 0, s>>>(dref, ns);
+          c0->launches++;
           PG_CUDA(cudaEventRecord(ev.e[0], s));
           PG_TRY(batch_inner<T>(cand[i], s, dsys, (int)act.size(), grid_of(), kBatchTuneSteps));
           PG_CUDA(cudaEventRecord(ev.e[1], s));
@@ -2028,7 +2079,11 @@ Status solve_batch(petgem_ctx* const* ctxs, int n_ctx, const petgem_solve_opts& 
           PG_CUDA(cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]));
           best[i] = std::min(best[i], ms);
         }
-      G = cand[std::min_element(best, best + 3) - best];
+      G = cand[std::min_element(best, best + nc) - best];
+      if ((G == 1) != sell_now) PG_TRY(set_layout(G == 1));
+      k_cgb_start<T><<<vgrid, 256, 0, s>>>(dref, ns);  // the solve proper, from the start
+      c0->launches++;
+      PG_CUDA(cudaGetLastError());
       tuned = true;
     }
     PG_TRY(all_done());

@@ -79,7 +79,7 @@ def test_batch_matches_oracle(precision):
             check_against_oracle(m, ref, xr, x.cpu().numpy(), info[k:k + ns], c)
             k += ns
         assert k == len(info) == 4
-        assert all(i["spmv_lanes"] in (2, 4, 8) for i in info)  # the autotuner's pick
+        assert all(i["spmv_lanes"] in (1, 2, 4, 8) for i in info)  # the autotuner's pick
         print("\nbatch %s: iterations %s, inner solves %s, lanes %d" % (
             "c128" if precision == api.PREC_C128 else "mixed", [i["iters"] for i in info],
             [i["restarts"] for i in info], info[0]["spmv_lanes"]))
@@ -88,7 +88,7 @@ def test_batch_matches_oracle(precision):
             c.close()
 
 
-@pytest.mark.parametrize("lanes", [2, 4, 8])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
 def test_batch_graph_replay_is_bit_identical(lanes):
     refs = [reference(i) for i in (0, 1)]
     ctxs = contexts([r[0] for r in refs])
