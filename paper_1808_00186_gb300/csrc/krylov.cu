@@ -552,7 +552,9 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
                                     (uint64_t)ld, (uint64_t)m, (uint64_t)orth, (uint64_t)sizeof(T),
                                     (uint64_t)spmv_blocks, (uint64_t)S->sms, (uint64_t)sell,
                                     (uint64_t)(uintptr_t)(sell ? (c128 ? S->sell128.ptr : S->sell64.ptr) : nullptr),
-                                    (uint64_t)(uintptr_t)c->sell_perm.ptr});
+                                    (uint64_t)(uintptr_t)c->sell_perm.ptr, (uint64_t)(uintptr_t)c->sell_sp.ptr,
+                                    (uint64_t)(uintptr_t)c->sell_col.ptr, (uint64_t)c->sell_ns,
+                                    (uint64_t)(uintptr_t)c->val.ptr, (uint64_t)(uintptr_t)S->r.ptr});
     if (!S->graph || S->graph_key != key) {
       if (S->graph) cudaGraphExecDestroy(S->graph);
       S->graph = nullptr;
