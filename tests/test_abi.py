@@ -36,6 +36,10 @@ def test_status_strings_without_gpu(lib_path):
     # A null context is rejected before any CUDA call.
     assert L.petgem_solve(None, None, None, None) == api.ERR_INVALID_ARG
     assert L.petgem_destroy(None) == api.OK
+    # the batch solver and the frequency re-assembly check their arguments on the host too
+    assert L.petgem_solve_batch(None, 0, None, None, None) == api.OK  # nothing to do
+    assert L.petgem_solve_batch(None, 1, None, None, None) == api.ERR_INVALID_ARG
+    assert L.petgem_assemble_frequency(None, 1.0, 1, None) == api.ERR_INVALID_ARG
 
 
 def test_no_cpu_fallback_when_library_missing(tmp_path):
