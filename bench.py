@@ -37,6 +37,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=64, help="cells per axis of the marine model")
     p.add_argument("--no-plain", action="store_true", help="skip the complex128 comparison run")
+    p.add_argument("--no-all-cores", action="store_true", help="skip the all-cores oracle throughput leg")
     p.add_argument("--block-sources", type=int, default=32, help="sources of the multi-source block solve (0 = skip)")
     p.add_argument("--profile-step", action="store_true",
                    help="run one untimed step of the hot path and exit (the command profilers capture)")
@@ -556,6 +557,49 @@ def oracle_sample(n, gpu_iters=None):
                       "assembly + per-iteration time x %d iterations" % (n, k, iters)}
 
 
+def _oracle_worker(job):
+    n, iters = job
+    return oracle_sample(n, gpu_iters=iters)
+
+
+def host_info():
+    """nproc and the CPU model of the host the oracle runs on (/proc/cpuinfo, else lscpu, which
+    names Arm cores that /proc/cpuinfo gives only as part numbers)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            model = next((l.split(":", 1)[1].strip() for l in f if l.lower().startswith("model name")), None)
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            model = next((l.split(":", 1)[1].strip() for l in out.splitlines() if l.startswith("Model name:")), None)
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"nproc": len(os.sched_getaffinity(0)), "cpu_model": model}
+
+
+def oracle_all_cores(n, iters, per_proc_bytes=3.0e9):
+    """The unmodified single-threaded oracle on all host cores: one independent single-source
+    sample per process, as many processes as cores, bounded so that they hold at most half of
+    the host's available memory.  Throughput per source = median per-process time / processes."""
+    import multiprocessing as mp
+    P = len(os.sched_getaffinity(0))
+    try:
+        with open("/proc/meminfo") as f:
+            avail = next(int(l.split()[1]) * 1024 for l in f if l.startswith("MemAvailable:"))
+        P = max(1, min(P, int(0.5 * avail // per_proc_bytes)))
+    except (OSError, StopIteration):
+        P = 1
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(P) as pool:  # spawn: the parent holds a CUDA context
+        rs = pool.map(_oracle_worker, [(n, iters)] * P)
+    wall = time.perf_counter() - t0
+    per = statistics.median(r["value"] for r in rs)
+    return {"value": per / P, "processes": P, "per_process_s": per, "wall_s": wall}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -571,16 +615,24 @@ def main():
                           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
                           "config": {"workload": "marine_n%d_1src_1Hz" % args.n},
                           "cpu_baseline": {"value": round(v, 3), "unit": "s/source", "cores": 1, "kind": "oracle",
-                                           "sample": samp["sample"]},
+                                           "sample": samp["sample"], **host_info()},
                           "e2e": {"value": round(v, 3), "unit": "s/source", "h2d_bytes_per_step": 0,
                                   "d2h_bytes_per_step": 0},
                           "wall_s": round(time.perf_counter() - t0, 1)}))
         return
     res = run_ours(args)
     if rank == 0 and res is not None:
-        cpu = oracle_sample(args.n, gpu_iters=(res["plain_c128"] or {}).get("iters") or res["iters"])
+        iters = (res["plain_c128"] or {}).get("iters") or res["iters"]
+        cpu = oracle_sample(args.n, gpu_iters=iters)
         res["cpu_baseline"] = {"value": round(cpu["value"], 3), "unit": "s/source", "cores": cpu["cores"],
-                               "kind": "oracle", "sample": cpu["sample"]}
+                               "kind": "oracle", "sample": cpu["sample"], **host_info()}
+        if not args.no_all_cores:
+            allc = oracle_all_cores(args.n, iters)
+            res["cpu_baseline"]["all_cores"] = {
+                "value": round(allc["value"], 3), "unit": "s/source", "processes": allc["processes"],
+                "per_process_s": round(allc["per_process_s"], 3), "wall_s": round(allc["wall_s"], 1),
+                "sample": "the same sample in %d concurrent single-threaded oracle processes; value = median "
+                          "per-process time / processes" % allc["processes"]}
         print(json.dumps(res))
 
 
