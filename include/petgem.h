@@ -41,7 +41,7 @@ enum {
   PETGEM_ERR_NOT_CONVERGED = 6,   /* iteration cap reached; info is still filled */
   PETGEM_ERR_BREAKDOWN = 7,       /* Krylov breakdown or a NaN/Inf in the iteration */
   PETGEM_ERR_RECEIVER_OUTSIDE = 8,/* a receiver lies in no tet; its outputs are NaN */
-  PETGEM_ERR_UNSUPPORTED = 9,    /* a size or option this build does not handle */
+  PETGEM_ERR_UNSUPPORTED = 9,    /* a size or option the library does not handle */
   PETGEM_ERR_TIMEOUT = 10         /* a bounded device-side wait gave up; the call was abandoned */
 };
 
