@@ -9,7 +9,8 @@ SQMR runs the symmetric Lanczos recurrences in the bilinear form u^T v (the same
 directions q_n and scalars alpha, beta as COCG) and takes as iterate the quasi-minimal-residual
 combination of them, which smooths COCG's erratic residual history.  Preconditioner: the Jacobi
 diagonal split symmetrically, M = M1 M2 with M1 = M2 = D^{1/2} (D = diag(A)); only
-M1^{-1} v = D^{-1/2} v (principal complex square root) and M^{-1} v = D^{-1} v are applied.
+M1^{-1} v = D^{-1/2} v (principal complex square root) and M^{-1} v = D^{-1} v are applied.  The
+symmetric SOR split of oracle/ssor.py (the paper's SQMR + SOR runs) can be passed instead.
 
 Steps, in the method's order (x0 given; r0 = b - A x0; t = M1^{-1} r0; tau0 = ||t||_2;
 q0 = M2^{-1} t; theta0 = 0; rho0 = r0^T q0; d0 = 0):
@@ -25,17 +26,23 @@ from __future__ import annotations
 import numpy as np
 
 
-def sqmr(A, b, tol: float = 1e-8, maxit: int = 100000, x0=None, record=False):
+def sqmr(A, b, tol: float = 1e-8, maxit: int = 100000, x0=None, record=False, precond=None):
     """Returns (x, iterations, relative residual ||b - A x|| / ||b|| recomputed at the end, record)
-    where record (if asked) holds per step the iterate x_n, tau_n and the Lanczos residual r_n."""
+    where record (if asked) holds per step the iterate x_n, tau_n and the Lanczos residual r_n.
+    precond: None for the Jacobi split, else an object whose m1inv / m2inv apply M1^{-1} and
+    M2^{-1} of a symmetric split M = M1 M2, M2 = M1^T (oracle.ssor.SSOR)."""
     b = np.asarray(b, dtype=np.complex128)
-    d = np.asarray(A.diagonal(), dtype=np.complex128)
-    m1 = 1.0 / np.sqrt(d)  # M1^{-1} = M2^{-1} = D^{-1/2}, principal root
+    if precond is None:
+        d = np.asarray(A.diagonal(), dtype=np.complex128)
+        m1 = 1.0 / np.sqrt(d)  # M1^{-1} = M2^{-1} = D^{-1/2}, principal root
+        m1inv = m2inv = lambda v: m1 * v
+    else:
+        m1inv, m2inv = precond.m1inv, precond.m2inv
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128)
     r = b - A @ x
-    t = m1 * r
+    t = m1inv(r)
     tau = np.linalg.norm(t)
-    q = m1 * t
+    q = m2inv(t)
     theta = 0.0
     rho = np.dot(r, q)  # bilinear: no conjugate
     dv = np.zeros_like(b)
@@ -51,7 +58,7 @@ def sqmr(A, b, tol: float = 1e-8, maxit: int = 100000, x0=None, record=False):
             break  # breakdown of the bilinear form
         alpha = rho / sigma
         r = r - alpha * t
-        t = m1 * r
+        t = m1inv(r)
         theta_new = np.linalg.norm(t) / tau
         c2 = 1.0 / (1.0 + theta_new * theta_new)
         tau = tau * theta_new * np.sqrt(c2)
@@ -63,7 +70,7 @@ def sqmr(A, b, tol: float = 1e-8, maxit: int = 100000, x0=None, record=False):
             rec["x"].append(x.copy())
             rec["tau"].append(tau)
             rec["r"].append(r.copy())
-        u = m1 * t
+        u = m2inv(t)
         rho_new = np.dot(r, u)
         beta = rho_new / rho
         rho = rho_new
