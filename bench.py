@@ -38,6 +38,7 @@ def parse():
     p.add_argument("--n", type=int, default=64, help="cells per axis of the marine model")
     p.add_argument("--no-plain", action="store_true", help="skip the complex128 comparison run")
     p.add_argument("--no-all-cores", action="store_true", help="skip the all-cores oracle throughput leg")
+    p.add_argument("--no-ssor", action="store_true", help="skip the SSOR-preconditioned SQMR comparison")
     p.add_argument("--block-sources", type=int, default=32, help="sources of the multi-source block solve (0 = skip)")
     p.add_argument("--profile-step", action="store_true",
                    help="run one untimed step of the hot path and exit (the command profilers capture)")
@@ -159,13 +160,13 @@ def run_ours(args):
 
     n_edges = [0]
 
-    def step(precision, method=api.METHOD_GMRES, graphs=1):
+    def step(precision, method=api.METHOD_GMRES, graphs=1, precond=api.PRECOND_JACOBI):
         E = api.petgem_mesh_edges(ctx.h, nodes, tets)
         n_edges[0] = E
         api.petgem_assemble(ctx.h, m.freq, sigma, m.sigma_p, m.sources)
         x = torch.zeros((S, E), dtype=torch.complex128, device=dev)
         st, info = api.petgem_solve(ctx.h, x, S, api.solve_opts(precision=precision, tol=1e-8, method=method,
-                                                                use_graphs=graphs))
+                                                                use_graphs=graphs, precond=precond))
         out = torch.empty((S, rx.shape[0], 3, 3), dtype=torch.complex128, device=dev)
         api.petgem_receivers(ctx.h, rx, x, out)
         return info, out
@@ -176,9 +177,10 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def timed(precision, steps, warmup, profile=False, clocks=None, method=api.METHOD_GMRES, graphs=1):
+    def timed(precision, steps, warmup, profile=False, clocks=None, method=api.METHOD_GMRES, graphs=1,
+              precond=api.PRECOND_JACOBI):
         for _ in range(warmup):
-            step(precision, method, graphs)
+            step(precision, method, graphs, precond)
         barrier()
         if profile:
             api.petgem_profile(ctx.h, True)
@@ -189,7 +191,7 @@ def run_ours(args):
         e0.record()
         infos = []
         for _ in range(steps):
-            infos.append(step(precision, method, graphs)[0])
+            infos.append(step(precision, method, graphs, precond)[0])
         e1.record()
         barrier()
         cl = clocks.stop() if clocks else None
@@ -269,6 +271,25 @@ def run_ours(args):
         cocg["sqmr"] = {"precision": "mixed", "ms_per_step": round(ms_q, 3), "s_per_source": round(ms_q / 1e3 / S, 6),
                         "iters": info_q[0]["iters"], "inner_solves": info_q[0]["restarts"],
                         "true_rel_residual": info_q[0]["true_rel_residual"]}
+        # SQMR with the multicolour SSOR preconditioner (the paper's SQMR + SOR runs), FP64, beside
+        # the Jacobi-split SQMR in FP64; a step includes the colouring (the mesh is renumbered)
+        if not args.no_ssor:
+            ms_s, info_s, _, _ = timed(api.PREC_C128, 1, 1, method=api.METHOD_SQMR, precond=api.PRECOND_SSOR)
+            timed(api.PREC_C128, 1, 0, profile=True, method=api.METHOD_SQMR, precond=api.PRECOND_SSOR)
+            sks = {}
+            for name in ("ssor_spmv", "ssor_forward", "ssor_backward", "ssor_residual"):
+                n_, kms, by = api.petgem_kernel_stats(ctx.h, name)
+                if n_:
+                    sks[name] = {"timed_scopes": n_, "ms": round(kms, 3), "gbs": round(by / (kms * 1e-3) / 1e9, 1)}
+            api.petgem_profile(ctx.h, False)
+            nc, nr = api.petgem_colouring(ctx.h)
+            ms_j, info_j, _, _ = timed(api.PREC_C128, 1, 1, method=api.METHOD_SQMR)
+            cocg["sqmr_ssor_c128"] = {
+                "ms_per_step": round(ms_s, 3), "s_per_source": round(ms_s / 1e3 / S, 6), "iters": info_s[0]["iters"],
+                "inner_solves": info_s[0]["restarts"], "true_rel_residual": info_s[0]["true_rel_residual"],
+                "omega": 1.0, "colours": nc, "colouring_rounds": nr, "kernels": sks,
+                "jacobi_sqmr_c128": {"ms_per_step": round(ms_j, 3), "iters": info_j[0]["iters"],
+                                     "true_rel_residual": info_j[0]["true_rel_residual"]}}
 
     # Multi-source block solve (all sources of one frequency in one SpMM-based solve): the marine
     # mesh with args.block_sources dipoles along x in [-4, 4] km; timed once after a warm-up.

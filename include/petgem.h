@@ -58,7 +58,7 @@ typedef struct {
 } petgem_dipole;
 
 enum { PETGEM_PREC_C128 = 0, PETGEM_PREC_MIXED = 1 };
-enum { PETGEM_PRECOND_JACOBI = 0, PETGEM_PRECOND_LEARNED = 1 };
+enum { PETGEM_PRECOND_JACOBI = 0, PETGEM_PRECOND_LEARNED = 1, PETGEM_PRECOND_SSOR = 2 };
 
 /* Solver options.  Restarted GMRES(restart), right-preconditioned by Jacobi D = diag(A),
  * x0 taken from the x argument, stopping when ||b - A x||_2 / ||b||_2 <= tol with the
@@ -74,7 +74,13 @@ enum { PETGEM_PRECOND_JACOBI = 0, PETGEM_PRECOND_LEARNED = 1 };
  *     z = s N(v / s) (N the network of petgem_learned_create, s the RMS of v, Jacobi-scaled
  *     variables) and whose even steps use Jacobi, with two-pass Gram-Schmidt.  The first cycle
  *     runs with Jacobi and measures its FP64 residual reduction; a learned cycle that does not
- *     beat it is undone and the solve continues with Jacobi alone (info.fell_back). */
+ *     beat it is undone and the solve continues with Jacobi alone (info.fell_back).
+ *   precond = PETGEM_PRECOND_SSOR (method SQMR, precision C128 only; PETGEM_ERR_UNSUPPORTED
+ *     otherwise): symmetric SOR, the preconditioner of the paper's Section 5.3 runs, in the
+ *     order of a multicolour colouring of the matrix graph (petgem_colouring): with A = D + L + U
+ *     split by colour, M = (D + omega L) D^{-1} (D + omega U), applied to SQMR as the symmetric
+ *     split M1 = (D + omega L) D^{-1/2}, M2 = M1^T.  Each SQMR step then costs a forward and a
+ *     backward sweep (one launch per colour each) besides the product. */
 typedef struct {
   int32_t restart;
   int32_t precision;
@@ -93,6 +99,7 @@ typedef struct {
                           many lanes per row, 1 = SELL-32 with rows grouped by edge kind (CSR with
                           4 lanes when a mesh lacks that layout); 0 = chosen by the autotuner;
                           ignored by petgem_solve (which uses SELL-32 when the mesh has it) */
+  double omega;        /* SSOR relaxation factor, 0 < omega < 2; 0 = 1 (symmetric Gauss-Seidel) */
 } petgem_solve_opts;
 
 /* Krylov method.
@@ -233,6 +240,25 @@ int petgem_solve_batch(petgem_ctx *const *ctxs, int32_t n_ctx, const petgem_solv
 
 /* y = A x for the assembled matrix (complex128, device, n_src = 1 vector of E entries). */
 int petgem_spmv(petgem_ctx *ctx, const void *x, void *y);
+
+/* Multicolour ordering of the SSOR preconditioner (Jones and Plassmann's parallel colouring):
+ * row i has the priority key (splitmix64(i), i), splitmix64 being the output function of Steele,
+ * Lea and Flood's SplitMix64 generator for the state i (add 0x9E3779B97F4A7C15; xor-shift 30,
+ * multiply by 0xBF58476D1CE4E5B9; xor-shift 27, multiply by 0x94D049BB133111EB; xor-shift 31;
+ * all modulo 2^64), keys compared lexicographically.  Each round, every uncoloured row whose key
+ * exceeds those of all its uncoloured neighbours (the off-diagonal columns of its pattern row)
+ * takes the smallest colour none of its coloured neighbours holds: the greedy colouring in
+ * decreasing key order.  Needs petgem_mesh_edges; computed once per mesh.
+ *   colour: device int32[E] (optional) receives each row's colour.
+ *   n_colours, n_rounds: host (optional) receive the number of colours and of rounds.
+ * Synchronises the stream.  Errors: PETGEM_ERR_UNSUPPORTED when a row would need more than 64
+ * colours (a row with more than 63 neighbours) or E >= 2^31. */
+int petgem_colouring(petgem_ctx *ctx, int32_t *colour, int32_t *n_colours, int32_t *n_rounds);
+
+/* z = M^{-1} r for the SSOR preconditioner above (forward sweep, scaling by D, backward sweep).
+ * r, z: device complex128[E], distinct.  omega as in petgem_solve_opts (0 = 1).  Needs
+ * petgem_assemble.  Synchronises the stream. */
+int petgem_ssor_apply(petgem_ctx *ctx, double omega, const void *r, void *z);
 
 /* ----------------------------------------------------------------------- receivers (eq. 7) */
 /* Field at receiver points.  rx: device double[n_rcv][3].  x: device complex128[n_src][E]

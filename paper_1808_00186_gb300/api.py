@@ -23,7 +23,7 @@ OK, ERR_INVALID_ARG, ERR_BAD_MESH, ERR_DEGENERATE_TET, ERR_OUT_OF_MEMORY, ERR_CU
     ERR_BREAKDOWN, ERR_RECEIVER_OUTSIDE, ERR_UNSUPPORTED, ERR_TIMEOUT = range(11)
 PREC_C128, PREC_MIXED = 0, 1
 ORTH_CGS2, ORTH_CGS, ORTH_CGS_IFNEEDED = 0, 1, 2
-PRECOND_JACOBI, PRECOND_LEARNED = 0, 1
+PRECOND_JACOBI, PRECOND_LEARNED, PRECOND_SSOR = 0, 1, 2
 METHOD_GMRES, METHOD_COCG, METHOD_SQMR = 0, 1, 2
 
 
@@ -36,7 +36,7 @@ class petgem_solve_opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("precision", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("max_iters", ctypes.c_int64), ("orth", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
-                ("method", ctypes.c_int32), ("spmv_lanes", ctypes.c_int32)]
+                ("method", ctypes.c_int32), ("spmv_lanes", ctypes.c_int32), ("omega", ctypes.c_double)]
 
 
 class petgem_solve_info(ctypes.Structure):
@@ -61,6 +61,8 @@ _SIGNATURES = {
     "petgem_solve_batch": (ctypes.c_int, [ctypes.POINTER(_P), _I32, ctypes.POINTER(petgem_solve_opts),
                                           ctypes.POINTER(_P), ctypes.POINTER(petgem_solve_info)]),
     "petgem_spmv": (ctypes.c_int, [_P, _P, _P]),
+    "petgem_colouring": (ctypes.c_int, [_P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "petgem_ssor_apply": (ctypes.c_int, [_P, _D, _P, _P]),
     "petgem_receivers": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     "petgem_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "petgem_kernel_stats": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.POINTER(_I64), ctypes.POINTER(_D),
@@ -174,9 +176,9 @@ def petgem_get_elements(ctx, K21=None, M21=None, vol=None):
 
 def solve_opts(restart=50, precision=PREC_C128, tol=1e-8, inner_tol=1e-4, max_iters=200000, batch=1,
                orth=ORTH_CGS, use_graphs=0, precond=PRECOND_JACOBI, method=METHOD_GMRES,
-               spmv_lanes=0) -> petgem_solve_opts:
+               spmv_lanes=0, omega=0.0) -> petgem_solve_opts:
     return petgem_solve_opts(restart, precision, precond, batch, tol, inner_tol, max_iters, orth, use_graphs, method,
-                             spmv_lanes)
+                             spmv_lanes, omega)
 
 
 def petgem_solve(ctx, x, n_src, opts=None, allow_not_converged=False):
@@ -209,6 +211,17 @@ def petgem_solve_batch(ctxs, xs, n_srcs, opts=None, allow_not_converged=False):
 
 def petgem_spmv(ctx, x, y):
     _check(ctx, load().petgem_spmv(ctx, _ptr(x), _ptr(y)))
+
+
+def petgem_colouring(ctx, colour=None):
+    """Returns (number of colours, rounds); colour: optional device int32[E] tensor to fill."""
+    nc, nr = _I32(0), _I32(0)
+    _check(ctx, load().petgem_colouring(ctx, _ptr(colour), ctypes.byref(nc), ctypes.byref(nr)))
+    return nc.value, nr.value
+
+
+def petgem_ssor_apply(ctx, omega, r, z):
+    _check(ctx, load().petgem_ssor_apply(ctx, omega, _ptr(r), _ptr(z)))
 
 
 def petgem_receivers(ctx, rx, x, out, allow_outside=False) -> int:
@@ -405,6 +418,19 @@ class Context:
         allow = opts.pop("allow_not_converged", False)
         st, info = petgem_solve(self.h, x, self.n_src, solve_opts(**opts), allow_not_converged=allow)
         return x, info, st
+
+    def colouring(self):
+        """(colour int32[E] device tensor, number of colours, rounds) of the SSOR ordering."""
+        tt = self.torch
+        colour = tt.empty(self.n_edges, dtype=tt.int32, device=self.nodes.device)
+        nc, nr = petgem_colouring(self.h, colour)
+        return colour, nc, nr
+
+    def ssor_apply(self, r, omega=1.0):
+        """z = M^{-1} r for the SSOR preconditioner (r: device complex128[E])."""
+        z = self.torch.empty_like(r)
+        petgem_ssor_apply(self.h, omega, r, z)
+        return z
 
     def receivers(self, rx, x, allow_outside=False):
         tt = self.torch

@@ -134,6 +134,7 @@ int petgem_destroy(petgem_ctx* c) {
   cudaStreamSynchronize(c->stream);
   petgem::destroy_solver(c);
   petgem::destroy_cocg(c);
+  petgem::destroy_ssor(c);
   delete c->net;
   c->net = nullptr;
   c->slots.release();
@@ -311,17 +312,27 @@ int petgem_solve(petgem_ctx* c, const petgem_solve_opts* opts, void* x, petgem_s
   if (opts) o = *opts;
   if (o.method != PETGEM_METHOD_GMRES && o.method != PETGEM_METHOD_COCG && o.method != PETGEM_METHOD_SQMR)
     return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve: unknown method"});
-  if (o.method != PETGEM_METHOD_GMRES && o.precond != PETGEM_PRECOND_JACOBI)
-    return finish(c, Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve: COCG and SQMR take the Jacobi preconditioner only"});
+  if (o.precond == PETGEM_PRECOND_SSOR) {
+    if (o.method != PETGEM_METHOD_SQMR || o.precision != PETGEM_PREC_C128)
+      return finish(c, Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve: SSOR preconditions complex128 SQMR only"});
+    if (o.omega == 0.0) o.omega = 1.0;
+    if (!(o.omega > 0.0 && o.omega < 2.0))
+      return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve: SSOR needs 0 < omega < 2"});
+  } else if (o.method != PETGEM_METHOD_GMRES && o.precond != PETGEM_PRECOND_JACOBI) {
+    return finish(c, Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve: COCG takes the Jacobi preconditioner only"});
+  }
   if (!(o.tol > 0.0) || o.max_iters < 0 || (o.precision != PETGEM_PREC_C128 && o.precision != PETGEM_PREC_MIXED) ||
-      (o.precond != PETGEM_PRECOND_JACOBI && o.precond != PETGEM_PRECOND_LEARNED) ||
+      (o.precond != PETGEM_PRECOND_JACOBI && o.precond != PETGEM_PRECOND_LEARNED &&
+       o.precond != PETGEM_PRECOND_SSOR) ||
       !(o.inner_tol >= 0.0 && o.inner_tol < 1.0) || o.orth < 0 ||
       o.orth > PETGEM_ORTH_CGS_IFNEEDED)
     return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve: bad options"});
   if (o.precond == PETGEM_PRECOND_LEARNED && (!c->net || !c->slots_ready))
     return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve: learned preconditioner needs petgem_learned_create"});
   Status s = set_device(c);
-  if (s.ok()) s = petgem::run_solve(c, o, static_cast<double2*>(x), info);
+  if (s.ok())
+    s = o.precond == PETGEM_PRECOND_SSOR ? petgem::run_solve_ssor(c, o, static_cast<double2*>(x), info)
+                                         : petgem::run_solve(c, o, static_cast<double2*>(x), info);
   if (s.code == PETGEM_ERR_CUDA || s.code == PETGEM_ERR_OUT_OF_MEMORY) cudaGetLastError();
   return finish(c, s);
 }
@@ -363,6 +374,33 @@ int petgem_spmv(petgem_ctx* c, const void* x, void* y) {
   if (!c->assembled || !x || !y) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_spmv: not assembled or null"});
   Status s = set_device(c);
   if (s.ok()) s = petgem::run_spmv(c, static_cast<const double2*>(x), static_cast<double2*>(y));
+  return finish(c, s);
+}
+
+int petgem_colouring(petgem_ctx* c, int32_t* colour, int32_t* n_colours, int32_t* n_rounds) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (c->n_edges == 0) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_colouring: call petgem_mesh_edges first"});
+  Status s = set_device(c);
+  if (s.ok()) s = petgem::ssor_colouring(c);
+  if (s.ok() && colour) {
+    cudaError_t e = cudaMemcpyAsync(colour, c->ss_colour.ptr, c->n_edges * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                    c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) s = Status{PETGEM_ERR_CUDA, cudaGetErrorString(e)};
+  }
+  if (s.ok() && n_colours) *n_colours = (int32_t)c->ss_off.size() - 1;
+  if (s.ok() && n_rounds) *n_rounds = c->ss_rounds;
+  return finish(c, s);
+}
+
+int petgem_ssor_apply(petgem_ctx* c, double omega, const void* r, void* z) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (!c->assembled || !r || !z) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_ssor_apply: not assembled or null"});
+  if (omega == 0.0) omega = 1.0;
+  if (!(omega > 0.0 && omega < 2.0)) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_ssor_apply: 0 < omega < 2"});
+  if (r == z) return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_ssor_apply: r and z must not alias"});
+  Status s = set_device(c);
+  if (s.ok()) s = petgem::run_ssor_apply(c, omega, static_cast<const double2*>(r), static_cast<double2*>(z));
   return finish(c, s);
 }
 

@@ -78,6 +78,13 @@ struct petgem_ctx {
   petgem::DevBuf sell_perm, sell_inv;      // renumbered row r holds edge perm[r]; inv = perm^-1
   petgem::DevBuf sell_sp, sell_col, sell_src;  // slice offsets, columns, CSR entry per slot (-1 pad)
 
+  // ---- multicolour SSOR (ssor.cu): colour of each row, rows grouped by colour, group offsets
+  int64_t ss_version = -1;                 // mesh version the colouring belongs to
+  int32_t ss_rounds = 0;                   // Jones-Plassmann rounds it took
+  petgem::DevBuf ss_colour, ss_rows;
+  std::vector<int64_t> ss_off;             // rows of colour k: ss_rows[ss_off[k] .. ss_off[k + 1])
+  void* ssor = nullptr;                    // SSOR-SQMR workspaces
+
   // ---- assembly
   bool assembled = false;
   int64_t assembly_version = 0;
@@ -143,6 +150,10 @@ Status run_solve_cocg(petgem_ctx* c, const petgem_solve_opts& o, double2* x, pet
 Status run_solve_batch(petgem_ctx* const* ctxs, int n_ctx, const petgem_solve_opts& o, double2* const* x,
                        petgem_solve_info* info);
 Status run_spmv(petgem_ctx* c, const double2* x, double2* y);
+Status ssor_colouring(petgem_ctx* c);
+Status run_solve_ssor(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info);
+Status run_ssor_apply(petgem_ctx* c, double omega, const double2* r, double2* z);
+void destroy_ssor(petgem_ctx* c);
 void destroy_solver(petgem_ctx* c);
 void destroy_cocg(petgem_ctx* c);
 

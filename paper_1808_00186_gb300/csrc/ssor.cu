@@ -1,0 +1,643 @@
+// Multicolour symmetric SOR (SSOR) preconditioner and the SQMR solver it preconditions, complex128:
+// the configuration of the paper's Section 5.3 runs (SQMR with an SOR preconditioner).
+//
+// Colouring.  A Gauss-Seidel sweep is sequential row by row; on the GPU the rows are coloured so
+// that rows of one colour share no matrix entry and the sweep takes one colour per launch, all its
+// rows at once.  The colouring is Jones-Plassmann's: row i has the priority key
+// (splitmix64(i), i) (SplitMix64's output function, Steele, Lea and Flood 2014); in round k every
+// uncoloured row whose key exceeds those of all its uncoloured neighbours takes the smallest colour
+// none of its coloured neighbours holds.  The result is the greedy colouring in decreasing key
+// order, deterministic and independent of the launch shape.  Neighbours are the off-diagonal
+// entries of the CSR pattern; a Kuhn mesh's edge matrix takes about 12 colours in about 35 rounds.
+//
+// SSOR.  With A = D + L + U split in the colour order (L: entries whose column has a lower colour
+// than the row, U: a higher one), M = (D + w L) D^{-1} (D + w U), complex symmetric because
+// U = L^T.  SQMR takes the symmetric split M1 = (D + w L) D^{-1/2}, M2 = M1^T:
+//   M1^{-1} v = D^{1/2} F v and M2^{-1} t = B D^{1/2} t, F = (D + w L)^{-1} (forward sweep),
+//   B = (D + w U)^{-1} (backward sweep).
+// Neither D^{1/2} is formed: SQMR needs ||M1^{-1} r||, whose squares are |d_i| |(F r)_i|^2, and
+// M2^{-1} M1^{-1} r = B (D F r), whose backward sweep reads y = F r directly:
+//   forward, colours ascending:  y_i = (r_i - w sum_{col(j) < col(i)} a_ij y_j) / d_i
+//   backward, colours descending: u_i = y_i - (w / d_i) sum_{col(j) > col(i)} a_ij u_j.
+//
+// SQMR (Freund and Nachtigal 1994), in the order of the method: t = A q; sigma = q^T t;
+// alpha = rho / sigma; r -= alpha t; y = F r; theta' = ||D^{1/2} y|| / tau; c^2 = 1 / (1 + theta'^2);
+// tau = tau theta' c; d = c^2 theta^2 d + c^2 alpha q; x += d; u = B D y; rho' = r^T u;
+// beta = rho' / rho; q = u + beta q.  The kernels fuse neighbouring steps: the residual update into
+// the forward sweep, the d and x updates and rho' into the backward sweep, and the direction update
+// into the next product (q_new = u + beta q_old formed on the fly, double-buffered).  Every
+// reduction writes one partial per block; a one-block kernel sums them in a fixed order and forms
+// the scalars on the device.  No kernel waits on another: the iterations are plain launches, and
+// the host reads the state every kSsChunk iterations.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ctx.cuh"
+
+namespace petgem {
+namespace {
+
+constexpr int kSsLanes = 4;     // lanes per row (rows hold at most ~19 entries)
+constexpr int kSsThreads = 256;
+constexpr int kSsMaxColours = 64;
+constexpr int kSsChunk = 16;    // iterations enqueued between host reads of the state
+
+struct SsState {
+  double2 rho, sigma, alpha, beta, dc2, sum;
+  double tau, tau_stop, theta, dc1;
+  long long k, kmax;
+  int done;    // 0 running; 1 stop test met or budget used; 2 breakdown of the bilinear form
+  int finish;  // the stop test was met in this iteration: done follows once x is updated
+};
+
+struct SsBuffers {
+  DevBuf inv_d, absd, r, t, y, u, qa, qb, dv, state, part;
+};
+
+__device__ __forceinline__ unsigned long long ss_key(unsigned long long s) {
+  unsigned long long z = s + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// One Jones-Plassmann round.  rnd[i]: the round row i was coloured in (-1: not yet).  A neighbour
+// coloured in this same round counts as uncoloured (it was when the round began); its colour is
+// never read in this round.
+__global__ void k_jp_round(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int64_t n, int32_t round,
+                           int32_t* __restrict__ rnd, int32_t* __restrict__ colour,
+                           unsigned long long* __restrict__ coloured, int32_t* __restrict__ overflow) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  bool chosen = false;
+  if (i < n && rnd[i] < 0) {
+    const unsigned long long ki = ss_key((unsigned long long)i);
+    unsigned long long used = 0;
+    bool waits = false;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      const int32_t j = col[p];
+      if (j == i) continue;
+      const int32_t rj = rnd[j];
+      if (rj < 0 || rj == round) {
+        const unsigned long long kj = ss_key((unsigned long long)j);
+        if (kj > ki || (kj == ki && j > i)) {
+          waits = true;
+          break;
+        }
+      } else {
+        used |= 1ull << colour[j];
+      }
+    }
+    if (!waits) {
+      if (used == ~0ull) {
+        *overflow = 1;
+      } else {
+        colour[i] = __ffsll((long long)~used) - 1;
+        rnd[i] = round;
+        chosen = true;
+      }
+    }
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, chosen);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(coloured, (unsigned long long)__popc(m));
+}
+
+__global__ void k_ss_flag(const int32_t* __restrict__ colour, int64_t n, int32_t c, int32_t* __restrict__ flag) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = colour[i] == c;
+}
+
+__global__ void k_ss_place(const int32_t* __restrict__ flag, const int64_t* __restrict__ rank, int64_t n, int64_t base,
+                           int32_t* __restrict__ rows) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n && flag[i]) rows[base + rank[i]] = (int32_t)i;
+}
+
+// 1 / d_i and |d_i|.
+__global__ void k_ss_diag(const double2* __restrict__ d, int64_t n, double2* __restrict__ inv_d,
+                          double* __restrict__ absd) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 di = d[i];
+  inv_d[i] = cdiv(make_double2(1.0, 0.0), di);
+  absd[i] = sqrt(cabs2(di));
+}
+
+__device__ __forceinline__ double2 ss_lanes_sum(double2 a) {
+  for (int o = 1; o < kSsLanes; o <<= 1) {
+    a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+    a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+  }
+  return a;
+}
+
+// Block sum of v (fixed order), written by thread 0 to *out.
+__device__ __forceinline__ void ss_block_partial(double2 v, double2* out) {
+  __shared__ double2 sh[kSsThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 s = sh[0];
+    for (int w = 1; w < kSsThreads / 32; ++w) s = cadd(s, sh[w]);
+    *out = s;
+  }
+}
+
+// r = b - A x with partial sums of |r_i|^2 (mode 0), or partial sums of |v_i|^2 (mode 1: v = b).
+__global__ void __launch_bounds__(kSsThreads) k_ss_residual(const int64_t* __restrict__ rp,
+                                                            const int32_t* __restrict__ col,
+                                                            const double2* __restrict__ val,
+                                                            const double2* __restrict__ x,
+                                                            const double2* __restrict__ b, int64_t n, int mode,
+                                                            double2* __restrict__ r, double2* __restrict__ part) {
+  const int64_t i = (blockIdx.x * (int64_t)kSsThreads + threadIdx.x) / kSsLanes;
+  const int lane = threadIdx.x & (kSsLanes - 1);
+  double2 acc = make_double2(0.0, 0.0);
+  if (mode == 0 && i < n)
+    for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += kSsLanes) acc = cadd(acc, cmul(val[p], x[col[p]]));
+  acc = ss_lanes_sum(acc);
+  double s = 0.0;
+  if (i < n && lane == 0) {
+    const double2 ri = mode == 0 ? csub(b[i], acc) : b[i];
+    if (mode == 0) r[i] = ri;
+    s = cabs2(ri);
+  }
+  ss_block_partial(make_double2(s, 0.0), part + blockIdx.x);
+}
+
+// Forward sweep over the rows of colour c (rows[0..cnt)): with iter, first r_i -= alpha t_i; then
+// y_i = (r_i - w sum_{col(j) < c} a_ij y_j) / d_i; partial sums of |d_i| |y_i|^2.
+__global__ void __launch_bounds__(kSsThreads) k_ss_forward(const int64_t* __restrict__ rp,
+                                                           const int32_t* __restrict__ col,
+                                                           const double2* __restrict__ val,
+                                                           const int32_t* __restrict__ colour,
+                                                           const int32_t* __restrict__ rows, int64_t cnt, int32_t c,
+                                                           double omega, const double2* __restrict__ inv_d,
+                                                           const double* __restrict__ absd,
+                                                           const double2* __restrict__ t, double2* __restrict__ r,
+                                                           double2* __restrict__ y, const SsState* __restrict__ st,
+                                                           double2* __restrict__ part, int iter) {
+  if (st->done) return;
+  const int64_t g = (blockIdx.x * (int64_t)kSsThreads + threadIdx.x) / kSsLanes;
+  const int lane = threadIdx.x & (kSsLanes - 1);
+  const int32_t i = g < cnt ? rows[g] : -1;
+  double2 acc = make_double2(0.0, 0.0);
+  if (i >= 0)
+    for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += kSsLanes) {
+      const int32_t j = col[p];
+      if (colour[j] < c) acc = cadd(acc, cmul(val[p], y[j]));
+    }
+  acc = ss_lanes_sum(acc);
+  double s = 0.0;
+  if (i >= 0 && lane == 0) {
+    double2 ri = r[i];
+    if (iter) {
+      ri = csub(ri, cmul(st->alpha, t[i]));
+      r[i] = ri;
+    }
+    const double2 yi = cmul(csub(ri, cscale(acc, omega)), inv_d[i]);
+    y[i] = yi;
+    s = absd[i] * cabs2(yi);
+  }
+  ss_block_partial(make_double2(s, 0.0), part + blockIdx.x);
+}
+
+// Backward sweep over the rows of colour c: u_i = y_i - (w / d_i) sum_{col(j) > c} a_ij u_j; with
+// iter, d_i = dc1 d_i + dc2 q_i and x_i += d_i, else d_i = 0; partial sums of r_i u_i.
+__global__ void __launch_bounds__(kSsThreads) k_ss_backward(const int64_t* __restrict__ rp,
+                                                            const int32_t* __restrict__ col,
+                                                            const double2* __restrict__ val,
+                                                            const int32_t* __restrict__ colour,
+                                                            const int32_t* __restrict__ rows, int64_t cnt, int32_t c,
+                                                            double omega, const double2* __restrict__ inv_d,
+                                                            const double2* __restrict__ y, double2* __restrict__ u,
+                                                            const double2* __restrict__ r,
+                                                            const double2* __restrict__ q, double2* __restrict__ dv,
+                                                            double2* __restrict__ x, const SsState* __restrict__ st,
+                                                            double2* __restrict__ part, int iter) {
+  if (st->done) return;
+  const int64_t g = (blockIdx.x * (int64_t)kSsThreads + threadIdx.x) / kSsLanes;
+  const int lane = threadIdx.x & (kSsLanes - 1);
+  const int32_t i = g < cnt ? rows[g] : -1;
+  double2 acc = make_double2(0.0, 0.0);
+  if (i >= 0)
+    for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += kSsLanes) {
+      const int32_t j = col[p];
+      if (colour[j] > c) acc = cadd(acc, cmul(val[p], u[j]));
+    }
+  acc = ss_lanes_sum(acc);
+  double2 s = make_double2(0.0, 0.0);
+  if (i >= 0 && lane == 0) {
+    const double2 ui = csub(y[i], cscale(cmul(inv_d[i], acc), omega));
+    u[i] = ui;
+    if (iter) {
+      const double2 di = cadd(cscale(dv[i], st->dc1), cmul(st->dc2, q[i]));
+      dv[i] = di;
+      x[i] = cadd(x[i], di);
+    } else {
+      dv[i] = make_double2(0.0, 0.0);
+    }
+    s = cmul(r[i], ui);
+  }
+  ss_block_partial(s, part + blockIdx.x);
+}
+
+// t = A q_new with q_new = u + beta q_old formed on the fly (first: q_new = u); writes q_new and
+// partial sums of q_new^T t.
+__global__ void __launch_bounds__(kSsThreads) k_ss_spmv(const int64_t* __restrict__ rp,
+                                                        const int32_t* __restrict__ col,
+                                                        const double2* __restrict__ val, int64_t n,
+                                                        const double2* __restrict__ u,
+                                                        const double2* __restrict__ qold, double2* __restrict__ qnew,
+                                                        double2* __restrict__ t, const SsState* __restrict__ st,
+                                                        double2* __restrict__ part, int first) {
+  if (st->done) return;
+  const int64_t i = (blockIdx.x * (int64_t)kSsThreads + threadIdx.x) / kSsLanes;
+  const int lane = threadIdx.x & (kSsLanes - 1);
+  const double2 beta = st->beta;
+  double2 acc = make_double2(0.0, 0.0);
+  if (i < n)
+    for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += kSsLanes) {
+      const int32_t j = col[p];
+      const double2 qj = first ? u[j] : cadd(u[j], cmul(beta, qold[j]));
+      acc = cadd(acc, cmul(val[p], qj));
+    }
+  acc = ss_lanes_sum(acc);
+  double2 s = make_double2(0.0, 0.0);
+  if (i < n && lane == 0) {
+    const double2 qi = first ? u[i] : cadd(u[i], cmul(beta, qold[i]));
+    qnew[i] = qi;
+    t[i] = acc;
+    s = cmul(qi, acc);
+  }
+  ss_block_partial(s, part + blockIdx.x);
+}
+
+// Sum of np partials (fixed order) and the scalar step of a stage:
+//   0  after the first forward sweep: tau = tau0 = sqrt(sum); stop at tau <= arg tau0
+//   1  after the first backward sweep: rho = sum
+//   2  after the product: sigma = sum, alpha = rho / sigma (breakdown: sigma or rho zero)
+//   3  after the forward sweep: theta, c^2, tau, the coefficients of d; stop test
+//   4  after the backward sweep: rho' = sum, beta = rho' / rho
+//   5  plain sum (norms of the outer loop)
+template <int STAGE>
+__global__ void __launch_bounds__(kSsThreads) k_ss_scalar(SsState* __restrict__ st, const double2* __restrict__ part,
+                                                          int64_t np, double arg, long long kmax) {
+  if (STAGE >= 2 && STAGE <= 4 && st->done) return;
+  double2 v = make_double2(0.0, 0.0);
+  for (int64_t k = threadIdx.x; k < np; k += kSsThreads) v = cadd(v, part[k]);
+  __shared__ double2 tot;
+  {
+    __shared__ double2 sh[kSsThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double2 s = sh[0];
+      for (int w = 1; w < kSsThreads / 32; ++w) s = cadd(s, sh[w]);
+      tot = s;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double2 sum = tot;
+  if (STAGE == 0) {
+    st->tau = sqrt(sum.x);
+    st->tau_stop = arg * st->tau;
+    st->theta = 0.0;
+    st->k = 0;
+    st->kmax = kmax;
+    st->finish = 0;
+    st->beta = make_double2(0.0, 0.0);
+    st->done = !isfinite(st->tau) ? 2 : (st->tau == 0.0 || kmax <= 0 ? 1 : 0);
+  } else if (STAGE == 1) {
+    st->rho = sum;
+  } else if (STAGE == 2) {
+    st->sigma = sum;
+    if (cabs2(sum) == 0.0 || cabs2(st->rho) == 0.0 || !isfinite(sum.x) || !isfinite(sum.y)) {
+      st->done = 2;
+      return;
+    }
+    st->alpha = cdiv(st->rho, sum);
+  } else if (STAGE == 3) {
+    const double th = sqrt(sum.x) / st->tau;
+    const double c2 = 1.0 / (1.0 + th * th);
+    st->dc1 = c2 * st->theta * st->theta;
+    st->dc2 = cscale(st->alpha, c2);
+    st->tau = st->tau * th * sqrt(c2);
+    st->theta = th;
+    st->k += 1;
+    if (!(st->tau > st->tau_stop) || st->k >= st->kmax) st->finish = 1;  // NaN tau stops too
+  } else if (STAGE == 4) {
+    st->beta = cdiv(sum, st->rho);
+    st->rho = sum;
+    if (st->finish) st->done = 1;
+  } else {
+    st->sum = sum;
+  }
+}
+
+SsBuffers* ss_bufs(petgem_ctx* c) {
+  if (!c->ssor) c->ssor = new SsBuffers();
+  return static_cast<SsBuffers*>(c->ssor);
+}
+
+}  // namespace
+
+Status ssor_colouring(petgem_ctx* c) {
+  if (c->ss_version == c->mesh_version) return Status{};
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n_edges;
+  if (n >= (1ll << 31)) return Status{PETGEM_ERR_UNSUPPORTED, "SSOR colouring: more than 2^31 rows"};
+  PG_TRY(c->ss_colour.reserve(n * sizeof(int32_t)));
+  PG_TRY(c->ss_rows.reserve(n * sizeof(int32_t)));
+  DevBuf work;
+  PG_TRY(work.reserve((size_t)n * 4 + 64 + (size_t)(n + 1) * 8 + 64));
+  int32_t* rnd = work.as<int32_t>();  // later reused as the flags of one colour
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(work.ptr) + ((n * 4 + 15) / 16) * 16);
+  int32_t* overflow = reinterpret_cast<int32_t*>(ctr + 1);
+  int64_t* rank = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(ctr) + 64);
+  int32_t* colour = c->ss_colour.as<int32_t>();
+  auto body = [&]() -> Status {
+    PG_CUDA(cudaMemsetAsync(rnd, 0xff, n * sizeof(int32_t), s));
+    PG_CUDA(cudaMemsetAsync(colour, 0xff, n * sizeof(int32_t), s));
+    PG_CUDA(cudaMemsetAsync(ctr, 0, 16, s));
+    int32_t round = 0;
+    while (true) {
+      if (round > n) return Status{PETGEM_ERR_CUDA, "SSOR colouring made no progress"};
+      k_jp_round<<<blocks_for(n, 256), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), n, round, rnd,
+                                                    colour, ctr, overflow);
+      c->launches++;
+      PG_CUDA(cudaGetLastError());
+      ++round;
+      unsigned long long h[2] = {0, 0};
+      PG_CUDA(cudaMemcpyAsync(h, ctr, 16, cudaMemcpyDeviceToHost, s));
+      PG_CUDA(cudaStreamSynchronize(s));
+      if ((int32_t)h[1] != 0)
+        return Status{PETGEM_ERR_UNSUPPORTED, "SSOR colouring: a row needs more than 64 colours"};
+      if ((int64_t)h[0] >= n) break;
+    }
+    // rows grouped by colour, ascending row ids inside a colour
+    c->ss_off.assign(1, 0);
+    for (int32_t k = 0; c->ss_off.back() < n; ++k) {
+      if (k >= kSsMaxColours) return Status{PETGEM_ERR_CUDA, "SSOR colouring: colours do not cover the rows"};
+      k_ss_flag<<<blocks_for(n, 256), 256, 0, s>>>(colour, n, k, rnd);
+      c->launches++;
+      PG_CUDA(cudaGetLastError());
+      PG_TRY(exclusive_scan(rnd, rank, n, s));
+      k_ss_place<<<blocks_for(n, 256), 256, 0, s>>>(rnd, rank, n, c->ss_off.back(), c->ss_rows.as<int32_t>());
+      c->launches++;
+      PG_CUDA(cudaGetLastError());
+      int64_t cnt = 0;
+      PG_CUDA(cudaMemcpyAsync(&cnt, rank + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      PG_CUDA(cudaStreamSynchronize(s));
+      c->ss_off.push_back(c->ss_off.back() + cnt);
+    }
+    c->ss_rounds = round;
+    return Status{};
+  };
+  const Status st = body();
+  cudaStreamSynchronize(s);  // the work buffer is released on return
+  work.release();
+  if (!st.ok()) {
+    c->ss_off.clear();
+    return st;
+  }
+  c->ss_version = c->mesh_version;
+  return Status{};
+}
+
+namespace {
+
+struct SsLaunch {
+  petgem_ctx* c;
+  SsBuffers* B;
+  int64_t n, nb, np_sweep;
+  double omega;
+  std::vector<int64_t> pbase;  // first partial of each colour's sweep launch
+};
+
+Status ss_setup(petgem_ctx* c, double omega, SsLaunch& L) {
+  PG_TRY(ssor_colouring(c));
+  SsBuffers* B = ss_bufs(c);
+  const int64_t n = c->n_edges;
+  for (DevBuf* d : {&B->inv_d, &B->r, &B->t, &B->y, &B->u, &B->qa, &B->qb, &B->dv}) PG_TRY(d->reserve(n * sizeof(double2)));
+  PG_TRY(B->absd.reserve(n * sizeof(double)));
+  PG_TRY(B->state.reserve(sizeof(SsState)));
+  const int ncol = (int)c->ss_off.size() - 1;
+  L.c = c;
+  L.B = B;
+  L.n = n;
+  L.nb = blocks_for(n * kSsLanes, kSsThreads);
+  L.omega = omega;
+  L.pbase.assign(ncol + 1, 0);
+  for (int k = 0; k < ncol; ++k)
+    L.pbase[k + 1] = L.pbase[k] + blocks_for((c->ss_off[k + 1] - c->ss_off[k]) * kSsLanes, kSsThreads);
+  L.np_sweep = L.pbase[ncol];
+  PG_TRY(B->part.reserve((size_t)std::max<int64_t>(L.np_sweep, L.nb) * sizeof(double2)));
+  PG_CUDA(cudaMemsetAsync(B->state.ptr, 0, sizeof(SsState), c->stream));
+  k_ss_diag<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->diag.as<double2>(), n, B->inv_d.as<double2>(),
+                                                       B->absd.as<double>());
+  c->launches++;
+  PG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+// One sweep over all colours (ascending for the forward one).
+Status ss_forward(const SsLaunch& L, const double2* t, double2* r, double2* y, int iter) {
+  petgem_ctx* c = L.c;
+  const int ncol = (int)c->ss_off.size() - 1;
+  const double bytes = (double)c->nnz * 24 + 8.0 * (L.n + 1) + (double)L.n * (4 + 16 * 6 + 8);
+  KernelTimer kt(c, "ssor_forward", bytes);
+  for (int k = 0; k < ncol; ++k) {
+    const int64_t cnt = c->ss_off[k + 1] - c->ss_off[k];
+    if (cnt == 0) continue;
+    k_ss_forward<<<blocks_for(cnt * kSsLanes, kSsThreads), kSsThreads, 0, c->stream>>>(
+        c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(), c->ss_colour.as<int32_t>(),
+        c->ss_rows.as<int32_t>() + c->ss_off[k], cnt, k, L.omega, L.B->inv_d.as<double2>(), L.B->absd.as<double>(), t,
+        r, y, L.B->state.as<SsState>(), L.B->part.as<double2>() + L.pbase[k], iter);
+    c->launches++;
+  }
+  PG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+Status ss_backward(const SsLaunch& L, const double2* y, double2* u, const double2* r, const double2* q, double2* x,
+                   int iter) {
+  petgem_ctx* c = L.c;
+  const int ncol = (int)c->ss_off.size() - 1;
+  const double bytes = (double)c->nnz * 24 + 8.0 * (L.n + 1) + (double)L.n * (4 + 16 * (iter ? 9 : 5));
+  KernelTimer kt(c, "ssor_backward", bytes);
+  for (int k = ncol - 1; k >= 0; --k) {
+    const int64_t cnt = c->ss_off[k + 1] - c->ss_off[k];
+    if (cnt == 0) continue;
+    k_ss_backward<<<blocks_for(cnt * kSsLanes, kSsThreads), kSsThreads, 0, c->stream>>>(
+        c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(), c->ss_colour.as<int32_t>(),
+        c->ss_rows.as<int32_t>() + c->ss_off[k], cnt, k, L.omega, L.B->inv_d.as<double2>(), y, u, r, q,
+        L.B->dv.as<double2>(), x, L.B->state.as<SsState>(), L.B->part.as<double2>() + L.pbase[k], iter);
+    c->launches++;
+  }
+  PG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+template <int STAGE>
+Status ss_scalar(const SsLaunch& L, int64_t np, double arg = 0.0, long long kmax = 0) {
+  k_ss_scalar<STAGE><<<1, kSsThreads, 0, L.c->stream>>>(L.B->state.as<SsState>(), L.B->part.as<double2>(), np, arg,
+                                                        kmax);
+  L.c->launches++;
+  PG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+Status ss_read(const SsLaunch& L, SsState* h) {
+  PG_CUDA(cudaMemcpyAsync(h, L.B->state.ptr, sizeof(SsState), cudaMemcpyDeviceToHost, L.c->stream));
+  PG_CUDA(cudaStreamSynchronize(L.c->stream));
+  return Status{};
+}
+
+// ||v||^2 (mode 1) or ||b - A x||^2 into r (mode 0).
+Status ss_norm2(const SsLaunch& L, const double2* x, const double2* v, int mode, double* out) {
+  petgem_ctx* c = L.c;
+  {
+    KernelTimer kt(c, mode == 0 ? "ssor_residual" : "ssor_norm", mode == 0 ? (double)c->nnz * 20 + 8.0 * (L.n + 1) + 48.0 * L.n : 16.0 * L.n);
+    k_ss_residual<<<L.nb, kSsThreads, 0, c->stream>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(),
+                                                      c->val.as<double2>(), x, v, L.n, mode, L.B->r.as<double2>(),
+                                                      L.B->part.as<double2>());
+    c->launches++;
+  }
+  PG_CUDA(cudaGetLastError());
+  PG_TRY(ss_scalar<5>(L, L.nb));
+  SsState h;
+  PG_TRY(ss_read(L, &h));
+  *out = h.sum.x;
+  return Status{};
+}
+
+Status ssor_sqmr_source(const SsLaunch& L, const petgem_solve_opts& o, const double2* b, double2* x,
+                        petgem_solve_info& inf) {
+  petgem_ctx* c = L.c;
+  SsBuffers* B = L.B;
+  const int64_t n = L.n;
+  double2 *r = B->r.as<double2>(), *t = B->t.as<double2>(), *y = B->y.as<double2>(), *u = B->u.as<double2>();
+  double2* qbuf[2] = {B->qa.as<double2>(), B->qb.as<double2>()};
+  double bn2 = 0.0;
+  PG_TRY(ss_norm2(L, x, b, 1, &bn2));
+  const double bnorm = sqrt(bn2);
+  if (bnorm == 0.0) {
+    PG_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), c->stream));
+    inf.status = PETGEM_OK;
+    return Status{};
+  }
+  const double spmv_bytes = (double)c->nnz * 20 + 8.0 * (n + 1) + 16.0 * n * 5;
+  int64_t iters = 0, solves = 0;
+  double relres = 0.0, prev = INFINITY;
+  int status = PETGEM_OK, stalls = 0;
+  SsState hs;
+  while (true) {
+    double rn2 = 0.0;
+    PG_TRY(ss_norm2(L, x, b, 0, &rn2));
+    relres = sqrt(rn2) / bnorm;
+    if (!std::isfinite(relres)) {
+      status = PETGEM_ERR_BREAKDOWN;
+      break;
+    }
+    if (relres <= o.tol) break;
+    if (iters >= o.max_iters) {
+      status = PETGEM_ERR_NOT_CONVERGED;
+      break;
+    }
+    stalls = relres > 0.5 * prev ? stalls + 1 : 0;  // restarts at the rounding floor
+    if (stalls >= 3) {
+      status = PETGEM_ERR_NOT_CONVERGED;
+      break;
+    }
+    prev = relres;
+    // inner target on tau, relative to its start: what the final tolerance still needs, with a
+    // margin for the difference between tau and the true residual
+    const double inner = 0.3 * o.tol * bnorm / sqrt(rn2);
+    PG_CUDA(cudaMemsetAsync(B->state.ptr, 0, sizeof(SsState), c->stream));  // running again
+    PG_TRY(ss_forward(L, nullptr, r, y, 0));
+    PG_TRY(ss_scalar<0>(L, L.np_sweep, inner, (long long)(o.max_iters - iters)));
+    PG_TRY(ss_backward(L, y, u, r, nullptr, x, 0));
+    PG_TRY(ss_scalar<1>(L, L.np_sweep));
+    int cur = 0;
+    for (int64_t it = 0;; ++it) {
+      {
+        KernelTimer kt(c, "ssor_spmv", spmv_bytes);
+        k_ss_spmv<<<L.nb, kSsThreads, 0, c->stream>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(),
+                                                      c->val.as<double2>(), n, u, qbuf[cur], qbuf[cur ^ 1], t,
+                                                      B->state.as<SsState>(), B->part.as<double2>(), it == 0);
+        c->launches++;
+      }
+      PG_CUDA(cudaGetLastError());
+      cur ^= 1;  // q_new
+      PG_TRY(ss_scalar<2>(L, L.nb));
+      PG_TRY(ss_forward(L, t, r, y, 1));
+      PG_TRY(ss_scalar<3>(L, L.np_sweep));
+      PG_TRY(ss_backward(L, y, u, r, qbuf[cur], x, 1));
+      PG_TRY(ss_scalar<4>(L, L.np_sweep));
+      if ((it + 1) % kSsChunk == 0) {
+        PG_TRY(ss_read(L, &hs));
+        if (hs.done) break;
+      }
+    }
+    iters += hs.k;
+    solves += 1;
+    if (hs.done == 2 && hs.k == 0) {  // the bilinear form broke down at once: no progress possible
+      status = PETGEM_ERR_BREAKDOWN;
+      break;
+    }
+  }
+  inf.iters = iters;
+  inf.restarts = solves;
+  inf.refinements = solves;
+  inf.true_rel_residual = relres;
+  inf.status = status;
+  return Status{};
+}
+
+}  // namespace
+
+Status run_solve_ssor(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info) {
+  SsLaunch L;
+  PG_TRY(ss_setup(c, o.omega, L));
+  Status worst;
+  for (int32_t src = 0; src < c->n_src; ++src) {
+    petgem_solve_info& inf = info[src];
+    inf = petgem_solve_info{};
+    PG_TRY(ssor_sqmr_source(L, o, c->b.as<double2>() + (int64_t)src * L.n, x + (int64_t)src * L.n, inf));
+    if (inf.status != PETGEM_OK && worst.ok())
+      worst = Status{inf.status, "source " + std::to_string(src) + " did not converge (SQMR, SSOR)"};
+  }
+  PG_CUDA(cudaStreamSynchronize(c->stream));
+  return worst;
+}
+
+Status run_ssor_apply(petgem_ctx* c, double omega, const double2* r_in, double2* z) {
+  SsLaunch L;
+  PG_TRY(ss_setup(c, omega, L));
+  PG_CUDA(cudaMemcpyAsync(L.B->r.ptr, r_in, L.n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  PG_TRY(ss_forward(L, nullptr, L.B->r.as<double2>(), L.B->y.as<double2>(), 0));
+  PG_TRY(ss_backward(L, L.B->y.as<double2>(), z, L.B->r.as<double2>(), nullptr, nullptr, 0));
+  PG_CUDA(cudaStreamSynchronize(c->stream));
+  return Status{};
+}
+
+void destroy_ssor(petgem_ctx* c) {
+  if (!c->ssor) return;
+  SsBuffers* B = static_cast<SsBuffers*>(c->ssor);
+  for (DevBuf* d : {&B->inv_d, &B->absd, &B->r, &B->t, &B->y, &B->u, &B->qa, &B->qb, &B->dv, &B->state, &B->part})
+    d->release();
+  delete B;
+  c->ssor = nullptr;
+}
+
+}  // namespace petgem
