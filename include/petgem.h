@@ -75,12 +75,13 @@ enum { PETGEM_PRECOND_JACOBI = 0, PETGEM_PRECOND_LEARNED = 1, PETGEM_PRECOND_SSO
  *     variables) and whose even steps use Jacobi, with two-pass Gram-Schmidt.  The first cycle
  *     runs with Jacobi and measures its FP64 residual reduction; a learned cycle that does not
  *     beat it is undone and the solve continues with Jacobi alone (info.fell_back).
- *   precond = PETGEM_PRECOND_SSOR (method SQMR, precision C128 only; PETGEM_ERR_UNSUPPORTED
- *     otherwise): symmetric SOR, the preconditioner of the paper's Section 5.3 runs, in the
- *     order of a multicolour colouring of the matrix graph (petgem_colouring): with A = D + L + U
- *     split by colour, M = (D + omega L) D^{-1} (D + omega U), applied to SQMR as the symmetric
- *     split M1 = (D + omega L) D^{-1/2}, M2 = M1^T.  Each SQMR step then costs a forward and a
- *     backward sweep (one launch per colour each) besides the product. */
+ *   precond = PETGEM_PRECOND_SSOR (method SQMR only; PETGEM_ERR_UNSUPPORTED otherwise):
+ *     symmetric SOR, the preconditioner of the paper's Section 5.3 runs, in the order of a
+ *     multicolour colouring of the matrix graph (petgem_colouring): with A = D + L + U split by
+ *     colour, M = (D + omega L) D^{-1} (D + omega U), applied to SQMR as the symmetric split
+ *     M1 = (D + omega L) D^{-1/2}, M2 = M1^T.  Each SQMR step costs a forward and a backward
+ *     sweep (one launch per colour each) besides the product.  Precision as for COCG: FP64
+ *     residuals around inner solves in complex64 (MIXED) or complex128 (C128). */
 typedef struct {
   int32_t restart;
   int32_t precision;

@@ -313,8 +313,8 @@ int petgem_solve(petgem_ctx* c, const petgem_solve_opts* opts, void* x, petgem_s
   if (o.method != PETGEM_METHOD_GMRES && o.method != PETGEM_METHOD_COCG && o.method != PETGEM_METHOD_SQMR)
     return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve: unknown method"});
   if (o.precond == PETGEM_PRECOND_SSOR) {
-    if (o.method != PETGEM_METHOD_SQMR || o.precision != PETGEM_PREC_C128)
-      return finish(c, Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve: SSOR preconditions complex128 SQMR only"});
+    if (o.method != PETGEM_METHOD_SQMR)
+      return finish(c, Status{PETGEM_ERR_UNSUPPORTED, "petgem_solve: SSOR preconditions SQMR only"});
     if (o.omega == 0.0) o.omega = 1.0;
     if (!(o.omega > 0.0 && o.omega < 2.0))
       return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_solve: SSOR needs 0 < omega < 2"});

@@ -52,7 +52,9 @@ struct SsState {
 };
 
 struct SsBuffers {
-  DevBuf inv_d, absd, r, t, y, u, qa, qb, dv, state, part;
+  DevBuf inv_d, inv_d64, absd, val64;             // 1 / d (complex128, complex64), |d|, complex64 matrix
+  DevBuf r64, r, t, y, u, qa, qb, dv, e, state, part;  // inner vectors sized for complex128
+  int64_t version = -1;                           // assembly version of inv_d .. val64
 };
 
 __device__ __forceinline__ unsigned long long ss_key(unsigned long long s) {
@@ -169,112 +171,185 @@ __global__ void __launch_bounds__(kSsThreads) k_ss_residual(const int64_t* __res
   ss_block_partial(make_double2(s, 0.0), part + blockIdx.x);
 }
 
+// Precision of the inner solve: complex128 (T = double2) or complex64 (T = float2) vectors and
+// matrix; every sum across rows is taken in FP64 (the block partials).
+__device__ __forceinline__ void ss_fma(double2& acc, double2 a, double2 b) {  // acc += a b
+  acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+  acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+}
+__device__ __forceinline__ void ss_fma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+  acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+__device__ __forceinline__ double2 ss_d2(double2 a) { return a; }
+__device__ __forceinline__ double2 ss_d2(float2 a) { return make_double2(a.x, a.y); }
+template <typename T> __device__ __forceinline__ T ss_t(double2 a);
+template <> __device__ __forceinline__ double2 ss_t<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 ss_t<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+template <typename T> __device__ __forceinline__ T ss_zero() { T z; z.x = 0; z.y = 0; return z; }
+template <typename T> __device__ __forceinline__ T ss_lanes_sum_t(T a) {
+  for (int o = 1; o < kSsLanes; o <<= 1) {
+    a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+    a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+  }
+  return a;
+}
+
+// Inner right-hand side r = T(r64 * scale) and correction e = 0.
+template <typename T>
+__global__ void k_ss_start(const double2* __restrict__ r64, double scale, int64_t n, T* __restrict__ r,
+                           T* __restrict__ e) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  r[i] = ss_t<T>(cscale(r64[i], scale));
+  e[i] = ss_zero<T>();
+}
+
+// x += e * scale (FP64).
+template <typename T>
+__global__ void k_ss_finish(const T* __restrict__ e, double scale, int64_t n, double2* __restrict__ x) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i] = cadd(x[i], cscale(ss_d2(e[i]), scale));
+}
+
 // Forward sweep over the rows of colour c (rows[0..cnt)): with iter, first r_i -= alpha t_i; then
 // y_i = (r_i - w sum_{col(j) < c} a_ij y_j) / d_i; partial sums of |d_i| |y_i|^2.
+template <typename T>
 __global__ void __launch_bounds__(kSsThreads) k_ss_forward(const int64_t* __restrict__ rp,
                                                            const int32_t* __restrict__ col,
-                                                           const double2* __restrict__ val,
+                                                           const T* __restrict__ val,
                                                            const int32_t* __restrict__ colour,
                                                            const int32_t* __restrict__ rows, int64_t cnt, int32_t c,
-                                                           double omega, const double2* __restrict__ inv_d,
+                                                           double omega, const T* __restrict__ inv_d,
                                                            const double* __restrict__ absd,
-                                                           const double2* __restrict__ t, double2* __restrict__ r,
-                                                           double2* __restrict__ y, const SsState* __restrict__ st,
+                                                           const T* __restrict__ t, T* __restrict__ r,
+                                                           T* __restrict__ y, const SsState* __restrict__ st,
                                                            double2* __restrict__ part, int iter) {
   if (st->done) return;
   const int64_t g = (blockIdx.x * (int64_t)kSsThreads + threadIdx.x) / kSsLanes;
   const int lane = threadIdx.x & (kSsLanes - 1);
   const int32_t i = g < cnt ? rows[g] : -1;
-  double2 acc = make_double2(0.0, 0.0);
+  T acc = ss_zero<T>();
   if (i >= 0)
     for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += kSsLanes) {
       const int32_t j = col[p];
-      if (colour[j] < c) acc = cadd(acc, cmul(val[p], y[j]));
+      if (colour[j] < c) ss_fma(acc, val[p], y[j]);
     }
-  acc = ss_lanes_sum(acc);
+  acc = ss_lanes_sum_t(acc);
   double s = 0.0;
   if (i >= 0 && lane == 0) {
-    double2 ri = r[i];
+    T ri = r[i];
     if (iter) {
-      ri = csub(ri, cmul(st->alpha, t[i]));
+      const T al = ss_t<T>(st->alpha);
+      T mt = ss_zero<T>();
+      ss_fma(mt, al, t[i]);
+      ri.x -= mt.x;
+      ri.y -= mt.y;
       r[i] = ri;
     }
-    const double2 yi = cmul(csub(ri, cscale(acc, omega)), inv_d[i]);
+    T v = ri;
+    v.x -= (decltype(v.x))omega * acc.x;
+    v.y -= (decltype(v.y))omega * acc.y;
+    T yi = ss_zero<T>();
+    ss_fma(yi, v, inv_d[i]);
     y[i] = yi;
-    s = absd[i] * cabs2(yi);
+    s = absd[i] * cabs2(ss_d2(yi));
   }
   ss_block_partial(make_double2(s, 0.0), part + blockIdx.x);
 }
 
 // Backward sweep over the rows of colour c: u_i = y_i - (w / d_i) sum_{col(j) > c} a_ij u_j; with
-// iter, d_i = dc1 d_i + dc2 q_i and x_i += d_i, else d_i = 0; partial sums of r_i u_i.
+// iter, d_i = dc1 d_i + dc2 q_i and e_i += d_i, else d_i = 0; partial sums of r_i u_i.
+template <typename T>
 __global__ void __launch_bounds__(kSsThreads) k_ss_backward(const int64_t* __restrict__ rp,
                                                             const int32_t* __restrict__ col,
-                                                            const double2* __restrict__ val,
+                                                            const T* __restrict__ val,
                                                             const int32_t* __restrict__ colour,
                                                             const int32_t* __restrict__ rows, int64_t cnt, int32_t c,
-                                                            double omega, const double2* __restrict__ inv_d,
-                                                            const double2* __restrict__ y, double2* __restrict__ u,
-                                                            const double2* __restrict__ r,
-                                                            const double2* __restrict__ q, double2* __restrict__ dv,
-                                                            double2* __restrict__ x, const SsState* __restrict__ st,
+                                                            double omega, const T* __restrict__ inv_d,
+                                                            const T* __restrict__ y, T* __restrict__ u,
+                                                            const T* __restrict__ r, const T* __restrict__ q,
+                                                            T* __restrict__ dv, T* __restrict__ e,
+                                                            const SsState* __restrict__ st,
                                                             double2* __restrict__ part, int iter) {
   if (st->done) return;
   const int64_t g = (blockIdx.x * (int64_t)kSsThreads + threadIdx.x) / kSsLanes;
   const int lane = threadIdx.x & (kSsLanes - 1);
   const int32_t i = g < cnt ? rows[g] : -1;
-  double2 acc = make_double2(0.0, 0.0);
+  T acc = ss_zero<T>();
   if (i >= 0)
     for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += kSsLanes) {
       const int32_t j = col[p];
-      if (colour[j] > c) acc = cadd(acc, cmul(val[p], u[j]));
+      if (colour[j] > c) ss_fma(acc, val[p], u[j]);
     }
-  acc = ss_lanes_sum(acc);
+  acc = ss_lanes_sum_t(acc);
   double2 s = make_double2(0.0, 0.0);
   if (i >= 0 && lane == 0) {
-    const double2 ui = csub(y[i], cscale(cmul(inv_d[i], acc), omega));
+    T w = ss_zero<T>();
+    ss_fma(w, inv_d[i], acc);
+    T ui = y[i];
+    ui.x -= (decltype(ui.x))omega * w.x;
+    ui.y -= (decltype(ui.y))omega * w.y;
     u[i] = ui;
     if (iter) {
-      const double2 di = cadd(cscale(dv[i], st->dc1), cmul(st->dc2, q[i]));
+      const T c2 = ss_t<T>(st->dc2);
+      T di = dv[i];
+      const auto c1 = (decltype(di.x))st->dc1;
+      di.x *= c1;
+      di.y *= c1;
+      ss_fma(di, c2, q[i]);
       dv[i] = di;
-      x[i] = cadd(x[i], di);
+      T ei = e[i];
+      ei.x += di.x;
+      ei.y += di.y;
+      e[i] = ei;
     } else {
-      dv[i] = make_double2(0.0, 0.0);
+      dv[i] = ss_zero<T>();
     }
-    s = cmul(r[i], ui);
+    s = cmul(ss_d2(r[i]), ss_d2(ui));
   }
   ss_block_partial(s, part + blockIdx.x);
 }
 
 // t = A q_new with q_new = u + beta q_old formed on the fly (first: q_new = u); writes q_new and
 // partial sums of q_new^T t.
+template <typename T>
 __global__ void __launch_bounds__(kSsThreads) k_ss_spmv(const int64_t* __restrict__ rp,
                                                         const int32_t* __restrict__ col,
-                                                        const double2* __restrict__ val, int64_t n,
-                                                        const double2* __restrict__ u,
-                                                        const double2* __restrict__ qold, double2* __restrict__ qnew,
-                                                        double2* __restrict__ t, const SsState* __restrict__ st,
+                                                        const T* __restrict__ val, int64_t n,
+                                                        const T* __restrict__ u, const T* __restrict__ qold,
+                                                        T* __restrict__ qnew, T* __restrict__ t,
+                                                        const SsState* __restrict__ st,
                                                         double2* __restrict__ part, int first) {
   if (st->done) return;
   const int64_t i = (blockIdx.x * (int64_t)kSsThreads + threadIdx.x) / kSsLanes;
   const int lane = threadIdx.x & (kSsLanes - 1);
-  const double2 beta = st->beta;
-  double2 acc = make_double2(0.0, 0.0);
+  const T beta = ss_t<T>(st->beta);
+  T acc = ss_zero<T>();
   if (i < n)
     for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += kSsLanes) {
       const int32_t j = col[p];
-      const double2 qj = first ? u[j] : cadd(u[j], cmul(beta, qold[j]));
-      acc = cadd(acc, cmul(val[p], qj));
+      T qj = u[j];
+      if (!first) ss_fma(qj, beta, qold[j]);
+      ss_fma(acc, val[p], qj);
     }
-  acc = ss_lanes_sum(acc);
+  acc = ss_lanes_sum_t(acc);
   double2 s = make_double2(0.0, 0.0);
   if (i < n && lane == 0) {
-    const double2 qi = first ? u[i] : cadd(u[i], cmul(beta, qold[i]));
+    T qi = u[i];
+    if (!first) ss_fma(qi, beta, qold[i]);
     qnew[i] = qi;
     t[i] = acc;
-    s = cmul(qi, acc);
+    s = cmul(ss_d2(qi), ss_d2(acc));
   }
   ss_block_partial(s, part + blockIdx.x);
+}
+
+// Complex64 copies of the matrix values and of 1 / d_i.
+__global__ void k_ss_to64(const double2* __restrict__ a, int64_t m, float2* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < m) out[i] = make_float2((float)a[i].x, (float)a[i].y);
 }
 
 // Sum of np partials (fixed order) and the scalar step of a stage:
@@ -416,6 +491,8 @@ Status ssor_colouring(petgem_ctx* c) {
 
 namespace {
 
+constexpr int64_t kSsInnerMax = 4096;  // iterations of one complex64 inner solve at most
+
 struct SsLaunch {
   petgem_ctx* c;
   SsBuffers* B;
@@ -428,8 +505,11 @@ Status ss_setup(petgem_ctx* c, double omega, SsLaunch& L) {
   PG_TRY(ssor_colouring(c));
   SsBuffers* B = ss_bufs(c);
   const int64_t n = c->n_edges;
-  for (DevBuf* d : {&B->inv_d, &B->r, &B->t, &B->y, &B->u, &B->qa, &B->qb, &B->dv}) PG_TRY(d->reserve(n * sizeof(double2)));
+  for (DevBuf* d : {&B->inv_d, &B->r64, &B->r, &B->t, &B->y, &B->u, &B->qa, &B->qb, &B->dv, &B->e})
+    PG_TRY(d->reserve(n * sizeof(double2)));
+  PG_TRY(B->inv_d64.reserve(n * sizeof(float2)));
   PG_TRY(B->absd.reserve(n * sizeof(double)));
+  PG_TRY(B->val64.reserve(c->nnz * sizeof(float2)));
   PG_TRY(B->state.reserve(sizeof(SsState)));
   const int ncol = (int)c->ss_off.size() - 1;
   L.c = c;
@@ -443,45 +523,63 @@ Status ss_setup(petgem_ctx* c, double omega, SsLaunch& L) {
   L.np_sweep = L.pbase[ncol];
   PG_TRY(B->part.reserve((size_t)std::max<int64_t>(L.np_sweep, L.nb) * sizeof(double2)));
   PG_CUDA(cudaMemsetAsync(B->state.ptr, 0, sizeof(SsState), c->stream));
-  k_ss_diag<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->diag.as<double2>(), n, B->inv_d.as<double2>(),
-                                                       B->absd.as<double>());
-  c->launches++;
-  PG_CUDA(cudaGetLastError());
+  if (B->version != c->assembly_version) {
+    k_ss_diag<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->diag.as<double2>(), n, B->inv_d.as<double2>(),
+                                                         B->absd.as<double>());
+    k_ss_to64<<<blocks_for(n, 256), 256, 0, c->stream>>>(B->inv_d.as<double2>(), n, B->inv_d64.as<float2>());
+    k_ss_to64<<<blocks_for(c->nnz, 256), 256, 0, c->stream>>>(c->val.as<double2>(), c->nnz, B->val64.as<float2>());
+    c->launches += 3;
+    PG_CUDA(cudaGetLastError());
+    B->version = c->assembly_version;
+  }
   return Status{};
 }
 
+template <typename T> const T* ss_val(const SsLaunch& L);
+template <> const double2* ss_val<double2>(const SsLaunch& L) { return L.c->val.as<double2>(); }
+template <> const float2* ss_val<float2>(const SsLaunch& L) { return L.B->val64.as<float2>(); }
+template <typename T> const T* ss_inv_d(const SsLaunch& L);
+template <> const double2* ss_inv_d<double2>(const SsLaunch& L) { return L.B->inv_d.as<double2>(); }
+template <> const float2* ss_inv_d<float2>(const SsLaunch& L) { return L.B->inv_d64.as<float2>(); }
+
 // One sweep over all colours (ascending for the forward one).
-Status ss_forward(const SsLaunch& L, const double2* t, double2* r, double2* y, int iter) {
+template <typename T>
+Status ss_forward(const SsLaunch& L, const T* t, T* r, T* y, int iter) {
   petgem_ctx* c = L.c;
   const int ncol = (int)c->ss_off.size() - 1;
-  const double bytes = (double)c->nnz * 24 + 8.0 * (L.n + 1) + (double)L.n * (4 + 16 * 6 + 8);
-  KernelTimer kt(c, "ssor_forward", bytes);
+  const double vb = sizeof(T);
+  // values and columns, the colour of every column, row pointers and ids, y gathered once;
+  // r read (and written), t, 1 / d, |d| read, y written
+  const double bytes = (double)c->nnz * (vb + 8) + 12.0 * L.n + L.n * (vb * (iter ? 6 : 4) + 8);
+  KernelTimer kt(c, sizeof(T) == 16 ? "ssor_forward_c128" : "ssor_forward_c64", bytes);
   for (int k = 0; k < ncol; ++k) {
     const int64_t cnt = c->ss_off[k + 1] - c->ss_off[k];
     if (cnt == 0) continue;
-    k_ss_forward<<<blocks_for(cnt * kSsLanes, kSsThreads), kSsThreads, 0, c->stream>>>(
-        c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(), c->ss_colour.as<int32_t>(),
-        c->ss_rows.as<int32_t>() + c->ss_off[k], cnt, k, L.omega, L.B->inv_d.as<double2>(), L.B->absd.as<double>(), t,
-        r, y, L.B->state.as<SsState>(), L.B->part.as<double2>() + L.pbase[k], iter);
+    k_ss_forward<T><<<blocks_for(cnt * kSsLanes, kSsThreads), kSsThreads, 0, c->stream>>>(
+        c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), ss_val<T>(L), c->ss_colour.as<int32_t>(),
+        c->ss_rows.as<int32_t>() + c->ss_off[k], cnt, k, L.omega, ss_inv_d<T>(L), L.B->absd.as<double>(), t, r, y,
+        L.B->state.as<SsState>(), L.B->part.as<double2>() + L.pbase[k], iter);
     c->launches++;
   }
   PG_CUDA(cudaGetLastError());
   return Status{};
 }
 
-Status ss_backward(const SsLaunch& L, const double2* y, double2* u, const double2* r, const double2* q, double2* x,
-                   int iter) {
+template <typename T>
+Status ss_backward(const SsLaunch& L, const T* y, T* u, const T* r, const T* q, T* e, int iter) {
   petgem_ctx* c = L.c;
   const int ncol = (int)c->ss_off.size() - 1;
-  const double bytes = (double)c->nnz * 24 + 8.0 * (L.n + 1) + (double)L.n * (4 + 16 * (iter ? 9 : 5));
-  KernelTimer kt(c, "ssor_backward", bytes);
+  const double vb = sizeof(T);
+  // as the forward sweep; y, r, 1 / d read, u written, and with iter d, q, e read and d, e written
+  const double bytes = (double)c->nnz * (vb + 8) + 12.0 * L.n + L.n * vb * (iter ? 9 : 5);
+  KernelTimer kt(c, sizeof(T) == 16 ? "ssor_backward_c128" : "ssor_backward_c64", bytes);
   for (int k = ncol - 1; k >= 0; --k) {
     const int64_t cnt = c->ss_off[k + 1] - c->ss_off[k];
     if (cnt == 0) continue;
-    k_ss_backward<<<blocks_for(cnt * kSsLanes, kSsThreads), kSsThreads, 0, c->stream>>>(
-        c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(), c->ss_colour.as<int32_t>(),
-        c->ss_rows.as<int32_t>() + c->ss_off[k], cnt, k, L.omega, L.B->inv_d.as<double2>(), y, u, r, q,
-        L.B->dv.as<double2>(), x, L.B->state.as<SsState>(), L.B->part.as<double2>() + L.pbase[k], iter);
+    k_ss_backward<T><<<blocks_for(cnt * kSsLanes, kSsThreads), kSsThreads, 0, c->stream>>>(
+        c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), ss_val<T>(L), c->ss_colour.as<int32_t>(),
+        c->ss_rows.as<int32_t>() + c->ss_off[k], cnt, k, L.omega, ss_inv_d<T>(L), y, u, r, q, L.B->dv.as<T>(), e,
+        L.B->state.as<SsState>(), L.B->part.as<double2>() + L.pbase[k], iter);
     c->launches++;
   }
   PG_CUDA(cudaGetLastError());
@@ -503,13 +601,14 @@ Status ss_read(const SsLaunch& L, SsState* h) {
   return Status{};
 }
 
-// ||v||^2 (mode 1) or ||b - A x||^2 into r (mode 0).
+// ||v||^2 (mode 1) or ||b - A x||^2 with the residual into r64 (mode 0), all in FP64.
 Status ss_norm2(const SsLaunch& L, const double2* x, const double2* v, int mode, double* out) {
   petgem_ctx* c = L.c;
   {
-    KernelTimer kt(c, mode == 0 ? "ssor_residual" : "ssor_norm", mode == 0 ? (double)c->nnz * 20 + 8.0 * (L.n + 1) + 48.0 * L.n : 16.0 * L.n);
+    KernelTimer kt(c, mode == 0 ? "ssor_residual_c128" : "ssor_norm",
+                   mode == 0 ? (double)c->nnz * 20 + 8.0 * (L.n + 1) + 48.0 * L.n : 16.0 * L.n);
     k_ss_residual<<<L.nb, kSsThreads, 0, c->stream>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(),
-                                                      c->val.as<double2>(), x, v, L.n, mode, L.B->r.as<double2>(),
+                                                      c->val.as<double2>(), x, v, L.n, mode, L.B->r64.as<double2>(),
                                                       L.B->part.as<double2>());
     c->launches++;
   }
@@ -521,13 +620,17 @@ Status ss_norm2(const SsLaunch& L, const double2* x, const double2* v, int mode,
   return Status{};
 }
 
+// One source: FP64 residuals r = b - A x; each inner solve runs SQMR in T on A e = r / ||r||
+// (e0 = 0) until tau fell by its target, then x += ||r|| e in FP64.
+template <typename T>
 Status ssor_sqmr_source(const SsLaunch& L, const petgem_solve_opts& o, const double2* b, double2* x,
                         petgem_solve_info& inf) {
   petgem_ctx* c = L.c;
   SsBuffers* B = L.B;
   const int64_t n = L.n;
-  double2 *r = B->r.as<double2>(), *t = B->t.as<double2>(), *y = B->y.as<double2>(), *u = B->u.as<double2>();
-  double2* qbuf[2] = {B->qa.as<double2>(), B->qb.as<double2>()};
+  const bool c128 = sizeof(T) == 16;
+  T *r = B->r.as<T>(), *t = B->t.as<T>(), *y = B->y.as<T>(), *u = B->u.as<T>(), *e = B->e.as<T>();
+  T* qbuf[2] = {B->qa.as<T>(), B->qb.as<T>()};
   double bn2 = 0.0;
   PG_TRY(ss_norm2(L, x, b, 1, &bn2));
   const double bnorm = sqrt(bn2);
@@ -536,7 +639,8 @@ Status ssor_sqmr_source(const SsLaunch& L, const petgem_solve_opts& o, const dou
     inf.status = PETGEM_OK;
     return Status{};
   }
-  const double spmv_bytes = (double)c->nnz * 20 + 8.0 * (n + 1) + 16.0 * n * 5;
+  const double vb = sizeof(T);
+  const double spmv_bytes = (double)c->nnz * (vb + 4) + 8.0 * (n + 1) + vb * n * 6;
   int64_t iters = 0, solves = 0;
   double relres = 0.0, prev = INFINITY;
   int status = PETGEM_OK, stalls = 0;
@@ -560,35 +664,45 @@ Status ssor_sqmr_source(const SsLaunch& L, const petgem_solve_opts& o, const dou
       break;
     }
     prev = relres;
-    // inner target on tau, relative to its start: what the final tolerance still needs, with a
-    // margin for the difference between tau and the true residual
-    const double inner = 0.3 * o.tol * bnorm / sqrt(rn2);
+    // inner target on tau, relative to its start: what the final tolerance still needs (with a
+    // margin for the difference between tau and the true residual); complex64 inner solves stop
+    // at inner_tol at most and run kSsInnerMax iterations at most (their recursively updated
+    // residual drifts from the true one in FP32; a fresh FP64 residual bounds the drift)
+    const double rnorm = sqrt(rn2);
+    const double need = 0.3 * o.tol * bnorm / rnorm;
+    const double inner = c128 ? need : std::min(std::max(o.inner_tol, need), 0.5);
+    const int64_t kmax = std::min<int64_t>(o.max_iters - iters, c128 ? INT64_MAX : kSsInnerMax);
+    k_ss_start<T><<<blocks_for(n, 256), 256, 0, c->stream>>>(B->r64.as<double2>(), 1.0 / rnorm, n, r, e);
+    c->launches++;
     PG_CUDA(cudaMemsetAsync(B->state.ptr, 0, sizeof(SsState), c->stream));  // running again
-    PG_TRY(ss_forward(L, nullptr, r, y, 0));
-    PG_TRY(ss_scalar<0>(L, L.np_sweep, inner, (long long)(o.max_iters - iters)));
-    PG_TRY(ss_backward(L, y, u, r, nullptr, x, 0));
+    PG_TRY(ss_forward<T>(L, nullptr, r, y, 0));
+    PG_TRY(ss_scalar<0>(L, L.np_sweep, inner, (long long)kmax));
+    PG_TRY(ss_backward<T>(L, y, u, r, nullptr, e, 0));
     PG_TRY(ss_scalar<1>(L, L.np_sweep));
     int cur = 0;
     for (int64_t it = 0;; ++it) {
       {
-        KernelTimer kt(c, "ssor_spmv", spmv_bytes);
-        k_ss_spmv<<<L.nb, kSsThreads, 0, c->stream>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(),
-                                                      c->val.as<double2>(), n, u, qbuf[cur], qbuf[cur ^ 1], t,
-                                                      B->state.as<SsState>(), B->part.as<double2>(), it == 0);
+        KernelTimer kt(c, c128 ? "ssor_spmv_c128" : "ssor_spmv_c64", spmv_bytes);
+        k_ss_spmv<T><<<L.nb, kSsThreads, 0, c->stream>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(),
+                                                         ss_val<T>(L), n, u, qbuf[cur], qbuf[cur ^ 1], t,
+                                                         B->state.as<SsState>(), B->part.as<double2>(), it == 0);
         c->launches++;
       }
       PG_CUDA(cudaGetLastError());
       cur ^= 1;  // q_new
       PG_TRY(ss_scalar<2>(L, L.nb));
-      PG_TRY(ss_forward(L, t, r, y, 1));
+      PG_TRY(ss_forward<T>(L, t, r, y, 1));
       PG_TRY(ss_scalar<3>(L, L.np_sweep));
-      PG_TRY(ss_backward(L, y, u, r, qbuf[cur], x, 1));
+      PG_TRY(ss_backward<T>(L, y, u, r, qbuf[cur], e, 1));
       PG_TRY(ss_scalar<4>(L, L.np_sweep));
       if ((it + 1) % kSsChunk == 0) {
         PG_TRY(ss_read(L, &hs));
         if (hs.done) break;
       }
     }
+    k_ss_finish<T><<<blocks_for(n, 256), 256, 0, c->stream>>>(e, rnorm, n, x);
+    c->launches++;
+    PG_CUDA(cudaGetLastError());
     iters += hs.k;
     solves += 1;
     if (hs.done == 2 && hs.k == 0) {  // the bilinear form broke down at once: no progress possible
@@ -613,7 +727,12 @@ Status run_solve_ssor(petgem_ctx* c, const petgem_solve_opts& o, double2* x, pet
   for (int32_t src = 0; src < c->n_src; ++src) {
     petgem_solve_info& inf = info[src];
     inf = petgem_solve_info{};
-    PG_TRY(ssor_sqmr_source(L, o, c->b.as<double2>() + (int64_t)src * L.n, x + (int64_t)src * L.n, inf));
+    const double2* b = c->b.as<double2>() + (int64_t)src * L.n;
+    double2* xs = x + (int64_t)src * L.n;
+    if (o.precision == PETGEM_PREC_MIXED)
+      PG_TRY(ssor_sqmr_source<float2>(L, o, b, xs, inf));
+    else
+      PG_TRY(ssor_sqmr_source<double2>(L, o, b, xs, inf));
     if (inf.status != PETGEM_OK && worst.ok())
       worst = Status{inf.status, "source " + std::to_string(src) + " did not converge (SQMR, SSOR)"};
   }
@@ -624,9 +743,10 @@ Status run_solve_ssor(petgem_ctx* c, const petgem_solve_opts& o, double2* x, pet
 Status run_ssor_apply(petgem_ctx* c, double omega, const double2* r_in, double2* z) {
   SsLaunch L;
   PG_TRY(ss_setup(c, omega, L));
-  PG_CUDA(cudaMemcpyAsync(L.B->r.ptr, r_in, L.n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-  PG_TRY(ss_forward(L, nullptr, L.B->r.as<double2>(), L.B->y.as<double2>(), 0));
-  PG_TRY(ss_backward(L, L.B->y.as<double2>(), z, L.B->r.as<double2>(), nullptr, nullptr, 0));
+  double2* r = L.B->r.as<double2>();
+  PG_CUDA(cudaMemcpyAsync(r, r_in, L.n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  PG_TRY(ss_forward<double2>(L, nullptr, r, L.B->y.as<double2>(), 0));
+  PG_TRY(ss_backward<double2>(L, L.B->y.as<double2>(), z, r, nullptr, nullptr, 0));
   PG_CUDA(cudaStreamSynchronize(c->stream));
   return Status{};
 }
@@ -634,7 +754,8 @@ Status run_ssor_apply(petgem_ctx* c, double omega, const double2* r_in, double2*
 void destroy_ssor(petgem_ctx* c) {
   if (!c->ssor) return;
   SsBuffers* B = static_cast<SsBuffers*>(c->ssor);
-  for (DevBuf* d : {&B->inv_d, &B->absd, &B->r, &B->t, &B->y, &B->u, &B->qa, &B->qb, &B->dv, &B->state, &B->part})
+  for (DevBuf* d : {&B->inv_d, &B->inv_d64, &B->absd, &B->val64, &B->r64, &B->r, &B->t, &B->y, &B->u, &B->qa, &B->qb,
+                    &B->dv, &B->e, &B->state, &B->part})
     d->release();
   delete B;
   c->ssor = nullptr;

@@ -107,19 +107,20 @@ def test_ssor_apply_matches_oracle(name, omega):
     assert np.max(np.abs(z - want)) <= 1e-11 * np.max(np.abs(want))
 
 
-def gpu_ssor(m, **opts):
+def gpu_ssor(m, precision=api.PREC_C128, **opts):
     with api.Context(0) as ctx:
         ctx.mesh(m.mesh.nodes, m.mesh.tets)
         ctx.assemble(m.freq, m.sigma, m.sigma_p, m.sources)
-        x, info, st = ctx.solve(precision=api.PREC_C128, method=api.METHOD_SQMR, precond=api.PRECOND_SSOR, **opts)
+        x, info, st = ctx.solve(precision=precision, method=api.METHOD_SQMR, precond=api.PRECOND_SSOR, **opts)
         rcv, _ = ctx.receivers(m.receivers, x)
         return x.cpu().numpy(), info, st, rcv.cpu().numpy()
 
 
+@pytest.mark.parametrize("precision", [api.PREC_C128, api.PREC_MIXED])
 @pytest.mark.parametrize("name", list(MODELS))
-def test_ssor_sqmr_solution_and_receivers(name):
+def test_ssor_sqmr_solution_and_receivers(name, precision):
     m, ref, xr, A, b, colour_ref, _ = reference(name)
-    x, info, st, rcv = gpu_ssor(m, tol=1e-8)
+    x, info, st, rcv = gpu_ssor(m, precision, tol=1e-8)
     assert st == api.OK
     P = SSOR(A, colour_ref, 1.0)
     for s in range(len(m.sources)):
@@ -130,12 +131,15 @@ def test_ssor_sqmr_solution_and_receivers(name):
         _, it_ref, rel_ref, _ = sqmr(A, b[s], tol=1e-8, precond=P)
         assert rel_ref <= 1e-8
         # the device stops on the quasi-residual tau and checks the true residual after; the
-        # oracle checks the true residual at every step
-        assert abs(info[s]["iters"] - it_ref) <= 0.15 * it_ref + 10, (info[s]["iters"], it_ref)
+        # oracle checks the true residual at every step.  Complex64 inner solves restart from the
+        # FP64 residual, which costs a few tens of iterations more.
+        slack = 0.15 if precision == api.PREC_C128 else 0.5
+        assert abs(info[s]["iters"] - it_ref) <= slack * it_ref + 10, (info[s]["iters"], it_ref)
     rr, _ = ref.receivers(xr, m.receivers)
     assert rel(rcv, rr) <= 1e-6
-    print("\n%s: SSOR-SQMR iterations %s, inner solves %s" % (name, [i["iters"] for i in info],
-                                                              [i["restarts"] for i in info]))
+    print("\n%s %s: SSOR-SQMR iterations %s, inner solves %s" % (
+        name, "c128" if precision == api.PREC_C128 else "mixed", [i["iters"] for i in info],
+        [i["restarts"] for i in info]))
 
 
 def test_ssor_omega_and_unsupported_options():
@@ -147,15 +151,17 @@ def test_ssor_omega_and_unsupported_options():
         ctx.mesh(m6.mesh.nodes, m6.mesh.tets)
         ctx.assemble(m6.freq, m6.sigma, m6.sigma_p, m6.sources)
         for kw, code in ((dict(method=api.METHOD_COCG), api.ERR_UNSUPPORTED),
-                         (dict(method=api.METHOD_SQMR, precision=api.PREC_MIXED), api.ERR_UNSUPPORTED),
-                         (dict(method=api.METHOD_SQMR, omega=2.5), api.ERR_INVALID_ARG)):
+                         (dict(method=api.METHOD_GMRES), api.ERR_UNSUPPORTED),
+                         (dict(method=api.METHOD_SQMR, omega=2.5), api.ERR_INVALID_ARG),
+                         (dict(method=api.METHOD_SQMR, omega=-0.5), api.ERR_INVALID_ARG)):
             with pytest.raises(api.PetgemError) as e:
                 ctx.solve(precond=api.PRECOND_SSOR, **kw)
             assert e.value.status == code
 
 
-def test_ssor_zero_rhs():
+@pytest.mark.parametrize("precision", [api.PREC_C128, api.PREC_MIXED])
+def test_ssor_zero_rhs(precision):
     m = synth.cube_block_model(6)
     m.sigma = np.full_like(m.sigma, m.sigma_p)  # no anomaly: b = 0
-    x, info, st, _ = gpu_ssor(m)
+    x, info, st, _ = gpu_ssor(m, precision)
     assert st == api.OK and info[0]["iters"] == 0 and not np.any(x)
