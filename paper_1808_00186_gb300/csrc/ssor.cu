@@ -20,6 +20,15 @@
 //   forward, colours ascending:  y_i = (r_i - w sum_{col(j) < col(i)} a_ij y_j) / d_i
 //   backward, colours descending: u_i = y_i - (w / d_i) sum_{col(j) > col(i)} a_ij u_j.
 //
+// Layout.  The solver works in the colour order: rows (and columns) renumbered so that each
+// colour's rows are consecutive (ascending original ids inside a colour), every row holding its
+// off-diagonal entries split as [lower-colour entries | higher-colour entries] with renumbered
+// columns, the diagonal apart.  A sweep over one colour then streams a contiguous block of rows
+// and only the half of each row it needs (no per-entry colour test), and the product reads both
+// halves plus the diagonal: one matrix pass per sweep pair beyond the product.  Values are gathered
+// into the layout once per assembly (complex128 and complex64); the vectors are permuted at the
+// start of an inner solve and scattered back at its end.
+//
 // SQMR (Freund and Nachtigal 1994), in the order of the method: t = A q; sigma = q^T t;
 // alpha = rho / sigma; r -= alpha t; y = F r; theta' = ||D^{1/2} y|| / tau; c^2 = 1 / (1 + theta'^2);
 // tau = tau theta' c; d = c^2 theta^2 d + c^2 alpha q; x += d; u = B D y; rho' = r^T u;
@@ -52,9 +61,15 @@ struct SsState {
 };
 
 struct SsBuffers {
-  DevBuf inv_d, inv_d64, absd, val64;             // 1 / d (complex128, complex64), |d|, complex64 matrix
+  // colour-order layout of the pattern (mesh version `layout`): row offsets, lower/upper split,
+  // renumbered columns, CSR entry each slot takes its value from, old -> new row ids
+  DevBuf prp, psp, pcol, psrc, inv;
+  int64_t layout = -1, noff = 0;
+  // values in that layout (assembly version `version`): off-diagonal entries, diagonal, 1 / d
+  // (complex128 and complex64) and |d|
+  DevBuf pv128, pv64, dg128, dg64, id128, id64, absd;
+  int64_t version = -1;
   DevBuf r64, r, t, y, u, qa, qb, dv, e, state, part;  // inner vectors sized for complex128
-  int64_t version = -1;                           // assembly version of inv_d .. val64
 };
 
 __device__ __forceinline__ unsigned long long ss_key(unsigned long long s) {
@@ -115,14 +130,77 @@ __global__ void k_ss_place(const int32_t* __restrict__ flag, const int64_t* __re
   if (i < n && flag[i]) rows[base + rank[i]] = (int32_t)i;
 }
 
-// 1 / d_i and |d_i|.
-__global__ void k_ss_diag(const double2* __restrict__ d, int64_t n, double2* __restrict__ inv_d,
-                          double* __restrict__ absd) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double2 di = d[i];
-  inv_d[i] = cdiv(make_double2(1.0, 0.0), di);
-  absd[i] = sqrt(cabs2(di));
+// Layout construction.  inv[perm[r]] = r.
+__global__ void k_ss_inv(const int32_t* __restrict__ perm, int64_t n, int32_t* __restrict__ inv) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r < n) inv[perm[r]] = (int32_t)r;
+}
+
+// Off-diagonal entries of new row r (the pattern holds every row's diagonal).
+__global__ void k_ss_offlen(const int64_t* __restrict__ rp, const int32_t* __restrict__ perm, int64_t n,
+                            int32_t* __restrict__ len) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int32_t i = perm[r];
+  len[r] = (int32_t)(rp[i + 1] - rp[i]) - 1;
+}
+
+// New row r: its lower-colour entries, then its higher-colour ones, each in CSR order, with
+// renumbered columns and the CSR entry they come from; psp[r] = the first higher-colour slot.
+__global__ void k_ss_split(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                           const int32_t* __restrict__ colour, const int32_t* __restrict__ perm,
+                           const int32_t* __restrict__ inv, const int64_t* __restrict__ prp, int64_t n,
+                           int32_t* __restrict__ pcol, int32_t* __restrict__ psrc, int64_t* __restrict__ psp,
+                           int32_t* __restrict__ bad) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int32_t i = perm[r];
+  const int32_t ci = colour[i];
+  int64_t q = prp[r];
+  const int64_t end = prp[r + 1];
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) psp[r] = q;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      const int32_t j = col[p];
+      if (j == i) continue;
+      const int32_t cj = colour[j];
+      if (cj == ci) *bad = 1;  // not a colouring of this pattern
+      if ((pass == 0) != (cj < ci)) continue;
+      if (q >= end) {
+        *bad = 1;
+        return;
+      }
+      pcol[q] = inv[j];
+      psrc[q] = (int32_t)p;
+      ++q;
+    }
+  }
+  if (q != end) *bad = 1;
+}
+
+// Values into the layout: off-diagonal entries (complex128 and complex64) ...
+__global__ void k_ss_values(const int32_t* __restrict__ psrc, int64_t m, const double2* __restrict__ val,
+                            double2* __restrict__ v128, float2* __restrict__ v64) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= m) return;
+  const double2 a = val[psrc[q]];
+  v128[q] = a;
+  v64[q] = make_float2((float)a.x, (float)a.y);
+}
+
+// ... and d_r, 1 / d_r (both precisions) and |d_r| in the new order.
+__global__ void k_ss_diag(const double2* __restrict__ d, const int32_t* __restrict__ perm, int64_t n,
+                          double2* __restrict__ dg128, float2* __restrict__ dg64, double2* __restrict__ id128,
+                          float2* __restrict__ id64, double* __restrict__ absd) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const double2 di = d[perm[r]];
+  const double2 ii = cdiv(make_double2(1.0, 0.0), di);
+  dg128[r] = di;
+  dg64[r] = make_float2((float)di.x, (float)di.y);
+  id128[r] = ii;
+  id64[r] = make_float2((float)ii.x, (float)ii.y);
+  absd[r] = sqrt(cabs2(di));
 }
 
 __device__ __forceinline__ double2 ss_lanes_sum(double2 a) {
@@ -195,32 +273,33 @@ template <typename T> __device__ __forceinline__ T ss_lanes_sum_t(T a) {
   return a;
 }
 
-// Inner right-hand side r = T(r64 * scale) and correction e = 0.
+// Inner right-hand side r = T(r64 * scale) in the new order and correction e = 0.
 template <typename T>
-__global__ void k_ss_start(const double2* __restrict__ r64, double scale, int64_t n, T* __restrict__ r,
-                           T* __restrict__ e) {
+__global__ void k_ss_start(const double2* __restrict__ r64, const int32_t* __restrict__ perm, double scale, int64_t n,
+                           T* __restrict__ r, T* __restrict__ e) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  r[i] = ss_t<T>(cscale(r64[i], scale));
+  r[i] = ss_t<T>(cscale(r64[perm[i]], scale));
   e[i] = ss_zero<T>();
 }
 
-// x += e * scale (FP64).
+// x += e * scale (FP64), back in the original order.
 template <typename T>
-__global__ void k_ss_finish(const T* __restrict__ e, double scale, int64_t n, double2* __restrict__ x) {
+__global__ void k_ss_finish(const T* __restrict__ e, const int32_t* __restrict__ perm, double scale, int64_t n,
+                            double2* __restrict__ x) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  x[i] = cadd(x[i], cscale(ss_d2(e[i]), scale));
+  const int32_t o = perm[i];
+  x[o] = cadd(x[o], cscale(ss_d2(e[i]), scale));
 }
 
-// Forward sweep over the rows of colour c (rows[0..cnt)): with iter, first r_i -= alpha t_i; then
-// y_i = (r_i - w sum_{col(j) < c} a_ij y_j) / d_i; partial sums of |d_i| |y_i|^2.
+// Forward sweep over the rows [r0, r0 + cnt) of one colour: with iter, first r_i -= alpha t_i;
+// then y_i = (r_i - w sum_lower a_ij y_j) / d_i; partial sums of |d_i| |y_i|^2.
 template <typename T>
-__global__ void __launch_bounds__(kSsThreads) k_ss_forward(const int64_t* __restrict__ rp,
-                                                           const int32_t* __restrict__ col,
-                                                           const T* __restrict__ val,
-                                                           const int32_t* __restrict__ colour,
-                                                           const int32_t* __restrict__ rows, int64_t cnt, int32_t c,
+__global__ void __launch_bounds__(kSsThreads) k_ss_forward(const int64_t* __restrict__ prp,
+                                                           const int64_t* __restrict__ psp,
+                                                           const int32_t* __restrict__ pcol,
+                                                           const T* __restrict__ pv, int64_t r0, int64_t cnt,
                                                            double omega, const T* __restrict__ inv_d,
                                                            const double* __restrict__ absd,
                                                            const T* __restrict__ t, T* __restrict__ r,
@@ -229,16 +308,13 @@ __global__ void __launch_bounds__(kSsThreads) k_ss_forward(const int64_t* __rest
   if (st->done) return;
   const int64_t g = (blockIdx.x * (int64_t)kSsThreads + threadIdx.x) / kSsLanes;
   const int lane = threadIdx.x & (kSsLanes - 1);
-  const int32_t i = g < cnt ? rows[g] : -1;
+  const int64_t i = r0 + g;
   T acc = ss_zero<T>();
-  if (i >= 0)
-    for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += kSsLanes) {
-      const int32_t j = col[p];
-      if (colour[j] < c) ss_fma(acc, val[p], y[j]);
-    }
+  if (g < cnt)
+    for (int64_t q = prp[i] + lane; q < psp[i]; q += kSsLanes) ss_fma(acc, pv[q], y[pcol[q]]);
   acc = ss_lanes_sum_t(acc);
   double s = 0.0;
-  if (i >= 0 && lane == 0) {
+  if (g < cnt && lane == 0) {
     T ri = r[i];
     if (iter) {
       const T al = ss_t<T>(st->alpha);
@@ -259,14 +335,13 @@ __global__ void __launch_bounds__(kSsThreads) k_ss_forward(const int64_t* __rest
   ss_block_partial(make_double2(s, 0.0), part + blockIdx.x);
 }
 
-// Backward sweep over the rows of colour c: u_i = y_i - (w / d_i) sum_{col(j) > c} a_ij u_j; with
-// iter, d_i = dc1 d_i + dc2 q_i and e_i += d_i, else d_i = 0; partial sums of r_i u_i.
+// Backward sweep over the rows [r0, r0 + cnt) of one colour: u_i = y_i - (w / d_i) sum_upper a_ij u_j;
+// with iter, d_i = dc1 d_i + dc2 q_i and e_i += d_i, else d_i = 0; partial sums of r_i u_i.
 template <typename T>
-__global__ void __launch_bounds__(kSsThreads) k_ss_backward(const int64_t* __restrict__ rp,
-                                                            const int32_t* __restrict__ col,
-                                                            const T* __restrict__ val,
-                                                            const int32_t* __restrict__ colour,
-                                                            const int32_t* __restrict__ rows, int64_t cnt, int32_t c,
+__global__ void __launch_bounds__(kSsThreads) k_ss_backward(const int64_t* __restrict__ prp,
+                                                            const int64_t* __restrict__ psp,
+                                                            const int32_t* __restrict__ pcol,
+                                                            const T* __restrict__ pv, int64_t r0, int64_t cnt,
                                                             double omega, const T* __restrict__ inv_d,
                                                             const T* __restrict__ y, T* __restrict__ u,
                                                             const T* __restrict__ r, const T* __restrict__ q,
@@ -276,16 +351,13 @@ __global__ void __launch_bounds__(kSsThreads) k_ss_backward(const int64_t* __res
   if (st->done) return;
   const int64_t g = (blockIdx.x * (int64_t)kSsThreads + threadIdx.x) / kSsLanes;
   const int lane = threadIdx.x & (kSsLanes - 1);
-  const int32_t i = g < cnt ? rows[g] : -1;
+  const int64_t i = r0 + g;
   T acc = ss_zero<T>();
-  if (i >= 0)
-    for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += kSsLanes) {
-      const int32_t j = col[p];
-      if (colour[j] > c) ss_fma(acc, val[p], u[j]);
-    }
+  if (g < cnt)
+    for (int64_t k = psp[i] + lane; k < prp[i + 1]; k += kSsLanes) ss_fma(acc, pv[k], u[pcol[k]]);
   acc = ss_lanes_sum_t(acc);
   double2 s = make_double2(0.0, 0.0);
-  if (i >= 0 && lane == 0) {
+  if (g < cnt && lane == 0) {
     T w = ss_zero<T>();
     ss_fma(w, inv_d[i], acc);
     T ui = y[i];
@@ -312,15 +384,15 @@ __global__ void __launch_bounds__(kSsThreads) k_ss_backward(const int64_t* __res
   ss_block_partial(s, part + blockIdx.x);
 }
 
-// t = A q_new with q_new = u + beta q_old formed on the fly (first: q_new = u); writes q_new and
-// partial sums of q_new^T t.
+// t = A q_new with q_new = u + beta q_old formed on the fly (first: q_new = u): both halves of
+// each row plus the diagonal; writes q_new and partial sums of q_new^T t.
 template <typename T>
-__global__ void __launch_bounds__(kSsThreads) k_ss_spmv(const int64_t* __restrict__ rp,
-                                                        const int32_t* __restrict__ col,
-                                                        const T* __restrict__ val, int64_t n,
-                                                        const T* __restrict__ u, const T* __restrict__ qold,
-                                                        T* __restrict__ qnew, T* __restrict__ t,
-                                                        const SsState* __restrict__ st,
+__global__ void __launch_bounds__(kSsThreads) k_ss_spmv(const int64_t* __restrict__ prp,
+                                                        const int32_t* __restrict__ pcol,
+                                                        const T* __restrict__ pv, const T* __restrict__ dg,
+                                                        int64_t n, const T* __restrict__ u,
+                                                        const T* __restrict__ qold, T* __restrict__ qnew,
+                                                        T* __restrict__ t, const SsState* __restrict__ st,
                                                         double2* __restrict__ part, int first) {
   if (st->done) return;
   const int64_t i = (blockIdx.x * (int64_t)kSsThreads + threadIdx.x) / kSsLanes;
@@ -328,28 +400,23 @@ __global__ void __launch_bounds__(kSsThreads) k_ss_spmv(const int64_t* __restric
   const T beta = ss_t<T>(st->beta);
   T acc = ss_zero<T>();
   if (i < n)
-    for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += kSsLanes) {
-      const int32_t j = col[p];
+    for (int64_t k = prp[i] + lane; k < prp[i + 1]; k += kSsLanes) {
+      const int32_t j = pcol[k];
       T qj = u[j];
       if (!first) ss_fma(qj, beta, qold[j]);
-      ss_fma(acc, val[p], qj);
+      ss_fma(acc, pv[k], qj);
     }
   acc = ss_lanes_sum_t(acc);
   double2 s = make_double2(0.0, 0.0);
   if (i < n && lane == 0) {
     T qi = u[i];
     if (!first) ss_fma(qi, beta, qold[i]);
+    ss_fma(acc, dg[i], qi);
     qnew[i] = qi;
     t[i] = acc;
     s = cmul(ss_d2(qi), ss_d2(acc));
   }
   ss_block_partial(s, part + blockIdx.x);
-}
-
-// Complex64 copies of the matrix values and of 1 / d_i.
-__global__ void k_ss_to64(const double2* __restrict__ a, int64_t m, float2* __restrict__ out) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < m) out[i] = make_float2((float)a[i].x, (float)a[i].y);
 }
 
 // Sum of np partials (fixed order) and the scalar step of a stage:
@@ -493,6 +560,12 @@ namespace {
 
 constexpr int64_t kSsInnerMax = 4096;  // iterations of one complex64 inner solve at most
 
+__global__ void k_ss_scatter(const double2* __restrict__ v, const int32_t* __restrict__ perm, int64_t n,
+                             double2* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[perm[i]] = v[i];
+}
+
 struct SsLaunch {
   petgem_ctx* c;
   SsBuffers* B;
@@ -501,15 +574,68 @@ struct SsLaunch {
   std::vector<int64_t> pbase;  // first partial of each colour's sweep launch
 };
 
+// The colour-order layout of the pattern (once per mesh).
+Status ss_layout(petgem_ctx* c, SsBuffers* B) {
+  if (B->layout == c->mesh_version) return Status{};
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n_edges;
+  const int64_t m = c->nnz - n;  // off-diagonal entries
+  if (c->nnz >= (1ll << 31)) return Status{PETGEM_ERR_UNSUPPORTED, "SSOR layout: more than 2^31 entries"};
+  const int32_t* perm = c->ss_rows.as<int32_t>();
+  PG_TRY(B->inv.reserve(n * sizeof(int32_t)));
+  PG_TRY(B->prp.reserve((n + 1) * sizeof(int64_t)));
+  PG_TRY(B->psp.reserve(n * sizeof(int64_t)));
+  PG_TRY(B->pcol.reserve(std::max<int64_t>(m, 1) * sizeof(int32_t)));
+  PG_TRY(B->psrc.reserve(std::max<int64_t>(m, 1) * sizeof(int32_t)));
+  DevBuf work;
+  PG_TRY(work.reserve((size_t)n * sizeof(int32_t) + 16));
+  int32_t* len = work.as<int32_t>();
+  int32_t* bad = len + n;
+  auto body = [&]() -> Status {
+    PG_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), s));
+    k_ss_inv<<<blocks_for(n, 256), 256, 0, s>>>(perm, n, B->inv.as<int32_t>());
+    k_ss_offlen<<<blocks_for(n, 256), 256, 0, s>>>(c->row_ptr.as<int64_t>(), perm, n, len);
+    c->launches += 2;
+    PG_CUDA(cudaGetLastError());
+    PG_TRY(exclusive_scan(len, B->prp.as<int64_t>(), n, s));
+    int64_t total = 0;
+    PG_CUDA(cudaMemcpyAsync(&total, B->prp.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    if (total != m) return Status{PETGEM_ERR_CUDA, "SSOR layout: a pattern row lacks its diagonal"};
+    k_ss_split<<<blocks_for(n, 128), 128, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(),
+                                                  c->ss_colour.as<int32_t>(), perm, B->inv.as<int32_t>(),
+                                                  B->prp.as<int64_t>(), n, B->pcol.as<int32_t>(),
+                                                  B->psrc.as<int32_t>(), B->psp.as<int64_t>(), bad);
+    c->launches++;
+    PG_CUDA(cudaGetLastError());
+    int32_t hbad = 0;
+    PG_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    if (hbad) return Status{PETGEM_ERR_CUDA, "SSOR layout: the colouring does not match the pattern"};
+    return Status{};
+  };
+  const Status st = body();
+  cudaStreamSynchronize(s);  // the work buffer is released on return
+  work.release();
+  if (!st.ok()) return st;
+  B->noff = m;
+  B->layout = c->mesh_version;
+  B->version = -1;  // values follow the new layout
+  return Status{};
+}
+
 Status ss_setup(petgem_ctx* c, double omega, SsLaunch& L) {
   PG_TRY(ssor_colouring(c));
   SsBuffers* B = ss_bufs(c);
+  PG_TRY(ss_layout(c, B));
   const int64_t n = c->n_edges;
-  for (DevBuf* d : {&B->inv_d, &B->r64, &B->r, &B->t, &B->y, &B->u, &B->qa, &B->qb, &B->dv, &B->e})
+  for (DevBuf* d : {&B->r64, &B->r, &B->t, &B->y, &B->u, &B->qa, &B->qb, &B->dv, &B->e, &B->dg128, &B->id128})
     PG_TRY(d->reserve(n * sizeof(double2)));
-  PG_TRY(B->inv_d64.reserve(n * sizeof(float2)));
+  PG_TRY(B->dg64.reserve(n * sizeof(float2)));
+  PG_TRY(B->id64.reserve(n * sizeof(float2)));
   PG_TRY(B->absd.reserve(n * sizeof(double)));
-  PG_TRY(B->val64.reserve(c->nnz * sizeof(float2)));
+  PG_TRY(B->pv128.reserve(std::max<int64_t>(B->noff, 1) * sizeof(double2)));
+  PG_TRY(B->pv64.reserve(std::max<int64_t>(B->noff, 1) * sizeof(float2)));
   PG_TRY(B->state.reserve(sizeof(SsState)));
   const int ncol = (int)c->ss_off.size() - 1;
   L.c = c;
@@ -524,23 +650,32 @@ Status ss_setup(petgem_ctx* c, double omega, SsLaunch& L) {
   PG_TRY(B->part.reserve((size_t)std::max<int64_t>(L.np_sweep, L.nb) * sizeof(double2)));
   PG_CUDA(cudaMemsetAsync(B->state.ptr, 0, sizeof(SsState), c->stream));
   if (B->version != c->assembly_version) {
-    k_ss_diag<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->diag.as<double2>(), n, B->inv_d.as<double2>(),
+    if (B->noff > 0)
+      k_ss_values<<<blocks_for(B->noff, 256), 256, 0, c->stream>>>(B->psrc.as<int32_t>(), B->noff,
+                                                                   c->val.as<double2>(), B->pv128.as<double2>(),
+                                                                   B->pv64.as<float2>());
+    k_ss_diag<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->diag.as<double2>(), c->ss_rows.as<int32_t>(), n,
+                                                         B->dg128.as<double2>(), B->dg64.as<float2>(),
+                                                         B->id128.as<double2>(), B->id64.as<float2>(),
                                                          B->absd.as<double>());
-    k_ss_to64<<<blocks_for(n, 256), 256, 0, c->stream>>>(B->inv_d.as<double2>(), n, B->inv_d64.as<float2>());
-    k_ss_to64<<<blocks_for(c->nnz, 256), 256, 0, c->stream>>>(c->val.as<double2>(), c->nnz, B->val64.as<float2>());
-    c->launches += 3;
+    c->launches += 2;
     PG_CUDA(cudaGetLastError());
     B->version = c->assembly_version;
   }
   return Status{};
 }
 
-template <typename T> const T* ss_val(const SsLaunch& L);
-template <> const double2* ss_val<double2>(const SsLaunch& L) { return L.c->val.as<double2>(); }
-template <> const float2* ss_val<float2>(const SsLaunch& L) { return L.B->val64.as<float2>(); }
-template <typename T> const T* ss_inv_d(const SsLaunch& L);
-template <> const double2* ss_inv_d<double2>(const SsLaunch& L) { return L.B->inv_d.as<double2>(); }
-template <> const float2* ss_inv_d<float2>(const SsLaunch& L) { return L.B->inv_d64.as<float2>(); }
+template <typename T> struct SsVals;
+template <> struct SsVals<double2> {
+  static const double2* pv(const SsBuffers* B) { return B->pv128.as<double2>(); }
+  static const double2* dg(const SsBuffers* B) { return B->dg128.as<double2>(); }
+  static const double2* id(const SsBuffers* B) { return B->id128.as<double2>(); }
+};
+template <> struct SsVals<float2> {
+  static const float2* pv(const SsBuffers* B) { return B->pv64.as<float2>(); }
+  static const float2* dg(const SsBuffers* B) { return B->dg64.as<float2>(); }
+  static const float2* id(const SsBuffers* B) { return B->id64.as<float2>(); }
+};
 
 // One sweep over all colours (ascending for the forward one).
 template <typename T>
@@ -548,17 +683,17 @@ Status ss_forward(const SsLaunch& L, const T* t, T* r, T* y, int iter) {
   petgem_ctx* c = L.c;
   const int ncol = (int)c->ss_off.size() - 1;
   const double vb = sizeof(T);
-  // values and columns, the colour of every column, row pointers and ids, y gathered once;
-  // r read (and written), t, 1 / d, |d| read, y written
-  const double bytes = (double)c->nnz * (vb + 8) + 12.0 * L.n + L.n * (vb * (iter ? 6 : 4) + 8);
+  // the lower halves (values and columns, y gathered once), row offsets and splits; r read (and
+  // written), t, 1 / d, |d| read, y written
+  const double bytes = 0.5 * (double)L.B->noff * (vb + 4) + 16.0 * L.n + L.n * (vb * (iter ? 6 : 4) + 8);
   KernelTimer kt(c, sizeof(T) == 16 ? "ssor_forward_c128" : "ssor_forward_c64", bytes);
   for (int k = 0; k < ncol; ++k) {
     const int64_t cnt = c->ss_off[k + 1] - c->ss_off[k];
     if (cnt == 0) continue;
     k_ss_forward<T><<<blocks_for(cnt * kSsLanes, kSsThreads), kSsThreads, 0, c->stream>>>(
-        c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), ss_val<T>(L), c->ss_colour.as<int32_t>(),
-        c->ss_rows.as<int32_t>() + c->ss_off[k], cnt, k, L.omega, ss_inv_d<T>(L), L.B->absd.as<double>(), t, r, y,
-        L.B->state.as<SsState>(), L.B->part.as<double2>() + L.pbase[k], iter);
+        L.B->prp.as<int64_t>(), L.B->psp.as<int64_t>(), L.B->pcol.as<int32_t>(), SsVals<T>::pv(L.B), c->ss_off[k], cnt,
+        L.omega, SsVals<T>::id(L.B), L.B->absd.as<double>(), t, r, y, L.B->state.as<SsState>(),
+        L.B->part.as<double2>() + L.pbase[k], iter);
     c->launches++;
   }
   PG_CUDA(cudaGetLastError());
@@ -570,16 +705,17 @@ Status ss_backward(const SsLaunch& L, const T* y, T* u, const T* r, const T* q, 
   petgem_ctx* c = L.c;
   const int ncol = (int)c->ss_off.size() - 1;
   const double vb = sizeof(T);
-  // as the forward sweep; y, r, 1 / d read, u written, and with iter d, q, e read and d, e written
-  const double bytes = (double)c->nnz * (vb + 8) + 12.0 * L.n + L.n * vb * (iter ? 9 : 5);
+  // the upper halves as the forward sweep's lower ones; y, r, 1 / d read, u written, and with
+  // iter d, q, e read and d, e written
+  const double bytes = 0.5 * (double)L.B->noff * (vb + 4) + 16.0 * L.n + L.n * vb * (iter ? 9 : 5);
   KernelTimer kt(c, sizeof(T) == 16 ? "ssor_backward_c128" : "ssor_backward_c64", bytes);
   for (int k = ncol - 1; k >= 0; --k) {
     const int64_t cnt = c->ss_off[k + 1] - c->ss_off[k];
     if (cnt == 0) continue;
     k_ss_backward<T><<<blocks_for(cnt * kSsLanes, kSsThreads), kSsThreads, 0, c->stream>>>(
-        c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), ss_val<T>(L), c->ss_colour.as<int32_t>(),
-        c->ss_rows.as<int32_t>() + c->ss_off[k], cnt, k, L.omega, ss_inv_d<T>(L), y, u, r, q, L.B->dv.as<T>(), e,
-        L.B->state.as<SsState>(), L.B->part.as<double2>() + L.pbase[k], iter);
+        L.B->prp.as<int64_t>(), L.B->psp.as<int64_t>(), L.B->pcol.as<int32_t>(), SsVals<T>::pv(L.B), c->ss_off[k], cnt,
+        L.omega, SsVals<T>::id(L.B), y, u, r, q, L.B->dv.as<T>(), e, L.B->state.as<SsState>(),
+        L.B->part.as<double2>() + L.pbase[k], iter);
     c->launches++;
   }
   PG_CUDA(cudaGetLastError());
@@ -640,7 +776,9 @@ Status ssor_sqmr_source(const SsLaunch& L, const petgem_solve_opts& o, const dou
     return Status{};
   }
   const double vb = sizeof(T);
-  const double spmv_bytes = (double)c->nnz * (vb + 4) + 8.0 * (n + 1) + vb * n * 6;
+  // off-diagonal values and columns, row offsets, the diagonal; u and q_old gathered once and
+  // read by row, q_new and t written
+  const double spmv_bytes = (double)B->noff * (vb + 4) + 8.0 * (n + 1) + vb * n * 7;
   int64_t iters = 0, solves = 0;
   double relres = 0.0, prev = INFINITY;
   int status = PETGEM_OK, stalls = 0;
@@ -672,7 +810,8 @@ Status ssor_sqmr_source(const SsLaunch& L, const petgem_solve_opts& o, const dou
     const double need = 0.3 * o.tol * bnorm / rnorm;
     const double inner = c128 ? need : std::min(std::max(o.inner_tol, need), 0.5);
     const int64_t kmax = std::min<int64_t>(o.max_iters - iters, c128 ? INT64_MAX : kSsInnerMax);
-    k_ss_start<T><<<blocks_for(n, 256), 256, 0, c->stream>>>(B->r64.as<double2>(), 1.0 / rnorm, n, r, e);
+    k_ss_start<T><<<blocks_for(n, 256), 256, 0, c->stream>>>(B->r64.as<double2>(), c->ss_rows.as<int32_t>(),
+                                                             1.0 / rnorm, n, r, e);
     c->launches++;
     PG_CUDA(cudaMemsetAsync(B->state.ptr, 0, sizeof(SsState), c->stream));  // running again
     PG_TRY(ss_forward<T>(L, nullptr, r, y, 0));
@@ -683,9 +822,10 @@ Status ssor_sqmr_source(const SsLaunch& L, const petgem_solve_opts& o, const dou
     for (int64_t it = 0;; ++it) {
       {
         KernelTimer kt(c, c128 ? "ssor_spmv_c128" : "ssor_spmv_c64", spmv_bytes);
-        k_ss_spmv<T><<<L.nb, kSsThreads, 0, c->stream>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(),
-                                                         ss_val<T>(L), n, u, qbuf[cur], qbuf[cur ^ 1], t,
-                                                         B->state.as<SsState>(), B->part.as<double2>(), it == 0);
+        k_ss_spmv<T><<<L.nb, kSsThreads, 0, c->stream>>>(B->prp.as<int64_t>(), B->pcol.as<int32_t>(),
+                                                         SsVals<T>::pv(B), SsVals<T>::dg(B), n, u, qbuf[cur],
+                                                         qbuf[cur ^ 1], t, B->state.as<SsState>(),
+                                                         B->part.as<double2>(), it == 0);
         c->launches++;
       }
       PG_CUDA(cudaGetLastError());
@@ -700,7 +840,7 @@ Status ssor_sqmr_source(const SsLaunch& L, const petgem_solve_opts& o, const dou
         if (hs.done) break;
       }
     }
-    k_ss_finish<T><<<blocks_for(n, 256), 256, 0, c->stream>>>(e, rnorm, n, x);
+    k_ss_finish<T><<<blocks_for(n, 256), 256, 0, c->stream>>>(e, c->ss_rows.as<int32_t>(), rnorm, n, x);
     c->launches++;
     PG_CUDA(cudaGetLastError());
     iters += hs.k;
@@ -743,10 +883,16 @@ Status run_solve_ssor(petgem_ctx* c, const petgem_solve_opts& o, double2* x, pet
 Status run_ssor_apply(petgem_ctx* c, double omega, const double2* r_in, double2* z) {
   SsLaunch L;
   PG_TRY(ss_setup(c, omega, L));
-  double2* r = L.B->r.as<double2>();
-  PG_CUDA(cudaMemcpyAsync(r, r_in, L.n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  double2 *r = L.B->r.as<double2>(), *u = L.B->u.as<double2>();
+  const int32_t* perm = c->ss_rows.as<int32_t>();
+  k_ss_start<double2><<<blocks_for(L.n, 256), 256, 0, c->stream>>>(r_in, perm, 1.0, L.n, r, L.B->e.as<double2>());
+  c->launches++;
+  PG_CUDA(cudaGetLastError());
   PG_TRY(ss_forward<double2>(L, nullptr, r, L.B->y.as<double2>(), 0));
-  PG_TRY(ss_backward<double2>(L, L.B->y.as<double2>(), z, r, nullptr, nullptr, 0));
+  PG_TRY(ss_backward<double2>(L, L.B->y.as<double2>(), u, r, nullptr, nullptr, 0));
+  k_ss_scatter<<<blocks_for(L.n, 256), 256, 0, c->stream>>>(u, perm, L.n, z);
+  c->launches++;
+  PG_CUDA(cudaGetLastError());
   PG_CUDA(cudaStreamSynchronize(c->stream));
   return Status{};
 }
@@ -754,8 +900,9 @@ Status run_ssor_apply(petgem_ctx* c, double omega, const double2* r_in, double2*
 void destroy_ssor(petgem_ctx* c) {
   if (!c->ssor) return;
   SsBuffers* B = static_cast<SsBuffers*>(c->ssor);
-  for (DevBuf* d : {&B->inv_d, &B->inv_d64, &B->absd, &B->val64, &B->r64, &B->r, &B->t, &B->y, &B->u, &B->qa, &B->qb,
-                    &B->dv, &B->e, &B->state, &B->part})
+  for (DevBuf* d : {&B->prp, &B->psp, &B->pcol, &B->psrc, &B->inv, &B->pv128, &B->pv64, &B->dg128, &B->dg64, &B->id128,
+                    &B->id64, &B->absd, &B->r64, &B->r, &B->t, &B->y, &B->u, &B->qa, &B->qb, &B->dv, &B->e, &B->state,
+                    &B->part})
     d->release();
   delete B;
   c->ssor = nullptr;
