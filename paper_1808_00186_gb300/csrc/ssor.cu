@@ -273,6 +273,56 @@ template <typename T> __device__ __forceinline__ T ss_lanes_sum_t(T a) {
   return a;
 }
 
+// acc += sum over the slots [beg, end) of lane `lane` (every kSsLanes-th slot) of pv[k] x[pcol[k]]:
+// kSsU slots per lane at a time, their columns and values loaded together, then the gathers, then
+// the products, so that each lane keeps kSsU loads in flight (a row's half holds at most ~18).
+constexpr int kSsU = 5;
+template <typename T>
+__device__ __forceinline__ void ss_row_sum(const int32_t* __restrict__ pcol, const T* __restrict__ pv,
+                                           const T* __restrict__ x, int64_t beg, int64_t end, int lane, T& acc) {
+  for (int64_t b = beg + lane; b < end; b += kSsLanes * kSsU) {
+    int32_t j[kSsU];
+    T a[kSsU], xv[kSsU];
+#pragma unroll
+    for (int u = 0; u < kSsU; ++u) {
+      const int64_t k = b + (int64_t)u * kSsLanes;
+      j[u] = k < end ? pcol[k] : -1;
+      a[u] = k < end ? pv[k] : ss_zero<T>();
+    }
+#pragma unroll
+    for (int u = 0; u < kSsU; ++u) xv[u] = j[u] >= 0 ? x[j[u]] : ss_zero<T>();
+#pragma unroll
+    for (int u = 0; u < kSsU; ++u) ss_fma(acc, a[u], xv[u]);
+  }
+}
+
+// The same for the product with q_new = u + beta q_old formed on the fly (first: q_new = u).
+template <typename T>
+__device__ __forceinline__ void ss_row_sum2(const int32_t* __restrict__ pcol, const T* __restrict__ pv,
+                                            const T* __restrict__ u, const T* __restrict__ qold, T beta, bool first,
+                                            int64_t beg, int64_t end, int lane, T& acc) {
+  for (int64_t b = beg + lane; b < end; b += kSsLanes * kSsU) {
+    int32_t j[kSsU];
+    T a[kSsU], uv[kSsU], qv[kSsU];
+#pragma unroll
+    for (int k = 0; k < kSsU; ++k) {
+      const int64_t s = b + (int64_t)k * kSsLanes;
+      j[k] = s < end ? pcol[s] : -1;
+      a[k] = s < end ? pv[s] : ss_zero<T>();
+    }
+#pragma unroll
+    for (int k = 0; k < kSsU; ++k) {
+      uv[k] = j[k] >= 0 ? u[j[k]] : ss_zero<T>();
+      qv[k] = (j[k] >= 0 && !first) ? qold[j[k]] : ss_zero<T>();
+    }
+#pragma unroll
+    for (int k = 0; k < kSsU; ++k) {
+      ss_fma(uv[k], beta, qv[k]);
+      ss_fma(acc, a[k], uv[k]);
+    }
+  }
+}
+
 // Inner right-hand side r = T(r64 * scale) in the new order and correction e = 0.
 template <typename T>
 __global__ void k_ss_start(const double2* __restrict__ r64, const int32_t* __restrict__ perm, double scale, int64_t n,
@@ -310,8 +360,7 @@ __global__ void __launch_bounds__(kSsThreads) k_ss_forward(const int64_t* __rest
   const int lane = threadIdx.x & (kSsLanes - 1);
   const int64_t i = r0 + g;
   T acc = ss_zero<T>();
-  if (g < cnt)
-    for (int64_t q = prp[i] + lane; q < psp[i]; q += kSsLanes) ss_fma(acc, pv[q], y[pcol[q]]);
+  if (g < cnt) ss_row_sum(pcol, pv, y, prp[i], psp[i], lane, acc);
   acc = ss_lanes_sum_t(acc);
   double s = 0.0;
   if (g < cnt && lane == 0) {
@@ -353,8 +402,7 @@ __global__ void __launch_bounds__(kSsThreads) k_ss_backward(const int64_t* __res
   const int lane = threadIdx.x & (kSsLanes - 1);
   const int64_t i = r0 + g;
   T acc = ss_zero<T>();
-  if (g < cnt)
-    for (int64_t k = psp[i] + lane; k < prp[i + 1]; k += kSsLanes) ss_fma(acc, pv[k], u[pcol[k]]);
+  if (g < cnt) ss_row_sum(pcol, pv, u, psp[i], prp[i + 1], lane, acc);
   acc = ss_lanes_sum_t(acc);
   double2 s = make_double2(0.0, 0.0);
   if (g < cnt && lane == 0) {
@@ -399,13 +447,7 @@ __global__ void __launch_bounds__(kSsThreads) k_ss_spmv(const int64_t* __restric
   const int lane = threadIdx.x & (kSsLanes - 1);
   const T beta = ss_t<T>(st->beta);
   T acc = ss_zero<T>();
-  if (i < n)
-    for (int64_t k = prp[i] + lane; k < prp[i + 1]; k += kSsLanes) {
-      const int32_t j = pcol[k];
-      T qj = u[j];
-      if (!first) ss_fma(qj, beta, qold[j]);
-      ss_fma(acc, pv[k], qj);
-    }
+  if (i < n) ss_row_sum2(pcol, pv, u, qold, beta, first != 0, prp[i], prp[i + 1], lane, acc);
   acc = ss_lanes_sum_t(acc);
   double2 s = make_double2(0.0, 0.0);
   if (i < n && lane == 0) {
