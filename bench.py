@@ -43,7 +43,8 @@ def parse():
     p.add_argument("--profile-step", action="store_true",
                    help="run one untimed step of the hot path and exit (the command profilers capture)")
     p.add_argument("--precision", default="mixed", choices=["mixed", "c128"], help="solver of --profile-step")
-    p.add_argument("--solver", default="gmres", choices=["gmres", "cocg"], help="Krylov method of --profile-step / --profile-block")
+    p.add_argument("--solver", default="gmres", choices=["gmres", "cocg", "ssor"],
+                   help="Krylov method of --profile-step / --profile-block (ssor: SQMR with the SSOR preconditioner)")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-network measurement")
     p.add_argument("--no-cocg", action="store_true", help="skip the COCG measurement")
     p.add_argument("--no-batch", action="store_true", help="skip the batch of uneven meshes")
@@ -218,9 +219,12 @@ def run_ours(args):
         ctx.close()
         return None
 
+    if args.profile_block and args.solver == "ssor":
+        raise SystemExit("--profile-block runs GMRES or COCG")
     if args.profile_step:
-        info, _ = step(api.PREC_MIXED if args.precision == "mixed" else api.PREC_C128,
-                       api.METHOD_COCG if args.solver == "cocg" else api.METHOD_GMRES)
+        method = {"gmres": api.METHOD_GMRES, "cocg": api.METHOD_COCG, "ssor": api.METHOD_SQMR}[args.solver]
+        info, _ = step(api.PREC_MIXED if args.precision == "mixed" else api.PREC_C128, method,
+                       precond=api.PRECOND_SSOR if args.solver == "ssor" else api.PRECOND_JACOBI)
         torch.cuda.synchronize()
         print(json.dumps({"profile_step": True, "n": args.n, "edges": n_edges[0], "info": info,
                           "launches": api.petgem_launch_count(ctx.h)}))
