@@ -95,7 +95,7 @@ typedef struct {
                           solve configuration (Jacobi preconditioner; ignored with the learned
                           one, while kernel profiling is on, and by COCG, whose iterations run in
                           one persistent kernel); results are identical to direct launches */
-  int32_t method;      /* PETGEM_METHOD_GMRES (default) or PETGEM_METHOD_COCG */
+  int32_t method;      /* PETGEM_METHOD_GMRES (default), PETGEM_METHOD_COCG or PETGEM_METHOD_SQMR */
   int32_t spmv_lanes;  /* petgem_solve_batch: layout of the sparse product: 2, 4 or 8 = CSR with that
                           many lanes per row, 1 = SELL-32 with rows grouped by edge kind (CSR with
                           4 lanes when a mesh lacks that layout); 0 = chosen by the autotuner;
