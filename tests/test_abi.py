@@ -40,6 +40,17 @@ def test_status_strings_without_gpu(lib_path):
     assert L.petgem_solve_batch(None, 0, None, None, None) == api.OK  # nothing to do
     assert L.petgem_solve_batch(None, 1, None, None, None) == api.ERR_INVALID_ARG
     assert L.petgem_assemble_frequency(None, 1.0, 1, None) == api.ERR_INVALID_ARG
+    # the SSOR ordering and preconditioner entry points
+    assert L.petgem_colouring(None, None, None, None) == api.ERR_INVALID_ARG
+    assert L.petgem_ssor_apply(None, 1.0, None, None) == api.ERR_INVALID_ARG
+
+
+def test_solve_opts_layout_matches_the_header():
+    # the omega field closes the struct: int32 x4, double x2, int64, int32 x4, double = 64 bytes
+    assert ctypes.sizeof(api.petgem_solve_opts) == 64
+    assert api.petgem_solve_opts.omega.offset == 56
+    o = api.solve_opts(precond=api.PRECOND_SSOR, method=api.METHOD_SQMR, omega=1.2)
+    assert (o.precond, o.method, o.omega) == (2, 2, 1.2)
 
 
 def test_no_cpu_fallback_when_library_missing(tmp_path):
