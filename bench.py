@@ -195,6 +195,8 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    step_ms = []  # per-step times of the last timed() call (CUDA events between steps)
+
     def timed(precision, steps, warmup, profile=False, clocks=None, method=api.METHOD_GMRES, graphs=1,
               precond=api.PRECOND_JACOBI):
         for _ in range(warmup):
@@ -205,15 +207,16 @@ def run_ours(args):
         launches0 = api.petgem_launch_count(ctx.h)
         if clocks:
             clocks.start()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        evs[0].record()
         infos = []
-        for _ in range(steps):
+        for k in range(steps):
             infos.append(step(precision, method, graphs, precond)[0])
-        e1.record()
+            evs[k + 1].record()
         barrier()
         cl = clocks.stop() if clocks else None
-        ms = e0.elapsed_time(e1) / steps
+        ms = evs[0].elapsed_time(evs[-1]) / steps
+        step_ms[:] = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
         launches = (api.petgem_launch_count(ctx.h) - launches0) // steps
         return max_over_ranks(ms, world, dev), infos[-1], launches, cl
 
@@ -252,6 +255,8 @@ def run_ours(args):
     # the per-kernel times come from one more step of the same workload with the events on (direct
     # launches), right after.
     ms_mixed, info_mixed, launches, cl = timed(api.PREC_MIXED, args.steps, args.warmup, clocks=clocks)
+    head_steps = list(step_ms)
+    ms_median = max_over_ranks(statistics.median(head_steps), world, dev)
     ms_events, _, _, _ = timed(api.PREC_MIXED, 1, 0, profile=True)
     # Dominant kernel over that step (CUDA events around each launch on the ctx stream).
     kstats = {}
@@ -544,6 +549,8 @@ def run_ours(args):
             "steps": args.steps,
             "warmup": args.warmup,
             "ms_per_step": round(ms_mixed, 3),
+            "ms_per_step_median": round(ms_median, 3),
+            "ms_per_step_each": [round(x, 3) for x in head_steps],
             "ms_per_step_with_kernel_events": round(ms_events, 3),
             "ms_per_step_without_graphs": round(ms_direct, 3),
             "higher_is_better": False,
