@@ -1,5 +1,6 @@
-// Multicolour symmetric SOR (SSOR) preconditioner and the SQMR solver it preconditions, complex128:
-// the configuration of the paper's Section 5.3 runs (SQMR with an SOR preconditioner).
+// Multicolour symmetric SOR (SSOR) preconditioner and the SQMR solver it preconditions: the
+// configuration of the paper's Section 5.3 runs (SQMR with an SOR preconditioner).  FP64 residuals
+// around inner solves in complex64 or complex128.
 //
 // Colouring.  A Gauss-Seidel sweep is sequential row by row; on the GPU the rows are coloured so
 // that rows of one colour share no matrix entry and the sweep takes one colour per launch, all its
@@ -8,7 +9,7 @@
 // uncoloured row whose key exceeds those of all its uncoloured neighbours takes the smallest colour
 // none of its coloured neighbours holds.  The result is the greedy colouring in decreasing key
 // order, deterministic and independent of the launch shape.  Neighbours are the off-diagonal
-// entries of the CSR pattern; a Kuhn mesh's edge matrix takes about 12 colours in about 35 rounds.
+// entries of the CSR pattern; a Kuhn mesh's edge matrix takes 12 or 13 colours in 35 to 40 rounds.
 //
 // SSOR.  With A = D + L + U split in the colour order (L: entries whose column has a lower colour
 // than the row, U: a higher one), M = (D + w L) D^{-1} (D + w U), complex symmetric because
