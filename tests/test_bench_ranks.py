@@ -51,3 +51,13 @@ def test_one_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(2.0, 1) == 2.0
     assert bench.job_seconds_per_source(2.0, 4, 1) == 0.5
+
+
+def test_cpu_baseline_host_facts_and_all_cores_leg():
+    sys.path.insert(0, ROOT)
+    import bench
+    info = bench.host_info()
+    assert info["nproc"] >= 1 and info["cpu_model"]
+    r = bench.oracle_all_cores(4, 100)  # a 4^3 sample in every process
+    assert 1 <= r["processes"] <= info["nproc"]
+    assert r["value"] == pytest.approx(r["per_process_s"] / r["processes"])
