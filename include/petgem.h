@@ -256,9 +256,12 @@ int petgem_spmv(petgem_ctx *ctx, const void *x, void *y);
  * colours (a row with more than 63 neighbours) or E >= 2^31. */
 int petgem_colouring(petgem_ctx *ctx, int32_t *colour, int32_t *n_colours, int32_t *n_rounds);
 
-/* z = M^{-1} r for the SSOR preconditioner above (forward sweep, scaling by D, backward sweep).
- * r, z: device complex128[E], distinct.  omega as in petgem_solve_opts (0 = 1).  Needs
- * petgem_assemble.  Synchronises the stream. */
+/* z = M^{-1} r for the SSOR preconditioner above (forward sweep, scaling by D, backward sweep),
+ * in FP64.  r, z: device complex128[E] in the edge order, caller-owned, distinct (r is only read).
+ * omega as in petgem_solve_opts (0 = 1).  Needs petgem_assemble; computes the colouring first if
+ * the mesh has none yet.  Synchronises the stream.
+ * Errors: PETGEM_ERR_INVALID_ARG (not assembled, null or aliased vectors, omega outside (0, 2)),
+ * the colouring's errors (petgem_colouring). */
 int petgem_ssor_apply(petgem_ctx *ctx, double omega, const void *r, void *z);
 
 /* ----------------------------------------------------------------------- receivers (eq. 7) */
