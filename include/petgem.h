@@ -81,7 +81,9 @@ enum { PETGEM_PRECOND_JACOBI = 0, PETGEM_PRECOND_LEARNED = 1, PETGEM_PRECOND_SSO
  *     colour, M = (D + omega L) D^{-1} (D + omega U), applied to SQMR as the symmetric split
  *     M1 = (D + omega L) D^{-1/2}, M2 = M1^T.  Each SQMR step costs a forward and a backward
  *     sweep (one launch per colour each) besides the product.  Precision as for COCG: FP64
- *     residuals around inner solves in complex64 (MIXED) or complex128 (C128). */
+ *     residuals around inner solves in complex64 (MIXED) or complex128 (C128).  Sources are
+ *     solved one after the other (`batch` and `use_graphs` are ignored); `omega` sets the
+ *     relaxation factor. */
 typedef struct {
   int32_t restart;
   int32_t precision;
