@@ -305,7 +305,10 @@ int petgem_learned_apply(petgem_ctx *ctx, const void *r, void *z);
  * [27][cout][cin] with tap t = (dx+1) + 3 (dy+1) + 9 (dz+1), zero "same" padding; cin, cout in
  * {16, 32}.  petgem_nn_conv3d: y[v][co] = bias[co] + sum_t,ci W[t][co][ci] x[v + d_t][ci], ReLU
  * when relu != 0, y BF16 (y_fp32 = 0) or FP32 [V][cout].  petgem_nn_conv3d_wgrad: dw[t][co][ci] =
- * sum_v dy[v][co] x[v + d_t][ci] (FP32).  All pointers device; work ordered on `stream`. */
+ * sum_v dy[v][co] x[v + d_t][ci] (FP32).  All pointers device; work ordered on `stream`.
+ * Errors: a dimension < 1 or a null pointer: PETGEM_ERR_INVALID_ARG; gx gy gz 32 >= 2^31 (the
+ * kernels index voxel channels in 32 bits) or cin / cout not in {16, 32}: PETGEM_ERR_UNSUPPORTED,
+ * nothing launched. */
 int petgem_nn_conv3d(void *stream, int32_t gx, int32_t gy, int32_t gz, int32_t cin, int32_t cout, const void *x,
                      const void *w, const float *bias, int32_t relu, void *y, int32_t y_fp32);
 int petgem_nn_conv3d_wgrad(void *stream, int32_t gx, int32_t gy, int32_t gz, int32_t cin, int32_t cout, const void *x,
@@ -320,7 +323,8 @@ int petgem_nn_conv3d_wgrad(void *stream, int32_t gx, int32_t gy, int32_t gz, int
  * a release can synchronise the device): it calls no cudaMalloc, cudaMallocAsync, cudaFree or
  * other allocating routine, and works in a fixed scratch array of the library's device code
  * (3.4 MB per device) that holds grids of at most PETGEM_NOALLOC_MAX_VOXELS voxels.
- *   - gx gy gz > PETGEM_NOALLOC_MAX_VOXELS, or cin / cout not in {16, 32}: PETGEM_ERR_UNSUPPORTED,
+ *   - any of gx, gy, gz or their product > PETGEM_NOALLOC_MAX_VOXELS (each dimension is checked
+ *     before the product is formed, so no product wraps), or cin / cout not in {16, 32}: PETGEM_ERR_UNSUPPORTED,
  *     nothing launched and dw untouched.  Null pointer or a dimension < 1: PETGEM_ERR_INVALID_ARG.
  *   - The first call on a device looks the scratch's address up (cudaGetSymbolAddress, with that
  *     device current; PETGEM_ERR_CUDA if it fails); make that first call before any stream capture.

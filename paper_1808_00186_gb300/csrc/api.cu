@@ -540,6 +540,7 @@ int petgem_learned_apply(petgem_ctx* c, const void* r, void* z) {
 int petgem_nn_conv3d(void* stream, int32_t gx, int32_t gy, int32_t gz, int32_t cin, int32_t cout, const void* x,
                      const void* w, const float* bias, int32_t relu, void* y, int32_t y_fp32) {
   if (gx < 1 || gy < 1 || gz < 1 || !x || !w || !bias || !y) return PETGEM_ERR_INVALID_ARG;
+  if (!petgem::nn::grid_fits(gx, gy, gz)) return PETGEM_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int* err = nullptr;
   if (cudaMallocAsync((void**)&err, sizeof(int), s) != cudaSuccess) return PETGEM_ERR_OUT_OF_MEMORY;
@@ -556,6 +557,7 @@ int petgem_nn_conv3d(void* stream, int32_t gx, int32_t gy, int32_t gz, int32_t c
 int petgem_nn_conv3d_wgrad(void* stream, int32_t gx, int32_t gy, int32_t gz, int32_t cin, int32_t cout, const void* x,
                            const void* dy, float* dw) {
   if (gx < 1 || gy < 1 || gz < 1 || !x || !dy || !dw) return PETGEM_ERR_INVALID_ARG;
+  if (!petgem::nn::grid_fits(gx, gy, gz)) return PETGEM_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t V = (int64_t)gx * gy * gz;
   const int splits = petgem::nn::wgrad_splits(V);

@@ -45,6 +45,14 @@ Status conv3d(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, const _
 Status conv3d_wgrad(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, const __nv_bfloat16* x,
                     const __nv_bfloat16* dy, float* part, int splits, float* dw, bool accumulate, int* err);
 int wgrad_splits(int64_t V);
+// The convolution kernels index voxels (and voxels x 32 channels) in 32 bits: a grid fits when
+// gx gy gz 32 < 2^31.  Each factor is bounded before the next product, so nothing wraps.
+inline bool grid_fits(int64_t gx, int64_t gy, int64_t gz) {
+  const int64_t lim = (int64_t(1) << 31) / 32;
+  if (gx < 1 || gy < 1 || gz < 1 || gx > lim || gy > lim || gz > lim) return false;
+  const int64_t xy = gx * gy;
+  return xy < lim && xy * gz < lim;
+}
 Status edge_slots(cudaStream_t s, const int32_t* edges, int64_t E, int gx, int gy, int gz, int32_t* slot, int* bad);
 Status check_err(cudaStream_t s, const int* err, const char* where);
 // r = b - A x and du = D (x* - x) for the context's assembled system (source 0), complex128.

@@ -62,8 +62,12 @@ extern "C" int petgem_nn_conv3d_wgrad_noalloc(void* stream, int32_t gx, int32_t 
                                               int32_t cout, const void* x, const void* dy, float* dw) {
   if (gx < 1 || gy < 1 || gz < 1 || !x || !dy || !dw) return PETGEM_ERR_INVALID_ARG;
   if ((cin != 16 && cin != 32) || (cout != 16 && cout != 32)) return PETGEM_ERR_UNSUPPORTED;
+  // Each dimension is checked before the product is formed: three dimensions up to the limit
+  // multiply to at most 2^51, so the 64-bit product below cannot wrap.
+  const int64_t lim = PETGEM_NOALLOC_MAX_VOXELS;
+  if (gx > lim || gy > lim || gz > lim) return PETGEM_ERR_UNSUPPORTED;
   const int64_t V = (int64_t)gx * gy * gz;
-  if (V > PETGEM_NOALLOC_MAX_VOXELS) return PETGEM_ERR_UNSUPPORTED;  // beyond the fixed scratch
+  if (V > lim) return PETGEM_ERR_UNSUPPORTED;  // beyond the fixed scratch
   const int splits = petgem::nn::wgrad_splits(V);
   if (splits > kMaxSplits) return PETGEM_ERR_UNSUPPORTED;
   unsigned char* base = nullptr;

@@ -72,3 +72,16 @@ def test_noalloc_limit_matches_header_and_is_checked_on_the_host(lib_path):
     assert L.petgem_nn_conv3d_wgrad_noalloc(None, 64, 64, 33, 16, 16, fake, fake, fake) == api.ERR_UNSUPPORTED
     assert L.petgem_nn_conv3d_wgrad_noalloc(None, 8, 8, 8, 24, 16, fake, fake, fake) == api.ERR_UNSUPPORTED
     assert L.petgem_nn_conv3d_wgrad_noalloc(None, 0, 8, 8, 16, 16, fake, fake, fake) == api.ERR_INVALID_ARG
+
+
+def test_conv_grids_whose_voxel_count_wraps_are_rejected_on_the_host(lib_path):
+    """Dimensions whose product overflows 64 bits (2^21 + 1 cubed wraps negative) or exceeds the
+    kernels' 32-bit voxel indexing are refused before any CUDA call, with nothing written."""
+    L = api.load(lib_path)
+    fake = ctypes.c_void_p(256)  # never dereferenced
+    big = 2 ** 21 + 1
+    assert L.petgem_nn_conv3d_wgrad_noalloc(None, big, big, big, 16, 16, fake, fake, fake) == api.ERR_UNSUPPORTED
+    assert L.petgem_nn_conv3d_wgrad_noalloc(None, 131073, 1, 1, 16, 16, fake, fake, fake) == api.ERR_UNSUPPORTED
+    assert L.petgem_nn_conv3d_wgrad(None, big, big, big, 16, 16, fake, fake, fake) == api.ERR_UNSUPPORTED
+    assert L.petgem_nn_conv3d_wgrad(None, 1024, 1024, 64, 16, 16, fake, fake, fake) == api.ERR_UNSUPPORTED
+    assert L.petgem_nn_conv3d(None, big, big, big, 16, 16, fake, fake, fake, 0, fake, 1) == api.ERR_UNSUPPORTED
