@@ -722,6 +722,13 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
         status = PETGEM_ERR_NOT_CONVERGED;
         break;
       }
+      if (hs.k == 0 && hs.done != 2) {
+        // The cycle stopped before its first step although the FP64 residual is above tol (its
+        // working-precision start vector had norm zero, e.g. every entry of r underflowed in
+        // complex64): a repeat would do the same, so stop instead of cycling without progress.
+        status = PETGEM_ERR_BREAKDOWN;
+        break;
+      }
       iters += hs.k;
       cycles += 1;
       reorth += hs.n_refine;

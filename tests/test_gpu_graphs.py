@@ -69,3 +69,29 @@ def test_graph_recaptured_for_a_new_mesh():
             assert sg == sd == api.OK
             assert np.array_equal(xg.cpu().numpy(), xd.cpu().numpy())
             assert ig == idr
+
+
+def test_graph_replay_with_sources_of_different_norms_and_a_second_tolerance():
+    """The stop tolerance of a cycle (tol ||b||, and the inner tolerance of the mixed solver) is
+    set by the cycle's initialisation, which runs outside the captured graph: sources whose
+    right-hand sides differ in norm by 10^6 and a second solve at another tol, all replaying one
+    capture, must give the direct launches' results bit for bit and each meet its own tol."""
+    m = synth.cube_block_model(10)
+    srcs = [synth.Dipole(1.0, 1.0, 1.0, 0, 1.0), synth.Dipole(60.0, -40.0, 1.0, 1, 1e-3),
+            synth.Dipole(-30.0, 20.0, 1.0, 2, 1e3)]
+    ref = oracle.System(m.mesh.nodes, m.mesh.tets, m.sigma, m.sigma_p, m.freq, synth.sources_array(srcs))
+    xr, _, st_r = ref.solve(tol=1e-10)
+    assert st_r == oracle.OK
+    with api.Context(0) as ctx:
+        ctx.mesh(m.mesh.nodes, m.mesh.tets)
+        ctx.assemble(m.freq, m.sigma, m.sigma_p, srcs)
+        for precision in (api.PREC_MIXED, api.PREC_C128):
+            for tol in (1e-8, 1e-6, 1e-9):
+                xg, ig, sg = ctx.solve(precision=precision, tol=tol, use_graphs=1, batch=1)
+                xd, idr, sd = ctx.solve(precision=precision, tol=tol, use_graphs=0, batch=1)
+                assert sg == sd == api.OK
+                assert np.array_equal(xg.cpu().numpy(), xd.cpu().numpy())
+                assert ig == idr
+                for s in range(3):
+                    assert ig[s]["true_rel_residual"] <= tol
+                    assert rel(xg.cpu().numpy()[s], xr[s]) <= 1e3 * tol
