@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(128) k_conv3d(const __nv_bfloat16* __restrict_
   unsigned char* sW = smem + 2 * kConvRows * CIN * 2;     // 27 x COUT x CIN bf16
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ unsigned tbase;
+  __shared__ int s_ok;  // block-uniform outcome of the last mbarrier wait (thread 0 waits)
   const int tid = threadIdx.x, warp = tid >> 5;
   const int V = gx * gy * gz;
   // weights -> core-matrix layout (8 input channels = one 16-byte core row)
@@ -47,6 +48,7 @@ __global__ void __launch_bounds__(128) k_conv3d(const __nv_bfloat16* __restrict_
     tc::mbar_init(&bar[0]);
     tc::mbar_init(&bar[1]);
     tc::mbar_init_fence();
+    s_ok = 1;
   }
   if (warp == 0) tc::tmem_alloc(&tbase, 32);
   tc::fence_before();
@@ -57,10 +59,17 @@ __global__ void __launch_bounds__(128) k_conv3d(const __nv_bfloat16* __restrict_
   const int x = v % gx, y = (v / gx) % gy, z = v / (gx * gy);
   const uint32_t idesc = tc::idesc_bf16(kConvRows, COUT);
   const unsigned sbo = (CIN / 8) * 128;
-  bool ok = true;
+  // A timed-out wait stops the tap loop for the whole block: no further buffer rewrite or MMA
+  // issue, no TMEM load; the MMAs already issued are drained with one more bounded wait before
+  // TMEM is freed, and the error flag is set.
+  int issued = 0;  // taps whose MMAs were issued
   for (int t = 0; t < 27; ++t) {
     const int buf = t & 1;
-    if (t >= 2 && !tc::mbar_wait(&bar[buf], ((t - 2) >> 1) & 1)) ok = false;
+    if (t >= 2) {
+      if (tid == 0 && !tc::mbar_wait(&bar[buf], ((t - 2) >> 1) & 1)) s_ok = 0;
+      __syncthreads();
+      if (!s_ok) break;
+    }
     const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
     const int nx = x + dx, ny = y + dy, nz = z + dz;
     const bool in = v < V && nx >= 0 && nx < gx && ny >= 0 && ny < gy && nz >= 0 && nz < gz;
@@ -83,10 +92,17 @@ __global__ void __launch_bounds__(128) k_conv3d(const __nv_bfloat16* __restrict_
       }
       tc::commit(&bar[buf]);
     }
+    issued = t + 1;
   }
-  // the commit of the last tap (the 14th on buffer 0) covers every MMA issued before it
-  if (!tc::mbar_wait(&bar[0], 1)) ok = false;
+  // the commit of the last issued tap covers every MMA issued before it (after all 27 taps: the
+  // 14th commit on buffer 0, parity 1)
+  if (tid == 0 && issued > 0) {
+    const int last = issued - 1;
+    if (!tc::mbar_wait(&bar[last & 1], (last >> 1) & 1)) s_ok = 0;
+  }
+  __syncthreads();
   tc::fence_after();
+  const bool ok = s_ok != 0 && issued == 27;
   if (ok) {
 #pragma unroll
     for (int c0 = 0; c0 < COUT; c0 += 16) {
@@ -132,6 +148,7 @@ __global__ void __launch_bounds__(128) k_conv3d_wgrad(const __nv_bfloat16* __res
   __shared__ __align__(1024) unsigned char sB[COUT * kWgChunk * 2];
   __shared__ __align__(8) uint64_t bar;
   __shared__ unsigned tbase;
+  __shared__ int s_ok;  // block-uniform outcome of the last mbarrier wait (thread 0 waits)
   const int tid = threadIdx.x, warp = tid >> 5;
   const int V = gx * gy * gz;
   const int rows = 27 * CIN;
@@ -141,6 +158,7 @@ __global__ void __launch_bounds__(128) k_conv3d_wgrad(const __nv_bfloat16* __res
   if (tid == 0) {
     tc::mbar_init(&bar);
     tc::mbar_init_fence();
+    s_ok = 1;
   }
   if (warp == 0) tc::tmem_alloc(&tbase, 32);
   tc::fence_before();
@@ -153,7 +171,6 @@ __global__ void __launch_bounds__(128) k_conv3d_wgrad(const __nv_bfloat16* __res
   const int k = tid & (kWgChunk - 1), half = tid >> 6;
   // the taps whose rows meet this tile
   const int t_lo = row0 / CIN, t_hi = min(26, (row0 + kConvRows - 1) / CIN);
-  bool ok = true;
   int issued = 0;
   for (int ch = split; ch < nchunks; ch += splits) {
     const int v = ch * kWgChunk + k;
@@ -200,11 +217,19 @@ __global__ void __launch_bounds__(128) k_conv3d_wgrad(const __nv_bfloat16* __res
       }
       tc::commit(&bar);
     }
-    // the tiles are rewritten next chunk: wait for these MMAs
-    if (!tc::mbar_wait(&bar, issued & 1)) ok = false;
+    // the tiles are rewritten next chunk: wait for these MMAs.  On a timeout the whole block
+    // stops issuing (the decision is block-uniform), skips the TMEM loads and sets the error flag;
+    // a timed-out commit gets one more bounded wait before TMEM is freed.
+    if (tid == 0 && !tc::mbar_wait(&bar, issued & 1)) {
+      s_ok = 0;
+      tc::mbar_wait(&bar, issued & 1);
+    }
     ++issued;
+    __syncthreads();
     tc::fence_after();
+    if (!s_ok) break;
   }
+  const bool ok = s_ok != 0;
   if (ok) {
 #pragma unroll
     for (int c0 = 0; c0 < COUT; c0 += 16) {
