@@ -55,7 +55,7 @@ def parse():
 
 
 # DRAM traffic per launch / algorithmic bytes per launch, from one ncu capture of each kernel at
-# 48^3 (profiles/krylov_kernels_marine_n48_full.md, Arnoldi step j = 20): these kernels stream
+# 48^3 (the marine model, Arnoldi step j = 20): these kernels stream
 # their vectors once, so the traffic of a bench launch is this ratio times its algorithmic bytes.
 TRAFFIC_RATIO = {"spmv_c64": 1.0013, "mdot_c64": 1.0301, "cgs_upd_c64": 0.9860}
 
