@@ -235,3 +235,123 @@ def angle_loss(y_grid: np.ndarray, r: np.ndarray, slot: np.ndarray, spmv, diag: 
     gy[v, cc] = gz.real
     gy[v, 7 + cc] = gz.imag
     return L, gy
+
+
+# ---------------------------------------------------------------- auxiliary-space preconditioner
+# The network acts through the two auxiliary spaces of lowest-order edge elements (the
+# Hiptmair-Xu decomposition): nodal gradients G phi, on which the curl-curl term vanishes, and
+# nodal vector fields Pi w.  With phi and w on the lattice nodes,
+#     z = D^{-1} r + G phi + Pi w,
+# where phi, w are the nodal values of a scalar and a vector field, interpolated linearly, and
+# phi, w are zero on nodes of the outer boundary (Dirichlet condition, Section 2).  With the
+# exact auxiliary solutions phi = (G^T A G)^{-1} G^T r, w = (Pi^T A Pi)^{-1} Pi^T r this is the
+# additive auxiliary-space preconditioner; the network approximates both solves.  The edge
+# degrees of freedom of the basis of eqs. B.8-B.13 (scaled by the edge length) are tangential
+# components, E . t_e / |t_e|, so both maps carry a factor 1 / |t_e|:
+#     (G phi)_e = (phi_hi - phi_lo) / |t_e|,    (Pi w)_e = (w_lo + w_hi) . t_e / (2 |t_e|).
+#
+# Network input (grid [V, 16], V = lattice nodes): with sg = |diag(G^T A G)|^{-1/2},
+# sp = |diag(Pi^T A Pi)|^{-1/2} (per node and component, zero on boundary nodes),
+#     fg = sg * (G^T r),  fp = sp * (Pi^T r),
+#     s  = sqrt((sum |fg|^2 + sum |fp|^2) / (4 n_interior))   (1 when r = 0),
+#     channels 0, 1 = Re, Im fg / s;  2..4 = Re fp / s (x, y, z);  5..7 = Im fp / s;
+#     8, 9 = the node features;  10..15 = 0.
+# Network output y [V, 16]: phi = s sg (y0 + i y1), w_a = s sp_a (y_{2+a} + i y_{5+a}).
+AUX_IN = 8
+
+
+def interior_nodes(n: int) -> np.ndarray:
+    """Nodes of an (n+1)^3 lattice off the outer boundary (bool [(n+1)^3], node i + (n+1)(j + (n+1)k))."""
+    s = n + 1
+    ijk = np.stack(np.meshgrid(np.arange(s), np.arange(s), np.arange(s), indexing="ij"), -1)
+    inner = np.all((ijk >= 1) & (ijk <= n - 1), axis=-1)     # [i, j, k]
+    return inner.transpose(2, 1, 0).reshape(-1)               # flat index i + s (j + s k)
+
+
+def aux_operators(edges: np.ndarray, nodes: np.ndarray, n: int):
+    """(G [E x V], Pi [E x 3V]) as scipy CSR matrices; columns of boundary nodes are empty."""
+    import scipy.sparse as sp
+    E, V = edges.shape[0], (n + 1) ** 3
+    inner = interior_nodes(n)
+    lo, hi = edges[:, 0].astype(np.int64), edges[:, 1].astype(np.int64)
+    t = nodes[hi] - nodes[lo]
+    ell = np.linalg.norm(t, axis=1)
+    rows, cols, vals = [], [], []
+    for end, sign in ((lo, -1.0), (hi, 1.0)):
+        keep = inner[end]
+        rows.append(np.nonzero(keep)[0])
+        cols.append(end[keep])
+        vals.append(sign / ell[keep])
+    G = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(E, V))
+    rows, cols, vals = [], [], []
+    for end in (lo, hi):
+        keep = inner[end]
+        for a in range(3):
+            rows.append(np.nonzero(keep)[0])
+            cols.append(3 * end[keep] + a)
+            vals.append(0.5 * t[keep, a] / ell[keep])
+    Pi = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(E, 3 * V))
+    return G, Pi
+
+
+def aux_scales(G, Pi, A):
+    """sg [V] = |diag(G^T A G)|^{-1/2}, sp [V, 3] = |diag(Pi^T A Pi)|^{-1/2}; zero where the
+    diagonal is zero (boundary nodes).  A: scipy CSR of the assembled system."""
+    dg = np.abs((G.T @ A @ G).diagonal())
+    dp = np.abs((Pi.T @ A @ Pi).diagonal())
+    sg = np.where(dg > 0, 1.0 / np.sqrt(np.where(dg > 0, dg, 1.0)), 0.0)
+    spp = np.where(dp > 0, 1.0 / np.sqrt(np.where(dp > 0, dp, 1.0)), 0.0)
+    return sg, spp.reshape(-1, 3)
+
+
+def node_features(sigma: np.ndarray, cells, sigma_p: float, freq: float, h: float) -> np.ndarray:
+    """[V, 2]: log10(sigma / sigma_p) and log10(w mu0 sigma h^2) of the cell whose lowest corner is
+    the node (clamped to the last cell), sigma of a cell = the mean over its six tets 6c .. 6c+5."""
+    nx, ny, nz = cells
+    sig = sigma.reshape(nz, ny, nx, 6).mean(axis=3)
+    ix, iy, iz = (np.minimum(np.arange(m + 1), m - 1) for m in (nx, ny, nz))
+    sc = sig[np.ix_(iz, iy, ix)].reshape(-1)
+    w = 2.0 * np.pi * freq * 4e-7 * np.pi
+    return np.stack([np.log10(sc / sigma_p), np.log10(w * sc * h * h)], axis=1)
+
+
+def hx_input(r: np.ndarray, G, Pi, sg: np.ndarray, sp_: np.ndarray, feat: np.ndarray):
+    """Network input grid [V, 16] and the scale s for the residual r (complex [E])."""
+    V = G.shape[1]
+    fg = sg * (G.T @ r)
+    fp = sp_ * (Pi.T @ r).reshape(-1, 3)
+    n_in = int(np.count_nonzero(sg))
+    tot = (np.abs(fg) ** 2).sum() + (np.abs(fp) ** 2).sum()
+    s = float(np.sqrt(tot / (4 * n_in))) if n_in and tot > 0 else 1.0
+    x = np.zeros((V, 16))
+    x[:, 0], x[:, 1] = fg.real / s, fg.imag / s
+    x[:, 2:5], x[:, 5:8] = fp.real / s, fp.imag / s
+    x[:, 8:10] = feat
+    return x, s
+
+
+def hx_direction(y: np.ndarray, r: np.ndarray, s: float, G, Pi, sg, sp_, diag: np.ndarray) -> np.ndarray:
+    """z = D^{-1} r + G phi + Pi w for the network output y [V, 16]."""
+    phi = s * sg * (y[:, 0] + 1j * y[:, 1])
+    w = s * sp_ * (y[:, 2:5] + 1j * y[:, 5:8])
+    return r / diag + G @ phi + Pi @ w.reshape(-1)
+
+
+def hx_angle_loss(y: np.ndarray, r: np.ndarray, s: float, G, Pi, sg, sp_, diag, spmv):
+    """L = 1 - |<r, A z>|^2 / (|r|^2 |A z|^2) for z = hx_direction(y, ...): zero when one step
+    along z removes the whole residual.  Returns (L, dL/dy [V, 16]), the gradient with respect to
+    the real output channels (channels 8..15 get zero)."""
+    z = hx_direction(y, r, s, G, Pi, sg, sp_, diag)
+    w = spmv(z)
+    a = np.vdot(r, w)
+    b = np.vdot(w, w).real
+    c = np.vdot(r, r).real
+    L = 1.0 - abs(a) ** 2 / (b * c)
+    gw = -2.0 * (a * r / (c * b) - abs(a) ** 2 * w / (c * b * b))   # dL/dRe w + i dL/dIm w
+    gz = np.conj(spmv(np.conj(gw)))                                 # A^H gw (A complex symmetric)
+    gphi = G.T @ gz                                                 # real G: dL/dRe phi + i dL/dIm phi
+    gwn = (Pi.T @ gz).reshape(-1, 3)
+    gy = np.zeros_like(y)
+    gy[:, 0], gy[:, 1] = s * sg * gphi.real, s * sg * gphi.imag
+    gy[:, 2:5], gy[:, 5:8] = s * sp_ * gwn.real, s * sp_ * gwn.imag
+    return L, gy

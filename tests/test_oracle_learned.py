@@ -120,3 +120,116 @@ def test_angle_loss_gradient_by_finite_differences():
     yz = L.edges_to_grid(z, slot, 4 ** 3)
     l0, _ = L.angle_loss(yz, r, slot, sysm.spmv, diag)
     assert l0 < 1e-10
+
+
+# ---------------------------------------------------------------- auxiliary-space preconditioner
+def hx_case(n, seed=3, jitter=0.15):
+    """A jittered Kuhn lattice with a random block model, its oracle system as a scipy matrix."""
+    import scipy.sparse as sp
+    from paper_1808_00186_gb300 import learned as PL
+    m = PL.random_block_model(n, seed)
+    mesh = synth.kuhn_mesh(n, (-1000.0,) * 3, (1000.0,) * 3, jitter=jitter)
+    ref = oracle.System(mesh.nodes, mesh.tets, m.sigma, m.sigma_p, m.freq, synth.sources_array(m.sources))
+    rp, col, val, b = ref.system()
+    A = sp.csr_matrix((val, col, rp), shape=(ref.n_edges, ref.n_edges))
+    edges, _, _, bd = ref.topology()
+    return m, mesh, ref, A, edges, bd
+
+
+def test_gradient_and_vector_maps_reproduce_fields_they_represent_exactly():
+    """The degrees of freedom of the edge basis are tangential components (a constant field E0
+    has DOFs E0 . t_e / |t_e|, as the element pins fix): G of the nodal values of a linear function
+    a . x is the DOF vector of its gradient a, and Pi of a constant vector field v is the DOF vector
+    of v, exactly, on every edge whose two nodes are interior."""
+    n = 5
+    _, mesh, ref, A, edges, bd = hx_case(n)
+    G, Pi = L.aux_operators(edges, mesh.nodes, n)
+    inner = L.interior_nodes(n)
+    both = inner[edges[:, 0]] & inner[edges[:, 1]]
+    assert both.sum() > 0 and inner.sum() == (n - 1) ** 3
+    a = np.array([0.3, -1.7, 2.2])
+    t = mesh.nodes[edges[:, 1]] - mesh.nodes[edges[:, 0]]
+    t = t / np.linalg.norm(t, axis=1)[:, None]
+    phi = np.where(inner, mesh.nodes @ a, 0.0)
+    assert np.allclose((G @ phi)[both], (t @ a)[both], rtol=1e-13, atol=1e-9)
+    v = np.array([1.1, 0.4, -0.8])
+    w = np.where(inner[:, None], v[None, :], 0.0).reshape(-1)
+    assert np.allclose((Pi @ w)[both], (t @ v)[both], rtol=1e-13, atol=1e-9)
+    # boundary edges (Dirichlet rows) receive nothing from either space
+    assert np.all((abs(G) @ np.ones(G.shape[1]))[bd == 1] == 0)
+    assert np.all((abs(Pi) @ np.ones(Pi.shape[1]))[bd == 1] == 0)
+
+
+def test_gradient_space_diagonal_is_the_nodal_stiffness_times_i_omega_mu0():
+    """K annihilates discrete gradients, so diag(G^T A G) = i w mu0 diag(G^T M_sigma G), and
+    G^T M_sigma G is the P1 nodal stiffness with coefficient sigma: its diagonal is
+    sum over the node's tets of sigma V |grad lambda_i|^2 (barycentric gradients, closed form)."""
+    n = 4
+    m, mesh, ref, A, edges, bd = hx_case(n, seed=5)
+    G, Pi = L.aux_operators(edges, mesh.nodes, n)
+    dg = (G.T @ A @ G).diagonal()
+    inner = L.interior_nodes(n)
+    wmu0 = 2.0 * np.pi * m.freq * 4e-7 * np.pi
+    stiff = np.zeros(mesh.nodes.shape[0])
+    for t, tet in enumerate(mesh.tets):
+        _, grad, _, vol = oracle.geometry(mesh.nodes[tet])
+        for k in range(4):
+            stiff[tet[k]] += m.sigma[t] * vol * grad[k] @ grad[k]
+    assert np.all(np.abs(dg.real[inner]) <= 1e-9 * np.abs(dg.imag[inner]))
+    assert np.allclose(dg.imag[inner], wmu0 * stiff[inner], rtol=1e-10)
+    sg, sp_ = L.aux_scales(G, Pi, A)
+    assert np.allclose(sg[inner], 1.0 / np.sqrt(wmu0 * stiff[inner]), rtol=1e-10)
+    assert np.all(sg[~inner] == 0) and np.all(sp_[~inner] == 0) and np.all(sp_[inner] > 0)
+    # the vector space's diagonal is the diagonal of the explicit Galerkin product, node by node
+    dp = np.abs((Pi.T @ A @ Pi).diagonal()).reshape(-1, 3)
+    assert np.allclose(sp_[inner], 1.0 / np.sqrt(dp[inner]), rtol=1e-12)
+
+
+def test_hx_loss_gradient_by_finite_differences_and_exact_auxiliary_solves():
+    n = 3
+    m, mesh, ref, A, edges, bd = hx_case(n, seed=2, jitter=0.1)
+    G, Pi = L.aux_operators(edges, mesh.nodes, n)
+    sg, sp_ = L.aux_scales(G, Pi, A)
+    diag = A.diagonal()
+    feat = L.node_features(m.sigma, (n, n, n), m.sigma_p, m.freq, 2000.0 / n)
+    rng = np.random.default_rng(0)
+    r = rng.normal(size=A.shape[0]) + 1j * rng.normal(size=A.shape[0])
+    r[bd == 1] = 0.0
+    x, s = L.hx_input(r, G, Pi, sg, sp_, feat)
+    # the input is normalised: RMS over the interior nodes' four complex channels is one
+    inner = L.interior_nodes(n)
+    assert np.isclose((x[inner, :8] ** 2).sum() / (4 * inner.sum()), 1.0)
+    assert np.all(x[~inner, :8] == 0)
+    y = rng.normal(size=x.shape)
+    loss, gy = L.hx_angle_loss(y, r, s, G, Pi, sg, sp_, diag, ref.spmv)
+    assert 0.0 <= loss <= 1.0
+    for idx in rng.choice(np.nonzero(inner)[0], 6, replace=False):
+        for c in (0, 1, 3, 7):
+            old = y[idx, c]
+            y[idx, c] = old + 1e-6
+            lp, _ = L.hx_angle_loss(y, r, s, G, Pi, sg, sp_, diag, ref.spmv)
+            y[idx, c] = old - 1e-6
+            lm, _ = L.hx_angle_loss(y, r, s, G, Pi, sg, sp_, diag, ref.spmv)
+            y[idx, c] = old
+            assert abs((lp - lm) / 2e-6 - gy[idx, c]) <= 1e-6 * max(1.0, abs(gy[idx, c])), (idx, c)
+    assert np.all(gy[:, 8:] == 0)
+    # with the exact auxiliary solutions encoded in y, the direction is the additive
+    # auxiliary-space preconditioner D^-1 r + G (G^T A G)^-1 G^T r + Pi (Pi^T A Pi)^-1 Pi^T r
+    import scipy.sparse.linalg as spl
+    ig, ip = np.nonzero(sg)[0], np.nonzero(sp_.reshape(-1))[0]
+    phi = np.zeros(G.shape[1], complex)
+    phi[ig] = spl.spsolve((G.T @ A @ G)[ig][:, ig].tocsc(), (G.T @ r)[ig])
+    w = np.zeros(Pi.shape[1], complex)
+    w[ip] = spl.spsolve((Pi.T @ A @ Pi)[ip][:, ip].tocsc(), (Pi.T @ r)[ip])
+    ye = np.zeros_like(y)
+    ye[ig, 0], ye[ig, 1] = (phi[ig] / (s * sg[ig])).real, (phi[ig] / (s * sg[ig])).imag
+    wn, spn = w.reshape(-1, 3), sp_
+    ok = spn > 0
+    ye[:, 2:5] = np.where(ok, (wn / np.where(ok, s * spn, 1)).real, 0)
+    ye[:, 5:8] = np.where(ok, (wn / np.where(ok, s * spn, 1)).imag, 0)
+    z = L.hx_direction(ye, r, s, G, Pi, sg, sp_, diag)
+    assert np.allclose(z, r / diag + G @ phi + Pi @ w, rtol=1e-10, atol=1e-14 * np.abs(z).max())
+    # and that preconditioner lowers the one-step residual angle below Jacobi's on this residual
+    zj = r / diag
+    ang = lambda zz: 1 - abs(np.vdot(r, A @ zz)) ** 2 / (np.vdot(A @ zz, A @ zz).real * np.vdot(r, r).real)
+    assert ang(z) < ang(zj)
