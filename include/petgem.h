@@ -70,11 +70,11 @@ enum { PETGEM_PRECOND_JACOBI = 0, PETGEM_PRECOND_LEARNED = 1, PETGEM_PRECOND_SSO
  *     inner_tol or restart steps have run; x and the residual stay complex128.
  *   batch: number of sources iterated together (their SpMVs become one SpMM); 0 = all (groups
  *     of up to 32).  batch = 1 solves the sources one after the other.
- *   precond = PETGEM_PRECOND_LEARNED (single-source solves): flexible GMRES whose odd steps use
- *     z = s N(v / s) (N the network of petgem_learned_create, s the RMS of v, Jacobi-scaled
- *     variables) and whose even steps use Jacobi, with two-pass Gram-Schmidt.  The first cycle
- *     runs with Jacobi and measures its FP64 residual reduction; a learned cycle that does not
- *     beat it is undone and the solve continues with Jacobi alone (info.fell_back).
+ *   precond = PETGEM_PRECOND_LEARNED (single-source solves): flexible GMRES whose every step
+ *     uses the learned auxiliary-space preconditioner z = M^{-1} v (petgem_learned_create; in the
+ *     Jacobi-scaled variables D M^{-1} v), with two-pass Gram-Schmidt, from the first cycle on.
+ *     A learned cycle that removes less than 10 % of the FP64 residual is undone and the solve
+ *     continues with Jacobi alone (info.fell_back).
  *   precond = PETGEM_PRECOND_SSOR (method SQMR only; PETGEM_ERR_UNSUPPORTED otherwise):
  *     symmetric SOR, the preconditioner of the paper's Section 5.3 runs, in the order of a
  *     multicolour colouring of the matrix graph (petgem_colouring): with A = D + L + U split by
@@ -276,14 +276,23 @@ int petgem_ssor_apply(petgem_ctx *ctx, double omega, const void *r, void *z);
 int petgem_receivers(petgem_ctx *ctx, int32_t n_rcv, const double *rx, const void *x, void *out);
 
 /* ----------------------------------------------------------------------- learned preconditioner */
-/* Not in the paper (it solves with GMRES, SQMR and MUMPS, Sections 5.1-5.3).  A 3-D
- * convolutional network on the node grid of a Kuhn-split lattice of nx x ny x nz cells whose
- * node ids are i + (nx+1) (j + (ny+1) k): every edge is a step (+x, +y, +z, +xy, +xz, +yz or
- * +xyz) from its low node, so edge vectors map one-to-one onto 7 grid channels (x Re, Im).  Four
- * levels (the node grid and three 2x poolings), seven 3x3x3 convolutions (16/32 channels, BF16
- * operands on the tensor cores, FP32 accumulation and FP32 master weights), ReLU, skip additions.
- * Input: the residual (16 channels with two conductivity features); output: a correction
- * direction, trained so that one step along it removes as much of the residual as possible.
+/* Not in the paper (it solves with GMRES, SQMR and MUMPS, Sections 5.1-5.3).  An additive
+ * auxiliary-space preconditioner for the edge-element system (Hiptmair-Xu decomposition) whose
+ * two nodal solves are replaced by a 3-D convolutional network on the node grid of a Kuhn-split
+ * lattice of nx x ny x nz cells (node ids i + (nx+1) (j + (ny+1) k), every edge a step +x, +y,
+ * +z, +xy, +xz, +yz or +xyz from its low node):
+ *     z = M^{-1} r = D^{-1} r + G phi + Pi w,
+ * with D = diag(A), (G phi)_e = (phi_hi - phi_lo) / |t_e| (nodal gradients, which the curl-curl
+ * term annihilates), (Pi w)_e = (w_lo + w_hi) . t_e / (2 |t_e|) (nodal vector fields), t_e =
+ * x_hi - x_lo, and phi, w zero on the outer boundary.  Network input (16 channels per node): with
+ * sg = |diag(G^T A G)|^{-1/2}, sp = |diag(Pi^T A Pi)|^{-1/2} (per axis; zero on boundary nodes),
+ * fg = sg G^T r, fp = sp Pi^T r, s = the RMS of (fg, fp) over the interior nodes' four complex
+ * values: Re fg / s, Im fg / s, Re fp / s (x, y, z), Im fp / s (x, y, z), log10(sigma / sigma_p),
+ * log10(w mu0 sigma h^2) of the cell whose lowest corner is the node (h = the first cell's
+ * geometric-mean spacing), and six zeros.  Output channels: phi = s sg (y0 + i y1), w = s sp
+ * (y2..4 + i y5..7); channels 8..15 unused.  Four levels (the node grid and three 2x poolings),
+ * seven 3x3x3 convolutions (16/32 channels, BF16 operands on the tensor cores, FP32 accumulation
+ * and FP32 master weights), ReLU, skip additions.
  * petgem_learned_create: after petgem_mesh_edges on such a lattice; keeps the parameters when
  *   called again for another mesh (the network is fully convolutional).  PETGEM_ERR_UNSUPPORTED
  *   if some edge is not a lattice step.
@@ -291,10 +300,10 @@ int petgem_receivers(petgem_ctx *ctx, int32_t n_rcv, const double *rx, const voi
  *   the last train step, scaled by 1 / n_samples); NULL to skip; *n_params receives the count.
  * petgem_learned_train_step: one Adam step (lr) on the mean over n_samples solver iterates
  *   x_iters (device complex128 [n_samples][E], e.g. the iterate at the start of every GMRES cycle)
- *   of the residual angle L = 1 - |<r, Ahat z>|^2 / (|r|^2 |Ahat z|^2), r = b - A x of the
- *   assembled system (source 0), z the network's direction for r, Ahat = A D^{-1}: zero when
- *   one step along z removes the whole residual.  *loss (host) receives the mean L.
- * petgem_learned_apply: z = s N(r / s), s = RMS(r), for one device complex128 vector r of E entries. */
+ *   of the residual angle L = 1 - |<r, A z>|^2 / (|r|^2 |A z|^2), r = b - A x of the assembled
+ *   system (source 0), z = M^{-1} r: zero when one step along z removes the whole residual.
+ *   *loss (host) receives the mean L.
+ * petgem_learned_apply: z = M^{-1} r for one device complex128 vector r of E entries. */
 int petgem_learned_create(petgem_ctx *ctx, int32_t nx, int32_t ny, int32_t nz);
 int petgem_learned_params(petgem_ctx *ctx, const float *set, float *get, float *grad, int64_t *n_params);
 int petgem_learned_train_step(petgem_ctx *ctx, int32_t n_samples, const void *x_iters, float lr, double *loss);

@@ -531,7 +531,7 @@ int petgem_learned_apply(petgem_ctx* c, const void* r, void* z) {
   if (s.ok()) s = N->features(c->stream, c->sigma.as<double>(), c->sigma_p, c->omega, c->lattice_h);
   if (s.ok())
     s = N->apply<double2>(c->stream, static_cast<const double2*>(r), c->slots.as<int32_t>(), c->n_edges,
-                          static_cast<double2*>(z));
+                          static_cast<double2*>(z), true);
   c->launches += 20;
   if (s.ok()) s = petgem::nn::check_err(c->stream, N->err.as<int>(), "petgem_learned_apply");
   return finish(c, s);

@@ -496,15 +496,11 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
       T* vj = V + (int64_t)j * ld;
       T* vn = vj + ld;
       const T* xin = vj;
-      if (learned) {  // odd steps: the network's direction; even steps: Jacobi (z = v)
+      if (learned) {  // every step: z = D (D^{-1} v + G phi + Pi w), the network's auxiliary-space direction
         T* zj = Z + (int64_t)j * ld;
-        if (j & 1) {
-          KernelTimer kt(c, "learned_apply", 0.0, j, 0);
-          PG_TRY(c->net->apply<T>(s, vj, c->slots.as<int32_t>(), n, zj));
-          c->launches += 20;
-        } else {
-          PG_CUDA(cudaMemcpyAsync(zj, vj, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
-        }
+        KernelTimer kt(c, "learned_apply", 0.0, j, 0);
+        PG_TRY(c->net->apply<T>(s, vj, c->slots.as<int32_t>(), n, zj));
+        c->launches += 28;
         xin = zj;
       }
       {
@@ -664,11 +660,11 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
     int64_t iters = 0, cycles = 0, reorth = 0;
     int status = PETGEM_OK;
     double relres = 0.0, prev_relres = 0.0;
-    // Learned preconditioner: the first cycle runs with Jacobi and measures its residual reduction
-    // per cycle; learned cycles follow while each reduces the FP64 residual more than that.
+    // Learned preconditioner: learned cycles from the start while each removes at least 10 % of
+    // the FP64 residual; one that does not is undone and the solve goes on with Jacobi alone.
     bool want_learned = o.precond == PETGEM_PRECOND_LEARNED;
     bool learned = false;
-    double jacobi_rate = -1.0;
+    constexpr double kLearnedRate = 0.9;
     int fell_back = 0;
     if (want_learned) {
       PG_TRY(S->Z.reserve((size_t)m * S->ld * (o.precision == PETGEM_PREC_MIXED ? sizeof(float2) : sizeof(double2))));
@@ -691,17 +687,15 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
         c->launches++;
         PG_TRY(read_state(c, &hs));
         const double rate = sqrt(hs.rnorm2) / bnorm / prev_relres;
-        if (prev_learned && !(rate < jacobi_rate)) {
-          // the learned cycle just run did no better than a Jacobi cycle: undo it, stay with Jacobi
+        if (prev_learned && !(rate < kLearnedRate)) {
+          // the learned cycle just run removed too little of the residual: undo it, stay with Jacobi
           PG_CUDA(cudaMemcpyAsync(S->u.ptr, S->usave.ptr, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
           PG_TRY(residual());
           want_learned = false;
           fell_back = 1;
-        } else if (!prev_learned && jacobi_rate < 0.0) {
-          jacobi_rate = rate;
         }
       }
-      learned = want_learned && jacobi_rate >= 0.0;
+      learned = want_learned;
       if (learned) PG_CUDA(cudaMemcpyAsync(S->usave.ptr, S->u.ptr, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
       const int mj = (int)std::min<int64_t>(m, std::max<int64_t>(o.max_iters - iters, 0));
       const double tol_abs = o.tol * bnorm;

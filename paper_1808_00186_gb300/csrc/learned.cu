@@ -1,10 +1,16 @@
-// Learned preconditioner: a small 4-level 3-D convolutional network on the structured grid of a
-// Kuhn-split lattice (one grid node per mesh node, seven edge classes per node), trained on the
-// GPU with the library's own tensor-core kernels to predict the direction of the exact correction
-// Ahat^{-1} r from the residual r (Jacobi-scaled variables).  Inside flexible GMRES its output
-// z = s N(r / s) is used on every other Arnoldi step, the Jacobi step z = r on the others, so the
-// Krylov space holds both kinds of directions.  Not part of the paper: the paper solves with
-// GMRES / SQMR / MUMPS (Sections 5.1-5.3); the plain solver stays the fallback.
+// Learned preconditioner: a small 4-level 3-D convolutional network on the node lattice of a
+// Kuhn-split mesh, acting through the two auxiliary spaces of lowest-order edge elements (the
+// Hiptmair-Xu decomposition): nodal gradients G phi, which the curl-curl term annihilates, and
+// nodal vector fields Pi w.  For a residual r the preconditioner returns
+//     z = D^{-1} r + G phi + Pi w,   (phi, w) = network(G^T r, Pi^T r, model features),
+// the additive auxiliary-space preconditioner with the two nodal solves (G^T A G and Pi^T A Pi,
+// nodal problems on the lattice) replaced by the network.  The edge degrees of freedom are
+// tangential components, so (G phi)_e = (phi_hi - phi_lo) / |t_e| and
+// (Pi w)_e = (w_lo + w_hi) . t_e / (2 |t_e|); phi, w vanish on the outer boundary (Dirichlet).
+// Trained on the GPU with the library's own tensor-core kernels on solver residuals, loss = the
+// residual angle of one step along z.  Inside flexible GMRES every step uses z (in the solver's
+// Jacobi-scaled variables, D z).  Not part of the paper: the paper solves with GMRES / SQMR /
+// MUMPS (Sections 5.1-5.3); the plain solver stays the fallback.
 //
 // Network (levels G0 = lattice nodes, G1..G3 = successive 2x poolings, BF16 activations, FP32
 // accumulation and master weights):
@@ -12,9 +18,12 @@
 //   p2 = pool a2                      a3 = relu(c3 32->32 on G2)
 //   p3 = pool a3                      a4 = relu(c4 32->32 on G3)
 //   a5 = relu(c5 32->32 on up(a4) + a3)       a6 = relu(c6 32->16 on up(a5) + a2)
-//   y  = c7 16->16 on up(a6) + a1     (channels 14, 15 of y unused)
-// Input channels: 7 edge classes x (Re, Im) of the residual scaled by its RMS, log10(sigma / sigma_p)
-// and log10(w mu0 sigma h^2) of the cell at the node.  Output: the correction on the same slots.
+//   y  = c7 16->16 on up(a6) + a1     (channels 8..15 of y unused)
+// Input channels (sg = |diag(G^T A G)|^{-1/2}, sp = |diag(Pi^T A Pi)|^{-1/2} per node and axis,
+// zero on boundary nodes; fg = sg G^T r, fp = sp Pi^T r; s = RMS of (fg, fp) over the interior
+// nodes' four complex values): Re fg / s, Im fg / s, Re fp / s (x, y, z), Im fp / s (x, y, z),
+// log10(sigma / sigma_p), log10(w mu0 sigma h^2) of the cell at the node, six zeros.
+// Output: phi = s sg (y0 + i y1), w = s sp (y2..4 + i y5..7).
 #include <math.h>
 
 #include <algorithm>
@@ -175,53 +184,167 @@ __global__ void k_node_features(const double* __restrict__ sigma, int nx, int ny
   feat[2 * v] = (float)log10(s / sigma_p);
   feat[2 * v + 1] = (float)log10(wmu0h2 * s);
 }
-// Network input: residual (complex) on the edge slots scaled by 1/s, plus the two features.
-template <typename T>
-__global__ void k_to_grid(const T* __restrict__ r, const int32_t* __restrict__ slot, int64_t E,
-                          const float* __restrict__ inv_s, float* __restrict__ g32) {
+// Lattice step from the low to the high node of each edge class.
+__constant__ int kStep[7][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};
+
+// Edge of every slot, and the slot's unit tangent t / |t| with 1 / |t| (the edge's true geometry,
+// so jittered lattices are handled exactly).
+__global__ void k_slot_geometry(const int32_t* __restrict__ edges, const int32_t* __restrict__ slot, int64_t E,
+                                const double* __restrict__ nodes, int32_t* __restrict__ slot_edge,
+                                float4* __restrict__ tang) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= E) return;
   const int32_t sl = slot[e];
   if (sl < 0) return;
-  const int64_t v = sl / 7;
-  const int c = sl - (int)(v * 7);
-  const float f = *inv_s;
-  g32[v * kIn + c] = (float)r[e].x * f;
-  g32[v * kIn + 7 + c] = (float)r[e].y * f;
+  const int64_t lo = edges[2 * e], hi = edges[2 * e + 1];
+  const double tx = nodes[3 * hi] - nodes[3 * lo], ty = nodes[3 * hi + 1] - nodes[3 * lo + 1],
+               tz = nodes[3 * hi + 2] - nodes[3 * lo + 2];
+  const double l = sqrt(tx * tx + ty * ty + tz * tz);
+  slot_edge[sl] = (int32_t)e;
+  tang[sl] = make_float4((float)(tx / l), (float)(ty / l), (float)(tz / l), (float)(1.0 / l));
 }
-__global__ void k_pack_input(const float* __restrict__ g32, const float* __restrict__ feat, int64_t V,
-                             __nv_bfloat16* __restrict__ x) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= V * kIn) return;
-  const int c = (int)(i % kIn);
-  const int64_t v = i / kIn;
-  x[i] = __float2bfloat16(c < 14 ? g32[i] : feat[2 * v + (c - 14)]);
+
+__device__ inline bool interior(int x, int y, int z, int gx, int gy, int gz) {
+  return x >= 1 && y >= 1 && z >= 1 && x <= gx - 2 && y <= gy - 2 && z <= gz - 2;
 }
-// z_e = s * y[slot] (complex: Re from class c, Im from class 7 + c)
-template <typename T>
-__global__ void k_from_grid(const float* __restrict__ y, const int32_t* __restrict__ slot, int64_t E,
-                            const float* __restrict__ s_ptr, T* __restrict__ z) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= E) return;
-  const int32_t sl = slot[e];
-  T out;
-  out.x = 0;
-  out.y = 0;
-  if (sl >= 0) {
-    const int64_t v = sl / 7;
-    const int c = sl - (int)(v * 7);
-    const float s = *s_ptr;
-    out.x = s * y[v * 16 + c];
-    out.y = s * y[v * 16 + 7 + c];
+
+// The (up to 14) edges at node v with their coefficients in G (g) and Pi (p = t / (2 |t|)):
+// the seven edges leaving v (v is their low node, g = -1/|t|) and the seven arriving at v.
+struct Incident {
+  int n;
+  int32_t e[14];
+  float g[14];
+  float3 p[14];
+};
+__device__ inline void incident_edges(int64_t v, int x, int y, int z, int gx, int gy, const int32_t* slot_edge,
+                                      const float4* tang, Incident& I) {
+  I.n = 0;
+#pragma unroll
+  for (int c = 0; c < 7; ++c) {
+    const int64_t so = v * 7 + c;
+    const int32_t eo = slot_edge[so];
+    if (eo >= 0) {
+      const float4 t = tang[so];
+      I.e[I.n] = eo;
+      I.g[I.n] = -t.w;
+      I.p[I.n] = make_float3(0.5f * t.x, 0.5f * t.y, 0.5f * t.z);
+      ++I.n;
+    }
+    const int ux = x - kStep[c][0], uy = y - kStep[c][1], uz = z - kStep[c][2];
+    if (ux >= 0 && uy >= 0 && uz >= 0) {
+      const int64_t si = ((int64_t)ux + (int64_t)gx * ((int64_t)uy + (int64_t)gy * uz)) * 7 + c;
+      const int32_t ei = slot_edge[si];
+      if (ei >= 0) {
+        const float4 t = tang[si];
+        I.e[I.n] = ei;
+        I.g[I.n] = t.w;
+        I.p[I.n] = make_float3(0.5f * t.x, 0.5f * t.y, 0.5f * t.z);
+        ++I.n;
+      }
+    }
   }
-  z[e] = out;
 }
-// RMS of a complex vector -> (1/s, s) with s = RMS (1 when the vector is zero).
+
+// Per-node scales (sg, sp_x, sp_y, sp_z) = |diag|^{-1/2} of G^T A G and Pi^T A Pi, from the
+// assembled A (complex128 CSR, ascending columns): diag_v = sum over incident edge pairs (e, f) of
+// coef_e coef_f A_ef (entries outside the pattern are zero).  Zero on boundary nodes.
+__global__ void k_hx_diag(const int32_t* __restrict__ slot_edge, const float4* __restrict__ tang,
+                          const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                          const double2* __restrict__ val, int gx, int gy, int gz, float4* __restrict__ aux) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= (int64_t)gx * gy * gz) return;
+  int x, y, z;
+  grid_coords(v, gx, gy, x, y, z);
+  if (!interior(x, y, z, gx, gy, gz)) {
+    aux[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  Incident I;
+  incident_edges(v, x, y, z, gx, gy, slot_edge, tang, I);
+  double2 dg = make_double2(0.0, 0.0), dp[3] = {dg, dg, dg};
+  for (int i = 0; i < I.n; ++i) {
+    const int64_t r0 = rp[I.e[i]], r1 = rp[I.e[i] + 1];
+    for (int j = 0; j < I.n; ++j) {
+      int64_t lo = r0, hi = r1;  // binary search for column e_j in row e_i
+      const int32_t want = I.e[j];
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (col[mid] < want) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo >= r1 || col[lo] != want) continue;
+      const double2 a = val[lo];
+      dg = cadd(dg, cscale(a, (double)I.g[i] * I.g[j]));
+      dp[0] = cadd(dp[0], cscale(a, (double)I.p[i].x * I.p[j].x));
+      dp[1] = cadd(dp[1], cscale(a, (double)I.p[i].y * I.p[j].y));
+      dp[2] = cadd(dp[2], cscale(a, (double)I.p[i].z * I.p[j].z));
+    }
+  }
+  auto inv_sqrt_abs = [](double2 d) -> float {
+    const double m = sqrt(d.x * d.x + d.y * d.y);
+    return m > 0.0 ? (float)(1.0 / sqrt(m)) : 0.f;
+  };
+  aux[v] = make_float4(inv_sqrt_abs(dg), inv_sqrt_abs(dp[0]), inv_sqrt_abs(dp[1]), inv_sqrt_abs(dp[2]));
+}
+
+// Node fields of an edge vector r: [sg Re G^T r, sg Im G^T r, sp Re Pi^T r (x, y, z), sp Im Pi^T r
+// (x, y, z)] per node, and per-block sums of their squares (FP64) for the scale s.
 template <typename T>
-__global__ void k_rms(const T* __restrict__ r, int64_t E, float* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_hx_in(const T* __restrict__ r, const int32_t* __restrict__ slot_edge,
+                                               const float4* __restrict__ tang, const float4* __restrict__ aux,
+                                               int gx, int gy, int gz, float* __restrict__ out,
+                                               double* __restrict__ part) {
+  __shared__ double red[8];
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double ss = 0.0;
+  if (v < (int64_t)gx * gy * gz) {
+    const float4 a = aux[v];
+    float o[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (a.x > 0.f) {
+      int x, y, z;
+      grid_coords(v, gx, gy, x, y, z);
+      Incident I;
+      incident_edges(v, x, y, z, gx, gy, slot_edge, tang, I);
+      double gr = 0.0, gi = 0.0, pr[3] = {0.0, 0.0, 0.0}, pi[3] = {0.0, 0.0, 0.0};
+      for (int k = 0; k < I.n; ++k) {
+        const T re = r[I.e[k]];
+        const double xr = (double)re.x, xi = (double)re.y;
+        gr += I.g[k] * xr;
+        gi += I.g[k] * xi;
+        pr[0] += I.p[k].x * xr;
+        pi[0] += I.p[k].x * xi;
+        pr[1] += I.p[k].y * xr;
+        pi[1] += I.p[k].y * xi;
+        pr[2] += I.p[k].z * xr;
+        pi[2] += I.p[k].z * xi;
+      }
+      o[0] = (float)(a.x * gr);
+      o[1] = (float)(a.x * gi);
+      o[2] = (float)(a.y * pr[0]);
+      o[3] = (float)(a.z * pr[1]);
+      o[4] = (float)(a.w * pr[2]);
+      o[5] = (float)(a.y * pi[0]);
+      o[6] = (float)(a.z * pi[1]);
+      o[7] = (float)(a.w * pi[2]);
+      for (int k = 0; k < 8; ++k) ss += (double)o[k] * o[k];
+    }
+    reinterpret_cast<float4*>(out)[2 * v] = make_float4(o[0], o[1], o[2], o[3]);
+    reinterpret_cast<float4*>(out)[2 * v + 1] = make_float4(o[4], o[5], o[6], o[7]);
+  }
+  for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+// s = sqrt(sum / (4 n_interior)) (1 when the sum is zero) -> scal[0] = 1 / s, scal[1] = s.
+__global__ void k_hx_scale(const double* __restrict__ part, int nb, int64_t n_interior, float* __restrict__ scal) {
   __shared__ double red[256];
   double a = 0.0;
-  for (int64_t i = threadIdx.x; i < E; i += 256) a += (double)r[i].x * r[i].x + (double)r[i].y * r[i].y;
+  for (int i = threadIdx.x; i < nb; i += 256) a += part[i];
   red[threadIdx.x] = a;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
@@ -229,11 +352,105 @@ __global__ void k_rms(const T* __restrict__ r, int64_t E, float* __restrict__ ou
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    double s = sqrt(red[0] / (double)E);
-    if (!(s > 0.0)) s = 1.0;
-    out[0] = (float)(1.0 / s);
-    out[1] = (float)s;
+    double sc = n_interior > 0 ? sqrt(red[0] / (4.0 * (double)n_interior)) : 0.0;
+    if (!(sc > 0.0) || !isfinite(sc)) sc = 1.0;
+    scal[0] = (float)(1.0 / sc);
+    scal[1] = (float)sc;
   }
+}
+__global__ void k_hx_pack(const float* __restrict__ nodes8, const float* __restrict__ feat, int64_t V,
+                          const float* __restrict__ scal, __nv_bfloat16* __restrict__ x) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= V * kIn) return;
+  const int c = (int)(i % kIn);
+  const int64_t v = i / kIn;
+  const float val = c < 8 ? nodes8[v * 8 + c] * scal[0] : (c < 10 ? feat[2 * v + (c - 8)] : 0.f);
+  x[i] = __float2bfloat16(val);
+}
+// z_e = D^{-1} r_e + (G phi + Pi w)_e (XS) or r_e + D_e (G phi + Pi w)_e, from the network output y
+// [V][16] (FP32): phi = s sg (y0 + i y1), w_k = s sp_k (y_{2+k} + i y_{5+k}) at the edge's nodes.
+template <typename T, bool XS>
+__global__ void k_hx_out(const T* __restrict__ r, const int32_t* __restrict__ slot, int64_t E,
+                         const float* __restrict__ y, const float4* __restrict__ aux, const float4* __restrict__ tang,
+                         const float* __restrict__ scal, const double2* __restrict__ diag, int gx, int gy,
+                         T* __restrict__ z) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int32_t sl = slot[e];
+  const T re = r[e];
+  double cr = 0.0, ci = 0.0;
+  if (sl >= 0) {
+    const int64_t lo = sl / 7;
+    const int c = sl - (int)(lo * 7);
+    const int64_t hi = lo + kStep[c][0] + (int64_t)gx * (kStep[c][1] + (int64_t)gy * kStep[c][2]);
+    const float4 t = tang[sl];
+    const float s = scal[1];
+    const float4 al = aux[lo], ah = aux[hi];
+    const float4* yl = reinterpret_cast<const float4*>(y + lo * 16);
+    const float4* yh = reinterpret_cast<const float4*>(y + hi * 16);
+    const float4 l0 = yl[0], l1 = yl[1], h0 = yh[0], h1 = yh[1];
+    // G phi: (phi_hi - phi_lo) / |t|
+    cr = (double)t.w * s * ((double)ah.x * h0.x - (double)al.x * l0.x);
+    ci = (double)t.w * s * ((double)ah.x * h0.y - (double)al.x * l0.y);
+    // Pi w: (w_lo + w_hi) . t / (2 |t|); channels: Re x,y,z = 2,3,4; Im x,y,z = 5,6,7
+    const double hs = 0.5 * s;
+    cr += hs * (t.x * ((double)al.y * l0.z + (double)ah.y * h0.z) + t.y * ((double)al.z * l0.w + (double)ah.z * h0.w) +
+                t.z * ((double)al.w * l1.x + (double)ah.w * h1.x));
+    ci += hs * (t.x * ((double)al.y * l1.y + (double)ah.y * h1.y) + t.y * ((double)al.z * l1.z + (double)ah.z * h1.z) +
+                t.z * ((double)al.w * l1.w + (double)ah.w * h1.w));
+  }
+  const double2 d = diag[e];
+  double2 out;
+  if (XS) {
+    out = cadd(cdiv(make_double2((double)re.x, (double)re.y), d), make_double2(cr, ci));
+  } else {
+    out = cadd(make_double2((double)re.x, (double)re.y), cmul(d, make_double2(cr, ci)));
+  }
+  T o;
+  o.x = out.x;
+  o.y = out.y;
+  z[e] = o;
+}
+// Gradient of the loss with respect to the network output: with gzp = Ahat^H gw and
+// g = conj(D) gzp = A^H gw (the gradient at z in the unscaled variables),
+// dy[v] = s [sg Re G^T g, sg Im G^T g, sp Re Pi^T g (x, y, z), sp Im Pi^T g (x, y, z), 0 ...].
+__global__ void k_hx_dy(const double2* __restrict__ gzp, const double2* __restrict__ diag,
+                        const int32_t* __restrict__ slot_edge, const float4* __restrict__ tang,
+                        const float4* __restrict__ aux, const float* __restrict__ scal, int gx, int gy, int gz,
+                        __nv_bfloat16* __restrict__ dy) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= (int64_t)gx * gy * gz) return;
+  const float4 a = aux[v];
+  float o[16];
+  for (int k = 0; k < 16; ++k) o[k] = 0.f;
+  if (a.x > 0.f) {
+    int x, y, z;
+    grid_coords(v, gx, gy, x, y, z);
+    Incident I;
+    incident_edges(v, x, y, z, gx, gy, slot_edge, tang, I);
+    double gr = 0.0, gi = 0.0, pr[3] = {0.0, 0.0, 0.0}, pi[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < I.n; ++k) {
+      const double2 g = cconjmul(diag[I.e[k]], gzp[I.e[k]]);
+      gr += I.g[k] * g.x;
+      gi += I.g[k] * g.y;
+      pr[0] += I.p[k].x * g.x;
+      pi[0] += I.p[k].x * g.y;
+      pr[1] += I.p[k].y * g.x;
+      pi[1] += I.p[k].y * g.y;
+      pr[2] += I.p[k].z * g.x;
+      pi[2] += I.p[k].z * g.y;
+    }
+    const double s = scal[1];
+    o[0] = (float)(s * a.x * gr);
+    o[1] = (float)(s * a.x * gi);
+    o[2] = (float)(s * a.y * pr[0]);
+    o[3] = (float)(s * a.z * pr[1]);
+    o[4] = (float)(s * a.w * pr[2]);
+    o[5] = (float)(s * a.y * pi[0]);
+    o[6] = (float)(s * a.z * pi[1]);
+    o[7] = (float)(s * a.w * pi[2]);
+  }
+  for (int k = 0; k < 16; ++k) dy[v * 16 + k] = __float2bfloat16(o[k]);
 }
 // Adam (Kingma & Ba 2015) on FP32 master weights.
 __global__ void k_adam(float* __restrict__ w, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
@@ -327,19 +544,6 @@ __global__ void k_angle_gw(const double2* __restrict__ r, const double2* __restr
   const double2 t2 = cscale(w[i], a2 / (c * b * b));
   gw[i] = cscale(csub(t1, t2), -2.0);
 }
-// dy on the grid (BF16): Re / Im of the edge gradient on the edge's slot, zero elsewhere.
-__global__ void k_grad_to_grid(const double2* __restrict__ gz, const int32_t* __restrict__ slot, int64_t E,
-                               __nv_bfloat16* __restrict__ dy) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= E) return;
-  const int32_t sl = slot[e];
-  if (sl < 0) return;
-  const int64_t v = sl / 7;
-  const int c = sl - (int)(v * 7);
-  dy[v * 16 + c] = __float2bfloat16((float)gz[e].x);
-  dy[v * 16 + 7 + c] = __float2bfloat16((float)gz[e].y);
-}
-__global__ void k_set_one(float* p) { *p = 1.0f; }
 
 unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
@@ -452,7 +656,6 @@ Status Net::init(petgem_ctx* c, int nx_, int ny_, int nz_) {
   PG_TRY(act(dp2, 2, 32));
   PG_TRY(act(dp1, 1, 16));
   PG_TRY(y.reserve((size_t)V[0] * 16 * sizeof(float)));
-  PG_TRY(g32.reserve((size_t)V[0] * 16 * sizeof(float)));
   PG_TRY(feat.reserve((size_t)V[0] * 2 * sizeof(float)));
   PG_TRY(scal.reserve(16 * sizeof(float)));
   PG_TRY(loss_acc.reserve(sizeof(double)));
@@ -552,48 +755,89 @@ Status Net::backward(cudaStream_t s, bool acc) {
   return Status{};
 }
 
-// Build the input grid from an edge vector r (Jacobi-scaled residual); *inv_s, s in scal[0..1].
+// Slot map and tangents of the current mesh, and the auxiliary scales of the current assembly.
+Status Net::prepare_aux(petgem_ctx* c) {
+  cudaStream_t s = c->stream;
+  const int gx = g[0][0], gy = g[0][1], gz = g[0][2];
+  if (geom_version != c->mesh_version) {
+    PG_TRY(slot_edge.reserve((size_t)V[0] * 7 * sizeof(int32_t)));
+    PG_TRY(tang.reserve((size_t)V[0] * 7 * sizeof(float4)));
+    PG_CUDA(cudaMemsetAsync(slot_edge.ptr, 0xff, (size_t)V[0] * 7 * sizeof(int32_t), s));  // -1: no edge
+    PG_CUDA(cudaMemsetAsync(tang.ptr, 0, (size_t)V[0] * 7 * sizeof(float4), s));
+    k_slot_geometry<<<nb(c->n_edges), 256, 0, s>>>(c->edges.as<int32_t>(), c->slots.as<int32_t>(), c->n_edges,
+                                                    c->nodes.as<double>(), slot_edge.as<int32_t>(), tang.as<float4>());
+    PG_CUDA(cudaGetLastError());
+    geom_version = c->mesh_version;
+    aux_version = -1;
+  }
+  if (aux_version != c->assembly_version) {
+    PG_TRY(aux.reserve((size_t)V[0] * sizeof(float4)));
+    PG_TRY(nodes8.reserve((size_t)V[0] * 8 * sizeof(float)));
+    PG_TRY(npart.reserve((size_t)nb(V[0]) * sizeof(double)));
+    k_hx_diag<<<nb(V[0]), 256, 0, s>>>(slot_edge.as<int32_t>(), tang.as<float4>(), c->row_ptr.as<int64_t>(),
+                                       c->col.as<int32_t>(), c->val.as<double2>(), gx, gy, gz, aux.as<float4>());
+    PG_CUDA(cudaGetLastError());
+    aux_version = c->assembly_version;
+  }
+  return Status{};
+}
+
+// Network input x0 from an edge vector r (a residual): the gathered, scaled node fields, the scale
+// s in scal[0..1] (1 / s, s), the two features.
 template <typename T>
-Status Net::load_input(cudaStream_t s, const T* r, const int32_t* slot, int64_t E) {
-  k_rms<T><<<1, 256, 0, s>>>(r, E, scal.as<float>());
-  PG_CUDA(cudaMemsetAsync(g32.ptr, 0, (size_t)V[0] * 16 * sizeof(float), s));
-  k_to_grid<T><<<nb(E), 256, 0, s>>>(r, slot, E, scal.as<float>(), g32.as<float>());
-  k_pack_input<<<nb(V[0] * kIn), 256, 0, s>>>(g32.as<float>(), feat.as<float>(), V[0], x0.as<__nv_bfloat16>());
+Status Net::load_input(cudaStream_t s, const T* r, int64_t E) {
+  (void)E;
+  const int gx = g[0][0], gy = g[0][1], gz = g[0][2];
+  const unsigned blocks = nb(V[0]);
+  k_hx_in<T><<<blocks, 256, 0, s>>>(r, slot_edge.as<int32_t>(), tang.as<float4>(), aux.as<float4>(), gx, gy, gz,
+                                    nodes8.as<float>(), npart.as<double>());
+  const int64_t n_in = (int64_t)std::max(gx - 2, 0) * std::max(gy - 2, 0) * std::max(gz - 2, 0);
+  k_hx_scale<<<1, 256, 0, s>>>(npart.as<double>(), (int)blocks, n_in, scal.as<float>());
+  k_hx_pack<<<nb(V[0] * kIn), 256, 0, s>>>(nodes8.as<float>(), feat.as<float>(), V[0], scal.as<float>(),
+                                           x0.as<__nv_bfloat16>());
   PG_CUDA(cudaGetLastError());
   return Status{};
 }
 
 template <typename T>
-Status Net::apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T* z) {
-  PG_TRY(load_input(s, r, slot, E));
+Status Net::apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T* z, bool xspace) {
+  PG_TRY(load_input(s, r, E));
   PG_TRY(forward(s));
-  k_from_grid<T><<<nb(E), 256, 0, s>>>(y.as<float>(), slot, E, scal.as<float>() + 1, z);
+  const double2* d = ctx->diag.as<double2>();
+  if (xspace)
+    k_hx_out<T, true><<<nb(E), 256, 0, s>>>(r, slot, E, y.as<float>(), aux.as<float4>(), tang.as<float4>(),
+                                            scal.as<float>(), d, g[0][0], g[0][1], z);
+  else
+    k_hx_out<T, false><<<nb(E), 256, 0, s>>>(r, slot, E, y.as<float>(), aux.as<float4>(), tang.as<float4>(),
+                                             scal.as<float>(), d, g[0][0], g[0][1], z);
   PG_CUDA(cudaGetLastError());
   return Status{};
 }
 
-template Status Net::apply<float2>(cudaStream_t, const float2*, const int32_t*, int64_t, float2*);
-template Status Net::apply<double2>(cudaStream_t, const double2*, const int32_t*, int64_t, double2*);
+template Status Net::apply<float2>(cudaStream_t, const float2*, const int32_t*, int64_t, float2*, bool);
+template Status Net::apply<double2>(cudaStream_t, const double2*, const int32_t*, int64_t, double2*, bool);
 
 // One training sample, r = the residual of a solver iterate (complex128 edge vector).  Loss: the
-// residual angle L = 1 - |<r, Ahat z>|^2 / (|r|^2 |Ahat z|^2) of the network's direction z
-// (scale-free, as flexible GMRES is), back-propagated through Ahat^H to the grid.
+// residual angle L = 1 - |<r, A z>|^2 / (|r|^2 |A z|^2) of the preconditioned direction
+// z = D^{-1} r + G phi + Pi w (scale-free, as flexible GMRES is), back-propagated through A^H and
+// the auxiliary maps to the network output.  A z = Ahat (D z) with Ahat = A D^{-1}.
 Status Net::sample_grad(cudaStream_t s, petgem_ctx* c, const double2* r, const int32_t* slot, int64_t E, bool acc) {
-  PG_TRY(load_input(s, r, slot, E));
+  PG_TRY(load_input(s, r, E));
   PG_TRY(forward(s));
-  double2* z = dutmp.as<double2>();
+  double2* zu = dutmp.as<double2>();
   double2* w = wtmp.as<double2>();
   double2* gw = gtmp.as<double2>();
-  k_set_one<<<1, 1, 0, s>>>(scal.as<float>() + 4);
-  k_from_grid<double2><<<nb(E), 256, 0, s>>>(y.as<float>(), slot, E, scal.as<float>() + 4, z);
+  k_hx_out<double2, false><<<nb(E), 256, 0, s>>>(r, slot, E, y.as<float>(), aux.as<float4>(), tang.as<float4>(),
+                                                 scal.as<float>(), c->diag.as<double2>(), g[0][0], g[0][1], zu);
   k_ahat_apply<<<nb(E), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(),
-                                     c->diag.as<double2>(), z, E, w);
+                                     c->diag.as<double2>(), zu, E, w);
   k_angle_dots<<<1, 1024, 0, s>>>(r, w, E, dvec.as<double>(), loss_acc.as<double>());
   k_angle_gw<<<nb(E), 256, 0, s>>>(r, w, E, dvec.as<double>(), gw);
   k_ahat_adjoint<<<nb(E), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(),
-                                       c->diag.as<double2>(), gw, E, z);
-  PG_CUDA(cudaMemsetAsync(dy.ptr, 0, (size_t)V[0] * 16 * sizeof(__nv_bfloat16), s));
-  k_grad_to_grid<<<nb(E), 256, 0, s>>>(z, slot, E, dy.as<__nv_bfloat16>());
+                                       c->diag.as<double2>(), gw, E, zu);
+  k_hx_dy<<<nb(V[0]), 256, 0, s>>>(zu, c->diag.as<double2>(), slot_edge.as<int32_t>(), tang.as<float4>(),
+                                   aux.as<float4>(), scal.as<float>(), g[0][0], g[0][1], g[0][2],
+                                   dy.as<__nv_bfloat16>());
   PG_CUDA(cudaGetLastError());
   PG_TRY(backward(s, acc));
   return Status{};
@@ -610,6 +854,7 @@ Status Net::adam_step(cudaStream_t s, float lr, float gscale) {
 }
 
 Status Net::features(cudaStream_t s, const double* sigma, double sigma_p, double omega, double h) {
+  PG_TRY(prepare_aux(ctx));
   const double mu0 = 4.0e-7 * 3.141592653589793238462643383279502884;
   k_node_features<<<nb(V[0]), 256, 0, s>>>(sigma, nx, ny, nz, sigma_p, omega * mu0 * h * h, feat.as<float>());
   PG_CUDA(cudaGetLastError());

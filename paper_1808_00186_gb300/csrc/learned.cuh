@@ -25,6 +25,12 @@ struct Net {
   DevBuf x0, a1, p1, a2, p2, a3, p3, a4, s5, a5, s6, a6, s7, y;
   DevBuf dy, ds7, da6, ds6, da5, ds5, da4, dp3, dp2, dp1;
   DevBuf g32, feat, scal, loss_acc, err, wpart, rtmp, dutmp, wtmp, gtmp, dvec;
+  // auxiliary spaces on the lattice: edge of every slot (node * 7 + class, -1 if none), the
+  // slot's unit tangent and inverse length, per-node scales (sg, sp_x, sp_y, sp_z), the gathered
+  // node fields [V0][8] and per-block partial sums
+  DevBuf slot_edge, tang, aux, nodes8, npart;
+  int64_t aux_version = -1;    // assembly the scales belong to
+  int64_t geom_version = -1;   // mesh the slot map and tangents belong to
 
   Status init(petgem_ctx* c, int nx, int ny, int nz);
   Status pack_weights(cudaStream_t s);
@@ -33,8 +39,12 @@ struct Net {
   Status wgrad(cudaStream_t s, int i, const __nv_bfloat16* in, const __nv_bfloat16* dout, bool acc);
   Status forward(cudaStream_t s);
   Status backward(cudaStream_t s, bool acc);
-  template <typename T> Status load_input(cudaStream_t s, const T* r, const int32_t* slot, int64_t E);
-  template <typename T> Status apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T* z);
+  Status prepare_aux(petgem_ctx* c);
+  template <typename T> Status load_input(cudaStream_t s, const T* r, int64_t E);
+  // z = D (D^{-1} r + G phi + Pi w) (the solver's Jacobi-scaled variables) or, with xspace,
+  // z = D^{-1} r + G phi + Pi w, for the residual r of E entries.
+  template <typename T> Status apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T* z,
+                                     bool xspace = false);
   Status sample_grad(cudaStream_t s, petgem_ctx* c, const double2* r, const int32_t* slot, int64_t E, bool acc);
   Status adam_step(cudaStream_t s, float lr, float gscale);
   Status features(cudaStream_t s, const double* sigma, double sigma_p, double omega, double h);

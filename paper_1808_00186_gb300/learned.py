@@ -1,12 +1,17 @@
 """Training and use of the learned preconditioner (network and kernels in the CUDA library).
 
+The preconditioner is z = D^{-1} r + G phi + Pi w: Jacobi plus the two auxiliary spaces of the
+edge elements (nodal gradients and nodal vector fields), with the two nodal solves replaced by a
+3-D convolutional network on the node lattice (include/petgem.h, "learned preconditioner").
+
 Parameter layout of the flat vector the library exposes (petgem_learned_params): for each of the
 seven convolutions c1..c7 in order, W[27][cout][cin] then b[cout], with (cin, cout) =
-(16,16), (16,32), (32,32), (32,32), (32,32), (32,16), (16,16).  Output channels 14, 15 of c7 are
-padding and stay zero.
+(16,16), (16,32), (32,32), (32,32), (32,32), (32,16), (16,16).  Output channels 8..15 of c7 are
+unused and stay zero.
 
 Training samples come from the plain solver: the iterate x_k at the start of every GMRES cycle; the
-library turns each into its residual and trains the network's direction on the residual angle.
+library turns each into its residual and trains the network on the residual angle of one step
+along z.
 """
 from __future__ import annotations
 
@@ -17,7 +22,7 @@ import numpy as np
 from . import api, synth
 
 LAYERS = [(16, 16), (16, 32), (32, 32), (32, 32), (32, 32), (32, 16), (16, 16)]
-N_OUT = 14
+N_OUT = 8
 
 
 def layout():
@@ -92,43 +97,96 @@ def solver_pairs(ctx: api.Context, restart: int = 50, max_cycles: int = 400, pre
     return torch.stack(iterates), x[0].clone(), len(iterates)
 
 
-def train(n: int = 32, models: int = 200, epochs: int = 2, lr: float = 1e-3, seed: int = 0, samples_per_model: int = 12,
-          params: np.ndarray | None = None, log=None):
-    """Train the network on residual / correction pairs of the plain solver over random block models.
+def solve_samples(ctx: api.Context, samples: int, restart: int = 50, max_cycles: int = 400,
+                  precision=api.PREC_MIXED):
+    """Iterates at `samples` cycle starts, spread evenly over the plain solve of the context's
+    assembled system (source 0), as a device tensor [k, E]; and the number of cycles it took."""
+    its, _, cyc = solver_pairs(ctx, restart=restart, max_cycles=max_cycles, precision=precision)
+    if its.shape[0] > samples:
+        idx = np.linspace(0, its.shape[0] - 1, samples).round().astype(int)
+        its = its[idx]
+    return its, cyc
+
+
+def train(n: int = 32, models: int = 200, epochs: int = 2, lr: float = 1e-3, seed: int = 0, samples_per_model: int = 8,
+          params: np.ndarray | None = None, log=None, lr_final: float | None = None):
+    """Train the network on residuals of the plain solver over random block models on one n^3 cube
+    lattice (models differ in conductivity and frequency only, so the mesh is built once).
+    The learning rate decays geometrically from lr to lr_final (default lr / 10) over the epochs.
     Returns (params, history)."""
-    import torch
     ctx = api.Context()
+    mdl0 = random_block_model(n, seed * 100000)
+    ctx.mesh(mdl0.mesh.nodes, mdl0.mesh.tets)
+    api.petgem_learned_create(ctx.h, n, n, n)
     data = []
     t0 = time.time()
+    cycles = []
     for m in range(models):
         mdl = random_block_model(n, seed * 100000 + m)
-        ctx.mesh(mdl.mesh.nodes, mdl.mesh.tets)
         ctx.assemble(mdl.freq, mdl.sigma, mdl.sigma_p, mdl.sources)
-        its, xstar, cyc = solver_pairs(ctx)
-        if its.shape[0] > samples_per_model:
-            idx = np.linspace(0, its.shape[0] - 1, samples_per_model).round().astype(int)
-            its = its[idx]
-        data.append((mdl, its, xstar))
+        its, cyc = solve_samples(ctx, samples_per_model)
+        cycles.append(cyc)
+        data.append((mdl.freq, mdl.sigma, mdl.sigma_p, mdl.sources, its))
     gen_s = time.time() - t0
     history = []
     p = init_params(seed) if params is None else params
-    first = True
+    api.petgem_learned_params(ctx.h, set_params=p)
+    lr_final = lr / 10.0 if lr_final is None else lr_final
     t0 = time.time()
+    steps = 0
     for ep in range(epochs):
         order = np.random.default_rng(seed + ep).permutation(len(data))
+        lr_ep = lr * (lr_final / lr) ** (ep / max(1, epochs - 1))
         losses = []
         for i in order:
-            mdl, its, xstar = data[i]
-            ctx.mesh(mdl.mesh.nodes, mdl.mesh.tets)
-            ctx.assemble(mdl.freq, mdl.sigma, mdl.sigma_p, mdl.sources)
-            api.petgem_learned_create(ctx.h, n, n, n)
-            if first:
-                api.petgem_learned_params(ctx.h, set_params=p)
-                first = False
-            losses.append(api.petgem_learned_train_step(ctx.h, its.contiguous(), lr))
+            freq, sigma, sigma_p, sources, its = data[i]
+            ctx.assemble(freq, sigma, sigma_p, sources)
+            losses.append(api.petgem_learned_train_step(ctx.h, its.contiguous(), lr_ep))
+            steps += 1
         history.append(float(np.mean(losses)))
         if log:
-            log("epoch %d loss %.4e" % (ep, history[-1]))
+            log("epoch %d lr %.2e loss %.4e (%.0f s)" % (ep, lr_ep, history[-1], time.time() - t0))
     p = api.petgem_learned_params(ctx.h, get=True)
     ctx.close()
-    return p, {"loss": history, "generate_s": gen_s, "train_s": time.time() - t0, "models": models, "n": n}
+    return p, {"loss": history, "generate_s": gen_s, "train_s": time.time() - t0, "models": models, "n": n,
+               "samples_per_model": samples_per_model, "epochs": epochs, "steps": steps,
+               "mean_cycles": float(np.mean(cycles))}
+
+
+def evaluate(params: np.ndarray, n: int, seeds, precision=api.PREC_MIXED, tol: float = 1e-8, log=None):
+    """Learned FGMRES against plain Jacobi GMRES(50) on unseen random block models of n^3 cells:
+    [{seed, iters_jacobi, iters_learned, s_jacobi, s_learned, fell_back, relres}] (times from
+    CUDA events around each solve, assembly excluded)."""
+    import torch
+    out = []
+    ctx = api.Context()
+    try:
+        for k, sd in enumerate(seeds):
+            mdl = random_block_model(n, sd)
+            if k == 0:
+                ctx.mesh(mdl.mesh.nodes, mdl.mesh.tets)
+                api.petgem_learned_create(ctx.h, n, n, n)
+                api.petgem_learned_params(ctx.h, set_params=params)
+            ctx.assemble(mdl.freq, mdl.sigma, mdl.sigma_p, mdl.sources)
+            rec = {"seed": int(sd), "freq": mdl.freq}
+            for name, pc in (("jacobi", api.PRECOND_JACOBI), ("learned", api.PRECOND_LEARNED)):
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                ev0.record()
+                x, info, st = ctx.solve(precision=precision, precond=pc, tol=tol, allow_not_converged=True)
+                ev1.record()
+                torch.cuda.synchronize()
+                rec["iters_" + name] = int(info[0]["iters"])
+                rec["s_" + name] = ev0.elapsed_time(ev1) / 1e3
+                rec["relres_" + name] = float(info[0]["true_rel_residual"])
+                rec["status_" + name] = int(st)
+                if name == "learned":
+                    rec["fell_back"] = int(info[0]["fell_back"])
+            out.append(rec)
+            if log:
+                log("eval n=%d seed %d f=%.2f: jacobi %d its %.3f s, learned %d its %.3f s (fell back %d)"
+                    % (n, sd, mdl.freq, rec["iters_jacobi"], rec["s_jacobi"], rec["iters_learned"],
+                       rec["s_learned"], rec["fell_back"]))
+    finally:
+        ctx.close()
+    return out

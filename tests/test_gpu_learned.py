@@ -82,33 +82,63 @@ def lattice_case(n, seed):
     return m, ref
 
 
-def oracle_input(m, ref, x, n):
-    """The network input grid defined in the library's documentation, built from the oracle's
-    assembled system: residual r = b - A x scaled by 1 / RMS(r), plus the two node features."""
+def oracle_maps(m, ref, n):
+    """The auxiliary-space maps, scales, features and the system matrix of the oracle's assembly."""
+    import scipy.sparse as sp
     rp, col, val, b = ref.system()
     edges, _, _, _ = ref.topology()
+    A = sp.csr_matrix((val, col, rp), shape=(ref.n_edges, ref.n_edges))
+    G, Pi = OL.aux_operators(edges, m.mesh.nodes, n)
+    sg, sp_ = OL.aux_scales(G, Pi, A)
+    nd = m.mesh.nodes
+    h = (abs(nd[1, 0] - nd[0, 0]) * abs(nd[n + 1, 1] - nd[0, 1]) * abs(nd[(n + 1) ** 2, 2] - nd[0, 2])) ** (1 / 3)
+    feat = OL.node_features(m.sigma, (n, n, n), m.sigma_p, m.freq, h)
+    return A, b, G, Pi, sg, sp_, feat
+
+
+def perturbed_iterate(xstar, seed):
+    rng = np.random.default_rng(seed)
+    return xstar * (1 + 0.3 * rng.normal(size=xstar.shape)) + 1e-3 * np.abs(xstar).max() * rng.normal(size=xstar.shape)
+
+
+def test_auxiliary_space_maps_match_oracle():
+    """With all weights zero the network's output is its last bias b at every node, so
+    z = D^-1 r + G phi + Pi w is a fixed function of the auxiliary maps, their diagonal scales and
+    the residual's scale s: the kernels must reproduce the oracle's z to FP32 rounding."""
+    n = 7
+    m, ref = lattice_case(n, 21)
+    A, b, G, Pi, sg, sp_, feat = oracle_maps(m, ref, n)
+    xstar = ref.solve(tol=1e-10)[0][0]
+    x = perturbed_iterate(xstar, 2)
     r = b[0] - ref.spmv(x)
-    diag = np.array([val[rp[i]:rp[i + 1]][col[rp[i]:rp[i + 1]] == i][0] for i in range(ref.n_edges)])
-    s = math.sqrt(np.mean(np.abs(r) ** 2))
-    slot = OL.edge_grid_index(edges, n)
-    grid = OL.edges_to_grid(r, slot, (n + 1) ** 3, 1.0 / s)
-    # node features: cell whose lowest corner is the node (clamped), log10(sigma/sigma_p), log10(w mu0 sigma h^2)
-    sig_cell = m.sigma.reshape(n, n, n, 6).mean(axis=3)        # [k][j][i]
-    idx = np.minimum(np.arange(n + 1), n - 1)
-    sc = sig_cell[np.ix_(idx, idx, idx)].reshape(-1)
-    h = 2000.0 / n
-    w = 2 * math.pi * m.freq * 4e-7 * math.pi
-    grid[:, 14] = np.log10(sc / m.sigma_p)
-    grid[:, 15] = np.log10(w * sc * h * h)
-    return grid, r, s, slot, diag
+    lay, n_par = PL.layout()
+    p = np.zeros(n_par, np.float32)
+    bias = np.random.default_rng(4).normal(size=16).astype(np.float32)
+    bias[8:] = 0.0
+    p[lay[-1][2]:lay[-1][2] + 16] = bias
+    with api.Context(0) as ctx:
+        ctx.mesh(m.mesh.nodes, m.mesh.tets)
+        ctx.assemble(m.freq, m.sigma, m.sigma_p, m.sources)
+        api.petgem_learned_create(ctx.h, n, n, n)
+        api.petgem_learned_params(ctx.h, set_params=p)
+        r_t = ctx.tensor(r)
+        z_t = torch.empty_like(r_t)
+        api.petgem_learned_apply(ctx.h, r_t, z_t)
+        z = z_t.cpu().numpy()
+    _, s = OL.hx_input(r, G, Pi, sg, sp_, feat)
+    y = np.tile(bias.astype(np.float64), (G.shape[1], 1))
+    zr = OL.hx_direction(y, r, s, G, Pi, sg, sp_, A.diagonal())
+    assert np.linalg.norm(z - zr) <= 1e-5 * np.linalg.norm(zr)
+    # the correction is a real part of z (not just the Jacobi term)
+    assert np.linalg.norm(zr - r / A.diagonal()) >= 1e-2 * np.linalg.norm(zr)
 
 
 def test_network_forward_loss_and_gradients_match_oracle():
     n = 6
     m, ref = lattice_case(n, 11)
+    A, b, G, Pi, sg, sp_, feat = oracle_maps(m, ref, n)
     xstar = ref.solve(tol=1e-12)[0][0]
-    rng = np.random.default_rng(1)
-    x = xstar * (1 + 0.3 * rng.normal(size=xstar.shape)) + 1e-3 * np.abs(xstar).max() * rng.normal(size=xstar.shape)
+    x = perturbed_iterate(xstar, 1)
     p = PL.init_params(5)
     lay, _ = PL.layout()
     with api.Context(0) as ctx:
@@ -118,42 +148,52 @@ def test_network_forward_loss_and_gradients_match_oracle():
         api.petgem_learned_params(ctx.h, set_params=p)
         loss = api.petgem_learned_train_step(ctx.h, ctx.tensor(x[None, :]), 1e-12)
         g_gpu = api.petgem_learned_params(ctx.h, grad=True)
-        r_t = ctx.tensor(ref.system()[3][0] - ref.spmv(x))
+        r_t = ctx.tensor(b[0] - ref.spmv(x))
         z_t = torch.empty_like(r_t)
         api.petgem_learned_apply(ctx.h, r_t, z_t)
         z = z_t.cpu().numpy()
-    grid, r, s, slot, diag = oracle_input(m, ref, x, n)
+    r = b[0] - ref.spmv(x)
+    xin, s = OL.hx_input(r, G, Pi, sg, sp_, feat)
     P = PL.unflatten(p)
     shape = (n + 1, n + 1, n + 1)
-    y, cache = OL.forward(P, grid.reshape(*shape, 16))
-    L, gy = OL.angle_loss(y.reshape(-1, 16), r, slot, ref.spmv, diag)
+    y, cache = OL.forward(P, xin.reshape(*shape, 16))
+    L, gy = OL.hx_angle_loss(y.reshape(-1, 16), r, s, G, Pi, sg, sp_, A.diagonal(), ref.spmv)
     gref = OL.backward(P, cache, gy.reshape(*shape, 16))
     assert abs(loss - L) <= 5e-2 * L
-    for name, w, b, ci, co in lay:
+    for name, w, bb, ci, co in lay:
         gw = g_gpu[w:w + 27 * co * ci].reshape(27, co, ci)
         assert np.linalg.norm(gw - gref[name + ".W"]) <= 5e-2 * np.linalg.norm(gref[name + ".W"]) + 1e-12, name
-        gb = g_gpu[b:b + co]
+        gb = g_gpu[bb:bb + co]
         assert np.linalg.norm(gb - gref[name + ".b"]) <= 5e-2 * np.linalg.norm(gref[name + ".b"]) + 1e-12, name
-    # apply: z = s N(r / s) on the edges
-    corr = s * OL.grid_to_edges(y.reshape(-1, 16), slot)
-    assert np.linalg.norm(z - corr) <= 5e-2 * np.linalg.norm(corr)
+    # apply: z = D^-1 r + G phi + Pi w from the network's output
+    zr = OL.hx_direction(y.reshape(-1, 16), r, s, G, Pi, sg, sp_, A.diagonal())
+    assert np.linalg.norm(z - zr) <= 5e-2 * np.linalg.norm(zr - r / A.diagonal())
 
 
-def test_learned_fgmres_converges_and_is_compared_with_jacobi():
+def test_learned_fgmres_gains_over_jacobi_on_unseen_models():
+    """A network trained on the GPU (the library's own forward and backward kernels) on residuals
+    of the plain solver over random block models lowers the FGMRES iteration count against plain
+    Jacobi GMRES(50) on models it has not seen, without falling back, and the answer is the
+    oracle's (the FP64 true residual decides convergence)."""
     n = 12
-    params, hist = PL.train(n=n, models=6, epochs=3, lr=2e-3, seed=1)
+    params, hist = PL.train(n=n, models=32, epochs=8, lr=2e-3, seed=1, samples_per_model=8)
     assert hist["loss"][-1] < hist["loss"][0]
-    m, ref = lattice_case(n, 999)
+    res = PL.evaluate(params, n, [10000, 10001, 10002])
+    for rec in res:
+        assert rec["status_learned"] == api.OK and rec["fell_back"] == 0
+        assert rec["relres_learned"] <= 1e-8
+    ratio = np.mean([r["iters_learned"] / r["iters_jacobi"] for r in res])
+    print("\nlearned FGMRES / Jacobi GMRES iterations on unseen n=%d models: %s (mean ratio %.2f)"
+          % (n, [(r["iters_learned"], r["iters_jacobi"]) for r in res], ratio))
+    assert ratio <= 0.75
+    m, ref = lattice_case(n, 10000)
     xr = ref.solve(tol=1e-10)[0][0]
     with api.Context(0) as ctx:
         ctx.mesh(m.mesh.nodes, m.mesh.tets)
         ctx.assemble(m.freq, m.sigma, m.sigma_p, m.sources)
         api.petgem_learned_create(ctx.h, n, n, n)
         api.petgem_learned_params(ctx.h, set_params=params)
-        xj, info_j, _ = ctx.solve(precision=api.PREC_MIXED)
         xl, info_l, st = ctx.solve(precision=api.PREC_MIXED, precond=api.PRECOND_LEARNED)
         xl = xl.cpu().numpy()[0]
-    assert st == api.OK and info_l[0]["true_rel_residual"] <= 1e-8
+    assert st == api.OK and info_l[0]["fell_back"] == 0
     assert np.linalg.norm(xl - xr) <= 1e-6 * np.linalg.norm(xr)
-    print("\nlearned FGMRES: %d iterations (fell back: %d), Jacobi GMRES: %d iterations"
-          % (info_l[0]["iters"], info_l[0]["fell_back"], info_j[0]["iters"]))
