@@ -699,8 +699,9 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
       if (learned) PG_CUDA(cudaMemcpyAsync(S->usave.ptr, S->u.ptr, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
       const int mj = (int)std::min<int64_t>(m, std::max<int64_t>(o.max_iters - iters, 0));
       const double tol_abs = o.tol * bnorm;
-      // Learned cycles always re-orthogonalise: the network's directions can be nearly dependent.
-      const int orth = learned ? PETGEM_ORTH_CGS2 : o.orth;
+      // Learned cycles take a second Gram-Schmidt pass whenever the first one lost more than a
+      // factor 1/sqrt(2) of the norm (the network's directions can be nearly dependent).
+      const int orth = learned && o.orth == PETGEM_ORTH_CGS ? PETGEM_ORTH_CGS_IFNEEDED : o.orth;
       // A cycle whose starting residual already meets tol runs no iteration (k = 0).
       if (o.precision == PETGEM_PREC_MIXED)
         PG_TRY(run_cycle<float2>(c, S->ahat64.as<float2>(), mj, orth, tol_abs, o.inner_tol, learned, o.use_graphs != 0, &hs));

@@ -59,25 +59,33 @@ __device__ inline void grid_coords(int64_t v, int gx, int gy, int& x, int& y, in
   z = (int)(v / ((int64_t)gx * gy));
 }
 
-// Average of the existing children 2c + {0,1}^3 of every coarse voxel.
+// Average of the existing children 2c + {0,1}^3 of every coarse voxel; one thread per coarse
+// voxel and 8 channels (16-byte loads and stores).
 __global__ void k_pool(const __nv_bfloat16* __restrict__ in, int gx, int gy, int gz, int C,
                        __nv_bfloat16* __restrict__ out) {
   const int cx = (gx + 1) / 2, cy = (gy + 1) / 2, cz = (gz + 1) / 2;
+  const int C8 = C / 8;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)cx * cy * cz * C) return;
-  const int c = (int)(idx % C);
+  if (idx >= (int64_t)cx * cy * cz * C8) return;
+  const int c8 = (int)(idx % C8);
   int x, y, z;
-  grid_coords(idx / C, cx, cy, x, y, z);
-  float s = 0.f;
+  grid_coords(idx / C8, cx, cy, x, y, z);
+  float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int n = 0;
   for (int o = 0; o < 8; ++o) {
     const int fx = 2 * x + (o & 1), fy = 2 * y + ((o >> 1) & 1), fz = 2 * z + (o >> 2);
     if (fx < gx && fy < gy && fz < gz) {
-      s += __bfloat162float(in[((int64_t)fx + gx * ((int64_t)fy + (int64_t)gy * fz)) * C + c]);
+      const uint4 u = *reinterpret_cast<const uint4*>(in + ((int64_t)fx + gx * ((int64_t)fy + (int64_t)gy * fz)) * C + 8 * c8);
+      const __nv_bfloat16* b = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s[k] += __bfloat162float(b[k]);
       ++n;
     }
   }
-  out[idx] = __float2bfloat16(s / n);
+  __align__(16) __nv_bfloat16 o8[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) o8[k] = __float2bfloat16(s[k] / n);
+  *reinterpret_cast<uint4*>(out + (idx / C8) * C + 8 * c8) = *reinterpret_cast<const uint4*>(o8);
 }
 // din[f] += dout[parent(f)] / (children of the parent)
 __global__ void k_pool_bwd_add(const __nv_bfloat16* __restrict__ dout, int gx, int gy, int gz, int C,
@@ -93,17 +101,26 @@ __global__ void k_pool_bwd_add(const __nv_bfloat16* __restrict__ dout, int gx, i
   const float g = __bfloat162float(dout[((int64_t)px + cx * ((int64_t)py + (int64_t)cy * pz)) * C + c]) / (nx * ny * nz);
   din[idx] = __float2bfloat16(__bfloat162float(din[idx]) + g);
 }
-// out[f] = coarse[parent(f)] + skip[f]
+// out[f] = coarse[parent(f)] + skip[f]; one thread per fine voxel and 8 channels.
 __global__ void k_up_add(const __nv_bfloat16* __restrict__ coarse, const __nv_bfloat16* __restrict__ skip, int gx,
                          int gy, int gz, int C, __nv_bfloat16* __restrict__ out) {
+  const int C8 = C / 8;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)gx * gy * gz * C) return;
-  const int c = (int)(idx % C);
+  if (idx >= (int64_t)gx * gy * gz * C8) return;
+  const int c8 = (int)(idx % C8);
+  const int64_t v = idx / C8;
   int x, y, z;
-  grid_coords(idx / C, gx, gy, x, y, z);
+  grid_coords(v, gx, gy, x, y, z);
   const int cx = (gx + 1) / 2, cy = (gy + 1) / 2;
-  const float a = __bfloat162float(coarse[((int64_t)(x / 2) + cx * ((int64_t)(y / 2) + (int64_t)cy * (z / 2))) * C + c]);
-  out[idx] = __float2bfloat16(a + __bfloat162float(skip[idx]));
+  const uint4 a = *reinterpret_cast<const uint4*>(
+      coarse + ((int64_t)(x / 2) + cx * ((int64_t)(y / 2) + (int64_t)cy * (z / 2))) * C + 8 * c8);
+  const uint4 b = *reinterpret_cast<const uint4*>(skip + v * C + 8 * c8);
+  const __nv_bfloat16* pa = reinterpret_cast<const __nv_bfloat16*>(&a);
+  const __nv_bfloat16* pb = reinterpret_cast<const __nv_bfloat16*>(&b);
+  __align__(16) __nv_bfloat16 o8[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) o8[k] = __float2bfloat16(__bfloat162float(pa[k]) + __bfloat162float(pb[k]));
+  *reinterpret_cast<uint4*>(out + v * C + 8 * c8) = *reinterpret_cast<const uint4*>(o8);
 }
 // dcoarse[c] = sum of dfine over c's children
 __global__ void k_up_bwd(const __nv_bfloat16* __restrict__ dfine, int gx, int gy, int gz, int C,
@@ -288,15 +305,18 @@ __global__ void k_hx_diag(const int32_t* __restrict__ slot_edge, const float4* _
 }
 
 // Node fields of an edge vector r: [sg Re G^T r, sg Im G^T r, sp Re Pi^T r (x, y, z), sp Im Pi^T r
-// (x, y, z)] per node, and per-block sums of their squares (FP64) for the scale s.
+// (x, y, z)] per node, and per-block sums of their squares (FP64) for the scale s.  The sums run
+// in the vector's own precision (FP32 for complex64: FP64 arithmetic per node would cost more
+// than the node's memory traffic on this GPU).
 template <typename T>
 __global__ void __launch_bounds__(256) k_hx_in(const T* __restrict__ r, const int32_t* __restrict__ slot_edge,
                                                const float4* __restrict__ tang, const float4* __restrict__ aux,
                                                int gx, int gy, int gz, float* __restrict__ out,
                                                double* __restrict__ part) {
+  using R = typename real_of<T>::type;
   __shared__ double red[8];
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double ss = 0.0;
+  float ss = 0.f;
   if (v < (int64_t)gx * gy * gz) {
     const float4 a = aux[v];
     float o[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -305,18 +325,18 @@ __global__ void __launch_bounds__(256) k_hx_in(const T* __restrict__ r, const in
       grid_coords(v, gx, gy, x, y, z);
       Incident I;
       incident_edges(v, x, y, z, gx, gy, slot_edge, tang, I);
-      double gr = 0.0, gi = 0.0, pr[3] = {0.0, 0.0, 0.0}, pi[3] = {0.0, 0.0, 0.0};
+      R gr = 0, gi = 0, pr[3] = {0, 0, 0}, pi[3] = {0, 0, 0};
       for (int k = 0; k < I.n; ++k) {
         const T re = r[I.e[k]];
-        const double xr = (double)re.x, xi = (double)re.y;
-        gr += I.g[k] * xr;
-        gi += I.g[k] * xi;
-        pr[0] += I.p[k].x * xr;
-        pi[0] += I.p[k].x * xi;
-        pr[1] += I.p[k].y * xr;
-        pi[1] += I.p[k].y * xi;
-        pr[2] += I.p[k].z * xr;
-        pi[2] += I.p[k].z * xi;
+        const R xr = (R)re.x, xi = (R)re.y;
+        gr += (R)I.g[k] * xr;
+        gi += (R)I.g[k] * xi;
+        pr[0] += (R)I.p[k].x * xr;
+        pi[0] += (R)I.p[k].x * xi;
+        pr[1] += (R)I.p[k].y * xr;
+        pi[1] += (R)I.p[k].y * xi;
+        pr[2] += (R)I.p[k].z * xr;
+        pi[2] += (R)I.p[k].z * xi;
       }
       o[0] = (float)(a.x * gr);
       o[1] = (float)(a.x * gi);
@@ -326,13 +346,15 @@ __global__ void __launch_bounds__(256) k_hx_in(const T* __restrict__ r, const in
       o[5] = (float)(a.y * pi[0]);
       o[6] = (float)(a.z * pi[1]);
       o[7] = (float)(a.w * pi[2]);
-      for (int k = 0; k < 8; ++k) ss += (double)o[k] * o[k];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) ss += o[k] * o[k];
     }
     reinterpret_cast<float4*>(out)[2 * v] = make_float4(o[0], o[1], o[2], o[3]);
     reinterpret_cast<float4*>(out)[2 * v + 1] = make_float4(o[4], o[5], o[6], o[7]);
   }
-  for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  double sd = ss;
+  for (int off = 16; off > 0; off >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sd;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -360,55 +382,64 @@ __global__ void k_hx_scale(const double* __restrict__ part, int nb, int64_t n_in
 }
 __global__ void k_hx_pack(const float* __restrict__ nodes8, const float* __restrict__ feat, int64_t V,
                           const float* __restrict__ scal, __nv_bfloat16* __restrict__ x) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= V * kIn) return;
-  const int c = (int)(i % kIn);
-  const int64_t v = i / kIn;
-  const float val = c < 8 ? nodes8[v * 8 + c] * scal[0] : (c < 10 ? feat[2 * v + (c - 8)] : 0.f);
-  x[i] = __float2bfloat16(val);
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const float is = scal[0];
+  const float4 a = reinterpret_cast<const float4*>(nodes8)[2 * v], b = reinterpret_cast<const float4*>(nodes8)[2 * v + 1];
+  const float2 f = reinterpret_cast<const float2*>(feat)[v];
+  __align__(16) __nv_bfloat16 o[16];
+  const float in[10] = {a.x * is, a.y * is, a.z * is, a.w * is, b.x * is, b.y * is, b.z * is, b.w * is, f.x, f.y};
+#pragma unroll
+  for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16(c < 10 ? in[c] : 0.f);
+  reinterpret_cast<uint4*>(x)[2 * v] = reinterpret_cast<const uint4*>(o)[0];
+  reinterpret_cast<uint4*>(x)[2 * v + 1] = reinterpret_cast<const uint4*>(o)[1];
 }
 // z_e = D^{-1} r_e + (G phi + Pi w)_e (XS) or r_e + D_e (G phi + Pi w)_e, from the network output y
 // [V][16] (FP32): phi = s sg (y0 + i y1), w_k = s sp_k (y_{2+k} + i y_{5+k}) at the edge's nodes.
+// Arithmetic in the vector's precision (FP32 for complex64).
 template <typename T, bool XS>
 __global__ void k_hx_out(const T* __restrict__ r, const int32_t* __restrict__ slot, int64_t E,
                          const float* __restrict__ y, const float4* __restrict__ aux, const float4* __restrict__ tang,
                          const float* __restrict__ scal, const double2* __restrict__ diag, int gx, int gy,
                          T* __restrict__ z) {
+  using R = typename real_of<T>::type;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= E) return;
   const int32_t sl = slot[e];
   const T re = r[e];
-  double cr = 0.0, ci = 0.0;
+  R cr = 0, ci = 0;
   if (sl >= 0) {
     const int64_t lo = sl / 7;
     const int c = sl - (int)(lo * 7);
     const int64_t hi = lo + kStep[c][0] + (int64_t)gx * (kStep[c][1] + (int64_t)gy * kStep[c][2]);
     const float4 t = tang[sl];
-    const float s = scal[1];
+    const R s = scal[1];
     const float4 al = aux[lo], ah = aux[hi];
     const float4* yl = reinterpret_cast<const float4*>(y + lo * 16);
     const float4* yh = reinterpret_cast<const float4*>(y + hi * 16);
     const float4 l0 = yl[0], l1 = yl[1], h0 = yh[0], h1 = yh[1];
     // G phi: (phi_hi - phi_lo) / |t|
-    cr = (double)t.w * s * ((double)ah.x * h0.x - (double)al.x * l0.x);
-    ci = (double)t.w * s * ((double)ah.x * h0.y - (double)al.x * l0.y);
+    cr = (R)t.w * s * ((R)ah.x * h0.x - (R)al.x * l0.x);
+    ci = (R)t.w * s * ((R)ah.x * h0.y - (R)al.x * l0.y);
     // Pi w: (w_lo + w_hi) . t / (2 |t|); channels: Re x,y,z = 2,3,4; Im x,y,z = 5,6,7
-    const double hs = 0.5 * s;
-    cr += hs * (t.x * ((double)al.y * l0.z + (double)ah.y * h0.z) + t.y * ((double)al.z * l0.w + (double)ah.z * h0.w) +
-                t.z * ((double)al.w * l1.x + (double)ah.w * h1.x));
-    ci += hs * (t.x * ((double)al.y * l1.y + (double)ah.y * h1.y) + t.y * ((double)al.z * l1.z + (double)ah.z * h1.z) +
-                t.z * ((double)al.w * l1.w + (double)ah.w * h1.w));
+    const R hs = (R)0.5 * s;
+    cr += hs * ((R)t.x * ((R)al.y * l0.z + (R)ah.y * h0.z) + (R)t.y * ((R)al.z * l0.w + (R)ah.z * h0.w) +
+                (R)t.z * ((R)al.w * l1.x + (R)ah.w * h1.x));
+    ci += hs * ((R)t.x * ((R)al.y * l1.y + (R)ah.y * h1.y) + (R)t.y * ((R)al.z * l1.z + (R)ah.z * h1.z) +
+                (R)t.z * ((R)al.w * l1.w + (R)ah.w * h1.w));
   }
-  const double2 d = diag[e];
-  double2 out;
-  if (XS) {
-    out = cadd(cdiv(make_double2((double)re.x, (double)re.y), d), make_double2(cr, ci));
-  } else {
-    out = cadd(make_double2((double)re.x, (double)re.y), cmul(d, make_double2(cr, ci)));
-  }
+  const double2 dd = diag[e];
+  const R dr = (R)dd.x, di = (R)dd.y;
+  const R rr = (R)re.x, ri = (R)re.y;
   T o;
-  o.x = out.x;
-  o.y = out.y;
+  if (XS) {  // r / d + corr
+    const R den = dr * dr + di * di;
+    o.x = (rr * dr + ri * di) / den + cr;
+    o.y = (ri * dr - rr * di) / den + ci;
+  } else {  // r + d corr
+    o.x = rr + (dr * cr - di * ci);
+    o.y = ri + (dr * ci + di * cr);
+  }
   z[e] = o;
 }
 // Gradient of the loss with respect to the network output: with gzp = Ahat^H gw and
@@ -691,17 +722,17 @@ Status Net::conv(cudaStream_t s, int i, const __nv_bfloat16* in, __nv_bfloat16* 
 Status Net::forward(cudaStream_t s) {
   using B = __nv_bfloat16;
   PG_TRY(conv(s, 0, x0.as<B>(), a1.as<B>(), nullptr));
-  k_pool<<<nb(V[1] * 16), 256, 0, s>>>(a1.as<B>(), g[0][0], g[0][1], g[0][2], 16, p1.as<B>());
+  k_pool<<<nb(V[1] * 2), 256, 0, s>>>(a1.as<B>(), g[0][0], g[0][1], g[0][2], 16, p1.as<B>());
   PG_TRY(conv(s, 1, p1.as<B>(), a2.as<B>(), nullptr));
-  k_pool<<<nb(V[2] * 32), 256, 0, s>>>(a2.as<B>(), g[1][0], g[1][1], g[1][2], 32, p2.as<B>());
+  k_pool<<<nb(V[2] * 4), 256, 0, s>>>(a2.as<B>(), g[1][0], g[1][1], g[1][2], 32, p2.as<B>());
   PG_TRY(conv(s, 2, p2.as<B>(), a3.as<B>(), nullptr));
-  k_pool<<<nb(V[3] * 32), 256, 0, s>>>(a3.as<B>(), g[2][0], g[2][1], g[2][2], 32, p3.as<B>());
+  k_pool<<<nb(V[3] * 4), 256, 0, s>>>(a3.as<B>(), g[2][0], g[2][1], g[2][2], 32, p3.as<B>());
   PG_TRY(conv(s, 3, p3.as<B>(), a4.as<B>(), nullptr));
-  k_up_add<<<nb(V[2] * 32), 256, 0, s>>>(a4.as<B>(), a3.as<B>(), g[2][0], g[2][1], g[2][2], 32, s5.as<B>());
+  k_up_add<<<nb(V[2] * 4), 256, 0, s>>>(a4.as<B>(), a3.as<B>(), g[2][0], g[2][1], g[2][2], 32, s5.as<B>());
   PG_TRY(conv(s, 4, s5.as<B>(), a5.as<B>(), nullptr));
-  k_up_add<<<nb(V[1] * 32), 256, 0, s>>>(a5.as<B>(), a2.as<B>(), g[1][0], g[1][1], g[1][2], 32, s6.as<B>());
+  k_up_add<<<nb(V[1] * 4), 256, 0, s>>>(a5.as<B>(), a2.as<B>(), g[1][0], g[1][1], g[1][2], 32, s6.as<B>());
   PG_TRY(conv(s, 5, s6.as<B>(), a6.as<B>(), nullptr));
-  k_up_add<<<nb(V[0] * 16), 256, 0, s>>>(a6.as<B>(), a1.as<B>(), g[0][0], g[0][1], g[0][2], 16, s7.as<B>());
+  k_up_add<<<nb(V[0] * 2), 256, 0, s>>>(a6.as<B>(), a1.as<B>(), g[0][0], g[0][1], g[0][2], 16, s7.as<B>());
   PG_TRY(conv(s, 6, s7.as<B>(), nullptr, y.as<float>()));
   PG_CUDA(cudaGetLastError());
   return Status{};
@@ -793,8 +824,8 @@ Status Net::load_input(cudaStream_t s, const T* r, int64_t E) {
                                     nodes8.as<float>(), npart.as<double>());
   const int64_t n_in = (int64_t)std::max(gx - 2, 0) * std::max(gy - 2, 0) * std::max(gz - 2, 0);
   k_hx_scale<<<1, 256, 0, s>>>(npart.as<double>(), (int)blocks, n_in, scal.as<float>());
-  k_hx_pack<<<nb(V[0] * kIn), 256, 0, s>>>(nodes8.as<float>(), feat.as<float>(), V[0], scal.as<float>(),
-                                           x0.as<__nv_bfloat16>());
+  k_hx_pack<<<nb(V[0]), 256, 0, s>>>(nodes8.as<float>(), feat.as<float>(), V[0], scal.as<float>(),
+                                     x0.as<__nv_bfloat16>());
   PG_CUDA(cudaGetLastError());
   return Status{};
 }

@@ -109,7 +109,7 @@ def solve_samples(ctx: api.Context, samples: int, restart: int = 50, max_cycles:
 
 
 def train(n: int = 32, models: int = 200, epochs: int = 2, lr: float = 1e-3, seed: int = 0, samples_per_model: int = 8,
-          params: np.ndarray | None = None, log=None, lr_final: float | None = None):
+          params: np.ndarray | None = None, log=None, lr_final: float | None = None, max_cycles: int = 400):
     """Train the network on residuals of the plain solver over random block models on one n^3 cube
     lattice (models differ in conductivity and frequency only, so the mesh is built once).
     The learning rate decays geometrically from lr to lr_final (default lr / 10) over the epochs.
@@ -124,9 +124,11 @@ def train(n: int = 32, models: int = 200, epochs: int = 2, lr: float = 1e-3, see
     for m in range(models):
         mdl = random_block_model(n, seed * 100000 + m)
         ctx.assemble(mdl.freq, mdl.sigma, mdl.sigma_p, mdl.sources)
-        its, cyc = solve_samples(ctx, samples_per_model)
+        its, cyc = solve_samples(ctx, samples_per_model, max_cycles=max_cycles)
         cycles.append(cyc)
         data.append((mdl.freq, mdl.sigma, mdl.sigma_p, mdl.sources, its))
+        if log and (m + 1) % 200 == 0:
+            log("data: %d models, %.0f s" % (m + 1, time.time() - t0))
     gen_s = time.time() - t0
     history = []
     p = init_params(seed) if params is None else params
