@@ -106,11 +106,25 @@ def upsample_backward(dy: np.ndarray, coarse_shape) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- the network
-# name: (in channels, out channels, relu).  Level 0 is the (N+1)^3 node grid, levels 1..3 are
-# successive poolings.  Decoder levels add the upsampled coarse features to the encoder's.
+# name: (in channels, out channels, relu).  Level 0 is the node grid, level l + 1 the pooling of
+# level l; the number of levels grows with the grid (levels()): poolings continue until the
+# coarsest grid has at most 3 nodes along every axis (at least 3 levels), so the coarsest level
+# spans the whole domain at every resolution.  c1 / c7 act on level 0, c2 / c6 on level 1, c4 on
+# the coarsest level, and c3 / c5 on every level in between (weights shared between those
+# levels, as a multigrid cycle uses one smoother on every level).  Decoder levels add the
+# upsampled coarse features to the encoder's.
 LAYERS = [("c1", 16, 16, True), ("c2", 16, 32, True), ("c3", 32, 32, True), ("c4", 32, 32, True),
           ("c5", 32, 32, True), ("c6", 32, 16, True), ("c7", 16, 16, False)]
 N_IN, N_OUT = 16, 14
+
+
+def levels(shape) -> int:
+    """Number of levels for a grid of `shape` nodes (any axis order)."""
+    dims, L = list(shape[:3]), 1
+    while max(dims) > 3:
+        dims = [(d + 1) // 2 for d in dims]
+        L += 1
+    return max(3, L)
 
 
 def init_params(seed: int = 0, scale: float = 1.0) -> dict:
@@ -126,51 +140,52 @@ def init_params(seed: int = 0, scale: float = 1.0) -> dict:
 
 
 def forward(p: dict, x: np.ndarray):
-    """x [Z,Y,X,16] -> (y [Z,Y,X,16], cache).  Channels 14, 15 of y are zero."""
+    """x [Z,Y,X,16] -> (y [Z,Y,X,16], cache)."""
     relu = lambda a: np.maximum(a, 0.0)
-    a1 = relu(conv3d(x, p["c1.W"], p["c1.b"]))
-    p1 = pool(a1)
-    a2 = relu(conv3d(p1, p["c2.W"], p["c2.b"]))
-    p2 = pool(a2)
-    a3 = relu(conv3d(p2, p["c3.W"], p["c3.b"]))
-    p3 = pool(a3)
-    a4 = relu(conv3d(p3, p["c4.W"], p["c4.b"]))
-    s5 = upsample(a4, a3.shape) + a3
-    a5 = relu(conv3d(s5, p["c5.W"], p["c5.b"]))
-    s6 = upsample(a5, a2.shape) + a2
-    a6 = relu(conv3d(s6, p["c6.W"], p["c6.b"]))
-    s7 = upsample(a6, a1.shape) + a1
-    y = conv3d(s7, p["c7.W"], p["c7.b"])
-    cache = dict(x=x, a1=a1, p1=p1, a2=a2, p2=p2, a3=a3, p3=p3, a4=a4, s5=s5, a5=a5, s6=s6, a6=a6, s7=s7)
-    return y, cache
+    L = levels(x.shape)
+    conv = lambda name, a: conv3d(a, p[name + ".W"], p[name + ".b"])
+    enc_name = lambda l: "c1" if l == 0 else "c2" if l == 1 else "c4" if l == L - 1 else "c3"
+    dec_name = lambda l: "c7" if l == 0 else "c6" if l == 1 else "c5"
+    q, e = {0: x}, {}
+    for l in range(L):
+        if l > 0:
+            q[l] = pool(e[l - 1])
+        e[l] = relu(conv(enc_name(l), q[l]))
+    d, sk = {L - 1: e[L - 1]}, {}
+    for l in range(L - 2, -1, -1):
+        sk[l] = upsample(d[l + 1], e[l].shape) + e[l]
+        out = conv(dec_name(l), sk[l])
+        d[l] = out if l == 0 else relu(out)
+    return d[0], dict(L=L, q=q, e=e, d=d, s=sk)
 
 
 def backward(p: dict, cache: dict, dy: np.ndarray) -> dict:
-    """Gradients of sum(dy * forward(p, x)) with respect to every parameter."""
-    c = cache
-    g = {}
-    ds7, g["c7.W"], g["c7.b"] = conv3d_backward(c["s7"], p["c7.W"], dy)
-    da1 = ds7.copy()
-    da6 = upsample_backward(ds7, c["a6"].shape)
-    dz6 = da6 * (c["a6"] > 0)
-    ds6, g["c6.W"], g["c6.b"] = conv3d_backward(c["s6"], p["c6.W"], dz6)
-    da2 = ds6.copy()
-    da5 = upsample_backward(ds6, c["a5"].shape)
-    dz5 = da5 * (c["a5"] > 0)
-    ds5, g["c5.W"], g["c5.b"] = conv3d_backward(c["s5"], p["c5.W"], dz5)
-    da3 = ds5.copy()
-    da4 = upsample_backward(ds5, c["a4"].shape)
-    dz4 = da4 * (c["a4"] > 0)
-    dp3, g["c4.W"], g["c4.b"] = conv3d_backward(c["p3"], p["c4.W"], dz4)
-    da3 += pool_backward(dp3, c["a3"].shape)
-    dz3 = da3 * (c["a3"] > 0)
-    dp2, g["c3.W"], g["c3.b"] = conv3d_backward(c["p2"], p["c3.W"], dz3)
-    da2 += pool_backward(dp2, c["a2"].shape)
-    dz2 = da2 * (c["a2"] > 0)
-    dp1, g["c2.W"], g["c2.b"] = conv3d_backward(c["p1"], p["c2.W"], dz2)
-    da1 += pool_backward(dp1, c["a1"].shape)
-    dz1 = da1 * (c["a1"] > 0)
-    _, g["c1.W"], g["c1.b"] = conv3d_backward(c["x"], p["c1.W"], dz1)
+    """Gradients of sum(dy * forward(p, x)) with respect to every parameter (shared weights
+    collect the gradients of every level they act on)."""
+    L, q, e, d, sk = cache["L"], cache["q"], cache["e"], cache["d"], cache["s"]
+    enc_name = lambda l: "c1" if l == 0 else "c2" if l == 1 else "c4" if l == L - 1 else "c3"
+    dec_name = lambda l: "c7" if l == 0 else "c6" if l == 1 else "c5"
+    g = {k: np.zeros_like(v) for k, v in p.items()}
+
+    def conv_back(name, inp, dz):
+        dx, dW, db = conv3d_backward(inp, p[name + ".W"], dz)
+        g[name + ".W"] += dW
+        g[name + ".b"] += db
+        return dx
+
+    de = {}
+    dd = dy                                   # gradient at d[0] = y (no ReLU on the output)
+    for l in range(0, L - 1):
+        dz = dd if l == 0 else dd * (d[l] > 0)
+        ds = conv_back(dec_name(l), sk[l], dz)
+        de[l] = ds.copy()                     # skip path into e[l]
+        dd = upsample_backward(ds, d[l + 1].shape)
+    de[L - 1] = dd                            # d[L-1] = e[L-1]
+    for l in range(L - 1, -1, -1):
+        dz = de[l] * (e[l] > 0)
+        dq = conv_back(enc_name(l), q[l], dz)
+        if l > 0:
+            de[l - 1] += pool_backward(dq, e[l - 1].shape)
     return g
 
 

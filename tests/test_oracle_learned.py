@@ -233,3 +233,32 @@ def test_hx_loss_gradient_by_finite_differences_and_exact_auxiliary_solves():
     zj = r / diag
     ang = lambda zz: 1 - abs(np.vdot(r, A @ zz)) ** 2 / (np.vdot(A @ zz, A @ zz).real * np.vdot(r, r).real)
     assert ang(z) < ang(zj)
+
+
+def test_depth_grows_with_the_grid_and_shared_weights_get_every_levels_gradient():
+    """Poolings continue until the coarsest grid has at most 3 nodes per axis: 33 nodes a side gives
+    33, 17, 9, 5, 3 (five levels), 65 gives six.  On a five-level grid c3 and c5 act on two levels
+    each; central finite differences of the whole network's loss check that their gradients
+    collect both uses."""
+    assert [L.levels((g, g, g)) for g in (5, 7, 13, 33, 65, 97)] == [3, 3, 4, 5, 6, 7]
+    assert L.levels((65, 9, 5)) == 6
+    rng = np.random.default_rng(7)
+    p = L.init_params(seed=4)
+    x = rng.normal(size=(5, 6, 33, L.N_IN))
+    t = rng.normal(size=(5, 6, 33, 16))
+    _, dy, cache = L.loss(p, x, t)
+    assert cache["L"] == 5
+    g = L.backward(p, cache, dy)
+    for name in ["c3.W", "c5.W", "c4.W", "c3.b", "c5.b", "c1.W"]:
+        flat = p[name].reshape(-1)
+        for idx in rng.choice(flat.size, 3, replace=False):
+            old = flat[idx]
+            eps = 1e-5 * max(1.0, abs(old))
+            flat[idx] = old + eps
+            lp, _, _ = L.loss(p, x, t)
+            flat[idx] = old - eps
+            lm, _, _ = L.loss(p, x, t)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * eps)
+            an = g[name].reshape(-1)[idx]
+            assert abs(fd - an) <= 1e-6 * max(1e-8, abs(fd)) + 1e-10, (name, idx, fd, an)
