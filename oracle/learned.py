@@ -275,18 +275,25 @@ def angle_loss(y_grid: np.ndarray, r: np.ndarray, slot: np.ndarray, spmv, diag: 
 AUX_IN = 8
 
 
-def interior_nodes(n: int) -> np.ndarray:
-    """Nodes of an (n+1)^3 lattice off the outer boundary (bool [(n+1)^3], node i + (n+1)(j + (n+1)k))."""
-    s = n + 1
-    ijk = np.stack(np.meshgrid(np.arange(s), np.arange(s), np.arange(s), indexing="ij"), -1)
-    inner = np.all((ijk >= 1) & (ijk <= n - 1), axis=-1)     # [i, j, k]
-    return inner.transpose(2, 1, 0).reshape(-1)               # flat index i + s (j + s k)
+def _cells(n):
+    return (n, n, n) if np.isscalar(n) else tuple(int(v) for v in n)
 
 
-def aux_operators(edges: np.ndarray, nodes: np.ndarray, n: int):
-    """(G [E x V], Pi [E x 3V]) as scipy CSR matrices; columns of boundary nodes are empty."""
+def interior_nodes(n) -> np.ndarray:
+    """Nodes of a lattice of n = (nx, ny, nz) cells (or n^3) off the outer boundary: bool over the
+    (nx+1)(ny+1)(nz+1) nodes, node i + (nx+1)(j + (ny+1) k)."""
+    nx, ny, nz = _cells(n)
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    inner = (i >= 1) & (i <= nx - 1) & (j >= 1) & (j <= ny - 1) & (k >= 1) & (k <= nz - 1)
+    return inner.reshape(-1)
+
+
+def aux_operators(edges: np.ndarray, nodes: np.ndarray, n):
+    """(G [E x V], Pi [E x 3V]) as scipy CSR matrices for a lattice of n = (nx, ny, nz) cells (or
+    n^3); columns of boundary nodes are empty."""
     import scipy.sparse as sp
-    E, V = edges.shape[0], (n + 1) ** 3
+    nx, ny, nz = _cells(n)
+    E, V = edges.shape[0], (nx + 1) * (ny + 1) * (nz + 1)
     inner = interior_nodes(n)
     lo, hi = edges[:, 0].astype(np.int64), edges[:, 1].astype(np.int64)
     t = nodes[hi] - nodes[lo]
