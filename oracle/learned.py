@@ -118,6 +118,14 @@ LAYERS = [("c1", 16, 16, True), ("c2", 16, 32, True), ("c3", 32, 32, True), ("c4
 N_IN, N_OUT = 16, 14
 
 
+def bf16(a: np.ndarray) -> np.ndarray:
+    """Round to the nearest bfloat16 (ties to even), through float32, returned as float64: the
+    storage format of the network's activations, gradients and weights on the GPU."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 def levels(shape) -> int:
     """Number of levels for a grid of `shape` nodes (any axis order)."""
     dims, L = list(shape[:3]), 1
@@ -139,53 +147,58 @@ def init_params(seed: int = 0, scale: float = 1.0) -> dict:
     return p
 
 
-def forward(p: dict, x: np.ndarray):
-    """x [Z,Y,X,16] -> (y [Z,Y,X,16], cache)."""
+def forward(p: dict, x: np.ndarray, round_bf16: bool = False):
+    """x [Z,Y,X,16] -> (y [Z,Y,X,16], cache).  With round_bf16 the weights and every stored
+    activation (encoder inputs and outputs, decoder inputs and hidden outputs) are rounded to
+    bfloat16 where the GPU kernels store them; arithmetic stays FP64."""
     relu = lambda a: np.maximum(a, 0.0)
+    rnd = bf16 if round_bf16 else (lambda a: a)
     L = levels(x.shape)
-    conv = lambda name, a: conv3d(a, p[name + ".W"], p[name + ".b"])
+    conv = lambda name, a: conv3d(a, rnd(p[name + ".W"]), p[name + ".b"])
     enc_name = lambda l: "c1" if l == 0 else "c2" if l == 1 else "c4" if l == L - 1 else "c3"
     dec_name = lambda l: "c7" if l == 0 else "c6" if l == 1 else "c5"
-    q, e = {0: x}, {}
+    q, e = {0: rnd(x)}, {}
     for l in range(L):
         if l > 0:
-            q[l] = pool(e[l - 1])
-        e[l] = relu(conv(enc_name(l), q[l]))
+            q[l] = rnd(pool(e[l - 1]))
+        e[l] = rnd(relu(conv(enc_name(l), q[l])))
     d, sk = {L - 1: e[L - 1]}, {}
     for l in range(L - 2, -1, -1):
-        sk[l] = upsample(d[l + 1], e[l].shape) + e[l]
+        sk[l] = rnd(upsample(d[l + 1], e[l].shape) + e[l])
         out = conv(dec_name(l), sk[l])
-        d[l] = out if l == 0 else relu(out)
-    return d[0], dict(L=L, q=q, e=e, d=d, s=sk)
+        d[l] = out if l == 0 else rnd(relu(out))
+    return d[0], dict(L=L, q=q, e=e, d=d, s=sk, round_bf16=round_bf16)
 
 
 def backward(p: dict, cache: dict, dy: np.ndarray) -> dict:
     """Gradients of sum(dy * forward(p, x)) with respect to every parameter (shared weights
-    collect the gradients of every level they act on)."""
+    collect the gradients of every level they act on).  When the forward pass rounded to
+    bfloat16, dy and every stored gradient tensor are rounded where the GPU stores them."""
     L, q, e, d, sk = cache["L"], cache["q"], cache["e"], cache["d"], cache["s"]
+    rnd = bf16 if cache.get("round_bf16") else (lambda a: a)
     enc_name = lambda l: "c1" if l == 0 else "c2" if l == 1 else "c4" if l == L - 1 else "c3"
     dec_name = lambda l: "c7" if l == 0 else "c6" if l == 1 else "c5"
     g = {k: np.zeros_like(v) for k, v in p.items()}
 
     def conv_back(name, inp, dz):
-        dx, dW, db = conv3d_backward(inp, p[name + ".W"], dz)
+        dx, dW, db = conv3d_backward(inp, rnd(p[name + ".W"]), dz)
         g[name + ".W"] += dW
         g[name + ".b"] += db
-        return dx
+        return rnd(dx)
 
     de = {}
-    dd = dy                                   # gradient at d[0] = y (no ReLU on the output)
+    dd = rnd(dy)                              # gradient at d[0] = y (no ReLU on the output)
     for l in range(0, L - 1):
         dz = dd if l == 0 else dd * (d[l] > 0)
         ds = conv_back(dec_name(l), sk[l], dz)
         de[l] = ds.copy()                     # skip path into e[l]
-        dd = upsample_backward(ds, d[l + 1].shape)
+        dd = rnd(upsample_backward(ds, d[l + 1].shape))
     de[L - 1] = dd                            # d[L-1] = e[L-1]
     for l in range(L - 1, -1, -1):
         dz = de[l] * (e[l] > 0)
         dq = conv_back(enc_name(l), q[l], dz)
         if l > 0:
-            de[l - 1] += pool_backward(dq, e[l - 1].shape)
+            de[l - 1] = rnd(de[l - 1] + pool_backward(dq, e[l - 1].shape))
     return g
 
 

@@ -262,3 +262,20 @@ def test_depth_grows_with_the_grid_and_shared_weights_get_every_levels_gradient(
             fd = (lp - lm) / (2 * eps)
             an = g[name].reshape(-1)[idx]
             assert abs(fd - an) <= 1e-6 * max(1e-8, abs(fd)) + 1e-10, (name, idx, fd, an)
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    """Values of the bfloat16 grid (8 significand bits) stay, halfway cases go to the even
+    neighbour, others to the nearest; the rounding matches torch's float -> bfloat16 conversion."""
+    eps = 2.0 ** -7                         # spacing of bfloat16 in [1, 2)
+    v = np.array([1.0, 1.0 + eps, 1.0 + eps / 2, 1.0 + 3 * eps / 2, 1.0 + 0.3 * eps, -2.5, 3.0e38, 1e-39])
+    out = L.bf16(v)
+    assert out[0] == 1.0 and out[1] == 1.0 + eps
+    assert out[2] == 1.0                    # tie -> even (1.0)
+    assert out[3] == 1.0 + 2 * eps          # tie -> even (1 + 2 eps)
+    assert out[4] == 1.0 and out[5] == -2.5
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=1000) * 10.0 ** rng.uniform(-20, 20, 1000)
+    ref = torch.as_tensor(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(L.bf16(x), ref)
