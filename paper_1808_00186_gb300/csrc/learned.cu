@@ -634,17 +634,18 @@ Status Net::init(petgem_ctx* c, int nx_, int ny_, int nz_) {
   g[0][0] = nx + 1;
   g[0][1] = ny + 1;
   g[0][2] = nz + 1;
-  for (int l = 1; l < 4; ++l)
+  nlev = net_levels(g[0][0], g[0][1], g[0][2]);
+  if (nlev > kMaxLevels) return Status{PETGEM_ERR_UNSUPPORTED, "learned network: grid too large"};
+  for (int l = 1; l < nlev; ++l)
     for (int a = 0; a < 3; ++a) g[l][a] = (g[l - 1][a] + 1) / 2;
-  for (int l = 0; l < 4; ++l) V[l] = (int64_t)g[l][0] * g[l][1] * g[l][2];
-  const int spec[7][4] = {{16, 16, 1, 0}, {16, 32, 1, 1}, {32, 32, 1, 2}, {32, 32, 1, 3},
-                          {32, 32, 1, 2}, {32, 16, 1, 1}, {16, 16, 0, 0}};  // cin, cout, relu, level
+  for (int l = 0; l < nlev; ++l) V[l] = (int64_t)g[l][0] * g[l][1] * g[l][2];
+  const int spec[7][3] = {{16, 16, 1}, {16, 32, 1}, {32, 32, 1}, {32, 32, 1},
+                          {32, 32, 1}, {32, 16, 1}, {16, 16, 0}};  // cin, cout, relu
   n_params = 0;
   for (int i = 0; i < 7; ++i) {
     L[i].cin = spec[i][0];
     L[i].cout = spec[i][1];
     L[i].relu = spec[i][2];
-    L[i].level = spec[i][3];
     L[i].w_off = n_params;
     n_params += 27 * L[i].cin * L[i].cout;
     L[i].b_off = n_params;
@@ -661,31 +662,19 @@ Status Net::init(petgem_ctx* c, int nx_, int ny_, int nz_) {
   PG_CUDA(cudaMemsetAsync(adam_m.ptr, 0, n_params * sizeof(float), s));
   PG_CUDA(cudaMemsetAsync(adam_v.ptr, 0, n_params * sizeof(float), s));
   adam_t = 0;
-  // activations (BF16) by level
+  // activations and their gradients (BF16) by level
   auto act = [&](DevBuf& b, int lvl, int ch) { return b.reserve((size_t)V[lvl] * ch * sizeof(__nv_bfloat16) + 64); };
-  PG_TRY(act(x0, 0, 16));
-  PG_TRY(act(a1, 0, 16));
-  PG_TRY(act(p1, 1, 16));
-  PG_TRY(act(a2, 1, 32));
-  PG_TRY(act(p2, 2, 32));
-  PG_TRY(act(a3, 2, 32));
-  PG_TRY(act(p3, 3, 32));
-  PG_TRY(act(a4, 3, 32));
-  PG_TRY(act(s5, 2, 32));
-  PG_TRY(act(a5, 2, 32));
-  PG_TRY(act(s6, 1, 32));
-  PG_TRY(act(a6, 1, 16));
-  PG_TRY(act(s7, 0, 16));
-  PG_TRY(act(dy, 0, 16));
-  PG_TRY(act(ds7, 0, 16));
-  PG_TRY(act(da6, 1, 16));
-  PG_TRY(act(ds6, 1, 32));
-  PG_TRY(act(da5, 2, 32));
-  PG_TRY(act(ds5, 2, 32));
-  PG_TRY(act(da4, 3, 32));
-  PG_TRY(act(dp3, 3, 32));
-  PG_TRY(act(dp2, 2, 32));
-  PG_TRY(act(dp1, 1, 16));
+  for (int l = 0; l < nlev; ++l) {
+    PG_TRY(act(q[l], l, ch_q(l)));
+    PG_TRY(act(e[l], l, ch_e(l)));
+    PG_TRY(act(dd[l], l, l == 0 ? 16 : (l == nlev - 1 ? ch_e(l) : ch_d(l))));
+    if (l < nlev - 1) {
+      PG_TRY(act(sk[l], l, ch_e(l)));
+      PG_TRY(act(ds[l], l, ch_e(l)));
+      if (l > 0) PG_TRY(act(d[l], l, ch_d(l)));
+    }
+    if (l > 0) PG_TRY(act(dq[l], l, ch_q(l)));
+  }
   PG_TRY(y.reserve((size_t)V[0] * 16 * sizeof(float)));
   PG_TRY(feat.reserve((size_t)V[0] * 2 * sizeof(float)));
   PG_TRY(scal.reserve(16 * sizeof(float)));
@@ -697,6 +686,8 @@ Status Net::init(petgem_ctx* c, int nx_, int ny_, int nz_) {
   const int splits = wgrad_splits(V[0]);
   PG_TRY(wpart.reserve((size_t)splits * 27 * 32 * 32 * sizeof(float)));
   PG_CUDA(cudaMemsetAsync(feat.ptr, 0, (size_t)V[0] * 2 * sizeof(float), s));
+  geom_version = -1;
+  aux_version = -1;
   ready = true;
   return Status{};
 }
@@ -710,42 +701,45 @@ Status Net::pack_weights(cudaStream_t s) {
   return Status{};
 }
 
-Status Net::conv(cudaStream_t s, int i, const __nv_bfloat16* in, __nv_bfloat16* out, float* outf) {
-  const int* gg = g[L[i].level];
+Status Net::conv(cudaStream_t s, int i, int lvl, const __nv_bfloat16* in, __nv_bfloat16* out, float* outf) {
+  const int* gg = g[lvl];
   // timed (when profiling) with its floating-point operations in place of bytes
   KernelTimer kt(ctx, "conv3d_fwd", 2.0 * 27.0 * L[i].cin * L[i].cout * (double)gg[0] * gg[1] * gg[2]);
   return conv3d(s, gg[0], gg[1], gg[2], L[i].cin, L[i].cout, in, wb.as<__nv_bfloat16>() + L[i].w_off,
                 params.as<float>() + L[i].b_off, L[i].relu != 0, out, outf, err.as<int>());
 }
 
-// Input grid x0 (BF16 [V0][16]) -> y (FP32 [V0][16]).
+// Input grid q[0] (BF16 [V0][16]) -> y (FP32 [V0][16]): encoder down to the coarsest level, then
+// decoder levels that add the upsampled coarse output to the encoder's.
 Status Net::forward(cudaStream_t s) {
   using B = __nv_bfloat16;
-  PG_TRY(conv(s, 0, x0.as<B>(), a1.as<B>(), nullptr));
-  k_pool<<<nb(V[1] * 2), 256, 0, s>>>(a1.as<B>(), g[0][0], g[0][1], g[0][2], 16, p1.as<B>());
-  PG_TRY(conv(s, 1, p1.as<B>(), a2.as<B>(), nullptr));
-  k_pool<<<nb(V[2] * 4), 256, 0, s>>>(a2.as<B>(), g[1][0], g[1][1], g[1][2], 32, p2.as<B>());
-  PG_TRY(conv(s, 2, p2.as<B>(), a3.as<B>(), nullptr));
-  k_pool<<<nb(V[3] * 4), 256, 0, s>>>(a3.as<B>(), g[2][0], g[2][1], g[2][2], 32, p3.as<B>());
-  PG_TRY(conv(s, 3, p3.as<B>(), a4.as<B>(), nullptr));
-  k_up_add<<<nb(V[2] * 4), 256, 0, s>>>(a4.as<B>(), a3.as<B>(), g[2][0], g[2][1], g[2][2], 32, s5.as<B>());
-  PG_TRY(conv(s, 4, s5.as<B>(), a5.as<B>(), nullptr));
-  k_up_add<<<nb(V[1] * 4), 256, 0, s>>>(a5.as<B>(), a2.as<B>(), g[1][0], g[1][1], g[1][2], 32, s6.as<B>());
-  PG_TRY(conv(s, 5, s6.as<B>(), a6.as<B>(), nullptr));
-  k_up_add<<<nb(V[0] * 2), 256, 0, s>>>(a6.as<B>(), a1.as<B>(), g[0][0], g[0][1], g[0][2], 16, s7.as<B>());
-  PG_TRY(conv(s, 6, s7.as<B>(), nullptr, y.as<float>()));
+  for (int l = 0; l < nlev; ++l) {
+    if (l > 0)
+      k_pool<<<nb(V[l] * ch_e(l - 1) / 8), 256, 0, s>>>(e[l - 1].as<B>(), g[l - 1][0], g[l - 1][1], g[l - 1][2],
+                                                        ch_e(l - 1), q[l].as<B>());
+    PG_TRY(conv(s, enc(l), l, q[l].as<B>(), e[l].as<B>(), nullptr));
+  }
+  for (int l = nlev - 2; l >= 0; --l) {
+    const B* coarse = (l + 1 == nlev - 1) ? e[l + 1].as<B>() : d[l + 1].as<B>();
+    k_up_add<<<nb(V[l] * ch_e(l) / 8), 256, 0, s>>>(coarse, e[l].as<B>(), g[l][0], g[l][1], g[l][2], ch_e(l),
+                                                    sk[l].as<B>());
+    if (l == 0)
+      PG_TRY(conv(s, dec(0), 0, sk[0].as<B>(), nullptr, y.as<float>()));
+    else
+      PG_TRY(conv(s, dec(l), l, sk[l].as<B>(), d[l].as<B>(), nullptr));
+  }
   PG_CUDA(cudaGetLastError());
   return Status{};
 }
 
-Status Net::dgrad(cudaStream_t s, int i, const __nv_bfloat16* dout, __nv_bfloat16* din) {
-  const int* gg = g[L[i].level];  // the input gradient has no bias term: zbias is all zeros
+Status Net::dgrad(cudaStream_t s, int i, int lvl, const __nv_bfloat16* dout, __nv_bfloat16* din) {
+  const int* gg = g[lvl];  // the input gradient has no bias term: zbias is all zeros
   return conv3d(s, gg[0], gg[1], gg[2], L[i].cout, L[i].cin, dout, wd.as<__nv_bfloat16>() + L[i].w_off,
                 zbias.as<float>(), false, din, nullptr, err.as<int>());
 }
 
-Status Net::wgrad(cudaStream_t s, int i, const __nv_bfloat16* in, const __nv_bfloat16* dout, bool acc) {
-  const int* gg = g[L[i].level];
+Status Net::wgrad(cudaStream_t s, int i, int lvl, const __nv_bfloat16* in, const __nv_bfloat16* dout, bool acc) {
+  const int* gg = g[lvl];
   const int64_t Vl = (int64_t)gg[0] * gg[1] * gg[2];
   PG_TRY(conv3d_wgrad(s, gg[0], gg[1], gg[2], L[i].cin, L[i].cout, in, dout, wpart.as<float>(), wgrad_splits(Vl),
                       grads.as<float>() + L[i].w_off, acc, err.as<int>()));
@@ -754,34 +748,36 @@ Status Net::wgrad(cudaStream_t s, int i, const __nv_bfloat16* in, const __nv_bfl
   return Status{};
 }
 
-// dy (BF16 [V0][16]) -> parameter gradients (accumulated when acc).
+// dd[0] (BF16 [V0][16], the gradient at y) -> parameter gradients (accumulated when acc; a
+// layer that acts on several levels collects every level's gradient).
 Status Net::backward(cudaStream_t s, bool acc) {
   using B = __nv_bfloat16;
-  PG_TRY(wgrad(s, 6, s7.as<B>(), dy.as<B>(), acc));
-  PG_TRY(dgrad(s, 6, dy.as<B>(), ds7.as<B>()));                        // = da1 (skip) part
-  k_up_bwd<<<nb(V[1] * 16), 256, 0, s>>>(ds7.as<B>(), g[0][0], g[0][1], g[0][2], 16, da6.as<B>());
-  k_relu_bwd<<<nb(V[1] * 16), 256, 0, s>>>(da6.as<B>(), a6.as<B>(), V[1] * 16);
-  PG_TRY(wgrad(s, 5, s6.as<B>(), da6.as<B>(), acc));
-  PG_TRY(dgrad(s, 5, da6.as<B>(), ds6.as<B>()));                       // = da2 part
-  k_up_bwd<<<nb(V[2] * 32), 256, 0, s>>>(ds6.as<B>(), g[1][0], g[1][1], g[1][2], 32, da5.as<B>());
-  k_relu_bwd<<<nb(V[2] * 32), 256, 0, s>>>(da5.as<B>(), a5.as<B>(), V[2] * 32);
-  PG_TRY(wgrad(s, 4, s5.as<B>(), da5.as<B>(), acc));
-  PG_TRY(dgrad(s, 4, da5.as<B>(), ds5.as<B>()));                       // = da3 part
-  k_up_bwd<<<nb(V[3] * 32), 256, 0, s>>>(ds5.as<B>(), g[2][0], g[2][1], g[2][2], 32, da4.as<B>());
-  k_relu_bwd<<<nb(V[3] * 32), 256, 0, s>>>(da4.as<B>(), a4.as<B>(), V[3] * 32);
-  PG_TRY(wgrad(s, 3, p3.as<B>(), da4.as<B>(), acc));
-  PG_TRY(dgrad(s, 3, da4.as<B>(), dp3.as<B>()));
-  k_pool_bwd_add<<<nb(V[2] * 32), 256, 0, s>>>(dp3.as<B>(), g[2][0], g[2][1], g[2][2], 32, ds5.as<B>());  // da3
-  k_relu_bwd<<<nb(V[2] * 32), 256, 0, s>>>(ds5.as<B>(), a3.as<B>(), V[2] * 32);
-  PG_TRY(wgrad(s, 2, p2.as<B>(), ds5.as<B>(), acc));
-  PG_TRY(dgrad(s, 2, ds5.as<B>(), dp2.as<B>()));
-  k_pool_bwd_add<<<nb(V[1] * 32), 256, 0, s>>>(dp2.as<B>(), g[1][0], g[1][1], g[1][2], 32, ds6.as<B>());  // da2
-  k_relu_bwd<<<nb(V[1] * 32), 256, 0, s>>>(ds6.as<B>(), a2.as<B>(), V[1] * 32);
-  PG_TRY(wgrad(s, 1, p1.as<B>(), ds6.as<B>(), acc));
-  PG_TRY(dgrad(s, 1, ds6.as<B>(), dp1.as<B>()));
-  k_pool_bwd_add<<<nb(V[0] * 16), 256, 0, s>>>(dp1.as<B>(), g[0][0], g[0][1], g[0][2], 16, ds7.as<B>());  // da1
-  k_relu_bwd<<<nb(V[0] * 16), 256, 0, s>>>(ds7.as<B>(), a1.as<B>(), V[0] * 16);
-  PG_TRY(wgrad(s, 0, x0.as<B>(), ds7.as<B>(), acc));
+  bool touched[7] = {false, false, false, false, false, false, false};
+  auto W = [&](int i, int lvl, const B* in, const B* dout) -> Status {
+    const bool a = acc || touched[i];
+    touched[i] = true;
+    return wgrad(s, i, lvl, in, dout, a);
+  };
+  // decoder, finest level first: ds[l] is the gradient at sk[l], and (skip path) at e[l]
+  for (int l = 0; l <= nlev - 2; ++l) {
+    const int ci = ch_e(l);
+    if (l > 0) k_relu_bwd<<<nb(V[l] * ch_d(l)), 256, 0, s>>>(dd[l].as<B>(), d[l].as<B>(), V[l] * ch_d(l));
+    PG_TRY(W(dec(l), l, sk[l].as<B>(), dd[l].as<B>()));
+    PG_TRY(dgrad(s, dec(l), l, dd[l].as<B>(), ds[l].as<B>()));
+    k_up_bwd<<<nb(V[l + 1] * ci), 256, 0, s>>>(ds[l].as<B>(), g[l][0], g[l][1], g[l][2], ci, dd[l + 1].as<B>());
+  }
+  // encoder, coarsest level first: the gradient at e[l] is dd[nlev-1] (bottom) or ds[l]
+  for (int l = nlev - 1; l >= 0; --l) {
+    B* de = l == nlev - 1 ? dd[l].as<B>() : ds[l].as<B>();
+    k_relu_bwd<<<nb(V[l] * ch_e(l)), 256, 0, s>>>(de, e[l].as<B>(), V[l] * ch_e(l));
+    PG_TRY(W(enc(l), l, q[l].as<B>(), de));
+    if (l > 0) {
+      PG_TRY(dgrad(s, enc(l), l, de, dq[l].as<B>()));
+      B* de_below = l - 1 == nlev - 1 ? dd[l - 1].as<B>() : ds[l - 1].as<B>();
+      k_pool_bwd_add<<<nb(V[l - 1] * ch_q(l)), 256, 0, s>>>(dq[l].as<B>(), g[l - 1][0], g[l - 1][1], g[l - 1][2],
+                                                             ch_q(l), de_below);
+    }
+  }
   PG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -825,7 +821,7 @@ Status Net::load_input(cudaStream_t s, const T* r, int64_t E) {
   const int64_t n_in = (int64_t)std::max(gx - 2, 0) * std::max(gy - 2, 0) * std::max(gz - 2, 0);
   k_hx_scale<<<1, 256, 0, s>>>(npart.as<double>(), (int)blocks, n_in, scal.as<float>());
   k_hx_pack<<<nb(V[0]), 256, 0, s>>>(nodes8.as<float>(), feat.as<float>(), V[0], scal.as<float>(),
-                                     x0.as<__nv_bfloat16>());
+                                     q[0].as<__nv_bfloat16>());
   PG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -868,7 +864,7 @@ Status Net::sample_grad(cudaStream_t s, petgem_ctx* c, const double2* r, const i
                                        c->diag.as<double2>(), gw, E, zu);
   k_hx_dy<<<nb(V[0]), 256, 0, s>>>(zu, c->diag.as<double2>(), slot_edge.as<int32_t>(), tang.as<float4>(),
                                    aux.as<float4>(), scal.as<float>(), g[0][0], g[0][1], g[0][2],
-                                   dy.as<__nv_bfloat16>());
+                                   dd[0].as<__nv_bfloat16>());
   PG_CUDA(cudaGetLastError());
   PG_TRY(backward(s, acc));
   return Status{};

@@ -8,35 +8,59 @@ namespace petgem {
 namespace nn {
 
 struct Layer {
-  int cin, cout, relu, level;
+  int cin, cout, relu;
   int64_t w_off, b_off;  // offsets into the parameter vector: W[27][cout][cin] then b[cout]
 };
+
+constexpr int kMaxLevels = 12;
+
+// Levels of a grid: poolings until the coarsest grid has at most 3 nodes per axis (at least 3).
+inline int net_levels(int gx, int gy, int gz) {
+  int L = 1;
+  while (gx > 3 || gy > 3 || gz > 3) {
+    gx = (gx + 1) / 2;
+    gy = (gy + 1) / 2;
+    gz = (gz + 1) / 2;
+    ++L;
+  }
+  return L < 3 ? 3 : L;
+}
 
 struct Net {
   petgem_ctx* ctx = nullptr;
   bool ready = false;
   int nx = 0, ny = 0, nz = 0;
-  int g[4][3];      // grid dimensions of levels 0..3
-  int64_t V[4];     // voxels per level
+  int nlev = 0;                // levels (net_levels of the node grid)
+  int g[kMaxLevels][3];        // grid dimensions per level
+  int64_t V[kMaxLevels];       // voxels per level
   Layer L[7];
   int64_t n_params = 0;
   int64_t adam_t = 0;
   DevBuf params, grads, adam_m, adam_v, wb, wd, zbias;
-  DevBuf x0, a1, p1, a2, p2, a3, p3, a4, s5, a5, s6, a6, s7, y;
-  DevBuf dy, ds7, da6, ds6, da5, ds5, da4, dp3, dp2, dp1;
-  DevBuf g32, feat, scal, loss_acc, err, wpart, rtmp, dutmp, wtmp, gtmp, dvec;
+  // per level l: q = encoder input (q[0] = the network input), e = encoder output, sk = decoder
+  // input (upsampled coarse + e), d = decoder output (d[0] is y, FP32; d[nlev-1] is e[nlev-1]);
+  // dd = gradient at d (dd[0] = dy), ds = gradient at sk, dq = gradient at q
+  DevBuf q[kMaxLevels], e[kMaxLevels], sk[kMaxLevels], d[kMaxLevels];
+  DevBuf dd[kMaxLevels], ds[kMaxLevels], dq[kMaxLevels];
+  DevBuf y;
+  DevBuf feat, scal, loss_acc, err, wpart, rtmp, dutmp, wtmp, gtmp, dvec;
   // auxiliary spaces on the lattice: edge of every slot (node * 7 + class, -1 if none), the
   // slot's unit tangent and inverse length, per-node scales (sg, sp_x, sp_y, sp_z), the gathered
   // node fields [V0][8] and per-block partial sums
   DevBuf slot_edge, tang, aux, nodes8, npart;
   int64_t aux_version = -1;    // assembly the scales belong to
   int64_t geom_version = -1;   // mesh the slot map and tangents belong to
-
   Status init(petgem_ctx* c, int nx, int ny, int nz);
   Status pack_weights(cudaStream_t s);
-  Status conv(cudaStream_t s, int i, const __nv_bfloat16* in, __nv_bfloat16* out, float* outf);
-  Status dgrad(cudaStream_t s, int i, const __nv_bfloat16* dout, __nv_bfloat16* din);
-  Status wgrad(cudaStream_t s, int i, const __nv_bfloat16* in, const __nv_bfloat16* dout, bool acc);
+  // layer i on level lvl
+  Status conv(cudaStream_t s, int i, int lvl, const __nv_bfloat16* in, __nv_bfloat16* out, float* outf);
+  Status dgrad(cudaStream_t s, int i, int lvl, const __nv_bfloat16* dout, __nv_bfloat16* din);
+  Status wgrad(cudaStream_t s, int i, int lvl, const __nv_bfloat16* in, const __nv_bfloat16* dout, bool acc);
+  int enc(int l) const { return l == 0 ? 0 : l == 1 ? 1 : l == nlev - 1 ? 3 : 2; }  // c1, c2, c4, c3
+  int dec(int l) const { return l == 0 ? 6 : l == 1 ? 5 : 4; }                        // c7, c6, c5
+  static int ch_e(int l) { return l == 0 ? 16 : 32; }
+  static int ch_q(int l) { return l <= 1 ? 16 : 32; }
+  static int ch_d(int l) { return l == 1 ? 16 : 32; }
   Status forward(cudaStream_t s);
   Status backward(cudaStream_t s, bool acc);
   Status prepare_aux(petgem_ctx* c);

@@ -82,19 +82,34 @@ def lattice_case(n, seed):
     return m, ref
 
 
-def oracle_maps(m, ref, n):
-    """The auxiliary-space maps, scales, features and the system matrix of the oracle's assembly."""
+def oracle_maps(m, ref, cells):
+    """The auxiliary-space maps, scales, features and the system matrix of the oracle's assembly
+    on a lattice of cells = (nx, ny, nz)."""
     import scipy.sparse as sp
+    nx, ny, nz = (cells, cells, cells) if np.isscalar(cells) else cells
     rp, col, val, b = ref.system()
     edges, _, _, _ = ref.topology()
     A = sp.csr_matrix((val, col, rp), shape=(ref.n_edges, ref.n_edges))
-    G, Pi = OL.aux_operators(edges, m.mesh.nodes, n)
+    G, Pi = OL.aux_operators(edges, m.mesh.nodes, (nx, ny, nz))
     sg, sp_ = OL.aux_scales(G, Pi, A)
     nd = m.mesh.nodes
-    h = (abs(nd[1, 0] - nd[0, 0]) * abs(nd[n + 1, 1] - nd[0, 1]) * abs(nd[(n + 1) ** 2, 2] - nd[0, 2])) ** (1 / 3)
-    feat = OL.node_features(m.sigma, (n, n, n), m.sigma_p, m.freq, h)
+    h = (abs(nd[1, 0] - nd[0, 0]) * abs(nd[nx + 1, 1] - nd[0, 1]) * abs(nd[(nx + 1) * (ny + 1), 2] - nd[0, 2])) ** (1 / 3)
+    feat = OL.node_features(m.sigma, (nx, ny, nz), m.sigma_p, m.freq, h)
     return A, b, G, Pi, sg, sp_, feat
 
+
+def anisotropic_case(cells=(32, 4, 4), seed=3):
+    """A jittered 32 x 4 x 4 lattice (five network levels along x, so c3 and c5 act on two levels
+    each) with a resistive half and a conductive block, 1.5 Hz."""
+    nx, ny, nz = cells
+    xs = [np.linspace(-1000.0, 1000.0, nx + 1), np.linspace(-250.0, 250.0, ny + 1), np.linspace(-250.0, 250.0, nz + 1)]
+    mesh = synth.kuhn_mesh_axes(xs, jitter=0.1, seed=seed)
+    cen = mesh.centroids()
+    sigma = np.where(cen[:, 0] > 300.0, 0.05, 1.0)
+    sigma[(cen[:, 0] < -400.0) & (cen[:, 2] < 0.0)] = 4.0
+    m = synth.Model("aniso", mesh, sigma, 1.0, 1.5, [synth.Dipole(1.0, 1.0, 1.0, 0, 1.0)], np.zeros((1, 3)))
+    ref = oracle.System(mesh.nodes, mesh.tets, m.sigma, m.sigma_p, m.freq, synth.sources_array(m.sources))
+    return m, ref
 
 def perturbed_iterate(xstar, seed):
     rng = np.random.default_rng(seed)
@@ -134,17 +149,19 @@ def test_auxiliary_space_maps_match_oracle():
 
 
 def test_network_forward_loss_and_gradients_match_oracle():
-    n = 6
-    m, ref = lattice_case(n, 11)
-    A, b, G, Pi, sg, sp_, feat = oracle_maps(m, ref, n)
-    xstar = ref.solve(tol=1e-12)[0][0]
-    x = perturbed_iterate(xstar, 1)
+    cells = (32, 4, 4)
+    m, ref = anisotropic_case(cells)
+    A, b, G, Pi, sg, sp_, feat = oracle_maps(m, ref, cells)
+    assert OL.levels((cells[2] + 1, cells[1] + 1, cells[0] + 1)) == 5
+    rng = np.random.default_rng(1)
+    x = (rng.normal(size=ref.n_edges) + 1j * rng.normal(size=ref.n_edges)) * 1e-9
+    x[ref.topology()[3] == 1] = 0.0
     p = PL.init_params(5)
     lay, _ = PL.layout()
     with api.Context(0) as ctx:
         ctx.mesh(m.mesh.nodes, m.mesh.tets)
         ctx.assemble(m.freq, m.sigma, m.sigma_p, m.sources)
-        api.petgem_learned_create(ctx.h, n, n, n)
+        api.petgem_learned_create(ctx.h, *cells)
         api.petgem_learned_params(ctx.h, set_params=p)
         loss = api.petgem_learned_train_step(ctx.h, ctx.tensor(x[None, :]), 1e-12)
         g_gpu = api.petgem_learned_params(ctx.h, grad=True)
@@ -155,19 +172,25 @@ def test_network_forward_loss_and_gradients_match_oracle():
     r = b[0] - ref.spmv(x)
     xin, s = OL.hx_input(r, G, Pi, sg, sp_, feat)
     P = PL.unflatten(p)
-    shape = (n + 1, n + 1, n + 1)
-    y, cache = OL.forward(P, xin.reshape(*shape, 16))
+    shape = (cells[2] + 1, cells[1] + 1, cells[0] + 1)
+    # the oracle rounds weights, activations and gradients to bfloat16 where the kernels store
+    # them, so both sides take the same rounding steps; what remains is FP32 against FP64
+    # accumulation, which can flip single roundings
+    y, cache = OL.forward(P, xin.reshape(*shape, 16), round_bf16=True)
     L, gy = OL.hx_angle_loss(y.reshape(-1, 16), r, s, G, Pi, sg, sp_, A.diagonal(), ref.spmv)
     gref = OL.backward(P, cache, gy.reshape(*shape, 16))
-    assert abs(loss - L) <= 5e-2 * L
+    assert abs(loss - L) <= 1e-3 * L
     for name, w, bb, ci, co in lay:
-        gw = g_gpu[w:w + 27 * co * ci].reshape(27, co, ci)
-        assert np.linalg.norm(gw - gref[name + ".W"]) <= 5e-2 * np.linalg.norm(gref[name + ".W"]) + 1e-12, name
-        gb = g_gpu[bb:bb + co]
-        assert np.linalg.norm(gb - gref[name + ".b"]) <= 5e-2 * np.linalg.norm(gref[name + ".b"]) + 1e-12, name
+        for got, ref_ in ((g_gpu[w:w + 27 * co * ci].reshape(27, co, ci), gref[name + ".W"]),
+                          (g_gpu[bb:bb + co], gref[name + ".b"])):
+            got, ref_ = got.reshape(-1).astype(np.float64), ref_.reshape(-1)
+            err = np.linalg.norm(got - ref_) / max(np.linalg.norm(ref_), 1e-30)
+            cos = got @ ref_ / max(np.linalg.norm(got) * np.linalg.norm(ref_), 1e-300)
+            print("%s: normwise %.3f cosine %.5f" % (name, err, cos))
+            assert err <= 2e-2 and cos >= 0.9998, name
     # apply: z = D^-1 r + G phi + Pi w from the network's output
     zr = OL.hx_direction(y.reshape(-1, 16), r, s, G, Pi, sg, sp_, A.diagonal())
-    assert np.linalg.norm(z - zr) <= 5e-2 * np.linalg.norm(zr - r / A.diagonal())
+    assert np.linalg.norm(z - zr) <= 1e-3 * np.linalg.norm(zr - r / A.diagonal())
 
 
 def test_learned_fgmres_gains_over_jacobi_on_unseen_models():
