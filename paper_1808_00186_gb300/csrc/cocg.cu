@@ -1464,7 +1464,10 @@ Status cocg_group(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, const
     int64_t done_iters = 0;
     BGrp hg{};
     while (true) {
-      const int64_t steps = std::min<int64_t>(chunk, o.max_iters - max_done - done_iters);
+      // complex64 inner solves stop after at most kCgInnerMax iterations, as the single-source
+      // solver's do (a complex64 COCG left running drifts); the FP64 refinement restarts them
+      int64_t steps = std::min<int64_t>(chunk, o.max_iters - max_done - done_iters);
+      if (!c128) steps = std::min<int64_t>(steps, kCgInnerMax - done_iters);
       if (steps <= 0) break;
       for (int64_t k = 0; k < steps; ++k) {
         {
