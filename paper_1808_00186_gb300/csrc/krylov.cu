@@ -499,7 +499,7 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
       if (learned) {  // every step: z = D (D^{-1} v + G phi + Pi w), the network's auxiliary-space direction
         T* zj = Z + (int64_t)j * ld;
         KernelTimer kt(c, "learned_apply", 0.0, j, 0);
-        PG_TRY(c->net->apply<T>(s, vj, c->slots.as<int32_t>(), n, zj));
+        PG_TRY(c->net->apply<T>(s, vj, c->slots.as<int32_t>(), n, zj, false, &st->done));
         c->launches += 28;
         xin = zj;
       }
@@ -554,7 +554,7 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
     PG_CUDA(cudaGetLastError());
     return Status{};
   };
-  if (!graph || learned || c->profiling) {
+  if (!graph || c->profiling) {
     PG_TRY(cycle_body());
   } else {
     // CUDA graph: captured once for these buffers, sizes and options, replayed every cycle (the
@@ -567,7 +567,10 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
                                     (uint64_t)(uintptr_t)(sell ? (c128 ? S->sell128.ptr : S->sell64.ptr) : nullptr),
                                     (uint64_t)(uintptr_t)c->sell_perm.ptr, (uint64_t)(uintptr_t)c->sell_sp.ptr,
                                     (uint64_t)(uintptr_t)c->sell_col.ptr, (uint64_t)c->sell_ns,
-                                    (uint64_t)(uintptr_t)c->val.ptr, (uint64_t)(uintptr_t)S->r.ptr});
+                                    (uint64_t)(uintptr_t)c->val.ptr, (uint64_t)(uintptr_t)S->r.ptr,
+                                    (uint64_t)learned, (uint64_t)(uintptr_t)Z, (uint64_t)(uintptr_t)c->net,
+                                    (uint64_t)(c->net ? c->net->alloc_gen : 0),
+                                    (uint64_t)(uintptr_t)c->slots.ptr, (uint64_t)(uintptr_t)c->diag.ptr});
     if (!S->graph || S->graph_key != key) {
       if (S->graph) cudaGraphExecDestroy(S->graph);
       S->graph = nullptr;

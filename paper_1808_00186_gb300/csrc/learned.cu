@@ -62,7 +62,8 @@ __device__ inline void grid_coords(int64_t v, int gx, int gy, int& x, int& y, in
 // Average of the existing children 2c + {0,1}^3 of every coarse voxel; one thread per coarse
 // voxel and 8 channels (16-byte loads and stores).
 __global__ void k_pool(const __nv_bfloat16* __restrict__ in, int gx, int gy, int gz, int C,
-                       __nv_bfloat16* __restrict__ out) {
+                       __nv_bfloat16* __restrict__ out, const int* __restrict__ stop) {
+  if (stop && *stop) return;
   const int cx = (gx + 1) / 2, cy = (gy + 1) / 2, cz = (gz + 1) / 2;
   const int C8 = C / 8;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -103,7 +104,8 @@ __global__ void k_pool_bwd_add(const __nv_bfloat16* __restrict__ dout, int gx, i
 }
 // out[f] = coarse[parent(f)] + skip[f]; one thread per fine voxel and 8 channels.
 __global__ void k_up_add(const __nv_bfloat16* __restrict__ coarse, const __nv_bfloat16* __restrict__ skip, int gx,
-                         int gy, int gz, int C, __nv_bfloat16* __restrict__ out) {
+                         int gy, int gz, int C, __nv_bfloat16* __restrict__ out, const int* __restrict__ stop) {
+  if (stop && *stop) return;
   const int C8 = C / 8;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)gx * gy * gz * C8) return;
@@ -312,7 +314,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_hx_in(const T* __restrict__ r, const int32_t* __restrict__ slot_edge,
                                                const float4* __restrict__ tang, const float4* __restrict__ aux,
                                                int gx, int gy, int gz, float* __restrict__ out,
-                                               double* __restrict__ part) {
+                                               double* __restrict__ part, const int* __restrict__ stop) {
+  if (stop && *stop) return;
   using R = typename real_of<T>::type;
   __shared__ double red[8];
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -363,7 +366,8 @@ __global__ void __launch_bounds__(256) k_hx_in(const T* __restrict__ r, const in
   }
 }
 // s = sqrt(sum / (4 n_interior)) (1 when the sum is zero) -> scal[0] = 1 / s, scal[1] = s.
-__global__ void k_hx_scale(const double* __restrict__ part, int nb, int64_t n_interior, float* __restrict__ scal) {
+__global__ void k_hx_scale(const double* __restrict__ part, int nb, int64_t n_interior, float* __restrict__ scal, const int* __restrict__ stop) {
+  if (stop && *stop) return;
   __shared__ double red[256];
   double a = 0.0;
   for (int i = threadIdx.x; i < nb; i += 256) a += part[i];
@@ -381,7 +385,8 @@ __global__ void k_hx_scale(const double* __restrict__ part, int nb, int64_t n_in
   }
 }
 __global__ void k_hx_pack(const float* __restrict__ nodes8, const float* __restrict__ feat, int64_t V,
-                          const float* __restrict__ scal, __nv_bfloat16* __restrict__ x) {
+                          const float* __restrict__ scal, __nv_bfloat16* __restrict__ x, const int* __restrict__ stop) {
+  if (stop && *stop) return;
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (v >= V) return;
   const float is = scal[0];
@@ -401,7 +406,8 @@ template <typename T, bool XS>
 __global__ void k_hx_out(const T* __restrict__ r, const int32_t* __restrict__ slot, int64_t E,
                          const float* __restrict__ y, const float4* __restrict__ aux, const float4* __restrict__ tang,
                          const float* __restrict__ scal, const double2* __restrict__ diag, int gx, int gy,
-                         T* __restrict__ z) {
+                         T* __restrict__ z, const int* __restrict__ stop) {
+  if (stop && *stop) return;
   using R = typename real_of<T>::type;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= E) return;
@@ -580,23 +586,107 @@ unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
+// Direct 3x3x3 convolution on the CUDA cores for the network's small coarse grids, where a
+// 128-voxel tensor-core tile would mostly be padding and per-tile set-up.  The block stages the
+// weights transposed to [t][ci][co] in shared memory (a warp's lanes, consecutive output
+// channels, then read consecutive addresses), then walks the outputs (voxel, channel) with a grid
+// stride; FP32 accumulation over BF16 operands, 16-byte loads of 8 input channels.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) k_conv3d_small(const __nv_bfloat16* __restrict__ X,
+                                                      const __nv_bfloat16* __restrict__ W,
+                                                      const float* __restrict__ bias, int gx, int gy, int gz,
+                                                      int relu, __nv_bfloat16* __restrict__ Ybf,
+                                                      float* __restrict__ Yf, const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __nv_bfloat16* ws = reinterpret_cast<__nv_bfloat16*>(smem_raw);  // [27][CIN][COUT]
+  for (int i = threadIdx.x; i < 27 * CIN * COUT; i += 256) {
+    const int ci = i % CIN, co = (i / CIN) % COUT, t = i / (CIN * COUT);  // i indexes W[t][co][ci]
+    ws[(t * CIN + ci) * COUT + co] = W[i];
+  }
+  __syncthreads();
+  const int64_t total = (int64_t)gx * gy * gz * COUT;
+  for (int64_t idx = blockIdx.x * 256 + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * 256) {
+    const int co = (int)(idx % COUT);
+    const int64_t v = idx / COUT;
+    int x, y, z;
+    grid_coords(v, gx, gy, x, y, z);
+    float acc = 0.f;
+    for (int t = 0; t < 27; ++t) {
+      const int nx = x + t % 3 - 1, ny = y + (t / 3) % 3 - 1, nz = z + t / 9 - 1;
+      if (nx < 0 || nx >= gx || ny < 0 || ny >= gy || nz < 0 || nz >= gz) continue;
+      const __nv_bfloat16* xs = X + ((int64_t)nx + gx * ((int64_t)ny + (int64_t)gy * nz)) * CIN;
+      const __nv_bfloat16* wt = ws + t * CIN * COUT + co;
+#pragma unroll
+      for (int c8 = 0; c8 < CIN / 8; ++c8) {
+        const uint4 a = *reinterpret_cast<const uint4*>(xs + 8 * c8);
+        const __nv_bfloat16* pa = reinterpret_cast<const __nv_bfloat16*>(&a);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc = fmaf(__bfloat162float(pa[k]), __bfloat162float(wt[(8 * c8 + k) * COUT]), acc);
+      }
+    }
+    acc += bias[co];
+    if (relu) acc = fmaxf(acc, 0.f);
+    if (Yf)
+      Yf[v * COUT + co] = acc;
+    else
+      Ybf[v * COUT + co] = __float2bfloat16(acc);
+  }
+}
+
+// Grids of at most this many voxels take the direct CUDA-core convolution inside the network.
+constexpr int64_t kSmallConvVoxels = 8192;
+
+Status conv3d_small(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, const __nv_bfloat16* x,
+                    const __nv_bfloat16* w, const float* bias, bool relu, __nv_bfloat16* ybf, float* yf,
+                    const int* stop) {
+  const int64_t V = (int64_t)gx * gy * gz;
+  PG_TRY(conv3d_attributes());
+  int dev = 0, sms = 0;
+  PG_CUDA(cudaGetDevice(&dev));
+  PG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+#define PG_CONVS(CI, CO)                                                                                         \
+  if (cin == CI && cout == CO) {                                                                                 \
+    const unsigned grid = (unsigned)std::min<int64_t>(nb(V * CO, 256), (int64_t)4 * sms);                        \
+    k_conv3d_small<CI, CO><<<grid, 256, 27 * CI * CO * 2, s>>>(x, w, bias, gx, gy, gz, relu ? 1 : 0, ybf, yf, stop); \
+    PG_CUDA(cudaGetLastError());                                                                                 \
+    return Status{};                                                                                             \
+  }
+  PG_CONVS(16, 16)
+  PG_CONVS(16, 32)
+  PG_CONVS(32, 16)
+  PG_CONVS(32, 32)
+#undef PG_CONVS
+  return Status{PETGEM_ERR_UNSUPPORTED, "conv3d_small: channel counts must be 16 or 32"};
+}
+
 // ------------------------------------------------------------ host side
+Status conv3d_attributes() {
+  static bool done = false;
+  if (done) return Status{};
+  PG_CUDA(cudaFuncSetAttribute(k_conv3d<16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem(16, 16)));
+  PG_CUDA(cudaFuncSetAttribute(k_conv3d<16, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem(16, 32)));
+  PG_CUDA(cudaFuncSetAttribute(k_conv3d<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem(32, 16)));
+  PG_CUDA(cudaFuncSetAttribute(k_conv3d<32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem(32, 32)));
+  PG_CUDA(cudaFuncSetAttribute(k_conv3d_small<32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 27 * 32 * 32 * 2));
+  PG_CUDA(cudaFuncSetAttribute(k_conv3d_small<16, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 27 * 16 * 32 * 2));
+  PG_CUDA(cudaFuncSetAttribute(k_conv3d_small<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 27 * 32 * 16 * 2));
+  done = true;
+  return Status{};
+}
+
 Status conv3d(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, const __nv_bfloat16* x,
-              const __nv_bfloat16* w, const float* bias, bool relu, __nv_bfloat16* ybf, float* yf, int* err) {
+              const __nv_bfloat16* w, const float* bias, bool relu, __nv_bfloat16* ybf, float* yf, int* err,
+              const int* stop) {
   const int64_t V = (int64_t)gx * gy * gz;
   const unsigned grid = nb(V, kConvRows);
 #define PG_CONV(CI, CO)                                                                                        \
   if (cin == CI && cout == CO) {                                                                               \
-    static bool attr = false;                                                                                  \
-    if (!attr) {                                                                                               \
-      PG_CUDA(cudaFuncSetAttribute(k_conv3d<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
-                                   conv_smem(CI, CO)));                                                        \
-      attr = true;                                                                                             \
-    }                                                                                                          \
-    k_conv3d<CI, CO><<<grid, 128, conv_smem(CI, CO), s>>>(x, w, bias, gx, gy, gz, relu ? 1 : 0, ybf, yf, err); \
+    k_conv3d<CI, CO><<<grid, 128, conv_smem(CI, CO), s>>>(x, w, bias, gx, gy, gz, relu ? 1 : 0, ybf, yf, err, stop); \
     PG_CUDA(cudaGetLastError());                                                                               \
     return Status{};                                                                                           \
   }
+  PG_TRY(conv3d_attributes());
   PG_CONV(16, 16)
   PG_CONV(16, 32)
   PG_CONV(32, 16)
@@ -688,6 +778,8 @@ Status Net::init(petgem_ctx* c, int nx_, int ny_, int nz_) {
   PG_CUDA(cudaMemsetAsync(feat.ptr, 0, (size_t)V[0] * 2 * sizeof(float), s));
   geom_version = -1;
   aux_version = -1;
+  ++alloc_gen;
+  PG_TRY(conv3d_attributes());
   ready = true;
   return Status{};
 }
@@ -701,32 +793,39 @@ Status Net::pack_weights(cudaStream_t s) {
   return Status{};
 }
 
-Status Net::conv(cudaStream_t s, int i, int lvl, const __nv_bfloat16* in, __nv_bfloat16* out, float* outf) {
+Status Net::conv(cudaStream_t s, int i, int lvl, const __nv_bfloat16* in, __nv_bfloat16* out, float* outf,
+                 const int* stop) {
   const int* gg = g[lvl];
   // timed (when profiling) with its floating-point operations in place of bytes
-  KernelTimer kt(ctx, "conv3d_fwd", 2.0 * 27.0 * L[i].cin * L[i].cout * (double)gg[0] * gg[1] * gg[2]);
+  const double flops = 2.0 * 27.0 * L[i].cin * L[i].cout * (double)gg[0] * gg[1] * gg[2];
+  if (V[lvl] <= kSmallConvVoxels) {
+    KernelTimer kt(ctx, "conv3d_small_fwd", flops);
+    return conv3d_small(s, gg[0], gg[1], gg[2], L[i].cin, L[i].cout, in, wb.as<__nv_bfloat16>() + L[i].w_off,
+                        params.as<float>() + L[i].b_off, L[i].relu != 0, out, outf, stop);
+  }
+  KernelTimer kt(ctx, "conv3d_fwd", flops);
   return conv3d(s, gg[0], gg[1], gg[2], L[i].cin, L[i].cout, in, wb.as<__nv_bfloat16>() + L[i].w_off,
-                params.as<float>() + L[i].b_off, L[i].relu != 0, out, outf, err.as<int>());
+                params.as<float>() + L[i].b_off, L[i].relu != 0, out, outf, err.as<int>(), stop);
 }
 
 // Input grid q[0] (BF16 [V0][16]) -> y (FP32 [V0][16]): encoder down to the coarsest level, then
 // decoder levels that add the upsampled coarse output to the encoder's.
-Status Net::forward(cudaStream_t s) {
+Status Net::forward(cudaStream_t s, const int* stop) {
   using B = __nv_bfloat16;
   for (int l = 0; l < nlev; ++l) {
     if (l > 0)
       k_pool<<<nb(V[l] * ch_e(l - 1) / 8), 256, 0, s>>>(e[l - 1].as<B>(), g[l - 1][0], g[l - 1][1], g[l - 1][2],
-                                                        ch_e(l - 1), q[l].as<B>());
-    PG_TRY(conv(s, enc(l), l, q[l].as<B>(), e[l].as<B>(), nullptr));
+                                                        ch_e(l - 1), q[l].as<B>(), stop);
+    PG_TRY(conv(s, enc(l), l, q[l].as<B>(), e[l].as<B>(), nullptr, stop));
   }
   for (int l = nlev - 2; l >= 0; --l) {
     const B* coarse = (l + 1 == nlev - 1) ? e[l + 1].as<B>() : d[l + 1].as<B>();
     k_up_add<<<nb(V[l] * ch_e(l) / 8), 256, 0, s>>>(coarse, e[l].as<B>(), g[l][0], g[l][1], g[l][2], ch_e(l),
-                                                    sk[l].as<B>());
+                                                    sk[l].as<B>(), stop);
     if (l == 0)
-      PG_TRY(conv(s, dec(0), 0, sk[0].as<B>(), nullptr, y.as<float>()));
+      PG_TRY(conv(s, dec(0), 0, sk[0].as<B>(), nullptr, y.as<float>(), stop));
     else
-      PG_TRY(conv(s, dec(l), l, sk[l].as<B>(), d[l].as<B>(), nullptr));
+      PG_TRY(conv(s, dec(l), l, sk[l].as<B>(), d[l].as<B>(), nullptr, stop));
   }
   PG_CUDA(cudaGetLastError());
   return Status{};
@@ -734,6 +833,9 @@ Status Net::forward(cudaStream_t s) {
 
 Status Net::dgrad(cudaStream_t s, int i, int lvl, const __nv_bfloat16* dout, __nv_bfloat16* din) {
   const int* gg = g[lvl];  // the input gradient has no bias term: zbias is all zeros
+  if (V[lvl] <= kSmallConvVoxels)
+    return conv3d_small(s, gg[0], gg[1], gg[2], L[i].cout, L[i].cin, dout, wd.as<__nv_bfloat16>() + L[i].w_off,
+                        zbias.as<float>(), false, din, nullptr, nullptr);
   return conv3d(s, gg[0], gg[1], gg[2], L[i].cout, L[i].cin, dout, wd.as<__nv_bfloat16>() + L[i].w_off,
                 zbias.as<float>(), false, din, nullptr, err.as<int>());
 }
@@ -796,6 +898,7 @@ Status Net::prepare_aux(petgem_ctx* c) {
     PG_CUDA(cudaGetLastError());
     geom_version = c->mesh_version;
     aux_version = -1;
+    ++alloc_gen;
   }
   if (aux_version != c->assembly_version) {
     PG_TRY(aux.reserve((size_t)V[0] * sizeof(float4)));
@@ -812,37 +915,49 @@ Status Net::prepare_aux(petgem_ctx* c) {
 // Network input x0 from an edge vector r (a residual): the gathered, scaled node fields, the scale
 // s in scal[0..1] (1 / s, s), the two features.
 template <typename T>
-Status Net::load_input(cudaStream_t s, const T* r, int64_t E) {
+Status Net::load_input(cudaStream_t s, const T* r, int64_t E, const int* stop) {
   (void)E;
   const int gx = g[0][0], gy = g[0][1], gz = g[0][2];
   const unsigned blocks = nb(V[0]);
-  k_hx_in<T><<<blocks, 256, 0, s>>>(r, slot_edge.as<int32_t>(), tang.as<float4>(), aux.as<float4>(), gx, gy, gz,
-                                    nodes8.as<float>(), npart.as<double>());
+  // algorithmic bytes: every edge value read twice (once from each end node), each node's 14
+  // slots (edge id and tangent) read once, 32 B of node output written
+  {
+    KernelTimer kt(ctx, sizeof(T) == 8 ? "hx_in_c64" : "hx_in_c128",
+                   2.0 * sizeof(T) * (double)ctx->n_edges + (double)V[0] * (14.0 * 20.0 + 32.0 + 16.0));
+    k_hx_in<T><<<blocks, 256, 0, s>>>(r, slot_edge.as<int32_t>(), tang.as<float4>(), aux.as<float4>(), gx, gy, gz,
+                                      nodes8.as<float>(), npart.as<double>(), stop);
+  }
   const int64_t n_in = (int64_t)std::max(gx - 2, 0) * std::max(gy - 2, 0) * std::max(gz - 2, 0);
-  k_hx_scale<<<1, 256, 0, s>>>(npart.as<double>(), (int)blocks, n_in, scal.as<float>());
+  k_hx_scale<<<1, 256, 0, s>>>(npart.as<double>(), (int)blocks, n_in, scal.as<float>(), stop);
   k_hx_pack<<<nb(V[0]), 256, 0, s>>>(nodes8.as<float>(), feat.as<float>(), V[0], scal.as<float>(),
-                                     q[0].as<__nv_bfloat16>());
+                                     q[0].as<__nv_bfloat16>(), stop);
   PG_CUDA(cudaGetLastError());
   return Status{};
 }
 
 template <typename T>
-Status Net::apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T* z, bool xspace) {
-  PG_TRY(load_input(s, r, E));
-  PG_TRY(forward(s));
+Status Net::apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T* z, bool xspace,
+                  const int* stop) {
+  PG_TRY(load_input(s, r, E, stop));
+  PG_TRY(forward(s, stop));
   const double2* d = ctx->diag.as<double2>();
+  // algorithmic bytes per edge: r, z, diag, slot, tangent, and 2 x (32 B of y + 16 B of scales)
+  KernelTimer kt(ctx, sizeof(T) == 8 ? "hx_out_c64" : "hx_out_c128",
+                 (double)E * (2.0 * sizeof(T) + 16.0 + 4.0 + 16.0 + 96.0));
   if (xspace)
     k_hx_out<T, true><<<nb(E), 256, 0, s>>>(r, slot, E, y.as<float>(), aux.as<float4>(), tang.as<float4>(),
-                                            scal.as<float>(), d, g[0][0], g[0][1], z);
+                                            scal.as<float>(), d, g[0][0], g[0][1], z, stop);
   else
     k_hx_out<T, false><<<nb(E), 256, 0, s>>>(r, slot, E, y.as<float>(), aux.as<float4>(), tang.as<float4>(),
-                                             scal.as<float>(), d, g[0][0], g[0][1], z);
+                                             scal.as<float>(), d, g[0][0], g[0][1], z, stop);
   PG_CUDA(cudaGetLastError());
   return Status{};
 }
 
-template Status Net::apply<float2>(cudaStream_t, const float2*, const int32_t*, int64_t, float2*, bool);
-template Status Net::apply<double2>(cudaStream_t, const double2*, const int32_t*, int64_t, double2*, bool);
+template Status Net::apply<float2>(cudaStream_t, const float2*, const int32_t*, int64_t, float2*, bool,
+                                  const int*);
+template Status Net::apply<double2>(cudaStream_t, const double2*, const int32_t*, int64_t, double2*, bool,
+                                   const int*);
 
 // One training sample, r = the residual of a solver iterate (complex128 edge vector).  Loss: the
 // residual angle L = 1 - |<r, A z>|^2 / (|r|^2 |A z|^2) of the preconditioned direction
@@ -855,7 +970,8 @@ Status Net::sample_grad(cudaStream_t s, petgem_ctx* c, const double2* r, const i
   double2* w = wtmp.as<double2>();
   double2* gw = gtmp.as<double2>();
   k_hx_out<double2, false><<<nb(E), 256, 0, s>>>(r, slot, E, y.as<float>(), aux.as<float4>(), tang.as<float4>(),
-                                                 scal.as<float>(), c->diag.as<double2>(), g[0][0], g[0][1], zu);
+                                                 scal.as<float>(), c->diag.as<double2>(), g[0][0], g[0][1], zu,
+                                                 nullptr);
   k_ahat_apply<<<nb(E), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(),
                                      c->diag.as<double2>(), zu, E, w);
   k_angle_dots<<<1, 1024, 0, s>>>(r, w, E, dvec.as<double>(), loss_acc.as<double>());

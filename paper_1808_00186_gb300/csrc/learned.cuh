@@ -50,10 +50,12 @@ struct Net {
   DevBuf slot_edge, tang, aux, nodes8, npart;
   int64_t aux_version = -1;    // assembly the scales belong to
   int64_t geom_version = -1;   // mesh the slot map and tangents belong to
+  int64_t alloc_gen = 0;       // bumped whenever a buffer may have moved (captured graphs key on it)
   Status init(petgem_ctx* c, int nx, int ny, int nz);
   Status pack_weights(cudaStream_t s);
   // layer i on level lvl
-  Status conv(cudaStream_t s, int i, int lvl, const __nv_bfloat16* in, __nv_bfloat16* out, float* outf);
+  Status conv(cudaStream_t s, int i, int lvl, const __nv_bfloat16* in, __nv_bfloat16* out, float* outf,
+              const int* stop = nullptr);
   Status dgrad(cudaStream_t s, int i, int lvl, const __nv_bfloat16* dout, __nv_bfloat16* din);
   Status wgrad(cudaStream_t s, int i, int lvl, const __nv_bfloat16* in, const __nv_bfloat16* dout, bool acc);
   int enc(int l) const { return l == 0 ? 0 : l == 1 ? 1 : l == nlev - 1 ? 3 : 2; }  // c1, c2, c4, c3
@@ -61,21 +63,31 @@ struct Net {
   static int ch_e(int l) { return l == 0 ? 16 : 32; }
   static int ch_q(int l) { return l <= 1 ? 16 : 32; }
   static int ch_d(int l) { return l == 1 ? 16 : 32; }
-  Status forward(cudaStream_t s);
+  // stop: optional device flag; when nonzero every kernel of the pass returns at once (a FGMRES
+  // cycle that already stopped)
+  Status forward(cudaStream_t s, const int* stop = nullptr);
   Status backward(cudaStream_t s, bool acc);
   Status prepare_aux(petgem_ctx* c);
-  template <typename T> Status load_input(cudaStream_t s, const T* r, int64_t E);
+  template <typename T> Status load_input(cudaStream_t s, const T* r, int64_t E, const int* stop = nullptr);
   // z = D (D^{-1} r + G phi + Pi w) (the solver's Jacobi-scaled variables) or, with xspace,
   // z = D^{-1} r + G phi + Pi w, for the residual r of E entries.
   template <typename T> Status apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T* z,
-                                     bool xspace = false);
+                                     bool xspace = false, const int* stop = nullptr);
   Status sample_grad(cudaStream_t s, petgem_ctx* c, const double2* r, const int32_t* slot, int64_t E, bool acc);
   Status adam_step(cudaStream_t s, float lr, float gscale);
   Status features(cudaStream_t s, const double* sigma, double sigma_p, double omega, double h);
 };
 
 Status conv3d(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, const __nv_bfloat16* x,
-              const __nv_bfloat16* w, const float* bias, bool relu, __nv_bfloat16* ybf, float* yf, int* err);
+              const __nv_bfloat16* w, const float* bias, bool relu, __nv_bfloat16* ybf, float* yf, int* err,
+              const int* stop = nullptr);
+// The same convolution on the CUDA cores (small grids).
+Status conv3d_small(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, const __nv_bfloat16* x,
+                    const __nv_bfloat16* w, const float* bias, bool relu, __nv_bfloat16* ybf, float* yf,
+                    const int* stop = nullptr);
+// Dynamic shared-memory limits of the tensor-core convolutions (once per process; before any
+// stream capture).
+Status conv3d_attributes();
 Status conv3d_wgrad(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, const __nv_bfloat16* x,
                     const __nv_bfloat16* dy, float* part, int splits, float* dw, bool accumulate, int* err);
 int wgrad_splits(int64_t V);

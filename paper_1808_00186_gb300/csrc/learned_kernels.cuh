@@ -27,8 +27,10 @@ template <int CIN, int COUT>
 __global__ void __launch_bounds__(128) k_conv3d(const __nv_bfloat16* __restrict__ X,
                                                 const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias,
                                                 int gx, int gy, int gz, int relu, __nv_bfloat16* __restrict__ Ybf,
-                                                float* __restrict__ Yf, int* __restrict__ err) {
+                                                float* __restrict__ Yf, int* __restrict__ err,
+                                                const int* __restrict__ stop) {
   static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 32, "channel counts");
+  if (stop && *stop) return;  // block-uniform: before any barrier or TMEM allocation
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;                               // 2 x 128 x CIN bf16
   unsigned char* sW = smem + 2 * kConvRows * CIN * 2;     // 27 x COUT x CIN bf16

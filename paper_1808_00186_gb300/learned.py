@@ -15,6 +15,7 @@ along z.
 """
 from __future__ import annotations
 
+import os
 import time
 
 import numpy as np
@@ -22,7 +23,19 @@ import numpy as np
 from . import api, synth
 
 LAYERS = [(16, 16), (16, 32), (32, 32), (32, 32), (32, 32), (32, 16), (16, 16)]
+# the network trained by train_learned at the 2000-model 32^3 scale (its run record beside it)
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "learned_n32.npy")
 N_OUT = 8
+
+
+def levels(grid) -> int:
+    """Levels of the network on a node grid (poolings until the coarsest grid has at most 3 nodes
+    per axis, at least 3 levels), as the library builds it."""
+    dims, L = list(grid), 1
+    while max(dims) > 3:
+        dims = [(d + 1) // 2 for d in dims]
+        L += 1
+    return max(3, L)
 
 
 def layout():
@@ -155,7 +168,8 @@ def train(n: int = 32, models: int = 200, epochs: int = 2, lr: float = 1e-3, see
                "mean_cycles": float(np.mean(cycles))}
 
 
-def evaluate(params: np.ndarray, n: int, seeds, precision=api.PREC_MIXED, tol: float = 1e-8, log=None):
+def evaluate(params: np.ndarray, n: int, seeds, precision=api.PREC_MIXED, tol: float = 1e-8, log=None,
+             use_graphs: int = 1):
     """Learned FGMRES against plain Jacobi GMRES(50) on unseen random block models of n^3 cells:
     [{seed, iters_jacobi, iters_learned, s_jacobi, s_learned, fell_back, relres}] (times from
     CUDA events around each solve, assembly excluded)."""
@@ -175,7 +189,8 @@ def evaluate(params: np.ndarray, n: int, seeds, precision=api.PREC_MIXED, tol: f
                 ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize()
                 ev0.record()
-                x, info, st = ctx.solve(precision=precision, precond=pc, tol=tol, allow_not_converged=True)
+                x, info, st = ctx.solve(precision=precision, precond=pc, tol=tol, allow_not_converged=True,
+                                        use_graphs=use_graphs)
                 ev1.record()
                 torch.cuda.synchronize()
                 rec["iters_" + name] = int(info[0]["iters"])

@@ -220,3 +220,25 @@ def test_learned_fgmres_gains_over_jacobi_on_unseen_models():
         xl = xl.cpu().numpy()[0]
     assert st == api.OK and info_l[0]["fell_back"] == 0
     assert np.linalg.norm(xl - xr) <= 1e-6 * np.linalg.norm(xr)
+
+
+def test_learned_cycles_replayed_as_cuda_graphs_are_bit_identical():
+    """Learned FGMRES cycles captured once as a CUDA graph and replayed give the direct launches'
+    solution and iteration record bit for bit, in both precisions, with the committed weights
+    (cycles that stop early skip the remaining network applications in both modes)."""
+    n = 10
+    m, ref = lattice_case(n, 10003)
+    p = np.load(PL.WEIGHTS)
+    with api.Context(0) as ctx:
+        ctx.mesh(m.mesh.nodes, m.mesh.tets)
+        ctx.assemble(m.freq, m.sigma, m.sigma_p, m.sources)
+        api.petgem_learned_create(ctx.h, n, n, n)
+        api.petgem_learned_params(ctx.h, set_params=p)
+        for prec in (api.PREC_MIXED, api.PREC_C128):
+            out = []
+            for g in (0, 1, 1):
+                x, info, st = ctx.solve(precision=prec, precond=api.PRECOND_LEARNED, use_graphs=g)
+                assert st == api.OK and info[0]["true_rel_residual"] <= 1e-8
+                out.append((x.cpu().numpy(), info))
+            for x, info in out[1:]:
+                assert np.array_equal(x, out[0][0]) and info == out[0][1]
