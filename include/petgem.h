@@ -275,6 +275,41 @@ int petgem_ssor_apply(petgem_ctx *ctx, double omega, const void *r, void *z);
  * some receiver is in no tet (its nine outputs are NaN). */
 int petgem_receivers(petgem_ctx *ctx, int32_t n_rcv, const double *rx, const void *x, void *out);
 
+/* ----------------------------------------------------------------------- layered background */
+/* Primary field of a horizontal electric dipole in a horizontally layered Earth (Section 2: for a
+ * layered background the primary field is computed semi-analytically by Hankel transforms, where
+ * the paper uses filters it does not give).  The field is App. A's whole-space field of the source
+ * layer's conductivity plus Hankel integrals of the difference between the layered and the
+ * whole-space TE/TM mode spectra, evaluated by a fixed 8-point Gauss-Legendre panel rule:
+ * lambda_max = 36 / D (D = the shortest source - interface - point path for a point in the source
+ * layer, else |z - z_s|, at least 1e-3 m), the panel [0, k_min / 16] (k_min = min_j sqrt(w mu0
+ * sigma_j)), panels doubling up to w = min(pi / rho, lambda_max / 16), then width w, at most 16384.
+ * Same conventions as App. A (operator curl curl + i w mu0 sigma, e^{-ikr} decay).
+ *   n_layers: 1..8, top first.  z_interfaces: host double[n_layers - 1], strictly decreasing (z up);
+ *   layer 0 lies above z_interfaces[0]; a point on an interface belongs to the layer above.
+ *   sigma_layers: host double[n_layers] (S/m, > 0).  src: host, axis 0 or 1 (horizontal dipoles).
+ *   pts: device double[n_pts][3]; out: device complex128[n_pts][3] (E_x, E_y, E_z), overwritten.
+ * Work is enqueued on `stream` (the call returns at once; nothing is allocated).
+ * Errors (nothing launched): null pointers, n_pts < 0, freq <= 0, interfaces not decreasing or a
+ * conductivity <= 0: PETGEM_ERR_INVALID_ARG; more than 8 layers or a vertical dipole:
+ * PETGEM_ERR_UNSUPPORTED. */
+int petgem_primary_layered(void *stream, int32_t n_layers, const double *z_interfaces, const double *sigma_layers,
+                           double freq_hz, const petgem_dipole *src, int32_t n_pts, const double *pts, void *out);
+
+/* Assembly with a layered background (Section 2, eq. 6 with sigma_p(z) layered): as
+ * petgem_assemble, with the primary field of petgem_primary_layered and delta sigma_e = sigma_e -
+ * (conductivity of the layer holding the tet's centroid), so only tets that differ from their
+ * layer carry a right-hand side.  The background stays with the context: petgem_assemble_frequency
+ * re-forms the right-hand sides in it, and petgem_receivers reports E_p of the layered background
+ * (kind 0) and E_p + E_s.  The context's sigma_p (network features) becomes the conductivity of the
+ * first source's layer.  petgem_assemble returns the context to a homogeneous background.
+ * z_interfaces, sigma_layers: host, as for petgem_primary_layered; sigma: device double[n_tets];
+ * src: host, horizontal dipoles.  Errors as petgem_assemble, plus PETGEM_ERR_UNSUPPORTED for more
+ * than 8 layers or a vertical dipole. */
+int petgem_assemble_layered(petgem_ctx *ctx, double freq_hz, const double *sigma, int32_t n_layers,
+                            const double *z_interfaces, const double *sigma_layers, int32_t n_src,
+                            const petgem_dipole *src);
+
 /* ----------------------------------------------------------------------- learned preconditioner */
 /* Not in the paper (it solves with GMRES, SQMR and MUMPS, Sections 5.1-5.3).  An additive
  * auxiliary-space preconditioner for the edge-element system (Hiptmair-Xu decomposition) whose

@@ -246,3 +246,41 @@ def spectral_field(p, src, sigma, freq, D):
     if int(axis) == 1:
         e = np.array([-e[1], e[0], e[2]])
     return e
+
+
+# ---------------------------------------------------------------- right-hand sides (eq. 6)
+LOCAL_EDGES = [(0, 1), (0, 2), (0, 3), (1, 2), (3, 1), (2, 3)]   # eqs. B.1-B.6 (N5 = W42)
+
+
+def layer_sigma(z: float, z_if, sig) -> float:
+    return float(np.asarray(sig)[layer_of(z, np.asarray(z_if, dtype=np.float64))])
+
+
+def rhs(nodes, tets, sigma, z_if, sig, freq, sources, tet_edges, signs, boundary, n_edges):
+    """b[s][e] of eq. 6 with the layered background: for every tet whose conductivity differs from
+    that of the layer holding its centroid, b^e_k = -i w mu0 (sigma_e - sigma_layer) sum_q (V/4)
+    N_k(x_q) . E_p(x_q) on the oracle's 4-point rule (oracle.quadrature), N_k = S_k l_k (lambda_a
+    grad lambda_b - lambda_b grad lambda_a); gathered over the edges, zero on boundary edges."""
+    import oracle
+    z_if = np.asarray(z_if, dtype=np.float64)
+    omega = 2.0 * np.pi * freq
+    Q = oracle.quadrature()                 # rows: barycentric coordinates of the 4 points
+    b = np.zeros((len(sources), n_edges), dtype=np.complex128)
+    for t in range(len(tets)):
+        P = nodes[tets[t]]
+        ds = sigma[t] - layer_sigma(P[:, 2].mean(), z_if, sig)
+        if ds == 0.0:
+            continue
+        c0, grad, ln, vol = oracle.geometry(P)
+        xq = Q[:, :4] @ P                    # [4 points][3]
+        for si, src in enumerate(sources):
+            Ep = primary_field(xq, src, z_if, sig, freq)
+            for k, (a, bb) in enumerate(LOCAL_EDGES):
+                acc = 0.0
+                for q in range(4):
+                    lam = Q[q, :4]
+                    N = signs[t, k] * ln[k] * (lam[a] * grad[bb] - lam[bb] * grad[a])
+                    acc = acc + N @ Ep[q]
+                b[si, tet_edges[t, k]] += -1j * omega * MU0 * ds * (vol / 4.0) * acc
+    b[:, boundary == 1] = 0.0
+    return b

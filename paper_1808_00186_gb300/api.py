@@ -75,6 +75,8 @@ _SIGNATURES = {
     "petgem_nn_conv3d": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _P, _P, _I32, _P, _I32]),
     "petgem_nn_conv3d_wgrad": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _P, _P]),
     "petgem_nn_conv3d_wgrad_noalloc": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _P, _P]),
+    "petgem_primary_layered": (ctypes.c_int, [_P, _I32, _P, _P, _D, ctypes.POINTER(petgem_dipole), _I32, _P, _P]),
+    "petgem_assemble_layered": (ctypes.c_int, [_P, _D, _P, _I32, _P, _P, _I32, ctypes.POINTER(petgem_dipole)]),
 }
 
 _lib = None
@@ -304,6 +306,29 @@ def petgem_nn_conv3d_wgrad_noalloc(stream, grid, cin, cout, x, dy, dw):
         raise PetgemError(st, "petgem_nn_conv3d_wgrad_noalloc")
 
 
+def petgem_primary_layered(stream, z_interfaces, sigma_layers, freq, src, pts, out):
+    """Primary field of a horizontal dipole in a layered Earth at device points pts [n, 3] into the
+    device complex128 tensor out [n, 3] (enqueued on stream).  z_interfaces decreasing (host
+    sequence), sigma_layers one longer; src: a synth.Dipole-like object."""
+    zi = np.ascontiguousarray(z_interfaces, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma_layers, dtype=np.float64)
+    d = petgem_dipole(src.x, src.y, src.z, src.moment, src.axis, 0)
+    n = 0 if pts is None else int(pts.shape[0])
+    st = load().petgem_primary_layered(stream, len(sg), zi.ctypes.data_as(_P) if zi.size else None,
+                                       sg.ctypes.data_as(_P), freq, ctypes.byref(d), n, _ptr(pts), _ptr(out))
+    if st != OK:
+        raise PetgemError(st, "petgem_primary_layered")
+
+
+def petgem_assemble_layered(ctx, freq, sigma, z_interfaces, sigma_layers, sources):
+    """Assembly with a layered background (host sequences z_interfaces, sigma_layers)."""
+    zi = np.ascontiguousarray(z_interfaces, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma_layers, dtype=np.float64)
+    arr = dipoles(sources)
+    _check(ctx, load().petgem_assemble_layered(ctx, freq, _ptr(sigma), len(sg), zi.ctypes.data_as(_P) if zi.size else None,
+                                               sg.ctypes.data_as(_P), len(sources), arr))
+
+
 def petgem_launch_count(ctx) -> int:
     return load().petgem_launch_count(ctx)
 
@@ -384,6 +409,11 @@ class Context:
         self.sigma = sigma if hasattr(sigma, "data_ptr") else self.tensor(sigma, self.torch.float64)
         self.n_src = len(sources)
         petgem_assemble(self.h, freq, self.sigma, sigma_p, sources)
+
+    def assemble_layered(self, freq, sigma, z_interfaces, sigma_layers, sources):
+        self.sigma = sigma if hasattr(sigma, "data_ptr") else self.tensor(sigma, self.torch.float64)
+        self.n_src = len(sources)
+        petgem_assemble_layered(self.h, freq, self.sigma, z_interfaces, sigma_layers, sources)
 
     def assemble_frequency(self, freq, sources):
         self.n_src = len(sources)

@@ -233,6 +233,49 @@ int petgem_assemble(petgem_ctx* c, double freq_hz, const double* sigma, double s
   c->freq = freq_hz;
   c->omega = 2.0 * 3.141592653589793238462643383279502884 * freq_hz;
   c->sigma_p = sigma_p;
+  c->bg_layers = 0;
+  c->n_src = n_src;
+  c->src.assign(src, src + n_src);
+  c->assembled = false;
+  s = petgem::build_assembly(c, sigma);
+  if (!s.ok()) cudaGetLastError();
+  return finish(c, s);
+}
+
+int petgem_assemble_layered(petgem_ctx* c, double freq_hz, const double* sigma, int32_t n_layers,
+                            const double* z_interfaces, const double* sigma_layers, int32_t n_src,
+                            const petgem_dipole* src) {
+  if (!c) return PETGEM_ERR_INVALID_ARG;
+  if (c->n_edges == 0)
+    return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_assemble_layered: call petgem_mesh_edges first"});
+  if (!sigma || !(freq_hz > 0.0) || n_src < 1 || !src || n_layers < 1 || !sigma_layers || (n_layers > 1 && !z_interfaces))
+    return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_assemble_layered: bad arguments"});
+  if (n_layers > 8) return finish(c, Status{PETGEM_ERR_UNSUPPORTED, "petgem_assemble_layered: at most 8 layers"});
+  for (int32_t j = 0; j < n_layers; ++j)
+    if (!(sigma_layers[j] > 0.0) || !std::isfinite(sigma_layers[j]))
+      return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_assemble_layered: layer conductivities must be > 0"});
+  for (int32_t j = 0; j + 1 < n_layers; ++j)
+    if (!std::isfinite(z_interfaces[j]) || (j > 0 && !(z_interfaces[j] < z_interfaces[j - 1])))
+      return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_assemble_layered: interfaces must decrease"});
+  for (int32_t i = 0; i < n_src; ++i) {
+    if (!std::isfinite(src[i].x) || !std::isfinite(src[i].y) || !std::isfinite(src[i].z) ||
+        !std::isfinite(src[i].moment) || src[i].axis < 0 || src[i].axis > 2)
+      return finish(c, Status{PETGEM_ERR_INVALID_ARG, "petgem_assemble_layered: bad dipole " + std::to_string(i)});
+    if (src[i].axis == 2)
+      return finish(c, Status{PETGEM_ERR_UNSUPPORTED, "petgem_assemble_layered: horizontal dipoles only"});
+  }
+  Status s = set_device(c);
+  if (!s.ok()) return finish(c, s);
+  c->freq = freq_hz;
+  c->omega = 2.0 * 3.141592653589793238462643383279502884 * freq_hz;
+  c->bg_layers = n_layers;
+  for (int32_t j = 0; j < 7; ++j) c->bg_z[j] = j + 1 < n_layers ? z_interfaces[j] : 0.0;
+  for (int32_t j = 0; j < 8; ++j) c->bg_sig[j] = j < n_layers ? sigma_layers[j] : 0.0;
+  {  // sigma_p of the context: the conductivity of the first source's layer
+    int32_t j = 0;
+    while (j + 1 < n_layers && src[0].z < z_interfaces[j]) ++j;
+    c->sigma_p = sigma_layers[j];
+  }
   c->n_src = n_src;
   c->src.assign(src, src + n_src);
   c->assembled = false;

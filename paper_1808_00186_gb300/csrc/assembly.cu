@@ -120,6 +120,92 @@ __global__ void k_rhs(const double* __restrict__ nodes, const int32_t* __restric
   }
 }
 
+// ---- layered background (Section 2): sigma_p varies by layer, E_p from the layered kernel
+struct BgLayers {
+  int nl;
+  double zif[7];
+  double sig[8];
+};
+// Layer holding height z (a point on an interface belongs to the layer above it).
+__device__ inline int bg_layer(double z, const BgLayers& B) {
+  int j = 0;
+  while (j < B.nl - 1 && z < B.zif[j]) ++j;
+  return j;
+}
+// Tets whose conductivity differs from their layer's (layer of the centroid): dsig[t], and with
+// pts given, a slot each (tet_slot[t], -1 for the others) holding the four quadrature points of
+// the 4-point rule (pts[4 slot + q][3]); *count receives the number of such tets.
+__global__ void k_rhs_layered_points(const double* __restrict__ nodes, const int32_t* __restrict__ tets,
+                                     const double* __restrict__ sigma, int64_t n_tets, BgLayers B,
+                                     int32_t* __restrict__ count, int32_t* __restrict__ tet_slot,
+                                     double* __restrict__ dsig, double* __restrict__ pts) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n_tets) return;
+  double p[4][3], zc = 0.0;
+  for (int j = 0; j < 4; ++j) {
+    const int64_t v = tets[4 * t + j];
+    for (int d = 0; d < 3; ++d) p[j][d] = nodes[3 * v + d];
+    zc += 0.25 * p[j][2];
+  }
+  const double ds = sigma[t] - B.sig[bg_layer(zc, B)];
+  if (!pts) {
+    dsig[t] = ds;
+    if (ds != 0.0) atomicAdd(count, 1);
+    return;
+  }
+  if (ds == 0.0) {
+    tet_slot[t] = -1;
+    return;
+  }
+  const int32_t slot = atomicAdd(count, 1);
+  tet_slot[t] = slot;
+  const double alpha = 0.58541019662496845446, beta = 0.13819660112501051518;
+  for (int q = 0; q < 4; ++q) {
+    double lam[4] = {beta, beta, beta, beta};
+    lam[q] = alpha;
+    for (int d = 0; d < 3; ++d)
+      pts[(4 * (int64_t)slot + q) * 3 + d] = lam[0] * p[0][d] + lam[1] * p[1][d] + lam[2] * p[2][d] + lam[3] * p[3][d];
+  }
+}
+// k_rhs with the primary field read from Ep[source][4 slot + q][3] (computed at the same points).
+__global__ void k_rhs_layered(const double* __restrict__ nodes, const int32_t* __restrict__ tets,
+                              const int8_t* __restrict__ signs, const double* __restrict__ dsig,
+                              const int32_t* __restrict__ tet_slot, int64_t n_tets, double omega,
+                              const double2* __restrict__ Ep, int64_t n_pts, int s0, int n_chunk,
+                              double2* __restrict__ be) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n_tets * n_chunk) return;
+  int64_t t = idx / n_chunk;
+  int sc = (int)(idx - t * n_chunk);
+  const int32_t slot = tet_slot[t];
+  TetGeom G;
+  if (slot < 0 || !tet_geometry(nodes, tets, t, G)) {
+    for (int k = 0; k < 6; ++k) be[(6 * t + k) * n_chunk + sc] = make_double2(0.0, 0.0);
+    return;
+  }
+  const double alpha = 0.58541019662496845446, beta = 0.13819660112501051518;
+  const double2* ep = Ep + ((int64_t)(s0 + sc) * n_pts + 4 * (int64_t)slot) * 3;
+  double2 R[6];
+  for (int k = 0; k < 6; ++k) R[k] = make_double2(0.0, 0.0);
+  for (int q = 0; q < 4; ++q) {
+    double lam[4] = {beta, beta, beta, beta};
+    lam[q] = alpha;
+    const double2* E = ep + 3 * q;
+    for (int k = 0; k < 6; ++k) {
+      const int a = kA[k], b = kB[k];
+      double N[3];
+      for (int d = 0; d < 3; ++d) N[d] = G.len[k] * (lam[a] * G.g[b][d] - lam[b] * G.g[a][d]);
+      R[k] = cadd(R[k], make_double2(N[0] * E[0].x + N[1] * E[1].x + N[2] * E[2].x,
+                                     N[0] * E[0].y + N[1] * E[1].y + N[2] * E[2].y));
+    }
+  }
+  const double f = omega * kMu0 * dsig[t] * G.vol * 0.25;
+  for (int k = 0; k < 6; ++k) {
+    double sg = (double)signs[6 * t + k] * f;
+    be[(6 * t + k) * n_chunk + sc] = make_double2(sg * R[k].y, -sg * R[k].x);
+  }
+}
+
 // b[s][e] = sum over the occurrences of edge e (sorted by slot = 6 t + k) of be; 0 on the boundary.
 __global__ void k_rhs_gather(const int64_t* __restrict__ eptr, const int32_t* __restrict__ occ,
                              const uint8_t* __restrict__ boundary, int64_t n_edges, const double2* __restrict__ be,
@@ -264,13 +350,48 @@ Status build_rhs(petgem_ctx* c) {
   for (int64_t i = 0; i < S; ++i)
     hsrc[i] = DipoleDev{c->src[i].x, c->src[i].y, c->src[i].z, c->src[i].moment, c->src[i].axis};
   PG_CUDA(cudaMemcpyAsync(dsrc, hsrc.data(), sizeof(DipoleDev) * S, cudaMemcpyHostToDevice, s));
+  // layered background: the quadrature points of the tets whose conductivity differs from their
+  // layer's, and the layered primary field of every source there
+  int32_t *lcount = nullptr, *tet_slot = nullptr;
+  double *dsig = nullptr, *lpts = nullptr;
+  double2* Ep = nullptr;
+  int64_t n_pts = 0;
+  if (c->bg_layers > 0) {
+    BgLayers B{};
+    B.nl = c->bg_layers;
+    for (int j = 0; j < 7; ++j) B.zif[j] = c->bg_z[j];
+    for (int j = 0; j < 8; ++j) B.sig[j] = c->bg_sig[j];
+    PG_CUDA(cudaMallocAsync((void**)&lcount, sizeof(int32_t), s));
+    PG_CUDA(cudaMallocAsync((void**)&tet_slot, T * sizeof(int32_t), s));
+    PG_CUDA(cudaMallocAsync((void**)&dsig, T * sizeof(double), s));
+    PG_CUDA(cudaMemsetAsync(lcount, 0, sizeof(int32_t), s));
+    k_rhs_layered_points<<<blocks_for(T, 256), 256, 0, s>>>(c->nodes.as<double>(), c->tets.as<int32_t>(),
+                                                            c->sigma.as<double>(), T, B, lcount, tet_slot, dsig, nullptr);
+    int32_t hcount = 0;
+    PG_CUDA(cudaMemcpyAsync(&hcount, lcount, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    n_pts = 4 * (int64_t)hcount;
+    PG_CUDA(cudaMallocAsync((void**)&lpts, std::max<int64_t>(n_pts, 1) * 3 * sizeof(double), s));
+    PG_CUDA(cudaMallocAsync((void**)&Ep, std::max<int64_t>(n_pts * S, 1) * 3 * sizeof(double2), s));
+    PG_CUDA(cudaMemsetAsync(lcount, 0, sizeof(int32_t), s));
+    k_rhs_layered_points<<<blocks_for(T, 256), 256, 0, s>>>(c->nodes.as<double>(), c->tets.as<int32_t>(),
+                                                            c->sigma.as<double>(), T, B, lcount, tet_slot, dsig, lpts);
+    c->launches += 2;
+    PG_CUDA(cudaGetLastError());
+    for (int64_t i = 0; i < S; ++i) PG_TRY(layered_primary(c, c->src[i], n_pts, lpts, Ep + i * n_pts * 3));
+  }
   for (int s0 = 0; s0 < S; s0 += chunk) {
     int n_chunk = (int)std::min<int64_t>(chunk, S - s0);
     {
       KernelTimer kt(c, "rhs", (double)T * n_chunk * 6 * 16);
-      k_rhs<<<blocks_for(T * n_chunk, 128), 128, 0, s>>>(c->nodes.as<double>(), c->tets.as<int32_t>(),
-                                                          c->signs.as<int8_t>(), c->sigma.as<double>(), T, c->sigma_p,
-                                                          c->omega, dsrc + s0, n_chunk, be);
+      if (c->bg_layers > 0)
+        k_rhs_layered<<<blocks_for(T * n_chunk, 128), 128, 0, s>>>(c->nodes.as<double>(), c->tets.as<int32_t>(),
+                                                                    c->signs.as<int8_t>(), dsig, tet_slot, T,
+                                                                    c->omega, Ep, n_pts, s0, n_chunk, be);
+      else
+        k_rhs<<<blocks_for(T * n_chunk, 128), 128, 0, s>>>(c->nodes.as<double>(), c->tets.as<int32_t>(),
+                                                            c->signs.as<int8_t>(), c->sigma.as<double>(), T,
+                                                            c->sigma_p, c->omega, dsrc + s0, n_chunk, be);
       c->launches++;
     }
     PG_CUDA(cudaGetLastError());
@@ -282,6 +403,13 @@ Status build_rhs(petgem_ctx* c) {
   }
   PG_CUDA(cudaFreeAsync(be, s));
   PG_CUDA(cudaFreeAsync(dsrc, s));
+  if (c->bg_layers > 0) {
+    PG_CUDA(cudaFreeAsync(lcount, s));
+    PG_CUDA(cudaFreeAsync(tet_slot, s));
+    PG_CUDA(cudaFreeAsync(dsig, s));
+    PG_CUDA(cudaFreeAsync(lpts, s));
+    PG_CUDA(cudaFreeAsync(Ep, s));
+  }
   PG_TRY(check_flags(c, "petgem_assemble"));
   return Status{};
 }

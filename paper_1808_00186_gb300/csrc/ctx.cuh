@@ -89,6 +89,11 @@ struct petgem_ctx {
   bool assembled = false;
   int64_t assembly_version = 0;
   double freq = 0.0, omega = 0.0, sigma_p = 1.0;
+  // layered background (petgem_assemble_layered): bg_layers > 0 layers top first, their
+  // interfaces (decreasing z) and conductivities; 0 = the homogeneous background sigma_p
+  int32_t bg_layers = 0;
+  double bg_z[7] = {0, 0, 0, 0, 0, 0, 0};
+  double bg_sig[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int32_t n_src = 0;
   std::vector<petgem_dipole> src;
   petgem::DevBuf sigma, K21, M21, vol;
@@ -150,6 +155,8 @@ Status run_solve_cocg(petgem_ctx* c, const petgem_solve_opts& o, double2* x, pet
 Status run_solve_batch(petgem_ctx* const* ctxs, int n_ctx, const petgem_solve_opts& o, double2* const* x,
                        petgem_solve_info* info);
 Status run_spmv(petgem_ctx* c, const double2* x, double2* y);
+// Primary field of dipole src in the context's layered background at n device points (layered.cu).
+Status layered_primary(petgem_ctx* c, const petgem_dipole& src, int64_t n, const double* pts, double2* out);
 Status ssor_colouring(petgem_ctx* c);
 Status run_solve_ssor(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info);
 Status run_ssor_apply(petgem_ctx* c, double omega, const double2* r, double2* z);

@@ -53,7 +53,8 @@ __global__ void k_rcv_eval(const double* __restrict__ nodes, const int32_t* __re
                            const int32_t* __restrict__ tet_edges, const int8_t* __restrict__ signs,
                            const double* __restrict__ rx, int n_rcv, const int32_t* __restrict__ found,
                            const double2* __restrict__ xs, int64_t n_edges, int n_src, const double* __restrict__ src5,
-                           double sigma_p, double kappa, double2* __restrict__ out) {
+                           double sigma_p, double kappa, const double2* __restrict__ ep_pre,
+                           double2* __restrict__ out) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)n_src * n_rcv) return;
   int s = (int)(idx / n_rcv), r = (int)(idx - (int64_t)s * n_rcv);
@@ -86,7 +87,11 @@ __global__ void k_rcv_eval(const double* __restrict__ nodes, const int32_t* __re
   const double* sp = src5 + 5 * s;
   double dv[3] = {x[0] - sp[0], x[1] - sp[1], x[2] - sp[2]};
   double2 Ep[3];
-  dipole_field(dv, (int)sp[4], sp[3], sigma_p, kappa, Ep);
+  if (ep_pre) {  // layered background: E_p computed beforehand at the receivers
+    for (int dd = 0; dd < 3; ++dd) Ep[dd] = ep_pre[idx * 3 + dd];
+  } else {
+    dipole_field(dv, (int)sp[4], sp[3], sigma_p, kappa, Ep);
+  }
   for (int dd = 0; dd < 3; ++dd) {
     o[dd] = Ep[dd];
     o[3 + dd] = Es[dd];
@@ -131,13 +136,19 @@ Status run_receivers(petgem_ctx* c, int32_t n_rcv, const double* rx, const doubl
     }
   PG_CUDA(cudaMemcpyAsync(found, hf.data(), n_rcv * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   const double kappa = sqrt(c->omega * phys::kMu0 * c->sigma_p * 0.5);
+  double2* ep = nullptr;
+  if (c->bg_layers > 0) {  // layered background: E_p of every source at every receiver
+    PG_CUDA(cudaMallocAsync((void**)&ep, (size_t)c->n_src * n_rcv * 3 * sizeof(double2), s));
+    for (int i = 0; i < c->n_src; ++i) PG_TRY(layered_primary(c, c->src[i], n_rcv, rx, ep + (int64_t)i * n_rcv * 3));
+  }
   k_rcv_eval<<<blocks_for((int64_t)c->n_src * n_rcv, 128), 128, 0, s>>>(
       c->nodes.as<double>(), c->tets.as<int32_t>(), c->tet_edges.as<int32_t>(), c->signs.as<int8_t>(), rx, n_rcv,
-      found, x, c->n_edges, c->n_src, src5, c->sigma_p, kappa, out);
+      found, x, c->n_edges, c->n_src, src5, c->sigma_p, kappa, ep, out);
   c->launches++;
   PG_CUDA(cudaGetLastError());
   PG_CUDA(cudaFreeAsync(found, s));
   PG_CUDA(cudaFreeAsync(src5, s));
+  if (ep) PG_CUDA(cudaFreeAsync(ep, s));
   PG_CUDA(cudaStreamSynchronize(s));
   return Status{};
 }

@@ -85,3 +85,21 @@ def test_conv_grids_whose_voxel_count_wraps_are_rejected_on_the_host(lib_path):
     assert L.petgem_nn_conv3d_wgrad(None, big, big, big, 16, 16, fake, fake, fake) == api.ERR_UNSUPPORTED
     assert L.petgem_nn_conv3d_wgrad(None, 1024, 1024, 64, 16, 16, fake, fake, fake) == api.ERR_UNSUPPORTED
     assert L.petgem_nn_conv3d(None, big, big, big, 16, 16, fake, fake, fake, 0, fake, 1) == api.ERR_UNSUPPORTED
+
+
+def test_layered_primary_field_checks_its_arguments_on_the_host(lib_path):
+    L = api.load(lib_path)
+    d = api.petgem_dipole(0.0, 0.0, 50.0, 1.0, 0, 0)
+    dz = api.petgem_dipole(0.0, 0.0, 50.0, 1.0, 2, 0)
+    zi = (ctypes.c_double * 2)(0.0, -100.0)
+    zbad = (ctypes.c_double * 2)(0.0, 10.0)
+    sg = (ctypes.c_double * 3)(3.3, 1.0, 0.01)
+    sneg = (ctypes.c_double * 3)(3.3, -1.0, 0.01)
+    fake = ctypes.c_void_p(256)  # never dereferenced
+    assert L.petgem_primary_layered(None, 3, zi, sg, 1.0, ctypes.byref(d), 0, None, None) == api.OK
+    assert L.petgem_primary_layered(None, 3, zbad, sg, 1.0, ctypes.byref(d), 4, fake, fake) == api.ERR_INVALID_ARG
+    assert L.petgem_primary_layered(None, 3, zi, sneg, 1.0, ctypes.byref(d), 4, fake, fake) == api.ERR_INVALID_ARG
+    assert L.petgem_primary_layered(None, 3, zi, sg, 0.0, ctypes.byref(d), 4, fake, fake) == api.ERR_INVALID_ARG
+    assert L.petgem_primary_layered(None, 3, zi, sg, 1.0, ctypes.byref(dz), 4, fake, fake) == api.ERR_UNSUPPORTED
+    assert L.petgem_primary_layered(None, 9, zi, sg, 1.0, ctypes.byref(d), 4, fake, fake) == api.ERR_UNSUPPORTED
+    assert L.petgem_primary_layered(None, 3, zi, sg, 1.0, ctypes.byref(d), 4, None, fake) == api.ERR_INVALID_ARG

@@ -132,3 +132,20 @@ def test_quadrature_rule_and_layer_lookup():
     assert np.diff(LY.panel_edges(2000.0, 50.0, 1e-3)).max() <= math.pi / 2000.0 * (1 + 1e-12)
     z_if = np.array([0.0, -100.0])
     assert [LY.layer_of(z, z_if) for z in (5.0, 0.0, -50.0, -100.0, -101.0)] == [0, 0, 1, 1, 2]
+
+
+def test_layered_rhs_with_equal_layers_is_the_assembled_whole_space_rhs():
+    """The layered right-hand side restated in Python equals the C++ oracle's assembled b (its own
+    whole-space field and quadrature, pinned elsewhere) when every layer has the background
+    conductivity."""
+    from paper_1808_00186_gb300 import synth
+    m = synth.kuhn_mesh(3, (-600.0, -600.0, -600.0), (600.0, 600.0, 600.0), jitter=0.1)
+    cen = m.centroids()
+    sigma = np.where(np.all(np.abs(cen - 150.0) < 250.0, axis=1), 0.05, 1.3)
+    srcs = [(20.0, -10.0, 400.0, 0, 1.0), (-30.0, 15.0, 420.0, 1, 2.0)]
+    ref = oracle.System(m.nodes, m.tets, sigma, 1.3, 1.5, np.array(srcs))
+    edges, te, sg, bd = ref.topology()
+    b_ref = ref.system()[3]
+    b = LY.rhs(m.nodes, m.tets, sigma, [100.0, -200.0], [1.3, 1.3, 1.3], 1.5, srcs, te, sg, bd, ref.n_edges)
+    assert np.abs(b_ref).max() > 0
+    assert rel(b, b_ref) <= 1e-10
