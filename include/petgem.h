@@ -94,14 +94,18 @@ typedef struct {
   int64_t max_iters;   /* cap on Krylov iterations per source */
   int32_t orth;        /* Arnoldi orthogonalisation: PETGEM_ORTH_CGS (default), _CGS2, _CGS_IFNEEDED */
   int32_t use_graphs;  /* 1 = replay each GMRES restart cycle as a CUDA graph, captured once per
-                          solve configuration (Jacobi preconditioner; ignored with the learned
-                          one, while kernel profiling is on, and by COCG, whose iterations run in
-                          one persistent kernel); results are identical to direct launches */
+                          solve configuration (Jacobi or learned preconditioner; ignored while
+                          kernel profiling is on, and by COCG, whose iterations run in one
+                          persistent kernel); results are identical to direct launches */
   int32_t method;      /* PETGEM_METHOD_GMRES (default), PETGEM_METHOD_COCG or PETGEM_METHOD_SQMR */
   int32_t spmv_lanes;  /* petgem_solve_batch: layout of the sparse product: 2, 4 or 8 = CSR with that
                           many lanes per row, 1 = SELL-32 with rows grouped by edge kind (CSR with
-                          4 lanes when a mesh lacks that layout); 0 = chosen by the autotuner;
-                          ignored by petgem_solve (which uses SELL-32 when the mesh has it) */
+                          4 lanes when a mesh lacks that layout); 0 = chosen by the autotuner.
+                          petgem_solve with several sources iterated together (batch != 1): the
+                          block SpMM, 0 = chosen by the autotuner, 1 = one lane per (row, source),
+                          16 / 32 / 64 = the staged kernel with that band height (other values:
+                          PETGEM_ERR_UNSUPPORTED); ignored by single-source solves (which use
+                          SELL-32 when the mesh has it) */
   double omega;        /* SSOR relaxation factor, 0 < omega < 2; 0 = 1 (symmetric Gauss-Seidel) */
 } petgem_solve_opts;
 
@@ -141,7 +145,11 @@ typedef struct {
   int32_t reorth;      /* Arnoldi steps that needed a second Gram-Schmidt pass */
   int32_t fell_back;   /* learned preconditioner: 1 if the solve switched back to Jacobi */
   int32_t spmv_lanes;  /* petgem_solve_batch: the product's layout it ran with (as in the options:
-                          1 = SELL-32, 2 / 4 / 8 = CSR lanes per row); 0 otherwise */
+                          1 = SELL-32, 2 / 4 / 8 = CSR lanes per row).  Multi-source block solves
+                          (batch != 1): the block SpMM the autotuner chose for this mesh and group
+                          size, 16 / 32 / 64 = the band height of the staged kernel (each band's
+                          distinct rows of the block vector copied to shared memory once), 1 = one
+                          lane per (row, source) reading the block vector directly.  0 otherwise */
 } petgem_solve_info;
 
 /* ----------------------------------------------------------------------- lifecycle */

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpetgem.so")
-SOURCES = ["topology.cu", "assembly.cu", "krylov.cu", "block.cu", "learned.cu", "receivers.cu", "api.cu", "noalloc.cu", "cocg.cu", "sell.cu", "ssor.cu", "layered.cu"]
+SOURCES = ["topology.cu", "assembly.cu", "krylov.cu", "block.cu", "learned.cu", "receivers.cu", "api.cu", "noalloc.cu", "cocg.cu", "sell.cu", "ssor.cu", "layered.cu", "bands.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I" + INCLUDE, "-I" + CSRC, "--expt-relaxed-constexpr"]

@@ -13,6 +13,7 @@
 
 #include "krylov.cuh"
 #include "gs.cuh"
+#include "bands.cuh"
 
 namespace petgem {
 namespace {
@@ -63,6 +64,21 @@ __device__ inline void store_scaled(double2* y, double2 acc, const GState& g, in
   *y = make_double2(acc.x * f, acc.y * f);
 }
 
+// Epilogue of the staged SpMM for block GMRES: V_{j+1} = (Ahat V_j) / ||V_j|| per source, zero for a
+// source whose cycle stopped (as k_bspmm).
+struct SpmmStoreGmres {
+  const GState* sts;
+  int j;
+  template <typename T>
+  __device__ void operator()(T* Y, int64_t row, int s, int P, typename Acc<T>::type acc) const {
+    const GState& g = sts[s];
+    if (g.done)
+      Y[row * P + s] = zero<T>();
+    else
+      store_scaled(&Y[row * P + s], acc, g, j);
+  }
+};
+
 // Per-source sums of partials[b * P + s] over b < nb with the whole block (P divides 256); the
 // results land in out[0..P) (shared memory), visible after the call.
 template <int P>
@@ -95,6 +111,7 @@ __global__ void __launch_bounds__(256) k_bresidual(const int64_t* __restrict__ r
   for (int64_t p = rp[row]; p < rp[row + 1]; ++p) fma_c(acc, __ldg(&val[p]), U[(int64_t)__ldg(&col[p]) * P + s]);
   R[row * P + s] = csub(B[row * P + s], acc);
 }
+
 
 // Y = (Ahat X) diag(1 / ||X_s||), zero for stopped sources.  P lanes per row, lane = source: the
 // row's entries are read by the whole lane group (one broadcast transaction) four at a time, all
@@ -294,6 +311,27 @@ Status run_group(petgem_ctx* c, const petgem_solve_opts& o, const double2* b, do
     if (i >= S_g || bn2[i] == 0.0) finished[i] = 1;
   std::vector<HostState> hs(P);
   const unsigned spmm_grid = blocks_for(n * P, 256);
+  // SpMM form for this mesh and group size: the autotuner times the row-per-lane kernel and the
+  // staged band kernels on the basis buffers (before the first cycle writes them) and caches the
+  // choice; the states are zero here, so every launch runs in full.
+  int spmm_form = -1;
+  if (o.spmv_lanes == 0) {
+    PG_TRY((tune_spmm<T, P>(c, s, ahat, V, V + ldb,
+                            [&]() -> Status {
+                              PG_CUDA(pdl_launch(k_bspmm<T, P>, dim3(spmm_grid), dim3(256), 0, s, false,
+                                                 (const int64_t*)c->row_ptr.as<int64_t>(),
+                                                 (const int32_t*)c->col.as<int32_t>(), ahat, (const T*)V, V + ldb, n,
+                                                 (const GState*)sts, (const BGroup*)grp, 0));
+                              return Status{};
+                            },
+                            &spmm_form)));
+  } else if (o.spmv_lanes != 1) {
+    spmm_form = o.spmv_lanes == 16 ? 0 : o.spmv_lanes == 32 ? 1 : o.spmv_lanes == 64 ? 2 : -2;
+    if (spmm_form < 0) return Status{PETGEM_ERR_UNSUPPORTED, "block SpMM: spmv_lanes must be 0, 1, 16, 32 or 64"};
+    PG_TRY(band_layout(c, spmm_form));
+    if ((size_t)c->bands[spmm_form].max_u * P * sizeof(T) > kBandSmemMax)
+      return Status{PETGEM_ERR_UNSUPPORTED, "block SpMM: the bands of this height are too wide"};
+  }
   const double spmm_bytes = (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 2.0 * n * P * sizeof(T);
   int64_t max_done = 0;
   while (true) {
@@ -311,9 +349,13 @@ Status run_group(petgem_ctx* c, const petgem_solve_opts& o, const double2* b, do
       T* vj = V + (int64_t)j * ldb;
       {
         KernelTimer kt(c, sizeof(T) == 8 ? "bspmm_c64" : "bspmm_c128", spmm_bytes);
-        PG_CUDA(pdl_launch(k_bspmm<T, P>, dim3(spmm_grid), dim3(256), 0, s, false,
-                           (const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), ahat,
-                           (const T*)vj, vj + ldb, n, (const GState*)sts, (const BGroup*)grp, j));
+        if (spmm_form >= 0)
+          PG_TRY((launch_spmm_band<T, P>(c, s, spmm_form, ahat, (const T*)vj, vj + ldb, &grp->all_done,
+                                         SpmmStoreGmres{sts, j})));
+        else
+          PG_CUDA(pdl_launch(k_bspmm<T, P>, dim3(spmm_grid), dim3(256), 0, s, false,
+                             (const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), ahat,
+                             (const T*)vj, vj + ldb, n, (const GState*)sts, (const BGroup*)grp, j));
       }
       {
         KernelTimer kt(c, sizeof(T) == 8 ? "bmdot_c64" : "bmdot_c128", (double)(j + 2) * n * P * sizeof(T));
@@ -374,6 +416,7 @@ Status run_group(petgem_ctx* c, const petgem_solve_opts& o, const double2* b, do
     info[i].refinements = cycles[i];
     info[i].true_rel_residual = bn2[i] == 0.0 ? 0.0 : relres[i];
     info[i].status = status[i];
+    info[i].spmv_lanes = spmm_form >= 0 ? kBandHeights[spmm_form] : 1;
   }
   return Status{};
 }

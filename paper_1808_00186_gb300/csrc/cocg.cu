@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "krylov.cuh"
+#include "bands.cuh"
 
 namespace petgem {
 namespace {
@@ -1202,6 +1203,7 @@ __global__ void __launch_bounds__(kBcgThreads) k_bcg_start(const double2* __rest
   }
 }
 
+
 // Q = Atil Pm for all P sources: the row's entries read by its lane group four at a time (the
 // wavefront form of the block GMRES SpMM).
 template <typename T, int P>
@@ -1411,10 +1413,30 @@ Status cocg_group(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, const
     if (i >= S_g || bn[i] == 0.0) finished[i] = 1;
   }
   const int chunk = std::max(1, o.restart);
-  const unsigned spmm_grid = blocks_for(nP, 256);
   const double vb = (double)nP * sizeof(T);
   const double spmm_bytes = (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 2.0 * vb;
   int64_t max_done = 0;
+  const unsigned spmm_grid = blocks_for(nP, 256);
+  // SpMM form for this mesh and group size (autotuned on the direction and product buffers before
+  // the first inner solve writes them; the group state is zero, so every launch runs in full)
+  int spmm_form = -1;
+  if (o.spmv_lanes == 0) {
+    PG_TRY((tune_spmm<T, P>(c, s, at, pm, q,
+                            [&]() -> Status {
+                              PG_CUDA(pdl_launch(k_bcg_spmm<T, P>, dim3(spmm_grid), dim3(256), 0, s, false,
+                                                 (const int64_t*)c->row_ptr.as<int64_t>(),
+                                                 (const int32_t*)c->col.as<int32_t>(), at, (const T*)pm, q, n,
+                                                 (const BGrp*)grp));
+                              return Status{};
+                            },
+                            &spmm_form)));
+  } else if (o.spmv_lanes != 1) {
+    spmm_form = o.spmv_lanes == 16 ? 0 : o.spmv_lanes == 32 ? 1 : o.spmv_lanes == 64 ? 2 : -2;
+    if (spmm_form < 0) return Status{PETGEM_ERR_UNSUPPORTED, "block SpMM: spmv_lanes must be 0, 1, 16, 32 or 64"};
+    PG_TRY(band_layout(c, spmm_form));
+    if ((size_t)c->bands[spmm_form].max_u * P * sizeof(T) > kBandSmemMax)
+      return Status{PETGEM_ERR_UNSUPPORTED, "block SpMM: the bands of this height are too wide"};
+  }
   while (true) {
     {
       KernelTimer kt(c, "bcg_residual_c128", (double)c->nnz * 20 + 48.0 * nP);
@@ -1472,9 +1494,12 @@ Status cocg_group(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, const
       for (int64_t k = 0; k < steps; ++k) {
         {
           KernelTimer kt(c, c128 ? "bcg_spmm_c128" : "bcg_spmm_c64", spmm_bytes);
-          PG_CUDA(pdl_launch(k_bcg_spmm<T, P>, dim3(spmm_grid), dim3(256), 0, s, false,
-                             (const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), at,
-                             (const T*)pm, q, n, (const BGrp*)grp));
+          if (spmm_form >= 0)
+            PG_TRY((launch_spmm_band<T, P>(c, s, spmm_form, at, (const T*)pm, q, &grp->all_done, SpmmStorePlain{})));
+          else
+            PG_CUDA(pdl_launch(k_bcg_spmm<T, P>, dim3(spmm_grid), dim3(256), 0, s, false,
+                               (const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), at,
+                               (const T*)pm, q, n, (const BGrp*)grp));
         }
         {
           KernelTimer kt(c, c128 ? "bcg_pq_c128" : "bcg_pq_c64", 2.0 * vb);
@@ -1524,6 +1549,7 @@ Status cocg_group(petgem_ctx* c, const petgem_solve_opts& o, CgBuffers* B, const
     info[i].refinements = solves[i];
     info[i].true_rel_residual = relres[i];
     info[i].status = status[i];
+    info[i].spmv_lanes = spmm_form >= 0 ? kBandHeights[spmm_form] : 1;
   }
   return Status{};
 }

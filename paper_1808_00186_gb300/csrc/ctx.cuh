@@ -49,6 +49,16 @@ struct PendingTiming {
   int pass;   // 0: runs whenever the cycle is alive, 1: only when that step re-orthogonalised
 };
 
+// Band layout of the CSR pattern for the staged block SpMM (bands.cu): bands of R consecutive
+// rows, each band's sorted distinct columns (ucol, band b at off[b] .. off[b + 1]) and, per
+// nonzero, its index in its band's list (lcol).
+struct BandLayout {
+  int64_t version = -1;  // mesh version the layout belongs to
+  int64_t nb = 0;        // bands
+  int max_u = 0;         // most distinct columns of one band
+  DevBuf off, ucol, lcol;
+};
+
 struct Solver;  // Krylov workspaces (krylov.cu)
 namespace nn {
 struct Net;  // learned preconditioner (learned.cu)
@@ -103,6 +113,12 @@ struct petgem_ctx {
   // ---- solver state (krylov.cu)
   petgem::Solver* solver = nullptr;
 
+  // ---- staged block SpMM (bands.cu): layouts for band heights 16, 32, 64 and the autotuner's
+  // choice per (mesh, rows, nonzeros, sources, value size): -1 the row-per-lane kernel, else the
+  // index of the band height
+  petgem::BandLayout bands[3];
+  std::map<uint64_t, int> spmm_choice;
+
   // ---- learned preconditioner (learned.cu): network, edge -> grid slots of the current mesh
   petgem::nn::Net* net = nullptr;
   void* cocg = nullptr;  // COCG solver workspaces (cocg.cu)
@@ -155,6 +171,8 @@ Status run_solve_cocg(petgem_ctx* c, const petgem_solve_opts& o, double2* x, pet
 Status run_solve_batch(petgem_ctx* const* ctxs, int n_ctx, const petgem_solve_opts& o, double2* const* x,
                        petgem_solve_info* info);
 Status run_spmv(petgem_ctx* c, const double2* x, double2* y);
+// Band layout for band height kBandHeights[which] of the current mesh (bands.cu).
+Status band_layout(petgem_ctx* c, int which);
 // Primary field of dipole src in the context's layered background at n device points (layered.cu).
 Status layered_primary(petgem_ctx* c, const petgem_dipole& src, int64_t n, const double* pts, double2* out);
 Status ssor_colouring(petgem_ctx* c);
