@@ -313,7 +313,8 @@ def snap_interfaces(axis: np.ndarray, interfaces) -> np.ndarray:
 
 def graded_marine_model(freq: float = 1.0, L_s: float = 250.0, r_delta: float = 3.0, r_s: float = 13.0,
                         r_xy: float = 8.0, r_z: float = 4.0, r_b: float = 4.0, sigma_min_depth: float = 3.3,
-                        sigma_ave: float = 1.0, n_src: int = 1) -> Model:
+                        sigma_ave: float = 1.0, n_src: int = 1, reservoir: bool = True,
+                        z_surface: float = 1000.0) -> Model:
     """The marine model of marine_model on a frequency-adapted graded Kuhn mesh (Section 5.3).
 
     Spacings: d_delta = delta_min / r_delta with delta_min the skin depth in seawater; near the
@@ -323,14 +324,14 @@ def graded_marine_model(freq: float = 1.0, L_s: float = 250.0, r_delta: float = 
     layers of r_b delta_ave on every other side.  delta_ave is the skin depth at sigma_ave (the
     sediment).  The core is centred on the (first) source.  Conductivities, sources and receivers
     as in marine_model (seawater 3.3 S/m above z = 0 up to the surface at z = 1000 m, sediment
-    1 S/m, the 0.01 S/m reservoir slab 1 km down)."""
+    1 S/m, the 0.01 S/m reservoir slab 1 km down; reservoir=False leaves the two half-spaces alone,
+    z_surface moves the top of the domain)."""
     d_min = skin_depth(freq, sigma_min_depth)
     d_ave = skin_depth(freq, sigma_ave)
     d_delta = d_min / r_delta
     d_s = min(L_s / r_s, d_delta)
     xs_src = [0.0] if n_src == 1 else list(np.linspace(-4000.0, 4000.0, n_src))
     src = (xs_src[0], 0.0, 50.0)
-    z_surface = 1000.0
     tb = r_b * d_ave
     ax = graded_axis(src[0], src[0] - r_xy * d_ave, src[0] + r_xy * d_ave, d_s, d_delta, tb, tb)
     ay = graded_axis(src[1], src[1] - r_xy * d_ave, src[1] + r_xy * d_ave, d_s, d_delta, tb, tb)
@@ -342,7 +343,8 @@ def graded_marine_model(freq: float = 1.0, L_s: float = 250.0, r_delta: float = 
     mesh = kuhn_mesh_axes([ax, ay, az])
     cen = mesh.centroids()
     sigma = np.where(cen[:, 2] > 0.0, 3.3, 1.0)
-    _boxes(cen, sigma, [((-1000, 1000, -1000, 1000, -1100, -1000), 0.01)])
+    if reservoir:
+        _boxes(cen, sigma, [((-1000, 1000, -1000, 1000, -1100, -1000), 0.01)])
     rx = np.stack([np.linspace(-4000.0, 4000.0, 101), np.zeros(101), np.zeros(101)], axis=1)
     return Model("graded_marine_%gHz" % freq, mesh, sigma, 3.3, freq,
                  [Dipole(x, 0.0, 50.0, 0, 1.0) for x in xs_src], rx,
