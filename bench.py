@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--profile-step", action="store_true",
                    help="run one untimed step of the hot path and exit (the command profilers capture)")
     p.add_argument("--precision", default="mixed", choices=["mixed", "c128"], help="solver of --profile-step")
-    p.add_argument("--solver", default="gmres", choices=["gmres", "cocg", "ssor"],
+    p.add_argument("--solver", default="gmres", choices=["gmres", "cocg", "ssor", "learned"],
                    help="Krylov method of --profile-step / --profile-block (ssor: SQMR with the SSOR preconditioner)")
     p.add_argument("--no-cocg", action="store_true", help="skip the COCG measurement")
     p.add_argument("--no-batch", action="store_true", help="skip the batch of uneven meshes")
@@ -259,9 +259,15 @@ def run_ours(args):
     if args.profile_block and args.solver == "ssor":
         raise SystemExit("--profile-block runs GMRES or COCG")
     if args.profile_step:
-        method = {"gmres": api.METHOD_GMRES, "cocg": api.METHOD_COCG, "ssor": api.METHOD_SQMR}[args.solver]
-        info, _ = step(api.PREC_MIXED if args.precision == "mixed" else api.PREC_C128, method,
-                       precond=api.PRECOND_SSOR if args.solver == "ssor" else api.PRECOND_JACOBI)
+        method = {"gmres": api.METHOD_GMRES, "cocg": api.METHOD_COCG, "ssor": api.METHOD_SQMR,
+                  "learned": api.METHOD_GMRES}[args.solver]
+        pc = {"ssor": api.PRECOND_SSOR, "learned": api.PRECOND_LEARNED}.get(args.solver, api.PRECOND_JACOBI)
+        if pc == api.PRECOND_LEARNED:
+            from paper_1808_00186_gb300 import learned as PL
+            api.petgem_mesh_edges(ctx.h, nodes, tets)
+            api.petgem_learned_create(ctx.h, args.n, args.n, args.n)
+            api.petgem_learned_params(ctx.h, set_params=np.load(PL.WEIGHTS))
+        info, _ = step(api.PREC_MIXED if args.precision == "mixed" else api.PREC_C128, method, precond=pc)
         torch.cuda.synchronize()
         print(json.dumps({"profile_step": True, "n": args.n, "edges": n_edges[0], "info": info,
                           "launches": api.petgem_launch_count(ctx.h)}))
