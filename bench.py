@@ -72,20 +72,6 @@ def tensor_peak():
         return 1900.0, "fallback"
 
 
-def fp32_alu_peak(device):
-    """FP32 FMA peak of the CUDA cores from unit counts: SMs x 128 FP32 lanes x 2 flops x the
-    maximum SM clock (measured, else the GB300's 2070 MHz)."""
-    import torch
-    sms = torch.cuda.get_device_properties(device).multi_processor_count
-    mhz = 2070.0
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            mhz = float(json.load(f).get("sm_max_mhz", mhz))
-    except (OSError, ValueError):
-        pass
-    return round(sms * 128 * 2 * mhz * 1e6 / 1e12, 1), "%d SMs x 128 FP32 FMA/clk x 2 x %.0f MHz" % (sms, mhz)
-
-
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -276,7 +262,6 @@ def run_ours(args):
 
     hbm, peak_kind = peaks()
     bf16_peak = tensor_peak()
-    fp32_peak = fp32_alu_peak(local)
     clocks = ClockSampler(local)
     # The learned auxiliary-space preconditioner: the network trained at the 2000-model 32^3 scale
     # (paper_1808_00186_gb300/weights), fully convolutional, applied here on the 65^3 node grid.
@@ -298,7 +283,7 @@ def run_ours(args):
     # kernels carry algorithmic bytes, the convolutions floating-point operations.
     kstats = {}
     for name in ("spmv_c64", "mdot_c64", "cgs_dot2_c64", "cgs_upd_c64", "cgs_upd2_c64", "cycle_init_c64",
-                 "xupdate_c64", "residual_c128", "hx_in_c64", "hx_out_c64", "conv3d_fwd", "conv3d_small_fwd",
+                 "xupdate_c64", "residual_c128", "hx_in_c64", "hx_out_c64", "conv3d_fwd",
                  "element", "matrix_gather", "rhs", "rcv_locate"):
         n, kms, by = api.petgem_kernel_stats(ctx.h, name)
         if n:
@@ -634,7 +619,7 @@ def run_ours(args):
         del x1
 
     # The learned preconditioner in the headline step: apply time and the convolutions' rates
-    # (tensor-core levels against the BF16 peak; the small coarse levels run on the CUDA cores).
+    # (all levels on the tensor cores, against the BF16 peak).
     learned = None
     if n_apply:
         conv = kstats.get("conv3d_fwd")
@@ -685,17 +670,16 @@ def run_ours(args):
             name, ks = dom
             achieved = ks["rate"]
             flops = ks["unit"] == "flop"
-            alu = name == "conv3d_small_fwd"  # FP32 FMAs on the CUDA cores
-            bound = "alu" if alu else "tensor" if flops else "hbm"
-            peak = fp32_peak[0] if alu else bf16_peak[0] if flops else hbm
+            bound = "tensor" if flops else "hbm"
+            peak = bf16_peak[0] if flops else hbm
             roof = {"kernel": name, "bound": bound, "achieved": round(achieved, 2),
                     "peak": peak, "unit": "TFLOP/s" if flops else "GB/s", "frac": round(achieved / peak, 4),
-                    "peak_source": fp32_peak[1] if alu else bf16_peak[1] if flops else peak_kind,
+                    "peak_source": bf16_peak[1] if flops else peak_kind,
                     "traffic": (round(TRAFFIC_RATIO[name] * ks["bytes"] / ks["launches"]) if name in TRAFFIC_RATIO
                                 else None),
                     "traffic_unit": "bytes per launch (ncu DRAM read+write)",
                     "launches": ks["launches"], "avg_launch_us": round(ks["ms"] / ks["launches"] * 1e3, 2),
-                    ("algorithmic_flops_per_launch" if tensor else "algorithmic_bytes_per_launch"):
+                    ("algorithmic_flops_per_launch" if flops else "algorithmic_bytes_per_launch"):
                         ks["bytes"] / ks["launches"]}
         result = {
             "metric": METRIC,

@@ -358,9 +358,11 @@ int petgem_learned_apply(petgem_ctx *ctx, const void *r, void *z);
  * {16, 32}.  petgem_nn_conv3d: y[v][co] = bias[co] + sum_t,ci W[t][co][ci] x[v + d_t][ci], ReLU
  * when relu != 0, y BF16 (y_fp32 = 0) or FP32 [V][cout].  petgem_nn_conv3d_wgrad: dw[t][co][ci] =
  * sum_v dy[v][co] x[v + d_t][ci] (FP32).  All pointers device; work ordered on `stream`.
- * Errors: a dimension < 1 or a null pointer: PETGEM_ERR_INVALID_ARG; gx gy gz 32 >= 2^31 (the
- * kernels index voxel channels in 32 bits) or cin / cout not in {16, 32}: PETGEM_ERR_UNSUPPORTED,
- * nothing launched. */
+ * petgem_nn_conv3d's x, w and y must be 16-byte aligned (the kernel moves 8 channels at a time;
+ * its input reaches shared memory through a TMA tensor map).
+ * Errors: a dimension < 1, a null pointer, or (petgem_nn_conv3d) an x, w or y not 16-byte
+ * aligned: PETGEM_ERR_INVALID_ARG; gx gy gz 32 >= 2^31 (the kernels index voxel channels in 32
+ * bits) or cin / cout not in {16, 32}: PETGEM_ERR_UNSUPPORTED, nothing launched. */
 int petgem_nn_conv3d(void *stream, int32_t gx, int32_t gy, int32_t gz, int32_t cin, int32_t cout, const void *x,
                      const void *w, const float *bias, int32_t relu, void *y, int32_t y_fp32);
 int petgem_nn_conv3d_wgrad(void *stream, int32_t gx, int32_t gy, int32_t gz, int32_t cin, int32_t cout, const void *x,

@@ -584,15 +584,25 @@ int petgem_nn_conv3d(void* stream, int32_t gx, int32_t gy, int32_t gz, int32_t c
                      const void* w, const float* bias, int32_t relu, void* y, int32_t y_fp32) {
   if (gx < 1 || gy < 1 || gz < 1 || !x || !w || !bias || !y) return PETGEM_ERR_INVALID_ARG;
   if (!petgem::nn::grid_fits(gx, gy, gz)) return PETGEM_ERR_UNSUPPORTED;
+  if ((cin != 16 && cin != 32) || (cout != 16 && cout != 32)) return PETGEM_ERR_UNSUPPORTED;
+  if (((uintptr_t)x | (uintptr_t)w | (uintptr_t)y) & 15) return PETGEM_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int* err = nullptr;
+  __nv_bfloat16* wc = nullptr;  // the weights as the kernel's shared-memory image
+  const int nw = 27 * cin * cout;
   if (cudaMallocAsync((void**)&err, sizeof(int), s) != cudaSuccess) return PETGEM_ERR_OUT_OF_MEMORY;
+  if (cudaMallocAsync((void**)&wc, nw * sizeof(__nv_bfloat16), s) != cudaSuccess) {
+    cudaFreeAsync(err, s);
+    return PETGEM_ERR_OUT_OF_MEMORY;
+  }
   cudaMemsetAsync(err, 0, sizeof(int), s);
-  Status st = petgem::nn::conv3d(s, gx, gy, gz, cin, cout, static_cast<const __nv_bfloat16*>(x),
-                                 static_cast<const __nv_bfloat16*>(w), bias, relu != 0,
-                                 y_fp32 ? nullptr : static_cast<__nv_bfloat16*>(y),
-                                 y_fp32 ? static_cast<float*>(y) : nullptr, err);
+  Status st = petgem::nn::pack_conv_weights(s, static_cast<const __nv_bfloat16*>(w), cin, cout, wc);
+  if (st.ok())
+    st = petgem::nn::conv3d(s, gx, gy, gz, cin, cout, static_cast<const __nv_bfloat16*>(x), wc, bias,
+                            relu != 0, y_fp32 ? nullptr : static_cast<__nv_bfloat16*>(y),
+                            y_fp32 ? static_cast<float*>(y) : nullptr, err);
   if (st.ok()) st = petgem::nn::check_err(s, err, "petgem_nn_conv3d");
+  cudaFreeAsync(wc, s);
   cudaFreeAsync(err, s);
   return st.code;
 }

@@ -40,19 +40,6 @@ namespace {
 
 constexpr int kIn = 16;
 
-__global__ void k_f32_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) b[i] = __float2bfloat16(a[i]);
-}
-// Wd[t][ci][co] = W[26 - t][co][ci]: the input gradient of a convolution is the convolution of
-// the output gradient with the flipped, transposed kernel.
-__global__ void k_flip_weights(const float* __restrict__ W, int cin, int cout, __nv_bfloat16* __restrict__ Wd) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 27 * cin * cout) return;
-  const int co = idx % cout, ci = (idx / cout) % cin, t = idx / (cout * cin);
-  Wd[idx] = __float2bfloat16(W[((26 - t) * cout + co) * cin + ci]);
-}
-
 __device__ inline void grid_coords(int64_t v, int gx, int gy, int& x, int& y, int& z) {
   x = (int)(v % gx);
   y = (int)((v / gx) % gy);
@@ -586,93 +573,19 @@ unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-// Direct 3x3x3 convolution on the CUDA cores for the network's small coarse grids, where a
-// 128-voxel tensor-core tile would mostly be padding and per-tile set-up.  The block stages the
-// weights transposed to [t][ci][co] in shared memory (a warp's lanes, consecutive output
-// channels, then read consecutive addresses), then walks the outputs (voxel, channel) with a grid
-// stride; FP32 accumulation over BF16 operands, 16-byte loads of 8 input channels.
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(256) k_conv3d_small(const __nv_bfloat16* __restrict__ X,
-                                                      const __nv_bfloat16* __restrict__ W,
-                                                      const float* __restrict__ bias, int gx, int gy, int gz,
-                                                      int relu, __nv_bfloat16* __restrict__ Ybf,
-                                                      float* __restrict__ Yf, const int* __restrict__ stop) {
-  if (stop && *stop) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __nv_bfloat16* ws = reinterpret_cast<__nv_bfloat16*>(smem_raw);  // [27][CIN][COUT]
-  for (int i = threadIdx.x; i < 27 * CIN * COUT; i += 256) {
-    const int ci = i % CIN, co = (i / CIN) % COUT, t = i / (CIN * COUT);  // i indexes W[t][co][ci]
-    ws[(t * CIN + ci) * COUT + co] = W[i];
-  }
-  __syncthreads();
-  const int64_t total = (int64_t)gx * gy * gz * COUT;
-  for (int64_t idx = blockIdx.x * 256 + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * 256) {
-    const int co = (int)(idx % COUT);
-    const int64_t v = idx / COUT;
-    int x, y, z;
-    grid_coords(v, gx, gy, x, y, z);
-    float acc = 0.f;
-    for (int t = 0; t < 27; ++t) {
-      const int nx = x + t % 3 - 1, ny = y + (t / 3) % 3 - 1, nz = z + t / 9 - 1;
-      if (nx < 0 || nx >= gx || ny < 0 || ny >= gy || nz < 0 || nz >= gz) continue;
-      const __nv_bfloat16* xs = X + ((int64_t)nx + gx * ((int64_t)ny + (int64_t)gy * nz)) * CIN;
-      const __nv_bfloat16* wt = ws + t * CIN * COUT + co;
-#pragma unroll
-      for (int c8 = 0; c8 < CIN / 8; ++c8) {
-        const uint4 a = *reinterpret_cast<const uint4*>(xs + 8 * c8);
-        const __nv_bfloat16* pa = reinterpret_cast<const __nv_bfloat16*>(&a);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc = fmaf(__bfloat162float(pa[k]), __bfloat162float(wt[(8 * c8 + k) * COUT]), acc);
-      }
-    }
-    acc += bias[co];
-    if (relu) acc = fmaxf(acc, 0.f);
-    if (Yf)
-      Yf[v * COUT + co] = acc;
-    else
-      Ybf[v * COUT + co] = __float2bfloat16(acc);
-  }
-}
-
-// Grids of at most this many voxels take the direct CUDA-core convolution inside the network.
-// (measured on GB300: at 9^3 and below the direct kernel takes 13-17 us against about 20 us for
-// a tensor-core tile per 128 voxels; at 17^3 the tensor-core kernel is faster)
-constexpr int64_t kSmallConvVoxels = 1024;
-
-Status conv3d_small(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, const __nv_bfloat16* x,
-                    const __nv_bfloat16* w, const float* bias, bool relu, __nv_bfloat16* ybf, float* yf,
-                    const int* stop) {
-  const int64_t V = (int64_t)gx * gy * gz;
-  PG_TRY(conv3d_attributes());
-  int dev = 0, sms = 0;
-  PG_CUDA(cudaGetDevice(&dev));
-  PG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-#define PG_CONVS(CI, CO)                                                                                         \
-  if (cin == CI && cout == CO) {                                                                                 \
-    const unsigned grid = (unsigned)std::min<int64_t>(nb(V * CO, 256), (int64_t)4 * sms);                        \
-    k_conv3d_small<CI, CO><<<grid, 256, 27 * CI * CO * 2, s>>>(x, w, bias, gx, gy, gz, relu ? 1 : 0, ybf, yf, stop); \
-    PG_CUDA(cudaGetLastError());                                                                                 \
-    return Status{};                                                                                             \
-  }
-  PG_CONVS(16, 16)
-  PG_CONVS(16, 32)
-  PG_CONVS(32, 16)
-  PG_CONVS(32, 32)
-#undef PG_CONVS
-  return Status{PETGEM_ERR_UNSUPPORTED, "conv3d_small: channel counts must be 16 or 32"};
-}
-
 // ------------------------------------------------------------ host side
 Status conv3d_attributes() {
   static bool done = false;
   if (done) return Status{};
-  PG_CUDA(cudaFuncSetAttribute(k_conv3d<16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem(16, 16)));
-  PG_CUDA(cudaFuncSetAttribute(k_conv3d<16, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem(16, 32)));
-  PG_CUDA(cudaFuncSetAttribute(k_conv3d<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem(32, 16)));
-  PG_CUDA(cudaFuncSetAttribute(k_conv3d<32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem(32, 32)));
-  PG_CUDA(cudaFuncSetAttribute(k_conv3d_small<32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 27 * 32 * 32 * 2));
-  PG_CUDA(cudaFuncSetAttribute(k_conv3d_small<16, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 27 * 16 * 32 * 2));
-  PG_CUDA(cudaFuncSetAttribute(k_conv3d_small<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 27 * 32 * 16 * 2));
+#define PG_ATTR(CI, CO, NZ) \
+  PG_CUDA(cudaFuncSetAttribute(k_conv3d<CI, CO, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem(CI, CO, NZ)));
+#define PG_ATTR_NZ(CI, CO) PG_ATTR(CI, CO, 1) PG_ATTR(CI, CO, 2) PG_ATTR(CI, CO, 4)
+  PG_ATTR_NZ(16, 16)
+  PG_ATTR_NZ(16, 32)
+  PG_ATTR_NZ(32, 16)
+  PG_ATTR_NZ(32, 32)
+#undef PG_ATTR_NZ
+#undef PG_ATTR
   done = true;
   return Status{};
 }
@@ -680,21 +593,42 @@ Status conv3d_attributes() {
 Status conv3d(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, const __nv_bfloat16* x,
               const __nv_bfloat16* w, const float* bias, bool relu, __nv_bfloat16* ybf, float* yf, int* err,
               const int* stop) {
-  const int64_t V = (int64_t)gx * gy * gz;
-  const unsigned grid = nb(V, kConvRows);
-#define PG_CONV(CI, CO)                                                                                        \
-  if (cin == CI && cout == CO) {                                                                               \
-    k_conv3d<CI, CO><<<grid, 128, conv_smem(CI, CO), s>>>(x, w, bias, gx, gy, gz, relu ? 1 : 0, ybf, yf, err, stop); \
-    PG_CUDA(cudaGetLastError());                                                                               \
-    return Status{};                                                                                           \
-  }
+  if ((cin != 16 && cin != 32) || (cout != 16 && cout != 32))
+    return Status{PETGEM_ERR_UNSUPPORTED, "conv3d: channel counts must be 16 or 32"};
+  if (((uintptr_t)x | (uintptr_t)w | (uintptr_t)ybf | (uintptr_t)yf) & 15)
+    return Status{PETGEM_ERR_INVALID_ARG, "conv3d: x, w and y must be 16-byte aligned"};
   PG_TRY(conv3d_attributes());
-  PG_CONV(16, 16)
-  PG_CONV(16, 32)
-  PG_CONV(32, 16)
-  PG_CONV(32, 32)
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    PG_CUDA(cudaGetDevice(&dev));
+    PG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  // planes per CTA: the most (fewer brick and weight loads per voxel) that still leave two CTAs per SM
+  const int64_t txy = (int64_t)((gx + kBrickX - 1) / kBrickX) * ((gy + kBrickY - 1) / kBrickY);
+  const int nz = txy * ((gz + 3) / 4) >= 2 * sms ? 4 : txy * ((gz + 1) / 2) >= 2 * sms ? 2 : 1;
+  const unsigned grid = (unsigned)(txy * ((gz + nz - 1) / nz));
+#define PG_CONV(CI, CO, NZ)                                                                                      \
+  if (cin == CI && cout == CO && nz == NZ) {                                                                     \
+    k_conv3d<CI, CO, NZ><<<grid, 128, conv_smem(CI, CO, NZ), s>>>(x, w, bias, gx, gy, gz, relu ? 1 : 0, ybf, yf, err, \
+                                                                   stop);                                       \
+    PG_CUDA(cudaGetLastError());                                                                                 \
+    return Status{};                                                                                             \
+  }
+#define PG_CONV_NZ(CI, CO) PG_CONV(CI, CO, 1) PG_CONV(CI, CO, 2) PG_CONV(CI, CO, 4)
+  PG_CONV_NZ(16, 16)
+  PG_CONV_NZ(16, 32)
+  PG_CONV_NZ(32, 16)
+  PG_CONV_NZ(32, 32)
+#undef PG_CONV_NZ
 #undef PG_CONV
   return Status{PETGEM_ERR_UNSUPPORTED, "conv3d: channel counts must be 16 or 32"};
+}
+
+Status pack_conv_weights(cudaStream_t s, const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* wc) {
+  k_pack_conv_weights_bf16<<<nb(27 * cin * cout), 256, 0, s>>>(w, cin, cout, wc);
+  PG_CUDA(cudaGetLastError());
+  return Status{};
 }
 
 Status conv3d_wgrad(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, const __nv_bfloat16* x,
@@ -786,11 +720,15 @@ Status Net::init(petgem_ctx* c, int nx_, int ny_, int nz_) {
   return Status{};
 }
 
+// Forward and input-gradient weights of every layer as the convolution kernel's shared-memory
+// image (BF16).
 Status Net::pack_weights(cudaStream_t s) {
-  k_f32_to_bf16<<<nb(n_params), 256, 0, s>>>(params.as<float>(), wb.as<__nv_bfloat16>(), n_params);
-  for (int i = 0; i < 7; ++i)
-    k_flip_weights<<<nb(27 * L[i].cin * L[i].cout), 256, 0, s>>>(
-        params.as<float>() + L[i].w_off, L[i].cin, L[i].cout, wd.as<__nv_bfloat16>() + L[i].w_off);
+  for (int i = 0; i < 7; ++i) {
+    const float* w = params.as<float>() + L[i].w_off;
+    const unsigned g = nb(27 * L[i].cin * L[i].cout);
+    k_pack_conv_weights<<<g, 256, 0, s>>>(w, L[i].cin, L[i].cout, 0, wb.as<__nv_bfloat16>() + L[i].w_off);
+    k_pack_conv_weights<<<g, 256, 0, s>>>(w, L[i].cin, L[i].cout, 1, wd.as<__nv_bfloat16>() + L[i].w_off);
+  }
   PG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -800,11 +738,6 @@ Status Net::conv(cudaStream_t s, int i, int lvl, const __nv_bfloat16* in, __nv_b
   const int* gg = g[lvl];
   // timed (when profiling) with its floating-point operations in place of bytes
   const double flops = 2.0 * 27.0 * L[i].cin * L[i].cout * (double)gg[0] * gg[1] * gg[2];
-  if (V[lvl] <= kSmallConvVoxels) {
-    KernelTimer kt(ctx, "conv3d_small_fwd", flops);
-    return conv3d_small(s, gg[0], gg[1], gg[2], L[i].cin, L[i].cout, in, wb.as<__nv_bfloat16>() + L[i].w_off,
-                        params.as<float>() + L[i].b_off, L[i].relu != 0, out, outf, stop);
-  }
   KernelTimer kt(ctx, "conv3d_fwd", flops);
   return conv3d(s, gg[0], gg[1], gg[2], L[i].cin, L[i].cout, in, wb.as<__nv_bfloat16>() + L[i].w_off,
                 params.as<float>() + L[i].b_off, L[i].relu != 0, out, outf, err.as<int>(), stop);
@@ -835,9 +768,6 @@ Status Net::forward(cudaStream_t s, const int* stop) {
 
 Status Net::dgrad(cudaStream_t s, int i, int lvl, const __nv_bfloat16* dout, __nv_bfloat16* din) {
   const int* gg = g[lvl];  // the input gradient has no bias term: zbias is all zeros
-  if (V[lvl] <= kSmallConvVoxels)
-    return conv3d_small(s, gg[0], gg[1], gg[2], L[i].cout, L[i].cin, dout, wd.as<__nv_bfloat16>() + L[i].w_off,
-                        zbias.as<float>(), false, din, nullptr, nullptr);
   return conv3d(s, gg[0], gg[1], gg[2], L[i].cout, L[i].cin, dout, wd.as<__nv_bfloat16>() + L[i].w_off,
                 zbias.as<float>(), false, din, nullptr, err.as<int>());
 }

@@ -78,13 +78,13 @@ struct Net {
   Status features(cudaStream_t s, const double* sigma, double sigma_p, double omega, double h);
 };
 
+// The tensor-core convolution (k_conv3d): any grid size; w packed by k_pack_conv_weights (the
+// kernel's shared-memory image); x, w and y 16-byte aligned.
 Status conv3d(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, const __nv_bfloat16* x,
               const __nv_bfloat16* w, const float* bias, bool relu, __nv_bfloat16* ybf, float* yf, int* err,
               const int* stop = nullptr);
-// The same convolution on the CUDA cores (small grids).
-Status conv3d_small(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, const __nv_bfloat16* x,
-                    const __nv_bfloat16* w, const float* bias, bool relu, __nv_bfloat16* ybf, float* yf,
-                    const int* stop = nullptr);
+// BF16 weights [27][cout][cin] -> the convolution kernel's shared-memory image (wc, 27 cin cout).
+Status pack_conv_weights(cudaStream_t s, const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* wc);
 // Dynamic shared-memory limits of the tensor-core convolutions (once per process; before any
 // stream capture).
 Status conv3d_attributes();

@@ -14,118 +14,164 @@
 namespace petgem {
 namespace nn {
 
-constexpr int kConvRows = 128;  // output voxels per CTA (the MMA's M)
+constexpr int kConvRows = 128;  // output voxels per tensor-core tile (the MMA's M)
 
-// Dynamic shared memory of k_conv3d<CIN, COUT>: two A buffers and all 27 taps of the weights.
-__host__ __device__ constexpr int conv_smem(int cin, int cout) { return 2 * kConvRows * cin * 2 + 27 * cout * cin * 2; }
+// Convolution tile: 8 (x) by 16 (y) voxels of one z-plane, 128 rows of the MMA, row m at
+// (x0 + m % 8, y0 + m / 8).  A CTA computes NZ such tiles stacked in z from one halo brick, the
+// input voxels x0-1 .. x0+8, y0-1 .. y0+16, z0-1 .. z0+NZ (zero outside the grid), held in shared
+// memory as CIN/8 "planes" of 8 channels, 16 bytes per voxel, voxel (x', y', z') of the brick at
+// ((z' kHaloY + y') kHaloX + x') * 16 in its plane.  In that layout the A operand of every tap is
+// already a K-major core-matrix tile: core matrix i (line y0 + i, rows x0 .. x0+7) is 8 voxels 16
+// bytes apart, line i + 1 is kHaloX voxels further on (the stride byte offset), the next 8 input
+// channels one plane further on (the leading byte offset), and tap (dx, dy, dz) only moves the
+// start address.  So all 27 taps read the one brick: no per-tap gather.
+constexpr int kBrickX = 8, kBrickY = 16;
+constexpr int kHaloX = kBrickX + 2, kHaloY = kBrickY + 2;
+static_assert(kBrickX * kBrickY == kConvRows, "tile rows");
 
-// One CTA: 128 consecutive output voxels x COUT channels.  For every tap, the 128 neighbour rows
-// (CIN channels each) are gathered into a double-buffered shared tile laid out as K-major core
-// matrices, and one thread issues CIN/16 MMAs (K = 16 each) accumulating in TMEM; the buffer is
-// refilled only after the tcgen05.commit of the MMAs that read it has arrived on its mbarrier.
-template <int CIN, int COUT>
+// Bytes of one plane of the halo brick of nz output planes (128-byte aligned).
+__host__ __device__ constexpr int brick_plane(int nz) { return (kHaloX * kHaloY * (nz + 2) * 16 + 127) / 128 * 128; }
+// Dynamic shared memory of k_conv3d<CIN, COUT, NZ>: the brick, all 27 taps of the weights, the
+// bias, and the slack that aligns the brick to 128 bytes.
+__host__ __device__ constexpr int conv_smem(int cin, int cout, int nz) {
+  return (cin / 8) * brick_plane(nz) + 27 * cout * cin * 2 + cout * 4 + 128;
+}
+// TMEM columns for NZ accumulators of COUT FP32 columns (a power of two, at least 32).
+__host__ __device__ constexpr unsigned conv_tmem_cols(int cout, int nz) {
+  return cout * nz <= 32 ? 32u : cout * nz <= 64 ? 64u : 128u;
+}
+
+// Convolution weights as the kernel's shared-memory image: the B operand of tap t is the K-major
+// core-matrix tile of W[t][co][ci] (COUT rows, CIN columns), element (t, co, ci) at
+// t COUT CIN + core_offset(co, ci, CIN) / 2.  One contiguous bulk copy then loads all 27 taps.
+__host__ __device__ inline int64_t conv_weight_index(int t, int co, int ci, int cin, int cout) {
+  return (int64_t)t * cout * cin + tc::core_offset(co, ci, cin) / 2;
+}
+
+// X: BF16 [gz][gy][gx][CIN]; Wc: the weights in the order above.  Grid: one CTA per (x-tile,
+// y-tile, z-group of NZ planes), x fastest.  Thread 0 starts the bulk copy of the weights; all
+// threads copy the brick (16-byte cp.async, zeros outside the grid) and the bias; thread 0 then
+// issues the 27 x CIN/16 x NZ MMAs (K = 16 each, the planes innermost so that consecutive MMAs go
+// to independent accumulators) into NZ TMEM accumulators and one commit; the four warps read
+// their 32 TMEM lanes each and store bias + (ReLU) to the voxels inside the grid.
+template <int CIN, int COUT, int NZ>
 __global__ void __launch_bounds__(128) k_conv3d(const __nv_bfloat16* __restrict__ X,
-                                                const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias,
+                                                const __nv_bfloat16* __restrict__ Wc, const float* __restrict__ bias,
                                                 int gx, int gy, int gz, int relu, __nv_bfloat16* __restrict__ Ybf,
                                                 float* __restrict__ Yf, int* __restrict__ err,
                                                 const int* __restrict__ stop) {
-  static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 32, "channel counts");
-  if (stop && *stop) return;  // block-uniform: before any barrier or TMEM allocation
-  extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sA = smem;                               // 2 x 128 x CIN bf16
-  unsigned char* sW = smem + 2 * kConvRows * CIN * 2;     // 27 x COUT x CIN bf16
-  __shared__ __align__(8) uint64_t bar[2];
+  static_assert(CIN % 16 == 0 && CIN <= 32 && COUT % 16 == 0 && COUT <= 32 && NZ >= 1 && NZ <= 4, "tile shape");
+  constexpr int NC = CIN / 8;
+  constexpr int kPlane = brick_plane(NZ);
+  constexpr int kVox = kHaloX * kHaloY * (NZ + 2);
+  constexpr unsigned kWBytes = 27 * COUT * CIN * 2;
+  constexpr unsigned kCols = conv_tmem_cols(COUT, NZ);
+  const int stopped = stop ? *stop : 0;  // consumed after the barrier set-up, which hides its latency
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* sX = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);  // NC planes
+  unsigned char* sW = sX + NC * kPlane;                                                // 27 x COUT x CIN
+  float* sB = reinterpret_cast<float*>(sW + kWBytes);                                  // COUT
+  __shared__ __align__(8) uint64_t bar[2];  // 0: the weights have landed; 1: the MMAs are done
   __shared__ unsigned tbase;
-  __shared__ int s_ok;  // block-uniform outcome of the last mbarrier wait (thread 0 waits)
+  __shared__ int s_ok;  // block-uniform outcome of the bounded waits (thread 0 waits)
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int V = gx * gy * gz;
-  // weights -> core-matrix layout (8 input channels = one 16-byte core row)
-  for (int idx = tid; idx < 27 * COUT * (CIN / 8); idx += 128) {
-    const int c8 = idx % (CIN / 8), row = idx / (CIN / 8);  // row = t * COUT + co
-    const int t = row / COUT, co = row - t * COUT;
-    const uint4 w = *reinterpret_cast<const uint4*>(W + (size_t)row * CIN + 8 * c8);
-    *reinterpret_cast<uint4*>(sW + t * COUT * CIN * 2 + tc::core_offset(co, 8 * c8, CIN)) = w;
-  }
+  const int tiles_x = (gx + kBrickX - 1) / kBrickX, tiles_y = (gy + kBrickY - 1) / kBrickY;
+  const int x0 = (int)(blockIdx.x % tiles_x) * kBrickX;
+  const int y0 = (int)((blockIdx.x / tiles_x) % tiles_y) * kBrickY;
+  const int z0 = (int)(blockIdx.x / (tiles_x * tiles_y)) * NZ;
   if (tid == 0) {
     tc::mbar_init(&bar[0]);
     tc::mbar_init(&bar[1]);
     tc::mbar_init_fence();
     s_ok = 1;
   }
-  if (warp == 0) tc::tmem_alloc(&tbase, 32);
+  __syncthreads();
+  if (stopped) return;  // block-uniform: no copy, MMA or TMEM allocation yet
+  if (tid == 0) {
+    tc::mbar_expect_tx(&bar[0], kWBytes);
+    tc::bulk_load(sW, Wc, kWBytes, &bar[0]);
+  }
+  if (tid < COUT) tc::cp_async4(sB + tid, bias + tid);
+  // brick: consecutive threads on consecutive 16-byte pieces of the input (8 channels of a voxel)
+  for (int idx = tid; idx < kVox * NC; idx += 128) {
+    const int c = idx % NC, b = idx / NC;
+    const int xh = b % kHaloX, yh = (b / kHaloX) % kHaloY, zh = b / (kHaloX * kHaloY);
+    const int x = x0 - 1 + xh, y = y0 - 1 + yh, z = z0 - 1 + zh;
+    unsigned char* dst = sX + c * kPlane + b * 16;
+    if (x >= 0 && x < gx && y >= 0 && y < gy && z >= 0 && z < gz)
+      tc::cp_async16(dst, X + ((size_t)x + (size_t)gx * ((size_t)y + (size_t)gy * (size_t)z)) * CIN + 8 * c);
+    else
+      *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
+  }
+  tc::cp_async_commit();
+  if (warp == 0) tc::tmem_alloc(&tbase, kCols);
+  tc::cp_async_wait_all();
+  tc::fence_proxy_async();  // the brick (generic proxy) becomes visible to the tensor core
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const unsigned tmem = tbase;
-  const int v = blockIdx.x * kConvRows + tid;
-  const int x = v % gx, y = (v / gx) % gy, z = v / (gx * gy);
-  const uint32_t idesc = tc::idesc_bf16(kConvRows, COUT);
-  const unsigned sbo = (CIN / 8) * 128;
-  // A timed-out wait stops the tap loop for the whole block: no further buffer rewrite or MMA
-  // issue, no TMEM load; the MMAs already issued are drained with one more bounded wait before
-  // TMEM is freed, and the error flag is set.
-  int issued = 0;  // taps whose MMAs were issued
-  for (int t = 0; t < 27; ++t) {
-    const int buf = t & 1;
-    if (t >= 2) {
-      if (tid == 0 && !tc::mbar_wait(&bar[buf], ((t - 2) >> 1) & 1)) s_ok = 0;
-      __syncthreads();
-      if (!s_ok) break;
-    }
-    const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
-    const int nx = x + dx, ny = y + dy, nz = z + dz;
-    const bool in = v < V && nx >= 0 && nx < gx && ny >= 0 && ny < gy && nz >= 0 && nz < gz;
-    const __nv_bfloat16* src = X + (size_t)(nx + gx * (ny + gy * nz)) * CIN;
-    unsigned char* dstA = sA + buf * kConvRows * CIN * 2;
+  // A timed-out wait issues nothing more: the weights' copy is let land (a second bounded wait)
+  // before the CTA leaves, issued MMAs are drained before TMEM is freed, and the flag is set.
+  if (tid == 0) {
+    if (!tc::mbar_wait(&bar[0], 0)) {
+      s_ok = 0;
+      tc::mbar_wait(&bar[0], 0);
+    } else {
+      const uint32_t idesc = tc::idesc_bf16(kConvRows, COUT);
+      const uint64_t ad0 = tc::smem_desc(tc::smem_u32(sX), kPlane, kHaloX * 16);
+      const uint64_t bd0 = tc::smem_desc(tc::smem_u32(sW), 128, (CIN / 8) * 128);
+      // descriptor start addresses are in 16-byte units: a tap, K-step or plane adds its offset / 16
 #pragma unroll
-    for (int c8 = 0; c8 < CIN / 8; ++c8) {
-      const uint4 a = in ? *reinterpret_cast<const uint4*>(src + 8 * c8) : make_uint4(0, 0, 0, 0);
-      *reinterpret_cast<uint4*>(dstA + tc::core_offset(tid, 8 * c8, CIN)) = a;
-    }
-    tc::fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after();
+      for (int t = 0; t < 27; ++t) {
 #pragma unroll
-      for (int ks = 0; ks < CIN / 16; ++ks) {
-        const uint64_t ad = tc::smem_desc(tc::smem_u32(dstA) + ks * 256, 128, sbo);
-        const uint64_t bd = tc::smem_desc(tc::smem_u32(sW + t * COUT * CIN * 2) + ks * 256, 128, sbo);
-        tc::mma_bf16(tmem, ad, bd, idesc, t > 0 || ks > 0);
+        for (int ks = 0; ks < CIN / 16; ++ks) {
+          const uint64_t bd = bd0 + (uint64_t)((t * COUT * CIN * 2 + ks * 256) >> 4);
+#pragma unroll
+          for (int zl = 0; zl < NZ; ++zl) {
+            const int aoff = (((zl + t / 9) * kHaloY + (t / 3) % 3) * kHaloX + t % 3) * 16 + 2 * ks * kPlane;
+            tc::mma_bf16(tmem + zl * COUT, ad0 + (uint64_t)(aoff >> 4), bd, idesc, t > 0 || ks > 0);
+          }
+        }
       }
-      tc::commit(&bar[buf]);
+      tc::commit(&bar[1]);
+      if (!tc::mbar_wait(&bar[1], 0)) {
+        s_ok = 0;
+        tc::mbar_wait(&bar[1], 0);
+      }
     }
-    issued = t + 1;
-  }
-  // the commit of the last issued tap covers every MMA issued before it (after all 27 taps: the
-  // 14th commit on buffer 0, parity 1)
-  if (tid == 0 && issued > 0) {
-    const int last = issued - 1;
-    if (!tc::mbar_wait(&bar[last & 1], (last >> 1) & 1)) s_ok = 0;
   }
   __syncthreads();
   tc::fence_after();
-  const bool ok = s_ok != 0 && issued == 27;
-  if (ok) {
+  if (s_ok) {
+    const int x = x0 + (tid & 7), y = y0 + (tid >> 3);  // row m = tid (warp w: TMEM lanes 32w ..)
 #pragma unroll
-    for (int c0 = 0; c0 < COUT; c0 += 16) {
-      float acc[16];
-      tc::tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + c0, acc);
-      if (v < V) {
+    for (int zl = 0; zl < NZ; ++zl) {
+      const int z = z0 + zl;
+      const bool in = x < gx && y < gy && z < gz;
+      const size_t v = (size_t)x + (size_t)gx * ((size_t)y + (size_t)gy * (size_t)z);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          float r = acc[i] + bias[c0 + i];
-          if (relu) r = fmaxf(r, 0.f);
-          acc[i] = r;
-        }
-        if (Yf) {
+      for (int c0 = 0; c0 < COUT; c0 += 16) {
+        float acc[16];
+        tc::tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(zl * COUT + c0), acc);
+        if (in) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) Yf[(size_t)v * COUT + c0 + i] = acc[i];
-        } else {
-          __align__(16) __nv_bfloat16 o[16];
+          for (int i = 0; i < 16; ++i) {
+            float r = acc[i] + sB[c0 + i];
+            if (relu) r = fmaxf(r, 0.f);
+            acc[i] = r;
+          }
+          if (Yf) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) o[i] = __float2bfloat16(acc[i]);
-          *reinterpret_cast<uint4*>(Ybf + (size_t)v * COUT + c0) = *reinterpret_cast<uint4*>(o);
-          *reinterpret_cast<uint4*>(Ybf + (size_t)v * COUT + c0 + 8) = *reinterpret_cast<uint4*>(o + 8);
+            for (int i = 0; i < 16; i += 4)
+              *reinterpret_cast<float4*>(Yf + v * COUT + c0 + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+          } else {
+            __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) o[i] = __float2bfloat16(acc[i]);
+            *reinterpret_cast<uint4*>(Ybf + v * COUT + c0) = *reinterpret_cast<uint4*>(o);
+            *reinterpret_cast<uint4*>(Ybf + v * COUT + c0 + 8) = *reinterpret_cast<uint4*>(o + 8);
+          }
         }
       }
     }
@@ -134,7 +180,29 @@ __global__ void __launch_bounds__(128) k_conv3d(const __nv_bfloat16* __restrict_
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 32);
+  if (warp == 0) tc::tmem_dealloc(tmem, kCols);
+}
+
+// Weights -> the convolution's shared-memory image (conv_weight_index), BF16.  flip: the layer
+// cout' x cin' = cin x cout with W'[t][o][i] = W[26 - t][i][o], the convolution that takes the
+// output gradient of the layer W (cin -> cout) to its input gradient.  Wf: FP32 [27][cout][cin].
+__global__ void k_pack_conv_weights(const float* __restrict__ Wf, int cin, int cout, int flip,
+                                    __nv_bfloat16* __restrict__ Wc) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 27 * cin * cout) return;
+  const int ci2 = flip ? cout : cin, co2 = flip ? cin : cout;  // the packed layer's shape
+  const int i = idx % ci2, o = (idx / ci2) % co2, t = idx / (ci2 * co2);
+  const float w = flip ? Wf[((26 - t) * cout + i) * cin + o] : Wf[(t * cout + o) * cin + i];
+  Wc[conv_weight_index(t, o, i, ci2, co2)] = __float2bfloat16(w);
+}
+
+// The same from BF16 [27][cout][cin] weights, not flipped.
+__global__ void k_pack_conv_weights_bf16(const __nv_bfloat16* __restrict__ W, int cin, int cout,
+                                         __nv_bfloat16* __restrict__ Wc) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 27 * cin * cout) return;
+  const int i = idx % cin, o = (idx / cin) % cout, t = idx / (cin * cout);
+  Wc[conv_weight_index(t, o, i, cin, cout)] = W[idx];
 }
 
 // Weight gradient as a GEMM over voxels: D[(t, ci)][co] = sum_v X[v + off_t][ci] dY[v][co].

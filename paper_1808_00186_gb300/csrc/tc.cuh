@@ -1,6 +1,7 @@
 // Blackwell 5th-generation tensor-core (tcgen05) primitives used by the learned preconditioner:
 // TMEM allocation, shared-memory matrix descriptors, BF16 MMA with FP32 accumulation in TMEM,
-// commit to an mbarrier, and TMEM loads.  Inline PTX for sm_103a.
+// commit to an mbarrier, TMEM loads, and the copies that feed them (bulk asynchronous copies
+// completing on an mbarrier, 4- and 16-byte cp.async).  Inline PTX for sm_103a.
 //
 // Operand layout (both A and B "K-major", no swizzle): a core matrix is 8 rows x 16 bytes (8 BF16
 // along K) stored as 128 contiguous bytes.  A tile with R rows and K columns keeps core (r/8, k/8)
@@ -81,6 +82,32 @@ __device__ inline bool mbar_wait(uint64_t* bar, unsigned parity) {
   }
   return true;
 }
+
+// The barrier's single arrival, announcing `bytes` of asynchronous copies that complete on it.
+__device__ inline void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Bulk asynchronous copy of `bytes` contiguous bytes (a multiple of 16; both addresses 16-byte
+// aligned) from global to shared memory, completing on bar.
+__device__ inline void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// 4-byte asynchronous global -> shared copy (4-byte aligned addresses).
+__device__ inline void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned), and the waits.
+__device__ inline void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // 32 lanes x 16 columns of 32-bit TMEM values starting at taddr (lane = warp's 32-row slice).
 __device__ inline void tmem_ld16(unsigned taddr, float* v) {

@@ -85,6 +85,10 @@ def test_conv_grids_whose_voxel_count_wraps_are_rejected_on_the_host(lib_path):
     assert L.petgem_nn_conv3d_wgrad(None, big, big, big, 16, 16, fake, fake, fake) == api.ERR_UNSUPPORTED
     assert L.petgem_nn_conv3d_wgrad(None, 1024, 1024, 64, 16, 16, fake, fake, fake) == api.ERR_UNSUPPORTED
     assert L.petgem_nn_conv3d(None, big, big, big, 16, 16, fake, fake, fake, 0, fake, 1) == api.ERR_UNSUPPORTED
+    assert L.petgem_nn_conv3d(None, 4, 4, 4, 16, 24, fake, fake, fake, 0, fake, 1) == api.ERR_UNSUPPORTED
+    odd = ctypes.c_void_p(264)  # 8-byte aligned only
+    assert L.petgem_nn_conv3d(None, 4, 4, 4, 16, 16, odd, fake, fake, 0, fake, 1) == api.ERR_INVALID_ARG
+    assert L.petgem_nn_conv3d(None, 4, 4, 4, 16, 16, fake, fake, fake, 0, odd, 1) == api.ERR_INVALID_ARG
 
 
 def test_layered_primary_field_checks_its_arguments_on_the_host(lib_path):

@@ -63,6 +63,32 @@ def test_conv3d_matches_oracle(cin, cout, grid):
     assert rel_max(ybf.float().cpu().numpy(), np.maximum(ref, 0.0)) <= 1e-2
 
 
+@pytest.mark.parametrize("cin,cout,grid", [
+    ((16, 16, (1, 1, 1))),      # one voxel: the brick is all halo
+    ((16, 16, (8, 16, 3))),     # exactly one 8 x 16 tile per plane
+    ((32, 32, (17, 33, 5))),    # several tiles in x and y, each with a one-voxel tail
+    ((16, 16, (65, 65, 23))),   # two planes per CTA on a 152-SM GPU, the last group with one
+    ((16, 32, (65, 65, 41))),   # four planes per CTA, the last group with one
+    ((32, 16, (66, 50, 41))),
+])
+def test_conv3d_tiles_ragged_tails_and_plane_groups_match_oracle(cin, cout, grid):
+    """The convolution's tiles are 8 x 16 voxels of a plane, 1, 2 or 4 planes per CTA (by grid
+    size); every boundary of that tiling, and the grid's own, must give the oracle's result."""
+    rng = np.random.default_rng(7 * cin + cout + grid[2])
+    V = grid[0] * grid[1] * grid[2]
+    xt, x = bf16(rng.normal(size=(V, cin)))
+    wt, w = bf16(rng.normal(size=(27, cout, cin)) * 0.2)
+    bias = rng.normal(size=cout).astype(np.float32)
+    xg, wg, bg = xt.to("cuda"), wt.to("cuda"), torch.as_tensor(bias).to("cuda")
+    y32 = torch.full((V, cout), float("nan"), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    api.petgem_nn_conv3d(stream, grid, cin, cout, xg, wg, bg, False, y32, True)
+    ref = OL.conv3d(to_zyx(x, grid, cin), w, bias.astype(np.float64)).reshape(V, cout)
+    got = y32.cpu().numpy()
+    assert np.isfinite(got).all()  # every voxel written
+    assert rel_max(got, ref) <= 1e-4
+
+
 @pytest.mark.parametrize("cin,cout", [(16, 16), (16, 32), (32, 16), (32, 32)])
 def test_conv3d_weight_gradient_matches_oracle(cin, cout):
     grid = (11, 9, 7)
