@@ -214,40 +214,36 @@ __device__ inline bool interior(int x, int y, int z, int gx, int gy, int gz) {
   return x >= 1 && y >= 1 && z >= 1 && x <= gx - 2 && y <= gy - 2 && z <= gz - 2;
 }
 
-// The (up to 14) edges at node v with their coefficients in G (g) and Pi (p = t / (2 |t|)):
-// the seven edges leaving v (v is their low node, g = -1/|t|) and the seven arriving at v.
+// The 14 edge slots at node v with their coefficients in G (g) and Pi (p = t / (2 |t|)): slot 2c
+// is the edge leaving v in lattice direction c (v its low node, g = -1/|t|), slot 2c + 1 the edge
+// arriving from v - step_c.  A slot without an edge has e = -1 and zero coefficients (its tangent
+// entry is zero), so every array index is a compile-time constant once the loops are unrolled
+// and the slots stay in registers; the 14 edge ids and tangents are independent loads.
 struct Incident {
-  int n;
   int32_t e[14];
   float g[14];
   float3 p[14];
 };
 __device__ inline void incident_edges(int64_t v, int x, int y, int z, int gx, int gy, const int32_t* slot_edge,
                                       const float4* tang, Incident& I) {
-  I.n = 0;
 #pragma unroll
   for (int c = 0; c < 7; ++c) {
     const int64_t so = v * 7 + c;
-    const int32_t eo = slot_edge[so];
-    if (eo >= 0) {
-      const float4 t = tang[so];
-      I.e[I.n] = eo;
-      I.g[I.n] = -t.w;
-      I.p[I.n] = make_float3(0.5f * t.x, 0.5f * t.y, 0.5f * t.z);
-      ++I.n;
-    }
+    const float4 t = tang[so];
+    I.e[2 * c] = slot_edge[so];
+    I.g[2 * c] = -t.w;
+    I.p[2 * c] = make_float3(0.5f * t.x, 0.5f * t.y, 0.5f * t.z);
     const int ux = x - kStep[c][0], uy = y - kStep[c][1], uz = z - kStep[c][2];
+    int32_t ei = -1;
+    float4 ti = make_float4(0.f, 0.f, 0.f, 0.f);
     if (ux >= 0 && uy >= 0 && uz >= 0) {
       const int64_t si = ((int64_t)ux + (int64_t)gx * ((int64_t)uy + (int64_t)gy * uz)) * 7 + c;
-      const int32_t ei = slot_edge[si];
-      if (ei >= 0) {
-        const float4 t = tang[si];
-        I.e[I.n] = ei;
-        I.g[I.n] = t.w;
-        I.p[I.n] = make_float3(0.5f * t.x, 0.5f * t.y, 0.5f * t.z);
-        ++I.n;
-      }
+      ei = slot_edge[si];
+      ti = tang[si];
     }
+    I.e[2 * c + 1] = ei;
+    I.g[2 * c + 1] = ti.w;
+    I.p[2 * c + 1] = make_float3(0.5f * ti.x, 0.5f * ti.y, 0.5f * ti.z);
   }
 }
 
@@ -268,9 +264,13 @@ __global__ void k_hx_diag(const int32_t* __restrict__ slot_edge, const float4* _
   Incident I;
   incident_edges(v, x, y, z, gx, gy, slot_edge, tang, I);
   double2 dg = make_double2(0.0, 0.0), dp[3] = {dg, dg, dg};
-  for (int i = 0; i < I.n; ++i) {
+#pragma unroll
+  for (int i = 0; i < 14; ++i) {
+    if (I.e[i] < 0) continue;
     const int64_t r0 = rp[I.e[i]], r1 = rp[I.e[i] + 1];
-    for (int j = 0; j < I.n; ++j) {
+#pragma unroll
+    for (int j = 0; j < 14; ++j) {
+      if (I.e[j] < 0) continue;
       int64_t lo = r0, hi = r1;  // binary search for column e_j in row e_i
       const int32_t want = I.e[j];
       while (lo < hi) {
@@ -315,9 +315,13 @@ __global__ void __launch_bounds__(256) k_hx_in(const T* __restrict__ r, const in
       grid_coords(v, gx, gy, x, y, z);
       Incident I;
       incident_edges(v, x, y, z, gx, gy, slot_edge, tang, I);
+      T rv[14];
+#pragma unroll
+      for (int k = 0; k < 14; ++k) rv[k] = I.e[k] >= 0 ? r[I.e[k]] : T{0, 0};
       R gr = 0, gi = 0, pr[3] = {0, 0, 0}, pi[3] = {0, 0, 0};
-      for (int k = 0; k < I.n; ++k) {
-        const T re = r[I.e[k]];
+#pragma unroll
+      for (int k = 0; k < 14; ++k) {
+        const T re = rv[k];
         const R xr = (R)re.x, xi = (R)re.y;
         gr += (R)I.g[k] * xr;
         gi += (R)I.g[k] * xi;
@@ -388,11 +392,11 @@ __global__ void k_hx_pack(const float* __restrict__ nodes8, const float* __restr
 }
 // z_e = D^{-1} r_e + (G phi + Pi w)_e (XS) or r_e + D_e (G phi + Pi w)_e, from the network output y
 // [V][16] (FP32): phi = s sg (y0 + i y1), w_k = s sp_k (y_{2+k} + i y_{5+k}) at the edge's nodes.
-// Arithmetic in the vector's precision (FP32 for complex64).
+// Arithmetic, and the diagonal D, in the vector's precision (FP32 for complex64).
 template <typename T, bool XS>
 __global__ void k_hx_out(const T* __restrict__ r, const int32_t* __restrict__ slot, int64_t E,
                          const float* __restrict__ y, const float4* __restrict__ aux, const float4* __restrict__ tang,
-                         const float* __restrict__ scal, const double2* __restrict__ diag, int gx, int gy,
+                         const float* __restrict__ scal, const T* __restrict__ diag, int gx, int gy,
                          T* __restrict__ z, const int* __restrict__ stop) {
   if (stop && *stop) return;
   using R = typename real_of<T>::type;
@@ -421,8 +425,8 @@ __global__ void k_hx_out(const T* __restrict__ r, const int32_t* __restrict__ sl
     ci += hs * ((R)t.x * ((R)al.y * l1.y + (R)ah.y * h1.y) + (R)t.y * ((R)al.z * l1.z + (R)ah.z * h1.z) +
                 (R)t.z * ((R)al.w * l1.w + (R)ah.w * h1.w));
   }
-  const double2 dd = diag[e];
-  const R dr = (R)dd.x, di = (R)dd.y;
+  const T dd = diag[e];
+  const R dr = dd.x, di = dd.y;
   const R rr = (R)re.x, ri = (R)re.y;
   T o;
   if (XS) {  // r / d + corr
@@ -434,6 +438,11 @@ __global__ void k_hx_out(const T* __restrict__ r, const int32_t* __restrict__ sl
     o.y = ri + (dr * ci + di * cr);
   }
   z[e] = o;
+}
+// The diagonal of A in single precision, for the complex64 application.
+__global__ void k_diag_f32(const double2* __restrict__ d, int64_t n, float2* __restrict__ o) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) o[i] = make_float2((float)d[i].x, (float)d[i].y);
 }
 // Gradient of the loss with respect to the network output: with gzp = Ahat^H gw and
 // g = conj(D) gzp = A^H gw (the gradient at z in the unscaled variables),
@@ -453,7 +462,9 @@ __global__ void k_hx_dy(const double2* __restrict__ gzp, const double2* __restri
     Incident I;
     incident_edges(v, x, y, z, gx, gy, slot_edge, tang, I);
     double gr = 0.0, gi = 0.0, pr[3] = {0.0, 0.0, 0.0}, pi[3] = {0.0, 0.0, 0.0};
-    for (int k = 0; k < I.n; ++k) {
+#pragma unroll
+    for (int k = 0; k < 14; ++k) {
+      if (I.e[k] < 0) continue;
       const double2 g = cconjmul(diag[I.e[k]], gzp[I.e[k]]);
       gr += I.g[k] * g.x;
       gi += I.g[k] * g.y;
@@ -838,6 +849,8 @@ Status Net::prepare_aux(petgem_ctx* c) {
     PG_TRY(npart.reserve((size_t)nb(V[0]) * sizeof(double)));
     k_hx_diag<<<nb(V[0]), 256, 0, s>>>(slot_edge.as<int32_t>(), tang.as<float4>(), c->row_ptr.as<int64_t>(),
                                        c->col.as<int32_t>(), c->val.as<double2>(), gx, gy, gz, aux.as<float4>());
+    PG_TRY(diag32.reserve((size_t)c->n_edges * sizeof(float2)));
+    k_diag_f32<<<nb(c->n_edges), 256, 0, s>>>(c->diag.as<double2>(), c->n_edges, diag32.as<float2>());
     PG_CUDA(cudaGetLastError());
     aux_version = c->assembly_version;
   }
@@ -872,10 +885,11 @@ Status Net::apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T*
                   const int* stop) {
   PG_TRY(load_input(s, r, E, stop));
   PG_TRY(forward(s, stop));
-  const double2* d = ctx->diag.as<double2>();
+  const T* d = sizeof(T) == 8 ? reinterpret_cast<const T*>(diag32.as<float2>())
+                              : reinterpret_cast<const T*>(ctx->diag.as<double2>());
   // algorithmic bytes per edge: r, z, diag, slot, tangent, and 2 x (32 B of y + 16 B of scales)
   KernelTimer kt(ctx, sizeof(T) == 8 ? "hx_out_c64" : "hx_out_c128",
-                 (double)E * (2.0 * sizeof(T) + 16.0 + 4.0 + 16.0 + 96.0));
+                 (double)E * (3.0 * sizeof(T) + 4.0 + 16.0 + 96.0));
   if (xspace)
     k_hx_out<T, true><<<nb(E), 256, 0, s>>>(r, slot, E, y.as<float>(), aux.as<float4>(), tang.as<float4>(),
                                             scal.as<float>(), d, g[0][0], g[0][1], z, stop);

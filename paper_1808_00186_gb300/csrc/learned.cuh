@@ -47,7 +47,7 @@ struct Net {
   // auxiliary spaces on the lattice: edge of every slot (node * 7 + class, -1 if none), the
   // slot's unit tangent and inverse length, per-node scales (sg, sp_x, sp_y, sp_z), the gathered
   // node fields [V0][8] and per-block partial sums
-  DevBuf slot_edge, tang, aux, nodes8, npart;
+  DevBuf slot_edge, tang, aux, nodes8, npart, diag32;  // diag32: diag(A) as complex64
   int64_t aux_version = -1;    // assembly the scales belong to
   int64_t geom_version = -1;   // mesh the slot map and tangents belong to
   int64_t alloc_gen = 0;       // bumped whenever a buffer may have moved (captured graphs key on it)
