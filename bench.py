@@ -701,7 +701,7 @@ def run_ours(args):
             "config": {"workload": "marine_n%d_1src_1Hz" % args.n, "tets": m.mesh.n_tets,
                        "edges": n_edges[0], "sources": S, "restart": 50, "tol": 1e-8, "precision": "mixed",
                        "preconditioner": "learned auxiliary-space (Jacobi + network on the node lattice)",
-                       "orth": "cgs, second pass when the norm fell by 1/sqrt(2)",
+                       "orth": "cgs, second pass when the norm fell below 1/sqrt(10)",
                        "l2": "working set > L2 (no flush needed)", "parallelism": "replicas" if world > 1 else "single"},
             "iters": info_mixed[0]["iters"], "cycles": info_mixed[0]["restarts"],
             "reorth_steps": info_mixed[0]["reorth"],

@@ -132,7 +132,8 @@ enum { PETGEM_METHOD_GMRES = 0, PETGEM_METHOD_COCG = 1, PETGEM_METHOD_SQMR = 2 }
 /* Orthogonalisation of each new Krylov vector w against the basis V:
  *   CGS: classical Gram-Schmidt once (two passes over V per step; the default of PETSc's GMRES);
  *   CGS2: classical Gram-Schmidt twice (three passes);
- *   CGS_IFNEEDED: a second pass only when ||w|| fell below 1/sqrt(2) of its value. */
+ *   CGS_IFNEEDED: a second pass only when ||w|| fell below 1/sqrt(10) of its value (one classical
+ *     pass loses orthogonality in proportion to that cancellation). */
 enum { PETGEM_ORTH_CGS2 = 0, PETGEM_ORTH_CGS = 1, PETGEM_ORTH_CGS_IFNEEDED = 2 };
 
 /* Per-source results of petgem_solve. */

@@ -13,7 +13,7 @@
 //
 // Arnoldi with classical Gram-Schmidt (gs.cuh): one projection pass and one update pass (CGS, the
 // default), two of each (CGS2), or a second pair only when ||w|| fell below eta * ||w_before||
-// (eta = 1/sqrt(2)).  Each Krylov vector V_k is stored unnormalised with its scale 1/||V_k|| on
+// (eta = 1/sqrt(10), kReorthEta2).  Each Krylov vector V_k is stored unnormalised with its scale 1/||V_k|| on
 // the device, so no separate normalisation pass is needed.  The Hessenberg column, its Givens
 // rotations and the stopping test run in the last block of the update kernel: a cycle of m
 // iterations needs no host synchronisation, and kernels after the stop return at once.
@@ -28,6 +28,14 @@
 namespace petgem {
 
 namespace {
+
+// Conditional second Gram-Schmidt pass: taken when the first pass left less than 1/sqrt(10) of
+// the vector's norm (||w'||^2 < 0.1 ||w||^2).  One classical pass loses orthogonality in
+// proportion to the cancellation ||w|| / ||w'|| times the unit rounding, so below that factor
+// (sqrt(10)) a single complex64 pass stays near 2e-7, far inside what an inner cycle that FP64
+// refinement restarts needs; the classical 1/sqrt(2) test fired on nearly every step of the
+// learned cycles (whose new directions lose 30-70% of their norm) for no change in iterations.
+constexpr double kReorthEta2 = 0.1;
 
 // ------------------------------------------------------------------ kernels
 // Output scaling of the Arnoldi SpMV.  complex64: FP32 only (no FP64 instruction in the kernel:
@@ -536,9 +544,9 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
       } else if (orth == 1) {  // CGS: dots, update + norm
         PG_TRY(sdot(0, 0, c128 ? "mdot_c128" : "mdot_c64", dot_b, 0));
         PG_TRY(supd(0, 0, 0.0, 1, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0));
-      } else {  // CGS, second pass when the norm fell below 1/sqrt(2) of its value
+      } else {  // CGS, second pass when the norm fell below 1/sqrt(10) of its value
         PG_TRY(sdot(0, 0, c128 ? "mdot_c128" : "mdot_c64", dot_b, 0));
-        PG_TRY(supd(0, 0, 0.5, 1, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0));
+        PG_TRY(supd(0, 0, kReorthEta2, 1, c128 ? "cgs_upd_c128" : "cgs_upd_c64", upd_b, 0));
         PG_TRY(sdot(1, 1, c128 ? "cgs_dot2_c128" : "cgs_dot2_c64", dot_b, 1));
         PG_TRY(supd(1, 1, 0.0, 1, c128 ? "cgs_upd2_c128" : "cgs_upd2_c64", upd_b, 1));
       }
@@ -703,7 +711,7 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
       const int mj = (int)std::min<int64_t>(m, std::max<int64_t>(o.max_iters - iters, 0));
       const double tol_abs = o.tol * bnorm;
       // Learned cycles take a second Gram-Schmidt pass whenever the first one lost more than a
-      // factor 1/sqrt(2) of the norm (the network's directions can be nearly dependent).
+      // factor 1/sqrt(10) of the norm (the network's directions can be nearly dependent).
       const int orth = learned && o.orth == PETGEM_ORTH_CGS ? PETGEM_ORTH_CGS_IFNEEDED : o.orth;
       // A cycle whose starting residual already meets tol runs no iteration (k = 0).
       if (o.precision == PETGEM_PREC_MIXED)
