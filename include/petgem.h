@@ -102,7 +102,8 @@ typedef struct {
                           many lanes per row, 1 = SELL-32 with rows grouped by edge kind (CSR with
                           4 lanes when a mesh lacks that layout); 0 = chosen by the autotuner.
                           petgem_solve with several sources iterated together (batch != 1): the
-                          block SpMM, 0 = chosen by the autotuner, 1 = one lane per (row, source),
+                          block SpMM, 0 = chosen by the autotuner (once per context and problem
+                          shape: rows, nonzeros, sources, precision), 1 = one lane per (row, source),
                           16 / 32 / 64 = the staged kernel with that band height (other values:
                           PETGEM_ERR_UNSUPPORTED); ignored by single-source solves (which use
                           SELL-32 when the mesh has it) */

@@ -128,12 +128,13 @@ Status launch_spmm_band(petgem_ctx* c, cudaStream_t s, int which, const T* val, 
 // Autotuner of the block SpMM: on the solver's own operands (val, X; Y is overwritten) it times
 // the solver's row kernel (rows(), a launch of it) and the staged kernel for every band height
 // (the band layouts are built on first use), one warm-up and ten timed launches each with CUDA
-// events on the stream, and keeps the fastest for this mesh, size, source count and value type.
+// events on the stream, and keeps the fastest for this problem shape: rows, nonzeros, source
+// count and value type.  A new mesh of the same shape (a re-meshed model) keeps the choice, and
+// a band form then gets its layout for the new mesh where it is launched.
 // *choice: -1 for the row kernel, else the band height's index.
 template <typename T, int P, typename Rows>
 Status tune_spmm(petgem_ctx* c, cudaStream_t s, const T* val, const T* X, T* Y, Rows rows, int* choice) {
-  const uint64_t key = ((uint64_t)c->mesh_version << 40) ^ ((uint64_t)c->n_edges << 16) ^ ((uint64_t)c->nnz << 8) ^
-                       ((uint64_t)P << 4) ^ (uint64_t)sizeof(T);
+  const uint64_t key = ((uint64_t)c->n_edges << 24) ^ ((uint64_t)c->nnz << 8) ^ ((uint64_t)P << 4) ^ (uint64_t)sizeof(T);
   auto it = c->spmm_choice.find(key);
   if (it != c->spmm_choice.end()) {
     *choice = it->second;
