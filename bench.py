@@ -62,6 +62,11 @@ def parse():
 # 48^3 (the marine model, Arnoldi step j = 20): these kernels stream
 # their vectors once, so the traffic of a bench launch is this ratio times its algorithmic bytes.
 TRAFFIC_RATIO = {"spmv_c64": 1.0013, "mdot_c64": 1.0301, "cgs_upd_c64": 0.9860}
+# DRAM traffic per launch of kernels whose algorithmic unit is FLOPs, from one ncu capture of the
+# same workload (the 11 convolution layers of one network application on the 65^3 lattice:
+# 22.48 MB read, 0 written, over 11 launches; each layer's input is read once, its output stays
+# in L2 for the next layer).
+TRAFFIC_BYTES = {"conv3d_fwd": 2043392}
 
 
 def tensor_peak():
@@ -676,7 +681,7 @@ def run_ours(args):
                     "peak": peak, "unit": "TFLOP/s" if flops else "GB/s", "frac": round(achieved / peak, 4),
                     "peak_source": bf16_peak[1] if flops else peak_kind,
                     "traffic": (round(TRAFFIC_RATIO[name] * ks["bytes"] / ks["launches"]) if name in TRAFFIC_RATIO
-                                else None),
+                                else TRAFFIC_BYTES.get(name)),
                     "traffic_unit": "bytes per launch (ncu DRAM read+write)",
                     "launches": ks["launches"], "avg_launch_us": round(ks["ms"] / ks["launches"] * 1e3, 2),
                     ("algorithmic_flops_per_launch" if flops else "algorithmic_bytes_per_launch"):
