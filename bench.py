@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--no-cocg", action="store_true", help="skip the COCG measurement")
     p.add_argument("--no-batch", action="store_true", help="skip the batch of uneven meshes")
     p.add_argument("--no-graded", action="store_true", help="skip the graded-mesh measurement")
+    p.add_argument("--no-general", action="store_true", help="skip the randomly numbered mesh")
     p.add_argument("--profile-block", type=int, default=0, metavar="ITERS",
                    help="run only the 32-source block solve, capped at ITERS iterations (for ncu)")
     return p.parse_args()
@@ -75,6 +76,20 @@ def tensor_peak():
         return float(json.load(open(MEASURED))["bf16_tflops"]), "measured"
     except Exception:
         return 1900.0, "fallback"
+
+
+def fp64_peak(device):
+    """FP64 FMA peak of the CUDA cores from unit counts: SMs x 2 FP64 FMA/clk x 2 flops x the
+    maximum SM clock (measured, else the GB300's 2070 MHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = 2070.0
+    try:
+        with open(MEASURED) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except (OSError, ValueError):
+        pass
+    return round(sms * 2 * 2 * mhz * 1e6 / 1e12, 3), "%d SMs x 2 FP64 FMA/clk x 2 x %.0f MHz" % (sms, mhz)
 
 
 def dist_env():
@@ -309,6 +324,27 @@ def run_ours(args):
         ms_plain, info_plain, _, _ = timed(api.PREC_C128, 1, 1)
         plain = {"ms_per_step": ms_plain, "s_per_source": ms_plain / 1e3 / S, "iters": info_plain[0]["iters"],
                  "true_rel_residual": info_plain[0]["true_rel_residual"]}
+        # Its Gram-Schmidt kernels are bound by the FP64 pipe (ncu: 87-95 % busy, DRAM 11-26 %), so
+        # their roofline is FP64 arithmetic: one more step with per-kernel events, FLOPs from the
+        # timed bytes (projections over j + 1 vectors: (j + 2) 16 n bytes, 8 (j + 1) n + 4 n FLOP;
+        # update: (j + 3) 16 n bytes, 8 (j + 1) n + 4 n FLOP), peak from the unit counts.
+        timed(api.PREC_C128, 1, 0, profile=True)
+        n_e = n_edges[0]
+        pk = {}
+        for name, extra in (("mdot_c128", 4.0), ("cgs_upd_c128", 12.0)):
+            nl, kms, by = api.petgem_kernel_stats(ctx.h, name)
+            if nl:
+                pk[name] = {"launches": nl, "ms": round(kms, 3), "tflops": (by / 2.0 - extra * n_e * nl) / (kms * 1e-3) / 1e12,
+                            "gbs": round(by / (kms * 1e-3) / 1e9, 1)}
+        api.petgem_profile(ctx.h, False)
+        if pk:
+            kname, kd = max(pk.items(), key=lambda kv: kv[1]["ms"])
+            fp64 = fp64_peak(local)
+            plain["roofline"] = {"kernel": kname, "bound": "alu", "achieved": round(kd["tflops"], 3), "peak": fp64[0],
+                                 "unit": "TFLOP/s (FP64)", "frac": round(kd["tflops"] / fp64[0], 4),
+                                 "peak_source": fp64[1], "hbm_gbs": kd["gbs"], "hbm_frac": round(kd["gbs"] / hbm, 4)}
+            plain["kernels"] = {k: {kk: (round(vv, 3) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                                for k, v in pk.items()}
 
     # COCG (short-recurrence complex-symmetric solver), same workload and tolerance: mixed
     # precision timed like the headline, then one step with per-kernel events.
@@ -528,6 +564,41 @@ def run_ours(args):
         for cc in bctx:
             cc.close()
 
+    # A general mesh: the bench model with its node ids and tets in random order (seeded), so that
+    # the numbering carries none of the lattice's locality.  The SELL-32 layout needs at most 64
+    # distinct edge node-id differences and so falls back to the CSR product; mixed Jacobi-GMRES(50),
+    # timed like the headline, then one step with per-kernel events for the SpMV's rate.
+    general = None
+    if not args.no_general:
+        mg = synth.relabel(m)
+        gc = api.Context(local)
+
+        def gen_step(profile=False):
+            gc.mesh(mg.mesh.nodes, mg.mesh.tets)
+            gc.assemble(mg.freq, mg.sigma, mg.sigma_p, mg.sources)
+            if profile:
+                api.petgem_profile(gc.h, True)
+            _, gi, gst = gc.solve(precision=api.PREC_MIXED, tol=1e-8, use_graphs=1)
+            return gi
+
+        gen_step()
+        barrier()
+        t0 = time.perf_counter()
+        gi = gen_step()
+        barrier()
+        t_g = time.perf_counter() - t0
+        gen_step(profile=True)
+        nl, kms, by = api.petgem_kernel_stats(gc.h, "spmv_c64")
+        api.petgem_profile(gc.h, False)
+        general = {"mesh": "marine 64^3, node ids and tets randomly permuted", "edges": gc.n_edges,
+                   "s_per_source": round(t_g / S, 6), "iters": gi[0]["iters"],
+                   "true_rel_residual": gi[0]["true_rel_residual"],
+                   "spmv_c64": {"launches": nl, "avg_us": round(kms / max(nl, 1) * 1e3, 2),
+                                "gbs": round(by / (kms * 1e-3) / 1e9, 1) if kms else None,
+                                "frac_of_hbm": round(by / (kms * 1e-3) / 1e9 / hbm, 4) if kms else None,
+                                "layout": "CSR (no SELL-32 on this numbering)"}}
+        gc.close()
+
     # Many sources at several frequencies on the bench mesh (64 x-HEDs along x in [-4, 4] km at
     # 0.25, 1 and 3 Hz): the first frequency assembled in full, the others re-formed from the kept K
     # and M_sigma; each frequency's sources solved together by block COCG in mixed precision (the
@@ -716,6 +787,7 @@ def run_ours(args):
             "cocg": cocg,
             "block_multi_source": block,
             "uneven_batch": uneven,
+            "general_mesh": general,
             "graded_mesh": graded,
             "frequency_reuse": freq_reuse,
             "learned_network": learned,

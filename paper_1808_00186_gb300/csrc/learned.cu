@@ -589,7 +589,8 @@ Status conv3d_attributes() {
   static bool done = false;
   if (done) return Status{};
 #define PG_ATTR(CI, CO, NZ) \
-  PG_CUDA(cudaFuncSetAttribute(k_conv3d<CI, CO, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem(CI, CO, NZ)));
+  PG_CUDA(cudaFuncSetAttribute(k_conv3d<CI, CO, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                               conv_smem_launch(CI, CO, NZ)));
 #define PG_ATTR_NZ(CI, CO) PG_ATTR(CI, CO, 1) PG_ATTR(CI, CO, 2) PG_ATTR(CI, CO, 4)
   PG_ATTR_NZ(16, 16)
   PG_ATTR_NZ(16, 32)
@@ -621,7 +622,7 @@ Status conv3d(cudaStream_t s, int gx, int gy, int gz, int cin, int cout, const _
   const unsigned grid = (unsigned)(txy * ((gz + nz - 1) / nz));
 #define PG_CONV(CI, CO, NZ)                                                                                      \
   if (cin == CI && cout == CO && nz == NZ) {                                                                     \
-    k_conv3d<CI, CO, NZ><<<grid, 128, conv_smem(CI, CO, NZ), s>>>(x, w, bias, gx, gy, gz, relu ? 1 : 0, ybf, yf, err, \
+    k_conv3d<CI, CO, NZ><<<grid, 128, conv_smem_launch(CI, CO, NZ), s>>>(x, w, bias, gx, gy, gz, relu ? 1 : 0, ybf, yf, err, \
                                                                    stop);                                       \
     PG_CUDA(cudaGetLastError());                                                                                 \
     return Status{};                                                                                             \

@@ -36,24 +36,48 @@ __host__ __device__ constexpr int brick_plane(int nz) { return (kHaloX * kHaloY 
 __host__ __device__ constexpr int conv_smem(int cin, int cout, int nz) {
   return (cin / 8) * brick_plane(nz) + 27 * cout * cin * 2 + cout * 4 + 128;
 }
-// TMEM columns for NZ accumulators of COUT FP32 columns (a power of two, at least 32).
+// Planes per CTA from which the MMAs are shared between output planes: the A operand of tap dz
+// for output plane zl is brick plane zl + dz, so one MMA per brick plane and (dy, dx) with the
+// three z-taps' weights stacked (N = 3 COUT) adds that plane's contribution to three output
+// planes' accumulators at once: (NZ + 2) 9 MMAs instead of 27 NZ (54 against 108 at NZ = 4), at
+// the same issue cost (an M = 128 MMA costs the issuing thread the same for any N up to 64 and
+// little more up to 128).  The accumulators of planes -2, -1, NZ and NZ + 1 are scratch.
+__host__ __device__ constexpr bool conv_shares(int nz) { return nz >= 2; }
+// TMEM columns: NZ accumulators of COUT FP32 columns, NZ + 4 when the MMAs are shared (a power
+// of two, at least 32).
 __host__ __device__ constexpr unsigned conv_tmem_cols(int cout, int nz) {
-  return cout * nz <= 32 ? 32u : cout * nz <= 64 ? 64u : 128u;
+  return (conv_shares(nz) ? nz + 4 : nz) * cout <= 32    ? 32u
+         : (conv_shares(nz) ? nz + 4 : nz) * cout <= 64  ? 64u
+         : (conv_shares(nz) ? nz + 4 : nz) * cout <= 128 ? 128u
+                                                         : 256u;
+}
+// Dynamic shared memory a launch requests: at least conv_smem, and enough that the CTAs one SM
+// holds (233,472 bytes of shared memory, 1 KB reserved per CTA) never ask for more than the 512
+// TMEM columns, so no allocation waits for another CTA.
+__host__ __device__ constexpr int conv_smem_launch(int cin, int cout, int nz) {
+  return conv_smem(cin, cout, nz) > 233472 / (int)(512 / conv_tmem_cols(cout, nz) + 1) - 1024 + 16
+             ? conv_smem(cin, cout, nz)
+             : 233472 / (int)(512 / conv_tmem_cols(cout, nz) + 1) - 1024 + 16;
 }
 
-// Convolution weights as the kernel's shared-memory image: the B operand of tap t is the K-major
-// core-matrix tile of W[t][co][ci] (COUT rows, CIN columns), element (t, co, ci) at
-// t COUT CIN + core_offset(co, ci, CIN) / 2.  One contiguous bulk copy then loads all 27 taps.
+// Convolution weights as the kernel's shared-memory image, grouped by (dy, dx): group
+// g = 3 (dy+1) + (dx+1) is one K-major core-matrix tile of 3 COUT rows (CIN columns), the
+// weights of dz = +1, 0, -1 stacked in that order, so that a group is the B operand of a shared
+// MMA and one dz block of it (COUT rows, COUT CIN elements further per block) the B operand of a
+// single tap.  Element (t, co, ci) of W[t][co][ci], t = (dx+1) + 3 (dy+1) + 9 (dz+1), sits at
+// g 3 COUT CIN + core_offset((1 - dz) COUT + co, ci, CIN) / 2.  One bulk copy loads all 27 taps.
 __host__ __device__ inline int64_t conv_weight_index(int t, int co, int ci, int cin, int cout) {
-  return (int64_t)t * cout * cin + tc::core_offset(co, ci, cin) / 2;
+  const int g = t % 9, j = 2 - t / 9;
+  return (int64_t)g * 3 * cout * cin + tc::core_offset(j * cout + co, ci, cin) / 2;
 }
 
 // X: BF16 [gz][gy][gx][CIN]; Wc: the weights in the order above.  Grid: one CTA per (x-tile,
 // y-tile, z-group of NZ planes), x fastest.  Thread 0 starts the bulk copy of the weights; all
 // threads copy the brick (16-byte cp.async, zeros outside the grid) and the bias; thread 0 then
-// issues the 27 x CIN/16 x NZ MMAs (K = 16 each, the planes innermost so that consecutive MMAs go
-// to independent accumulators) into NZ TMEM accumulators and one commit; the four warps read
-// their 32 TMEM lanes each and store bias + (ReLU) to the voxels inside the grid.
+// issues the MMAs (K = 16 each) into the TMEM accumulators and one commit: (NZ + 2) 9 CIN/16
+// shared ones of N = 3 COUT when NZ >= 2 (conv_shares; the accumulators zeroed first), else
+// 27 CIN/16 of N = COUT; the four warps read their 32 TMEM lanes each and store bias + (ReLU) to
+// the voxels inside the grid.
 template <int CIN, int COUT, int NZ>
 __global__ void __launch_bounds__(128) k_conv3d(const __nv_bfloat16* __restrict__ X,
                                                 const __nv_bfloat16* __restrict__ Wc, const float* __restrict__ bias,
@@ -66,6 +90,7 @@ __global__ void __launch_bounds__(128) k_conv3d(const __nv_bfloat16* __restrict_
   constexpr int kVox = kHaloX * kHaloY * (NZ + 2);
   constexpr unsigned kWBytes = 27 * COUT * CIN * 2;
   constexpr unsigned kCols = conv_tmem_cols(COUT, NZ);
+  constexpr bool kShare = conv_shares(NZ);
   const int stopped = stop ? *stop : 0;  // consumed after the barrier set-up, which hides its latency
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* sX = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);  // NC planes
@@ -105,6 +130,14 @@ __global__ void __launch_bounds__(128) k_conv3d(const __nv_bfloat16* __restrict_
   }
   tc::cp_async_commit();
   if (warp == 0) tc::tmem_alloc(&tbase, kCols);
+  if (kShare) {  // every shared MMA accumulates: the accumulators start at zero
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+#pragma unroll
+    for (unsigned c = 0; c < (NZ + 4) * COUT; c += 16) tc::tmem_zero16(tbase + ((unsigned)(warp * 32) << 16) + c);
+    tc::tmem_wait_st();
+  }
   tc::cp_async_wait_all();
   tc::fence_proxy_async();  // the brick (generic proxy) becomes visible to the tensor core
   tc::fence_before();
@@ -118,19 +151,38 @@ __global__ void __launch_bounds__(128) k_conv3d(const __nv_bfloat16* __restrict_
       s_ok = 0;
       tc::mbar_wait(&bar[0], 0);
     } else {
-      const uint32_t idesc = tc::idesc_bf16(kConvRows, COUT);
       const uint64_t ad0 = tc::smem_desc(tc::smem_u32(sX), kPlane, kHaloX * 16);
       const uint64_t bd0 = tc::smem_desc(tc::smem_u32(sW), 128, (CIN / 8) * 128);
       // descriptor start addresses are in 16-byte units: a tap, K-step or plane adds its offset / 16
+      if (kShare) {
+        // brick plane p, tap (dy, dx): D columns [p COUT, (p + 3) COUT) are the accumulators of
+        // output planes p - 2, p - 1, p (dz = +1, 0, -1), accumulator a of plane a - 2
+        const uint32_t idesc = tc::idesc_bf16(kConvRows, 3 * COUT);
 #pragma unroll
-      for (int t = 0; t < 27; ++t) {
+        for (int p = 0; p < NZ + 2; ++p) {
 #pragma unroll
-        for (int ks = 0; ks < CIN / 16; ++ks) {
-          const uint64_t bd = bd0 + (uint64_t)((t * COUT * CIN * 2 + ks * 256) >> 4);
+          for (int g = 0; g < 9; ++g) {
 #pragma unroll
-          for (int zl = 0; zl < NZ; ++zl) {
-            const int aoff = (((zl + t / 9) * kHaloY + (t / 3) % 3) * kHaloX + t % 3) * 16 + 2 * ks * kPlane;
-            tc::mma_bf16(tmem + zl * COUT, ad0 + (uint64_t)(aoff >> 4), bd, idesc, t > 0 || ks > 0);
+            for (int ks = 0; ks < CIN / 16; ++ks) {
+              const int aoff = ((p * kHaloY + g / 3) * kHaloX + g % 3) * 16 + 2 * ks * kPlane;
+              const uint64_t bd = bd0 + (uint64_t)((g * 3 * COUT * CIN * 2 + ks * 256) >> 4);
+              tc::mma_bf16(tmem + p * COUT, ad0 + (uint64_t)(aoff >> 4), bd, idesc, true);
+            }
+          }
+        }
+      } else {
+        const uint32_t idesc = tc::idesc_bf16(kConvRows, COUT);
+#pragma unroll
+        for (int t = 0; t < 27; ++t) {
+#pragma unroll
+          for (int ks = 0; ks < CIN / 16; ++ks) {
+            const int woff = (t % 9) * 3 * COUT * CIN * 2 + (2 - t / 9) * COUT * CIN * 2 + ks * 256;
+            const uint64_t bd = bd0 + (uint64_t)(woff >> 4);
+#pragma unroll
+            for (int zl = 0; zl < NZ; ++zl) {
+              const int aoff = (((zl + t / 9) * kHaloY + (t / 3) % 3) * kHaloX + t % 3) * 16 + 2 * ks * kPlane;
+              tc::mma_bf16(tmem + zl * COUT, ad0 + (uint64_t)(aoff >> 4), bd, idesc, t > 0 || ks > 0);
+            }
           }
         }
       }
@@ -153,7 +205,7 @@ __global__ void __launch_bounds__(128) k_conv3d(const __nv_bfloat16* __restrict_
 #pragma unroll
       for (int c0 = 0; c0 < COUT; c0 += 16) {
         float acc[16];
-        tc::tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(zl * COUT + c0), acc);
+        tc::tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)((zl + (kShare ? 2 : 0)) * COUT + c0), acc);
         if (in) {
 #pragma unroll
           for (int i = 0; i < 16; ++i) {

@@ -109,6 +109,17 @@ __device__ inline void cp_async16(void* dst, const void* src) {
 __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Zeros into 32 lanes x 16 columns of TMEM starting at taddr (the warp's lanes), and the wait for
+// this thread's TMEM stores.
+__device__ inline void tmem_zero16(unsigned taddr) {
+  const uint32_t z = 0;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+      "r"(z)
+      : "memory");
+}
+__device__ inline void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // 32 lanes x 16 columns of 32-bit TMEM values starting at taddr (lane = warp's 32-row slice).
 __device__ inline void tmem_ld16(unsigned taddr, float* v) {
   uint32_t r[16];

@@ -194,6 +194,22 @@ def whole_space_model(n: int, half: float = 500.0, sigma: float = 0.5, sigma_p: 
                  [Dipole(*src, 0, 1.0)], rx)
 
 
+def relabel(model: Model, seed: int = 20260) -> Model:
+    """The same model with its node ids and its tet order randomly permuted (seeded): the geometry,
+    the conductivity of every tet and the sources are unchanged, only the numbering loses the
+    lattice's locality, as a general unstructured mesher's output may."""
+    rng = np.random.default_rng(seed)
+    nn, nt = model.mesh.n_nodes, len(model.mesh.tets)
+    pn = rng.permutation(nn)           # new node k is old node pn[k]
+    inv = np.empty(nn, dtype=np.int64)
+    inv[pn] = np.arange(nn)
+    pt = rng.permutation(nt)           # new tet k is old tet pt[k]
+    mesh = Mesh(model.mesh.n, model.mesh.lo, model.mesh.hi, np.ascontiguousarray(model.mesh.nodes[pn]),
+                np.ascontiguousarray(inv[model.mesh.tets[pt]].astype(np.int32)))
+    return Model(model.name + "_relabelled", mesh, np.ascontiguousarray(model.sigma[pt]), model.sigma_p, model.freq,
+                 list(model.sources), model.receivers, dict(model.extra))
+
+
 def marine_model(n: int = 64, n_src: int = 1, freq: float = 1.0, jitter: float = 0.18) -> Model:
     """Marine layered model on [-5, 5] x [-5, 5] x [-4, 1] km: seawater 3.3 S/m above
     z = 0, sediment 1 S/m below, a 2 x 2 km x 100 m reservoir slab of 0.01 S/m 1 km below

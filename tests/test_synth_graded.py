@@ -76,3 +76,23 @@ def test_graded_small_model_is_conforming():
     # every tet lies entirely on one side of the seafloor plane z = 0
     zt = m.mesh.nodes[m.mesh.tets][:, :, 2]
     assert np.all((zt.min(axis=1) >= 0.0) | (zt.max(axis=1) <= 0.0))
+
+
+def test_relabel_keeps_the_geometry_and_each_tets_conductivity():
+    m = synth.marine_model(4, n_src=2)
+    r = synth.relabel(m, seed=3)
+    assert r.mesh.nodes.shape == m.mesh.nodes.shape and r.mesh.tets.shape == m.mesh.tets.shape
+    assert r.mesh.tets.dtype == np.int32 and r.mesh.tets.min() >= 0 and r.mesh.tets.max() < r.mesh.n_nodes
+
+    def keyed(mesh, sig):  # each tet as its sorted vertex coordinates, with its conductivity
+        P = mesh.nodes[mesh.tets]                                  # [T, 4, 3]
+        order = np.lexsort(P.transpose(2, 0, 1)[::-1])            # sort the 4 vertices of each tet
+        Ps = np.take_along_axis(P, order[..., None], axis=1).reshape(len(P), 12)
+        k = np.lexsort(Ps.T[::-1])
+        return Ps[k], sig[k]
+
+    a, sa = keyed(m.mesh, m.sigma)
+    b, sb = keyed(r.mesh, r.sigma)
+    assert np.array_equal(a, b) and np.array_equal(sa, sb)
+    assert not np.array_equal(r.mesh.tets, m.mesh.tets)           # the numbering did change
+    assert r.sources == m.sources and r.freq == m.freq and r.sigma_p == m.sigma_p
