@@ -45,6 +45,8 @@ def parse():
                    help="sources of the three-frequency block solve on the bench mesh (0 = skip)")
     p.add_argument("--bathy-n", type=int, default=96, help="cells per axis of the bathymetry case (0 = skip)")
     p.add_argument("--bathy-sources", type=int, default=4, help="sources of the bathymetry case solved with the network")
+    p.add_argument("--bathy-block-sources", type=int, default=32,
+                   help="sources of the bathymetry case in one learned block solve (0 = skip)")
     p.add_argument("--profile-step", action="store_true",
                    help="run one untimed step of the hot path and exit (the command profilers capture)")
     p.add_argument("--precision", default="mixed", choices=["mixed", "c128"], help="solver of --profile-step")
@@ -679,6 +681,29 @@ def run_ours(args):
                                          "worst_true_rel_residual": max(i["true_rel_residual"] for i in il),
                                          "not_converged": [j for j, i in enumerate(il) if i["status"] != api.OK]}
         del xs4
+        # All sources in one learned block solve (flexible GMRES on interleaved block vectors, the
+        # network applied to each source's column, one SpMM per step), mixed precision, to 1e-8.
+        # A short solve first sizes the block workspace and runs the SpMM autotuner.
+        if args.bathy_block_sources > 0:
+            nbs = min(args.bathy_block_sources, len(m4.sources))
+            c4.assemble(m4.freq, m4.sigma, m4.sigma_p, m4.sources[:nbs])
+            xb4 = torch.zeros((nbs, E4), dtype=torch.complex128, device=dev)
+            c4.solve(xb4, precision=api.PREC_MIXED, precond=LEARNED, tol=1e-8, batch=0, max_iters=60,
+                     allow_not_converged=True)
+            barrier()
+            t0 = time.perf_counter()
+            xb4.zero_()
+            _, ibl, _ = c4.solve(xb4, precision=api.PREC_MIXED, precond=LEARNED, tol=1e-8, batch=0,
+                                 allow_not_converged=True, max_iters=60000)
+            barrier()
+            dt = time.perf_counter() - t0
+            bathy["learned_block_mixed"] = {"sources": nbs, "s_per_source": round(dt / nbs, 6),
+                                            "iters_max": max(i["iters"] for i in ibl),
+                                            "iters": [i["iters"] for i in ibl],
+                                            "fell_back": [i["fell_back"] for i in ibl],
+                                            "worst_true_rel_residual": max(i["true_rel_residual"] for i in ibl),
+                                            "not_converged": [j for j, i in enumerate(ibl) if i["status"] != api.OK]}
+            del xb4
         c4.assemble(m4.freq, m4.sigma, m4.sigma_p, m4.sources[:1])
         x1 = torch.zeros((1, E4), dtype=torch.complex128, device=dev)
         for name, kw in (("jacobi_gmres_mixed", dict(use_graphs=1)), ("cocg_mixed", dict(method=api.METHOD_COCG))):

@@ -70,11 +70,14 @@ enum { PETGEM_PRECOND_JACOBI = 0, PETGEM_PRECOND_LEARNED = 1, PETGEM_PRECOND_SSO
  *     inner_tol or restart steps have run; x and the residual stay complex128.
  *   batch: number of sources iterated together (their SpMVs become one SpMM); 0 = all (groups
  *     of up to 32).  batch = 1 solves the sources one after the other.
- *   precond = PETGEM_PRECOND_LEARNED (single-source solves): flexible GMRES whose every step
- *     uses the learned auxiliary-space preconditioner z = M^{-1} v (petgem_learned_create; in the
- *     Jacobi-scaled variables D M^{-1} v), with two-pass Gram-Schmidt, from the first cycle on.
- *     A learned cycle that removes less than 10 % of the FP64 residual is undone and the solve
- *     continues with Jacobi alone (info.fell_back).
+ *   precond = PETGEM_PRECOND_LEARNED: flexible GMRES whose every step uses the learned
+ *     auxiliary-space preconditioner z = M^{-1} v (petgem_learned_create; in the Jacobi-scaled
+ *     variables D M^{-1} v) from the first cycle on.  Sources one by one (batch = 1): classical
+ *     Gram-Schmidt with a second pass when the norm fell below 1/sqrt(10).  Sources together
+ *     (batch != 1): the block solve above, with the network applied to every live source's
+ *     column in each step and one SpMM on the block of preconditioned vectors; classical
+ *     Gram-Schmidt, one pass.  A learned cycle that removes less than 10 % of a source's FP64
+ *     residual is undone and that source continues with Jacobi alone (info.fell_back).
  *   precond = PETGEM_PRECOND_SSOR (method SQMR only; PETGEM_ERR_UNSUPPORTED otherwise):
  *     symmetric SOR, the preconditioner of the paper's Section 5.3 runs, in the order of a
  *     multicolour colouring of the matrix graph (petgem_colouring): with A = D + L + U split by

@@ -6,6 +6,12 @@
 //
 // Layout: a "block vector" holds element (row i, source s) at i * P + s, P = the group size padded
 // to a power of two (2..32); padding sources have a zero right-hand side and stop at once.
+//
+// With the learned preconditioner the group runs flexible GMRES: each step applies the network to
+// every live source's column of V_j (read and written in place in the interleaved layout) into
+// the block vector Z_j, the SpMM takes Z_j, and the solution update uses Z.  As in the
+// single-source solve, a source whose learned cycle removes less than 10 % of its FP64 residual
+// has that cycle undone and goes on with Jacobi alone (its Z columns are copies of V's).
 #include <math.h>
 
 #include <algorithm>
@@ -14,6 +20,7 @@
 #include "krylov.cuh"
 #include "gs.cuh"
 #include "bands.cuh"
+#include "learned.cuh"
 
 namespace petgem {
 namespace {
@@ -25,6 +32,31 @@ struct BGroup {
   int all_done;
   unsigned long long gbar;  // arrivals at the projection kernel's grid barrier (only grows)
 };
+
+// -------------------------------------------------------------------- per-source columns
+// dst[i P + s] = src[i P + s] for the n rows (one source's column of a block vector).
+template <typename T, int P>
+__global__ void k_bcol_copy(const T* __restrict__ src, T* __restrict__ dst, int64_t n, int s) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[i * P + s] = src[i * P + s];
+}
+
+// out[s] += sum_i |v[i P + s]|^2 for every source (one pass over the block vector; FP64 partial
+// sums per block, added atomically: the result decides only whether a cycle gained 10 %).
+template <int P>
+__global__ void __launch_bounds__(256) k_bcol_norm2(const double2* __restrict__ v, int64_t n, double* __restrict__ out) {
+  __shared__ double red[256];
+  const int tid = threadIdx.x;
+  double a = 0.0;
+  for (int64_t e = blockIdx.x * 256 + tid; e < n * P; e += (int64_t)gridDim.x * 256) a += v[e].x * v[e].x + v[e].y * v[e].y;
+  red[tid] = a;  // the grid stride is a multiple of P, so thread tid always sees source tid % P
+  __syncthreads();
+  if (tid < P) {
+    double t = 0.0;
+    for (int k = tid; k < 256; k += P) t += red[k];
+    atomicAdd(&out[tid], t);
+  }
+}
 
 // -------------------------------------------------------------------- layout changes
 template <int P>
@@ -271,6 +303,13 @@ Status run_group(petgem_ctx* c, const petgem_solve_opts& o, const double2* b, do
   if (fresh) PG_CUDA(cudaMemsetAsync(S->Vb.ptr, 0, S->Vb.bytes, s));
   S->bprec = prec;
   S->bld_used = ldb;
+  const bool learned_req = o.precond == PETGEM_PRECOND_LEARNED;
+  if (learned_req) {
+    PG_TRY(S->Zb.reserve((size_t)m * ldb * sizeof(T)));
+    PG_CUDA(cudaMemsetAsync(S->Zb.ptr, 0, (size_t)m * ldb * sizeof(T), s));  // finite in every column
+    PG_TRY(S->Usb.reserve(n * P * sizeof(double2)));
+    PG_TRY(S->bnorm2.reserve(P * sizeof(double)));
+  }
   PG_TRY(S->Ub.reserve(n * P * sizeof(double2)));
   PG_TRY(S->Rb.reserve(n * P * sizeof(double2)));
   PG_TRY(S->Bb.reserve(n * P * sizeof(double2)));
@@ -334,28 +373,83 @@ Status run_group(petgem_ctx* c, const petgem_solve_opts& o, const double2* b, do
   }
   const double spmm_bytes = (double)c->nnz * (sizeof(T) + 4) + 8.0 * (n + 1) + 2.0 * n * P * sizeof(T);
   int64_t max_done = 0;
+  // learned preconditioner, per source: on from the start; the previous cycle's state
+  constexpr double kLearnedRate = 0.9;
+  std::vector<int> learned_on(P, 0), prev_learned(P, 0), fell_back(P, 0);
+  std::vector<double> prev_rel(P, 0.0);
+  for (int i = 0; i < S_g; ++i) learned_on[i] = learned_req && !finished[i];
+  T* Zb = learned_req ? S->Zb.as<T>() : nullptr;
+  const unsigned ncol = blocks_for(n, 256);
+  auto residual = [&]() -> Status {
+    KernelTimer kt(c, "bresidual_c128", (double)c->nnz * 20 + 48.0 * n * P);
+    k_bresidual<P><<<blocks_for(n * P, 256), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), ahat128,
+                                                          S->Ub.as<double2>(), S->Bb.as<double2>(),
+                                                          S->Rb.as<double2>(), n);
+    c->launches++;
+    PG_CUDA(cudaGetLastError());
+    return Status{};
+  };
   while (true) {
-    {
-      KernelTimer kt(c, "bresidual_c128", (double)c->nnz * 20 + 48.0 * n * P);
-      k_bresidual<P><<<blocks_for(n * P, 256), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), ahat128,
-                                                            S->Ub.as<double2>(), S->Bb.as<double2>(),
-                                                            S->Rb.as<double2>(), n);
+    PG_TRY(residual());
+    if (learned_req) {
+      bool judge = false, any_on = false;
+      for (int i = 0; i < S_g; ++i) judge |= !finished[i] && prev_learned[i];
+      if (judge) {  // did each source's learned cycle remove at least 10 % of its FP64 residual?
+        std::vector<double> rn2(P, 0.0);
+        PG_CUDA(cudaMemsetAsync(S->bnorm2.ptr, 0, P * sizeof(double), s));
+        k_bcol_norm2<P><<<std::min<unsigned>(blocks_for(n * P, 256), 8 * S->sms), 256, 0, s>>>(
+            S->Rb.as<double2>(), n, S->bnorm2.as<double>());
+        PG_CUDA(cudaMemcpyAsync(rn2.data(), S->bnorm2.ptr, P * sizeof(double), cudaMemcpyDeviceToHost, s));
+        PG_CUDA(cudaStreamSynchronize(s));
+        bool undone = false;
+        for (int i = 0; i < S_g; ++i) {
+          if (finished[i] || !prev_learned[i]) continue;
+          const double rate = sqrt(rn2[i] / bn2[i]) / prev_rel[i];
+          if (!(rate < kLearnedRate)) {  // undo that source's learned cycle; Jacobi from here on
+            k_bcol_copy<double2, P><<<ncol, 256, 0, s>>>(S->Usb.as<double2>(), S->Ub.as<double2>(), n, i);
+            learned_on[i] = 0;
+            fell_back[i] = 1;
+            undone = true;
+          }
+        }
+        c->launches += 2;
+        if (undone) PG_TRY(residual());
+      }
+      for (int i = 0; i < S_g; ++i) any_on |= !finished[i] && learned_on[i];
+      if (any_on)
+        PG_CUDA(cudaMemcpyAsync(S->Usb.ptr, S->Ub.ptr, n * P * sizeof(double2), cudaMemcpyDeviceToDevice, s));
     }
     k_bcycle_init<T, P><<<grid_init, 256, 0, s>>>(S->Rb.as<double2>(), V, n, sts, grp, part, S->btol.as<double>(),
                                                   prec == PETGEM_PREC_MIXED ? o.inner_tol : 0.0);
-    c->launches += 2;
+    c->launches += 1;
     const int mj = (int)std::min<int64_t>(m, std::max<int64_t>(o.max_iters - max_done, 0));
     for (int j = 0; j < mj; ++j) {
       T* vj = V + (int64_t)j * ldb;
+      const T* xin = vj;
+      if (learned_req) {  // z_j of every live source: the network (learned) or v_j itself (Jacobi)
+        T* zj = Zb + (int64_t)j * ldb;
+        for (int i = 0; i < S_g; ++i) {
+          if (finished[i]) continue;
+          if (learned_on[i]) {
+            KernelTimer kt(c, "learned_apply", 0.0, j, i);
+            PG_TRY(c->net->apply<T>(s, vj, c->slots.as<int32_t>(), n, zj, false, &sts[i].done, P, i));
+            c->launches += 28;
+          } else {
+            k_bcol_copy<T, P><<<ncol, 256, 0, s>>>(vj, zj, n, i);
+            c->launches++;
+          }
+        }
+        xin = zj;
+      }
       {
         KernelTimer kt(c, sizeof(T) == 8 ? "bspmm_c64" : "bspmm_c128", spmm_bytes);
         if (spmm_form >= 0)
-          PG_TRY((launch_spmm_band<T, P>(c, s, spmm_form, ahat, (const T*)vj, vj + ldb, &grp->all_done,
+          PG_TRY((launch_spmm_band<T, P>(c, s, spmm_form, ahat, xin, vj + ldb, &grp->all_done,
                                          SpmmStoreGmres{sts, j})));
         else
           PG_CUDA(pdl_launch(k_bspmm<T, P>, dim3(spmm_grid), dim3(256), 0, s, false,
                              (const int64_t*)c->row_ptr.as<int64_t>(), (const int32_t*)c->col.as<int32_t>(), ahat,
-                             (const T*)vj, vj + ldb, n, (const GState*)sts, (const BGroup*)grp, j));
+                             xin, vj + ldb, n, (const GState*)sts, (const BGroup*)grp, j));
       }
       {
         KernelTimer kt(c, sizeof(T) == 8 ? "bmdot_c64" : "bmdot_c128", (double)(j + 2) * n * P * sizeof(T));
@@ -370,7 +464,8 @@ Status run_group(petgem_ctx* c, const petgem_solve_opts& o, const double2* b, do
     }
     PG_CUDA(cudaGetLastError());
     k_bbacksolve<<<P, 32, 0, s>>>(sts);
-    k_bxupdate<T, P><<<blocks_for(n * P, 256), 256, 0, s>>>(V, ldb, n, S->Ub.as<double2>(), sts, std::max(mj, 1));
+    k_bxupdate<T, P><<<blocks_for(n * P, 256), 256, 0, s>>>(learned_req ? Zb : V, ldb, n, S->Ub.as<double2>(), sts,
+                                                            std::max(mj, 1));
     c->launches += 2;
     PG_CUDA(cudaGetLastError());
     PG_CUDA(cudaMemcpy2DAsync(hs.data(), sizeof(HostState), sts, sizeof(GState), sizeof(HostState), P,
@@ -397,6 +492,8 @@ Status run_group(petgem_ctx* c, const petgem_solve_opts& o, const double2* b, do
       iters[i] += hs[i].k;
       cycles[i] += 1;
       max_done = std::max(max_done, iters[i]);
+      prev_learned[i] = learned_on[i];
+      prev_rel[i] = relres[i];
       if (hs[i].done == 2) {
         status[i] = hs[i].timeout ? PETGEM_ERR_TIMEOUT : PETGEM_ERR_BREAKDOWN;
         finished[i] = 1;
@@ -417,7 +514,9 @@ Status run_group(petgem_ctx* c, const petgem_solve_opts& o, const double2* b, do
     info[i].true_rel_residual = bn2[i] == 0.0 ? 0.0 : relres[i];
     info[i].status = status[i];
     info[i].spmv_lanes = spmm_form >= 0 ? kBandHeights[spmm_form] : 1;
+    info[i].fell_back = fell_back[i];
   }
+  if (learned_req) PG_TRY(nn::check_err(s, c->net->err.as<int>(), "petgem_solve (learned, block)"));
   return Status{};
 }
 
@@ -435,6 +534,8 @@ Status run_group_p(petgem_ctx* c, const petgem_solve_opts& o, const double2* b, 
 
 Status run_solve_block(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_solve_info* info) {
   const int64_t n = c->n_edges;
+  if (o.precond == PETGEM_PRECOND_LEARNED)
+    PG_TRY(c->net->features(c->stream, c->sigma.as<double>(), c->sigma_p, c->omega, c->lattice_h));
   const int group = o.batch <= 0 ? kBMaxP : std::min(o.batch, kBMaxP);
   for (int s0 = 0; s0 < c->n_src; s0 += group) {
     const int S_g = std::min(group, c->n_src - s0);

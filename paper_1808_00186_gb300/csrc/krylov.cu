@@ -619,7 +619,7 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
 void destroy_solver(petgem_ctx* c) {
   if (!c->solver) return;
   Solver* S = c->solver;
-  for (DevBuf* d : {&S->ahat128, &S->ahat64, &S->sell128, &S->sell64, &S->dinv, &S->V, &S->u, &S->r, &S->partials, &S->state, &S->Z, &S->usave,
+  for (DevBuf* d : {&S->ahat128, &S->ahat64, &S->sell128, &S->sell64, &S->dinv, &S->V, &S->u, &S->r, &S->partials, &S->state, &S->Z, &S->usave, &S->Zb, &S->Usb, &S->bnorm2,
                     &S->Vb, &S->Ub, &S->Rb, &S->Bb, &S->bstates, &S->bgroup, &S->btol})
     d->release();
   if (S->graph) cudaGraphExecDestroy(S->graph);
@@ -640,7 +640,7 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
   const int m = o.restart;
   if (m < 1 || m > kMaxRestart) return Status{PETGEM_ERR_UNSUPPORTED, "restart must be in [1, 62]"};
   if (o.method == PETGEM_METHOD_COCG || o.method == PETGEM_METHOD_SQMR) return run_solve_cocg(c, o, x, info);
-  const bool block = o.batch != 1 && c->n_src > 1 && o.precond != PETGEM_PRECOND_LEARNED;
+  const bool block = o.batch != 1 && c->n_src > 1;
   PG_TRY(prepare(c, m, o.precision, !block));
   if (block) return run_solve_block(c, o, x, info);
   Solver* S = c->solver;

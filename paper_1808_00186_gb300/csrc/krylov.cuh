@@ -46,6 +46,7 @@ struct Solver {
   // multi-source solve (block.cu): interleaved basis / iterate / residual / right-hand sides,
   // one Arnoldi state per source, a group flag and the per-source stopping thresholds
   DevBuf Vb, Ub, Rb, Bb, bstates, bgroup, btol;
+  DevBuf Zb, Usb, bnorm2;  // learned block FGMRES: Z basis, saved solution, per-source norms
   int bprec = -1;
   int64_t bld_used = 0;
   int64_t n_blocks = 0;

@@ -301,7 +301,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_hx_in(const T* __restrict__ r, const int32_t* __restrict__ slot_edge,
                                                const float4* __restrict__ tang, const float4* __restrict__ aux,
                                                int gx, int gy, int gz, float* __restrict__ out,
-                                               double* __restrict__ part, const int* __restrict__ stop) {
+                                               double* __restrict__ part, const int* __restrict__ stop,
+                                               int64_t stride, int64_t off) {
   if (stop && *stop) return;
   using R = typename real_of<T>::type;
   __shared__ double red[8];
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(256) k_hx_in(const T* __restrict__ r, const in
       incident_edges(v, x, y, z, gx, gy, slot_edge, tang, I);
       T rv[14];
 #pragma unroll
-      for (int k = 0; k < 14; ++k) rv[k] = I.e[k] >= 0 ? r[I.e[k]] : T{0, 0};
+      for (int k = 0; k < 14; ++k) rv[k] = I.e[k] >= 0 ? r[(int64_t)I.e[k] * stride + off] : T{0, 0};
       R gr = 0, gi = 0, pr[3] = {0, 0, 0}, pi[3] = {0, 0, 0};
 #pragma unroll
       for (int k = 0; k < 14; ++k) {
@@ -397,13 +398,13 @@ template <typename T, bool XS>
 __global__ void k_hx_out(const T* __restrict__ r, const int32_t* __restrict__ slot, int64_t E,
                          const float* __restrict__ y, const float4* __restrict__ aux, const float4* __restrict__ tang,
                          const float* __restrict__ scal, const T* __restrict__ diag, int gx, int gy,
-                         T* __restrict__ z, const int* __restrict__ stop) {
+                         T* __restrict__ z, const int* __restrict__ stop, int64_t stride, int64_t off) {
   if (stop && *stop) return;
   using R = typename real_of<T>::type;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= E) return;
   const int32_t sl = slot[e];
-  const T re = r[e];
+  const T re = r[e * stride + off];
   R cr = 0, ci = 0;
   if (sl >= 0) {
     const int64_t lo = sl / 7;
@@ -437,7 +438,7 @@ __global__ void k_hx_out(const T* __restrict__ r, const int32_t* __restrict__ sl
     o.x = rr + (dr * cr - di * ci);
     o.y = ri + (dr * ci + di * cr);
   }
-  z[e] = o;
+  z[e * stride + off] = o;
 }
 // The diagonal of A in single precision, for the complex64 application.
 __global__ void k_diag_f32(const double2* __restrict__ d, int64_t n, float2* __restrict__ o) {
@@ -861,7 +862,7 @@ Status Net::prepare_aux(petgem_ctx* c) {
 // Network input x0 from an edge vector r (a residual): the gathered, scaled node fields, the scale
 // s in scal[0..1] (1 / s, s), the two features.
 template <typename T>
-Status Net::load_input(cudaStream_t s, const T* r, int64_t E, const int* stop) {
+Status Net::load_input(cudaStream_t s, const T* r, int64_t E, const int* stop, int64_t stride, int64_t off) {
   (void)E;
   const int gx = g[0][0], gy = g[0][1], gz = g[0][2];
   const unsigned blocks = nb(V[0]);
@@ -871,7 +872,7 @@ Status Net::load_input(cudaStream_t s, const T* r, int64_t E, const int* stop) {
     KernelTimer kt(ctx, sizeof(T) == 8 ? "hx_in_c64" : "hx_in_c128",
                    2.0 * sizeof(T) * (double)ctx->n_edges + (double)V[0] * (14.0 * 20.0 + 32.0 + 16.0));
     k_hx_in<T><<<blocks, 256, 0, s>>>(r, slot_edge.as<int32_t>(), tang.as<float4>(), aux.as<float4>(), gx, gy, gz,
-                                      nodes8.as<float>(), npart.as<double>(), stop);
+                                      nodes8.as<float>(), npart.as<double>(), stop, stride, off);
   }
   const int64_t n_in = (int64_t)std::max(gx - 2, 0) * std::max(gy - 2, 0) * std::max(gz - 2, 0);
   k_hx_scale<<<1, 256, 0, s>>>(npart.as<double>(), (int)blocks, n_in, scal.as<float>(), stop);
@@ -883,8 +884,8 @@ Status Net::load_input(cudaStream_t s, const T* r, int64_t E, const int* stop) {
 
 template <typename T>
 Status Net::apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T* z, bool xspace,
-                  const int* stop) {
-  PG_TRY(load_input(s, r, E, stop));
+                  const int* stop, int64_t stride, int64_t off) {
+  PG_TRY(load_input(s, r, E, stop, stride, off));
   PG_TRY(forward(s, stop));
   const T* d = sizeof(T) == 8 ? reinterpret_cast<const T*>(diag32.as<float2>())
                               : reinterpret_cast<const T*>(ctx->diag.as<double2>());
@@ -893,18 +894,18 @@ Status Net::apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T*
                  (double)E * (3.0 * sizeof(T) + 4.0 + 16.0 + 96.0));
   if (xspace)
     k_hx_out<T, true><<<nb(E), 256, 0, s>>>(r, slot, E, y.as<float>(), aux.as<float4>(), tang.as<float4>(),
-                                            scal.as<float>(), d, g[0][0], g[0][1], z, stop);
+                                            scal.as<float>(), d, g[0][0], g[0][1], z, stop, stride, off);
   else
     k_hx_out<T, false><<<nb(E), 256, 0, s>>>(r, slot, E, y.as<float>(), aux.as<float4>(), tang.as<float4>(),
-                                             scal.as<float>(), d, g[0][0], g[0][1], z, stop);
+                                             scal.as<float>(), d, g[0][0], g[0][1], z, stop, stride, off);
   PG_CUDA(cudaGetLastError());
   return Status{};
 }
 
 template Status Net::apply<float2>(cudaStream_t, const float2*, const int32_t*, int64_t, float2*, bool,
-                                  const int*);
+                                  const int*, int64_t, int64_t);
 template Status Net::apply<double2>(cudaStream_t, const double2*, const int32_t*, int64_t, double2*, bool,
-                                   const int*);
+                                   const int*, int64_t, int64_t);
 
 // One training sample, r = the residual of a solver iterate (complex128 edge vector).  Loss: the
 // residual angle L = 1 - |<r, A z>|^2 / (|r|^2 |A z|^2) of the preconditioned direction
@@ -918,7 +919,7 @@ Status Net::sample_grad(cudaStream_t s, petgem_ctx* c, const double2* r, const i
   double2* gw = gtmp.as<double2>();
   k_hx_out<double2, false><<<nb(E), 256, 0, s>>>(r, slot, E, y.as<float>(), aux.as<float4>(), tang.as<float4>(),
                                                  scal.as<float>(), c->diag.as<double2>(), g[0][0], g[0][1], zu,
-                                                 nullptr);
+                                                 nullptr, 1, 0);
   k_ahat_apply<<<nb(E), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(),
                                      c->diag.as<double2>(), zu, E, w);
   k_angle_dots<<<1, 1024, 0, s>>>(r, w, E, dvec.as<double>(), loss_acc.as<double>());

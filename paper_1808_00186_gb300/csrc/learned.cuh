@@ -68,11 +68,14 @@ struct Net {
   Status forward(cudaStream_t s, const int* stop = nullptr);
   Status backward(cudaStream_t s, bool acc);
   Status prepare_aux(petgem_ctx* c);
-  template <typename T> Status load_input(cudaStream_t s, const T* r, int64_t E, const int* stop = nullptr);
+  template <typename T> Status load_input(cudaStream_t s, const T* r, int64_t E, const int* stop = nullptr,
+                                          int64_t stride = 1, int64_t off = 0);
   // z = D (D^{-1} r + G phi + Pi w) (the solver's Jacobi-scaled variables) or, with xspace,
-  // z = D^{-1} r + G phi + Pi w, for the residual r of E entries.
+  // z = D^{-1} r + G phi + Pi w, for the residual r of E entries.  Entry e of r and z sits at
+  // e stride + off (one source of an interleaved block vector: stride = the group size).
   template <typename T> Status apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T* z,
-                                     bool xspace = false, const int* stop = nullptr);
+                                     bool xspace = false, const int* stop = nullptr, int64_t stride = 1,
+                                     int64_t off = 0);
   Status sample_grad(cudaStream_t s, petgem_ctx* c, const double2* r, const int32_t* slot, int64_t E, bool acc);
   Status adam_step(cudaStream_t s, float lr, float gscale);
   Status features(cudaStream_t s, const double* sigma, double sigma_p, double omega, double h);

@@ -268,3 +268,42 @@ def test_learned_cycles_replayed_as_cuda_graphs_are_bit_identical():
                 out.append((x.cpu().numpy(), info))
             for x, info in out[1:]:
                 assert np.array_equal(x, out[0][0]) and info == out[0][1]
+
+
+@pytest.mark.parametrize("precision", [api.PREC_MIXED, api.PREC_C128])
+def test_learned_block_fgmres_matches_oracle_and_single_source_solves(precision):
+    """Several sources of one frequency in one learned block solve (flexible GMRES on interleaved
+    block vectors, the network applied to every source's column, one SpMM per step): every
+    source meets the FP64 residual bar, matches its own oracle solution and receivers, and takes
+    about the iterations of its single-source learned solve (the SpMM sums in another order)."""
+    n = 12
+    m = PL.random_block_model(n, 10004)
+    rng = np.random.default_rng(5)
+    m.sources = [synth.Dipole(float(x), float(y), float(z), 0, 1.0)
+                 for x, y, z in zip(rng.uniform(-300, 300, 5), rng.uniform(-300, 300, 5), rng.uniform(-200, 200, 5))]
+    ref = oracle.System(m.mesh.nodes, m.mesh.tets, m.sigma, m.sigma_p, m.freq, synth.sources_array(m.sources))
+    xr, _, st_r = ref.solve(tol=1e-8)
+    assert st_r == oracle.OK
+    _, _, _, b = ref.system()
+    rr, _ = ref.receivers(xr, m.receivers)
+    p = np.load(PL.WEIGHTS)
+    with api.Context(0) as ctx:
+        ctx.mesh(m.mesh.nodes, m.mesh.tets)
+        ctx.assemble(m.freq, m.sigma, m.sigma_p, m.sources)
+        api.petgem_learned_create(ctx.h, n, n, n)
+        api.petgem_learned_params(ctx.h, set_params=p)
+        xb, ib, st = ctx.solve(precision=precision, precond=api.PRECOND_LEARNED, batch=0, tol=1e-8)
+        assert st == api.OK
+        xs, isg, st = ctx.solve(precision=precision, precond=api.PRECOND_LEARNED, batch=1, tol=1e-8)
+        assert st == api.OK
+        rcv = torch.empty((len(m.sources), len(m.receivers), 3, 3), dtype=torch.complex128, device="cuda")
+        api.petgem_receivers(ctx.h, torch.as_tensor(m.receivers, device="cuda"), xb, rcv)
+    xb = xb.cpu().numpy()
+    for s in range(len(m.sources)):
+        assert ib[s]["status"] == api.OK and ib[s]["true_rel_residual"] <= 1e-8, (s, ib[s])
+        assert np.linalg.norm(b[s] - ref.spmv(xb[s])) / np.linalg.norm(b[s]) <= 1.0001e-8
+        assert np.linalg.norm(xb[s] - xr[s]) / np.linalg.norm(xr[s]) <= 1e-6
+        assert ib[s]["fell_back"] == isg[s]["fell_back"]
+        assert abs(ib[s]["iters"] - isg[s]["iters"]) <= 0.1 * isg[s]["iters"] + 5, (s, ib[s], isg[s])
+    assert np.linalg.norm(rcv.cpu().numpy() - rr) / np.linalg.norm(rr) <= 1e-6
+    print("\nlearned block / single-source iterations:", [(i["iters"], j["iters"]) for i, j in zip(ib, isg)])
