@@ -480,8 +480,9 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
   const double vbytes = (double)sizeof(T) * n;
   const bool c128 = sizeof(T) == 16;
   const size_t pending0 = c->pending.size();
-  // SELL-32 products (renumbered basis) for Jacobi cycles when the mesh has the layout
-  const bool sell = c->sell_ok && !learned;
+  // SELL-32 products (renumbered basis) when the mesh has the layout; learned cycles then run the
+  // network's maps in the same row order (Net::renumber)
+  const bool sell = c->sell_ok;
   const int32_t* perm = sell ? c->sell_perm.as<int32_t>() : nullptr;
   {
     KernelTimer kt(c, c128 ? "cycle_init_c128" : "cycle_init_c64", 16.0 * n + vbytes);
@@ -507,7 +508,7 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
       if (learned) {  // every step: z = D (D^{-1} v + G phi + Pi w), the network's auxiliary-space direction
         T* zj = Z + (int64_t)j * ld;
         KernelTimer kt(c, "learned_apply", 0.0, j, 0);
-        PG_TRY(c->net->apply<T>(s, vj, c->slots.as<int32_t>(), n, zj, false, &st->done));
+        PG_TRY(c->net->apply<T>(s, vj, c->slots.as<int32_t>(), n, zj, false, &st->done, 1, 0, sell));
         c->launches += 28;
         xin = zj;
       }
@@ -681,6 +682,7 @@ Status run_solve(petgem_ctx* c, const petgem_solve_opts& o, double2* x, petgem_s
       PG_TRY(S->Z.reserve((size_t)m * S->ld * (o.precision == PETGEM_PREC_MIXED ? sizeof(float2) : sizeof(double2))));
       PG_TRY(S->usave.reserve(n * sizeof(double2)));
       PG_TRY(c->net->features(s, c->sigma.as<double>(), c->sigma_p, c->omega, c->lattice_h));
+      if (c->sell_ok) PG_TRY(c->net->renumber(c));
     }
     bool prev_learned = false;
     auto residual = [&]() -> Status {

@@ -398,7 +398,8 @@ template <typename T, bool XS>
 __global__ void k_hx_out(const T* __restrict__ r, const int32_t* __restrict__ slot, int64_t E,
                          const float* __restrict__ y, const float4* __restrict__ aux, const float4* __restrict__ tang,
                          const float* __restrict__ scal, const T* __restrict__ diag, int gx, int gy,
-                         T* __restrict__ z, const int* __restrict__ stop, int64_t stride, int64_t off) {
+                         T* __restrict__ z, const int* __restrict__ stop, int64_t stride, int64_t off,
+                         const int32_t* __restrict__ zrow) {
   if (stop && *stop) return;
   using R = typename real_of<T>::type;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -438,7 +439,15 @@ __global__ void k_hx_out(const T* __restrict__ r, const int32_t* __restrict__ sl
     o.x = rr + (dr * cr - di * ci);
     o.y = ri + (dr * ci + di * cr);
   }
-  z[e * stride + off] = o;
+  z[(zrow ? (int64_t)zrow[e] : e) * stride + off] = o;  // zrow: z in the SELL-32 row order
+}
+// out[e] = in[inv[e]]: a vector in the SELL-32 row order back in edge order.
+template <typename T>
+__global__ void k_from_rows(const T* __restrict__ in, const int32_t* __restrict__ inv, int64_t n, T* __restrict__ out,
+                            const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < n) out[e] = in[inv[e]];
 }
 // The diagonal of A in single precision, for the complex64 application.
 __global__ void k_diag_f32(const double2* __restrict__ d, int64_t n, float2* __restrict__ o) {
@@ -884,7 +893,16 @@ Status Net::load_input(cudaStream_t s, const T* r, int64_t E, const int* stop, i
 
 template <typename T>
 Status Net::apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T* z, bool xspace,
-                  const int* stop, int64_t stride, int64_t off) {
+                  const int* stop, int64_t stride, int64_t off, bool renum) {
+  // renum: both maps run in edge order, where an edge's node data and a node's edges are adjacent
+  // (measured faster than running the edge-wise map over the SELL-32 rows); r is gathered into
+  // edge order and z written back to its rows through zrow
+  const int32_t* zrow = nullptr;
+  if (renum) {
+    k_from_rows<T><<<nb(E), 256, 0, s>>>(r, ctx->sell_inv.as<int32_t>(), E, rorder.as<T>(), stop);
+    r = rorder.as<T>();
+    zrow = ctx->sell_inv.as<int32_t>();
+  }
   PG_TRY(load_input(s, r, E, stop, stride, off));
   PG_TRY(forward(s, stop));
   const T* d = sizeof(T) == 8 ? reinterpret_cast<const T*>(diag32.as<float2>())
@@ -894,18 +912,27 @@ Status Net::apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T*
                  (double)E * (3.0 * sizeof(T) + 4.0 + 16.0 + 96.0));
   if (xspace)
     k_hx_out<T, true><<<nb(E), 256, 0, s>>>(r, slot, E, y.as<float>(), aux.as<float4>(), tang.as<float4>(),
-                                            scal.as<float>(), d, g[0][0], g[0][1], z, stop, stride, off);
+                                            scal.as<float>(), d, g[0][0], g[0][1], z, stop, stride, off, zrow);
   else
     k_hx_out<T, false><<<nb(E), 256, 0, s>>>(r, slot, E, y.as<float>(), aux.as<float4>(), tang.as<float4>(),
-                                             scal.as<float>(), d, g[0][0], g[0][1], z, stop, stride, off);
+                                             scal.as<float>(), d, g[0][0], g[0][1], z, stop, stride, off, zrow);
   PG_CUDA(cudaGetLastError());
   return Status{};
 }
 
 template Status Net::apply<float2>(cudaStream_t, const float2*, const int32_t*, int64_t, float2*, bool,
-                                  const int*, int64_t, int64_t);
+                                  const int*, int64_t, int64_t, bool);
 template Status Net::apply<double2>(cudaStream_t, const double2*, const int32_t*, int64_t, double2*, bool,
-                                   const int*, int64_t, int64_t);
+                                   const int*, int64_t, int64_t, bool);
+
+Status Net::renumber(petgem_ctx* c) {
+  if (!c->sell_ok) return Status{PETGEM_ERR_UNSUPPORTED, "learned network: the mesh has no SELL-32 layout"};
+  if (rorder.bytes < (size_t)c->n_edges * sizeof(double2)) {
+    PG_TRY(rorder.reserve((size_t)c->n_edges * sizeof(double2)));
+    ++alloc_gen;
+  }
+  return Status{};
+}
 
 // One training sample, r = the residual of a solver iterate (complex128 edge vector).  Loss: the
 // residual angle L = 1 - |<r, A z>|^2 / (|r|^2 |A z|^2) of the preconditioned direction
@@ -919,7 +946,7 @@ Status Net::sample_grad(cudaStream_t s, petgem_ctx* c, const double2* r, const i
   double2* gw = gtmp.as<double2>();
   k_hx_out<double2, false><<<nb(E), 256, 0, s>>>(r, slot, E, y.as<float>(), aux.as<float4>(), tang.as<float4>(),
                                                  scal.as<float>(), c->diag.as<double2>(), g[0][0], g[0][1], zu,
-                                                 nullptr, 1, 0);
+                                                 nullptr, 1, 0, nullptr);
   k_ahat_apply<<<nb(E), 256, 0, s>>>(c->row_ptr.as<int64_t>(), c->col.as<int32_t>(), c->val.as<double2>(),
                                      c->diag.as<double2>(), zu, E, w);
   k_angle_dots<<<1, 1024, 0, s>>>(r, w, E, dvec.as<double>(), loss_acc.as<double>());
