@@ -579,7 +579,8 @@ Status run_cycle(petgem_ctx* c, const T* ahat, int m, int orth, double tol_abs, 
                                     (uint64_t)(uintptr_t)c->val.ptr, (uint64_t)(uintptr_t)S->r.ptr,
                                     (uint64_t)learned, (uint64_t)(uintptr_t)Z, (uint64_t)(uintptr_t)c->net,
                                     (uint64_t)(c->net ? c->net->alloc_gen : 0),
-                                    (uint64_t)(uintptr_t)c->slots.ptr, (uint64_t)(uintptr_t)c->diag.ptr});
+                                    (uint64_t)(uintptr_t)c->slots.ptr, (uint64_t)(uintptr_t)c->diag.ptr,
+                                    (uint64_t)(uintptr_t)c->sell_inv.ptr});
     if (!S->graph || S->graph_key != key) {
       if (S->graph) cudaGraphExecDestroy(S->graph);
       S->graph = nullptr;

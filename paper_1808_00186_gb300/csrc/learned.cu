@@ -842,6 +842,9 @@ Status Net::backward(cudaStream_t s, bool acc) {
 Status Net::prepare_aux(petgem_ctx* c) {
   cudaStream_t s = c->stream;
   const int gx = g[0][0], gy = g[0][1], gz = g[0][2];
+  // captured graphs hold these buffers' addresses: the generation moves only when one of them
+  // moved (a new mesh or assembly of the same sizes keeps the graphs)
+  const void* before[6] = {slot_edge.ptr, tang.ptr, aux.ptr, nodes8.ptr, npart.ptr, diag32.ptr};
   if (geom_version != c->mesh_version) {
     PG_TRY(slot_edge.reserve((size_t)V[0] * 7 * sizeof(int32_t)));
     PG_TRY(tang.reserve((size_t)V[0] * 7 * sizeof(float4)));
@@ -852,7 +855,6 @@ Status Net::prepare_aux(petgem_ctx* c) {
     PG_CUDA(cudaGetLastError());
     geom_version = c->mesh_version;
     aux_version = -1;
-    ++alloc_gen;
   }
   if (aux_version != c->assembly_version) {
     PG_TRY(aux.reserve((size_t)V[0] * sizeof(float4)));
@@ -865,6 +867,12 @@ Status Net::prepare_aux(petgem_ctx* c) {
     PG_CUDA(cudaGetLastError());
     aux_version = c->assembly_version;
   }
+  const void* after[6] = {slot_edge.ptr, tang.ptr, aux.ptr, nodes8.ptr, npart.ptr, diag32.ptr};
+  for (int k = 0; k < 6; ++k)
+    if (before[k] != after[k]) {
+      ++alloc_gen;
+      break;
+    }
   return Status{};
 }
 

@@ -307,3 +307,26 @@ def test_learned_block_fgmres_matches_oracle_and_single_source_solves(precision)
         assert abs(ib[s]["iters"] - isg[s]["iters"]) <= 0.1 * isg[s]["iters"] + 5, (s, ib[s], isg[s])
     assert np.linalg.norm(rcv.cpu().numpy() - rr) / np.linalg.norm(rr) <= 1e-6
     print("\nlearned block / single-source iterations:", [(i["iters"], j["iters"]) for i, j in zip(ib, isg)])
+
+
+def test_learned_cycle_graph_replayed_for_another_model_of_the_same_size():
+    """A captured learned cycle is kept when a new mesh and assembly of the same sizes move none
+    of its buffers: the second model's solve replays the first model's graph and must equal its
+    own direct launches bit for bit."""
+    n = 10
+    p = np.load(PL.WEIGHTS)
+    models = [PL.random_block_model(n, seed) for seed in (10005, 10006)]
+    out = {}
+    with api.Context(0) as ctx:
+        for g in (1, 0):
+            for k, m in enumerate(models):
+                ctx.mesh(m.mesh.nodes, m.mesh.tets)
+                ctx.assemble(m.freq, m.sigma, m.sigma_p, m.sources)
+                api.petgem_learned_create(ctx.h, n, n, n)
+                if not out:
+                    api.petgem_learned_params(ctx.h, set_params=p)
+                x, info, st = ctx.solve(precision=api.PREC_MIXED, precond=api.PRECOND_LEARNED, use_graphs=g)
+                assert st == api.OK and info[0]["true_rel_residual"] <= 1e-8
+                out[(g, k)] = (x.cpu().numpy(), info)
+    for k in range(2):
+        assert np.array_equal(out[(1, k)][0], out[(0, k)][0]) and out[(1, k)][1] == out[(0, k)][1]
