@@ -405,7 +405,8 @@ __global__ void k_hx_out(const T* __restrict__ r, const int32_t* __restrict__ sl
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= E) return;
   const int32_t sl = slot[e];
-  const T re = r[e * stride + off];
+  const int64_t er = zrow ? (int64_t)zrow[e] : e;  // zrow: r and z in the SELL-32 row order
+  const T re = r[er * stride + off];
   R cr = 0, ci = 0;
   if (sl >= 0) {
     const int64_t lo = sl / 7;
@@ -439,15 +440,13 @@ __global__ void k_hx_out(const T* __restrict__ r, const int32_t* __restrict__ sl
     o.x = rr + (dr * cr - di * ci);
     o.y = ri + (dr * ci + di * cr);
   }
-  z[(zrow ? (int64_t)zrow[e] : e) * stride + off] = o;  // zrow: z in the SELL-32 row order
+  z[er * stride + off] = o;
 }
-// out[e] = in[inv[e]]: a vector in the SELL-32 row order back in edge order.
-template <typename T>
-__global__ void k_from_rows(const T* __restrict__ in, const int32_t* __restrict__ inv, int64_t n, T* __restrict__ out,
-                            const int* __restrict__ stop) {
-  if (stop && *stop) return;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e < n) out[e] = in[inv[e]];
+// Slot si -> the SELL-32 row of its edge, inv[slot_edge[si]] (-1 for a slot without an edge).
+__global__ void k_renumber_slots(const int32_t* __restrict__ slot_edge, int64_t n_slots, const int32_t* __restrict__ inv,
+                                 int32_t* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n_slots) out[i] = slot_edge[i] >= 0 ? inv[slot_edge[i]] : -1;
 }
 // The diagonal of A in single precision, for the complex64 application.
 __global__ void k_diag_f32(const double2* __restrict__ d, int64_t n, float2* __restrict__ o) {
@@ -879,7 +878,8 @@ Status Net::prepare_aux(petgem_ctx* c) {
 // Network input x0 from an edge vector r (a residual): the gathered, scaled node fields, the scale
 // s in scal[0..1] (1 / s, s), the two features.
 template <typename T>
-Status Net::load_input(cudaStream_t s, const T* r, int64_t E, const int* stop, int64_t stride, int64_t off) {
+Status Net::load_input(cudaStream_t s, const T* r, int64_t E, const int* stop, int64_t stride, int64_t off,
+                       bool renum) {
   (void)E;
   const int gx = g[0][0], gy = g[0][1], gz = g[0][2];
   const unsigned blocks = nb(V[0]);
@@ -888,7 +888,8 @@ Status Net::load_input(cudaStream_t s, const T* r, int64_t E, const int* stop, i
   {
     KernelTimer kt(ctx, sizeof(T) == 8 ? "hx_in_c64" : "hx_in_c128",
                    2.0 * sizeof(T) * (double)ctx->n_edges + (double)V[0] * (14.0 * 20.0 + 32.0 + 16.0));
-    k_hx_in<T><<<blocks, 256, 0, s>>>(r, slot_edge.as<int32_t>(), tang.as<float4>(), aux.as<float4>(), gx, gy, gz,
+    k_hx_in<T><<<blocks, 256, 0, s>>>(r, (renum ? slot_edge_r : slot_edge).as<int32_t>(), tang.as<float4>(),
+                                      aux.as<float4>(), gx, gy, gz,
                                       nodes8.as<float>(), npart.as<double>(), stop, stride, off);
   }
   const int64_t n_in = (int64_t)std::max(gx - 2, 0) * std::max(gy - 2, 0) * std::max(gz - 2, 0);
@@ -902,16 +903,11 @@ Status Net::load_input(cudaStream_t s, const T* r, int64_t E, const int* stop, i
 template <typename T>
 Status Net::apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T* z, bool xspace,
                   const int* stop, int64_t stride, int64_t off, bool renum) {
-  // renum: both maps run in edge order, where an edge's node data and a node's edges are adjacent
-  // (measured faster than running the edge-wise map over the SELL-32 rows); r is gathered into
-  // edge order and z written back to its rows through zrow
-  const int32_t* zrow = nullptr;
-  if (renum) {
-    k_from_rows<T><<<nb(E), 256, 0, s>>>(r, ctx->sell_inv.as<int32_t>(), E, rorder.as<T>(), stop);
-    r = rorder.as<T>();
-    zrow = ctx->sell_inv.as<int32_t>();
-  }
-  PG_TRY(load_input(s, r, E, stop, stride, off));
+  // renum: the node-wise map gathers r through its slots' SELL-32 rows; the edge-wise map runs in
+  // edge order, where an edge's node data are adjacent (measured faster than over the rows), and
+  // reads r and writes z at the edge's row
+  const int32_t* zrow = renum ? ctx->sell_inv.as<int32_t>() : nullptr;
+  PG_TRY(load_input(s, r, E, stop, stride, off, renum));
   PG_TRY(forward(s, stop));
   const T* d = sizeof(T) == 8 ? reinterpret_cast<const T*>(diag32.as<float2>())
                               : reinterpret_cast<const T*>(ctx->diag.as<double2>());
@@ -935,10 +931,15 @@ template Status Net::apply<double2>(cudaStream_t, const double2*, const int32_t*
 
 Status Net::renumber(petgem_ctx* c) {
   if (!c->sell_ok) return Status{PETGEM_ERR_UNSUPPORTED, "learned network: the mesh has no SELL-32 layout"};
-  if (rorder.bytes < (size_t)c->n_edges * sizeof(double2)) {
-    PG_TRY(rorder.reserve((size_t)c->n_edges * sizeof(double2)));
-    ++alloc_gen;
-  }
+  if (renum_mesh == c->mesh_version) return Status{};
+  const int64_t ns = V[0] * 7;
+  const void* before = slot_edge_r.ptr;
+  PG_TRY(slot_edge_r.reserve((size_t)ns * sizeof(int32_t)));
+  if (slot_edge_r.ptr != before) ++alloc_gen;
+  k_renumber_slots<<<nb(ns), 256, 0, c->stream>>>(slot_edge.as<int32_t>(), ns, c->sell_inv.as<int32_t>(),
+                                                  slot_edge_r.as<int32_t>());
+  PG_CUDA(cudaGetLastError());
+  renum_mesh = c->mesh_version;
   return Status{};
 }
 

@@ -48,7 +48,8 @@ struct Net {
   // slot's unit tangent and inverse length, per-node scales (sg, sp_x, sp_y, sp_z), the gathered
   // node fields [V0][8] and per-block partial sums
   DevBuf slot_edge, tang, aux, nodes8, npart, diag32;  // diag32: diag(A) as complex64
-  DevBuf rorder;                                       // r in edge order (renumbered application)
+  DevBuf slot_edge_r;                                  // slot -> SELL-32 row of its edge (renumbered application)
+  int64_t renum_mesh = -1;
   int64_t aux_version = -1;    // assembly the scales belong to
   int64_t geom_version = -1;   // mesh the slot map and tangents belong to
   int64_t alloc_gen = 0;       // bumped whenever a buffer may have moved (captured graphs key on it)
@@ -70,16 +71,16 @@ struct Net {
   Status backward(cudaStream_t s, bool acc);
   Status prepare_aux(petgem_ctx* c);
   template <typename T> Status load_input(cudaStream_t s, const T* r, int64_t E, const int* stop = nullptr,
-                                          int64_t stride = 1, int64_t off = 0);
+                                          int64_t stride = 1, int64_t off = 0, bool renum = false);
   // z = D (D^{-1} r + G phi + Pi w) (the solver's Jacobi-scaled variables) or, with xspace,
   // z = D^{-1} r + G phi + Pi w, for the residual r of E entries.  Entry e of r and z sits at
   // e stride + off (one source of an interleaved block vector: stride = the group size).
-  // renum: r and z are in the SELL-32 row order of the context (renumber() first): r is gathered
-  // into the edge order the maps use (where an edge's node data are adjacent), z scattered back.
+  // renum: r and z are in the SELL-32 row order of the context (renumber() first): the node-wise
+  // map gathers r through the rows of its slots' edges, the edge-wise map runs in edge order.
   template <typename T> Status apply(cudaStream_t s, const T* r, const int32_t* slot, int64_t E, T* z,
                                      bool xspace = false, const int* stop = nullptr, int64_t stride = 1,
                                      int64_t off = 0, bool renum = false);
-  // Workspace of the renumbered application (before any stream capture).
+  // The slot map of the renumbered application (after prepare_aux, before any stream capture).
   Status renumber(petgem_ctx* c);
   Status sample_grad(cudaStream_t s, petgem_ctx* c, const double2* r, const int32_t* slot, int64_t E, bool acc);
   Status adam_step(cudaStream_t s, float lr, float gscale);
