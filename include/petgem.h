@@ -363,8 +363,8 @@ int petgem_learned_apply(petgem_ctx *ctx, const void *r, void *z);
  * {16, 32}.  petgem_nn_conv3d: y[v][co] = bias[co] + sum_t,ci W[t][co][ci] x[v + d_t][ci], ReLU
  * when relu != 0, y BF16 (y_fp32 = 0) or FP32 [V][cout].  petgem_nn_conv3d_wgrad: dw[t][co][ci] =
  * sum_v dy[v][co] x[v + d_t][ci] (FP32).  All pointers device; work ordered on `stream`.
- * petgem_nn_conv3d's x, w and y must be 16-byte aligned (the kernel moves 8 channels at a time;
- * its input reaches shared memory through a TMA tensor map).
+ * petgem_nn_conv3d's x, w and y must be 16-byte aligned (the kernel copies 8 channels, 16 bytes,
+ * at a time into shared memory and stores its output in 16-byte pieces).
  * Errors: a dimension < 1, a null pointer, or (petgem_nn_conv3d) an x, w or y not 16-byte
  * aligned: PETGEM_ERR_INVALID_ARG; gx gy gz 32 >= 2^31 (the kernels index voxel channels in 32
  * bits) or cin / cout not in {16, 32}: PETGEM_ERR_UNSUPPORTED, nothing launched. */
