@@ -1,5 +1,5 @@
-// Learned preconditioner: a small 4-level 3-D convolutional network on the node lattice of a
-// Kuhn-split mesh, acting through the two auxiliary spaces of lowest-order edge elements (the
+// Learned preconditioner: a small 3-D convolutional U-Net on the node lattice of a Kuhn-split
+// mesh, acting through the two auxiliary spaces of lowest-order edge elements (the
 // Hiptmair-Xu decomposition): nodal gradients G phi, which the curl-curl term annihilates, and
 // nodal vector fields Pi w.  For a residual r the preconditioner returns
 //     z = D^{-1} r + G phi + Pi w,   (phi, w) = network(G^T r, Pi^T r, model features),
@@ -12,13 +12,15 @@
 // Jacobi-scaled variables, D z).  Not part of the paper: the paper solves with GMRES / SQMR /
 // MUMPS (Sections 5.1-5.3); the plain solver stays the fallback.
 //
-// Network (levels G0 = lattice nodes, G1..G3 = successive 2x poolings, BF16 activations, FP32
-// accumulation and master weights):
-//   a1 = relu(c1 16->16 on G0)        p1 = pool a1     a2 = relu(c2 16->32 on G1)
-//   p2 = pool a2                      a3 = relu(c3 32->32 on G2)
-//   p3 = pool a3                      a4 = relu(c4 32->32 on G3)
-//   a5 = relu(c5 32->32 on up(a4) + a3)       a6 = relu(c6 32->16 on up(a5) + a2)
-//   y  = c7 16->16 on up(a6) + a1     (channels 8..15 of y unused)
+// Network (levels G0 = lattice nodes, G1 .. G(L-1) = successive 2x average poolings until the
+// coarsest level has at most 3 nodes per axis, L >= 3; BF16 activations, FP32 accumulation and
+// master weights).  Seven weight sets serve any depth:
+//   e0 = relu(c1 16->16 on G0)                  e1 = relu(c2 16->32 on pool e0)
+//   e_l = relu(c3 32->32 on pool e_(l-1))       for 2 <= l <= L-2 (c3 shared by these levels)
+//   e_(L-1) = relu(c4 32->32 on pool e_(L-2))   (the coarsest level)
+//   d_l = relu(c5 32->32 on up(d_(l+1)) + e_l)  for L-2 >= l >= 2 (d_(L-1) = e_(L-1); c5 shared)
+//   d1 = relu(c6 32->16 on up(d2) + e1)         y = c7 16->16 on up(d1) + e0
+//   (channels 8..15 of y unused; with L = 3 the c3 / c5 levels are absent)
 // Input channels (sg = |diag(G^T A G)|^{-1/2}, sp = |diag(Pi^T A Pi)|^{-1/2} per node and axis,
 // zero on boundary nodes; fg = sg G^T r, fp = sp Pi^T r; s = RMS of (fg, fp) over the interior
 // nodes' four complex values): Re fg / s, Im fg / s, Re fp / s (x, y, z), Im fp / s (x, y, z),

@@ -1,6 +1,8 @@
-// Kernels of the learned preconditioner's network: 3x3x3 convolutions as implicit GEMMs on the
-// tcgen05 tensor cores (forward, and the input gradient through flipped weights), the weight
-// gradient as a split-K tcgen05 GEMM, and the grid element-wise operations.
+// Kernels of the learned preconditioner's network: the 3x3x3 convolution on the tcgen05 tensor
+// cores (forward, and the input gradient through flipped weights; one halo brick per CTA, the
+// taps as descriptor offsets into it), the packing of its weights into the kernel's shared-memory
+// image, and the weight gradient as a split-K tcgen05 GEMM.  Pooling, upsampling and the
+// auxiliary maps are in learned.cu.
 //
 // Grid tensors: BF16 [V][C], voxel v = x + gx (y + gy z), channels innermost (C = 16 or 32).
 // Convolution weights: W[t][co][ci], tap t = (dx+1) + 3 (dy+1) + 9 (dz+1), zero "same" padding:
